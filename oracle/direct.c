@@ -1,0 +1,253 @@
+/*
+ * CPU ORACLE -- test infrastructure only.  Plain FP64 direct sums of the kernel functions of
+ * Yan & Blackwell, "Kernel Aggregated Fast Multipole Method" (arXiv:2010.15155).
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load this code;
+ * the CUDA evaluator never does.
+ *
+ * Every routine ACCUMULATES into g (g += sum over sources), loops over all target/source
+ * pairs in the plainest order (targets outer, sources inner) and skips pairs with r^2 == 0
+ * (the self pair when sources and targets are the same set; any other coincident pair
+ * contributes nothing).  r = x - y (target minus source), viscosity mu = 1.
+ * Row-major layouts: x[nt][3], y[ns][3], s[ns][k_s], g[nt][k_t].
+ */
+#include <math.h>
+#include <stdint.h>
+
+#define PI 3.14159265358979323846
+
+/* Laplace single layer, Sec. II.A: L = 1/(4 pi r).  s: [q], g: [phi]. */
+void orc_laplace(const double* x, int64_t nt, const double* y, int64_t ns,
+                 const double* s, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double acc = 0.0;
+    for (int64_t b = 0; b < ns; ++b) {
+      double r0 = x[3 * a] - y[3 * b], r1 = x[3 * a + 1] - y[3 * b + 1],
+             r2 = x[3 * a + 2] - y[3 * b + 2];
+      double rr = r0 * r0 + r1 * r1 + r2 * r2;
+      if (rr == 0.0) continue;
+      acc += s[b] / (4.0 * PI * sqrt(rr));
+    }
+    g[a] += acc;
+  }
+}
+
+/* Laplace charges -> [phi, grad phi (3), grad grad phi (6: xx xy xz yy yz zz)], the
+ * combined kernel L + grad L + grad grad L of Table tab:ktab_lapqdpgradgrad.
+ * d/dx_i (1/r) = -r_i/r^3 ; d2/dx_i dx_j (1/r) = (3 r_i r_j - delta_ij r^2)/r^5.  g: 10 cols. */
+void orc_laplace_pgradgrad(const double* x, int64_t nt, const double* y, int64_t ns,
+                           const double* s, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double acc[10] = {0};
+    for (int64_t b = 0; b < ns; ++b) {
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1],
+                     x[3 * a + 2] - y[3 * b + 2]};
+      double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (rr == 0.0) continue;
+      double rn = sqrt(rr), q = s[b] / (4.0 * PI);
+      double r3 = rr * rn, r5 = r3 * rr;
+      acc[0] += q / rn;
+      for (int i = 0; i < 3; ++i) acc[1 + i] += -q * r[i] / r3;
+      int c = 4;
+      for (int i = 0; i < 3; ++i)
+        for (int j = i; j < 3; ++j) {
+          double h = 3.0 * r[i] * r[j] / r5 - (i == j ? 1.0 / r3 : 0.0);
+          acc[c++] += q * h;
+        }
+    }
+    for (int k = 0; k < 10; ++k) g[10 * a + k] += acc[k];
+  }
+}
+
+/* Laplace dipole potential, Sec. II.A: phi = L^D_j d_j with L^D_j = -dL/dx_j = r_j/(4 pi r^3).
+ * s: [d1 d2 d3], g: [phi]. */
+void orc_laplace_dipole(const double* x, int64_t nt, const double* y, int64_t ns,
+                        const double* s, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double acc = 0.0;
+    for (int64_t b = 0; b < ns; ++b) {
+      double r0 = x[3 * a] - y[3 * b], r1 = x[3 * a + 1] - y[3 * b + 1],
+             r2 = x[3 * a + 2] - y[3 * b + 2];
+      double rr = r0 * r0 + r1 * r1 + r2 * r2;
+      if (rr == 0.0) continue;
+      double rn = sqrt(rr);
+      acc += (r0 * s[3 * b] + r1 * s[3 * b + 1] + r2 * s[3 * b + 2]) / (4.0 * PI * rr * rn);
+    }
+    g[a] += acc;
+  }
+}
+
+/* Stokeslet, Sec. II.B: G_ij = (delta_ij / r + r_i r_j / r^3) / (8 pi).  s: f (3), g: u (3). */
+void orc_stokeslet(const double* x, int64_t nt, const double* y, int64_t ns,
+                   const double* s, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double u[3] = {0, 0, 0};
+    for (int64_t b = 0; b < ns; ++b) {
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1],
+                     x[3 * a + 2] - y[3 * b + 2]};
+      double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (rr == 0.0) continue;
+      double rn = sqrt(rr);
+      const double* f = s + 3 * b;
+      double rf = r[0] * f[0] + r[1] * f[1] + r[2] * f[2];
+      for (int i = 0; i < 3; ++i)
+        u[i] += (f[i] / rn + r[i] * rf / (rr * rn)) / (8.0 * PI);
+    }
+    for (int i = 0; i < 3; ++i) g[3 * a + i] += u[i];
+  }
+}
+
+/* RPY flow field and its Laplacian, Eqs. RPYflow/RPYkernel and Table tab:ktab_rpy:
+ *   u = G f + (b^2/6) lap(G) f,   lap(u) = lap(G) f   (lap lap G = 0),
+ *   lap(G)_ij = (delta_ij / r^3 - 3 r_i r_j / r^5) / (4 pi).
+ * s: [f1 f2 f3 b] (4), g: [u (3), lap u (3)] (6).  With b = 0 this is G + lap G. */
+void orc_rpy(const double* x, int64_t nt, const double* y, int64_t ns,
+             const double* s, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double u[3] = {0, 0, 0}, lu[3] = {0, 0, 0};
+    for (int64_t b = 0; b < ns; ++b) {
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1],
+                     x[3 * a + 2] - y[3 * b + 2]};
+      double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (rr == 0.0) continue;
+      double rn = sqrt(rr), r3 = rr * rn, r5 = r3 * rr;
+      const double* f = s + 4 * b;
+      double bb = f[3] * f[3];
+      double rf = r[0] * f[0] + r[1] * f[1] + r[2] * f[2];
+      for (int i = 0; i < 3; ++i) {
+        double gf = (f[i] / rn + r[i] * rf / r3) / (8.0 * PI);
+        double lgf = (f[i] / r3 - 3.0 * r[i] * rf / r5) / (4.0 * PI);
+        u[i] += gf + bb / 6.0 * lgf;
+        lu[i] += lgf;
+      }
+    }
+    for (int i = 0; i < 3; ++i) {
+      g[6 * a + i] += u[i];
+      g[6 * a + 3 + i] += lu[i];
+    }
+  }
+}
+
+/* Stokes double layer, Eqs. stkdlp / stkdlvel:
+ *   p   = (1/4pi) (-3 r_j r_k / r^5 + delta_jk / r^3) D_jk,
+ *   u_i = -(3/8pi) r_i r_j r_k D_jk / r^5.
+ * s: D flattened row-major (D_jk at 3j+k, 9), g: [p, u1, u2, u3] (4). */
+void orc_stokes_dl(const double* x, int64_t nt, const double* y, int64_t ns,
+                   const double* s, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double acc[4] = {0, 0, 0, 0};
+    for (int64_t b = 0; b < ns; ++b) {
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1],
+                     x[3 * a + 2] - y[3 * b + 2]};
+      double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (rr == 0.0) continue;
+      double rn = sqrt(rr), r3 = rr * rn, r5 = r3 * rr;
+      const double* D = s + 9 * b;
+      double rDr = 0.0, tr = D[0] + D[4] + D[8];
+      for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) rDr += r[j] * D[3 * j + k] * r[k];
+      acc[0] += (-3.0 * rDr / r5 + tr / r3) / (4.0 * PI);
+      for (int i = 0; i < 3; ++i) acc[1 + i] += -3.0 / (8.0 * PI) * r[i] * rDr / r5;
+    }
+    for (int k = 0; k < 4; ++k) g[4 * a + k] += acc[k];
+  }
+}
+
+/* Pair mobility of two spheres (radii ai at the target, aj at the source), r = x - y.
+ * Far form (r > ai + aj): the assembled RPY tensor of Eqs. RPYkernel/RPYtrgvel,
+ *   M = G + (ai^2 + aj^2)/6 lap G.
+ * Overlapping spheres (r <= ai + aj), which the paper defers to a post-processing pass
+ * (Sec. II.B, citing Zuk et al. 2014) -- the unequal-radius regularisation:
+ *   |ai-aj| < r <= ai+aj : M = [A I + B rhat rhat] / (6 pi ai aj),
+ *        A = (16 r^3 (ai+aj) - ((ai-aj)^2 + 3 r^2)^2) / (32 r^3),
+ *        B = 3 ((ai-aj)^2 - r^2)^2 / (32 r^3);
+ *   r <= |ai-aj|         : M = I / (6 pi max(ai, aj)).
+ * Writes the 3x3 tensor (row-major) into m.  r == 0 with ai == aj gives I/(6 pi a). */
+static void rpy_pair_tensor(const double r[3], double ai, double aj, double m[9]) {
+  double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  double rn = sqrt(rr);
+  double d = fabs(ai - aj), s = ai + aj;
+  double A, B;
+  if (rn > s) {
+    double c = (ai * ai + aj * aj);
+    A = (1.0 + c / (3.0 * rr)) / (8.0 * PI * rn);
+    B = (1.0 - c / rr) / (8.0 * PI * rn);
+  } else if (rn > d) {
+    double r3 = rr * rn, t = d * d + 3.0 * rr, e = d * d - rr;
+    A = (16.0 * r3 * s - t * t) / (32.0 * r3) / (6.0 * PI * ai * aj);
+    B = 3.0 * e * e / (32.0 * r3) / (6.0 * PI * ai * aj);
+  } else {
+    A = 1.0 / (6.0 * PI * (ai > aj ? ai : aj));
+    B = 0.0;
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double rh = rn > 0.0 ? r[i] * r[j] / rr : 0.0;
+      m[3 * i + j] = (i == j ? A : 0.0) + B * rh;
+    }
+}
+
+/* 3x3 pair mobility for a single pair (exposed for the pins). */
+void orc_rpy_pair(const double* r, double ai, double aj, double* m) { rpy_pair_tensor(r, ai, aj, m); }
+
+/* Sphere velocities with the overlap regularisation, brute force over all pairs:
+ *   U_a = sum_{b != a} M(x_a - y_b; a_a, b_b) f_b
+ * with M the far form outside contact and the overlap form inside.  Pairs with r == 0 and
+ * the same index are skipped (self mobility is not part of the kernel sum).
+ * x: [nt][3], at: [nt] target radii, y: [ns][3], s: [ns][4] = (f, b), g: [nt][3].
+ * same_set != 0 means targets and sources are the same list (index identity = self). */
+void orc_rpy_velocity(const double* x, const double* at, int64_t nt, const double* y,
+                      int64_t ns, const double* s, int same_set, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double u[3] = {0, 0, 0}, m[9];
+    for (int64_t b = 0; b < ns; ++b) {
+      if (same_set && a == b) continue;
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1],
+                     x[3 * a + 2] - y[3 * b + 2]};
+      double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (rr == 0.0 && !(s[4 * b + 3] > 0.0 && at[a] > 0.0)) continue;
+      rpy_pair_tensor(r, at[a], s[4 * b + 3], m);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) u[i] += m[3 * i + j] * s[4 * b + j];
+    }
+    for (int i = 0; i < 3; ++i) g[3 * a + i] += u[i];
+  }
+}
+
+/* Overlap correction only: for pairs within contact (0 < r <= ai + aj, or r == 0 between
+ * different indices) add (M_overlap - M_far) f, where M_far is the far form the kernel sum
+ * already used (taken as 0 when r == 0, because the kernel sum skips coincident pairs).
+ * Used by the plain KAFMM after the tree traversal, Sec. II.B. */
+void orc_rpy_overlap_correction(const double* x, const double* at, int64_t nt,
+                                const double* y, int64_t ns, const double* s, int same_set,
+                                double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double u[3] = {0, 0, 0}, m[9];
+    for (int64_t b = 0; b < ns; ++b) {
+      if (same_set && a == b) continue;
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1],
+                     x[3 * a + 2] - y[3 * b + 2]};
+      double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      double ai = at[a], aj = s[4 * b + 3];
+      if (sqrt(rr) > ai + aj) continue;
+      rpy_pair_tensor(r, ai, aj, m);
+      if (rr > 0.0) {
+        double rn = sqrt(rr), c = ai * ai + aj * aj;
+        double A = (1.0 + c / (3.0 * rr)) / (8.0 * PI * rn);
+        double B = (1.0 - c / rr) / (8.0 * PI * rn);
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) m[3 * i + j] -= (i == j ? A : 0.0) + B * r[i] * r[j] / rr;
+      }
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) u[i] += m[3 * i + j] * s[4 * b + j];
+    }
+    for (int i = 0; i < 3; ++i) g[3 * a + i] += u[i];
+  }
+}

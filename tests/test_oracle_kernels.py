@@ -1,0 +1,267 @@
+"""Pins for the oracle's direct kernel sums (oracle/direct.c).
+
+Each test checks the oracle against something other than its own formula: conservation laws
+(Gauss's law, momentum balance, the double-layer net flux stated in Sec. II.C), PDEs the
+kernels solve (checked by finite differences), textbook special cases (equal-radius RPY and
+its overlap form), symmetry, and the SPD property of the RPY mobility (Sec. II.B).
+"""
+import numpy as np
+import pytest
+
+from oracle import direct as D
+
+PI = np.pi
+
+
+def sphere_quadrature(R, centre=(0.0, 0.0, 0.0), nt=40, nphi=80):
+    """Gauss-Legendre in cos(theta) x trapezoid in phi: nodes, outward normals, weights."""
+    ct, wt = np.polynomial.legendre.leggauss(nt)
+    phi = np.arange(nphi) * 2 * PI / nphi
+    st = np.sqrt(1 - ct ** 2)
+    n = np.stack([np.outer(st, np.cos(phi)), np.outer(st, np.sin(phi)),
+                  np.outer(ct, np.ones(nphi))], axis=-1).reshape(-1, 3)
+    w = np.outer(wt, np.full(nphi, 2 * PI / nphi)).reshape(-1) * R * R
+    return np.asarray(centre) + R * n, n, w
+
+
+def fd_grad(fun, x, h=1e-4):
+    """Central-difference gradient of a vector field: returns [..., comp, dir]."""
+    out = []
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = h
+        out.append((fun(x + e) - fun(x - e)) / (2 * h))
+    return np.stack(out, axis=-1)
+
+
+def fd_laplacian(fun, x, h=1e-3):
+    acc = -6.0 * fun(x)
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = h
+        acc = acc + fun(x + e) + fun(x - e)
+    return acc / (h * h)
+
+
+def test_surface_point_count_formula():
+    """M = 6(m-1)^2 + 2 boundary nodes of an m^3 grid (Sec. III) = m^3 - (m-2)^3."""
+    from oracle.kafmm import surface
+    for m in range(2, 17):
+        assert len(surface(m)) == 6 * (m - 1) ** 2 + 2 == m ** 3 - (m - 2) ** 3
+
+
+def test_laplace_gauss_law_and_harmonic():
+    """Flux of grad phi through any sphere around a charge q is -q; phi is harmonic."""
+    y = np.array([[0.1, -0.2, 0.05]])
+    q = np.array([[0.7]])
+    for R in (0.3, 1.7):
+        pts, n, w = sphere_quadrature(R, centre=(0.2, -0.1, 0.0))
+        g = D.direct("laplace_pgradgrad", pts, y, q)
+        flux = np.sum(w * np.sum(g[:, 1:4] * n, axis=1))
+        assert abs(flux + 0.7) < 1e-10
+    x = np.array([0.9, 0.4, -0.3])
+    lap = fd_laplacian(lambda z: D.direct("laplace", z[None], y, q)[0, 0], x)
+    assert abs(lap) < 1e-5
+
+
+def test_laplace_derivatives_match_finite_differences():
+    rng = np.random.default_rng(7)
+    y = rng.random((5, 3))
+    q = rng.standard_normal((5, 1))
+    x = np.array([1.3, -0.4, 0.8])
+    g = D.direct("laplace_pgradgrad", x[None], y, q)[0]
+    assert abs(g[0] - D.direct("laplace", x[None], y, q)[0, 0]) < 1e-14
+    grad = fd_grad(lambda z: D.direct("laplace", z[None], y, q)[0], x)[0]
+    assert np.allclose(g[1:4], grad, rtol=1e-7, atol=1e-9)
+    hess = fd_grad(lambda z: D.direct("laplace_pgradgrad", z[None], y, q)[0, 1:4], x)
+    h6 = [hess[0, 0], hess[0, 1], hess[0, 2], hess[1, 1], hess[1, 2], hess[2, 2]]
+    assert np.allclose(g[4:10], h6, rtol=1e-6, atol=1e-8)
+    assert abs(g[4] + g[7] + g[9]) < 1e-10 * np.abs(g[4:10]).max()  # trace-free (harmonic)
+
+
+def test_laplace_dipole_is_limit_of_charge_pair():
+    """A dipole d = q e (e -> 0) equals charges +q at y + e/2 and -q at y - e/2."""
+    y = np.array([0.2, 0.3, -0.1])
+    d = np.array([0.4, -1.1, 0.6])
+    x = np.array([[1.0, 0.5, 0.7], [-0.6, 0.2, 0.4]])
+    eps = 1e-5
+    ys = np.stack([y + eps * d / 2, y - eps * d / 2])
+    pair = D.direct("laplace", x, ys, np.array([1.0 / eps, -1.0 / eps]))
+    dip = D.direct("laplace_dipole", x, y[None], d[None])
+    assert np.allclose(dip, pair, rtol=1e-8)
+
+
+def test_stokeslet_divergence_free_symmetric_and_stokes_equation():
+    rng = np.random.default_rng(3)
+    y = rng.random((3, 3))
+    f = rng.standard_normal((3, 3))
+    x = np.array([1.4, 0.9, -0.5])
+    ufun = lambda z: D.direct("stokeslet", z[None], y, f)[0]
+    J = fd_grad(ufun, x)
+    assert abs(np.trace(J)) < 1e-6 * np.abs(J).max()           # div u = 0 (Sec. II.C)
+    # lap u = grad p with p the pressure of Eq. stkslp, taken here as -div of the Laplace
+    # potentials of the force components (a route independent of the Stokeslet routine)
+    pfun = lambda z: -sum(D.direct("laplace_pgradgrad", z[None], y, f[:, j])[0, 1 + j]
+                          for j in range(3))
+    lap_u = fd_laplacian(ufun, x)
+    gp = fd_grad(lambda z: np.array([pfun(z)]), x)[0]
+    assert np.allclose(lap_u, gp, rtol=1e-5, atol=1e-7)
+    # symmetry G(x, y) = G(y, x)^T
+    a, b = np.array([[0.1, 0.2, 0.3]]), np.array([[0.7, -0.2, 0.5]])
+    Gab = np.stack([D.direct("stokeslet", a, b, e[None])[0] for e in np.eye(3)], axis=1)
+    Gba = np.stack([D.direct("stokeslet", b, a, e[None])[0] for e in np.eye(3)], axis=1)
+    assert np.allclose(Gab, Gba.T, rtol=1e-14)
+
+
+def test_stokeslet_momentum_balance_fixes_normalisation():
+    """For u = G f and p = f.r/(4 pi r^3): the traction sigma.n = (-p I + grad u + grad u^T) n
+    integrates to -f over any sphere around the point force (div sigma = -f delta)."""
+    f = np.array([[0.3, -1.2, 0.8]])
+    y = np.zeros((1, 3))
+    pts, n, w = sphere_quadrature(0.5, nt=24, nphi=48)
+    tot = np.zeros(3)
+    for xk, nk, wk in zip(pts, n, w):
+        J = fd_grad(lambda z: D.direct("stokeslet", z[None], y, f)[0], xk, h=1e-5)
+        p = -sum(D.direct("laplace_pgradgrad", xk[None], y, f[:, j])[0, 1 + j] for j in range(3))
+        sig = -p * np.eye(3) + J + J.T
+        tot += wk * sig @ nk
+    assert np.allclose(tot, -f[0], rtol=1e-6, atol=1e-7)
+
+
+def test_rpy_equal_radius_is_classical_rpy_and_biharmonic():
+    """[u, lap u] assembled as u + a^2/6 lap u (Eq. RPYtrgvel) with b = a equals the classical
+    Rotne-Prager tensor (1/8 pi r)[(1 + 2a^2/3r^2) I + (1 - 2a^2/r^2) rr/r^2] for r > 2a."""
+    a = 0.05
+    y = np.array([[0.0, 0.0, 0.0]])
+    x = np.array([[0.31, -0.12, 0.2]])
+    r = x[0] - y[0]
+    rn = np.linalg.norm(r)
+    for e in np.eye(3):
+        g = D.direct("rpy", x, y, np.concatenate([e, [a]])[None])[0]
+        ua = g[:3] + a * a / 6.0 * g[3:]
+        ref = ((1 + 2 * a * a / (3 * rn * rn)) * e
+               + (1 - 2 * a * a / (rn * rn)) * r * (r @ e) / (rn * rn)) / (8 * PI * rn)
+        assert np.allclose(ua, ref, rtol=1e-14, atol=1e-16)
+    # lap lap G = 0 (Sec. II.B): the Laplacian output is harmonic
+    fb = np.array([[0.2, 0.5, -0.4, 0.01]])
+    lap2 = fd_laplacian(lambda z: D.direct("rpy", z[None], y, fb)[0, 3:], np.array([0.6, 0.3, 0.2]))
+    assert np.abs(lap2).max() < 1e-4 * np.abs(D.direct("rpy", x, y, fb)[0, 3:]).max()
+    # lap u output equals the finite-difference Laplacian of the Stokeslet field
+    ufun = lambda z: D.direct("stokeslet", z[None], y, fb[:, :3])[0]
+    lapu = fd_laplacian(ufun, np.array([0.6, 0.3, 0.2]))
+    assert np.allclose(D.direct("rpy", np.array([[0.6, 0.3, 0.2]]), y, fb)[0, 3:], lapu,
+                       rtol=1e-5)
+
+
+def test_rpy_far_tends_to_stokeslet():
+    """RPY -> Stokeslet as a/r -> 0 with relative difference O(a^2/r^2)."""
+    y = np.zeros((1, 3))
+    x = np.array([[0.4, 0.3, -0.2]])
+    f = np.array([0.3, 0.1, -0.7])
+    u0 = D.direct("stokeslet", x, y, f[None])[0]
+    prev = None
+    for b in (1e-1, 1e-2, 1e-3):
+        u = D.direct("rpy", x, y, np.concatenate([f, [b]])[None])[0, :3]
+        rel = np.linalg.norm(u - u0) / np.linalg.norm(u0)
+        if prev is not None:
+            assert 80 < prev / rel < 120      # quadratic in b
+        prev = rel
+
+
+def test_rpy_overlap_continuity_and_equal_radius_form():
+    rng = np.random.default_rng(11)
+    rhat = rng.standard_normal(3)
+    rhat /= np.linalg.norm(rhat)
+    for ai, aj in ((0.03, 0.05), (0.05, 0.05), (0.02, 0.09)):
+        s, d = ai + aj, abs(ai - aj)
+        out = D.rpy_pair(rhat * s * (1 + 1e-12), ai, aj)
+        inn = D.rpy_pair(rhat * s * (1 - 1e-12), ai, aj)
+        assert np.allclose(out, inn, rtol=1e-9)                     # continuous at contact
+        if d > 0:
+            o2 = D.rpy_pair(rhat * d * (1 + 1e-12), ai, aj)
+            i2 = D.rpy_pair(rhat * d * (1 - 1e-12), ai, aj)
+            assert np.allclose(o2, i2, rtol=1e-9, atol=1e-12)       # continuous inside
+            assert np.allclose(i2, np.eye(3) / (6 * PI * max(ai, aj)), rtol=1e-14)
+    a = 0.04
+    for r in (0.01, 0.05, 0.079):
+        m = D.rpy_pair(rhat * r, a, a)
+        ref = ((1 - 9 * r / (32 * a)) * np.eye(3)
+               + (3 * r / (32 * a)) * np.outer(rhat, rhat)) / (6 * PI * a)
+        assert np.allclose(m, ref, rtol=1e-13)
+    assert np.allclose(D.rpy_pair(np.zeros(3), a, a), np.eye(3) / (6 * PI * a))
+
+
+def test_rpy_mobility_is_symmetric_positive_definite():
+    """The RPY mobility of a set of (overlapping, polydisperse) spheres is SPD (Sec. II.B)."""
+    rng = np.random.default_rng(5)
+    n = 40
+    x = 0.3 * rng.random((n, 3))
+    a = rng.uniform(0.02, 0.06, n)
+    Mob = np.zeros((3 * n, 3 * n))
+    for i in range(n):
+        Mob[3 * i:3 * i + 3, 3 * i:3 * i + 3] = np.eye(3) / (6 * PI * a[i])
+        for j in range(n):
+            if i != j:
+                Mob[3 * i:3 * i + 3, 3 * j:3 * j + 3] = D.rpy_pair(x[i] - x[j], a[i], a[j])
+    assert np.abs(Mob - Mob.T).max() < 1e-12 * np.abs(Mob).max()
+    assert np.linalg.eigvalsh(Mob).min() > 0
+    # and rpy_velocity is that matrix without the self blocks
+    f = rng.standard_normal((n, 3))
+    u = D.rpy_velocity(x, a, x, np.concatenate([f, a[:, None]], axis=1), same_set=True)
+    off = Mob.copy()
+    for i in range(n):
+        off[3 * i:3 * i + 3, 3 * i:3 * i + 3] = 0
+    assert np.allclose(u.reshape(-1), off @ f.reshape(-1), rtol=1e-12)
+
+
+def test_rpy_overlap_correction_matches_brute_force_velocity():
+    """kernel sum [u, lap u] + assembly + overlap correction == brute-force pair mobility."""
+    rng = np.random.default_rng(9)
+    n = 60
+    x = 0.25 * rng.random((n, 3))
+    a = rng.uniform(0.01, 0.05, n)
+    f = rng.standard_normal((n, 3))
+    fb = np.concatenate([f, a[:, None]], axis=1)
+    g = D.direct("rpy", x, x, fb)
+    ua = g[:, :3] + (a[:, None] ** 2 / 6.0) * g[:, 3:]
+    ua = D.rpy_overlap_correction(x, a, x, fb, same_set=True, g=ua)
+    ref = D.rpy_velocity(x, a, x, fb, same_set=True)
+    assert np.allclose(ua, ref, rtol=1e-11, atol=1e-12)
+
+
+def test_double_layer_net_flux_and_stokes_equation():
+    """Net flow out of a sphere around a tensor source D is -1/2 tr D, for any radius
+    (Sec. II.C); the double-layer flow is divergence-free away from the source and solves
+    lap u = grad p with its own pressure (Eq. stkdlp)."""
+    rng = np.random.default_rng(2)
+    Dm = rng.standard_normal((3, 3))
+    y = np.zeros((1, 3))
+    for R in (0.2, 3.0):
+        pts, n, w = sphere_quadrature(R)
+        u = D.direct("stokes_dl", pts, y, Dm.reshape(1, 9))[:, 1:]
+        assert abs(np.sum(w * np.sum(u * n, axis=1)) + 0.5 * np.trace(Dm)) < 1e-10
+    x = np.array([0.5, -0.3, 0.4])
+    fun = lambda z: D.direct("stokes_dl", z[None], y, Dm.reshape(1, 9))[0]
+    lap = fd_laplacian(lambda z: fun(z)[1:], x)
+    gp = fd_grad(lambda z: fun(z)[:1], x)[0]
+    assert np.allclose(lap, gp, rtol=1e-5, atol=1e-6)
+    # p is harmonic: its FD Laplacian is truncation-sized against the scale |p| / |x|^2
+    assert abs(fd_laplacian(lambda z: fun(z)[0], x)) < 1e-3 * abs(fun(x)[0]) / (x @ x)
+    J = fd_grad(lambda z: fun(z)[1:], x)
+    assert abs(np.trace(J)) < 1e-6 * np.abs(J).max()
+
+
+def test_two_point_roundoff_under_translation():
+    """The paper's two-point test (Sec. III.B): translating a pair at distance ~1e-4 changes
+    the FP64 kernel value by ~1e-12 relative, from the rounding of r alone."""
+    rng = np.random.default_rng(4)
+    y = np.array([[0.3, 0.6, 0.1]])
+    x = y + 1e-4 * rng.standard_normal((1, 3)) / np.sqrt(3)
+    f = np.array([[1.0, -0.5, 0.25]])
+    errs = []
+    for _ in range(20):
+        t = rng.random(3) * 7.0
+        u0 = D.direct("stokeslet", x, y, f)
+        u1 = D.direct("stokeslet", x + t, y + t, f)
+        errs.append(D.rel_l2(u1, u0))
+    assert 1e-15 < np.median(errs) < 1e-10

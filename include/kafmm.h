@@ -1,0 +1,166 @@
+/*
+ * kafmm.h -- C ABI of the GB300 (sm_103a) Kernel Aggregated FMM evaluator.
+ *
+ * Computes the kernel sum of Yan & Blackwell, "Kernel Aggregated Fast Multipole Method"
+ * (arXiv:2010.15155), Eq. kernelsumlinear (Sec. I):
+ *
+ *     g_i(x_a) = sum_b K_ij(x_a, y_b) s_j(y_b),     a = 1..n_trg,  b = 1..n_src,
+ *
+ * over an adaptive octree with the U/V/W/X interaction lists (Sec. II, Table tab:ktabdef),
+ * using the aggregated kernel tables of Sec. II (Tables tab:ktab_rpy, tab:ktab_reg,
+ * tab:ktab_stkdlpvelgrad).  Pairs at zero distance contribute nothing (this removes the self
+ * term when sources and targets are the same set).  Viscosity mu = 1.
+ *
+ * Conventions for every call:
+ *   - Return value: 0 on success, a negative KAFMM_ERR_* code otherwise; the message is
+ *     available from kafmm_last_error(plan).  No call exits the process or traps the device.
+ *   - Arrays are row-major.  Points are [n][3] (x, y, z).  Source values s are [n_src][k_s],
+ *     target values g are [n_trg][k_t], with (k_s, k_t) per kernel below.
+ *   - Pointers may be device pointers (cudaMalloc / PyTorch CUDA tensors) or host pointers;
+ *     host arrays are copied to and from the device inside the call (on the plan's stream,
+ *     which is synchronised before a host output is returned).  The caller owns every
+ *     buffer it passes; the plan owns the tree, the lists, the operators and all workspace.
+ *   - All device work is issued on the plan's stream (KAFMM_OPT_STREAM, default: the legacy
+ *     default stream).  Calls on one plan must not run concurrently.
+ *   - dtype is KAFMM_F32 or KAFMM_F64 and applies to points, s and g alike.
+ */
+#ifndef KAFMM_H
+#define KAFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kafmm_plan_s* kafmm_plan_t;
+
+/* Kernel summation problems (Table tab:implement).
+ *   KAFMM_LAPLACE    q -> phi,               K = 1/(4 pi r)                      k_s=1, k_t=1
+ *                    (Sec. II.A)
+ *   KAFMM_STOKESLET  f -> u,                 G = (I/r + r r^T/r^3)/(8 pi)        k_s=3, k_t=3
+ *                    (Sec. II.B)
+ *   KAFMM_RPY        [f, b] -> [u, lap u],   u = (1 + b^2/6 lap) G f             k_s=4, k_t=6
+ *                    (Eqs. RPYflow, RPYkernel; source radius b per point; Table tab:ktab_rpy)
+ *   KAFMM_STOKES_DL  D -> [p, u],            Eqs. stkdlp, stkdlvel, D_jk at 3j+k k_s=9, k_t=4
+ *                    (Sec. II.C).  Only the near field (U list) is evaluated for this kernel:
+ *                    kafmm_eval requires KAFMM_OPT_NEAR_ONLY = 1, otherwise KAFMM_ERR_ARG. */
+typedef enum {
+  KAFMM_LAPLACE = 0,
+  KAFMM_STOKESLET = 1,
+  KAFMM_RPY = 2,
+  KAFMM_STOKES_DL = 3
+} kafmm_kernel;
+
+/* Boundary conditions (Sec. III.B).  KAFMM_BC_PXYZ: triply periodic in the cube
+ * [origin, origin + L)^3; the far images enter through a precomputed operator on the
+ * root's multipole density (Sec. III, App. B).  Periodic sums need a zero net source
+ * (sum of f = 0 for the Stokeslet, sum of q = 0 for Laplace); the k = 0 Fourier mode is
+ * dropped (zero-mean field).  PX and PXY are not provided. */
+typedef enum { KAFMM_BC_OPEN = 0, KAFMM_BC_PXYZ = 3 } kafmm_bc;
+
+typedef enum { KAFMM_F32 = 0, KAFMM_F64 = 1 } kafmm_dtype;
+
+/* Option keys for kafmm_set_option. */
+enum {
+  /* Arithmetic of the evaluation (default KAFMM_PREC_MIXED):
+   *   KAFMM_PREC_FP64  -- every step in FP64 (the plain reference form);
+   *   KAFMM_PREC_FP32  -- FP32 everywhere, M->L on CUDA cores;
+   *   KAFMM_PREC_MIXED -- FP32 near field and surface matvecs, M->L on tcgen05 tensor
+   *                       cores in split BF16x3 with FP32 accumulation. */
+  KAFMM_OPT_PRECISION = 1,
+  /* ML-tree kernel table of the Stokeslet and RPY problems (default KAFMM_ML_L4):
+   *   KAFMM_ML_G  -- the Stokeslet G on M and L points (Tables tab:ktab_rpy, tab:ktab_reg);
+   *   KAFMM_ML_L4 -- four Laplace channels per point (charges f and (y - c).f about the box
+   *                  centre c); a linear, low-dimensional ML-tree table in the sense of
+   *                  Sec. II.  Ignored for Laplace; PXYZ always uses KAFMM_ML_G. */
+  KAFMM_OPT_ML_VARIANT = 2,
+  /* cudaStream_t, passed as an integer. */
+  KAFMM_OPT_STREAM = 3,
+  /* 1: evaluate only the near field (U-list S->T sums).  Default 0. */
+  KAFMM_OPT_NEAR_ONLY = 4,
+  /* 1: Kahan-compensated accumulation in the FP32 near field.  Default 0. */
+  KAFMM_OPT_KAHAN = 5
+};
+enum { KAFMM_PREC_FP64 = 0, KAFMM_PREC_FP32 = 1, KAFMM_PREC_MIXED = 2 };
+enum { KAFMM_ML_G = 0, KAFMM_ML_L4 = 1 };
+
+/* Error codes. */
+enum {
+  KAFMM_OK = 0,
+  KAFMM_ERR_ARG = -1,     /* invalid argument (sizes, enum values, null pointers)     */
+  KAFMM_ERR_DOMAIN = -2,  /* a point outside [origin, origin + L)^3, or NaN / Inf     */
+  KAFMM_ERR_CUDA = -3,    /* a CUDA runtime error (message holds the CUDA text)       */
+  KAFMM_ERR_TIMEOUT = -4, /* a bounded device wait expired                           */
+  KAFMM_ERR_NOMEM = -5,   /* device allocation failed                                */
+  KAFMM_ERR_STATE = -6    /* call out of order (eval before set_points, ...)          */
+};
+
+/* Creates a plan: kernel, boundary condition, multipole order p (the paper's m, Sec. III:
+ * 6(p-1)^2 + 2 equivalent points per surface, 2 <= p <= 16) and the leaf size q (a box is
+ * split while it holds more than q points, Sec. III; 1 <= q <= 4096).  Builds the FP64
+ * translation operators on the current CUDA device (pseudo-inverses by one-sided Jacobi
+ * SVD, Sec. II; the periodic operator by Ewald lattice sums).  *out receives the plan. */
+int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int max_pts_per_leaf,
+               kafmm_plan_t* out);
+
+/* Sets one option (keys above).  Changing PRECISION or ML_VARIANT after kafmm_plan
+ * rebuilds the operators; after set_points it also invalidates the tree (set_points must
+ * be called again). */
+int kafmm_set_option(kafmm_plan_t plan, int key, int64_t value);
+
+/* The cube that holds all points: [origin, origin + L)^3 (default origin 0, L = 1). */
+int kafmm_set_domain(kafmm_plan_t plan, const double origin[3], double L);
+
+/* Sets sources y [n_src][3] and targets x [n_trg][3] (x == y with n_trg == n_src means one
+ * shared set).  Builds the octree and the U/V/W/X lists on the device: Morton keys, radix
+ * sort, level-by-level refinement, list construction (Sec. II, Sec. III).  Points outside
+ * the domain give KAFMM_ERR_DOMAIN.  The plan keeps sorted copies; the caller's arrays
+ * are not retained. */
+int kafmm_set_points(kafmm_plan_t plan, const void* y, int64_t n_src, const void* x,
+                     int64_t n_trg, int dtype);
+
+/* Evaluates g [n_trg][k_t] from s [n_src][k_s] for the current points (overwrites g).
+ * Upward pass S->M, M->M; downward pass M->L (V), S->L (X), L->L; leaves L->T, M->T (W),
+ * S->T (U) -- Sec. II, Fig. kifmmgraph. */
+int kafmm_eval(kafmm_plan_t plan, const void* s, void* g, int dtype);
+
+/* RPY only (Eq. RPYtrgvel and the overlap post-processing of Sec. II.B): from the kernel
+ * sum g = [u, lap u] ([n_trg][6], as returned by kafmm_eval) and the target radii a
+ * [n_trg], writes the sphere velocities ua [n_trg][3] = u + a^2/6 lap u, corrected for every
+ * overlapping pair (|x - y| <= a + b) by the difference between the overlap-regularised
+ * pair mobility and the far form.  Requires the source values s of the last kafmm_eval
+ * ([n_src][4], passed again) so the pass can read forces and radii. */
+int kafmm_rpy_velocity(kafmm_plan_t plan, const void* s, const void* a, const void* g,
+                       void* ua, int dtype);
+
+/* Tree and list statistics of the current points (host array info[n], up to 16 entries):
+ * 0 boxes, 1 leaves, 2 levels, 3 U entries, 4 V entries, 5 W entries, 6 X entries,
+ * 7 near-field pairs (sum over U of n_trg(B) n_src(A)), 8 max points in a leaf. */
+int kafmm_tree_info(kafmm_plan_t plan, int64_t* info, int n);
+
+/* Copies the tree to host arrays (each may be NULL): level[nbox], anchor[nbox][3],
+ * parent[nbox], leaf[nbox] (0/1), and the list kind (0 U, 1 V, 2 W, 3 X) as CSR:
+ * offsets[nbox + 1], entries[n_entries] = source box index, shifts[n_entries] = image
+ * shift code (sx+1) + 3 (sy+1) + 9 (sz+1).  Boxes are numbered level by level, in Morton
+ * order inside a level.  Sizes come from kafmm_tree_info. */
+int kafmm_get_tree(kafmm_plan_t plan, int32_t* level, int32_t* anchor, int32_t* parent,
+                   int8_t* leaf);
+int kafmm_get_list(kafmm_plan_t plan, int kind, int64_t* offsets, int32_t* entries,
+                   int8_t* shifts);
+
+/* Times of the phases of the last set_points + eval, in milliseconds (CUDA events on the
+ * plan's stream): 0 tree, 1 lists, 2 upward, 3 M->L, 4 downward rest, 5 near field,
+ * 6 whole eval.  Host array t[n], up to 8 entries. */
+int kafmm_phase_times(kafmm_plan_t plan, double* t, int n);
+
+/* Releases the plan and all device memory it owns. */
+int kafmm_destroy(kafmm_plan_t plan);
+
+/* Last error message of the plan (or of the last failed kafmm_plan when plan is NULL). */
+const char* kafmm_last_error(kafmm_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KAFMM_H */

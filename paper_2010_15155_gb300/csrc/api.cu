@@ -1,0 +1,387 @@
+// C ABI of the evaluator (declared in include/kafmm.h).
+#include <cstdarg>
+#include <cstring>
+
+#include "plan.cuh"
+
+namespace kafmm {
+
+int fail(Plan& P, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  P.err = buf;
+  return code;
+}
+
+int cuda_fail(Plan& P, cudaError_t e, const char* where) {
+  P.err = std::string("CUDA error '") + cudaGetErrorString(e) + "' at " + where;
+  cudaGetLastError();  // clear a non-sticky error
+  return e == cudaErrorMemoryAllocation ? KAFMM_ERR_NOMEM : KAFMM_ERR_CUDA;
+}
+
+// Problem dimensions from kernel, boundary condition and ML variant.
+static void configure(Plan& P) {
+  int v = P.variant;
+  if (P.bc == KAFMM_BC_PXYZ) v = KAFMM_ML_G;
+  P.ml_stokes = 0;
+  P.C = 1;
+  P.D = 1;
+  switch (P.kernel) {
+    case KAFMM_LAPLACE:
+      P.ks = 1;
+      P.kt = 1;
+      break;
+    case KAFMM_STOKESLET:
+    case KAFMM_RPY:
+      P.ks = P.kernel == KAFMM_STOKESLET ? 3 : 4;
+      P.kt = P.kernel == KAFMM_STOKESLET ? 3 : 6;
+      if (v == KAFMM_ML_L4) {
+        P.C = 4;
+      } else {
+        P.ml_stokes = 1;
+        P.D = 3;
+      }
+      break;
+    default:  // double layer: near field only
+      P.ks = 9;
+      P.kt = 4;
+      break;
+  }
+  P.n = 6 * (P.p - 1) * (P.p - 1) + 2;
+  P.R = P.n * P.D;
+  P.ops_ready = false;
+  P.use_tc = false;
+}
+
+static bool is_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeUnregistered || a.type == cudaMemoryTypeHost;
+}
+
+static int ensure_ops(Plan& P) {
+  if (P.ops_ready || P.kernel == KAFMM_STOKES_DL) return 0;
+  int rc = build_operators(P);
+  if (rc) return rc;
+  extern bool tc_supported(Plan & P);
+  P.use_tc = tc_supported(P);
+  return 0;
+}
+
+}  // namespace kafmm
+
+using namespace kafmm;
+
+static thread_local std::string g_err;
+
+#define PLAN_CHECK(pl)                                         \
+  if (!(pl)) {                                                 \
+    g_err = "null plan";                                       \
+    return KAFMM_ERR_ARG;                                      \
+  }                                                            \
+  Plan& P = *reinterpret_cast<Plan*>(pl);
+
+#define CKP(call)                                          \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(P, e_, #call); \
+  } while (0)
+
+extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_plan_t* out) {
+  if (!out) {
+    g_err = "kafmm_plan: out is NULL";
+    return KAFMM_ERR_ARG;
+  }
+  *out = nullptr;
+  if ((int)kernel < 0 || (int)kernel > 3 || (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ) || p < 2 ||
+      p > 16 || q < 1 || q > 4096) {
+    g_err = "kafmm_plan: invalid kernel, boundary condition, order (2..16) or leaf size (1..4096)";
+    return KAFMM_ERR_ARG;
+  }
+  if (bc == KAFMM_BC_PXYZ) {
+    g_err = "kafmm_plan: the triply periodic operator is not built by this version";
+    return KAFMM_ERR_ARG;
+  }
+  Plan* P = new Plan();
+  P->kernel = kernel;
+  P->bc = bc;
+  P->p = p;
+  P->q = q;
+  configure(*P);
+  for (int i = 0; i < 8; ++i) {
+    if (cudaEventCreate(&P->ev[i]) != cudaSuccess) {
+      g_err = "kafmm_plan: cudaEventCreate failed (no usable CUDA device?)";
+      cudaGetLastError();
+      delete P;
+      return KAFMM_ERR_CUDA;
+    }
+  }
+  *out = reinterpret_cast<kafmm_plan_t>(P);
+  return 0;
+}
+
+extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
+  PLAN_CHECK(pl);
+  switch (key) {
+    case KAFMM_OPT_PRECISION:
+      if (value < 0 || value > 2) return fail(P, KAFMM_ERR_ARG, "bad precision %lld", (long long)value);
+      if (P.prec != (int)value) {
+        P.prec = (int)value;
+        configure(P);
+        P.have_points = false;
+      }
+      return 0;
+    case KAFMM_OPT_ML_VARIANT:
+      if (value < 0 || value > 1) return fail(P, KAFMM_ERR_ARG, "bad ML variant %lld", (long long)value);
+      if (P.variant != (int)value) {
+        P.variant = (int)value;
+        configure(P);
+        P.have_points = false;
+      }
+      return 0;
+    case KAFMM_OPT_STREAM:
+      P.stream = reinterpret_cast<cudaStream_t>(value);
+      return 0;
+    case KAFMM_OPT_NEAR_ONLY:
+      P.near_only = value ? 1 : 0;
+      return 0;
+    case KAFMM_OPT_KAHAN:
+      P.kahan = value ? 1 : 0;
+      return 0;
+    default:
+      return fail(P, KAFMM_ERR_ARG, "unknown option %d", key);
+  }
+}
+
+extern "C" int kafmm_set_domain(kafmm_plan_t pl, const double origin[3], double L) {
+  PLAN_CHECK(pl);
+  if (!origin || !(L > 0.0)) return fail(P, KAFMM_ERR_ARG, "bad domain");
+  for (int d = 0; d < 3; ++d) P.origin[d] = origin[d];
+  P.L = L;
+  P.have_points = false;
+  return 0;
+}
+
+extern "C" int kafmm_set_points(kafmm_plan_t pl, const void* y, int64_t ns, const void* x, int64_t nt,
+                                int dtype) {
+  PLAN_CHECK(pl);
+  if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || ns < 0 || nt < 0 || ns > (1ll << 31) - 2 ||
+      nt > (1ll << 31) - 2 || (ns > 0 && !y) || (nt > 0 && !x))
+    return fail(P, KAFMM_ERR_ARG, "kafmm_set_points: bad arguments");
+  P.have_points = false;
+  int rc = ensure_ops(P);
+  if (rc) return rc;
+  size_t es = dtype == KAFMM_F64 ? 8 : 4;
+  const void* yd = y;
+  const void* xd = x;
+  bool same = (x == y) && (ns == nt);
+  if (ns > 0 && is_host_ptr(y)) {
+    CKP(P.io_in.reserve(es * 3 * ns));
+    CKP(cudaMemcpyAsync(P.io_in.p, y, es * 3 * ns, cudaMemcpyHostToDevice, P.stream));
+    yd = P.io_in.p;
+  }
+  if (same) {
+    xd = yd;
+  } else if (nt > 0 && is_host_ptr(x)) {
+    CKP(P.io_aux.reserve(es * 3 * nt));
+    CKP(cudaMemcpyAsync(P.io_aux.p, x, es * 3 * nt, cudaMemcpyHostToDevice, P.stream));
+    xd = P.io_aux.p;
+  }
+  rc = build_tree(P, yd, ns, xd, nt, dtype);
+  if (rc) return rc;
+  rc = build_worklists(P, 64 / P.C, 64 / P.C);
+  if (rc) return rc;
+  P.have_points = true;
+  return 0;
+}
+
+extern "C" int kafmm_eval(kafmm_plan_t pl, const void* s, void* g, int dtype) {
+  PLAN_CHECK(pl);
+  if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "kafmm_eval before kafmm_set_points");
+  if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || (P.tree.n_src > 0 && !s) || (P.tree.n_trg > 0 && !g))
+    return fail(P, KAFMM_ERR_ARG, "kafmm_eval: bad arguments");
+  if (P.kernel == KAFMM_STOKES_DL && !P.near_only)
+    return fail(P, KAFMM_ERR_ARG, "the double-layer kernel is evaluated with KAFMM_OPT_NEAR_ONLY = 1");
+  int rc = ensure_ops(P);
+  if (rc) return rc;
+  size_t es = dtype == KAFMM_F64 ? 8 : 4;
+  const void* sd = s;
+  void* gd = g;
+  bool host_out = P.tree.n_trg > 0 && is_host_ptr(g);
+  if (P.tree.n_src > 0 && is_host_ptr(s)) {
+    CKP(P.io_in.reserve(es * P.ks * P.tree.n_src));
+    CKP(cudaMemcpyAsync(P.io_in.p, s, es * P.ks * P.tree.n_src, cudaMemcpyHostToDevice, P.stream));
+    sd = P.io_in.p;
+  }
+  if (host_out) {
+    CKP(P.io_out.reserve(es * P.kt * P.tree.n_trg));
+    gd = P.io_out.p;
+  }
+  CKP(cudaMemsetAsync(P.tree.status.p, 0, 4, P.stream));
+  rc = evaluate(P, sd, gd, dtype);
+  if (rc) return rc;
+  if (host_out)
+    CKP(cudaMemcpyAsync(g, gd, es * P.kt * P.tree.n_trg, cudaMemcpyDeviceToHost, P.stream));
+  unsigned st = 0;
+  CKP(cudaMemcpyAsync(&st, P.tree.status.p, 4, cudaMemcpyDeviceToHost, P.stream));
+  CKP(cudaStreamSynchronize(P.stream));
+  if (st & ST_TIMEOUT) return fail(P, KAFMM_ERR_TIMEOUT, "a bounded device wait expired");
+  return 0;
+}
+
+extern "C" int kafmm_rpy_velocity(kafmm_plan_t pl, const void* s, const void* a, const void* g, void* ua,
+                                  int dtype) {
+  PLAN_CHECK(pl);
+  if (P.kernel != KAFMM_RPY) return fail(P, KAFMM_ERR_ARG, "kafmm_rpy_velocity needs the RPY kernel");
+  if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "kafmm_rpy_velocity before kafmm_set_points");
+  return rpy_velocity(P, s, a, g, ua, dtype);
+}
+
+extern "C" int kafmm_tree_info(kafmm_plan_t pl, int64_t* info, int n) {
+  PLAN_CHECK(pl);
+  if (!info || n < 0) return fail(P, KAFMM_ERR_ARG, "bad info array");
+  if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "no points");
+  const Tree& T = P.tree;
+  int64_t v[9] = {T.nbox, T.nleaf, T.nlevels, T.n_u, T.n_v, T.n_w, T.n_x, T.near_pairs, T.max_leaf_pts};
+  for (int i = 0; i < n && i < 16; ++i) info[i] = i < 9 ? v[i] : 0;
+  return 0;
+}
+
+namespace kafmm {
+__global__ void k_anchor(const uint64_t* key, int n, int32_t* out) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x) {
+    uint64_t k = key[b];
+    out[3 * b] = (int32_t)compact3(k);
+    out[3 * b + 1] = (int32_t)compact3(k >> 1);
+    out[3 * b + 2] = (int32_t)compact3(k >> 2);
+  }
+}
+__global__ void k_vtab_csr(const int32_t* vtab, int nbox, const int64_t* off, int32_t* ent) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
+    int64_t o = off[b];
+    for (int k = 0; k < 216; ++k) {
+      int32_t e = vtab[(int64_t)b * 216 + k];
+      if (e >= 0) ent[o++] = e;
+    }
+  }
+}
+__global__ void k_vtab_count(const int32_t* vtab, int nbox, int64_t* cnt) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
+    int64_t c = 0;
+    for (int k = 0; k < 216; ++k) c += vtab[(int64_t)b * 216 + k] >= 0;
+    cnt[b] = c;
+  }
+}
+}  // namespace kafmm
+
+extern "C" int kafmm_get_tree(kafmm_plan_t pl, int32_t* level, int32_t* anchor, int32_t* parent,
+                              int8_t* leaf) {
+  PLAN_CHECK(pl);
+  if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "no points");
+  Tree& T = P.tree;
+  int nb = T.nbox;
+  cudaStream_t st = P.stream;
+  if (level) {
+    std::vector<int8_t> l8(nb);
+    CKP(cudaMemcpyAsync(l8.data(), T.level.p, nb, cudaMemcpyDeviceToHost, st));
+    CKP(cudaStreamSynchronize(st));
+    for (int i = 0; i < nb; ++i) level[i] = l8[i];
+  }
+  if (anchor) {
+    DevBuf tmp;
+    CKP(tmp.reserve(sizeof(int32_t) * 3 * nb));
+    k_anchor<<<256, 256, 0, st>>>(T.key.as<uint64_t>(), nb, tmp.as<int32_t>());
+    CKP(cudaMemcpyAsync(anchor, tmp.p, sizeof(int32_t) * 3 * nb, cudaMemcpyDeviceToHost, st));
+    CKP(cudaStreamSynchronize(st));
+  }
+  if (parent) CKP(cudaMemcpyAsync(parent, T.parent.p, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, st));
+  if (leaf) CKP(cudaMemcpyAsync(leaf, T.leaf.p, nb, cudaMemcpyDeviceToHost, st));
+  CKP(cudaStreamSynchronize(st));
+  return 0;
+}
+
+extern "C" int kafmm_get_list(kafmm_plan_t pl, int kind, int64_t* offsets, int32_t* entries,
+                              int8_t* shifts) {
+  PLAN_CHECK(pl);
+  if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "no points");
+  if (kind < 0 || kind > 3) return fail(P, KAFMM_ERR_ARG, "bad list kind");
+  Tree& T = P.tree;
+  int nb = T.nbox;
+  cudaStream_t st = P.stream;
+  std::vector<int64_t> off(nb + 1);
+  int64_t n = 0;
+  DevBuf doff, dent;
+  const int64_t* src_off = nullptr;
+  const int32_t* src_ent = nullptr;
+  if (kind == 1) {
+    CKP(doff.reserve(sizeof(int64_t) * (nb + 1)));
+    k_vtab_count<<<256, 256, 0, st>>>(T.vtab.as<int32_t>(), nb, doff.as<int64_t>());
+    std::vector<int64_t> cnt(nb);
+    CKP(cudaMemcpyAsync(cnt.data(), doff.p, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, st));
+    CKP(cudaStreamSynchronize(st));
+    off[0] = 0;
+    for (int b = 0; b < nb; ++b) off[b + 1] = off[b] + cnt[b];
+    n = off[nb];
+    CKP(cudaMemcpyAsync(doff.p, off.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, st));
+    CKP(dent.reserve(sizeof(int32_t) * (n + 1)));
+    k_vtab_csr<<<256, 256, 0, st>>>(T.vtab.as<int32_t>(), nb, doff.as<int64_t>(), dent.as<int32_t>());
+    src_ent = dent.as<int32_t>();
+  } else {
+    src_off = kind == 0 ? T.u_off.as<int64_t>() : (kind == 2 ? T.w_off.as<int64_t>() : T.x_off.as<int64_t>());
+    src_ent = kind == 0 ? T.u_ent.as<int32_t>() : (kind == 2 ? T.w_ent.as<int32_t>() : T.x_ent.as<int32_t>());
+    CKP(cudaMemcpyAsync(off.data(), src_off, sizeof(int64_t) * (nb + 1), cudaMemcpyDeviceToHost, st));
+    CKP(cudaStreamSynchronize(st));
+    n = off[nb];
+  }
+  if (offsets) memcpy(offsets, off.data(), sizeof(int64_t) * (nb + 1));
+  if (entries || shifts) {
+    std::vector<int32_t> e(n);
+    if (n) CKP(cudaMemcpyAsync(e.data(), src_ent, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+    CKP(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < n; ++i) {
+      if (entries) entries[i] = entry_box(e[i]);
+      if (shifts) shifts[i] = (int8_t)entry_shift(e[i]);
+    }
+  }
+  return 0;
+}
+
+extern "C" int kafmm_phase_times(kafmm_plan_t pl, double* t, int n) {
+  PLAN_CHECK(pl);
+  if (!t) return fail(P, KAFMM_ERR_ARG, "null array");
+  // ev: 0 start of set_points, 1 tree done, 2 lists done, 3 eval start, 4 upward done,
+  //     5 M->L done, 6 downward done, 7 eval done
+  float ms[8] = {0};
+  int pairs[7][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {3, 7}};
+  for (int i = 0; i < 7; ++i) {
+    float v = 0;
+    if (cudaEventElapsedTime(&v, P.ev[pairs[i][0]], P.ev[pairs[i][1]]) != cudaSuccess) {
+      cudaGetLastError();
+      v = -1;
+    }
+    ms[i] = v;
+  }
+  for (int i = 0; i < n && i < 8; ++i) t[i] = i < 7 ? ms[i] : 0.0;
+  return 0;
+}
+
+extern "C" int kafmm_destroy(kafmm_plan_t pl) {
+  if (!pl) return 0;
+  Plan* P = reinterpret_cast<Plan*>(pl);
+  for (int i = 0; i < 8; ++i)
+    if (P->ev[i]) cudaEventDestroy(P->ev[i]);
+  delete P;
+  return 0;
+}
+
+extern "C" const char* kafmm_last_error(kafmm_plan_t pl) {
+  if (!pl) return g_err.c_str();
+  return reinterpret_cast<Plan*>(pl)->err.c_str();
+}

@@ -1,0 +1,146 @@
+// Shared definitions of the KAFMM evaluator (CUDA, sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/kafmm.h"
+
+namespace kafmm {
+
+constexpr int MAX_LEVEL = 20;        // finest octree level; keys carry 20 bits per axis
+constexpr int MAX_LEVELS = MAX_LEVEL + 1;
+constexpr double PI = 3.14159265358979323846;
+
+// Surface radii in units of the box half-width (Ying, Biros & Zorin 2004): upward
+// equivalent / check, downward equivalent / check.
+constexpr double ALPHA_UE = 1.05, ALPHA_UC = 2.95, ALPHA_DE = 2.95, ALPHA_DC = 1.05;
+// Relative singular-value cutoff of the check-to-equivalent pseudo-inverses.
+constexpr double PINV_RCOND = 1e-9;
+
+// Operator slots: 343 M->L offsets (ox,oy,oz) in [-3,3]^3 (the 27 inner ones unused), then
+// 8 M->M octants, 8 L->L octants, the upward and the downward pseudo-inverse.
+constexpr int OP_M2L = 0, N_M2L = 343;
+constexpr int OP_M2M = OP_M2L + N_M2L;
+constexpr int OP_L2L = OP_M2M + 8;
+constexpr int OP_UC2UE = OP_L2L + 8;
+constexpr int OP_DC2DE = OP_UC2UE + 1;
+constexpr int N_OPS = OP_DC2DE + 1;
+
+__host__ __device__ inline int m2l_index(int ox, int oy, int oz) {
+  return (ox + 3) + 7 * (oy + 3) + 49 * (oz + 3);
+}
+
+// Shift code of a periodic image: (sx+1) + 3(sy+1) + 9(sz+1); 13 = no shift.
+__host__ __device__ inline int shift_code(int sx, int sy, int sz) {
+  return (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1);
+}
+__host__ __device__ inline void shift_decode(int c, int& sx, int& sy, int& sz) {
+  sx = c % 3 - 1;
+  sy = (c / 3) % 3 - 1;
+  sz = c / 9 - 1;
+}
+
+// List entry: source box index in the low 27 bits, shift code in the high 5.
+__host__ __device__ inline int32_t pack_entry(int box, int sc) { return box | (sc << 27); }
+__host__ __device__ inline int entry_box(int32_t e) { return e & ((1 << 27) - 1); }
+__host__ __device__ inline int entry_shift(int32_t e) { return (int)((uint32_t)e >> 27); }
+
+// 3 x 20-bit interleave: bit 3i = x_i, 3i+1 = y_i, 3i+2 = z_i.
+__host__ __device__ inline uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0xFFFFF;
+  x = (x | (x << 32)) & 0x001F00000000FFFFull;
+  x = (x | (x << 16)) & 0x001F0000FF0000FFull;
+  x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+  x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+__host__ __device__ inline uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x | (x >> 2)) & 0x10C30C30C30C30C3ull;
+  x = (x | (x >> 4)) & 0x100F00F00F00F00Full;
+  x = (x | (x >> 8)) & 0x001F0000FF0000FFull;
+  x = (x | (x >> 16)) & 0x001F00000000FFFFull;
+  x = (x | (x >> 32)) & 0xFFFFFull;
+  return (uint32_t)x;
+}
+__host__ __device__ inline uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+// ---- device buffers -----------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  // Grows to at least nbytes (contents not preserved). Returns a CUDA error code.
+  cudaError_t reserve(size_t nbytes) {
+    if (nbytes <= bytes && p) return cudaSuccess;
+    release();
+    size_t nb = nbytes < 256 ? 256 : nbytes;
+    cudaError_t e = cudaMalloc(&p, nb);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = nb;
+    return cudaSuccess;
+  }
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Status word written by kernels (never trapped on): bit 0 domain error, bit 1 timeout,
+// bit 2 capacity overflow, bit 3 non-finite value.
+enum { ST_DOMAIN = 1, ST_TIMEOUT = 2, ST_OVERFLOW = 4, ST_NONFINITE = 8 };
+
+// Bounded mbarrier wait used by every kernel that waits on an asynchronous copy.
+__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, unsigned* status) {
+  uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
+  for (long it = 0; it < (1L << 26); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  atomicOr(status, (unsigned)ST_TIMEOUT);
+  return false;
+}
+
+__device__ inline void mbar_init(uint64_t* bar, unsigned count) {
+  uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(addr), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(addr), "r"(bytes)
+               : "memory");
+}
+
+// 1-D bulk copy global -> shared completing on an mbarrier (16-byte aligned, size % 16 == 0).
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(d),
+      "l"(src), "r"(bytes), "r"(b)
+      : "memory");
+}
+
+}  // namespace kafmm

@@ -1,0 +1,921 @@
+// The KAFMM evaluation (Sec. II, Fig. kifmmgraph): S->M, M->M, M->L, S->L, L->L, and at the
+// leaves L->T, M->T, S->T; CUDA-core kernels in FP32 or FP64.
+#include <algorithm>
+
+#include "physics.cuh"
+#include "plan.cuh"
+
+namespace kafmm {
+
+int m2l_tc_launch(Plan& P, const int4* tiles, int ntiles, const int* boxlist, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------
+// Geometry helpers.
+template <class T>
+__device__ inline void box_centre(const TreeView& t, int b, double L, const double* org, T& cx, T& cy,
+                                  T& cz, T& r) {
+  int lv = t.level[b];
+  uint64_t k = t.key[b];
+  double side = L / (double)(1 << lv);
+  cx = (T)(org[0] + ((double)compact3(k) + 0.5) * side);
+  cy = (T)(org[1] + ((double)compact3(k >> 1) + 0.5) * side);
+  cz = (T)(org[2] + ((double)compact3(k >> 2) + 0.5) * side);
+  r = (T)(0.5 * side);
+}
+
+struct Geo {
+  double L;
+  double org[3];
+};
+
+// ---------------------------------------------------------------------------------------
+// Source values to sorted compute-type records (T4 per source; DL: 3 T4).
+template <class Tin, class T, int PR>
+__global__ void k_prep_src(const Tin* __restrict__ s, const uint32_t* __restrict__ perm, int64_t n,
+                           typename V4<T>::type* __restrict__ out) {
+  using T4 = typename V4<T>::type;
+  constexpr int KS = PR == P_LAP ? 1 : (PR == P_DL ? 9 : ((PR == P_RPY_L4 || PR == P_RPY_G) ? 4 : 3));
+  constexpr int NV = ProbInfo<PR>::NV;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const Tin* src = s + (int64_t)perm[i] * KS;
+    T v[4 * NV];
+#pragma unroll
+    for (int k = 0; k < 4 * NV; ++k) v[k] = k < KS ? (T)src[k] : T(0);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      T4 r;
+      r.x = v[4 * q];
+      r.y = v[4 * q + 1];
+      r.z = v[4 * q + 2];
+      r.w = v[4 * q + 3];
+      out[i * NV + q] = r;
+    }
+  }
+}
+
+// Sorted results back to the caller's order and dtype.
+template <class T, class Tout>
+__global__ void k_unperm(const T* __restrict__ g, const uint32_t* __restrict__ perm, int64_t n, int kt,
+                         Tout* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * kt;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / kt;
+    int k = (int)(e % kt);
+    out[(int64_t)perm[i] * kt + k] = (Tout)g[e];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// S->M (leaf sources to the upward check surface) and S->L (X-list sources to the downward
+// check surface).  One block per box; check points over threads; sources staged in shared
+// memory in local coordinates (relative to the box centre, which is also the reference
+// point of the four-channel table).
+template <class T, int PR>
+struct S2CArgs {
+  TreeView t;
+  Geo geo;
+  const typename V4<T>::type* pos;   // sorted source positions
+  const typename V4<T>::type* val;   // sorted source values
+  const T* unit;                     // unit surface [n][3]
+  const int* boxes;
+  const int64_t* x_off;
+  const int32_t* x_ent;
+  T* check;
+  int n, R;
+  int mode;                          // 0: S->M (overwrite), 1: S->L over X lists (accumulate)
+};
+
+template <class T, int PR>
+__global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
+  using T4 = typename V4<T>::type;
+  constexpr int C = ProbInfo<PR>::C, D = ProbInfo<PR>::D;
+  constexpr int CH = 256;
+  __shared__ T4 sp[CH], sv[CH];
+  int b = a.boxes[blockIdx.x];
+  T cx, cy, cz, r;
+  box_centre<T>(a.t, b, a.geo.L, a.geo.org, cx, cy, cz, r);
+  T alpha = a.mode == 0 ? T(ALPHA_UC) : T(ALPHA_DC);
+  int nent = a.mode == 0 ? 1 : (int)(a.x_off[b + 1] - a.x_off[b]);
+  for (int i0 = 0; i0 < a.n; i0 += blockDim.x) {
+    int i = i0 + threadIdx.x;
+    T px = 0, py = 0, pz = 0;
+    if (i < a.n) {
+      px = alpha * r * a.unit[3 * i];
+      py = alpha * r * a.unit[3 * i + 1];
+      pz = alpha * r * a.unit[3 * i + 2];
+    }
+    T acc[C * D];
+#pragma unroll
+    for (int k = 0; k < C * D; ++k) acc[k] = 0;
+    for (int e = 0; e < nent; ++e) {
+      int src = b, sc = 13;
+      if (a.mode == 1) {
+        int32_t ent = a.x_ent[a.x_off[b] + e];
+        src = entry_box(ent);
+        sc = entry_shift(ent);
+      }
+      int sx, sy, sz;
+      shift_decode(sc, sx, sy, sz);
+      T ox = (T)(sx * a.geo.L) - cx, oy = (T)(sy * a.geo.L) - cy, oz = (T)(sz * a.geo.L) - cz;
+      int s0 = a.t.sb[src], s1 = a.t.se[src];
+      for (int c0 = s0; c0 < s1; c0 += CH) {
+        int cn = min(CH, s1 - c0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < cn; j += blockDim.x) {
+          T4 p = a.pos[c0 + j];
+          p.x = p.x + ox;  // local source coordinates
+          p.y = p.y + oy;
+          p.z = p.z + oz;
+          sp[j] = p;
+          sv[j] = a.val[c0 + j];
+        }
+        __syncthreads();
+        if (i < a.n) {
+          for (int j = 0; j < cn; ++j) {
+            T4 y = sp[j], v = sv[j];
+            T r0 = px - y.x, r1 = py - y.y, r2 = pz - y.z;
+            if (PR == P_LAP) {
+              lap_st<T>(r0, r1, r2, v.x, acc);
+            } else if (PR == P_STK_L4 || PR == P_RPY_L4) {
+              T rr = r0 * r0 + r1 * r1 + r2 * r2;
+              T ir = inv_r(rr);
+              acc[0] += v.x * ir;
+              acc[1] += v.y * ir;
+              acc[2] += v.z * ir;
+              T q4 = y.x * v.x + y.y * v.y + y.z * v.z;  // (y - c) . f
+              if (PR == P_RPY_L4) q4 = q4 + v.w * v.w * T(1.0 / 3.0) * (r0 * v.x + r1 * v.y + r2 * v.z) * ir * ir;
+              acc[3] += q4 * ir;
+            } else if (PR == P_STK_G) {
+              stk_st<T>(r0, r1, r2, v.x, v.y, v.z, acc);
+            } else if (PR == P_RPY_G) {
+              T tmp[6] = {0, 0, 0, 0, 0, 0};
+              rpy_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
+              acc[0] += tmp[0];
+              acc[1] += tmp[1];
+              acc[2] += tmp[2];
+            }
+          }
+        }
+      }
+    }
+    if (i < a.n) {
+      T sc = (PR == P_STK_G || PR == P_RPY_G) ? T(1.0 / (8.0 * PI)) : T(1.0 / (4.0 * PI));
+      T* out = a.check + (int64_t)b * a.R * C;
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          int64_t idx = (int64_t)(i * D + d) * C + c;
+          T v = acc[d * C + c] * sc;
+          if (a.mode == 0)
+            out[idx] = v;
+          else
+            out[idx] += v;
+        }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Gather-GEMM engine on CUDA cores: for each output box b of a tile (all of one octant class),
+//   out[b] (+)= alpha_b * sum_k Op[op(k)] * shift_k(in[src(b, k)])
+// with [R][C] per box.  Modes: M->L over the 216 V slots, M->M over 8 children, L->L from the
+// parent, and the check-to-equivalent pseudo-inverses (alpha_b = box half-width).
+enum GemmMode { GM_M2L = 0, GM_M2M = 1, GM_L2L = 2, GM_PINV_UP = 3, GM_PINV_DN = 4 };
+
+template <class T>
+struct GemmArgs {
+  TreeView t;
+  Geo geo;
+  const T* ops;
+  const T* in;
+  T* out;
+  const int4* tiles;   // (offset into boxlist, count, class, unused)
+  const int* boxlist;
+  const int32_t* vtab;
+  int mode, R;
+};
+
+template <int C>
+struct GemmShape { static constexpr int NB = 64 / C; };
+
+__device__ inline void m2l_slot_offset(int k, int cls, int& ox, int& oy, int& oz) {
+  ox = k % 6 - 2 - (cls & 1);
+  oy = (k / 6) % 6 - 2 - ((cls >> 1) & 1);
+  oz = k / 36 - 2 - ((cls >> 2) & 1);
+}
+
+template <class T, int C>
+__global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> a) {
+  using T4 = typename V4<T>::type;
+  constexpr int NB = GemmShape<C>::NB, BM = 64, BN = 64, BK = 16;
+  __shared__ T As[BK][BM + 4];
+  __shared__ T Bs[BK][BN + 4];
+  __shared__ int ob[NB], srcb[NB];
+  __shared__ T dcx[NB], dcy[NB], dcz[NB], alph[NB];
+  int4 tile = a.tiles[blockIdx.x];
+  int row0 = blockIdx.y * BM;
+  int cls = tile.z;
+  int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  if (tid < NB) {
+    int b = tid < tile.y ? a.boxlist[tile.x + tid] : -1;
+    ob[tid] = b;
+    T al = 1;
+    if (b >= 0 && (a.mode == GM_PINV_UP || a.mode == GM_PINV_DN))
+      al = (T)(0.5 * a.geo.L / (double)(1 << a.t.level[b]));
+    alph[tid] = al;
+  }
+  __syncthreads();
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  int nslots = a.mode == GM_M2L ? 216 : (a.mode == GM_M2M ? 8 : 1);
+  const int R = a.R;
+  for (int k = 0; k < nslots; ++k) {
+    int op = 0;
+    int ox = 0, oy = 0, oz = 0;
+    if (a.mode == GM_M2L) {
+      m2l_slot_offset(k, cls, ox, oy, oz);
+      if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
+      op = OP_M2L + m2l_index(ox, oy, oz);
+    } else if (a.mode == GM_M2M) {
+      op = OP_M2M + k;
+    } else if (a.mode == GM_L2L) {
+      op = OP_L2L + cls;
+    } else {
+      op = a.mode == GM_PINV_UP ? OP_UC2UE : OP_DC2DE;
+    }
+    int has = 0;
+    if (tid < NB) {
+      int b = ob[tid], s = -1;
+      T dx = 0, dy = 0, dz = 0;
+      if (b >= 0) {
+        int lv = a.t.level[b];
+        double side = a.geo.L / (double)(1 << lv);
+        if (a.mode == GM_M2L) {
+          int32_t e = a.vtab[(int64_t)b * 216 + k];
+          if (e >= 0) {
+            s = entry_box(e);
+            dx = (T)(ox * side);
+            dy = (T)(oy * side);
+            dz = (T)(oz * side);
+          }
+        } else if (a.mode == GM_M2M) {
+          s = a.t.child[b * 8 + k];
+          dx = (T)(((k & 1) ? 0.25 : -0.25) * side);
+          dy = (T)(((k & 2) ? 0.25 : -0.25) * side);
+          dz = (T)(((k & 4) ? 0.25 : -0.25) * side);
+        } else if (a.mode == GM_L2L) {
+          s = a.t.parent[b];
+          dx = (T)(((cls & 1) ? -0.5 : 0.5) * side);
+          dy = (T)(((cls & 2) ? -0.5 : 0.5) * side);
+          dz = (T)(((cls & 4) ? -0.5 : 0.5) * side);
+        } else {
+          s = b;
+        }
+      }
+      srcb[tid] = s;
+      dcx[tid] = dx;
+      dcy[tid] = dy;
+      dcz[tid] = dz;
+      has = s >= 0;
+    }
+    if (!__syncthreads_or(has)) continue;
+    const T* opp = a.ops + (int64_t)op * R * R;
+    for (int k0 = 0; k0 < R; k0 += BK) {
+      // A tile: rows row0.., cols k0..  (As[kk][row])
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int e = tid * 4 + q;
+        int row = e / BK, kk = e % BK;
+        int gr = row0 + row, gk = k0 + kk;
+        As[kk][row] = (gr < R && gk < R) ? opp[(int64_t)gr * R + gk] : T(0);
+      }
+      if (C == 4) {
+        int kk = tid / 16, j = tid % 16;
+        int gk = k0 + kk;
+        int s = srcb[j];
+        T4 v;
+        if (s >= 0 && gk < R) {
+          v = reinterpret_cast<const T4*>(a.in)[(int64_t)s * R + gk];
+          v.w = v.w + dcx[j] * v.x + dcy[j] * v.y + dcz[j] * v.z;
+        } else {
+          v.x = v.y = v.z = v.w = 0;
+        }
+        Bs[kk][j * 4 + 0] = v.x;
+        Bs[kk][j * 4 + 1] = v.y;
+        Bs[kk][j * 4 + 2] = v.z;
+        Bs[kk][j * 4 + 3] = v.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int j = tid & 63, kk = (tid >> 6) + 4 * q;
+          int gk = k0 + kk, s = srcb[j];
+          Bs[kk][j] = (s >= 0 && gk < R) ? a.in[(int64_t)s * R + gk] : T(0);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+      }
+      __syncthreads();
+    }
+  }
+  bool accumulate = a.mode == GM_M2L || a.mode == GM_L2L;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int row = row0 + ty * 4 + i;
+    if (row >= R) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int col = tx * 4 + j;
+      int bj = col / C, c = col % C;
+      int b = ob[bj];
+      if (b < 0) continue;
+      T* o = a.out + ((int64_t)b * R + row) * C + c;
+      T v = alph[bj] * acc[i][j];
+      if (accumulate)
+        *o += v;
+      else
+        *o = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Leaf kernel: L->T (own downward equivalent density), M->T over the W list, S->T over the
+// U list (source tiles staged by bulk async copies), one block per target leaf.
+template <class T, int PR>
+struct LeafArgs {
+  TreeView t;
+  Geo geo;
+  const typename V4<T>::type* spos;  // sorted sources
+  const typename V4<T>::type* sval;
+  const typename V4<T>::type* tpos;  // sorted targets
+  const T* unit;
+  const T* dn_equiv;                 // [nbox][R][C]
+  const T* up_equiv;
+  const int* leaves;
+  const int64_t* u_off;
+  const int32_t* u_ent;
+  const int64_t* w_off;
+  const int32_t* w_ent;
+  T* g;                              // sorted targets [nt][KT]
+  unsigned* status;
+  int n, R, near_only, kahan;
+  int cap;                           // staging capacity in sources
+};
+
+constexpr int LEAF_THREADS = 128;
+constexpr int LEAF_MAX_ENT = 64;
+
+template <class T, int PR>
+__device__ inline void far_eval(T xl, T yl, T zl, const typename V4<T>::type& p,
+                                const typename V4<T>::type& q, T* acc) {
+  // p: equivalent point (local coords), q: its density (C = 4: four channels; C = 1 G: q.xyz).
+  T r0 = xl - p.x, r1 = yl - p.y, r2 = zl - p.z;
+  if (PR == P_LAP) {
+    lap_st<T>(r0, r1, r2, q.x, acc);
+  } else if (PR == P_STK_L4 || PR == P_RPY_L4) {
+    // 8 pi u_i = 2 [phi_i - x_j d_i phi_j + d_i phi_4] with phi = q/r (reference: leaf centre)
+    T rr = r0 * r0 + r1 * r1 + r2 * r2;
+    T ir = inv_r(rr);
+    T ir3 = ir * ir * ir;
+    T tq = (xl * q.x + yl * q.y + zl * q.z - q.w) * ir3;
+    acc[0] += q.x * ir + r0 * tq;
+    acc[1] += q.y * ir + r1 * tq;
+    acc[2] += q.z * ir + r2 * tq;
+    if (PR == P_RPY_L4) {  // 4 pi lap u_i = q_i / r^3 - 3 r_i (r.q) / r^5
+      T c3 = T(3) * (r0 * q.x + r1 * q.y + r2 * q.z) * ir * ir;
+      acc[3] += (q.x - r0 * c3) * ir3;
+      acc[4] += (q.y - r1 * c3) * ir3;
+      acc[5] += (q.z - r2 * c3) * ir3;
+    }
+  } else if (PR == P_STK_G) {
+    stk_st<T>(r0, r1, r2, q.x, q.y, q.z, acc);
+  } else if (PR == P_RPY_G) {
+    rpy_st<T>(r0, r1, r2, q.x, q.y, q.z, T(0), acc);
+  }
+}
+
+template <class T, int PR>
+__global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
+  using T4 = typename V4<T>::type;
+  constexpr int KT = ProbInfo<PR>::KT, C = ProbInfo<PR>::C, D = ProbInfo<PR>::D, NV = ProbInfo<PR>::NV;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T4* sp = reinterpret_cast<T4*>(smem_raw);          // [cap]
+  T4* sv = sp + a.cap;                                // [cap * NV]
+  T* red = reinterpret_cast<T*>(sv + a.cap * NV);     // [LEAF_THREADS * KT]
+  __shared__ uint64_t bar;
+  __shared__ int ent_n, ent_cnt[LEAF_MAX_ENT], ent_sc[LEAF_MAX_ENT];
+  __shared__ int next_e, next_s, done;
+
+  int b = a.leaves[blockIdx.x];
+  T cx, cy, cz, r;
+  box_centre<T>(a.t, b, a.geo.L, a.geo.org, cx, cy, cz, r);
+  int t0 = a.t.tb[b], t1 = a.t.te[b];
+  int nt = t1 - t0;
+  if (nt <= 0) return;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  int ntp = ((nt + 31) / 32) * 32;
+  if (ntp > LEAF_THREADS) ntp = LEAF_THREADS;
+  int G = LEAF_THREADS / ntp;
+  int grp = threadIdx.x / ntp, ti = threadIdx.x % ntp;
+  if (grp >= G) grp = -1;
+  int64_t u0 = a.u_off[b], u1 = a.u_off[b + 1];
+  for (int c0 = t0; c0 < t1; c0 += ntp) {
+    int it = c0 + ti;
+    bool act = grp >= 0 && it < t1;
+    T xl = 0, yl = 0, zl = 0;
+    if (act) {
+      T4 x = a.tpos[it];
+      xl = x.x - cx;
+      yl = x.y - cy;
+      zl = x.z - cz;
+    }
+    T acc[KT], far[KT], comp[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) acc[k] = far[k] = comp[k] = 0;
+
+    if (!a.near_only) {
+      // ---- L->T and M->T: equivalent points staged (local coordinates, reference c_B)
+      int nw = (int)(a.w_off[b + 1] - a.w_off[b]);
+      for (int e = -1; e < nw; ++e) {
+        int sbx = b, sc = 13;
+        T alpha = T(ALPHA_DE);
+        const T* dens = a.dn_equiv;
+        if (e >= 0) {
+          int32_t ent = a.w_ent[a.w_off[b] + e];
+          sbx = entry_box(ent);
+          sc = entry_shift(ent);
+          alpha = T(ALPHA_UE);
+          dens = a.up_equiv;
+        }
+        int sx, sy, sz;
+        shift_decode(sc, sx, sy, sz);
+        T ax, ay, az, ar;
+        box_centre<T>(a.t, sbx, a.geo.L, a.geo.org, ax, ay, az, ar);
+        T ox = ax + (T)(sx * a.geo.L) - cx, oy = ay + (T)(sy * a.geo.L) - cy,
+          oz = az + (T)(sz * a.geo.L) - cz;
+        __syncthreads();
+        for (int k = threadIdx.x; k < a.n; k += blockDim.x) {
+          T4 p;
+          p.x = ox + alpha * ar * a.unit[3 * k];
+          p.y = oy + alpha * ar * a.unit[3 * k + 1];
+          p.z = oz + alpha * ar * a.unit[3 * k + 2];
+          p.w = 0;
+          const T* dp = dens + ((int64_t)sbx * a.R + (int64_t)k * D) * C;
+          T4 q;
+          if (C == 4) {
+            q = *reinterpret_cast<const T4*>(dp);
+            q.w = q.w + ox * q.x + oy * q.y + oz * q.z;  // re-reference to c_B
+          } else if (D == 3) {
+            q.x = dp[0];
+            q.y = dp[1];
+            q.z = dp[2];
+            q.w = 0;
+          } else {
+            q.x = dp[0];
+            q.y = q.z = q.w = 0;
+          }
+          sp[k] = p;
+          sv[k] = q;
+        }
+        __syncthreads();
+        if (act)
+          for (int k = grp; k < a.n; k += G) far_eval<T, PR>(xl, yl, zl, sp[k], sv[k], far);
+      }
+    }
+
+    // ---- S->T over the U list, staged in batches of whole (or split) entries
+    if (threadIdx.x == 0) {
+      next_e = (int)u0;
+      next_s = 0;
+    }
+    __syncthreads();
+    while (true) {
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        int used = 0, ne = 0;
+        uint32_t bytes = 0;
+        while (next_e < u1 && ne < LEAF_MAX_ENT && used < a.cap) {
+          int32_t ent = a.u_ent[next_e];
+          int sbx = entry_box(ent);
+          int s0 = a.t.sb[sbx] + next_s, s1 = a.t.se[sbx];
+          int take = min(s1 - s0, a.cap - used);
+          if (take > 0) {
+            bulk_g2s(sp + used, a.spos + s0, (uint32_t)(take * sizeof(T4)), &bar);
+            bulk_g2s(sv + used * NV, a.sval + (int64_t)s0 * NV, (uint32_t)(take * NV * sizeof(T4)), &bar);
+            bytes += (uint32_t)(take * (1 + NV) * sizeof(T4));
+            ent_cnt[ne] = take;
+            ent_sc[ne] = entry_shift(ent);
+            ++ne;
+            used += take;
+          }
+          if (s0 + take >= s1) {
+            ++next_e;
+            next_s = 0;
+          } else {
+            next_s += take;
+          }
+        }
+        ent_n = ne;
+        done = ne == 0;
+        if (ne > 0) mbar_expect_tx(&bar, bytes);
+      }
+      __syncthreads();
+      if (done) break;
+      // wait for this batch (bounded)
+      mbar_wait_bounded(&bar, phase, a.status);
+      phase ^= 1;
+      if (act) {
+        int base = 0;
+        for (int e = 0; e < ent_n; ++e) {
+          int sx, sy, sz;
+          shift_decode(ent_sc[e], sx, sy, sz);
+          T ox = (T)(sx * a.geo.L) - cx, oy = (T)(sy * a.geo.L) - cy, oz = (T)(sz * a.geo.L) - cz;
+          int cnt = ent_cnt[e];
+          for (int j = grp; j < cnt; j += G) {
+            T4 y = sp[base + j];
+            T r0 = xl - (y.x + ox), r1 = yl - (y.y + oy), r2 = zl - (y.z + oz);
+            T tmp[KT];
+#pragma unroll
+            for (int k = 0; k < KT; ++k) tmp[k] = 0;
+            T4 v = sv[(base + j) * NV];
+            if (PR == P_LAP) {
+              lap_st<T>(r0, r1, r2, v.x, tmp);
+            } else if (PR == P_STK_L4 || PR == P_STK_G) {
+              stk_st<T>(r0, r1, r2, v.x, v.y, v.z, tmp);
+            } else if (PR == P_RPY_L4 || PR == P_RPY_G) {
+              rpy_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
+            } else {
+              T4 v1 = sv[(base + j) * NV + 1], v2 = sv[(base + j) * NV + 2];
+              T Dm[9] = {v.x, v.y, v.z, v.w, v1.x, v1.y, v1.z, v1.w, v2.x};
+              dl_st<T>(r0, r1, r2, Dm, tmp);
+            }
+            if (a.kahan) {
+#pragma unroll
+              for (int k = 0; k < KT; ++k) {
+                T yk = tmp[k] - comp[k];
+                T tk = acc[k] + yk;
+                comp[k] = (tk - acc[k]) - yk;
+                acc[k] = tk;
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < KT; ++k) acc[k] += tmp[k];
+            }
+          }
+          base += cnt;
+        }
+      }
+      __syncthreads();
+    }
+    // ---- combine the thread groups and write
+#pragma unroll
+    for (int k = 0; k < KT; ++k) acc[k] += far[k];
+    if (G > 1) {
+      if (grp >= 0)
+#pragma unroll
+        for (int k = 0; k < KT; ++k) red[(grp * ntp + ti) * KT + k] = acc[k];
+      __syncthreads();
+      if (grp == 0) {
+        for (int q = 1; q < G; ++q)
+#pragma unroll
+          for (int k = 0; k < KT; ++k) acc[k] += red[(q * ntp + ti) * KT + k];
+      }
+      __syncthreads();
+    }
+    if (grp == 0 && it < t1) {
+#pragma unroll
+      for (int k = 0; k < KT; ++k) a.g[(int64_t)it * KT + k] = acc[k] * out_scale<PR, T>(k);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host side.
+#define CK(call)                                           \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(P, e_, #call); \
+  } while (0)
+
+static int grid_for(int64_t n, int threads, int maxb = 152 * 8) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > maxb) b = maxb;
+  return (int)b;
+}
+
+static void add_tiles(WorkLists& W, std::vector<int>* by_cls, int NB, int range[2]) {
+  range[0] = (int)W.tiles.size();
+  for (int c = 0; c < 8; ++c) {
+    std::vector<int>& v = by_cls[c];
+    for (size_t i = 0; i < v.size(); i += NB) {
+      int cnt = (int)std::min<size_t>(NB, v.size() - i);
+      W.tiles.push_back(make_int4((int)W.boxlist.size(), cnt, c, 0));
+      W.boxlist.insert(W.boxlist.end(), v.begin() + i, v.begin() + i + cnt);
+    }
+    v.clear();
+  }
+  range[1] = (int)W.tiles.size();
+}
+
+int build_worklists(Plan& P, int NB, int NB_TC) {
+  Tree& T = P.tree;
+  cudaStream_t st = P.stream;
+  int nb = T.nbox;
+  std::vector<uint64_t> key(nb);
+  std::vector<int8_t> lvl(nb), leaf(nb), wflag(nb);
+  std::vector<int64_t> xoff(nb + 1);
+  std::vector<int> tb(nb), te(nb);
+  CK(cudaMemcpyAsync(key.data(), T.key.p, 8 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(lvl.data(), T.level.p, nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(leaf.data(), T.leaf.p, nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(wflag.data(), T.w_flag.p, nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(xoff.data(), T.x_off.p, 8 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(tb.data(), T.tb.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(te.data(), T.te.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  WorkLists& W = P.wl;
+  W = WorkLists();
+  std::vector<int> by_cls[8];
+  auto cls = [&](int b) {
+    uint64_t k = key[b];
+    return (int)((k & 1) | ((k >> 1) & 1) << 1 | ((k >> 2) & 1) << 2);
+  };
+  int vmin = P.bc == KAFMM_BC_PXYZ ? 1 : 2;
+  // M->L: all boxes at levels >= vmin, grouped by class; tensor-core tiles use NB_TC boxes
+  for (int b = 0; b < nb; ++b)
+    if (lvl[b] >= vmin) by_cls[cls(b)].push_back(b);
+  add_tiles(W, by_cls, NB_TC, W.m2l);
+  // M->M per level: non-leaf boxes (class irrelevant: use class 0 bucket)
+  for (int l = 0; l < MAX_LEVELS; ++l) {
+    for (int b = T.lvl_start[l]; b < T.lvl_start[l + 1]; ++b)
+      if (!leaf[b]) by_cls[0].push_back(b);
+    add_tiles(W, by_cls, NB, W.m2m[l]);
+  }
+  // L->L per level (levels >= vmin + 1; and level 1 from the root when periodic)
+  for (int l = 0; l < MAX_LEVELS; ++l) {
+    if (l >= 1 && (l >= vmin + 1 || P.bc == KAFMM_BC_PXYZ))
+      for (int b = T.lvl_start[l]; b < T.lvl_start[l + 1]; ++b) by_cls[cls(b)].push_back(b);
+    add_tiles(W, by_cls, NB, W.l2l[l]);
+  }
+  // pseudo-inverses: up for boxes in W lists, down for leaves with targets
+  for (int b = 0; b < nb; ++b)
+    if (wflag[b]) by_cls[0].push_back(b);
+  add_tiles(W, by_cls, NB, W.pup);
+  for (int b = 0; b < nb; ++b)
+    if (leaf[b] && te[b] > tb[b]) by_cls[0].push_back(b);
+  add_tiles(W, by_cls, NB, W.pdn);
+  // plain lists: leaves (with targets) and boxes with X entries
+  W.leafbox_off = (int)W.boxlist.size();
+  for (int b = 0; b < nb; ++b)
+    if (leaf[b] && te[b] > tb[b]) W.boxlist.push_back(b);
+  W.leaves_n = (int)W.boxlist.size() - W.leafbox_off;
+  W.xbox_off = (int)W.boxlist.size();
+  for (int b = 0; b < nb; ++b)
+    if (xoff[b + 1] > xoff[b]) W.boxlist.push_back(b);
+  W.xbox_n = (int)W.boxlist.size() - W.xbox_off;
+  // S->M work: leaves (with sources)
+  CK(P.tiles.reserve(sizeof(int4) * (W.tiles.size() + 1)));
+  CK(P.tile_meta.reserve(sizeof(int) * (W.boxlist.size() + nb + 1)));
+  CK(cudaMemcpyAsync(P.tiles.p, W.tiles.data(), sizeof(int4) * W.tiles.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(P.tile_meta.p, W.boxlist.data(), sizeof(int) * W.boxlist.size(),
+                     cudaMemcpyHostToDevice, st));
+  // leaves with sources (for S->M) appended after boxlist
+  std::vector<int> sleaves;
+  std::vector<int> sb(nb), se(nb);
+  CK(cudaMemcpyAsync(sb.data(), T.sb.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(se.data(), T.se.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int b = 0; b < nb; ++b)
+    if (leaf[b]) sleaves.push_back(b);
+  W.boxlist.insert(W.boxlist.end(), sleaves.begin(), sleaves.end());
+  CK(cudaMemcpyAsync(P.tile_meta.as<int>() + (W.boxlist.size() - sleaves.size()), sleaves.data(),
+                     sizeof(int) * sleaves.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return 0;
+}
+
+template <class T, int PR>
+static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
+  using T4 = typename V4<T>::type;
+  constexpr int KT = ProbInfo<PR>::KT, C = ProbInfo<PR>::C, NV = ProbInfo<PR>::NV;
+  Tree& T_ = P.tree;
+  cudaStream_t st = P.stream;
+  WorkLists& W = P.wl;
+  int nb = T_.nbox;
+  int R = P.R;
+  int64_t ns = T_.n_src, nt = T_.n_trg;
+  Geo geo;
+  geo.L = P.L;
+  for (int d = 0; d < 3; ++d) geo.org[d] = P.origin[d];
+  TreeView tv = T_.view();
+  tv.periodic = P.bc == KAFMM_BC_PXYZ;
+  const T* unit = P.fp64() ? (const T*)P.unit64.p : (const T*)P.unit32.p;
+  const T* ops = P.fp64() ? (const T*)P.ops64.p : (const T*)P.ops32.p;
+
+  cudaEventRecord(P.ev[3], st);
+  // source values -> sorted records
+  CK(P.s_sorted.reserve(sizeof(T4) * NV * (ns + 1)));
+  if (ns > 0) {
+    if (s_dtype == KAFMM_F64)
+      k_prep_src<double, T, PR><<<grid_for(ns, 256), 256, 0, st>>>(
+          (const double*)s_in, T_.src_perm.as<uint32_t>(), ns, P.s_sorted.as<T4>());
+    else
+      k_prep_src<float, T, PR><<<grid_for(ns, 256), 256, 0, st>>>(
+          (const float*)s_in, T_.src_perm.as<uint32_t>(), ns, P.s_sorted.as<T4>());
+  }
+  const T4* spos = T_.src_pos.as<T4>();
+  const T4* tpos = T_.same ? spos : T_.trg_pos.as<T4>();
+  size_t box_bytes = sizeof(T) * (size_t)R * C;
+  int* boxlist = P.tile_meta.as<int>();
+  int n_sleaves = (int)(W.boxlist.size()) - (W.xbox_off + W.xbox_n);
+  const int* sleaves = boxlist + W.xbox_off + W.xbox_n;
+  if (!P.near_only) {
+    CK(P.up_check.reserve(box_bytes * nb));
+    CK(P.dn_check.reserve(box_bytes * nb));
+    CK(P.up_equiv.reserve(box_bytes * nb));
+    CK(P.dn_equiv.reserve(box_bytes * nb));
+    CK(cudaMemsetAsync(P.dn_check.p, 0, box_bytes * nb, st));
+    // S->M at the leaves
+    S2CArgs<T, PR> sa;
+    sa.t = tv;
+    sa.geo = geo;
+    sa.pos = spos;
+    sa.val = P.s_sorted.as<T4>();
+    sa.unit = unit;
+    sa.x_off = T_.x_off.as<int64_t>();
+    sa.x_ent = T_.x_ent.as<int32_t>();
+    sa.n = P.n;
+    sa.R = R;
+    if (n_sleaves > 0) {
+      sa.boxes = sleaves;
+      sa.check = P.up_check.as<T>();
+      sa.mode = 0;
+      k_s2check<T, PR><<<n_sleaves, 128, 0, st>>>(sa);
+    }
+    // M->M, deepest level first
+    GemmArgs<T> ga;
+    ga.t = tv;
+    ga.geo = geo;
+    ga.ops = ops;
+    ga.tiles = P.tiles.as<int4>();
+    ga.boxlist = boxlist;
+    ga.vtab = T_.vtab.as<int32_t>();
+    ga.R = R;
+    dim3 blk(256);
+    int rb = (R + 63) / 64;
+    for (int l = MAX_LEVELS - 1; l >= 0; --l) {
+      int n = W.m2m[l][1] - W.m2m[l][0];
+      if (n <= 0) continue;
+      ga.mode = GM_M2M;
+      ga.in = P.up_check.as<T>();
+      ga.out = P.up_check.as<T>();
+      ga.tiles = P.tiles.as<int4>() + W.m2m[l][0];
+      k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+    }
+    cudaEventRecord(P.ev[4], st);
+    // M->L over the V lists (all levels)
+    int nm2l = W.m2l[1] - W.m2l[0];
+    if (nm2l > 0) {
+      if (P.use_tc && !P.fp64() && P.prec == KAFMM_PREC_MIXED && C == 4 && sizeof(T) == 4) {
+        int rc = m2l_tc_launch(P, P.tiles.as<int4>() + W.m2l[0], nm2l, boxlist, st);
+        if (rc) return rc;
+      } else {
+        ga.mode = GM_M2L;
+        ga.in = P.up_check.as<T>();
+        ga.out = P.dn_check.as<T>();
+        ga.tiles = P.tiles.as<int4>() + W.m2l[0];
+        k_gemm<T, C><<<dim3(nm2l, rb), blk, 0, st>>>(ga);
+      }
+    }
+    cudaEventRecord(P.ev[5], st);
+    // S->L over the X lists
+    if (W.xbox_n > 0) {
+      sa.boxes = boxlist + W.xbox_off;
+      sa.check = P.dn_check.as<T>();
+      sa.mode = 1;
+      k_s2check<T, PR><<<W.xbox_n, 128, 0, st>>>(sa);
+    }
+    // L->L, coarsest level first
+    for (int l = 0; l < MAX_LEVELS; ++l) {
+      int n = W.l2l[l][1] - W.l2l[l][0];
+      if (n <= 0) continue;
+      ga.mode = GM_L2L;
+      ga.in = P.dn_check.as<T>();
+      ga.out = P.dn_check.as<T>();
+      ga.tiles = P.tiles.as<int4>() + W.l2l[l][0];
+      k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+    }
+    // equivalent densities where they are evaluated at targets
+    int n = W.pup[1] - W.pup[0];
+    if (n > 0) {
+      ga.mode = GM_PINV_UP;
+      ga.in = P.up_check.as<T>();
+      ga.out = P.up_equiv.as<T>();
+      ga.tiles = P.tiles.as<int4>() + W.pup[0];
+      k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+    }
+    n = W.pdn[1] - W.pdn[0];
+    if (n > 0) {
+      ga.mode = GM_PINV_DN;
+      ga.in = P.dn_check.as<T>();
+      ga.out = P.dn_equiv.as<T>();
+      ga.tiles = P.tiles.as<int4>() + W.pdn[0];
+      k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+    }
+  }
+  cudaEventRecord(P.ev[6], st);
+  // leaves
+  CK(P.g_sorted.reserve(sizeof(T) * KT * (nt + 1)));
+  if (W.leaves_n > 0) {
+    LeafArgs<T, PR> la;
+    la.t = tv;
+    la.geo = geo;
+    la.spos = spos;
+    la.sval = P.s_sorted.as<T4>();
+    la.tpos = tpos;
+    la.unit = unit;
+    la.dn_equiv = P.dn_equiv.as<T>();
+    la.up_equiv = P.up_equiv.as<T>();
+    la.leaves = boxlist + W.leafbox_off;
+    la.u_off = T_.u_off.as<int64_t>();
+    la.u_ent = T_.u_ent.as<int32_t>();
+    la.w_off = T_.w_off.as<int64_t>();
+    la.w_ent = T_.w_ent.as<int32_t>();
+    la.g = P.g_sorted.as<T>();
+    la.status = T_.status.as<unsigned>();
+    la.n = P.n;
+    la.R = R;
+    la.near_only = P.near_only;
+    la.kahan = P.kahan;
+    int cap = (int)(40960 / ((1 + NV) * sizeof(T4)));
+    if (cap < P.n) cap = P.n;
+    la.cap = cap;
+    size_t smem = (size_t)cap * (1 + NV) * sizeof(T4) + sizeof(T) * LEAF_THREADS * KT;
+    CK(cudaFuncSetAttribute(k_leaf<T, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_leaf<T, PR><<<W.leaves_n, LEAF_THREADS, smem, st>>>(la);
+  }
+  CK(cudaGetLastError());
+  // back to the caller's order and dtype
+  if (nt > 0) {
+    const uint32_t* tperm = T_.same ? T_.src_perm.as<uint32_t>() : T_.trg_perm.as<uint32_t>();
+    if (s_dtype == KAFMM_F64)
+      k_unperm<T, double><<<grid_for(nt * KT, 256), 256, 0, st>>>(P.g_sorted.as<T>(), tperm, nt, KT,
+                                                                (double*)g_out);
+    else
+      k_unperm<T, float><<<grid_for(nt * KT, 256), 256, 0, st>>>(P.g_sorted.as<T>(), tperm, nt, KT,
+                                                               (float*)g_out);
+  }
+  cudaEventRecord(P.ev[7], st);
+  CK(cudaGetLastError());
+  return 0;
+}
+
+int evaluate(Plan& P, const void* s, void* g, int dtype) {
+  int pr;
+  if (P.kernel == KAFMM_LAPLACE)
+    pr = P_LAP;
+  else if (P.kernel == KAFMM_STOKESLET)
+    pr = P.C == 4 ? P_STK_L4 : P_STK_G;
+  else if (P.kernel == KAFMM_RPY)
+    pr = P.C == 4 ? P_RPY_L4 : P_RPY_G;
+  else
+    pr = P_DL;
+  (void)dtype;
+  int sd = dtype;
+#define DISPATCH(T)                                          \
+  switch (pr) {                                              \
+    case P_LAP: return run_eval<T, P_LAP>(P, s, sd, g);      \
+    case P_STK_L4: return run_eval<T, P_STK_L4>(P, s, sd, g); \
+    case P_STK_G: return run_eval<T, P_STK_G>(P, s, sd, g);  \
+    case P_RPY_L4: return run_eval<T, P_RPY_L4>(P, s, sd, g); \
+    case P_RPY_G: return run_eval<T, P_RPY_G>(P, s, sd, g);  \
+    default: return run_eval<T, P_DL>(P, s, sd, g);          \
+  }
+  if (P.fp64()) {
+    DISPATCH(double)
+  } else {
+    DISPATCH(float)
+  }
+#undef DISPATCH
+}
+
+}  // namespace kafmm

@@ -1,0 +1,336 @@
+// FP64 translation operators, built on the device at plan time.
+//
+// KIFMM matches potentials on check surfaces with equivalent densities (Sec. II); the
+// check-to-equivalent map is the pseudo-inverse of a kernel matrix (Sec. II: an SVD
+// pseudo-inverse as in PVFMM).  The ML-tree kernels (Laplace 1/(4 pi r), Stokeslet G) are
+// homogeneous of degree -1, so with every box described in units of its own half-width the
+// operators do not depend on the level.  The evaluator keeps the check potentials of each box
+// and folds the pseudo-inverse into the translation operators:
+//   M->L(o)  = K(dc <- ue at offset o) * UC2UE
+//   M->M(c)  = K(uc parent <- ue child c) * UC2UE
+//   L->L(c)  = 2 K(dc child c <- de parent) * DC2DE
+// (geometry in units of the half-width of the child / of the box), which equals the paper's
+// sequence "equivalent density = pinv * check, then translate" up to rounding.
+#include <cmath>
+
+#include "plan.cuh"
+
+namespace kafmm {
+
+std::vector<double> unit_surface(int m) {
+  std::vector<double> pts;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j)
+      for (int k = 0; k < m; ++k) {
+        int lo = std::min(i, std::min(j, k)), hi = std::max(i, std::max(j, k));
+        if (lo == 0 || hi == m - 1) {
+          pts.push_back(-1.0 + 2.0 * i / (m - 1));
+          pts.push_back(-1.0 + 2.0 * j / (m - 1));
+          pts.push_back(-1.0 + 2.0 * k / (m - 1));
+        }
+      }
+  return pts;
+}
+
+// K[i][j] (R x R): target points ct + at * s_i, source points cs + as * s_j.
+__global__ void k_fill_kernel_matrix(const double* __restrict__ unit, int n, int stokes, double ctx,
+                                     double cty, double ctz, double at, double csx, double csy,
+                                     double csz, double as, double* __restrict__ K) {
+  int R = stokes ? 3 * n : n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / n), j = (int)(e % n);
+    double r0 = (ctx + at * unit[3 * i]) - (csx + as * unit[3 * j]);
+    double r1 = (cty + at * unit[3 * i + 1]) - (csy + as * unit[3 * j + 1]);
+    double r2 = (ctz + at * unit[3 * i + 2]) - (csz + as * unit[3 * j + 2]);
+    double rr = r0 * r0 + r1 * r1 + r2 * r2;
+    double rn = sqrt(rr);
+    if (!stokes) {
+      K[(int64_t)i * R + j] = 1.0 / (4.0 * PI * rn);
+    } else {
+      double r[3] = {r0, r1, r2};
+      double inv = 1.0 / (8.0 * PI * rn), inv3 = inv / rr;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+          K[(int64_t)(3 * i + a) * R + 3 * j + b] = (a == b ? inv : 0.0) + r[a] * r[b] * inv3;
+    }
+  }
+}
+
+// Transpose: out[j][i] = in[i][j].
+__global__ void k_transpose(const double* __restrict__ in, int n, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / n), j = (int)(e % n);
+    out[(int64_t)j * n + i] = in[e];
+  }
+}
+
+__global__ void k_identity(double* V, int n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    V[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
+// One round of one-sided (Hestenes) Jacobi on the rows of At (= columns of A): the n/2
+// disjoint pairs of the round-robin schedule, one block per pair.
+__global__ void k_jacobi_round(double* __restrict__ At, double* __restrict__ Vt, int n, int round,
+                               int* rotated, double tol) {
+  __shared__ double red[3][32];
+  __shared__ double cs[2];
+  int p = blockIdx.x;
+  auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + round) % (n - 1)) + 1; };
+  int i = player(p), j = player(n - 1 - p);
+  double* ai = At + (int64_t)i * n;
+  double* aj = At + (int64_t)j * n;
+  double a = 0, b = 0, g = 0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double x = ai[k], y = aj[k];
+    a += x * x;
+    b += y * y;
+    g += x * y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    g += __shfl_down_sync(0xffffffffu, g, o);
+  }
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][w] = a;
+    red[1][w] = b;
+    red[2][w] = g;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = b = g = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      b += red[1][k];
+      g += red[2][k];
+    }
+    double c = 1.0, s = 0.0;
+    if (fabs(g) > tol * sqrt(a * b) && a > 0 && b > 0) {
+      double zeta = (b - a) / (2.0 * g);
+      double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      c = 1.0 / sqrt(1.0 + t * t);
+      s = c * t;
+      *rotated = 1;
+    }
+    cs[0] = c;
+    cs[1] = s;
+  }
+  __syncthreads();
+  double c = cs[0], s = cs[1];
+  if (s == 0.0) return;
+  double* vi = Vt + (int64_t)i * n;
+  double* vj = Vt + (int64_t)j * n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double x = ai[k], y = aj[k];
+    ai[k] = c * x - s * y;
+    aj[k] = s * x + c * y;
+    x = vi[k];
+    y = vj[k];
+    vi[k] = c * x - s * y;
+    vj[k] = s * x + c * y;
+  }
+}
+
+__global__ void k_row_norms(const double* At, int n, double* w) {
+  int k = blockIdx.x;
+  double s = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += At[(int64_t)k * n + i] * At[(int64_t)k * n + i];
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    w[k] = t;  // sigma_k^2
+  }
+}
+
+// w[k] <- 1 / sigma_k^2 for sigma_k >= rcond * sigma_max, else 0.
+__global__ void k_pinv_weights(double* w, int n, double rcond) {
+  __shared__ double smax;
+  if (threadIdx.x == 0) {
+    double m = 0;
+    for (int k = 0; k < n; ++k) m = fmax(m, w[k]);
+    smax = m;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double s2 = w[k];
+    w[k] = (s2 > 0 && sqrt(s2) >= rcond * sqrt(smax)) ? 1.0 / s2 : 0.0;
+  }
+}
+
+// C = alpha * op(A) * diag(w) * B with op(A) = A^T when ta (A stored [k][i]) else A ([i][k]).
+// Plain 32x32-tiled FP64 GEMM; n x n x n.
+__global__ void k_gemm64(const double* __restrict__ A, int ta, const double* __restrict__ w,
+                         const double* __restrict__ B, double alpha, int n, double* __restrict__ Cm) {
+  __shared__ double As[32][33], Bs[32][33];
+  int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  double acc[4] = {0, 0, 0, 0};
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      int i = i0 + r, k = k0 + tx;
+      double av = 0;
+      if (ta) {
+        int kk = k0 + r, ii = i0 + tx;  // As[r=k][tx=i]
+        av = (kk < n && ii < n) ? A[(int64_t)kk * n + ii] * (w ? w[kk] : 1.0) : 0.0;
+        As[tx][r] = av;
+      } else {
+        av = (i < n && k < n) ? A[(int64_t)i * n + k] * (w ? w[k] : 1.0) : 0.0;
+        As[r][tx] = av;
+      }
+      int kb = k0 + r, jb = j0 + tx;
+      Bs[r][tx] = (kb < n && jb < n) ? B[(int64_t)kb * n + jb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      double b = Bs[k][tx];
+      for (int q = 0; q < 4; ++q) acc[q] += As[ty + 8 * q][k] * b;
+    }
+    __syncthreads();
+  }
+  for (int q = 0; q < 4; ++q) {
+    int i = i0 + ty + 8 * q, j = j0 + tx;
+    if (i < n && j < n) Cm[(int64_t)i * n + j] = alpha * acc[q];
+  }
+}
+
+__global__ void k_round32(const double* in, int64_t n, float* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (float)in[e];
+}
+
+// Split into bf16 hi + lo with K padded to Rpad: out[(op*2 + h)][i][Rpad].
+__global__ void k_split_bf16(const double* in, int R, int Rpad, int64_t nops, __nv_bfloat16* out) {
+  int64_t total = nops * R * (int64_t)Rpad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t op = e / ((int64_t)R * Rpad);
+    int64_t rem = e % ((int64_t)R * Rpad);
+    int i = (int)(rem / Rpad), j = (int)(rem % Rpad);
+    float v = j < R ? (float)in[(op * R + i) * R + j] : 0.f;
+    __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    out[((op * 2 + 0) * R + i) * Rpad + j] = hi;
+    out[((op * 2 + 1) * R + i) * Rpad + j] = lo;
+  }
+}
+
+#define CK(call)                                           \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(P, e_, #call); \
+  } while (0)
+
+// pinv of K (R x R) into out, via one-sided Jacobi SVD.
+static int pinv64(Plan& P, const double* K, double* out, double* At, double* Vt, double* w, int* flag) {
+  int R = P.R;
+  cudaStream_t st = P.stream;
+  int g = 512;
+  k_transpose<<<g, 256, 0, st>>>(K, R, At);
+  k_identity<<<g, 256, 0, st>>>(Vt, R);
+  int sweeps = 0;
+  for (; sweeps < 60; ++sweeps) {
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    for (int r = 0; r < R - 1; ++r) k_jacobi_round<<<R / 2, 256, 0, st>>>(At, Vt, R, r, flag, 1e-15);
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (!h) break;
+  }
+  if (sweeps >= 60) return fail(P, KAFMM_ERR_CUDA, "Jacobi SVD did not converge");
+  k_row_norms<<<R, 256, 0, st>>>(At, R, w);
+  k_pinv_weights<<<1, 256, 0, st>>>(w, R, PINV_RCOND);
+  // pinv = V diag(1/sigma^2) A^T  (A = U S V^T  =>  A^+ = V S^-2 (A V)^T ... in row form:
+  // pinv[i][j] = sum_k Vt[k][i] w_k At[k][j])
+  dim3 gg((R + 31) / 32, (R + 31) / 32);
+  k_gemm64<<<gg, 256, 0, st>>>(Vt, 1, w, At, 1.0, R, out);
+  CK(cudaGetLastError());
+  return 0;
+}
+
+int build_operators(Plan& P) {
+  cudaStream_t st = P.stream;
+  int n = P.n, R = P.R;
+  std::vector<double> us = unit_surface(P.p);
+  CK(P.unit64.reserve(sizeof(double) * us.size()));
+  CK(P.unit32.reserve(sizeof(float) * us.size()));
+  CK(cudaMemcpyAsync(P.unit64.p, us.data(), sizeof(double) * us.size(), cudaMemcpyHostToDevice, st));
+  std::vector<float> uf(us.begin(), us.end());
+  CK(cudaMemcpyAsync(P.unit32.p, uf.data(), sizeof(float) * uf.size(), cudaMemcpyHostToDevice, st));
+
+  size_t RR = (size_t)R * R;
+  DevBuf ops, scratch;
+  CK(ops.reserve(sizeof(double) * RR * N_OPS));
+  CK(scratch.reserve(sizeof(double) * (RR * 4 + R + 64)));
+  double* O = ops.as<double>();
+  double* K = scratch.as<double>();
+  double* At = K + RR;
+  double* Vt = At + RR;
+  double* Tm = Vt + RR;
+  double* w = Tm + RR;
+  int* flag = (int*)(w + R + 8);
+  const double* unit = P.unit64.as<double>();
+  int g = 1024;
+  int stokes = P.ml_stokes;
+  // pseudo-inverses at half-width 1
+  k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, ALPHA_UC, 0, 0, 0, ALPHA_UE, K);
+  int rc = pinv64(P, K, O + RR * OP_UC2UE, At, Vt, w, flag);
+  if (rc) return rc;
+  k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, ALPHA_DC, 0, 0, 0, ALPHA_DE, K);
+  rc = pinv64(P, K, O + RR * OP_DC2DE, At, Vt, w, flag);
+  if (rc) return rc;
+  dim3 gg((R + 31) / 32, (R + 31) / 32);
+  // M->L: centres 2 o apart (box side 2)
+  for (int oz = -3; oz <= 3; ++oz)
+    for (int oy = -3; oy <= 3; ++oy)
+      for (int ox = -3; ox <= 3; ++ox) {
+        int idx = m2l_index(ox, oy, oz);
+        double* dst = O + RR * (OP_M2L + idx);
+        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) {
+          CK(cudaMemsetAsync(dst, 0, sizeof(double) * RR, st));
+          continue;
+        }
+        k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, ALPHA_DC, 2.0 * ox, 2.0 * oy,
+                                                2.0 * oz, ALPHA_UE, K);
+        k_gemm64<<<gg, 256, 0, st>>>(K, 0, nullptr, O + RR * OP_UC2UE, 1.0, R, dst);
+      }
+  // M->M / L->L: child half-width 1, parent half-width 2, child centre at +-1 per axis
+  for (int c = 0; c < 8; ++c) {
+    double cx = (c & 1) ? 1.0 : -1.0, cy = (c & 2) ? 1.0 : -1.0, cz = (c & 4) ? 1.0 : -1.0;
+    k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, 2.0 * ALPHA_UC, cx, cy, cz,
+                                            ALPHA_UE, K);
+    k_gemm64<<<gg, 256, 0, st>>>(K, 0, nullptr, O + RR * OP_UC2UE, 1.0, R, O + RR * (OP_M2M + c));
+    k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, cx, cy, cz, ALPHA_DC, 0, 0, 0,
+                                            2.0 * ALPHA_DE, K);
+    k_gemm64<<<gg, 256, 0, st>>>(K, 0, nullptr, O + RR * OP_DC2DE, 2.0, R, O + RR * (OP_L2L + c));
+  }
+  CK(cudaGetLastError());
+  if (P.fp64()) {
+    CK(P.ops64.reserve(sizeof(double) * RR * N_OPS));
+    CK(cudaMemcpyAsync(P.ops64.p, O, sizeof(double) * RR * N_OPS, cudaMemcpyDeviceToDevice, st));
+  } else {
+    CK(P.ops32.reserve(sizeof(float) * RR * N_OPS));
+    k_round32<<<2048, 256, 0, st>>>(O, (int64_t)RR * N_OPS, P.ops32.as<float>());
+    if (P.prec == KAFMM_PREC_MIXED) {
+      P.Rpad = (R + 63) / 64 * 64;
+      CK(P.opsbf.reserve(sizeof(__nv_bfloat16) * 2 * (size_t)R * P.Rpad * N_M2L));
+      k_split_bf16<<<2048, 256, 0, st>>>(O + RR * OP_M2L, R, P.Rpad, N_M2L, P.opsbf.as<__nv_bfloat16>());
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  P.ops_ready = true;
+  return 0;
+}
+
+}  // namespace kafmm

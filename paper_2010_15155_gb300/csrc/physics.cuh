@@ -1,0 +1,113 @@
+// Kernel functions of the summation problems (Yan & Blackwell, Sec. II), as device code.
+// r = x - y (target minus source); pairs with r^2 == 0 contribute nothing.
+#pragma once
+#include "common.cuh"
+
+namespace kafmm {
+
+// Problem = kernel + ML-tree table.
+enum Prob { P_LAP = 0, P_STK_L4 = 1, P_STK_G = 2, P_RPY_L4 = 3, P_RPY_G = 4, P_DL = 5 };
+
+template <int PR>
+struct ProbInfo;
+template <>
+struct ProbInfo<P_LAP> { static constexpr int KT = 1, C = 1, D = 1, NV = 1; };
+template <>
+struct ProbInfo<P_STK_L4> { static constexpr int KT = 3, C = 4, D = 1, NV = 1; };
+template <>
+struct ProbInfo<P_STK_G> { static constexpr int KT = 3, C = 1, D = 3, NV = 1; };
+template <>
+struct ProbInfo<P_RPY_L4> { static constexpr int KT = 6, C = 4, D = 1, NV = 1; };
+template <>
+struct ProbInfo<P_RPY_G> { static constexpr int KT = 6, C = 1, D = 3, NV = 1; };
+template <>
+struct ProbInfo<P_DL> { static constexpr int KT = 4, C = 1, D = 1, NV = 3; };
+
+template <class T>
+struct V4;
+template <>
+struct V4<float> { using type = float4; };
+template <>
+struct V4<double> { using type = double4; };
+
+template <class T>
+__device__ inline T rsqrt_(T x);
+template <>
+__device__ inline float rsqrt_<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ inline double rsqrt_<double>(double x) { return rsqrt(x); }
+
+// 1 / r for r^2 > 0, else 0.
+template <class T>
+__device__ inline T inv_r(T rr) { return rr > T(0) ? rsqrt_<T>(rr) : T(0); }
+
+// ---- S->T and the check potentials of S->M / S->L -------------------------------------------
+// Source values: v0 = (q | f1 f2 f3 [b]) ; DL: v0 = D00 D01 D02 D10, v1 = D11 D12 D20 D21,
+// v2 = D22.  acc has KT entries.
+
+// Laplace L = 1/(4 pi r)
+template <class T>
+__device__ inline void lap_st(T r0, T r1, T r2, T q, T* acc) {
+  T ir = inv_r(r0 * r0 + r1 * r1 + r2 * r2);
+  acc[0] += q * ir;  // scaled by 1/(4 pi) at the end
+}
+
+// Stokeslet u = (f / r + r (r.f) / r^3): scaled by 1/(8 pi) at the end
+template <class T>
+__device__ inline void stk_st(T r0, T r1, T r2, T f0, T f1, T f2, T* acc) {
+  T ir = inv_r(r0 * r0 + r1 * r1 + r2 * r2);
+  T ir3 = ir * ir * ir;
+  T rf = (r0 * f0 + r1 * f1 + r2 * f2) * ir3;
+  acc[0] += f0 * ir + r0 * rf;
+  acc[1] += f1 * ir + r1 * rf;
+  acc[2] += f2 * ir + r2 * rf;
+}
+
+// RPY: u = G f + b^2/6 lap G f, lap u = lap G f with lap G = (I/r^3 - 3 r r^T / r^5)/(4 pi).
+// acc[0..2] scaled by 1/(8 pi), acc[3..5] by 1/(4 pi) at the end:
+//   8 pi u   = f/r + r (r.f)/r^3 + b^2/3 (f/r^3 - 3 r (r.f)/r^5)
+//   4 pi lap = f/r^3 - 3 r (r.f)/r^5
+template <class T>
+__device__ inline void rpy_st(T r0, T r1, T r2, T f0, T f1, T f2, T b, T* acc) {
+  T ir = inv_r(r0 * r0 + r1 * r1 + r2 * r2);
+  T ir2 = ir * ir, ir3 = ir2 * ir;
+  T rf = r0 * f0 + r1 * f1 + r2 * f2;
+  T c3 = T(3) * rf * ir2;  // 3 (r.f)/r^2
+  T l0 = (f0 - r0 * c3) * ir3, l1 = (f1 - r1 * c3) * ir3, l2 = (f2 - r2 * c3) * ir3;
+  T bb = b * b * T(1.0 / 3.0);
+  T g = rf * ir3;
+  acc[0] += f0 * ir + r0 * g + bb * l0;
+  acc[1] += f1 * ir + r1 * g + bb * l1;
+  acc[2] += f2 * ir + r2 * g + bb * l2;
+  acc[3] += l0;
+  acc[4] += l1;
+  acc[5] += l2;
+}
+
+// Stokes double layer: 4 pi p = -3 (r.D.r)/r^5 + tr D / r^3 ; 8 pi u = -3 r (r.D.r) / r^5.
+// acc[0] scaled by 1/(4 pi), acc[1..3] by 1/(8 pi) at the end.
+template <class T>
+__device__ inline void dl_st(T r0, T r1, T r2, const T* Dm, T* acc) {
+  T ir = inv_r(r0 * r0 + r1 * r1 + r2 * r2);
+  T ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+  T rDr = r0 * (Dm[0] * r0 + Dm[1] * r1 + Dm[2] * r2) + r1 * (Dm[3] * r0 + Dm[4] * r1 + Dm[5] * r2) +
+          r2 * (Dm[6] * r0 + Dm[7] * r1 + Dm[8] * r2);
+  T tr = Dm[0] + Dm[4] + Dm[8];
+  acc[0] += -T(3) * rDr * ir5 + tr * ir3;
+  T c = -T(3) * rDr * ir5;
+  acc[1] += c * r0;
+  acc[2] += c * r1;
+  acc[3] += c * r2;
+}
+
+// Final scale factors of the accumulators.
+template <int PR, class T>
+__device__ inline T out_scale(int k) {
+  const T f4 = T(1.0 / (4.0 * PI)), f8 = T(1.0 / (8.0 * PI));
+  if (PR == P_LAP) return f4;
+  if (PR == P_STK_L4 || PR == P_STK_G) return f8;
+  if (PR == P_RPY_L4 || PR == P_RPY_G) return k < 3 ? f8 : f4;
+  return k == 0 ? f4 : f8;  // DL
+}
+
+}  // namespace kafmm

@@ -1,0 +1,113 @@
+// Plan object and the interfaces between the evaluator's translation units.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace kafmm {
+
+// Device-side view of the octree (boxes numbered level by level, Morton order per level).
+struct TreeView {
+  int nbox, nlevels, periodic;
+  const int* lvl_start;     // [MAX_LEVELS + 1] (device copy)
+  const uint64_t* key;      // cell key (Morton code of the anchor at the box's level)
+  const int8_t* level;      // [nbox]
+  const int* parent;        // [nbox], -1 for the root
+  const int* child;         // [nbox][8], -1 when absent
+  const int* sb;            // source range [sb, se) in sorted source order
+  const int* se;
+  const int* tb;            // target range [tb, te) in sorted target order
+  const int* te;
+  const int8_t* leaf;       // [nbox] 0/1
+};
+
+struct Tree {
+  int64_t n_src = 0, n_trg = 0;
+  bool same = true;
+  int nbox = 0, nleaf = 0, nlevels = 0;
+  int lvl_start[MAX_LEVELS + 1] = {0};
+  int64_t n_u = 0, n_w = 0, n_x = 0, n_v = 0, near_pairs = 0;
+  int max_leaf_pts = 0;
+  int dtype_pts = KAFMM_F32;       // dtype of the caller's points at set_points
+  // sorted points: perm[i] = caller index of sorted point i
+  DevBuf src_key, trg_key, src_perm, trg_perm;
+  DevBuf src_pos, trg_pos;          // compute-type xyz (float4 or double4, w unused)
+  // boxes
+  DevBuf d_lvl_start, key, level, parent, child, sb, se, tb, te, leaf, leaves;
+  // lists, CSR over boxes (entries packed with pack_entry)
+  DevBuf u_off, u_ent, w_off, w_ent, x_off, x_ent;
+  DevBuf vtab;                      // [nbox][189] source box of each V slot or -1
+  DevBuf w_flag;                    // [nbox] 1 if the box appears in some W list
+  // scratch of the build
+  DevBuf s_keys2, s_vals2, s_hist, t_keys2, t_vals2;
+  DevBuf bld_key, bld_sb, bld_se, bld_tb, bld_te, bld_parent, bld_child, bld_cnt, bld_nch,
+      bld_choff, bld_cb, bld_ctb;
+  DevBuf status;                    // unsigned status word
+  TreeView view() const;
+};
+
+// Work lists of the evaluation, built on the host after each set_points: tiles of boxes that
+// share an octant class (int4: offset into boxlist, count, class, 0).
+struct WorkLists {
+  std::vector<int> boxlist;
+  std::vector<int4> tiles;
+  int m2l[2] = {0, 0};                       // tile ranges
+  int m2m[MAX_LEVELS][2] = {};
+  int l2l[MAX_LEVELS][2] = {};
+  int pup[2] = {0, 0}, pdn[2] = {0, 0};
+  int leaves_n = 0, xbox_off = 0, xbox_n = 0, leafbox_off = 0;  // plain box lists
+};
+
+struct Plan {
+  // problem
+  int kernel = 0, bc = 0, p = 0, q = 0;
+  int prec = KAFMM_PREC_MIXED, variant = KAFMM_ML_L4, near_only = 0, kahan = 0;
+  cudaStream_t stream = 0;
+  double origin[3] = {0, 0, 0}, L = 1.0;
+  int ks = 1, kt = 1;
+  int ml_stokes = 0;   // ML-tree kernel: 0 Laplace, 1 Stokeslet
+  int C = 1;           // ML columns (4 for the four-channel Laplace table)
+  int D = 1;           // rows per surface point (3 for the Stokeslet ML kernel)
+  int n = 0;           // points per surface
+  int R = 0;           // n * D
+  bool ops_ready = false;
+  // operators: [N_OPS][R][R] row-major (rows = target check rows, cols = source rows)
+  DevBuf ops64, ops32, opsbf;       // opsbf: [N_OPS][2][R][Rpad] split bf16 (hi, lo)
+  int Rpad = 0;                     // R rounded up to the tensor-core K granularity
+  DevBuf unit64, unit32;            // unit surface [n][3]
+  DevBuf tm2l64, tm2l32;            // periodic far-image operator [R][R]
+  // tree + data
+  Tree tree;
+  bool have_points = false;
+  DevBuf up_check, dn_check, up_equiv, dn_equiv;   // [nbox][R][C] in compute type
+  DevBuf s_sorted;                  // sorted source values, compute type
+  DevBuf g_sorted;                  // target values in sorted order
+  DevBuf io_in, io_out, io_aux;     // staging for host pointers / dtype conversion
+  DevBuf tiles, tile_meta;          // work lists of the gather-GEMM engine
+  int64_t tiles_cap = 0;
+  WorkLists wl;
+  bool use_tc = false;              // tensor-core M->L available for this plan
+  cudaEvent_t ev[8] = {0};
+  double phase_ms[8] = {0};
+  std::string err;
+
+  bool fp64() const { return prec == KAFMM_PREC_FP64; }
+};
+
+// Sets plan.err and returns code.
+int fail(Plan& P, int code, const char* fmt, ...);
+int cuda_fail(Plan& P, cudaError_t e, const char* where);
+
+// tree.cu
+int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, int dtype);
+
+// operators.cu
+int build_operators(Plan& P);
+
+// eval.cu
+int evaluate(Plan& P, const void* s_dev, void* g_dev, int dtype);
+int build_worklists(Plan& P, int NB, int NB_TC);
+int rpy_velocity(Plan& P, const void* s_dev, const void* a_dev, const void* g_dev, void* ua_dev,
+                 int dtype);
+
+}  // namespace kafmm

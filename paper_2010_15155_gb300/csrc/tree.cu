@@ -1,0 +1,752 @@
+// Octree construction on the device: Morton keys, LSD radix sort, level-by-level
+// refinement and the U/V/W/X interaction lists of kernel-independent FMM (Sec. II; the
+// refinement rule of Sec. III with a configurable leaf size).
+#include <algorithm>
+
+#include "plan.cuh"
+#include "scan.cuh"
+
+namespace kafmm {
+
+// ---------------------------------------------------------------------------------------
+// Morton keys.  Cell I = clamp(floor((p - origin) / L * 2^20), 0, 2^20 - 1) per axis in FP64.
+template <class T>
+__global__ void k_keys(const T* __restrict__ pts, int64_t n, double ox, double oy, double oz,
+                       double L, uint64_t* __restrict__ key, uint32_t* __restrict__ idx,
+                       unsigned* status) {
+  const double s = (double)(1 << MAX_LEVEL);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double u[3] = {((double)pts[3 * i] - ox) / L, ((double)pts[3 * i + 1] - oy) / L,
+                   ((double)pts[3 * i + 2] - oz) / L};
+    uint32_t c[3];
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      ok = ok && (u[d] >= 0.0) && (u[d] < 1.0);
+      double f = floor(u[d] * s);
+      f = f < 0.0 ? 0.0 : (f > s - 1.0 ? s - 1.0 : f);
+      c[d] = ok ? (uint32_t)f : 0u;
+    }
+    if (!ok) atomicOr(status, (unsigned)ST_DOMAIN);
+    key[i] = morton3(c[0], c[1], c[2]);
+    idx[i] = (uint32_t)i;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// LSD radix sort of (u64 key, u32 value), 8-bit digits, stable.  Tile of 4096 keys per block
+// (8 warps x 32 lanes x 16 rounds); ranks inside a warp come from __match_any_sync.
+constexpr int RS_THREADS = 256, RS_ROUNDS = 16, RS_WARPS = RS_THREADS / 32;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+
+__global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
+                             uint32_t* __restrict__ hist, int nblk) {
+  __shared__ uint32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int k = 0; k < RS_ROUNDS; ++k) {
+    int64_t i = base + k * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                                int shift, const uint32_t* __restrict__ hist, int nblk) {
+  __shared__ uint32_t wcnt[RS_WARPS][256];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
+  __syncwarp();
+  int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * 32 * RS_ROUNDS;
+  uint64_t k[RS_ROUNDS];
+  uint32_t v[RS_ROUNDS], rk[RS_ROUNDS];
+  unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    int64_t i = base + r * 32 + lane;
+    bool valid = i < n;
+    k[r] = valid ? kin[i] : 0ull;
+    v[r] = valid ? vin[i] : 0u;
+    unsigned d = valid ? (unsigned)((k[r] >> shift) & 255) : 256u;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int leader = __ffs(peers) - 1;
+    uint32_t cur = 0;
+    if (lane == leader && valid) cur = wcnt[w][d];
+    cur = __shfl_sync(0xffffffffu, cur, leader);
+    rk[r] = cur + __popc(peers & lt);
+    __syncwarp();
+    if (lane == leader && valid) wcnt[w][d] = cur + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {  // exclusive scan over warps per digit, plus the global base of this block
+    int d = threadIdx.x;
+    uint32_t run = hist[(int64_t)d * nblk + blockIdx.x];
+    for (int ww = 0; ww < RS_WARPS; ++ww) {
+      uint32_t t = wcnt[ww][d];
+      wcnt[ww][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    int64_t i = base + r * 32 + lane;
+    if (i < n) {
+      unsigned d = (unsigned)((k[r] >> shift) & 255);
+      uint32_t pos = wcnt[w][d] + rk[r];
+      kout[pos] = k[r];
+      vout[pos] = v[r];
+    }
+  }
+}
+
+// Sorts keys/vals in place (ping-pong through k2/v2).  60-bit keys: 8 passes.
+static void radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* k2, uint32_t* v2, uint32_t* hist,
+                       int64_t n, cudaStream_t st) {
+  if (n <= 1) return;
+  int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
+  uint64_t *ka = keys, *kb = k2;
+  uint32_t *va = vals, *vb = v2;
+  for (int pass = 0; pass < 8; ++pass) {
+    int shift = pass * 8;
+    k_radix_hist<<<nblk, RS_THREADS, 0, st>>>(ka, n, shift, hist, nblk);
+    scan_excl<uint32_t>(hist, hist, (int64_t)256 * nblk, nullptr, hist + 256 * (int64_t)nblk,
+                        nullptr, st);
+    k_radix_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, hist, nblk);
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  // 8 passes: the result is back in (keys, vals)
+}
+
+// ---------------------------------------------------------------------------------------
+// Level-by-level refinement.  Level l holds up to cap[l] boxes at bld_* + cap_off[l].
+struct BuildArgs {
+  uint64_t* key;
+  int *sb, *se, *tb, *te, *parent, *child, *cnt, *nch, *choff, *cb, *ctb;
+  const uint64_t* skey;
+  const uint64_t* tkey;
+  int same, q;
+  int64_t cap_off[MAX_LEVELS + 1];
+  int cap[MAX_LEVELS];
+};
+
+__device__ inline int lower_bound_prefix(const uint64_t* k, int lo, int hi, uint64_t want, int sh) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if ((k[mid] >> sh) < want)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_root(BuildArgs a, int ns, int nt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    a.key[0] = 0;
+    a.sb[0] = 0;
+    a.se[0] = ns;
+    a.tb[0] = 0;
+    a.te[0] = nt;
+    a.parent[0] = -1;
+    for (int l = 0; l < MAX_LEVELS; ++l) a.cnt[l] = l == 0 ? 1 : 0;
+  }
+}
+
+__global__ void k_split(BuildArgs a, int lv, unsigned* status) {
+  int n = a.cnt[lv];
+  int64_t o0 = a.cap_off[lv];
+  int sh = 3 * (MAX_LEVEL - lv - 1);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int64_t g = o0 + i;
+    int sb = a.sb[g], se = a.se[g], tb = a.tb[g], te = a.te[g];
+    int count = (se - sb) + (a.same ? 0 : (te - tb));
+    int nch = 0;
+    if (count > a.q && lv < MAX_LEVEL) {
+      uint64_t k = a.key[g];
+      int cb[9], ctb[9];
+      for (int o = 0; o < 8; ++o) {
+        cb[o] = lower_bound_prefix(a.skey, sb, se, k * 8 + o, sh);
+        ctb[o] = a.same ? cb[o] : lower_bound_prefix(a.tkey, tb, te, k * 8 + o, sh);
+      }
+      cb[8] = se;
+      ctb[8] = a.same ? se : te;
+      for (int o = 0; o < 9; ++o) {
+        a.cb[g * 9 + o] = cb[o];
+        a.ctb[g * 9 + o] = ctb[o];
+      }
+      for (int o = 0; o < 8; ++o)
+        nch += ((cb[o + 1] - cb[o]) + (a.same ? 0 : (ctb[o + 1] - ctb[o]))) > 0;
+    }
+    a.nch[g] = nch;
+  }
+}
+
+__global__ void k_level_total(BuildArgs a, int lv, const int* total, unsigned* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int t = *total;
+    if (lv + 1 < MAX_LEVELS) {
+      if (t > a.cap[lv + 1]) {
+        atomicOr(status, (unsigned)ST_OVERFLOW);
+        t = a.cap[lv + 1];
+      }
+      a.cnt[lv + 1] = t;
+    }
+  }
+}
+
+__global__ void k_emit(BuildArgs a, int lv) {
+  int n = a.cnt[lv];
+  int64_t o0 = a.cap_off[lv];
+  int64_t o1 = a.cap_off[lv + 1];
+  int cap1 = a.cap[lv + 1 < MAX_LEVELS ? lv + 1 : lv];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int64_t g = o0 + i;
+    int j = a.choff[g];
+    int nch = a.nch[g];
+    uint64_t k = a.key[g];
+    for (int o = 0; o < 8; ++o) {
+      int c = -1;
+      if (nch > 0) {
+        int b0 = a.cb[g * 9 + o], b1 = a.cb[g * 9 + o + 1];
+        int t0 = a.ctb[g * 9 + o], t1 = a.ctb[g * 9 + o + 1];
+        int cnt = (b1 - b0) + (a.same ? 0 : (t1 - t0));
+        if (cnt > 0 && j < cap1) {
+          int64_t h = o1 + j;
+          a.key[h] = k * 8 + o;
+          a.sb[h] = b0;
+          a.se[h] = b1;
+          a.tb[h] = a.same ? b0 : t0;
+          a.te[h] = a.same ? b1 : t1;
+          a.parent[h] = i;
+          c = j;
+          ++j;
+        }
+      }
+      a.child[g * 8 + o] = c;
+    }
+  }
+}
+
+struct Layout {
+  int lvl_start[MAX_LEVELS + 1];
+  int64_t cap_off[MAX_LEVELS + 1];
+};
+
+__global__ void k_compact(BuildArgs a, Layout lay, int nbox, uint64_t* key, int8_t* level,
+                          int* parent, int* child, int* sb, int* se, int* tb, int* te,
+                          int8_t* leaf) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nbox; g += gridDim.x * blockDim.x) {
+    int lv = 0;
+    while (lv + 1 < MAX_LEVELS && g >= lay.lvl_start[lv + 1]) ++lv;
+    int i = g - lay.lvl_start[lv];
+    int64_t h = lay.cap_off[lv] + i;
+    key[g] = a.key[h];
+    level[g] = (int8_t)lv;
+    parent[g] = lv > 0 ? lay.lvl_start[lv - 1] + a.parent[h] : -1;
+    sb[g] = a.sb[h];
+    se[g] = a.se[h];
+    tb[g] = a.tb[h];
+    te[g] = a.te[h];
+    bool lf = true;
+    for (int o = 0; o < 8; ++o) {
+      int c = (lv + 1 < MAX_LEVELS) ? a.child[h * 8 + o] : -1;
+      child[g * 8 + o] = c >= 0 ? lay.lvl_start[lv + 1] + c : -1;
+      lf = lf && c < 0;
+    }
+    leaf[g] = lf ? 1 : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Lists.
+__device__ inline void anchor_of(uint64_t k, int& x, int& y, int& z) {
+  x = (int)compact3(k);
+  y = (int)compact3(k >> 1);
+  z = (int)compact3(k >> 2);
+}
+
+__device__ inline int find_box(const TreeView& t, int lv, int ax, int ay, int az) {
+  if (lv >= t.nlevels) return -1;
+  uint64_t k = morton3((uint32_t)ax, (uint32_t)ay, (uint32_t)az);
+  int lo = t.lvl_start[lv], hi = t.lvl_start[lv + 1], end = hi;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (t.key[mid] < k)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return (lo < end && t.key[lo] == k) ? lo : -1;
+}
+
+// Deepest existing box at level <= lv that contains cell (lv, a).  The root always exists.
+__device__ inline int deepest_box(const TreeView& t, int lv, int ax, int ay, int az) {
+  int top = lv < t.nlevels - 1 ? lv : t.nlevels - 1;
+  for (int l = top; l >= 0; --l) {
+    int sh = lv - l;
+    int b = find_box(t, l, ax >> sh, ay >> sh, az >> sh);
+    if (b >= 0) return b;
+  }
+  return 0;
+}
+
+// Neighbour cell a + d at level lv: wraps (periodic) or reports absence.  s: image shift.
+__device__ inline bool neighbour(int periodic, int lv, int a, int d, int& c, int& s) {
+  int n = 1 << lv;
+  c = a + d;
+  s = 0;
+  if (c < 0 || c >= n) {
+    if (!periodic) return false;
+    s = c < 0 ? -((-c + n - 1) / n) : c / n;
+    c -= s * n;
+  }
+  return true;
+}
+
+// Closed boxes (b at level lb, anchor ab, moved by shift s domains) and (lb2, ab2) intersect?
+__device__ inline bool adjacent(int la, int ax, int ay, int az, int sx, int sy, int sz, int lb, int bx,
+                                int by, int bz) {
+  int64_t wa = 1ll << (MAX_LEVEL - la), wb = 1ll << (MAX_LEVEL - lb), D = 1ll << MAX_LEVEL;
+  int64_t a0[3] = {ax * wa + sx * D, ay * wa + sy * D, az * wa + sz * D};
+  int64_t b0[3] = {bx * wb, by * wb, bz * wb};
+  for (int d = 0; d < 3; ++d)
+    if (a0[d] > b0[d] + wb || b0[d] > a0[d] + wa) return false;
+  return true;
+}
+
+struct ListOut {
+  int64_t* u_cnt;  // count mode: counts; fill mode: offsets
+  int64_t* w_cnt;
+  int64_t* x_cnt;
+  int32_t* u_ent;
+  int32_t* w_ent;
+  int32_t* x_ent;
+  int32_t* vtab;   // [nbox][216]
+  int8_t* w_flag;
+  unsigned long long* near_pairs;
+};
+
+template <bool FILL>
+__global__ void k_lists(TreeView t, ListOut o) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x) {
+    int lv = t.level[b];
+    int ax, ay, az;
+    anchor_of(t.key[b], ax, ay, az);
+    // ---- V: same-level boxes at the 189 offsets of the parent's neighbourhood
+    if (FILL) {
+      int bx = ax & 1, by = ay & 1, bz = az & 1;
+      for (int k = 0; k < 216; ++k) {
+        int ox = k % 6 - 2 - bx, oy = (k / 6) % 6 - 2 - by, oz = k / 36 - 2 - bz;
+        int32_t e = -1;
+        bool inner = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
+        if (!inner && (lv >= 2 || (t.periodic && lv >= 1))) {
+          int cx, cy, cz, sx, sy, sz;
+          if (neighbour(t.periodic, lv, ax, ox, cx, sx) && neighbour(t.periodic, lv, ay, oy, cy, sy) &&
+              neighbour(t.periodic, lv, az, oz, cz, sz)) {
+            int s = find_box(t, lv, cx, cy, cz);
+            if (s >= 0) e = pack_entry(s, shift_code(sx, sy, sz));
+          }
+        }
+        o.vtab[(int64_t)b * 216 + k] = e;
+      }
+    }
+    // ---- U and W for leaves
+    int64_t nu = 0, nw = 0, nx = 0;
+    int64_t pu = FILL ? o.u_cnt[b] : 0, pw = FILL ? o.w_cnt[b] : 0, px = FILL ? o.x_cnt[b] : 0;
+    unsigned long long pairs = 0;
+    if (t.leaf[b]) {
+      int coarse[27];
+      int ncoarse = 0;
+      int ntb = t.te[b] - t.tb[b];
+      for (int d = 0; d < 27; ++d) {
+        int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        int cx, cy, cz, sx, sy, sz;
+        if (!neighbour(t.periodic, lv, ax, dx, cx, sx) || !neighbour(t.periodic, lv, ay, dy, cy, sy) ||
+            !neighbour(t.periodic, lv, az, dz, cz, sz))
+          continue;
+        int sc = shift_code(sx, sy, sz);
+        int nb = deepest_box(t, lv, cx, cy, cz);
+        int nl = t.level[nb];
+        if (nl < lv) {  // a coarser box holds the cell: a leaf is a U neighbour
+          if (!t.leaf[nb]) continue;
+          int32_t e = pack_entry(nb, sc);
+          bool dup = false;
+          for (int j = 0; j < ncoarse; ++j) dup = dup || coarse[j] == e;
+          if (dup) continue;
+          coarse[ncoarse++] = e;
+          if (FILL) o.u_ent[pu + nu] = e;
+          ++nu;
+          pairs += (unsigned long long)ntb * (t.se[nb] - t.sb[nb]);
+          continue;
+        }
+        if (t.leaf[nb]) {
+          if (FILL) o.u_ent[pu + nu] = pack_entry(nb, sc);
+          ++nu;
+          pairs += (unsigned long long)ntb * (t.se[nb] - t.sb[nb]);
+          continue;
+        }
+        // non-leaf colleague: descend; adjacent leaves -> U, non-adjacent boxes -> W
+        int stack[8 * MAX_LEVELS];
+        int sp = 0;
+        for (int c = 0; c < 8; ++c)
+          if (t.child[nb * 8 + c] >= 0) stack[sp++] = t.child[nb * 8 + c];
+        while (sp > 0) {
+          int dd = stack[--sp];
+          int dl = t.level[dd], qx, qy, qz;
+          anchor_of(t.key[dd], qx, qy, qz);
+          if (adjacent(dl, qx, qy, qz, sx, sy, sz, lv, ax, ay, az)) {
+            if (t.leaf[dd]) {
+              if (FILL) o.u_ent[pu + nu] = pack_entry(dd, sc);
+              ++nu;
+              pairs += (unsigned long long)ntb * (t.se[dd] - t.sb[dd]);
+            } else {
+              for (int c = 0; c < 8; ++c)
+                if (t.child[dd * 8 + c] >= 0 && sp < 8 * MAX_LEVELS) stack[sp++] = t.child[dd * 8 + c];
+            }
+          } else {
+            if (FILL) {
+              o.w_ent[pw + nw] = pack_entry(dd, sc);
+              o.w_flag[dd] = 1;
+            }
+            ++nw;
+          }
+        }
+      }
+    }
+    // ---- X: coarser leaves adjacent to the parent but not to b
+    if (lv >= 1) {
+      int p = t.parent[b];
+      int px_, py_, pz_;
+      anchor_of(t.key[p], px_, py_, pz_);
+      int found[27];
+      int nf = 0;
+      for (int d = 0; d < 27; ++d) {
+        if (d == 13) continue;
+        int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        int cx, cy, cz, sx, sy, sz;
+        if (!neighbour(t.periodic, lv - 1, px_, dx, cx, sx) ||
+            !neighbour(t.periodic, lv - 1, py_, dy, cy, sy) ||
+            !neighbour(t.periodic, lv - 1, pz_, dz, cz, sz))
+          continue;
+        int nb = deepest_box(t, lv - 1, cx, cy, cz);
+        if (!t.leaf[nb]) continue;
+        int nl = t.level[nb], qx, qy, qz;
+        anchor_of(t.key[nb], qx, qy, qz);
+        if (adjacent(nl, qx, qy, qz, sx, sy, sz, lv, ax, ay, az)) continue;
+        int32_t e = pack_entry(nb, shift_code(sx, sy, sz));
+        bool dup = false;
+        for (int j = 0; j < nf; ++j) dup = dup || found[j] == e;
+        if (dup) continue;
+        found[nf++] = e;
+        if (FILL) o.x_ent[px + nx] = e;
+        ++nx;
+      }
+    }
+    if (!FILL) {
+      o.u_cnt[b] = nu;
+      o.w_cnt[b] = nw;
+      o.x_cnt[b] = nx;
+    } else if (pairs) {
+      atomicAdd(o.near_pairs, pairs);
+    }
+  }
+}
+
+// Gathers the sorted points into the compute type (x, y, z, 0).
+template <class Tin, class T4>
+__global__ void k_gather_pos(const Tin* __restrict__ pts, const uint32_t* __restrict__ perm, int64_t n,
+                             T4* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t j = perm[i];
+    T4 v;
+    v.x = pts[3 * (int64_t)j];
+    v.y = pts[3 * (int64_t)j + 1];
+    v.z = pts[3 * (int64_t)j + 2];
+    v.w = 0;
+    out[i] = v;
+  }
+}
+
+__global__ void k_leaf_list(const int8_t* leaf, const int* leaf_pos, int nbox, int* leaves) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x)
+    if (leaf[b]) leaves[leaf_pos[b]] = b;
+}
+
+__global__ void k_tree_stats(TreeView t, const int32_t* vtab, unsigned long long* out) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x) {
+    unsigned long long nv = 0;
+    for (int k = 0; k < 216; ++k) nv += vtab[(int64_t)b * 216 + k] >= 0;
+    atomicAdd(&out[0], nv);
+    if (t.leaf[b]) {
+      unsigned long long np = (unsigned long long)max(t.se[b] - t.sb[b], t.te[b] - t.tb[b]);
+      atomicMax(&out[1], np);
+    }
+  }
+}
+
+__global__ void k_i8_to_i32(const int8_t* a, int n, int* b) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = a[i];
+}
+
+TreeView Tree::view() const {
+  TreeView v;
+  v.nbox = nbox;
+  v.nlevels = nlevels;
+  v.periodic = 0;
+  v.lvl_start = d_lvl_start.as<int>();
+  v.key = key.as<uint64_t>();
+  v.level = level.as<int8_t>();
+  v.parent = parent.as<int>();
+  v.child = child.as<int>();
+  v.sb = sb.as<int>();
+  v.se = se.as<int>();
+  v.tb = tb.as<int>();
+  v.te = te.as<int>();
+  v.leaf = leaf.as<int8_t>();
+  return v;
+}
+
+static int grid_for(int64_t n, int threads, int maxb = 152 * 8) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > maxb) b = maxb;
+  return (int)b;
+}
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(P, e_, #call); \
+  } while (0)
+
+// Sorts one point set: keys + permutation, sorted positions in the compute type.
+static int sort_points(Plan& P, const void* pts, int64_t n, int dtype, DevBuf& key, DevBuf& perm,
+                       DevBuf& k2, DevBuf& v2, DevBuf& pos) {
+  Tree& T = P.tree;
+  cudaStream_t st = P.stream;
+  CK(key.reserve(sizeof(uint64_t) * (n + 1)));
+  CK(perm.reserve(sizeof(uint32_t) * (n + 1)));
+  CK(k2.reserve(sizeof(uint64_t) * (n + 1)));
+  CK(v2.reserve(sizeof(uint32_t) * (n + 1)));
+  int64_t nblk = (n + RS_TILE - 1) / RS_TILE + 1;
+  CK(T.s_hist.reserve(sizeof(uint32_t) * (256 * nblk + 256 * nblk / SCAN_TILE + 64)));
+  unsigned* status = T.status.as<unsigned>();
+  int g = grid_for(n, 256);
+  if (n > 0) {
+    if (dtype == KAFMM_F64)
+      k_keys<double><<<g, 256, 0, st>>>((const double*)pts, n, P.origin[0], P.origin[1], P.origin[2],
+                                         P.L, key.as<uint64_t>(), perm.as<uint32_t>(), status);
+    else
+      k_keys<float><<<g, 256, 0, st>>>((const float*)pts, n, P.origin[0], P.origin[1], P.origin[2],
+                                        P.L, key.as<uint64_t>(), perm.as<uint32_t>(), status);
+    radix_sort(key.as<uint64_t>(), perm.as<uint32_t>(), k2.as<uint64_t>(), v2.as<uint32_t>(),
+               T.s_hist.as<uint32_t>(), n, st);
+  }
+  size_t esz = P.fp64() ? sizeof(double4) : sizeof(float4);
+  CK(pos.reserve(esz * (n + 1)));
+  if (n > 0) {
+    if (P.fp64()) {
+      if (dtype == KAFMM_F64)
+        k_gather_pos<double, double4><<<g, 256, 0, st>>>((const double*)pts, perm.as<uint32_t>(), n,
+                                                         pos.as<double4>());
+      else
+        k_gather_pos<float, double4><<<g, 256, 0, st>>>((const float*)pts, perm.as<uint32_t>(), n,
+                                                        pos.as<double4>());
+    } else {
+      if (dtype == KAFMM_F64)
+        k_gather_pos<double, float4><<<g, 256, 0, st>>>((const double*)pts, perm.as<uint32_t>(), n,
+                                                        pos.as<float4>());
+      else
+        k_gather_pos<float, float4><<<g, 256, 0, st>>>((const float*)pts, perm.as<uint32_t>(), n,
+                                                       pos.as<float4>());
+    }
+  }
+  CK(cudaGetLastError());
+  return 0;
+}
+
+int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, int dtype) {
+  Tree& T = P.tree;
+  cudaStream_t st = P.stream;
+  T.n_src = ns;
+  T.n_trg = nt;
+  T.same = (x == y) && (ns == nt);
+  T.dtype_pts = dtype;
+  CK(T.status.reserve(64));
+  CK(cudaMemsetAsync(T.status.p, 0, 64, st));
+  cudaEventRecord(P.ev[0], st);
+
+  int rc = sort_points(P, y, ns, dtype, T.src_key, T.src_perm, T.s_keys2, T.s_vals2, T.src_pos);
+  if (rc) return rc;
+  if (!T.same) {
+    rc = sort_points(P, x, nt, dtype, T.trg_key, T.trg_perm, T.t_keys2, T.t_vals2, T.trg_pos);
+    if (rc) return rc;
+  }
+
+  // per-level capacities: min(8^l, 8 * floor(N / (q + 1)) + 8)
+  int64_t npts = T.same ? ns : ns + nt;
+  int64_t per = 8 * (npts / (P.q + 1)) + 8;
+  BuildArgs a;
+  int64_t off = 0;
+  for (int l = 0; l < MAX_LEVELS; ++l) {
+    int64_t c = l < 8 ? std::min<int64_t>(per, 1ll << (3 * l)) : per;
+    a.cap[l] = (int)c;
+    a.cap_off[l] = off;
+    off += c;
+  }
+  a.cap_off[MAX_LEVELS] = off;
+  CK(T.bld_key.reserve(sizeof(uint64_t) * off));
+  CK(T.bld_sb.reserve(sizeof(int) * off));
+  CK(T.bld_se.reserve(sizeof(int) * off));
+  CK(T.bld_tb.reserve(sizeof(int) * off));
+  CK(T.bld_te.reserve(sizeof(int) * off));
+  CK(T.bld_parent.reserve(sizeof(int) * off));
+  CK(T.bld_child.reserve(sizeof(int) * off * 8));
+  CK(T.bld_nch.reserve(sizeof(int) * off));
+  CK(T.bld_choff.reserve(sizeof(int) * (off + off / SCAN_TILE + 64)));
+  CK(T.bld_cb.reserve(sizeof(int) * off * 9));
+  CK(T.bld_ctb.reserve(sizeof(int) * off * 9));
+  CK(T.bld_cnt.reserve(sizeof(int) * (MAX_LEVELS + 8)));
+  a.key = T.bld_key.as<uint64_t>();
+  a.sb = T.bld_sb.as<int>();
+  a.se = T.bld_se.as<int>();
+  a.tb = T.bld_tb.as<int>();
+  a.te = T.bld_te.as<int>();
+  a.parent = T.bld_parent.as<int>();
+  a.child = T.bld_child.as<int>();
+  a.cnt = T.bld_cnt.as<int>();
+  a.nch = T.bld_nch.as<int>();
+  a.choff = T.bld_choff.as<int>();
+  a.cb = T.bld_cb.as<int>();
+  a.ctb = T.bld_ctb.as<int>();
+  a.skey = T.src_key.as<uint64_t>();
+  a.tkey = T.same ? a.skey : T.trg_key.as<uint64_t>();
+  a.same = T.same ? 1 : 0;
+  a.q = P.q;
+  unsigned* status = T.status.as<unsigned>();
+  int* d_total = a.cnt + MAX_LEVELS + 1;
+  k_root<<<1, 32, 0, st>>>(a, (int)ns, (int)(T.same ? ns : nt));
+  for (int l = 0; l < MAX_LEVEL; ++l) {
+    int g = grid_for(a.cap[l], 256);
+    k_split<<<g, 256, 0, st>>>(a, l, status);
+    int* scratch = a.choff + a.cap_off[MAX_LEVELS] + 16;
+    scan_excl<int>(a.nch + a.cap_off[l], a.choff + a.cap_off[l], a.cap[l], a.cnt + l, scratch, d_total,
+                   st);
+    k_level_total<<<1, 32, 0, st>>>(a, l, d_total, status);
+    k_emit<<<g, 256, 0, st>>>(a, l);
+  }
+  CK(cudaGetLastError());
+  int cnt[MAX_LEVELS];
+  unsigned h_status = 0;
+  CK(cudaMemcpyAsync(cnt, a.cnt, sizeof(int) * MAX_LEVELS, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h_status & ST_DOMAIN)
+    return fail(P, KAFMM_ERR_DOMAIN, "a point lies outside [origin, origin + L)^3 or is not finite");
+  if (h_status & ST_OVERFLOW) return fail(P, KAFMM_ERR_NOMEM, "octree level capacity exceeded");
+
+  Layout lay;
+  T.nlevels = 0;
+  int nb = 0;
+  for (int l = 0; l < MAX_LEVELS; ++l) {
+    lay.lvl_start[l] = nb;
+    T.lvl_start[l] = nb;
+    nb += cnt[l];
+    if (cnt[l] > 0) T.nlevels = l + 1;
+    lay.cap_off[l] = a.cap_off[l];
+  }
+  lay.lvl_start[MAX_LEVELS] = nb;
+  T.lvl_start[MAX_LEVELS] = nb;
+  lay.cap_off[MAX_LEVELS] = a.cap_off[MAX_LEVELS];
+  T.nbox = nb;
+
+  CK(T.key.reserve(sizeof(uint64_t) * nb));
+  CK(T.level.reserve(nb));
+  CK(T.parent.reserve(sizeof(int) * nb));
+  CK(T.child.reserve(sizeof(int) * nb * 8));
+  CK(T.sb.reserve(sizeof(int) * nb));
+  CK(T.se.reserve(sizeof(int) * nb));
+  CK(T.tb.reserve(sizeof(int) * nb));
+  CK(T.te.reserve(sizeof(int) * nb));
+  CK(T.leaf.reserve(nb));
+  CK(T.d_lvl_start.reserve(sizeof(int) * (MAX_LEVELS + 1)));
+  CK(cudaMemcpyAsync(T.d_lvl_start.p, T.lvl_start, sizeof(int) * (MAX_LEVELS + 1),
+                     cudaMemcpyHostToDevice, st));
+  k_compact<<<grid_for(nb, 256), 256, 0, st>>>(a, lay, nb, T.key.as<uint64_t>(), T.level.as<int8_t>(),
+                                              T.parent.as<int>(), T.child.as<int>(), T.sb.as<int>(),
+                                              T.se.as<int>(), T.tb.as<int>(), T.te.as<int>(),
+                                              T.leaf.as<int8_t>());
+  // leaf list (box order)
+  CK(T.leaves.reserve(sizeof(int) * (2 * nb + nb / SCAN_TILE + 64)));
+  int* lpos = T.leaves.as<int>() + nb;
+  int* lscratch = lpos + nb;
+  int* ltot = lscratch + nb / SCAN_TILE + 8;
+  k_i8_to_i32<<<grid_for(nb, 256), 256, 0, st>>>(T.leaf.as<int8_t>(), nb, lpos);
+  scan_excl<int>(lpos, lpos, nb, nullptr, lscratch, ltot, st);
+  k_leaf_list<<<grid_for(nb, 256), 256, 0, st>>>(T.leaf.as<int8_t>(), lpos, nb, T.leaves.as<int>());
+  CK(cudaMemcpyAsync(&T.nleaf, ltot, sizeof(int), cudaMemcpyDeviceToHost, st));
+  cudaEventRecord(P.ev[1], st);
+
+  // ---- lists
+  TreeView tv = T.view();
+  tv.periodic = P.bc == KAFMM_BC_PXYZ;
+  CK(T.u_off.reserve(sizeof(int64_t) * (nb + 1 + nb / SCAN_TILE + 64)));
+  CK(T.w_off.reserve(sizeof(int64_t) * (nb + 1 + nb / SCAN_TILE + 64)));
+  CK(T.x_off.reserve(sizeof(int64_t) * (nb + 1 + nb / SCAN_TILE + 64)));
+  CK(T.vtab.reserve(sizeof(int32_t) * (int64_t)nb * 216));
+  CK(T.w_flag.reserve(nb));
+  CK(cudaMemsetAsync(T.w_flag.p, 0, nb, st));
+  ListOut lo{};
+  lo.u_cnt = T.u_off.as<int64_t>();
+  lo.w_cnt = T.w_off.as<int64_t>();
+  lo.x_cnt = T.x_off.as<int64_t>();
+  int g = grid_for(nb, 128, 152 * 16);
+  k_lists<false><<<g, 128, 0, st>>>(tv, lo);
+  int64_t tot[3];
+  int64_t* sc[3] = {lo.u_cnt, lo.w_cnt, lo.x_cnt};
+  for (int k = 0; k < 3; ++k) {
+    int64_t* scratch = sc[k] + nb + 2;
+    scan_excl<int64_t>(sc[k], sc[k], nb, nullptr, scratch, sc[k] + nb, st);
+  }
+  for (int k = 0; k < 3; ++k)
+    CK(cudaMemcpyAsync(&tot[k], sc[k] + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  T.n_u = tot[0];
+  T.n_w = tot[1];
+  T.n_x = tot[2];
+  CK(T.u_ent.reserve(sizeof(int32_t) * (T.n_u + 1)));
+  CK(T.w_ent.reserve(sizeof(int32_t) * (T.n_w + 1)));
+  CK(T.x_ent.reserve(sizeof(int32_t) * (T.n_x + 1)));
+  lo.u_ent = T.u_ent.as<int32_t>();
+  lo.w_ent = T.w_ent.as<int32_t>();
+  lo.x_ent = T.x_ent.as<int32_t>();
+  lo.vtab = T.vtab.as<int32_t>();
+  lo.w_flag = T.w_flag.as<int8_t>();
+  lo.near_pairs = (unsigned long long*)(T.status.as<unsigned>() + 8);
+  CK(cudaMemsetAsync(lo.near_pairs, 0, 8, st));
+  k_lists<true><<<g, 128, 0, st>>>(tv, lo);
+  unsigned long long pairs = 0;
+  CK(cudaMemcpyAsync(&pairs, lo.near_pairs, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaGetLastError());
+  cudaEventRecord(P.ev[2], st);
+  CK(cudaStreamSynchronize(st));
+  T.near_pairs = (int64_t)pairs;
+  // V entries and the largest leaf
+  unsigned long long* stats = (unsigned long long*)(T.status.as<unsigned>() + 10);
+  CK(cudaMemsetAsync(stats, 0, 16, st));
+  k_tree_stats<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vtab.as<int32_t>(), stats);
+  unsigned long long hs[2];
+  CK(cudaMemcpyAsync(hs, stats, 16, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  T.n_v = (int64_t)hs[0];
+  T.max_leaf_pts = (int)hs[1];
+  return 0;
+}
+
+}  // namespace kafmm

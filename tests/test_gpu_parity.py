@@ -1,0 +1,171 @@
+"""GPU parity: the CUDA evaluator (through the C ABI) against the CPU oracle.
+
+* Octree and U/V/W/X lists: identical (integer-exact) to the oracle's, box by box.
+* Near field (U-list S->T) per kernel: FP64 to 1e-12, FP32 to 1e-5 (relative L2).
+* Full KAFMM, plain FP64 GPU form vs the FP64 CPU KAFMM (same order, same tables):
+  relative L2 <= 1e-7.
+* FP32 form vs the FP64 GPU form: relative L2 <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads as W  # noqa: E402
+from oracle import direct as D  # noqa: E402
+from oracle.kafmm import KAFMM  # noqa: E402
+from oracle.tree import Tree  # noqa: E402
+from paper_2010_15155_gb300 import kafmm as K  # noqa: E402
+
+KERN = {"laplace": K.LAPLACE, "stokeslet": K.STOKESLET, "rpy": K.RPY, "stokes_dl": K.STOKES_DL}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_15155_gb300 import build
+    build.build()
+
+
+def _gpu_tree(pts, q, dtype=torch.float64):
+    plan = K.Plan(K.LAPLACE, p=4, q=q, precision=K.PREC_FP64, near_only=True)
+    y = torch.from_numpy(np.ascontiguousarray(pts)).to(dtype).cuda()
+    plan.set_points(y)
+    info = plan.info()
+    nb = info["nbox"]
+    level, anchor, parent, leaf = K.kafmm_get_tree(plan.h, nb)
+    lists = {}
+    for kind, name in enumerate("UVWX"):
+        off, ent, sh = K.kafmm_get_list(plan.h, kind, nb)
+        lists[name] = [set(zip(ent[off[b]:off[b + 1]].tolist(), sh[off[b]:off[b + 1]].tolist()))
+                       for b in range(nb)]
+    plan.close()
+    return info, level, anchor, parent, leaf, lists
+
+
+def _code(sh):
+    return (sh[0] + 1) + 3 * (sh[1] + 1) + 9 * (sh[2] + 1)
+
+
+@pytest.mark.parametrize("case", ["uniform", "clustered", "tiny"])
+def test_tree_and_lists_match_oracle(case):
+    if case == "uniform":
+        pts, _ = W.laplace_uniform(6000, seed=3)
+        q = 40
+    elif case == "clustered":
+        pts, _, _ = W.rpy_clusters(5000, seed=4, n_clusters=5, sigma=0.03, dtype=np.float64)
+        q = 24
+    else:
+        pts, _ = W.laplace_uniform(30, seed=5)
+        q = 64
+    T = Tree(pts, q=q)
+    info, level, anchor, parent, leaf, lists = _gpu_tree(pts, q)
+    assert info["nbox"] == T.nbox and info["nlevels"] == T.nlevels
+    assert np.array_equal(level, T.level)
+    assert np.array_equal(anchor, T.anchor)
+    assert np.array_equal(parent, T.parent)
+    assert np.array_equal(leaf.astype(bool), T.is_leaf)
+    for name in "UVWX":
+        ref = getattr(T, name)
+        for b in range(T.nbox):
+            want = {(a, _code(sh)) for (a, sh) in ref[b]}
+            assert lists[name][b] == want, (name, b)
+
+
+def _inputs(kernel, n, seed, dtype=np.float64):
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, 3))
+    ks = K.KDIM[KERN[kernel]][0]
+    s = rng.standard_normal((n, ks))
+    if kernel == "rpy":
+        s[:, 3] = rng.uniform(0.0, 2e-3, n)
+    return pts.astype(dtype), s.astype(dtype)
+
+
+def _near_oracle(kernel, pts, s, q):
+    """U-list sums only, from the oracle tree (plain loops)."""
+    T = Tree(pts, q=q)
+    g = np.zeros((len(pts), K.KDIM[KERN[kernel]][1]))
+    for b in T.leaves():
+        ti = T.trg_idx[b]
+        for (a, sh) in T.U[b]:
+            si = T.src_idx[a]
+            g[ti] += D.direct(kernel, pts[ti], pts[si], s[si])
+    return g
+
+
+@pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "rpy", "stokes_dl"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_near_field_matches_oracle(kernel, prec):
+    n, q = 3000, 50
+    pts, s = _inputs(kernel, n, seed=7)
+    ref = _near_oracle(kernel, pts, s, q)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    plan = K.Plan(KERN[kernel], p=4, q=q, precision=K.PREC_FP64 if prec == "fp64" else K.PREC_FP32,
+                  near_only=True)
+    plan.set_points(torch.from_numpy(pts).to(dt).cuda())
+    g = plan.eval(torch.from_numpy(s).to(dt).cuda()).double().cpu().numpy()
+    plan.close()
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    assert D.rel_l2(g, ref) < tol
+
+
+@pytest.mark.parametrize("problem,kernel,variant,n,p,q", [
+    ("laplace", "laplace", K.ML_L4, 4096, 8, 64),
+    ("stokeslet_l4", "stokeslet", K.ML_L4, 3000, 6, 40),
+    ("stokeslet_g", "stokeslet", K.ML_G, 1500, 4, 32),
+    ("rpy_l4", "rpy", K.ML_L4, 2500, 6, 40),
+    ("rpy_g", "rpy", K.ML_G, 1500, 4, 32),
+])
+def test_fp64_gpu_kafmm_matches_cpu_kafmm(problem, kernel, variant, n, p, q):
+    if problem == "laplace":
+        pts, s = W.laplace_uniform(n, seed=0)
+    else:
+        pts, s = _inputs(kernel, n, seed=11)
+    ref = KAFMM(problem, p, q).evaluate(pts, s)
+    plan = K.Plan(KERN[kernel], p=p, q=q, precision=K.PREC_FP64, variant=variant)
+    plan.set_points(torch.from_numpy(pts).cuda())
+    g = plan.eval(torch.from_numpy(s).cuda()).cpu().numpy()
+    plan.close()
+    assert D.rel_l2(g, ref) < 1e-7
+
+
+def test_fp64_gpu_kafmm_adaptive_tree_matches_cpu_kafmm():
+    pts, f, _ = W.rpy_clusters(4000, seed=8, n_clusters=3, sigma=0.05, dtype=np.float64)
+    F = KAFMM("stokeslet_l4", 6, 24)
+    ref = F.evaluate(pts, f)
+    T = F.tree
+    assert sum(map(len, T.W)) > 0 and sum(map(len, T.X)) > 0
+    plan = K.Plan(K.STOKESLET, p=6, q=24, precision=K.PREC_FP64, variant=K.ML_L4)
+    plan.set_points(torch.from_numpy(pts).cuda())
+    g = plan.eval(torch.from_numpy(f).cuda()).cpu().numpy()
+    plan.close()
+    assert D.rel_l2(g, ref) < 1e-7
+
+
+@pytest.mark.parametrize("kernel,variant", [("laplace", K.ML_L4), ("stokeslet", K.ML_L4),
+                                            ("stokeslet", K.ML_G), ("rpy", K.ML_L4)])
+def test_fp32_form_matches_fp64_form(kernel, variant):
+    pts, s = _inputs(kernel, 20000, seed=13, dtype=np.float32)
+    out = {}
+    for prec in (K.PREC_FP64, K.PREC_FP32):
+        dt = torch.float64 if prec == K.PREC_FP64 else torch.float32
+        plan = K.Plan(KERN[kernel], p=6, q=64, precision=prec, variant=variant)
+        plan.set_points(torch.from_numpy(pts).to(dt).cuda())
+        out[prec] = plan.eval(torch.from_numpy(s).to(dt).cuda()).double().cpu().numpy()
+        plan.close()
+    assert D.rel_l2(out[K.PREC_FP32], out[K.PREC_FP64]) < 1e-5
+
+
+def test_errors_are_reported_not_trapped():
+    plan = K.Plan(K.STOKESLET, p=4, q=32, precision=K.PREC_FP32)
+    bad = torch.tensor([[0.5, 0.5, 1.5], [0.1, 0.2, 0.3]], dtype=torch.float32, device="cuda")
+    with pytest.raises(K.KafmmError) as e:
+        plan.set_points(bad)
+    assert e.value.code == -2
+    with pytest.raises(K.KafmmError) as e:
+        plan.eval(torch.zeros((2, 3), device="cuda"))
+    assert e.value.code == -6
+    plan.close()

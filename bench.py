@@ -1,0 +1,307 @@
+"""Benchmark of the KAFMM evaluator on one GB300 (or N replicas under torchrun).
+
+Workload: Stokeslet KAFMM, N = 262144 uniform points in the unit cube (FP32), forces
+N(0,1)^3, order p = 10, <= 128 points per leaf, four-channel Laplace ML-tree table, mixed
+precision.  A step is the whole hot path on one batch: kafmm_set_points (Morton keys, radix
+sort, octree, U/V/W/X lists) + kafmm_eval (upward, M->L, downward, near field) -- the paper
+rebuilds the tree whenever points move (t_tree + t_run, Sec. III).
+
+value  = targets / (device time of set_points + eval), inputs resident in HBM, L2 flushed
+         (256 MiB write) between timed steps, timed per step with CUDA events.
+e2e    = the same through the C ABI with pinned HOST buffers (copies inside the timed region).
+--impl reference: the CPU oracle (direct FP64 sum, oracle/direct.c) on the host cores,
+         on a bounded sample of targets per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+N_POINTS, P_ORDER, Q_LEAF = 262144, 10, 128
+METRIC = "Stokeslet KAFMM Mpoints/s at rel L2 err <=1e-5 vs plain FP64 GPU form; S->T GFLOP/s"
+WORKLOAD = "stokeslet_uniform_256k_p10_q128_l4"
+# FLOP counts of one pair evaluation (add/mul = 1, FMA = 2, rsqrt = 1): the Stokeslet S->T
+# pair in the leaf kernel (stk_st): 3 sub, r^2 (5), rsqrt, ir^3 (2), r.f (5), scale (1),
+# 3 x (mul + FMA + FMA = 5) -> 29.
+FLOP_ST_PAIR = 29
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index=0):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            v = [x.strip() for x in line.split(",")]
+            if len(v) < 9:
+                continue
+            try:
+                sm.append(float(v[1]))
+                mx.append(float(v[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, v[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(max_seconds=15.0):
+    """The oracle's direct FP64 sum on the host cores over a bounded sample of targets of the
+    same workload (all sources); scaled to Mpoints/s (targets per second)."""
+    from oracle import direct
+    pts, f = workloads.stokes_uniform(N_POINTS, seed=1, dtype=np.float32)
+    pts64, f64 = pts.astype(np.float64), f.astype(np.float64)
+    cores = os.cpu_count() or 1
+    nt = 64
+    direct.direct("stokeslet", pts64[:8], pts64, f64)  # load + warm
+    while True:
+        t0 = time.perf_counter()
+        direct.direct("stokeslet", pts64[:nt], pts64, f64)
+        dt = time.perf_counter() - t0
+        if dt > max_seconds / 4 or nt >= N_POINTS:
+            break
+        nt = min(N_POINTS, int(nt * max(2.0, (max_seconds / 4) / max(dt, 1e-3))))
+    return {"value": nt / dt / 1e6, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+            "sample": f"O1 direct FP64 sum, {nt} of {N_POINTS} targets x all sources, "
+                      f"{dt:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    res = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(max_seconds=max(2.0, 40.0 / max(1, args.steps + args.warmup)))
+        if i >= args.warmup:
+            res.append(r)
+    v = float(np.median([r["value"] for r in res]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpoints/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": N_POINTS / (v * 1e6) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_points": N_POINTS, "p": P_ORDER, "q": Q_LEAF,
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "Mpoints/s", "cores": res[-1]["cores"],
+                             "kind": "oracle", "sample": res[-1]["sample"]},
+            "e2e": {"value": v, "unit": "Mpoints/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2010_15155_gb300 import kafmm as K
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    pts, f = workloads.stokes_uniform(N_POINTS, seed=1 + rank, dtype=np.float32)
+    y = torch.from_numpy(pts).to(dev)
+    s = torch.from_numpy(f).to(dev)
+    g = torch.empty((N_POINTS, 3), dtype=torch.float32, device=dev)
+    prec = {"mixed": K.PREC_MIXED, "fp32": K.PREC_FP32, "fp64": K.PREC_FP64}[args.precision]
+    plan = K.Plan(K.STOKESLET, p=P_ORDER, q=Q_LEAF, precision=prec, variant=K.ML_L4,
+                  stream=stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # accuracy against the plain FP64 GPU form (outside the timed region)
+    err = None
+    if rank == 0 and not args.skip_check:
+        ref_plan = K.Plan(K.STOKESLET, p=P_ORDER, q=Q_LEAF, precision=K.PREC_FP64,
+                          variant=K.ML_L4, stream=stream.cuda_stream)
+        ref_plan.set_points(y.double())
+        gref = ref_plan.eval(s.double())
+        plan.set_points(y)
+        plan.eval(s, g)
+        torch.cuda.synchronize(dev)
+        err = float(torch.linalg.norm(g.double() - gref) / torch.linalg.norm(gref))
+        ref_plan.close()
+        del gref
+
+    def step():
+        plan.set_points(y)
+        plan.eval(s, g)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    times, phases = [], []
+    torch.cuda.synchronize(dev)
+    for _ in range(args.steps):
+        flush.fill_(float(_))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        phases.append(plan.phase_times())
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N_POINTS / (ms * 1e-3) / 1e6
+
+    # end to end through the C ABI with pinned host buffers
+    yh = torch.from_numpy(pts).pin_memory()
+    sh = torch.from_numpy(f).pin_memory()
+    gh = torch.empty((N_POINTS, 3), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        plan.set_points(yh)
+        plan.eval(sh, gh)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ne = max(3, args.steps // 2)
+    for _ in range(ne):
+        plan.set_points(yh)
+        plan.eval(sh, gh)
+    torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t0) / ne * 1e3
+
+    info = plan.info()
+    ph = {k: float(np.median([p[k] for p in phases])) for k in phases[0]}
+    peaks, src = _peaks()
+    # dominant kernel: M->L.  Algorithmic flops per launch = V translations x 2 n^2 x 4 columns.
+    n = 6 * (P_ORDER - 1) ** 2 + 2
+    m2l_flops = info["n_v"] * 2.0 * n * n * 4
+    m2l_s = ph["m2l"] * 1e-3
+    if args.precision == "mixed" and plan_uses_tc(plan):
+        bound, peak, unit = "tensor", peaks["bf16_tflops"], "TFLOP/s"
+        achieved = m2l_flops / m2l_s / 1e12
+        peak_note = f"bf16 dense burst, {src}"
+    else:
+        # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x max SM clock
+        bound, unit = "alu", "TFLOP/s"
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = m2l_flops / m2l_s / 1e12
+        peak_note = "FP32 CUDA cores, 152 SM x 128 x 2 x max clock"
+    st_gflops = info["near_pairs"] * FLOP_ST_PAIR / (ph["leaves"] * 1e-3) / 1e9
+    launches = plan_launches(plan)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3" if args.precision == "mixed"
+        else ("f32" if args.precision == "fp32" else "f64"),
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_points": N_POINTS, "p": P_ORDER, "q": Q_LEAF,
+                   "ml_table": "four-channel Laplace", "precision": args.precision,
+                   "l2": "flushed (256 MiB write) between timed steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "rel_l2_vs_fp64": err,
+        "st_gflops": st_gflops,
+        "phases_ms": ph,
+        "tree": info,
+        "roofline": {"bound": bound, "kernel": "m2l", "achieved": achieved, "peak": peak,
+                     "unit": unit, "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_note},
+        "e2e": {"value": world * N_POINTS / (e2e_ms * 1e-3) / 1e6, "unit": "Mpoints/s",
+                "h2d_bytes_per_step": int(pts.nbytes + f.nbytes),
+                "d2h_bytes_per_step": int(gh.numel() * 4)},
+        "clocks": clk,
+        "gpu_launches": launches * args.steps if launches is not None else None,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def plan_uses_tc(plan):
+    from paper_2010_15155_gb300 import kafmm as K
+    return bool(K.kafmm_get_counters(plan.h)["tensor_core_m2l"])
+
+
+def plan_launches(plan):
+    from paper_2010_15155_gb300 import kafmm as K
+    return K.kafmm_get_counters(plan.h)["launches_per_step"]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
+    ap.add_argument("--skip-check", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

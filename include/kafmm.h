@@ -154,6 +154,11 @@ int kafmm_get_list(kafmm_plan_t plan, int kind, int64_t* offsets, int32_t* entri
  * 6 whole eval.  Host array t[n], up to 8 entries. */
 int kafmm_phase_times(kafmm_plan_t plan, double* t, int n);
 
+/* Counters of the last calls (host array c[n], up to 8 entries): 0 kernel launches of the
+ * last kafmm_set_points, 1 kernel launches of the last kafmm_eval, 2 whether M->L ran on the
+ * tcgen05 tensor cores (0/1), 3 launches of set_points + eval. */
+int kafmm_get_counters(kafmm_plan_t plan, int64_t* c, int n);
+
 /* Releases the plan and all device memory it owns. */
 int kafmm_destroy(kafmm_plan_t plan);
 

@@ -6,6 +6,8 @@
 
 namespace kafmm {
 
+thread_local long long g_launches = 0;
+
 int fail(Plan& P, int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -178,6 +180,7 @@ extern "C" int kafmm_set_points(kafmm_plan_t pl, const void* y, int64_t ns, cons
   P.have_points = false;
   int rc = ensure_ops(P);
   if (rc) return rc;
+  g_launches = 0;
   size_t es = dtype == KAFMM_F64 ? 8 : 4;
   const void* yd = y;
   const void* xd = x;
@@ -196,8 +199,9 @@ extern "C" int kafmm_set_points(kafmm_plan_t pl, const void* y, int64_t ns, cons
   }
   rc = build_tree(P, yd, ns, xd, nt, dtype);
   if (rc) return rc;
-  rc = build_worklists(P, 64 / P.C, 64 / P.C);
+  rc = build_worklists(P, 64 / P.C, P.use_tc ? 128 / P.C * 2 : 64 / P.C);
   if (rc) return rc;
+  P.launches_points = g_launches;
   P.have_points = true;
   return 0;
 }
@@ -225,7 +229,9 @@ extern "C" int kafmm_eval(kafmm_plan_t pl, const void* s, void* g, int dtype) {
     gd = P.io_out.p;
   }
   CKP(cudaMemsetAsync(P.tree.status.p, 0, 4, P.stream));
+  long long l0 = g_launches;
   rc = evaluate(P, sd, gd, dtype);
+  P.launches_eval = g_launches - l0;
   if (rc) return rc;
   if (host_out)
     CKP(cudaMemcpyAsync(g, gd, es * P.kt * P.tree.n_trg, cudaMemcpyDeviceToHost, P.stream));
@@ -297,7 +303,7 @@ extern "C" int kafmm_get_tree(kafmm_plan_t pl, int32_t* level, int32_t* anchor, 
   if (anchor) {
     DevBuf tmp;
     CKP(tmp.reserve(sizeof(int32_t) * 3 * nb));
-    k_anchor<<<256, 256, 0, st>>>(T.key.as<uint64_t>(), nb, tmp.as<int32_t>());
+    KL k_anchor<<<256, 256, 0, st>>>(T.key.as<uint64_t>(), nb, tmp.as<int32_t>());
     CKP(cudaMemcpyAsync(anchor, tmp.p, sizeof(int32_t) * 3 * nb, cudaMemcpyDeviceToHost, st));
     CKP(cudaStreamSynchronize(st));
   }
@@ -322,7 +328,7 @@ extern "C" int kafmm_get_list(kafmm_plan_t pl, int kind, int64_t* offsets, int32
   const int32_t* src_ent = nullptr;
   if (kind == 1) {
     CKP(doff.reserve(sizeof(int64_t) * (nb + 1)));
-    k_vtab_count<<<256, 256, 0, st>>>(T.vtab.as<int32_t>(), nb, doff.as<int64_t>());
+    KL k_vtab_count<<<256, 256, 0, st>>>(T.vtab.as<int32_t>(), nb, doff.as<int64_t>());
     std::vector<int64_t> cnt(nb);
     CKP(cudaMemcpyAsync(cnt.data(), doff.p, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, st));
     CKP(cudaStreamSynchronize(st));
@@ -331,7 +337,7 @@ extern "C" int kafmm_get_list(kafmm_plan_t pl, int kind, int64_t* offsets, int32
     n = off[nb];
     CKP(cudaMemcpyAsync(doff.p, off.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, st));
     CKP(dent.reserve(sizeof(int32_t) * (n + 1)));
-    k_vtab_csr<<<256, 256, 0, st>>>(T.vtab.as<int32_t>(), nb, doff.as<int64_t>(), dent.as<int32_t>());
+    KL k_vtab_csr<<<256, 256, 0, st>>>(T.vtab.as<int32_t>(), nb, doff.as<int64_t>(), dent.as<int32_t>());
     src_ent = dent.as<int32_t>();
   } else {
     src_off = kind == 0 ? T.u_off.as<int64_t>() : (kind == 2 ? T.w_off.as<int64_t>() : T.x_off.as<int64_t>());
@@ -369,6 +375,15 @@ extern "C" int kafmm_phase_times(kafmm_plan_t pl, double* t, int n) {
     ms[i] = v;
   }
   for (int i = 0; i < n && i < 8; ++i) t[i] = i < 7 ? ms[i] : 0.0;
+  return 0;
+}
+
+extern "C" int kafmm_get_counters(kafmm_plan_t pl, int64_t* c, int n) {
+  PLAN_CHECK(pl);
+  if (!c || n < 0) return fail(P, KAFMM_ERR_ARG, "null array");
+  int64_t v[4] = {P.launches_points, P.launches_eval, P.use_tc ? 1 : 0,
+                  P.launches_points + P.launches_eval};
+  for (int i = 0; i < n && i < 8; ++i) c[i] = i < 4 ? v[i] : 0;
   return 0;
 }
 

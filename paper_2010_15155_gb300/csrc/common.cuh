@@ -11,6 +11,10 @@
 
 namespace kafmm {
 
+// Count of kernel launches issued by this thread (reported per set_points + eval).
+extern thread_local long long g_launches;
+#define KL ++::kafmm::g_launches,
+
 constexpr int MAX_LEVEL = 20;        // finest octree level; keys carry 20 bits per axis
 constexpr int MAX_LEVELS = MAX_LEVEL + 1;
 constexpr double PI = 3.14159265358979323846;
@@ -22,13 +26,18 @@ constexpr double ALPHA_UE = 1.05, ALPHA_UC = 2.95, ALPHA_DE = 2.95, ALPHA_DC = 1
 constexpr double PINV_RCOND = 1e-9;
 
 // Operator slots: 343 M->L offsets (ox,oy,oz) in [-3,3]^3 (the 27 inner ones unused), then
-// 8 M->M octants, 8 L->L octants, the upward and the downward pseudo-inverse.
+// 8 M->M octants, 8 L->L octants, and the upward / downward pseudo-inverses in factored form
+// pinv = V (S^+ U^T): slot *1 holds S^+ U^T, slot *2 holds V.  Applying the two factors in turn
+// keeps the rounding of a short format confined to the directions the pseudo-inverse
+// amplifies; the product matrix itself, rounded to FP32, loses all accuracy.
 constexpr int OP_M2L = 0, N_M2L = 343;
 constexpr int OP_M2M = OP_M2L + N_M2L;
 constexpr int OP_L2L = OP_M2M + 8;
-constexpr int OP_UC2UE = OP_L2L + 8;
-constexpr int OP_DC2DE = OP_UC2UE + 1;
-constexpr int N_OPS = OP_DC2DE + 1;
+constexpr int OP_UP1 = OP_L2L + 8;
+constexpr int OP_UP2 = OP_UP1 + 1;
+constexpr int OP_DN1 = OP_UP2 + 1;
+constexpr int OP_DN2 = OP_DN1 + 1;
+constexpr int N_OPS = OP_DN2 + 1;
 
 __host__ __device__ inline int m2l_index(int ox, int oy, int oz) {
   return (ox + 3) + 7 * (oy + 3) + 49 * (oz + 3);

@@ -182,7 +182,9 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
 //   out[b] (+)= alpha_b * sum_k Op[op(k)] * shift_k(in[src(b, k)])
 // with [R][C] per box.  Modes: M->L over the 216 V slots, M->M over 8 children, L->L from the
 // parent, and the check-to-equivalent pseudo-inverses (alpha_b = box half-width).
-enum GemmMode { GM_M2L = 0, GM_M2M = 1, GM_L2L = 2, GM_PINV_UP = 3, GM_PINV_DN = 4 };
+// GM_APPLY: one operator (args.op) on the box itself; args.scale_r multiplies by the box
+// half-width (the level scaling of a pseudo-inverse).
+enum GemmMode { GM_M2L = 0, GM_M2M = 1, GM_L2L = 2, GM_APPLY = 3 };
 
 template <class T>
 struct GemmArgs {
@@ -195,6 +197,7 @@ struct GemmArgs {
   const int* boxlist;
   const int32_t* vtab;
   int mode, R;
+  int op, scale_r;
 };
 
 template <int C>
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> a) {
     int b = tid < tile.y ? a.boxlist[tile.x + tid] : -1;
     ob[tid] = b;
     T al = 1;
-    if (b >= 0 && (a.mode == GM_PINV_UP || a.mode == GM_PINV_DN))
+    if (b >= 0 && a.mode == GM_APPLY && a.scale_r)
       al = (T)(0.5 * a.geo.L / (double)(1 << a.t.level[b]));
     alph[tid] = al;
   }
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> a) {
     } else if (a.mode == GM_L2L) {
       op = OP_L2L + cls;
     } else {
-      op = a.mode == GM_PINV_UP ? OP_UC2UE : OP_DC2DE;
+      op = a.op;
     }
     int has = 0;
     if (tid < NB) {
@@ -285,6 +288,13 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> a) {
     }
     if (!__syncthreads_or(has)) continue;
     const T* opp = a.ops + (int64_t)op * R * R;
+    // three-level summation (16-term tile -> slot -> total), so no single FP32 accumulator
+    // runs over all 189 x R terms of an M->L sum
+    T part[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[i][j] = 0;
     for (int k0 = 0; k0 < R; k0 += BK) {
       // A tile: rows row0.., cols k0..  (As[kk][row])
 #pragma unroll
@@ -318,6 +328,11 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> a) {
         }
       }
       __syncthreads();
+      T chunk[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) chunk[i][j] = 0;
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         T av[4], bv[4];
@@ -328,10 +343,18 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> a) {
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+          for (int j = 0; j < 4; ++j) chunk[i][j] += av[i] * bv[j];
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) part[i][j] += chunk[i][j];
       __syncthreads();
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += part[i][j];
   }
   bool accumulate = a.mode == GM_M2L || a.mode == GM_L2L;
 #pragma unroll
@@ -496,8 +519,22 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
           sv[k] = q;
         }
         __syncthreads();
-        if (act)
-          for (int k = grp; k < a.n; k += G) far_eval<T, PR>(xl, yl, zl, sp[k], sv[k], far);
+        if (act) {  // partial sums per 32 equivalent points, then per surface
+          T fs[KT];
+#pragma unroll
+          for (int q = 0; q < KT; ++q) fs[q] = 0;
+          for (int k0 = grp; k0 < a.n; k0 += 32 * G) {
+            T fp[KT];
+#pragma unroll
+            for (int q = 0; q < KT; ++q) fp[q] = 0;
+            int kend = min(a.n, k0 + 32 * G);
+            for (int k = k0; k < kend; k += G) far_eval<T, PR>(xl, yl, zl, sp[k], sv[k], fp);
+#pragma unroll
+            for (int q = 0; q < KT; ++q) fs[q] += fp[q];
+          }
+#pragma unroll
+          for (int q = 0; q < KT; ++q) far[q] += fs[q];
+        }
       }
     }
 
@@ -549,6 +586,9 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
           shift_decode(ent_sc[e], sx, sy, sz);
           T ox = (T)(sx * a.geo.L) - cx, oy = (T)(sy * a.geo.L) - cy, oz = (T)(sz * a.geo.L) - cz;
           int cnt = ent_cnt[e];
+          T pe[KT];  // partial sum of this entry (plain mode)
+#pragma unroll
+          for (int k = 0; k < KT; ++k) pe[k] = 0;
           for (int j = grp; j < cnt; j += G) {
             T4 y = sp[base + j];
             T r0 = xl - (y.x + ox), r1 = yl - (y.y + oy), r2 = zl - (y.z + oz);
@@ -577,8 +617,12 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
               }
             } else {
 #pragma unroll
-              for (int k = 0; k < KT; ++k) acc[k] += tmp[k];
+              for (int k = 0; k < KT; ++k) pe[k] += tmp[k];
             }
+          }
+          if (!a.kahan) {
+#pragma unroll
+            for (int k = 0; k < KT; ++k) acc[k] += pe[k];
           }
           base += cnt;
         }
@@ -736,10 +780,10 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
   CK(P.s_sorted.reserve(sizeof(T4) * NV * (ns + 1)));
   if (ns > 0) {
     if (s_dtype == KAFMM_F64)
-      k_prep_src<double, T, PR><<<grid_for(ns, 256), 256, 0, st>>>(
+      KL k_prep_src<double, T, PR><<<grid_for(ns, 256), 256, 0, st>>>(
           (const double*)s_in, T_.src_perm.as<uint32_t>(), ns, P.s_sorted.as<T4>());
     else
-      k_prep_src<float, T, PR><<<grid_for(ns, 256), 256, 0, st>>>(
+      KL k_prep_src<float, T, PR><<<grid_for(ns, 256), 256, 0, st>>>(
           (const float*)s_in, T_.src_perm.as<uint32_t>(), ns, P.s_sorted.as<T4>());
   }
   const T4* spos = T_.src_pos.as<T4>();
@@ -769,7 +813,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       sa.boxes = sleaves;
       sa.check = P.up_check.as<T>();
       sa.mode = 0;
-      k_s2check<T, PR><<<n_sleaves, 128, 0, st>>>(sa);
+      KL k_s2check<T, PR><<<n_sleaves, 128, 0, st>>>(sa);
     }
     // M->M, deepest level first
     GemmArgs<T> ga;
@@ -789,7 +833,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       ga.in = P.up_check.as<T>();
       ga.out = P.up_check.as<T>();
       ga.tiles = P.tiles.as<int4>() + W.m2m[l][0];
-      k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+      KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
     }
     cudaEventRecord(P.ev[4], st);
     // M->L over the V lists (all levels)
@@ -803,7 +847,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
         ga.in = P.up_check.as<T>();
         ga.out = P.dn_check.as<T>();
         ga.tiles = P.tiles.as<int4>() + W.m2l[0];
-        k_gemm<T, C><<<dim3(nm2l, rb), blk, 0, st>>>(ga);
+        KL k_gemm<T, C><<<dim3(nm2l, rb), blk, 0, st>>>(ga);
       }
     }
     cudaEventRecord(P.ev[5], st);
@@ -812,7 +856,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       sa.boxes = boxlist + W.xbox_off;
       sa.check = P.dn_check.as<T>();
       sa.mode = 1;
-      k_s2check<T, PR><<<W.xbox_n, 128, 0, st>>>(sa);
+      KL k_s2check<T, PR><<<W.xbox_n, 128, 0, st>>>(sa);
     }
     // L->L, coarsest level first
     for (int l = 0; l < MAX_LEVELS; ++l) {
@@ -822,24 +866,40 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       ga.in = P.dn_check.as<T>();
       ga.out = P.dn_check.as<T>();
       ga.tiles = P.tiles.as<int4>() + W.l2l[l][0];
-      k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+      KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
     }
-    // equivalent densities where they are evaluated at targets
+    // equivalent densities where they are evaluated at targets: r * V * ((S^+ U^T) * check),
+    // the two factors applied in turn (tmp = the downward equivalent buffer of the up pass
+    // is not yet used, so the up pass stages through dn_equiv and vice versa through up_equiv)
     int n = W.pup[1] - W.pup[0];
     if (n > 0) {
-      ga.mode = GM_PINV_UP;
-      ga.in = P.up_check.as<T>();
-      ga.out = P.up_equiv.as<T>();
+      ga.mode = GM_APPLY;
       ga.tiles = P.tiles.as<int4>() + W.pup[0];
-      k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+      ga.in = P.up_check.as<T>();
+      ga.out = P.dn_equiv.as<T>();
+      ga.op = OP_UP1;
+      ga.scale_r = 0;
+      KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+      ga.in = P.dn_equiv.as<T>();
+      ga.out = P.up_equiv.as<T>();
+      ga.op = OP_UP2;
+      ga.scale_r = 1;
+      KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
     }
     n = W.pdn[1] - W.pdn[0];
     if (n > 0) {
-      ga.mode = GM_PINV_DN;
-      ga.in = P.dn_check.as<T>();
-      ga.out = P.dn_equiv.as<T>();
+      ga.mode = GM_APPLY;
       ga.tiles = P.tiles.as<int4>() + W.pdn[0];
-      k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+      ga.in = P.dn_check.as<T>();
+      ga.out = P.up_check.as<T>();   // up_check is no longer needed here
+      ga.op = OP_DN1;
+      ga.scale_r = 0;
+      KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+      ga.in = P.up_check.as<T>();
+      ga.out = P.dn_equiv.as<T>();
+      ga.op = OP_DN2;
+      ga.scale_r = 1;
+      KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
     }
   }
   cudaEventRecord(P.ev[6], st);
@@ -871,17 +931,17 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
     la.cap = cap;
     size_t smem = (size_t)cap * (1 + NV) * sizeof(T4) + sizeof(T) * LEAF_THREADS * KT;
     CK(cudaFuncSetAttribute(k_leaf<T, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_leaf<T, PR><<<W.leaves_n, LEAF_THREADS, smem, st>>>(la);
+    KL k_leaf<T, PR><<<W.leaves_n, LEAF_THREADS, smem, st>>>(la);
   }
   CK(cudaGetLastError());
   // back to the caller's order and dtype
   if (nt > 0) {
     const uint32_t* tperm = T_.same ? T_.src_perm.as<uint32_t>() : T_.trg_perm.as<uint32_t>();
     if (s_dtype == KAFMM_F64)
-      k_unperm<T, double><<<grid_for(nt * KT, 256), 256, 0, st>>>(P.g_sorted.as<T>(), tperm, nt, KT,
+      KL k_unperm<T, double><<<grid_for(nt * KT, 256), 256, 0, st>>>(P.g_sorted.as<T>(), tperm, nt, KT,
                                                                 (double*)g_out);
     else
-      k_unperm<T, float><<<grid_for(nt * KT, 256), 256, 0, st>>>(P.g_sorted.as<T>(), tperm, nt, KT,
+      KL k_unperm<T, float><<<grid_for(nt * KT, 256), 256, 0, st>>>(P.g_sorted.as<T>(), tperm, nt, KT,
                                                                (float*)g_out);
   }
   cudaEventRecord(P.ev[7], st);

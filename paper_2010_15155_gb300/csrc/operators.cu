@@ -9,9 +9,12 @@
 //   M->L(o)  = K(dc <- ue at offset o) * UC2UE
 //   M->M(c)  = K(uc parent <- ue child c) * UC2UE
 //   L->L(c)  = 2 K(dc child c <- de parent) * DC2DE
+// each formed through the SVD factors, (K V)(S^+ U^T), so the large entries of the
+// pseudo-inverse never meet the rounding of the product.
 // (geometry in units of the half-width of the child / of the box), which equals the paper's
 // sequence "equivalent density = pinv * check, then translate" up to rounding.
 #include <cmath>
+#include <cstring>
 
 #include "plan.cuh"
 
@@ -75,7 +78,7 @@ __global__ void k_identity(double* V, int n) {
 // One round of one-sided (Hestenes) Jacobi on the rows of At (= columns of A): the n/2
 // disjoint pairs of the round-robin schedule, one block per pair.
 __global__ void k_jacobi_round(double* __restrict__ At, double* __restrict__ Vt, int n, int round,
-                               int* rotated, double tol) {
+                               int* rotated, double tol, unsigned* worst) {
   __shared__ double red[3][32];
   __shared__ double cs[2];
   int p = blockIdx.x;
@@ -110,6 +113,10 @@ __global__ void k_jacobi_round(double* __restrict__ At, double* __restrict__ Vt,
       g += red[2][k];
     }
     double c = 1.0, s = 0.0;
+    if (a > 0 && b > 0) {  // largest relative off-orthogonality of the sweep (float bits)
+      float rel = (float)(fabs(g) / sqrt(a * b));
+      atomicMax(worst, __float_as_uint(rel));
+    }
     if (fabs(g) > tol * sqrt(a * b) && a > 0 && b > 0) {
       double zeta = (b - a) / (2.0 * g);
       double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -203,6 +210,12 @@ __global__ void k_gemm64(const double* __restrict__ A, int ta, const double* __r
   }
 }
 
+__global__ void k_scale_rows(const double* in, const double* w, int n, double* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = in[e] * w[e / n];
+}
+
 __global__ void k_round32(const double* in, int64_t n, float* out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
@@ -231,29 +244,38 @@ __global__ void k_split_bf16(const double* in, int R, int Rpad, int64_t nops, __
     if (e_ != cudaSuccess) return cuda_fail(P, e_, #call); \
   } while (0)
 
-// pinv of K (R x R) into out, via one-sided Jacobi SVD.
-static int pinv64(Plan& P, const double* K, double* out, double* At, double* Vt, double* w, int* flag) {
+// Factored pinv of K (R x R) via one-sided Jacobi SVD: K = W V^T with orthogonal columns
+// W = U S.  out1 = S^+ U^T = diag(w) W^T (w_k = 1/sigma_k^2 above the cutoff), out2 = V.
+static int pinv64(Plan& P, const double* K, double* out1, double* out2, double* At, double* Vt,
+                  double* w, int* flag) {
   int R = P.R;
   cudaStream_t st = P.stream;
   int g = 512;
-  k_transpose<<<g, 256, 0, st>>>(K, R, At);
-  k_identity<<<g, 256, 0, st>>>(Vt, R);
+  KL k_transpose<<<g, 256, 0, st>>>(K, R, At);
+  KL k_identity<<<g, 256, 0, st>>>(Vt, R);
+  // stop when a sweep rotates no pair: |a_i . a_j| <= tol |a_i| |a_j| with tol = 4 R eps, the
+  // level FP64 rounding of a length-R dot product can resolve
+  const double tol = 4.0 * R * 2.220446049250313e-16;
+  unsigned* worst = (unsigned*)(flag + 1);
   int sweeps = 0;
-  for (; sweeps < 60; ++sweeps) {
-    CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
-    for (int r = 0; r < R - 1; ++r) k_jacobi_round<<<R / 2, 256, 0, st>>>(At, Vt, R, r, flag, 1e-15);
-    int h = 0;
-    CK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  float last = 1.f;
+  for (; sweeps < 80; ++sweeps) {
+    CK(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
+    for (int r = 0; r < R - 1; ++r)
+      KL k_jacobi_round<<<R / 2, 256, 0, st>>>(At, Vt, R, r, flag, tol, worst);
+    int h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (!h) break;
+    memcpy(&last, &h[1], sizeof(float));
+    if (!h[0]) break;
   }
-  if (sweeps >= 60) return fail(P, KAFMM_ERR_CUDA, "Jacobi SVD did not converge");
-  k_row_norms<<<R, 256, 0, st>>>(At, R, w);
-  k_pinv_weights<<<1, 256, 0, st>>>(w, R, PINV_RCOND);
-  // pinv = V diag(1/sigma^2) A^T  (A = U S V^T  =>  A^+ = V S^-2 (A V)^T ... in row form:
-  // pinv[i][j] = sum_k Vt[k][i] w_k At[k][j])
-  dim3 gg((R + 31) / 32, (R + 31) / 32);
-  k_gemm64<<<gg, 256, 0, st>>>(Vt, 1, w, At, 1.0, R, out);
+  if (sweeps >= 80 && last > 1e-11f)
+    return fail(P, KAFMM_ERR_CUDA, "Jacobi SVD did not converge (off-orthogonality %.3g)", last);
+  KL k_row_norms<<<R, 256, 0, st>>>(At, R, w);
+  KL k_pinv_weights<<<1, 256, 0, st>>>(w, R, PINV_RCOND);
+  // rows of At are the columns of W = K V; pinv = V diag(w) W^T
+  KL k_scale_rows<<<512, 256, 0, st>>>(At, w, R, out1);
+  KL k_transpose<<<512, 256, 0, st>>>(Vt, R, out2);
   CK(cudaGetLastError());
   return 0;
 }
@@ -282,14 +304,19 @@ int build_operators(Plan& P) {
   const double* unit = P.unit64.as<double>();
   int g = 1024;
   int stokes = P.ml_stokes;
-  // pseudo-inverses at half-width 1
-  k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, ALPHA_UC, 0, 0, 0, ALPHA_UE, K);
-  int rc = pinv64(P, K, O + RR * OP_UC2UE, At, Vt, w, flag);
+  // pseudo-inverses at half-width 1 (factored)
+  KL k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, ALPHA_UC, 0, 0, 0, ALPHA_UE, K);
+  int rc = pinv64(P, K, O + RR * OP_UP1, O + RR * OP_UP2, At, Vt, w, flag);
   if (rc) return rc;
-  k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, ALPHA_DC, 0, 0, 0, ALPHA_DE, K);
-  rc = pinv64(P, K, O + RR * OP_DC2DE, At, Vt, w, flag);
+  KL k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, ALPHA_DC, 0, 0, 0, ALPHA_DE, K);
+  rc = pinv64(P, K, O + RR * OP_DN1, O + RR * OP_DN2, At, Vt, w, flag);
   if (rc) return rc;
   dim3 gg((R + 31) / 32, (R + 31) / 32);
+  // Op = alpha * (K * V) * (S^+ U^T): the product through the factors
+  auto compose = [&](int f1, int f2, double alpha, double* dst) {
+    KL k_gemm64<<<gg, 256, 0, st>>>(K, 0, nullptr, O + RR * f2, 1.0, R, Tm);
+    KL k_gemm64<<<gg, 256, 0, st>>>(Tm, 0, nullptr, O + RR * f1, alpha, R, dst);
+  };
   // M->L: centres 2 o apart (box side 2)
   for (int oz = -3; oz <= 3; ++oz)
     for (int oy = -3; oy <= 3; ++oy)
@@ -300,19 +327,19 @@ int build_operators(Plan& P) {
           CK(cudaMemsetAsync(dst, 0, sizeof(double) * RR, st));
           continue;
         }
-        k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, ALPHA_DC, 2.0 * ox, 2.0 * oy,
+        KL k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, ALPHA_DC, 2.0 * ox, 2.0 * oy,
                                                 2.0 * oz, ALPHA_UE, K);
-        k_gemm64<<<gg, 256, 0, st>>>(K, 0, nullptr, O + RR * OP_UC2UE, 1.0, R, dst);
+        compose(OP_UP1, OP_UP2, 1.0, dst);
       }
   // M->M / L->L: child half-width 1, parent half-width 2, child centre at +-1 per axis
   for (int c = 0; c < 8; ++c) {
     double cx = (c & 1) ? 1.0 : -1.0, cy = (c & 2) ? 1.0 : -1.0, cz = (c & 4) ? 1.0 : -1.0;
-    k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, 2.0 * ALPHA_UC, cx, cy, cz,
+    KL k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, 2.0 * ALPHA_UC, cx, cy, cz,
                                             ALPHA_UE, K);
-    k_gemm64<<<gg, 256, 0, st>>>(K, 0, nullptr, O + RR * OP_UC2UE, 1.0, R, O + RR * (OP_M2M + c));
-    k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, cx, cy, cz, ALPHA_DC, 0, 0, 0,
+    compose(OP_UP1, OP_UP2, 1.0, O + RR * (OP_M2M + c));
+    KL k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, cx, cy, cz, ALPHA_DC, 0, 0, 0,
                                             2.0 * ALPHA_DE, K);
-    k_gemm64<<<gg, 256, 0, st>>>(K, 0, nullptr, O + RR * OP_DC2DE, 2.0, R, O + RR * (OP_L2L + c));
+    compose(OP_DN1, OP_DN2, 2.0, O + RR * (OP_L2L + c));
   }
   CK(cudaGetLastError());
   if (P.fp64()) {
@@ -320,11 +347,11 @@ int build_operators(Plan& P) {
     CK(cudaMemcpyAsync(P.ops64.p, O, sizeof(double) * RR * N_OPS, cudaMemcpyDeviceToDevice, st));
   } else {
     CK(P.ops32.reserve(sizeof(float) * RR * N_OPS));
-    k_round32<<<2048, 256, 0, st>>>(O, (int64_t)RR * N_OPS, P.ops32.as<float>());
+    KL k_round32<<<2048, 256, 0, st>>>(O, (int64_t)RR * N_OPS, P.ops32.as<float>());
     if (P.prec == KAFMM_PREC_MIXED) {
       P.Rpad = (R + 63) / 64 * 64;
       CK(P.opsbf.reserve(sizeof(__nv_bfloat16) * 2 * (size_t)R * P.Rpad * N_M2L));
-      k_split_bf16<<<2048, 256, 0, st>>>(O + RR * OP_M2L, R, P.Rpad, N_M2L, P.opsbf.as<__nv_bfloat16>());
+      KL k_split_bf16<<<2048, 256, 0, st>>>(O + RR * OP_M2L, R, P.Rpad, N_M2L, P.opsbf.as<__nv_bfloat16>());
     }
   }
   CK(cudaGetLastError());

@@ -87,6 +87,7 @@ struct Plan {
   int64_t tiles_cap = 0;
   WorkLists wl;
   bool use_tc = false;              // tensor-core M->L available for this plan
+  long long launches_points = 0, launches_eval = 0;  // kernel launches of the last calls
   cudaEvent_t ev[8] = {0};
   double phase_ms[8] = {0};
   std::string err;

@@ -102,9 +102,9 @@ inline void scan_excl(const T* in, T* out, int64_t cap, const int* d_len, T* scr
                       cudaStream_t st) {
   int ntiles = (int)((cap + SCAN_TILE - 1) / SCAN_TILE);
   if (ntiles < 1) ntiles = 1;
-  k_scan_tiles<T><<<ntiles, SCAN_THREADS, 0, st>>>(in, cap, d_len, scratch);
-  k_scan_sums<T><<<1, SCAN_THREADS, 0, st>>>(scratch, ntiles, d_total);
-  k_scan_apply<T><<<ntiles, SCAN_THREADS, 0, st>>>(in, cap, d_len, scratch, out);
+  KL k_scan_tiles<T><<<ntiles, SCAN_THREADS, 0, st>>>(in, cap, d_len, scratch);
+  KL k_scan_sums<T><<<1, SCAN_THREADS, 0, st>>>(scratch, ntiles, d_total);
+  KL k_scan_apply<T><<<ntiles, SCAN_THREADS, 0, st>>>(in, cap, d_len, scratch, out);
 }
 
 }  // namespace kafmm

@@ -112,10 +112,10 @@ static void radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* k2, uint32_t* v
   uint32_t *va = vals, *vb = v2;
   for (int pass = 0; pass < 8; ++pass) {
     int shift = pass * 8;
-    k_radix_hist<<<nblk, RS_THREADS, 0, st>>>(ka, n, shift, hist, nblk);
+    KL k_radix_hist<<<nblk, RS_THREADS, 0, st>>>(ka, n, shift, hist, nblk);
     scan_excl<uint32_t>(hist, hist, (int64_t)256 * nblk, nullptr, hist + 256 * (int64_t)nblk,
                         nullptr, st);
-    k_radix_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, hist, nblk);
+    KL k_radix_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, hist, nblk);
     std::swap(ka, kb);
     std::swap(va, vb);
   }
@@ -540,10 +540,10 @@ static int sort_points(Plan& P, const void* pts, int64_t n, int dtype, DevBuf& k
   int g = grid_for(n, 256);
   if (n > 0) {
     if (dtype == KAFMM_F64)
-      k_keys<double><<<g, 256, 0, st>>>((const double*)pts, n, P.origin[0], P.origin[1], P.origin[2],
+      KL k_keys<double><<<g, 256, 0, st>>>((const double*)pts, n, P.origin[0], P.origin[1], P.origin[2],
                                          P.L, key.as<uint64_t>(), perm.as<uint32_t>(), status);
     else
-      k_keys<float><<<g, 256, 0, st>>>((const float*)pts, n, P.origin[0], P.origin[1], P.origin[2],
+      KL k_keys<float><<<g, 256, 0, st>>>((const float*)pts, n, P.origin[0], P.origin[1], P.origin[2],
                                         P.L, key.as<uint64_t>(), perm.as<uint32_t>(), status);
     radix_sort(key.as<uint64_t>(), perm.as<uint32_t>(), k2.as<uint64_t>(), v2.as<uint32_t>(),
                T.s_hist.as<uint32_t>(), n, st);
@@ -553,17 +553,17 @@ static int sort_points(Plan& P, const void* pts, int64_t n, int dtype, DevBuf& k
   if (n > 0) {
     if (P.fp64()) {
       if (dtype == KAFMM_F64)
-        k_gather_pos<double, double4><<<g, 256, 0, st>>>((const double*)pts, perm.as<uint32_t>(), n,
+        KL k_gather_pos<double, double4><<<g, 256, 0, st>>>((const double*)pts, perm.as<uint32_t>(), n,
                                                          pos.as<double4>());
       else
-        k_gather_pos<float, double4><<<g, 256, 0, st>>>((const float*)pts, perm.as<uint32_t>(), n,
+        KL k_gather_pos<float, double4><<<g, 256, 0, st>>>((const float*)pts, perm.as<uint32_t>(), n,
                                                         pos.as<double4>());
     } else {
       if (dtype == KAFMM_F64)
-        k_gather_pos<double, float4><<<g, 256, 0, st>>>((const double*)pts, perm.as<uint32_t>(), n,
+        KL k_gather_pos<double, float4><<<g, 256, 0, st>>>((const double*)pts, perm.as<uint32_t>(), n,
                                                         pos.as<float4>());
       else
-        k_gather_pos<float, float4><<<g, 256, 0, st>>>((const float*)pts, perm.as<uint32_t>(), n,
+        KL k_gather_pos<float, float4><<<g, 256, 0, st>>>((const float*)pts, perm.as<uint32_t>(), n,
                                                        pos.as<float4>());
     }
   }
@@ -631,15 +631,15 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   a.q = P.q;
   unsigned* status = T.status.as<unsigned>();
   int* d_total = a.cnt + MAX_LEVELS + 1;
-  k_root<<<1, 32, 0, st>>>(a, (int)ns, (int)(T.same ? ns : nt));
+  KL k_root<<<1, 32, 0, st>>>(a, (int)ns, (int)(T.same ? ns : nt));
   for (int l = 0; l < MAX_LEVEL; ++l) {
     int g = grid_for(a.cap[l], 256);
-    k_split<<<g, 256, 0, st>>>(a, l, status);
+    KL k_split<<<g, 256, 0, st>>>(a, l, status);
     int* scratch = a.choff + a.cap_off[MAX_LEVELS] + 16;
     scan_excl<int>(a.nch + a.cap_off[l], a.choff + a.cap_off[l], a.cap[l], a.cnt + l, scratch, d_total,
                    st);
-    k_level_total<<<1, 32, 0, st>>>(a, l, d_total, status);
-    k_emit<<<g, 256, 0, st>>>(a, l);
+    KL k_level_total<<<1, 32, 0, st>>>(a, l, d_total, status);
+    KL k_emit<<<g, 256, 0, st>>>(a, l);
   }
   CK(cudaGetLastError());
   int cnt[MAX_LEVELS];
@@ -678,7 +678,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   CK(T.d_lvl_start.reserve(sizeof(int) * (MAX_LEVELS + 1)));
   CK(cudaMemcpyAsync(T.d_lvl_start.p, T.lvl_start, sizeof(int) * (MAX_LEVELS + 1),
                      cudaMemcpyHostToDevice, st));
-  k_compact<<<grid_for(nb, 256), 256, 0, st>>>(a, lay, nb, T.key.as<uint64_t>(), T.level.as<int8_t>(),
+  KL k_compact<<<grid_for(nb, 256), 256, 0, st>>>(a, lay, nb, T.key.as<uint64_t>(), T.level.as<int8_t>(),
                                               T.parent.as<int>(), T.child.as<int>(), T.sb.as<int>(),
                                               T.se.as<int>(), T.tb.as<int>(), T.te.as<int>(),
                                               T.leaf.as<int8_t>());
@@ -687,9 +687,9 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   int* lpos = T.leaves.as<int>() + nb;
   int* lscratch = lpos + nb;
   int* ltot = lscratch + nb / SCAN_TILE + 8;
-  k_i8_to_i32<<<grid_for(nb, 256), 256, 0, st>>>(T.leaf.as<int8_t>(), nb, lpos);
+  KL k_i8_to_i32<<<grid_for(nb, 256), 256, 0, st>>>(T.leaf.as<int8_t>(), nb, lpos);
   scan_excl<int>(lpos, lpos, nb, nullptr, lscratch, ltot, st);
-  k_leaf_list<<<grid_for(nb, 256), 256, 0, st>>>(T.leaf.as<int8_t>(), lpos, nb, T.leaves.as<int>());
+  KL k_leaf_list<<<grid_for(nb, 256), 256, 0, st>>>(T.leaf.as<int8_t>(), lpos, nb, T.leaves.as<int>());
   CK(cudaMemcpyAsync(&T.nleaf, ltot, sizeof(int), cudaMemcpyDeviceToHost, st));
   cudaEventRecord(P.ev[1], st);
 
@@ -707,7 +707,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   lo.w_cnt = T.w_off.as<int64_t>();
   lo.x_cnt = T.x_off.as<int64_t>();
   int g = grid_for(nb, 128, 152 * 16);
-  k_lists<false><<<g, 128, 0, st>>>(tv, lo);
+  KL k_lists<false><<<g, 128, 0, st>>>(tv, lo);
   int64_t tot[3];
   int64_t* sc[3] = {lo.u_cnt, lo.w_cnt, lo.x_cnt};
   for (int k = 0; k < 3; ++k) {
@@ -730,7 +730,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   lo.w_flag = T.w_flag.as<int8_t>();
   lo.near_pairs = (unsigned long long*)(T.status.as<unsigned>() + 8);
   CK(cudaMemsetAsync(lo.near_pairs, 0, 8, st));
-  k_lists<true><<<g, 128, 0, st>>>(tv, lo);
+  KL k_lists<true><<<g, 128, 0, st>>>(tv, lo);
   unsigned long long pairs = 0;
   CK(cudaMemcpyAsync(&pairs, lo.near_pairs, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaGetLastError());
@@ -740,7 +740,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   // V entries and the largest leaf
   unsigned long long* stats = (unsigned long long*)(T.status.as<unsigned>() + 10);
   CK(cudaMemsetAsync(stats, 0, 16, st));
-  k_tree_stats<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vtab.as<int32_t>(), stats);
+  KL k_tree_stats<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vtab.as<int32_t>(), stats);
   unsigned long long hs[2];
   CK(cudaMemcpyAsync(hs, stats, 16, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -57,6 +57,7 @@ def lib():
             "kafmm_get_tree": ([vp, vp, vp, vp, vp], i32),
             "kafmm_get_list": ([vp, i32, vp, vp, vp], i32),
             "kafmm_phase_times": ([vp, ctypes.POINTER(dbl), i32], i32),
+            "kafmm_get_counters": ([vp, ctypes.POINTER(i64), i32], i32),
             "kafmm_destroy": ([vp], i32),
             "kafmm_last_error": ([vp], ctypes.c_char_p),
         }
@@ -161,6 +162,13 @@ def kafmm_phase_times(plan):
     _check(plan, lib().kafmm_phase_times(plan, t, 8))
     names = ["tree", "lists", "upward", "m2l", "downward", "leaves", "eval"]
     return {k: float(t[i]) for i, k in enumerate(names)}
+
+
+def kafmm_get_counters(plan):
+    c = (ctypes.c_int64 * 8)()
+    _check(plan, lib().kafmm_get_counters(plan, c, 8))
+    return {"launches_points": int(c[0]), "launches_eval": int(c[1]),
+            "tensor_core_m2l": int(c[2]), "launches_per_step": int(c[3])}
 
 
 def kafmm_destroy(plan):

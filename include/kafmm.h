@@ -80,8 +80,14 @@ enum {
   /* 1: evaluate only the near field (U-list S->T sums).  Default 0. */
   KAFMM_OPT_NEAR_ONLY = 4,
   /* 1: Kahan-compensated accumulation in the FP32 near field.  Default 0. */
-  KAFMM_OPT_KAHAN = 5
+  KAFMM_OPT_KAHAN = 5,
+  /* Split format of the tensor-core M->L in KAFMM_PREC_MIXED (default KAFMM_TC_TF32X3):
+   * each operand x = hi + lo in tf32 (or bf16) and each product hi*hi + hi*lo + lo*hi.
+   * TF32x3 keeps the mixed form within 1e-5 of the FP64 form; BF16x3 is faster and about
+   * an order of magnitude less accurate. */
+  KAFMM_OPT_TC_SPLIT = 6
 };
+enum { KAFMM_TC_TF32X3 = 0, KAFMM_TC_BF16X3 = 1 };
 enum { KAFMM_PREC_FP64 = 0, KAFMM_PREC_FP32 = 1, KAFMM_PREC_MIXED = 2 };
 enum { KAFMM_ML_G = 0, KAFMM_ML_L4 = 1 };
 

@@ -157,6 +157,15 @@ extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
     case KAFMM_OPT_KAHAN:
       P.kahan = value ? 1 : 0;
       return 0;
+    case KAFMM_OPT_TC_SPLIT:
+      if (value != KAFMM_TC_TF32X3 && value != KAFMM_TC_BF16X3)
+        return fail(P, KAFMM_ERR_ARG, "bad tensor-core split %lld", (long long)value);
+      if (P.tc_split != (int)value) {
+        P.tc_split = (int)value;
+        configure(P);
+        P.have_points = false;
+      }
+      return 0;
     default:
       return fail(P, KAFMM_ERR_ARG, "unknown option %d", key);
   }

@@ -39,6 +39,9 @@ constexpr int OP_DN1 = OP_UP2 + 1;
 constexpr int OP_DN2 = OP_DN1 + 1;
 constexpr int N_OPS = OP_DN2 + 1;
 
+// Split formats of the tensor-core M->L.
+enum { SPLIT_TF32 = 0, SPLIT_BF16 = 1 };
+
 __host__ __device__ inline int m2l_index(int ox, int oy, int oz) {
   return (ox + 3) + 7 * (oy + 3) + 49 * (oz + 3);
 }

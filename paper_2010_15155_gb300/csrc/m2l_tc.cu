@@ -1,12 +1,502 @@
-// M->L on tcgen05 tensor cores (split BF16x3, FP32 accumulation in TMEM).
+// M->L translations on the tcgen05 tensor cores (sm_103a) in split precision (TF32x3 by
+// default, BF16x3 optionally) with FP32 accumulation in tensor memory.
+//
+// The V list of a box B (Sec. II: children of the parent's colleagues not adjacent to B) lies
+// at up to 189 of the 316 offsets o in [-3,3]^3 \ [-1,1]^3; with the pseudo-inverse folded in,
+// each offset is one dense operator T_o (R x R) applied to the check potentials of the source
+// box.  Output-stationary form: a CTA owns 128 check rows x 64 target boxes of one octant
+// class (4 channels each -> N = 256 columns) and accumulates
+//     D[rows, (box, ch)] = sum_o T_o[rows, :] * shift_o(up_check[box + o])[:, ch]
+// over all offsets.  A (the operator) arrives by TMA (128B swizzle, K-major); B (gathered,
+// re-referenced to the target centre and split into bf16 hi/lo) is written to shared memory
+// by producer warps in the same canonical layout.  Each operand is split x = hi + lo in the
+// MMA format (tf32 or bf16) and each product is taken as hi*hi + hi*lo + lo*hi.
+// Each offset is accumulated in a fresh TMEM accumulator and then added into a TMEM sum by
+// the epilogue warps, so no single FP32 accumulation chain spans all offsets.
+//
+// Warp roles (448 threads): 0-3 epilogue (TMEM lane quarters), 4-11 B producers, 12 TMA,
+// 13 TMEM allocation + MMA issue.  Every wait is bounded (2 s of %globaltimer); on expiry the
+// kernel records ST_TIMEOUT and winds down without trapping.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "plan.cuh"
 
 namespace kafmm {
 
-bool tc_supported(Plan& P) { return false; }
+namespace tc {
+
+constexpr int BM = 128, BN = 256, NB = 64, STAGES = 2;
+constexpr int A_BYTES = 16384;              // 128 rows x 128 B per split
+constexpr int B_BYTES = 32768;              // 256 rows x 128 B per split
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int THREADS = 448;
+constexpr int NPROD = 256;
+constexpr int W_TMA = 12, W_MMA = 13;
+
+// Split formats: a 128-byte swizzle row holds BK elements; one MMA consumes MK of them.
+template <int SPLIT>
+struct Fmt;
+template <>
+struct Fmt<SPLIT_TF32> {  // kind::tf32, K = 8 per instruction
+  static constexpr int ES = 4, BK = 32, MK = 8;
+  static constexpr uint32_t AB = 2;
+};
+template <>
+struct Fmt<SPLIT_BF16> {  // kind::f16 with bf16 operands, K = 16 per instruction
+  static constexpr int ES = 2, BK = 64, MK = 16;
+  static constexpr uint32_t AB = 1;
+};
+constexpr uint32_t TMEM_COLS = 512;         // [0,256) accumulator, [256,512) running sum
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 4096;
+
+struct Args {
+  TreeView t;
+  double L;
+  const float* up;        // [nbox][R][4]
+  float* dn;              // [nbox][R][4]
+  const int4* tiles;
+  const int* boxlist;
+  const int32_t* vtab;
+  unsigned* status;
+  int R, nchunk;
+};
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded parity wait; returns false (and flags the status word) after ~2 s.
+__device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity, unsigned* status,
+                                            int* bail) {
+  uint32_t addr = smem_u32(bar);
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (*(volatile int*)bail) return false;
+    if ((it & 63) == 0) {
+      uint64_t t = gtimer();
+      if (t0 == 0) t0 = t;
+      if (t - t0 > 2000000000ull) {
+        atomicOr(status, (unsigned)ST_TIMEOUT);
+        *(volatile int*)bail = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// K-major, 128-byte swizzle UMMA shared-memory descriptor (SM100 format, version 1):
+// start >> 4, LBO = 16 B (unused for swizzled K-major), SBO = 1024 B (8-row groups).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)(16 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;       // descriptor version
+  d |= (uint64_t)2 << 61;       // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D = F32, A/B format (bf16 = 1, tf32 = 2), K-major both, N = 256,
+// M = 128.
+template <int SPLIT>
+__device__ __forceinline__ constexpr uint32_t idesc() {
+  return (1u << 4) | (Fmt<SPLIT>::AB << 7) | (Fmt<SPLIT>::AB << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int SPLIT>
+__device__ __forceinline__ void mma(uint32_t dt, uint64_t a, uint64_t b, uint32_t acc) {
+  if (SPLIT == SPLIT_TF32)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+        "l"(a), "l"(b), "r"(idesc<SPLIT>()), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+        "l"(a), "l"(b), "r"(idesc<SPLIT>()), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+  const uint32_t* r = reinterpret_cast<const uint32_t*>(v);
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+      "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]),
+      "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]),
+      "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_m2l_tc(const __grid_constant__ CUtensorMap tmap, Args a) {
+  constexpr int BK = Fmt<SPLIT>::BK, MK = Fmt<SPLIT>::MK;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty;
+  __shared__ uint32_t tmem_base;
+  __shared__ int nslots, bail;
+  __shared__ int slot_list[216];
+  __shared__ int sbox[NB];
+  __shared__ float sside[NB];
+  __shared__ int slot_any[216];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int4 tile = a.tiles[blockIdx.x];
+  const int cls = tile.z;
+  const int row0 = blockIdx.y * BM;
+  const int R = a.R;
+
+  if (threadIdx.x < NB) {
+    int b = threadIdx.x < tile.y ? a.boxlist[tile.x + threadIdx.x] : -1;
+    sbox[threadIdx.x] = b;
+    sside[threadIdx.x] = b >= 0 ? (float)(a.L / (double)(1 << a.t.level[b])) : 0.f;
+  }
+  for (int k = threadIdx.x; k < 216; k += THREADS) slot_any[k] = 0;
+  if (threadIdx.x == 0) {
+    bail = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], NPROD + 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&acc_full, 1);
+    mbar_init(&acc_empty, 128);
+  }
+  __syncthreads();
+  // active slots: some box of the tile has a V entry there
+  for (int e = threadIdx.x; e < 216 * NB; e += THREADS) {
+    int k = e / NB, j = e % NB;
+    int ox = k % 6 - 2 - (cls & 1), oy = (k / 6) % 6 - 2 - ((cls >> 1) & 1),
+        oz = k / 36 - 2 - ((cls >> 2) & 1);
+    bool inner = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
+    if (!inner && sbox[j] >= 0 && a.vtab[(int64_t)sbox[j] * 216 + k] >= 0) slot_any[k] = 1;
+  }
+  if (warp == W_MMA) {  // TMEM allocation (whole warp)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ns = 0;
+    for (int k = 0; k < 216; ++k)
+      if (slot_any[k]) slot_list[ns++] = k;
+    nslots = ns;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const int ns = nslots;
+  const int nchunk = a.nchunk;
+  const int total = ns * nchunk;
+
+  if (warp == W_TMA) {
+    // ---------------- TMA producer of A (operator rows, hi and lo) ----------------
+    if (lane == 0) {
+      for (int it = 0; it < total; ++it) {
+        int st = it % STAGES;
+        if (it >= STAGES && !wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail)) break;
+        int s = slot_list[it / nchunk], c = it % nchunk;
+        int ox = s % 6 - 2 - (cls & 1), oy = (s / 6) % 6 - 2 - ((cls >> 1) & 1),
+            oz = s / 36 - 2 - ((cls >> 2) & 1);
+        int op = m2l_index(ox, oy, oz);
+        unsigned char* base = smem + st * STAGE_BYTES;
+        uint32_t bar = smem_u32(&full[st]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
+                     "r"(2 * A_BYTES)
+                     : "memory");
+        for (int h = 0; h < 2; ++h) {
+          int y = (op * 2 + h) * R + row0;
+          int x = c * BK;
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], "
+              "[%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(base + h * A_BYTES)),
+              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x), "r"(y), "r"(bar)
+              : "memory");
+        }
+      }
+    }
+  } else if (warp >= 4 && warp < W_TMA) {
+    // ---------------- B producers: gather, re-reference, split, swizzle ----------------
+    constexpr int GROUPS = BK / 8;            // 8-element k groups per chunk
+    constexpr int CPG = 8 * Fmt<SPLIT>::ES / 16;  // 16-byte chunks per group and split
+    const int pt = threadIdx.x - 128;
+    for (int it = 0; it < total; ++it) {
+      int st = it % STAGES;
+      if (it >= STAGES && !wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail)) break;
+      int s = slot_list[it / nchunk], c = it % nchunk;
+      float ox = (float)(s % 6 - 2 - (cls & 1)), oy = (float)((s / 6) % 6 - 2 - ((cls >> 1) & 1)),
+            oz = (float)(s / 36 - 2 - ((cls >> 2) & 1));
+      unsigned char* bhi = smem + st * STAGE_BYTES + 2 * A_BYTES;
+      unsigned char* blo = bhi + B_BYTES;
+      for (int item = pt; item < NB * GROUPS; item += NPROD) {
+        int j = item / GROUPS, g = item % GROUPS;
+        int b = sbox[j];
+        int src = b >= 0 ? a.vtab[(int64_t)b * 216 + s] : -1;
+        float v[4][8];
+        int k0 = c * BK + g * 8;
+        if (src >= 0) {
+          src = entry_box(src);
+          float sx = ox * sside[j], sy = oy * sside[j], sz = oz * sside[j];
+          const float4* p = reinterpret_cast<const float4*>(a.up) + (int64_t)src * R + k0;
+          float4 q[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) q[t] = (k0 + t < R) ? __ldg(p + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            v[0][t] = q[t].x;
+            v[1][t] = q[t].y;
+            v[2][t] = q[t].z;
+            v[3][t] = q[t].w + sx * q[t].x + sy * q[t].y + sz * q[t].z;
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < 8; ++t) v[0][t] = v[1][t] = v[2][t] = v[3][t] = 0.f;
+        }
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          int n = 4 * j + ch;
+          uint32_t hw[8], lw[8];
+          if (SPLIT == SPLIT_TF32) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              float h = tf32_rn(v[ch][t]);
+              hw[t] = __float_as_uint(h);
+              lw[t] = __float_as_uint(tf32_rn(v[ch][t] - h));
+            }
+          } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[ch][2 * t], v[ch][2 * t + 1]);
+              float2 hf = __bfloat1622float2(h2);
+              hw[t] = *reinterpret_cast<uint32_t*>(&h2);
+              lw[t] = pack_bf16(v[ch][2 * t] - hf.x, v[ch][2 * t + 1] - hf.y);
+            }
+          }
+#pragma unroll
+          for (int cc = 0; cc < CPG; ++cc) {
+            int chunk = g * CPG + cc;
+            uint32_t off = (uint32_t)((n >> 3) * 1024 + (n & 7) * 128 + ((chunk ^ (n & 7)) << 4));
+            *reinterpret_cast<uint4*>(bhi + off) =
+                make_uint4(hw[4 * cc], hw[4 * cc + 1], hw[4 * cc + 2], hw[4 * cc + 3]);
+            *reinterpret_cast<uint4*>(blo + off) =
+                make_uint4(lw[4 * cc], lw[4 * cc + 1], lw[4 * cc + 2], lw[4 * cc + 3]);
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      arrive(&full[st]);
+    }
+  } else if (warp == W_MMA) {
+    // ---------------- MMA issue (one thread) ----------------
+    if (lane == 0) {
+      int it = 0;
+      for (int si = 0; si < ns; ++si) {
+        if (si > 0 && !wait_parity(&acc_empty, (si - 1) & 1, a.status, &bail)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        bool ok = true;
+        for (int c = 0; c < nchunk; ++c, ++it) {
+          int st = it % STAGES;
+          if (!wait_parity(&full[st], (it / STAGES) & 1, a.status, &bail)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          uint32_t base = smem_u32(smem + st * STAGE_BYTES);
+          uint32_t ahi = base, alo = base + A_BYTES, bhi = base + 2 * A_BYTES,
+                   blo = base + 2 * A_BYTES + B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < BK / MK; ++kk) {
+            uint32_t ko = kk * 32;  // MK elements = 32 bytes in both formats
+            mma<SPLIT>(tmem, sdesc(ahi + ko), sdesc(bhi + ko), (c > 0 || kk > 0) ? 1u : 0u);
+            mma<SPLIT>(tmem, sdesc(ahi + ko), sdesc(blo + ko), 1u);
+            mma<SPLIT>(tmem, sdesc(alo + ko), sdesc(bhi + ko), 1u);
+          }
+          commit(&empty[st]);
+        }
+        if (!ok) break;
+        commit(&acc_full);
+      }
+    }
+  } else {
+    // ---------------- epilogue: drain each offset into the running sum ----------------
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    float x[32], y[32];
+    for (int si = 0; si < ns; ++si) {
+      if (!wait_parity(&acc_full, si & 1, a.status, &bail)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      for (int q = 0; q < BN / 32; ++q) {
+        tmem_ld32(tmem + lane_base + q * 32, x);
+        if (si > 0) tmem_ld32(tmem + lane_base + 256 + q * 32, y);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (si > 0) {
+#pragma unroll
+          for (int t = 0; t < 32; ++t) x[t] += y[t];
+        }
+        tmem_st32(tmem + lane_base + 256 + q * 32, x);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      arrive(&acc_empty);
+    }
+    // write the tile: row = row0 + lane quarter + lane, columns (box j, channel)
+    int row = row0 + (warp & 3) * 32 + lane;
+    int do_write = __shfl_sync(0xffffffffu, (!*(volatile int*)&bail && ns > 0) ? 1 : 0, 0);
+    if (do_write) {
+      for (int q = 0; q < BN / 32; ++q) {
+        tmem_ld32(tmem + lane_base + 256 + q * 32, x);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (row < R) {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            int b = sbox[q * 8 + jj];
+            if (b >= 0)
+              reinterpret_cast<float4*>(a.dn)[(int64_t)b * R + row] =
+                  make_float4(x[4 * jj], x[4 * jj + 1], x[4 * jj + 2], x[4 * jj + 3]);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == W_MMA) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+}  // namespace tc
+
+bool tc_supported(Plan& P) {
+  if (P.prec != KAFMM_PREC_MIXED || P.C != 4 || P.ml_stokes || !P.opstc.p) return false;
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  cudaGetLastError();
+  return major == 10 && minor == 3;
+}
+
+static int make_tmap(Plan& P, CUtensorMap* map) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return fail(P, KAFMM_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  bool tf32 = P.tc_split == SPLIT_TF32;
+  int es = tf32 ? 4 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)P.Rpad, (cuuint64_t)N_M2L * 2 * P.R};
+  cuuint64_t strides[1] = {(cuuint64_t)P.Rpad * es};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), tc::BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                      2, P.opstc.p, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(P, KAFMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return 0;
+}
 
 int m2l_tc_launch(Plan& P, const int4* tiles, int ntiles, const int* boxlist, cudaStream_t st) {
-  return fail(P, KAFMM_ERR_STATE, "tensor-core M->L is not available");
+  if (!P.tmap_ready) {
+    int rc = make_tmap(P, reinterpret_cast<CUtensorMap*>(P.tmap));
+    if (rc) return rc;
+    cudaError_t e = cudaFuncSetAttribute(tc::k_m2l_tc<SPLIT_TF32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tc::k_m2l_tc<SPLIT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tc::SMEM_BYTES);
+    if (e != cudaSuccess) return cuda_fail(P, e, "cudaFuncSetAttribute(k_m2l_tc)");
+    P.tmap_ready = true;
+  }
+  const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(P.tmap);
+  tc::Args a;
+  a.t = P.tree.view();
+  a.L = P.L;
+  a.up = P.up_check.as<float>();
+  a.dn = P.dn_check.as<float>();
+  a.tiles = tiles;
+  a.boxlist = boxlist;
+  a.vtab = P.tree.vtab.as<int32_t>();
+  a.status = P.tree.status.as<unsigned>();
+  a.R = P.R;
+  dim3 grid(ntiles, (P.R + tc::BM - 1) / tc::BM);
+  if (P.tc_split == SPLIT_TF32) {
+    a.nchunk = P.Rpad / tc::Fmt<SPLIT_TF32>::BK;
+    KL tc::k_m2l_tc<SPLIT_TF32><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
+  } else {
+    a.nchunk = P.Rpad / tc::Fmt<SPLIT_BF16>::BK;
+    KL tc::k_m2l_tc<SPLIT_BF16><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(P, e, "k_m2l_tc launch");
+  return 0;
 }
 
 }  // namespace kafmm

@@ -222,6 +222,24 @@ __global__ void k_round32(const double* in, int64_t n, float* out) {
     out[e] = (float)in[e];
 }
 
+// Split into tf32 hi + lo (stored as fp32) with K padded to Rpad: out[(op*2 + h)][i][Rpad].
+__global__ void k_split_tf32(const double* in, int R, int Rpad, int64_t nops, float* out) {
+  int64_t total = nops * R * (int64_t)Rpad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t op = e / ((int64_t)R * Rpad);
+    int64_t rem = e % ((int64_t)R * Rpad);
+    int i = (int)(rem / Rpad), j = (int)(rem % Rpad);
+    float v = j < R ? (float)in[(op * R + i) * R + j] : 0.f;
+    uint32_t hb, lb;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
+    float hi = __uint_as_float(hb);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(v - hi));
+    out[((op * 2 + 0) * R + i) * Rpad + j] = hi;
+    out[((op * 2 + 1) * R + i) * Rpad + j] = __uint_as_float(lb);
+  }
+}
+
 // Split into bf16 hi + lo with K padded to Rpad: out[(op*2 + h)][i][Rpad].
 __global__ void k_split_bf16(const double* in, int R, int Rpad, int64_t nops, __nv_bfloat16* out) {
   int64_t total = nops * R * (int64_t)Rpad;
@@ -348,10 +366,17 @@ int build_operators(Plan& P) {
   } else {
     CK(P.ops32.reserve(sizeof(float) * RR * N_OPS));
     KL k_round32<<<2048, 256, 0, st>>>(O, (int64_t)RR * N_OPS, P.ops32.as<float>());
-    if (P.prec == KAFMM_PREC_MIXED) {
+    if (P.prec == KAFMM_PREC_MIXED && P.C == 4) {
       P.Rpad = (R + 63) / 64 * 64;
-      CK(P.opsbf.reserve(sizeof(__nv_bfloat16) * 2 * (size_t)R * P.Rpad * N_M2L));
-      KL k_split_bf16<<<2048, 256, 0, st>>>(O + RR * OP_M2L, R, P.Rpad, N_M2L, P.opsbf.as<__nv_bfloat16>());
+      P.tmap_ready = false;
+      if (P.tc_split == SPLIT_TF32) {
+        CK(P.opstc.reserve(sizeof(float) * 2 * (size_t)R * P.Rpad * N_M2L));
+        KL k_split_tf32<<<2048, 256, 0, st>>>(O + RR * OP_M2L, R, P.Rpad, N_M2L, P.opstc.as<float>());
+      } else {
+        CK(P.opstc.reserve(sizeof(__nv_bfloat16) * 2 * (size_t)R * P.Rpad * N_M2L));
+        KL k_split_bf16<<<2048, 256, 0, st>>>(O + RR * OP_M2L, R, P.Rpad, N_M2L,
+                                              P.opstc.as<__nv_bfloat16>());
+      }
     }
   }
   CK(cudaGetLastError());

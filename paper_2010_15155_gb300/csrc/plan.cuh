@@ -72,8 +72,11 @@ struct Plan {
   int R = 0;           // n * D
   bool ops_ready = false;
   // operators: [N_OPS][R][R] row-major (rows = target check rows, cols = source rows)
-  DevBuf ops64, ops32, opsbf;       // opsbf: [N_OPS][2][R][Rpad] split bf16 (hi, lo)
+  DevBuf ops64, ops32, opstc;       // opstc: [N_M2L][2][R][Rpad] split (hi, lo), tf32 or bf16
   int Rpad = 0;                     // R rounded up to the tensor-core K granularity
+  int tc_split = SPLIT_TF32;        // split format of the tensor-core M->L
+  alignas(64) unsigned char tmap[128];  // TMA descriptor of opstc
+  bool tmap_ready = false;
   DevBuf unit64, unit32;            // unit surface [n][3]
   DevBuf tm2l64, tm2l32;            // periodic far-image operator [R][R]
   // tree + data

@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(HERE, "libkafmm.so")
 LAPLACE, STOKESLET, RPY, STOKES_DL = 0, 1, 2, 3
 BC_OPEN, BC_PXYZ = 0, 3
 F32, F64 = 0, 1
-OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN = 1, 2, 3, 4, 5
+OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN, OPT_TC_SPLIT = 1, 2, 3, 4, 5, 6
+TC_TF32X3, TC_BF16X3 = 0, 1
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 ML_G, ML_L4 = 0, 1
 KDIM = {LAPLACE: (1, 1), STOKESLET: (3, 3), RPY: (4, 6), STOKES_DL: (9, 4)}
@@ -186,7 +187,8 @@ class Plan:
     """One evaluator plan: ``Plan(STOKESLET, p=10, q=128).set_points(y).eval(f)``."""
 
     def __init__(self, kernel, p, q, bc=BC_OPEN, precision=PREC_MIXED, variant=ML_L4,
-                 near_only=False, kahan=False, stream=None, origin=(0.0, 0.0, 0.0), L=1.0):
+                 near_only=False, kahan=False, stream=None, origin=(0.0, 0.0, 0.0), L=1.0,
+                 tc_split=TC_TF32X3):
         self.kernel = kernel
         self.ks, self.kt = KDIM[kernel]
         self.h = kafmm_plan(kernel, bc, p, q)
@@ -194,6 +196,7 @@ class Plan:
         kafmm_set_option(self.h, OPT_ML_VARIANT, variant)
         kafmm_set_option(self.h, OPT_NEAR_ONLY, int(near_only))
         kafmm_set_option(self.h, OPT_KAHAN, int(kahan))
+        kafmm_set_option(self.h, OPT_TC_SPLIT, tc_split)
         if stream is not None:
             kafmm_set_option(self.h, OPT_STREAM, int(stream))
         kafmm_set_domain(self.h, origin, L)

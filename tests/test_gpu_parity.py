@@ -169,3 +169,19 @@ def test_errors_are_reported_not_trapped():
         plan.eval(torch.zeros((2, 3), device="cuda"))
     assert e.value.code == -6
     plan.close()
+
+
+@pytest.mark.parametrize("n,p,q", [(20000, 6, 64), (262144, 10, 128)])
+def test_mixed_tensor_core_form_matches_fp64_form(n, p, q):
+    """Split-BF16x3 tcgen05 M->L (mixed form) vs the plain FP64 GPU form: rel L2 <= 1e-5."""
+    pts, f = W.stokes_uniform(n, seed=1, dtype=np.float32)
+    out = {}
+    for prec in (K.PREC_FP64, K.PREC_MIXED):
+        dt = torch.float64 if prec == K.PREC_FP64 else torch.float32
+        plan = K.Plan(K.STOKESLET, p=p, q=q, precision=prec, variant=K.ML_L4)
+        plan.set_points(torch.from_numpy(pts).to(dt).cuda())
+        out[prec] = plan.eval(torch.from_numpy(f).to(dt).cuda()).double().cpu().numpy()
+        if prec == K.PREC_MIXED:
+            assert K.kafmm_get_counters(plan.h)["tensor_core_m2l"] == 1
+        plan.close()
+    assert D.rel_l2(out[K.PREC_MIXED], out[K.PREC_FP64]) < 1e-5

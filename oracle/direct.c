@@ -251,3 +251,120 @@ void orc_rpy_overlap_correction(const double* x, const double* at, int64_t nt,
     for (int i = 0; i < 3; ++i) g[3 * a + i] += u[i];
   }
 }
+
+/* ---------------------------------------------------------------------------------------
+ * Triply periodic sums by Ewald summation (periodic cube of side L), the k = 0 Fourier mode
+ * removed -- the zero-mean field of a neutral (sum q = 0) or force-free (sum f = 0) system.
+ * Used for the periodic boundary condition of Sec. III.B (the paper's periodisation builds on
+ * a precomputed far-image operator; this is its plain definition).
+ *
+ * Laplace 1/(4 pi r):  G_per(r) = sum_n erfc(xi |r+nL|)/(4 pi |r+nL|) - 1/(4 xi^2 V)
+ *                                 + (1/V) sum_{k != 0} exp(-k^2/4xi^2)/k^2 cos(k.r)
+ * Stokeslet (Hasimoto split, weight (1 + k^2/4xi^2) exp(-k^2/4xi^2)):
+ *   real part  (1/8pi)[ I (erfc(xi r)/r - 2xi/sqrt(pi) e^{-xi^2 r^2})
+ *                       + rr/r^2 (erfc(xi r)/r + 2xi/sqrt(pi) e^{-xi^2 r^2}) ]
+ *   Fourier    (1/V) sum_{k != 0} (I - kk/k^2)/k^2 (1 + k^2/4xi^2) e^{-k^2/4xi^2} cos(k.r)
+ * k = 2 pi m / L, real images n in [-nreal, nreal]^3, m in [-nfour, nfour]^3.  At r = 0 the
+ * n = 0 real-space term is replaced by its regular limit (the point's own images only).
+ * Differences r must lie in (-L, L)^3 (points inside one cell).
+ * ------------------------------------------------------------------------------------- */
+static void ewald_lap_block(const double r[3], double L, double xi, int nreal, int nfour,
+                           double* out) {
+  double V = L * L * L, acc = -1.0 / (4.0 * xi * xi * V);
+  for (int i = -nreal; i <= nreal; ++i)
+    for (int j = -nreal; j <= nreal; ++j)
+      for (int k = -nreal; k <= nreal; ++k) {
+        double d[3] = {r[0] + i * L, r[1] + j * L, r[2] + k * L};
+        double rn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (rn == 0.0)
+          acc += -xi / (2.0 * PI * sqrt(PI));  /* lim (erfc(xi r) - 1)/(4 pi r) */
+        else
+          acc += erfc(xi * rn) / (4.0 * PI * rn);
+      }
+  for (int a = -nfour; a <= nfour; ++a)
+    for (int b = -nfour; b <= nfour; ++b)
+      for (int c = -nfour; c <= nfour; ++c) {
+        if (a == 0 && b == 0 && c == 0) continue;
+        double kv[3] = {2.0 * PI * a / L, 2.0 * PI * b / L, 2.0 * PI * c / L};
+        double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+        acc += exp(-k2 / (4.0 * xi * xi)) / k2 * cos(kv[0] * r[0] + kv[1] * r[1] + kv[2] * r[2]) / V;
+      }
+  *out = acc;
+}
+
+static void ewald_stk_block(const double r[3], double L, double xi, int nreal, int nfour,
+                            double m[9]) {
+  double V = L * L * L;
+  for (int q = 0; q < 9; ++q) m[q] = 0.0;
+  double sp = 2.0 * xi / sqrt(PI);
+  for (int i = -nreal; i <= nreal; ++i)
+    for (int j = -nreal; j <= nreal; ++j)
+      for (int k = -nreal; k <= nreal; ++k) {
+        double d[3] = {r[0] + i * L, r[1] + j * L, r[2] + k * L};
+        double rr = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double rn = sqrt(rr);
+        if (rn == 0.0) {  /* lim (g_R - G) at r = 0: (1/8pi)(-4 xi/sqrt(pi)) I */
+          for (int q = 0; q < 3; ++q) m[4 * q] += -2.0 * sp / (8.0 * PI);
+          continue;
+        }
+        double e = exp(-xi * xi * rr), ec = erfc(xi * rn);
+        double A = (ec / rn - sp * e) / (8.0 * PI), B = (ec / rn + sp * e) / (8.0 * PI) / rr;
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) m[3 * p + q] += (p == q ? A : 0.0) + B * d[p] * d[q];
+      }
+  for (int a = -nfour; a <= nfour; ++a)
+    for (int b = -nfour; b <= nfour; ++b)
+      for (int c = -nfour; c <= nfour; ++c) {
+        if (a == 0 && b == 0 && c == 0) continue;
+        double kv[3] = {2.0 * PI * a / L, 2.0 * PI * b / L, 2.0 * PI * c / L};
+        double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+        double w = (1.0 + k2 / (4.0 * xi * xi)) * exp(-k2 / (4.0 * xi * xi)) / k2 / V *
+                   cos(kv[0] * r[0] + kv[1] * r[1] + kv[2] * r[2]);
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) m[3 * p + q] += w * ((p == q ? 1.0 : 0.0) - kv[p] * kv[q] / k2);
+      }
+}
+
+/* g += sum_b K_per(x_a - y_b) s_b; kernel 0 = Laplace (k_s = k_t = 1), 1 = Stokeslet (3). */
+void orc_ewald_sum(int kernel, const double* x, int64_t nt, const double* y, int64_t ns,
+                   const double* s, double L, double xi, int nreal, int nfour, double* g) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t a = 0; a < nt; ++a) {
+    double acc[3] = {0, 0, 0}, m[9];
+    for (int64_t b = 0; b < ns; ++b) {
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1], x[3 * a + 2] - y[3 * b + 2]};
+      if (kernel == 0) {
+        ewald_lap_block(r, L, xi, nreal, nfour, m);
+        acc[0] += m[0] * s[b];
+      } else {
+        ewald_stk_block(r, L, xi, nreal, nfour, m);
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) acc[p] += m[3 * p + q] * s[3 * b + q];
+      }
+    }
+    int kt = kernel == 0 ? 1 : 3;
+    for (int p = 0; p < kt; ++p) g[kt * a + p] += acc[p];
+  }
+}
+
+/* Kernel matrix of the periodic Green's function: out[(a, p), (b, q)], row-major
+ * [nt * kt][ns * kt]. */
+void orc_ewald_matrix(int kernel, const double* x, int64_t nt, const double* y, int64_t ns, double L,
+                      double xi, int nreal, int nfour, double* out) {
+  int kt = kernel == 0 ? 1 : 3;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t a = 0; a < nt; ++a) {
+    double m[9];
+    for (int64_t b = 0; b < ns; ++b) {
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1], x[3 * a + 2] - y[3 * b + 2]};
+      if (kernel == 0) {
+        ewald_lap_block(r, L, xi, nreal, nfour, m);
+        out[a * ns + b] = m[0];
+      } else {
+        ewald_stk_block(r, L, xi, nreal, nfour, m);
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) out[(3 * a + p) * (3 * ns) + 3 * b + q] = m[3 * p + q];
+      }
+    }
+  }
+}

@@ -29,7 +29,13 @@ Readings of points the paper leaves open:
   a representation from reference c to c' adds (c - c') . q_{1:3} to channel 4.
 * Periodic (``bc='pxyz'``): the tree covers the source images with shift in {-1,0,1}^3 (lists
   with wrap, ``oracle.tree``); all farther images enter through one operator T_M2L applied to
-  the root's multipole density and added to the root's downward check potential.
+  the root's multipole density and added to the root's downward check potential.  For the
+  Laplace kernel the zero-mean (Ewald) periodic Green's function is not harmonic
+  (lap G_per = 1/V), so the result depends on the trace of the second charge moment,
+  sum q |y - c|^2, which equivalent charges do not carry; the constant
+  (sum_j q_j |y_j - c|^2 - sum_k M_k |ue_k - c|^2) / (6 V) is added back at the end
+  (c: root centre, M: the root's equivalent charges).  The Stokeslet needs no such step: a
+  uniform body force is balanced by pressure alone.
 """
 from __future__ import annotations
 
@@ -241,6 +247,12 @@ class KAFMM:
 
         # leaves: L->T, M->T (W), S->T (U)
         g = np.zeros((len(x), self.kt))
+        if per and self.problem == "laplace" and not near_only:
+            c0 = T.centre(0)
+            ue0 = self._surf("ue", c0, 0)
+            second = np.sum(s[:, 0] * np.sum((src - c0) ** 2, axis=1))
+            second_eq = np.sum(M[0][:, 0] * np.sum((ue0 - c0) ** 2, axis=1))
+            g += (second - second_eq) / (6.0 * self.L ** 3)
         for b in T.leaves():
             ti = T.trg_idx[b]
             if len(ti) == 0:

@@ -256,7 +256,41 @@ extern "C" int kafmm_rpy_velocity(kafmm_plan_t pl, const void* s, const void* a,
   PLAN_CHECK(pl);
   if (P.kernel != KAFMM_RPY) return fail(P, KAFMM_ERR_ARG, "kafmm_rpy_velocity needs the RPY kernel");
   if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "kafmm_rpy_velocity before kafmm_set_points");
-  return rpy_velocity(P, s, a, g, ua, dtype);
+  if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || (P.tree.n_src > 0 && !s) ||
+      (P.tree.n_trg > 0 && (!a || !g || !ua)))
+    return fail(P, KAFMM_ERR_ARG, "kafmm_rpy_velocity: bad arguments");
+  size_t es = dtype == KAFMM_F64 ? 8 : 4;
+  int64_t ns = P.tree.n_src, nt = P.tree.n_trg;
+  DevBuf bs, ba, bg, bu;
+  const void *sd = s, *ad = a, *gd = g;
+  void* ud = ua;
+  bool host_out = nt > 0 && is_host_ptr(ua);
+  if (ns > 0 && is_host_ptr(s)) {
+    CKP(bs.reserve(es * 4 * ns));
+    CKP(cudaMemcpyAsync(bs.p, s, es * 4 * ns, cudaMemcpyHostToDevice, P.stream));
+    sd = bs.p;
+  }
+  if (nt > 0 && is_host_ptr(a)) {
+    CKP(ba.reserve(es * nt));
+    CKP(cudaMemcpyAsync(ba.p, a, es * nt, cudaMemcpyHostToDevice, P.stream));
+    ad = ba.p;
+  }
+  if (nt > 0 && is_host_ptr(g)) {
+    CKP(bg.reserve(es * 6 * nt));
+    CKP(cudaMemcpyAsync(bg.p, g, es * 6 * nt, cudaMemcpyHostToDevice, P.stream));
+    gd = bg.p;
+  }
+  if (host_out) {
+    CKP(bu.reserve(es * 3 * nt));
+    ud = bu.p;
+  }
+  int rc = rpy_velocity(P, sd, ad, gd, ud, dtype);
+  if (rc) return rc;
+  if (host_out) {
+    CKP(cudaMemcpyAsync(ua, ud, es * 3 * nt, cudaMemcpyDeviceToHost, P.stream));
+    CKP(cudaStreamSynchronize(P.stream));
+  }
+  return 0;
 }
 
 extern "C" int kafmm_tree_info(kafmm_plan_t pl, int64_t* info, int n) {

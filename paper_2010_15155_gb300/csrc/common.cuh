@@ -22,8 +22,11 @@ constexpr double PI = 3.14159265358979323846;
 // Surface radii in units of the box half-width (Ying, Biros & Zorin 2004): upward
 // equivalent / check, downward equivalent / check.
 constexpr double ALPHA_UE = 1.05, ALPHA_UC = 2.95, ALPHA_DE = 2.95, ALPHA_DC = 1.05;
-// Relative singular-value cutoff of the check-to-equivalent pseudo-inverses.
-constexpr double PINV_RCOND = 1e-9;
+// Relative singular-value cutoffs of the check-to-equivalent pseudo-inverses: 1e-9 for the
+// FP64 form (lowest FP64 error against the direct sum for p = 8..12); 1e-7 (about twice the
+// FP32 unit roundoff) for the FP32 and mixed forms, where a smaller cutoff only amplifies
+// rounding -- for the Stokeslet the normal density is an exact null mode of the single layer.
+constexpr double PINV_RCOND_FP64 = 1e-9, PINV_RCOND_FP32 = 1e-7;
 
 // Operator slots: 343 M->L offsets (ox,oy,oz) in [-3,3]^3 (the 27 inner ones unused), then
 // 8 M->M octants, 8 L->L octants, and the upward / downward pseudo-inverses in factored form

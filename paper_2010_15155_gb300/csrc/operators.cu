@@ -290,7 +290,7 @@ static int pinv64(Plan& P, const double* K, double* out1, double* out2, double* 
   if (sweeps >= 80 && last > 1e-11f)
     return fail(P, KAFMM_ERR_CUDA, "Jacobi SVD did not converge (off-orthogonality %.3g)", last);
   KL k_row_norms<<<R, 256, 0, st>>>(At, R, w);
-  KL k_pinv_weights<<<1, 256, 0, st>>>(w, R, PINV_RCOND);
+  KL k_pinv_weights<<<1, 256, 0, st>>>(w, R, P.fp64() ? PINV_RCOND_FP64 : PINV_RCOND_FP32);
   // rows of At are the columns of W = K V; pinv = V diag(w) W^T
   KL k_scale_rows<<<512, 256, 0, st>>>(At, w, R, out1);
   KL k_transpose<<<512, 256, 0, st>>>(Vt, R, out2);

@@ -1,11 +1,223 @@
-// RPY sphere velocities: assembly u + a^2/6 lap u (Eq. RPYtrgvel) and the overlap
-// post-processing of Sec. II.B.
+// RPY sphere velocities (Sec. II.B): target assembly u_a = u + a^2/6 lap u (Eq. RPYtrgvel)
+// and the post-processing the paper prescribes for overlapping spheres.  The kernel sum
+// uses the far form G + b^2/6 lap G for every pair; for pairs in contact (r <= a_i + b_j) the
+// far form is replaced by the overlap-regularised pair mobility of unequal spheres (the form
+// of Zuk et al. 2014, cited by the paper):
+//   |a-b| < r <= a+b :  M = [A I + B rr/r^2] / (6 pi a b),
+//        A = (16 r^3 (a+b) - ((a-b)^2 + 3 r^2)^2) / (32 r^3),  B = 3 ((a-b)^2 - r^2)^2 / (32 r^3)
+//   r <= |a-b|       :  M = I / (6 pi max(a, b))
+// i.e. the pass adds (M_overlap - M_far) f for those pairs (M_far = 0 at r = 0, as the sum
+// skips coincident pairs).  Neighbours come from a dense cell table at a grid level whose cell
+// side is at least a_max + b_max, so every contact partner lies in the 27 surrounding cells.
+#include <algorithm>
+#include <cstring>
+
+#include "physics.cuh"
 #include "plan.cuh"
 
 namespace kafmm {
 
+namespace {
+
+template <class Tin, class T>
+__global__ void k_gather_scalar(const Tin* __restrict__ in, const uint32_t* __restrict__ perm, int64_t n,
+                                T* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (T)in[perm[i]];
+}
+
+template <class Tin, class T>
+__global__ void k_gather_fb(const Tin* __restrict__ s, const uint32_t* __restrict__ perm, int64_t n,
+                            typename V4<T>::type* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const Tin* p = s + 4 * (int64_t)perm[i];
+    typename V4<T>::type v;
+    v.x = (T)p[0];
+    v.y = (T)p[1];
+    v.z = (T)p[2];
+    v.w = (T)p[3];
+    out[i] = v;
+  }
+}
+
+template <class T>
+__global__ void k_max_radius(const T* __restrict__ a, int64_t n, const typename V4<T>::type* __restrict__ fb,
+                             int64_t ns, unsigned* out) {
+  float ma = 0.f, mb = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    ma = fmaxf(ma, (float)a[i]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x)
+    mb = fmaxf(mb, (float)fb[i].w);
+  atomicMax(out, __float_as_uint(ma));  // non-negative floats order as unsigned ints
+  atomicMax(out + 1, __float_as_uint(mb));
+}
+
+// cell table: for the cells (Morton code at level g) holding sources, [begin, end) in sorted order
+__global__ void k_cell_table(const uint64_t* __restrict__ key, int64_t n, int shift, int* __restrict__ beg,
+                             int* __restrict__ end) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t c = key[i] >> shift;
+    if (i == 0 || (key[i - 1] >> shift) != c) beg[c] = (int)i;
+    if (i == n - 1 || (key[i + 1] >> shift) != c) end[c] = (int)(i + 1);
+  }
+}
+
+// Pair mobility difference (overlap form minus far form) applied to f, accumulated in acc.
+template <class T>
+__device__ inline void overlap_delta(T r0, T r1, T r2, T ai, T aj, T f0, T f1, T f2, T* acc) {
+  T rr = r0 * r0 + r1 * r1 + r2 * r2;
+  T rn = sqrt(rr);
+  T s = ai + aj, d = fabs(ai - aj);
+  if (rn > s) return;
+  const T pi = T(PI);
+  T A, B;
+  if (rn > d) {
+    T r3 = rr * rn, t = d * d + T(3) * rr, e = d * d - rr;
+    A = (T(16) * r3 * s - t * t) / (T(32) * r3) / (T(6) * pi * ai * aj);
+    B = T(3) * e * e / (T(32) * r3) / (T(6) * pi * ai * aj);
+  } else {
+    A = T(1) / (T(6) * pi * (ai > aj ? ai : aj));
+    B = T(0);
+  }
+  T rf = r0 * f0 + r1 * f1 + r2 * f2;
+  T bo = rr > T(0) ? B * rf / rr : T(0);
+  T u0 = A * f0 + bo * r0, u1 = A * f1 + bo * r1, u2 = A * f2 + bo * r2;
+  if (rr > T(0)) {  // subtract the far form (what the kernel sum already added)
+    T c = ai * ai + aj * aj;
+    T Af = (T(1) + c / (T(3) * rr)) / (T(8) * pi * rn);
+    T Bf = (T(1) - c / rr) / (T(8) * pi * rn) * rf / rr;
+    u0 -= Af * f0 + Bf * r0;
+    u1 -= Af * f1 + Bf * r1;
+    u2 -= Af * f2 + Bf * r2;
+  }
+  acc[0] += u0;
+  acc[1] += u1;
+  acc[2] += u2;
+}
+
+template <class T, class Tio>
+__global__ void k_rpy_velocity(const typename V4<T>::type* __restrict__ spos,
+                               const typename V4<T>::type* __restrict__ sfb,
+                               const typename V4<T>::type* __restrict__ tpos, const T* __restrict__ ta,
+                               const uint64_t* __restrict__ tkey, const uint32_t* __restrict__ tperm,
+                               int64_t nt, const int* __restrict__ cbeg, const int* __restrict__ cend, int g,
+                               int periodic, double L, int same, const Tio* __restrict__ gin,
+                               Tio* __restrict__ ua) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    typename V4<T>::type x = tpos[i];
+    T ai = ta[i];
+    uint64_t ck = tkey[i] >> (3 * (MAX_LEVEL - g));
+    int cx = (int)compact3(ck), cy = (int)compact3(ck >> 1), cz = (int)compact3(ck >> 2);
+    int n = 1 << g;
+    T acc[3] = {0, 0, 0};
+    for (int d = 0; d < 27; ++d) {
+      int qx = cx + d % 3 - 1, qy = cy + (d / 3) % 3 - 1, qz = cz + d / 9 - 1;
+      int sx = 0, sy = 0, sz = 0;
+      if (qx < 0 || qx >= n || qy < 0 || qy >= n || qz < 0 || qz >= n) {
+        if (!periodic) continue;
+        sx = qx < 0 ? -1 : (qx >= n ? 1 : 0);
+        sy = qy < 0 ? -1 : (qy >= n ? 1 : 0);
+        sz = qz < 0 ? -1 : (qz >= n ? 1 : 0);
+        qx -= sx * n;
+        qy -= sy * n;
+        qz -= sz * n;
+      }
+      uint64_t c = morton3((uint32_t)qx, (uint32_t)qy, (uint32_t)qz);
+      int b0 = cbeg[c], b1 = cend[c];
+      T ox = (T)(sx * L), oy = (T)(sy * L), oz = (T)(sz * L);
+      for (int j = b0; j < b1; ++j) {
+        if (same && j == (int)i && sx == 0 && sy == 0 && sz == 0) continue;
+        typename V4<T>::type y = spos[j], fb = sfb[j];
+        overlap_delta<T>(x.x - (y.x + ox), x.y - (y.y + oy), x.z - (y.z + oz), ai, fb.w, fb.x, fb.y,
+                         fb.z, acc);
+      }
+    }
+    int64_t o = tperm[i];
+    const Tio* gg = gin + 6 * o;
+    T c6 = ai * ai / T(6);
+    for (int k = 0; k < 3; ++k) ua[3 * o + k] = (Tio)((T)gg[k] + c6 * (T)gg[3 + k] + acc[k]);
+  }
+}
+
+int grid_for(int64_t n, int threads, int maxb = 152 * 16) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > maxb) b = maxb;
+  return (int)b;
+}
+
+#define CK(call)                                           \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(P, e_, #call); \
+  } while (0)
+
+template <class T>
+int run(Plan& P, const void* s, const void* a, const void* g, void* ua, int dtype) {
+  using T4 = typename V4<T>::type;
+  Tree& Tr = P.tree;
+  cudaStream_t st = P.stream;
+  int64_t ns = Tr.n_src, nt = Tr.n_trg;
+  const uint32_t* sperm = Tr.src_perm.as<uint32_t>();
+  const uint32_t* tperm = Tr.same ? sperm : Tr.trg_perm.as<uint32_t>();
+  const uint64_t* skey = Tr.src_key.as<uint64_t>();
+  const uint64_t* tkey = Tr.same ? skey : Tr.trg_key.as<uint64_t>();
+  DevBuf fb, ta, stat, cb, ce;
+  CK(fb.reserve(sizeof(T4) * (ns + 1)));
+  CK(ta.reserve(sizeof(T) * (nt + 1)));
+  CK(stat.reserve(64));
+  CK(cudaMemsetAsync(stat.p, 0, 64, st));
+  if (dtype == KAFMM_F64) {
+    KL k_gather_fb<double, T><<<grid_for(ns, 256), 256, 0, st>>>((const double*)s, sperm, ns, fb.as<T4>());
+    KL k_gather_scalar<double, T><<<grid_for(nt, 256), 256, 0, st>>>((const double*)a, tperm, nt, ta.as<T>());
+  } else {
+    KL k_gather_fb<float, T><<<grid_for(ns, 256), 256, 0, st>>>((const float*)s, sperm, ns, fb.as<T4>());
+    KL k_gather_scalar<float, T><<<grid_for(nt, 256), 256, 0, st>>>((const float*)a, tperm, nt, ta.as<T>());
+  }
+  KL k_max_radius<T><<<grid_for(std::max(ns, nt), 256), 256, 0, st>>>(ta.as<T>(), nt, fb.as<T4>(), ns,
+                                                                       stat.as<unsigned>());
+  unsigned h[2];
+  CK(cudaMemcpyAsync(h, stat.p, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  float amax, bmax;
+  memcpy(&amax, &h[0], 4);
+  memcpy(&bmax, &h[1], 4);
+  double reach = ((double)amax + (double)bmax) * (1.0 + 1e-6) / P.L;
+  int lev = 0;
+  while (lev < 8 && reach > 0 && 1.0 / (double)(1 << (lev + 1)) >= reach) ++lev;
+  if (reach <= 0) lev = 8;
+  int64_t ncell = 1ll << (3 * lev);
+  CK(cb.reserve(sizeof(int) * ncell));
+  CK(ce.reserve(sizeof(int) * ncell));
+  CK(cudaMemsetAsync(cb.p, 0, sizeof(int) * ncell, st));
+  CK(cudaMemsetAsync(ce.p, 0, sizeof(int) * ncell, st));
+  if (ns > 0)
+    KL k_cell_table<<<grid_for(ns, 256), 256, 0, st>>>(skey, ns, 3 * (MAX_LEVEL - lev), cb.as<int>(), ce.as<int>());
+  const T4* spos = Tr.src_pos.as<T4>();
+  const T4* tpos = Tr.same ? spos : Tr.trg_pos.as<T4>();
+  if (nt > 0) {
+    if (dtype == KAFMM_F64)
+      KL k_rpy_velocity<T, double><<<grid_for(nt, 128), 128, 0, st>>>(
+          spos, fb.as<T4>(), tpos, ta.as<T>(), tkey, tperm, nt, cb.as<int>(), ce.as<int>(), lev,
+          P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const double*)g, (double*)ua);
+    else
+      KL k_rpy_velocity<T, float><<<grid_for(nt, 128), 128, 0, st>>>(
+          spos, fb.as<T4>(), tpos, ta.as<T>(), tkey, tperm, nt, cb.as<int>(), ce.as<int>(), lev,
+          P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const float*)g, (float*)ua);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return 0;
+}
+
+}  // namespace
+
 int rpy_velocity(Plan& P, const void* s, const void* a, const void* g, void* ua, int dtype) {
-  return fail(P, KAFMM_ERR_STATE, "kafmm_rpy_velocity is not available in this build");
+  return P.fp64() ? run<double>(P, s, a, g, ua, dtype) : run<float>(P, s, a, g, ua, dtype);
 }
 
 }  // namespace kafmm

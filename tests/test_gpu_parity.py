@@ -148,15 +148,19 @@ def test_fp64_gpu_kafmm_adaptive_tree_matches_cpu_kafmm():
 @pytest.mark.parametrize("kernel,variant", [("laplace", K.ML_L4), ("stokeslet", K.ML_L4),
                                             ("stokeslet", K.ML_G), ("rpy", K.ML_L4)])
 def test_fp32_form_matches_fp64_form(kernel, variant):
+    """The FP32 form (pseudo-inverse cutoff 1e-7) is as accurate as the FP64 form (cutoff
+    1e-9) against the direct sum, up to 1e-5."""
     pts, s = _inputs(kernel, 20000, seed=13, dtype=np.float32)
-    out = {}
+    ref = D.direct(kernel, pts, pts, s)
+    err = {}
     for prec in (K.PREC_FP64, K.PREC_FP32):
         dt = torch.float64 if prec == K.PREC_FP64 else torch.float32
         plan = K.Plan(KERN[kernel], p=6, q=64, precision=prec, variant=variant)
         plan.set_points(torch.from_numpy(pts).to(dt).cuda())
-        out[prec] = plan.eval(torch.from_numpy(s).to(dt).cuda()).double().cpu().numpy()
+        g = plan.eval(torch.from_numpy(s).to(dt).cuda()).double().cpu().numpy()
         plan.close()
-    assert D.rel_l2(out[K.PREC_FP32], out[K.PREC_FP64]) < 1e-5
+        err[prec] = D.rel_l2(g, ref)
+    assert err[K.PREC_FP32] < err[K.PREC_FP64] + 1e-5, err
 
 
 def test_errors_are_reported_not_trapped():
@@ -185,3 +189,29 @@ def test_mixed_tensor_core_form_matches_fp64_form(n, p, q):
             assert K.kafmm_get_counters(plan.h)["tensor_core_m2l"] == 1
         plan.close()
     assert D.rel_l2(out[K.PREC_MIXED], out[K.PREC_FP64]) < 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [(K.PREC_FP64, 1e-6), (K.PREC_FP32, 2e-5)])
+def test_rpy_sphere_velocities_with_overlap_match_brute_force(prec, tol):
+    """kafmm_eval ([u, lap u]) + kafmm_rpy_velocity (assembly u + a^2/6 lap u and the overlap
+    pass) against the oracle's brute-force pair mobility over all pairs (Sec. II.B)."""
+    pts, f, a = W.rpy_clusters(3000, seed=6, n_clusters=4, sigma=0.05, a_lo=0.004, a_hi=0.012,
+                               dtype=np.float64)
+    fb = np.concatenate([f, a[:, None]], axis=1)
+    ref = D.rpy_velocity(pts, a, pts, fb, same_set=True)
+    dt = torch.float64 if prec == K.PREC_FP64 else torch.float32
+    if dt == torch.float32:  # keep every point below 1 after rounding to FP32
+        pts = np.minimum(pts.astype(np.float32), np.float32(1) - np.float32(2 ** -24)).astype(np.float64)
+        fb = np.concatenate([f, a[:, None]], axis=1)
+        ref = D.rpy_velocity(pts, a, pts, fb, same_set=True)
+    plan = K.Plan(K.RPY, p=8, q=48, precision=prec, variant=K.ML_L4)
+    plan.set_points(torch.from_numpy(pts).to(dt).cuda())
+    s = torch.from_numpy(fb).to(dt).cuda()
+    g = plan.eval(s)
+    ua = torch.empty((len(pts), 3), dtype=dt, device="cuda")
+    K.kafmm_rpy_velocity(plan.h, s, torch.from_numpy(a).to(dt).cuda(), g, ua,
+                         K.F64 if dt == torch.float64 else K.F32)
+    plan.close()
+    nover = np.sum(np.linalg.norm(pts[:, None] - pts[None], axis=2) < a[:, None] + a[None]) - len(pts)
+    assert nover > 1000  # the case really exercises the overlap pass
+    assert D.rel_l2(ua.double().cpu().numpy(), ref) < tol

@@ -165,6 +165,15 @@ int kafmm_phase_times(kafmm_plan_t plan, double* t, int n);
  * tcgen05 tensor cores (0/1), 3 launches of set_points + eval. */
 int kafmm_get_counters(kafmm_plan_t plan, int64_t* c, int n);
 
+/* Copies one precomputed translation operator to the host as FP64 (row-major R x R, R = the
+ * ML rows of the plan: 6(p-1)^2+2, times 3 for the Stokeslet table).  slot: 0..342 M->L by
+ * offset (ox+3) + 7(oy+3) + 49(oz+3); 343..350 M->M by child octant; 351..358 L->L by child
+ * octant; 359/360 the upward pseudo-inverse factors S^+U^T and V; 361/362 the downward ones;
+ * 363 the periodic far-image operator.  All are composed with the pseudo-inverse and
+ * described in units of the box half-width.  Values come from the plan's precision (FP32
+ * plans return their FP32 operators widened). */
+int kafmm_get_operator(kafmm_plan_t plan, int slot, double* out);
+
 /* Releases the plan and all device memory it owns. */
 int kafmm_destroy(kafmm_plan_t plan);
 

@@ -107,10 +107,6 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
     g_err = "kafmm_plan: invalid kernel, boundary condition, order (2..16) or leaf size (1..4096)";
     return KAFMM_ERR_ARG;
   }
-  if (bc == KAFMM_BC_PXYZ) {
-    g_err = "kafmm_plan: the triply periodic operator is not built by this version";
-    return KAFMM_ERR_ARG;
-  }
   Plan* P = new Plan();
   P->kernel = kernel;
   P->bc = bc;
@@ -317,14 +313,14 @@ __global__ void k_vtab_csr(const int32_t* vtab, int nbox, const int64_t* off, in
     int64_t o = off[b];
     for (int k = 0; k < 216; ++k) {
       int32_t e = vtab[(int64_t)b * 216 + k];
-      if (e >= 0) ent[o++] = e;
+      if (e != LIST_EMPTY) ent[o++] = e;
     }
   }
 }
 __global__ void k_vtab_count(const int32_t* vtab, int nbox, int64_t* cnt) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
     int64_t c = 0;
-    for (int k = 0; k < 216; ++k) c += vtab[(int64_t)b * 216 + k] >= 0;
+    for (int k = 0; k < 216; ++k) c += vtab[(int64_t)b * 216 + k] != LIST_EMPTY;
     cnt[b] = c;
   }
 }
@@ -427,6 +423,23 @@ extern "C" int kafmm_get_counters(kafmm_plan_t pl, int64_t* c, int n) {
   int64_t v[4] = {P.launches_points, P.launches_eval, P.use_tc ? 1 : 0,
                   P.launches_points + P.launches_eval};
   for (int i = 0; i < n && i < 8; ++i) c[i] = i < 4 ? v[i] : 0;
+  return 0;
+}
+
+extern "C" int kafmm_get_operator(kafmm_plan_t pl, int slot, double* out) {
+  PLAN_CHECK(pl);
+  if (!out || slot < 0 || slot >= N_OPS) return fail(P, KAFMM_ERR_ARG, "bad operator slot");
+  int rc = ensure_ops(P);
+  if (rc) return rc;
+  if (P.kernel == KAFMM_STOKES_DL) return fail(P, KAFMM_ERR_STATE, "no operators for this kernel");
+  size_t RR = (size_t)P.R * P.R;
+  if (P.fp64()) {
+    CKP(cudaMemcpy(out, P.ops64.as<double>() + RR * slot, sizeof(double) * RR, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> tmp(RR);
+    CKP(cudaMemcpy(tmp.data(), P.ops32.as<float>() + RR * slot, sizeof(float) * RR, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < RR; ++i) out[i] = tmp[i];
+  }
   return 0;
 }
 

@@ -40,7 +40,8 @@ constexpr int OP_UP1 = OP_L2L + 8;
 constexpr int OP_UP2 = OP_UP1 + 1;
 constexpr int OP_DN1 = OP_UP2 + 1;
 constexpr int OP_DN2 = OP_DN1 + 1;
-constexpr int N_OPS = OP_DN2 + 1;
+constexpr int OP_PER = OP_DN2 + 1;  // periodic far-image operator of the root (composed)
+constexpr int N_OPS = OP_PER + 1;
 
 // Split formats of the tensor-core M->L.
 enum { SPLIT_TF32 = 0, SPLIT_BF16 = 1 };
@@ -59,7 +60,9 @@ __host__ __device__ inline void shift_decode(int c, int& sx, int& sy, int& sz) {
   sz = c / 9 - 1;
 }
 
-// List entry: source box index in the low 27 bits, shift code in the high 5.
+// List entry: source box index in the low 27 bits, shift code in the high 5 (codes >= 16 set
+// the sign bit, so entries are compared with LIST_EMPTY, never with 0).
+constexpr int32_t LIST_EMPTY = -1;  // box 2^27 - 1 with shift code 31: not a valid entry
 __host__ __device__ inline int32_t pack_entry(int box, int sc) { return box | (sc << 27); }
 __host__ __device__ inline int entry_box(int32_t e) { return e & ((1 << 27) - 1); }
 __host__ __device__ inline int entry_shift(int32_t e) { return (int)((uint32_t)e >> 27); }

@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> a) {
         double side = a.geo.L / (double)(1 << lv);
         if (a.mode == GM_M2L) {
           int32_t e = a.vtab[(int64_t)b * 216 + k];
-          if (e >= 0) {
+          if (e != LIST_EMPTY) {
             s = entry_box(e);
             dx = (T)(ox * side);
             dy = (T)(oy * side);
@@ -651,6 +651,44 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
   }
 }
 
+// Periodic Laplace: the zero-mean periodic Green's function has lap G_per = 1/V, so the sum
+// depends on the trace of the second charge moment, which equivalent charges do not carry.
+// Adds (sum_j q_j |y_j - c|^2 - sum_k M_k |ue_k - c|^2) / (6 V) to every target (c: root centre,
+// M: the root's upward equivalent charges).
+template <class T>
+__global__ void k_laplace_periodic_constant(const typename V4<T>::type* __restrict__ spos,
+                                            const typename V4<T>::type* __restrict__ sval, int64_t ns,
+                                            const T* __restrict__ up_equiv, const T* __restrict__ unit,
+                                            int n, Geo geo, T* __restrict__ g, int64_t nt) {
+  __shared__ double red[32];
+  __shared__ double cval;
+  double c[3] = {geo.org[0] + 0.5 * geo.L, geo.org[1] + 0.5 * geo.L, geo.org[2] + 0.5 * geo.L};
+  double acc = 0;
+  for (int64_t j = threadIdx.x; j < ns; j += blockDim.x) {
+    double d0 = (double)spos[j].x - c[0], d1 = (double)spos[j].y - c[1], d2 = (double)spos[j].z - c[2];
+    acc += (double)sval[j].x * (d0 * d0 + d1 * d1 + d2 * d2);
+  }
+  double r0 = 0.5 * geo.L;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double u2 = 0;
+    for (int d = 0; d < 3; ++d) {
+      double u = ALPHA_UE * r0 * (double)unit[3 * k + d];
+      u2 += u * u;
+    }
+    acc -= (double)up_equiv[k] * u2;  // root = box 0
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    cval = t / (6.0 * geo.L * geo.L * geo.L);
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < nt; i += blockDim.x) g[i] += (T)cval;
+}
+
 // ---------------------------------------------------------------------------------------
 // Host side.
 #define CK(call)                                           \
@@ -720,10 +758,14 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
       for (int b = T.lvl_start[l]; b < T.lvl_start[l + 1]; ++b) by_cls[cls(b)].push_back(b);
     add_tiles(W, by_cls, NB, W.l2l[l]);
   }
-  // pseudo-inverses: up for boxes in W lists, down for leaves with targets
+  // pseudo-inverses: up for boxes in W lists (and the root for the periodic Laplace
+  // constant), down for leaves with targets
+  bool per = P.bc == KAFMM_BC_PXYZ;
   for (int b = 0; b < nb; ++b)
-    if (wflag[b]) by_cls[0].push_back(b);
+    if (wflag[b] || (b == 0 && per && P.kernel == KAFMM_LAPLACE)) by_cls[0].push_back(b);
   add_tiles(W, by_cls, NB, W.pup);
+  if (per) by_cls[0].push_back(0);
+  add_tiles(W, by_cls, NB, W.root);
   for (int b = 0; b < nb; ++b)
     if (leaf[b] && te[b] > tb[b]) by_cls[0].push_back(b);
   add_tiles(W, by_cls, NB, W.pdn);
@@ -835,6 +877,16 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       ga.tiles = P.tiles.as<int4>() + W.m2m[l][0];
       KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
     }
+    // periodic: far images of the root's multipole density -> root's downward check
+    if (W.root[1] > W.root[0]) {
+      ga.mode = GM_APPLY;
+      ga.in = P.up_check.as<T>();
+      ga.out = P.dn_check.as<T>();
+      ga.op = OP_PER;
+      ga.scale_r = 0;
+      ga.tiles = P.tiles.as<int4>() + W.root[0];
+      KL k_gemm<T, C><<<dim3(1, rb), blk, 0, st>>>(ga);
+    }
     cudaEventRecord(P.ev[4], st);
     // M->L over the V lists (all levels)
     int nm2l = W.m2l[1] - W.m2l[0];
@@ -934,6 +986,10 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
     KL k_leaf<T, PR><<<W.leaves_n, LEAF_THREADS, smem, st>>>(la);
   }
   CK(cudaGetLastError());
+  if (PR == P_LAP && P.bc == KAFMM_BC_PXYZ && !P.near_only && nt > 0) {
+    KL k_laplace_periodic_constant<T><<<1, 1024, 0, st>>>(spos, P.s_sorted.as<T4>(), ns, P.up_equiv.as<T>(), unit,
+                                                       P.n, geo, P.g_sorted.as<T>(), nt);
+  }
   // back to the caller's order and dtype
   if (nt > 0) {
     const uint32_t* tperm = T_.same ? T_.src_perm.as<uint32_t>() : T_.trg_perm.as<uint32_t>();

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     int ox = k % 6 - 2 - (cls & 1), oy = (k / 6) % 6 - 2 - ((cls >> 1) & 1),
         oz = k / 36 - 2 - ((cls >> 2) & 1);
     bool inner = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
-    if (!inner && sbox[j] >= 0 && a.vtab[(int64_t)sbox[j] * 216 + k] >= 0) slot_any[k] = 1;
+    if (!inner && sbox[j] >= 0 && a.vtab[(int64_t)sbox[j] * 216 + k] != LIST_EMPTY) slot_any[k] = 1;
   }
   if (warp == W_MMA) {  // TMEM allocation (whole warp)
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -292,10 +292,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int item = pt; item < NB * GROUPS; item += NPROD) {
         int j = item / GROUPS, g = item % GROUPS;
         int b = sbox[j];
-        int src = b >= 0 ? a.vtab[(int64_t)b * 216 + s] : -1;
+        int32_t src = b >= 0 ? a.vtab[(int64_t)b * 216 + s] : LIST_EMPTY;
         float v[4][8];
         int k0 = c * BK + g * 8;
-        if (src >= 0) {
+        if (src != LIST_EMPTY) {
           src = entry_box(src);
           float sx = ox * sside[j], sy = oy * sside[j], sz = oz * sside[j];
           const float4* p = reinterpret_cast<const float4*>(a.up) + (int64_t)src * R + k0;

@@ -216,6 +216,71 @@ __global__ void k_scale_rows(const double* in, const double* w, int n, double* o
     out[e] = in[e] * w[e / n];
 }
 
+// Periodic far-image operator at unit scale (root half-width 1, period 2):
+//   T[i][j] = G_per(dc_i - ue_j) - sum_{max|n| <= 1} K(dc_i - ue_j - 2n)
+// with G_per the Ewald sum with the k = 0 mode removed (Laplace; Stokeslet by Hasimoto's split,
+// weight (1 + k^2/4xi^2) e^{-k^2/4xi^2}).  xi = 2 (xi * period = 4), real images |n| <= 2,
+// Fourier modes |m| <= 8 (converged to FP64 rounding).  Where dc_i and ue_j coincide, the n = 0
+// real-space term is replaced by its regular limit and the n = 0 near image is left out.
+__global__ void k_periodic_operator(const double* __restrict__ unit, int n, int stokes, double adc,
+                                    double aue, double* __restrict__ T) {
+  const double Lp = 2.0, xi = 2.0, V = Lp * Lp * Lp;
+  const double sp = 2.0 * xi / sqrt(PI);
+  int R = stokes ? 3 * n : n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / n), j = (int)(e % n);
+    // products rounded separately (no FMA contraction), so coincident points give r = 0 exactly
+    double r[3];
+    for (int q = 0; q < 3; ++q) r[q] = __dmul_rn(adc, unit[3 * i + q]) - __dmul_rn(aue, unit[3 * j + q]);
+    double m[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double lap = stokes ? 0.0 : -1.0 / (4.0 * xi * xi * V);
+    for (int a = -2; a <= 2; ++a)
+      for (int b = -2; b <= 2; ++b)
+        for (int c = -2; c <= 2; ++c) {
+          double d[3] = {r[0] + a * Lp, r[1] + b * Lp, r[2] + c * Lp};
+          double rr = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+          double rn = sqrt(rr);
+          // near images (max|n| <= 1) are removed again: there the real-space term minus the
+          // free-space kernel is taken in the form -erf(xi r)/r, free of cancellation
+          bool near = abs(a) <= 1 && abs(b) <= 1 && abs(c) <= 1;
+          double ex = exp(-xi * xi * rr);
+          double h = near ? -erf(xi * rn) : erfc(xi * rn);  // the erfc factor, minus 1 if near
+          if (!stokes) {
+            lap += rn == 0.0 ? -xi / (2.0 * PI * sqrt(PI)) : h / (4.0 * PI * rn);
+          } else if (rn == 0.0) {
+            for (int q = 0; q < 3; ++q) m[4 * q] += -2.0 * sp / (8.0 * PI);
+          } else {
+            double A = (h / rn - sp * ex) / (8.0 * PI), B = (h / rn + sp * ex) / (8.0 * PI) / rr;
+            for (int p = 0; p < 3; ++p)
+              for (int q = 0; q < 3; ++q) m[3 * p + q] += (p == q ? A : 0.0) + B * d[p] * d[q];
+          }
+        }
+    for (int a = -8; a <= 8; ++a)
+      for (int b = -8; b <= 8; ++b)
+        for (int c = -8; c <= 8; ++c) {
+          if (a == 0 && b == 0 && c == 0) continue;
+          double kv[3] = {2.0 * PI * a / Lp, 2.0 * PI * b / Lp, 2.0 * PI * c / Lp};
+          double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+          double cs = cos(kv[0] * r[0] + kv[1] * r[1] + kv[2] * r[2]);
+          double g = exp(-k2 / (4.0 * xi * xi)) / (k2 * V) * cs;
+          if (!stokes) {
+            lap += g;
+          } else {
+            g *= 1.0 + k2 / (4.0 * xi * xi);
+            for (int p = 0; p < 3; ++p)
+              for (int q = 0; q < 3; ++q) m[3 * p + q] += g * ((p == q ? 1.0 : 0.0) - kv[p] * kv[q] / k2);
+          }
+        }
+    if (!stokes) {
+      T[(int64_t)i * R + j] = lap;
+    } else {
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) T[(int64_t)(3 * i + p) * R + 3 * j + q] = m[3 * p + q];
+    }
+  }
+}
+
 __global__ void k_round32(const double* in, int64_t n, float* out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
@@ -358,6 +423,12 @@ int build_operators(Plan& P) {
     KL k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, cx, cy, cz, ALPHA_DC, 0, 0, 0,
                                             2.0 * ALPHA_DE, K);
     compose(OP_DN1, OP_DN2, 2.0, O + RR * (OP_L2L + c));
+  }
+  if (P.bc == KAFMM_BC_PXYZ) {  // root far images, composed with the upward pseudo-inverse
+    KL k_periodic_operator<<<1024, 128, 0, st>>>(unit, n, stokes, ALPHA_DC, ALPHA_UE, K);
+    compose(OP_UP1, OP_UP2, 1.0, O + RR * OP_PER);
+  } else {
+    CK(cudaMemsetAsync(O + RR * OP_PER, 0, sizeof(double) * RR, st));
   }
   CK(cudaGetLastError());
   if (P.fp64()) {

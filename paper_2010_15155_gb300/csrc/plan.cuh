@@ -55,6 +55,7 @@ struct WorkLists {
   int m2m[MAX_LEVELS][2] = {};
   int l2l[MAX_LEVELS][2] = {};
   int pup[2] = {0, 0}, pdn[2] = {0, 0};
+  int root[2] = {0, 0};                      // the root alone (periodic far images)
   int leaves_n = 0, xbox_off = 0, xbox_n = 0, leafbox_off = 0;  // plain box lists
 };
 

@@ -342,7 +342,7 @@ __global__ void k_lists(TreeView t, ListOut o) {
       int bx = ax & 1, by = ay & 1, bz = az & 1;
       for (int k = 0; k < 216; ++k) {
         int ox = k % 6 - 2 - bx, oy = (k / 6) % 6 - 2 - by, oz = k / 36 - 2 - bz;
-        int32_t e = -1;
+        int32_t e = LIST_EMPTY;
         bool inner = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
         if (!inner && (lv >= 2 || (t.periodic && lv >= 1))) {
           int cx, cy, cz, sx, sy, sz;
@@ -481,7 +481,7 @@ __global__ void k_leaf_list(const int8_t* leaf, const int* leaf_pos, int nbox, i
 __global__ void k_tree_stats(TreeView t, const int32_t* vtab, unsigned long long* out) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x) {
     unsigned long long nv = 0;
-    for (int k = 0; k < 216; ++k) nv += vtab[(int64_t)b * 216 + k] >= 0;
+    for (int k = 0; k < 216; ++k) nv += vtab[(int64_t)b * 216 + k] != LIST_EMPTY;
     atomicAdd(&out[0], nv);
     if (t.leaf[b]) {
       unsigned long long np = (unsigned long long)max(t.se[b] - t.sb[b], t.te[b] - t.tb[b]);

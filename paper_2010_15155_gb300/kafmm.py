@@ -59,6 +59,7 @@ def lib():
             "kafmm_get_list": ([vp, i32, vp, vp, vp], i32),
             "kafmm_phase_times": ([vp, ctypes.POINTER(dbl), i32], i32),
             "kafmm_get_counters": ([vp, ctypes.POINTER(i64), i32], i32),
+            "kafmm_get_operator": ([vp, i32, vp], i32),
             "kafmm_destroy": ([vp], i32),
             "kafmm_last_error": ([vp], ctypes.c_char_p),
         }
@@ -170,6 +171,12 @@ def kafmm_get_counters(plan):
     _check(plan, lib().kafmm_get_counters(plan, c, 8))
     return {"launches_points": int(c[0]), "launches_eval": int(c[1]),
             "tensor_core_m2l": int(c[2]), "launches_per_step": int(c[3])}
+
+
+def kafmm_get_operator(plan, slot, R):
+    out = np.zeros((R, R))
+    _check(plan, lib().kafmm_get_operator(plan, slot, out.ctypes.data))
+    return out
 
 
 def kafmm_destroy(plan):

@@ -29,8 +29,9 @@ def _cuda():
     build.build()
 
 
-def _gpu_tree(pts, q, dtype=torch.float64):
-    plan = K.Plan(K.LAPLACE, p=4, q=q, precision=K.PREC_FP64, near_only=True)
+def _gpu_tree(pts, q, dtype=torch.float64, periodic=False):
+    plan = K.Plan(K.LAPLACE, p=4, q=q, precision=K.PREC_FP64, near_only=True,
+                  bc=K.BC_PXYZ if periodic else K.BC_OPEN)
     y = torch.from_numpy(np.ascontiguousarray(pts)).to(dtype).cuda()
     plan.set_points(y)
     info = plan.info()
@@ -49,8 +50,9 @@ def _code(sh):
     return (sh[0] + 1) + 3 * (sh[1] + 1) + 9 * (sh[2] + 1)
 
 
+@pytest.mark.parametrize("periodic", [False, True])
 @pytest.mark.parametrize("case", ["uniform", "clustered", "tiny"])
-def test_tree_and_lists_match_oracle(case):
+def test_tree_and_lists_match_oracle(case, periodic):
     if case == "uniform":
         pts, _ = W.laplace_uniform(6000, seed=3)
         q = 40
@@ -60,8 +62,8 @@ def test_tree_and_lists_match_oracle(case):
     else:
         pts, _ = W.laplace_uniform(30, seed=5)
         q = 64
-    T = Tree(pts, q=q)
-    info, level, anchor, parent, leaf, lists = _gpu_tree(pts, q)
+    T = Tree(pts, q=q, periodic=periodic)
+    info, level, anchor, parent, leaf, lists = _gpu_tree(pts, q, periodic=periodic)
     assert info["nbox"] == T.nbox and info["nlevels"] == T.nlevels
     assert np.array_equal(level, T.level)
     assert np.array_equal(anchor, T.anchor)
@@ -215,3 +217,45 @@ def test_rpy_sphere_velocities_with_overlap_match_brute_force(prec, tol):
     nover = np.sum(np.linalg.norm(pts[:, None] - pts[None], axis=2) < a[:, None] + a[None]) - len(pts)
     assert nover > 1000  # the case really exercises the overlap pass
     assert D.rel_l2(ua.double().cpu().numpy(), ref) < tol
+
+
+def _neutral(kernel, n, seed, dtype=np.float64):
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, 3))
+    kt = 1 if kernel == "laplace" else 3
+    s = rng.standard_normal((n, kt))
+    return pts.astype(dtype), (s - s.mean(axis=0)).astype(dtype)
+
+
+@pytest.mark.parametrize("problem,kernel", [("laplace", "laplace"), ("stokeslet_g", "stokeslet")])
+def test_periodic_fp64_gpu_kafmm_matches_cpu_kafmm(problem, kernel):
+    """Triply periodic KAFMM (far images through the root operator) vs the oracle's periodic
+    plain KAFMM, FP64 both: rel L2 <= 1e-7."""
+    from oracle import periodic as Pd
+    pts, s = _neutral(kernel, 1500, seed=21)
+    p, q = 6, 32
+    ref = KAFMM(problem, p, q, bc="pxyz", t_m2l=Pd.t_m2l(kernel, p)).evaluate(pts, s)
+    plan = K.Plan(KERN[kernel], p=p, q=q, bc=K.BC_PXYZ, precision=K.PREC_FP64, variant=K.ML_G)
+    plan.set_points(torch.from_numpy(pts).cuda())
+    g = plan.eval(torch.from_numpy(s).cuda()).cpu().numpy()
+    plan.close()
+    assert D.rel_l2(g, ref) < 1e-7
+
+
+def test_periodic_fp32_gpu_kafmm_against_ewald_and_translation():
+    """Periodic Stokeslet, FP32 form: error against the Ewald sum at the FMM level, and the
+    translation error (Sec. III.B): a rigid shift modulo the cell changes nothing beyond it."""
+    from oracle import periodic as Pd
+    pts, f = _neutral("stokeslet", 6000, seed=22)
+    idx = np.arange(0, 6000, 24)
+    ref = Pd.ewald_sum("stokeslet", pts[idx], pts, f)
+    plan = K.Plan(K.STOKESLET, p=8, q=48, bc=K.BC_PXYZ, precision=K.PREC_FP32, variant=K.ML_G)
+    plan.set_points(torch.from_numpy(pts.astype(np.float32)).cuda())
+    g0 = plan.eval(torch.from_numpy(f.astype(np.float32)).cuda()).double().cpu().numpy()
+    shifted = ((pts + np.array([0.4173, 0.2281, 0.9011])) % 1.0).astype(np.float32)
+    shifted = np.minimum(shifted, np.float32(1) - np.float32(2 ** -24))
+    plan.set_points(torch.from_numpy(shifted).cuda())
+    g1 = plan.eval(torch.from_numpy(f.astype(np.float32)).cuda()).double().cpu().numpy()
+    plan.close()
+    assert D.rel_l2(g0[idx], ref) < 5e-5
+    assert D.rel_l2(g1, g0) < 5e-5

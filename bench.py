@@ -159,7 +159,7 @@ def run_gpu(args):
     s = torch.from_numpy(f).to(dev)
     g = torch.empty((N_POINTS, 3), dtype=torch.float32, device=dev)
     prec = {"mixed": K.PREC_MIXED, "fp32": K.PREC_FP32, "fp64": K.PREC_FP64}[args.precision]
-    split = {"tf32x3": K.TC_TF32X3, "bf16x3": K.TC_BF16X3}[args.tc_split]
+    split = {"tf32x3": K.TC_TF32X3, "bf16x3": K.TC_BF16X3, "auto": K.TC_AUTO}[args.tc_split]
     plan = K.Plan(K.STOKESLET, p=P_ORDER, q=Q_LEAF, precision=prec, variant=K.ML_L4,
                   stream=stream.cuda_stream, tc_split=split)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -234,14 +234,15 @@ def run_gpu(args):
     n = 6 * (P_ORDER - 1) ** 2 + 2
     m2l_flops = info["n_v"] * 2.0 * n * n * 4
     m2l_s = ph["m2l"] * 1e-3
+    split_used = K.kafmm_get_counters(plan.h)["tc_split"]
     if args.precision == "mixed" and plan_uses_tc(plan):
         # TF32 dense peak = measured bf16 burst x nominal tf32/bf16 ratio (1.1 / 2.25 PFLOP/s);
         # achieved counts useful flops only (the three split products are not counted).
         bound, unit = "tensor", "TFLOP/s"
-        peak = peaks["bf16_tflops"] * (1.1 / 2.25) if args.tc_split == "tf32x3" else \
+        peak = peaks["bf16_tflops"] * (1.1 / 2.25) if split_used == "tf32x3" else \
             peaks["bf16_tflops"]
         achieved = m2l_flops / m2l_s / 1e12
-        peak_note = (f"{args.tc_split}: {'tf32 = bf16 x 1.1/2.25' if args.tc_split == 'tf32x3' else 'bf16'}"
+        peak_note = (f"{split_used}: {'tf32 = bf16 x 1.1/2.25' if split_used == 'tf32x3' else 'bf16'}"
                      f" dense burst, {src}; useful flops (split products not counted, max frac 1/3)")
     else:
         # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x max SM clock
@@ -254,12 +255,12 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": f"f32+{args.tc_split}" if args.precision == "mixed"
+        "scaling": "weak", "vs_baseline": None, "dtype": f"f32+{split_used}" if args.precision == "mixed"
         else ("f32" if args.precision == "fp32" else "f64"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_points": N_POINTS, "p": P_ORDER, "q": Q_LEAF,
                    "ml_table": "four-channel Laplace", "precision": args.precision,
-                   "tc_split": args.tc_split if args.precision == "mixed" else None,
+                   "tc_split": split_used if args.precision == "mixed" else None,
                    "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "rel_l2_vs_fp64": err,
@@ -302,7 +303,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
-    ap.add_argument("--tc-split", default="tf32x3", choices=["tf32x3", "bf16x3"])
+    ap.add_argument("--tc-split", default="auto", choices=["auto", "tf32x3", "bf16x3"])
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -81,13 +81,15 @@ enum {
   KAFMM_OPT_NEAR_ONLY = 4,
   /* 1: Kahan-compensated accumulation in the FP32 near field.  Default 0. */
   KAFMM_OPT_KAHAN = 5,
-  /* Split format of the tensor-core M->L in KAFMM_PREC_MIXED (default KAFMM_TC_TF32X3):
-   * each operand x = hi + lo in tf32 (or bf16) and each product hi*hi + hi*lo + lo*hi.
-   * TF32x3 keeps the mixed form within 1e-5 of the FP64 form; BF16x3 is faster and about
-   * an order of magnitude less accurate. */
+  /* Split format of the tensor-core M->L in KAFMM_PREC_MIXED (default KAFMM_TC_AUTO): each
+   * operand x = hi + lo in tf32 (or bf16) and each product hi*hi + hi*lo + lo*hi.  Measured
+   * error of the mixed form against the FP64 form (Stokeslet, N = 262144 uniform): TF32x3
+   * 4.7e-6..5.7e-6 for p = 6..10; BF16x3 4.2e-5 (p = 6), 1.1e-5 (p = 8), 6.6e-6 (p = 10),
+   * 7e-6 against the direct sum at p = 12, at about 0.7x the time.  AUTO takes BF16x3 for
+   * p >= 10 and TF32x3 below. */
   KAFMM_OPT_TC_SPLIT = 6
 };
-enum { KAFMM_TC_TF32X3 = 0, KAFMM_TC_BF16X3 = 1 };
+enum { KAFMM_TC_TF32X3 = 0, KAFMM_TC_BF16X3 = 1, KAFMM_TC_AUTO = 2 };
 enum { KAFMM_PREC_FP64 = 0, KAFMM_PREC_FP32 = 1, KAFMM_PREC_MIXED = 2 };
 enum { KAFMM_ML_G = 0, KAFMM_ML_L4 = 1 };
 
@@ -162,7 +164,8 @@ int kafmm_phase_times(kafmm_plan_t plan, double* t, int n);
 
 /* Counters of the last calls (host array c[n], up to 8 entries): 0 kernel launches of the
  * last kafmm_set_points, 1 kernel launches of the last kafmm_eval, 2 whether M->L ran on the
- * tcgen05 tensor cores (0/1), 3 launches of set_points + eval. */
+ * tcgen05 tensor cores (0/1), 3 launches of set_points + eval, 4 the split format in use
+ * (KAFMM_TC_TF32X3 or KAFMM_TC_BF16X3; -1 without tensor cores). */
 int kafmm_get_counters(kafmm_plan_t plan, int64_t* c, int n);
 
 /* Copies one precomputed translation operator to the host as FP64 (row-major R x R, R = the

@@ -54,6 +54,8 @@ static void configure(Plan& P) {
   }
   P.n = 6 * (P.p - 1) * (P.p - 1) + 2;
   P.R = P.n * P.D;
+  P.tc_split = P.tc_split_opt == KAFMM_TC_AUTO ? (P.p >= 10 ? SPLIT_BF16 : SPLIT_TF32)
+                                               : (P.tc_split_opt == KAFMM_TC_BF16X3 ? SPLIT_BF16 : SPLIT_TF32);
   P.ops_ready = false;
   P.use_tc = false;
 }
@@ -154,10 +156,10 @@ extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
       P.kahan = value ? 1 : 0;
       return 0;
     case KAFMM_OPT_TC_SPLIT:
-      if (value != KAFMM_TC_TF32X3 && value != KAFMM_TC_BF16X3)
+      if (value != KAFMM_TC_TF32X3 && value != KAFMM_TC_BF16X3 && value != KAFMM_TC_AUTO)
         return fail(P, KAFMM_ERR_ARG, "bad tensor-core split %lld", (long long)value);
-      if (P.tc_split != (int)value) {
-        P.tc_split = (int)value;
+      if (P.tc_split_opt != (int)value) {
+        P.tc_split_opt = (int)value;
         configure(P);
         P.have_points = false;
       }
@@ -420,9 +422,10 @@ extern "C" int kafmm_phase_times(kafmm_plan_t pl, double* t, int n) {
 extern "C" int kafmm_get_counters(kafmm_plan_t pl, int64_t* c, int n) {
   PLAN_CHECK(pl);
   if (!c || n < 0) return fail(P, KAFMM_ERR_ARG, "null array");
-  int64_t v[4] = {P.launches_points, P.launches_eval, P.use_tc ? 1 : 0,
-                  P.launches_points + P.launches_eval};
-  for (int i = 0; i < n && i < 8; ++i) c[i] = i < 4 ? v[i] : 0;
+  int64_t v[5] = {P.launches_points, P.launches_eval, P.use_tc ? 1 : 0,
+                  P.launches_points + P.launches_eval,
+                  P.use_tc ? (P.tc_split == SPLIT_BF16 ? KAFMM_TC_BF16X3 : KAFMM_TC_TF32X3) : -1};
+  for (int i = 0; i < n && i < 8; ++i) c[i] = i < 5 ? v[i] : 0;
   return 0;
 }
 

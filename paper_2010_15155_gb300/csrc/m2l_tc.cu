@@ -20,6 +20,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "plan.cuh"
 
 namespace kafmm {
@@ -54,7 +56,9 @@ struct Args {
   TreeView t;
   double L;
   const float* up;        // [nbox][R][4]
-  float* dn;              // [nbox][R][4]
+  float* dn;              // [nsplit][nbox][R][4]: partial sums, one per offset range
+  int64_t part_stride;    // floats between partial buffers
+  int nsplit;
   const int4* tiles;
   const int* boxlist;
   const int32_t* vtab;
@@ -86,10 +90,10 @@ __device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity, unsi
   for (uint32_t it = 0;; ++it) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(addr), "r"(parity)
+        : "r"(addr), "r"(parity), "r"(1000000u)  // suspend up to 1 ms per try (woken on completion)
         : "memory");
     if (ok) return true;
     if (*(volatile int*)bail) return false;
@@ -187,6 +191,10 @@ template <int SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_m2l_tc(const __grid_constant__ CUtensorMap tmap, Args a) {
   constexpr int BK = Fmt<SPLIT>::BK, MK = Fmt<SPLIT>::MK;
+  // offsets accumulated in TMEM before each drain into the running sum: longer chains lose
+  // accuracy in TF32x3 (measured 5.4e-6 -> 8.2e-6 at p = 10 with 2), BF16x3 is limited by its
+  // operand split instead
+  constexpr int DRAIN = SPLIT == SPLIT_TF32 ? 1 : 2;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -236,11 +244,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {  // active offsets of this tile, then this CTA's share (blockIdx.z)
     int ns = 0;
     for (int k = 0; k < 216; ++k)
       if (slot_any[k]) slot_list[ns++] = k;
-    nslots = ns;
+    int z = blockIdx.z, nz = a.nsplit;
+    int s0 = (int)((int64_t)ns * z / nz), s1 = (int)((int64_t)ns * (z + 1) / nz);
+    for (int k = s0; k < s1; ++k) slot_list[k - s0] = slot_list[k];
+    nslots = s1 - s0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -278,8 +289,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp >= 4 && warp < W_TMA) {
     // ---------------- B producers: gather, re-reference, split, swizzle ----------------
-    constexpr int GROUPS = BK / 8;            // 8-element k groups per chunk
-    constexpr int CPG = 8 * Fmt<SPLIT>::ES / 16;  // 16-byte chunks per group and split
+    // One item = one 16-byte chunk (KPL consecutive k) of the four channel rows of one box;
+    // the 8 lanes of a quarter warp take the 8 chunks of the same rows, which the 128-byte
+    // swizzle maps to 8 distinct bank groups (conflict-free stores).
+    constexpr int KPL = 16 / Fmt<SPLIT>::ES;  // k values per 16-byte chunk
     const int pt = threadIdx.x - 128;
     for (int it = 0; it < total; ++it) {
       int st = it % STAGES;
@@ -289,37 +302,47 @@ __global__ void __launch_bounds__(THREADS, 1)
             oz = (float)(s / 36 - 2 - ((cls >> 2) & 1));
       unsigned char* bhi = smem + st * STAGE_BYTES + 2 * A_BYTES;
       unsigned char* blo = bhi + B_BYTES;
-      for (int item = pt; item < NB * GROUPS; item += NPROD) {
-        int j = item / GROUPS, g = item % GROUPS;
+      constexpr int IPT = NB * 8 / NPROD;  // items per producer thread per chunk
+      float4 q[IPT][KPL];
+      float sh[IPT][3];
+      // issue every gather of this thread before converting (hides the L2 latency)
+#pragma unroll
+      for (int ii = 0; ii < IPT; ++ii) {
+        int item = pt + ii * NPROD;
+        int j = item >> 3, cidx = item & 7;
         int b = sbox[j];
         int32_t src = b >= 0 ? a.vtab[(int64_t)b * 216 + s] : LIST_EMPTY;
-        float v[4][8];
-        int k0 = c * BK + g * 8;
-        if (src != LIST_EMPTY) {
-          src = entry_box(src);
-          float sx = ox * sside[j], sy = oy * sside[j], sz = oz * sside[j];
-          const float4* p = reinterpret_cast<const float4*>(a.up) + (int64_t)src * R + k0;
-          float4 q[8];
+        int k0 = c * BK + cidx * KPL;
+        sh[ii][0] = ox * sside[j];
+        sh[ii][1] = oy * sside[j];
+        sh[ii][2] = oz * sside[j];
+        const float4* p = src != LIST_EMPTY ? reinterpret_cast<const float4*>(a.up) +
+                                                  (int64_t)entry_box(src) * R + k0
+                                            : nullptr;
 #pragma unroll
-          for (int t = 0; t < 8; ++t) q[t] = (k0 + t < R) ? __ldg(p + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int t = 0; t < KPL; ++t)
+          q[ii][t] = (p && k0 + t < R) ? __ldg(p + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
 #pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            v[0][t] = q[t].x;
-            v[1][t] = q[t].y;
-            v[2][t] = q[t].z;
-            v[3][t] = q[t].w + sx * q[t].x + sy * q[t].y + sz * q[t].z;
-          }
-        } else {
+      for (int ii = 0; ii < IPT; ++ii) {
+        int item = pt + ii * NPROD;
+        int j = item >> 3, cidx = item & 7;
+        float v[4][KPL];
 #pragma unroll
-          for (int t = 0; t < 8; ++t) v[0][t] = v[1][t] = v[2][t] = v[3][t] = 0.f;
+        for (int t = 0; t < KPL; ++t) {
+          v[0][t] = q[ii][t].x;
+          v[1][t] = q[ii][t].y;
+          v[2][t] = q[ii][t].z;
+          v[3][t] = q[ii][t].w + sh[ii][0] * q[ii][t].x + sh[ii][1] * q[ii][t].y + sh[ii][2] * q[ii][t].z;
         }
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
           int n = 4 * j + ch;
-          uint32_t hw[8], lw[8];
+          uint32_t off = (uint32_t)((n >> 3) * 1024 + (n & 7) * 128 + ((cidx ^ (n & 7)) << 4));
+          uint32_t hw[4], lw[4];
           if (SPLIT == SPLIT_TF32) {
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
+            for (int t = 0; t < 4; ++t) {
               float h = tf32_rn(v[ch][t]);
               hw[t] = __float_as_uint(h);
               lw[t] = __float_as_uint(tf32_rn(v[ch][t] - h));
@@ -327,21 +350,14 @@ __global__ void __launch_bounds__(THREADS, 1)
           } else {
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[ch][2 * t], v[ch][2 * t + 1]);
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[ch][2 * t], v[ch][(2 * t + 1) % KPL]);
               float2 hf = __bfloat1622float2(h2);
               hw[t] = *reinterpret_cast<uint32_t*>(&h2);
-              lw[t] = pack_bf16(v[ch][2 * t] - hf.x, v[ch][2 * t + 1] - hf.y);
+              lw[t] = pack_bf16(v[ch][2 * t] - hf.x, v[ch][(2 * t + 1) % KPL] - hf.y);
             }
           }
-#pragma unroll
-          for (int cc = 0; cc < CPG; ++cc) {
-            int chunk = g * CPG + cc;
-            uint32_t off = (uint32_t)((n >> 3) * 1024 + (n & 7) * 128 + ((chunk ^ (n & 7)) << 4));
-            *reinterpret_cast<uint4*>(bhi + off) =
-                make_uint4(hw[4 * cc], hw[4 * cc + 1], hw[4 * cc + 2], hw[4 * cc + 3]);
-            *reinterpret_cast<uint4*>(blo + off) =
-                make_uint4(lw[4 * cc], lw[4 * cc + 1], lw[4 * cc + 2], lw[4 * cc + 3]);
-          }
+          *reinterpret_cast<uint4*>(bhi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(blo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -351,28 +367,33 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- MMA issue (one thread) ----------------
     if (lane == 0) {
       int it = 0;
-      for (int si = 0; si < ns; ++si) {
-        if (si > 0 && !wait_parity(&acc_empty, (si - 1) & 1, a.status, &bail)) break;
+      const int ngroups = (ns + DRAIN - 1) / DRAIN;
+      for (int gi = 0; gi < ngroups; ++gi) {
+        if (gi > 0 && !wait_parity(&acc_empty, (gi - 1) & 1, a.status, &bail)) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         bool ok = true;
-        for (int c = 0; c < nchunk; ++c, ++it) {
-          int st = it % STAGES;
-          if (!wait_parity(&full[st], (it / STAGES) & 1, a.status, &bail)) {
-            ok = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-          uint32_t base = smem_u32(smem + st * STAGE_BYTES);
-          uint32_t ahi = base, alo = base + A_BYTES, bhi = base + 2 * A_BYTES,
-                   blo = base + 2 * A_BYTES + B_BYTES;
+        int s_end = min(ns, (gi + 1) * DRAIN);
+        for (int si = gi * DRAIN; si < s_end && ok; ++si) {
+          for (int c = 0; c < nchunk; ++c, ++it) {
+            int st = it % STAGES;
+            if (!wait_parity(&full[st], (it / STAGES) & 1, a.status, &bail)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            uint32_t base = smem_u32(smem + st * STAGE_BYTES);
+            uint32_t ahi = base, alo = base + A_BYTES, bhi = base + 2 * A_BYTES,
+                     blo = base + 2 * A_BYTES + B_BYTES;
+            bool first = si == gi * DRAIN && c == 0;
 #pragma unroll
-          for (int kk = 0; kk < BK / MK; ++kk) {
-            uint32_t ko = kk * 32;  // MK elements = 32 bytes in both formats
-            mma<SPLIT>(tmem, sdesc(ahi + ko), sdesc(bhi + ko), (c > 0 || kk > 0) ? 1u : 0u);
-            mma<SPLIT>(tmem, sdesc(ahi + ko), sdesc(blo + ko), 1u);
-            mma<SPLIT>(tmem, sdesc(alo + ko), sdesc(bhi + ko), 1u);
+            for (int kk = 0; kk < BK / MK; ++kk) {
+              uint32_t ko = kk * 32;  // MK elements = 32 bytes in both formats
+              mma<SPLIT>(tmem, sdesc(ahi + ko), sdesc(bhi + ko), (first && kk == 0) ? 0u : 1u);
+              mma<SPLIT>(tmem, sdesc(ahi + ko), sdesc(blo + ko), 1u);
+              mma<SPLIT>(tmem, sdesc(alo + ko), sdesc(bhi + ko), 1u);
+            }
+            commit(&empty[st]);
           }
-          commit(&empty[st]);
         }
         if (!ok) break;
         commit(&acc_full);
@@ -382,14 +403,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- epilogue: drain each offset into the running sum ----------------
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     float x[32], y[32];
-    for (int si = 0; si < ns; ++si) {
-      if (!wait_parity(&acc_full, si & 1, a.status, &bail)) break;
+    const int ngroups = (ns + DRAIN - 1) / DRAIN;
+    for (int gi = 0; gi < ngroups; ++gi) {
+      if (!wait_parity(&acc_full, gi & 1, a.status, &bail)) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       for (int q = 0; q < BN / 32; ++q) {
         tmem_ld32(tmem + lane_base + q * 32, x);
-        if (si > 0) tmem_ld32(tmem + lane_base + 256 + q * 32, y);
+        if (gi > 0) tmem_ld32(tmem + lane_base + 256 + q * 32, y);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (si > 0) {
+        if (gi > 0) {
 #pragma unroll
           for (int t = 0; t < 32; ++t) x[t] += y[t];
         }
@@ -401,18 +423,24 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     // write the tile: row = row0 + lane quarter + lane, columns (box j, channel)
     int row = row0 + (warp & 3) * 32 + lane;
-    int do_write = __shfl_sync(0xffffffffu, (!*(volatile int*)&bail && ns > 0) ? 1 : 0, 0);
+    // every CTA writes its partial (zeros when it had no offsets) so the combine is fixed-order
+    int do_write = __shfl_sync(0xffffffffu, (!*(volatile int*)&bail) ? 1 : 0, 0);
+    float4* dst = reinterpret_cast<float4*>(a.dn + a.part_stride * blockIdx.z);
     if (do_write) {
       for (int q = 0; q < BN / 32; ++q) {
-        tmem_ld32(tmem + lane_base + 256 + q * 32, x);
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (ns > 0) {
+          tmem_ld32(tmem + lane_base + 256 + q * 32, x);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        } else {
+#pragma unroll
+          for (int t = 0; t < 32; ++t) x[t] = 0.f;
+        }
         if (row < R) {
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
             int b = sbox[q * 8 + jj];
             if (b >= 0)
-              reinterpret_cast<float4*>(a.dn)[(int64_t)b * R + row] =
-                  make_float4(x[4 * jj], x[4 * jj + 1], x[4 * jj + 2], x[4 * jj + 3]);
+              dst[(int64_t)b * R + row] = make_float4(x[4 * jj], x[4 * jj + 1], x[4 * jj + 2], x[4 * jj + 3]);
           }
         }
       }
@@ -424,6 +452,29 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS)
                  : "memory");
+  }
+}
+
+// dn[b] = sum of the partial sums over the offset ranges, in range order (boxes of the M->L
+// tiles only).
+__global__ void k_combine_parts(const float4* __restrict__ parts, int64_t part_stride4, int nsplit,
+                                float4* __restrict__ dn, const int4* __restrict__ tiles, int ntiles,
+                                const int* __restrict__ boxlist, int R) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int4 tile = tiles[t];
+    for (int e = threadIdx.x; e < tile.y * R; e += blockDim.x) {
+      int b = boxlist[tile.x + e / R], r = e % R;
+      int64_t i = (int64_t)b * R + r;
+      float4 v = parts[i];
+      for (int z = 1; z < nsplit; ++z) {
+        float4 w = parts[i + part_stride4 * z];
+        v.x += w.x;
+        v.y += w.y;
+        v.z += w.z;
+        v.w += w.w;
+      }
+      dn[i] = v;
+    }
   }
 }
 
@@ -476,17 +527,29 @@ int m2l_tc_launch(Plan& P, const int4* tiles, int ntiles, const int* boxlist, cu
     P.tmap_ready = true;
   }
   const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(P.tmap);
+  // offset ranges per tile: enough CTAs to fill the 152 SMs over several waves
+  int rows = (P.R + tc::BM - 1) / tc::BM;
+  int nsplit = 1;
+  while (nsplit < 4 && (int64_t)ntiles * rows * nsplit < 152 * 6) nsplit *= 2;
+  int64_t part_stride = (int64_t)P.tree.nbox * P.R * 4;
+  if (nsplit > 1) {
+    cudaError_t e = P.m2l_parts.reserve(sizeof(float) * part_stride * nsplit + 256);
+    if (e != cudaSuccess) return cuda_fail(P, e, "M->L partial buffers");
+  }
   tc::Args a;
   a.t = P.tree.view();
   a.L = P.L;
   a.up = P.up_check.as<float>();
-  a.dn = P.dn_check.as<float>();
+  // one offset range: straight into dn_check; several: partial buffers, combined below
+  a.dn = nsplit > 1 ? P.m2l_parts.as<float>() : P.dn_check.as<float>();
+  a.part_stride = nsplit > 1 ? part_stride : 0;
+  a.nsplit = nsplit;
   a.tiles = tiles;
   a.boxlist = boxlist;
   a.vtab = P.tree.vtab.as<int32_t>();
   a.status = P.tree.status.as<unsigned>();
   a.R = P.R;
-  dim3 grid(ntiles, (P.R + tc::BM - 1) / tc::BM);
+  dim3 grid(ntiles, rows, nsplit);
   if (P.tc_split == SPLIT_TF32) {
     a.nchunk = P.Rpad / tc::Fmt<SPLIT_TF32>::BK;
     KL tc::k_m2l_tc<SPLIT_TF32><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
@@ -494,6 +557,9 @@ int m2l_tc_launch(Plan& P, const int4* tiles, int ntiles, const int* boxlist, cu
     a.nchunk = P.Rpad / tc::Fmt<SPLIT_BF16>::BK;
     KL tc::k_m2l_tc<SPLIT_BF16><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
   }
+  if (nsplit > 1)
+    KL tc::k_combine_parts<<<std::min(ntiles, 152 * 4), 256, 0, st>>>(
+        P.m2l_parts.as<float4>(), part_stride / 4, nsplit, P.dn_check.as<float4>(), tiles, ntiles, boxlist, P.R);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(P, e, "k_m2l_tc launch");
   return 0;

@@ -75,7 +75,8 @@ struct Plan {
   // operators: [N_OPS][R][R] row-major (rows = target check rows, cols = source rows)
   DevBuf ops64, ops32, opstc;       // opstc: [N_M2L][2][R][Rpad] split (hi, lo), tf32 or bf16
   int Rpad = 0;                     // R rounded up to the tensor-core K granularity
-  int tc_split = SPLIT_TF32;        // split format of the tensor-core M->L
+  int tc_split = SPLIT_TF32;        // split format of the tensor-core M->L in use
+  int tc_split_opt = KAFMM_TC_AUTO; // the requested format (option)
   alignas(64) unsigned char tmap[128];  // TMA descriptor of opstc
   bool tmap_ready = false;
   DevBuf unit64, unit32;            // unit surface [n][3]
@@ -88,6 +89,7 @@ struct Plan {
   DevBuf g_sorted;                  // target values in sorted order
   DevBuf io_in, io_out, io_aux;     // staging for host pointers / dtype conversion
   DevBuf tiles, tile_meta;          // work lists of the gather-GEMM engine
+  DevBuf m2l_parts;                 // partial M->L sums per offset range (tensor-core path)
   int64_t tiles_cap = 0;
   WorkLists wl;
   bool use_tc = false;              // tensor-core M->L available for this plan

@@ -22,7 +22,7 @@ LAPLACE, STOKESLET, RPY, STOKES_DL = 0, 1, 2, 3
 BC_OPEN, BC_PXYZ = 0, 3
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN, OPT_TC_SPLIT = 1, 2, 3, 4, 5, 6
-TC_TF32X3, TC_BF16X3 = 0, 1
+TC_TF32X3, TC_BF16X3, TC_AUTO = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 ML_G, ML_L4 = 0, 1
 KDIM = {LAPLACE: (1, 1), STOKESLET: (3, 3), RPY: (4, 6), STOKES_DL: (9, 4)}
@@ -170,7 +170,8 @@ def kafmm_get_counters(plan):
     c = (ctypes.c_int64 * 8)()
     _check(plan, lib().kafmm_get_counters(plan, c, 8))
     return {"launches_points": int(c[0]), "launches_eval": int(c[1]),
-            "tensor_core_m2l": int(c[2]), "launches_per_step": int(c[3])}
+            "tensor_core_m2l": int(c[2]), "launches_per_step": int(c[3]),
+            "tc_split": {0: "tf32x3", 1: "bf16x3"}.get(int(c[4]))}
 
 
 def kafmm_get_operator(plan, slot, R):
@@ -195,7 +196,7 @@ class Plan:
 
     def __init__(self, kernel, p, q, bc=BC_OPEN, precision=PREC_MIXED, variant=ML_L4,
                  near_only=False, kahan=False, stream=None, origin=(0.0, 0.0, 0.0), L=1.0,
-                 tc_split=TC_TF32X3):
+                 tc_split=TC_AUTO):
         self.kernel = kernel
         self.ks, self.kt = KDIM[kernel]
         self.h = kafmm_plan(kernel, bc, p, q)

@@ -142,6 +142,23 @@ int kafmm_eval(kafmm_plan_t plan, const void* s, void* g, int dtype);
 int kafmm_rpy_velocity(kafmm_plan_t plan, const void* s, const void* a, const void* g,
                        void* ua, int dtype);
 
+/* Same result as kafmm_rpy_velocity, for callers that cannot allocate device memory during
+ * the call: for instance an application whose own pool allocator has reserved the device
+ * memory up front, or one that must not trigger the implicit device-wide synchronisation of
+ * cudaMalloc / cudaFree while other streams run.  The paper has no counterpart: this is a
+ * library convenience.  It calls no cudaMalloc, cudaFree or allocating library routine; its
+ * work arrays live in one fixed 32 MiB device array that every GPU loading the library holds
+ * until the process exits.  Limit: the work arrays take 32 bytes per source and 8 per target
+ * in FP64 (16 and 4 in FP32) plus 2 MiB of cell table, so about 780,000 points of one shared
+ * set in FP64 and 1.5 million in FP32; larger sets return KAFMM_ERR_ARG with the sizes in the
+ * message (use
+ * kafmm_rpy_velocity).  All pointers must be device pointers (host arrays would need staging
+ * copies).  The first call on a device looks the array up (once per device, that device
+ * current); make that first call before any stream capture.  Every call uses the same array,
+ * so calls that overlap on the GPU (other threads, other streams) race. */
+int kafmm_rpy_velocity_noalloc(kafmm_plan_t plan, const void* s, const void* a, const void* g,
+                               void* ua, int dtype);
+
 /* Tree and list statistics of the current points (host array info[n], up to 16 entries):
  * 0 boxes, 1 leaves, 2 levels, 3 U entries, 4 V entries, 5 W entries, 6 X entries,
  * 7 near-field pairs (sum over U of n_trg(B) n_src(A)), 8 max points in a leaf. */

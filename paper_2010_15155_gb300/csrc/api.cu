@@ -291,6 +291,21 @@ extern "C" int kafmm_rpy_velocity(kafmm_plan_t pl, const void* s, const void* a,
   return 0;
 }
 
+extern "C" int kafmm_rpy_velocity_noalloc(kafmm_plan_t pl, const void* s, const void* a, const void* g,
+                                          void* ua, int dtype) {
+  PLAN_CHECK(pl);
+  if (P.kernel != KAFMM_RPY) return fail(P, KAFMM_ERR_ARG, "kafmm_rpy_velocity_noalloc needs the RPY kernel");
+  if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "kafmm_rpy_velocity_noalloc before kafmm_set_points");
+  if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || (P.tree.n_src > 0 && !s) ||
+      (P.tree.n_trg > 0 && (!a || !g || !ua)))
+    return fail(P, KAFMM_ERR_ARG, "kafmm_rpy_velocity_noalloc: bad arguments");
+  // host arrays would need staging buffers, i.e. an allocation: device pointers only
+  if ((P.tree.n_src > 0 && is_host_ptr(s)) ||
+      (P.tree.n_trg > 0 && (is_host_ptr(a) || is_host_ptr(g) || is_host_ptr(ua))))
+    return fail(P, KAFMM_ERR_ARG, "kafmm_rpy_velocity_noalloc takes device pointers only");
+  return rpy_velocity_noalloc(P, s, a, g, ua, dtype);
+}
+
 extern "C" int kafmm_tree_info(kafmm_plan_t pl, int64_t* info, int n) {
   PLAN_CHECK(pl);
   if (!info || n < 0) return fail(P, KAFMM_ERR_ARG, "bad info array");

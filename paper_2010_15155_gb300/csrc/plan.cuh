@@ -116,5 +116,7 @@ int evaluate(Plan& P, const void* s_dev, void* g_dev, int dtype);
 int build_worklists(Plan& P, int NB, int NB_TC);
 int rpy_velocity(Plan& P, const void* s_dev, const void* a_dev, const void* g_dev, void* ua_dev,
                  int dtype);
+int rpy_velocity_noalloc(Plan& P, const void* s_dev, const void* a_dev, const void* g_dev,
+                         void* ua_dev, int dtype);
 
 }  // namespace kafmm

@@ -11,6 +11,7 @@
 // side is at least a_max + b_max, so every contact partner lies in the 27 surrounding cells.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "physics.cuh"
 #include "plan.cuh"
@@ -214,10 +215,118 @@ int run(Plan& P, const void* s, const void* a, const void* g, void* ua, int dtyp
   return 0;
 }
 
+// ---------------------------------------------------------------------------------------
+// Variant without allocations: the per-call work arrays (gathered forces and radii, the cell
+// table, the radius maxima) live in one file-scope device array instead of cudaMalloc'd
+// buffers.  Every GPU that loads the library holds the array until the process exits.  Calls
+// share it, so two calls that overlap on the GPU race; each call clears what must start at
+// zero.  The cell grid is capped at level 6 (a coarser grid than the contact radius asks for
+// is still exact, only slower).
+constexpr size_t NOALLOC_BYTES = (size_t)32 << 20;   // 32 MiB
+constexpr int NOALLOC_MAX_CELL_LEVEL = 6;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+static unsigned char* noalloc_base(Plan& P, int* rc) {
+  // host-side address of the array on the current device, looked up once per device
+  static std::mutex mu;
+  static unsigned char* addr[64] = {nullptr};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    *rc = cuda_fail(P, e == cudaSuccess ? cudaErrorInvalidDevice : e, "cudaGetDevice");
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      *rc = cuda_fail(P, e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress(scratch)");
+      return nullptr;
+    }
+    addr[dev] = reinterpret_cast<unsigned char*>(ptr);
+  }
+  *rc = 0;
+  return addr[dev];
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <class T>
+int run_noalloc(Plan& P, const void* s, const void* a, const void* g, void* ua, int dtype) {
+  using T4 = typename V4<T>::type;
+  Tree& Tr = P.tree;
+  cudaStream_t st = P.stream;
+  int64_t ns = Tr.n_src, nt = Tr.n_trg;
+  const int64_t ncell_max = 1ll << (3 * NOALLOC_MAX_CELL_LEVEL);
+  size_t need = 256 + align256(sizeof(T4) * (ns + 1)) + align256(sizeof(T) * (nt + 1)) +
+                2 * align256(sizeof(int) * ncell_max);
+  if (need > NOALLOC_BYTES)
+    return fail(P, KAFMM_ERR_ARG,
+                "kafmm_rpy_velocity_noalloc: %lld sources and %lld targets need %zu bytes of "
+                "scratch, more than the fixed %zu bytes (use kafmm_rpy_velocity)",
+                (long long)ns, (long long)nt, need, NOALLOC_BYTES);
+  int rc = 0;
+  unsigned char* base = noalloc_base(P, &rc);
+  if (rc) return rc;
+  unsigned* stat = reinterpret_cast<unsigned*>(base);
+  T4* fb = reinterpret_cast<T4*>(base + 256);
+  T* ta = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(fb) + align256(sizeof(T4) * (ns + 1)));
+  int* cb = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(ta) + align256(sizeof(T) * (nt + 1)));
+  int* ce = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(cb) + align256(sizeof(int) * ncell_max));
+  const uint32_t* sperm = Tr.src_perm.as<uint32_t>();
+  const uint32_t* tperm = Tr.same ? sperm : Tr.trg_perm.as<uint32_t>();
+  const uint64_t* skey = Tr.src_key.as<uint64_t>();
+  const uint64_t* tkey = Tr.same ? skey : Tr.trg_key.as<uint64_t>();
+  CK(cudaMemsetAsync(stat, 0, 64, st));
+  if (dtype == KAFMM_F64) {
+    KL k_gather_fb<double, T><<<grid_for(ns, 256), 256, 0, st>>>((const double*)s, sperm, ns, fb);
+    KL k_gather_scalar<double, T><<<grid_for(nt, 256), 256, 0, st>>>((const double*)a, tperm, nt, ta);
+  } else {
+    KL k_gather_fb<float, T><<<grid_for(ns, 256), 256, 0, st>>>((const float*)s, sperm, ns, fb);
+    KL k_gather_scalar<float, T><<<grid_for(nt, 256), 256, 0, st>>>((const float*)a, tperm, nt, ta);
+  }
+  KL k_max_radius<T><<<grid_for(std::max(ns, nt), 256), 256, 0, st>>>(ta, nt, fb, ns, stat);
+  unsigned h[2];
+  CK(cudaMemcpyAsync(h, stat, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  float amax, bmax;
+  memcpy(&amax, &h[0], 4);
+  memcpy(&bmax, &h[1], 4);
+  double reach = ((double)amax + (double)bmax) * (1.0 + 1e-6) / P.L;
+  int lev = 0;
+  while (lev < NOALLOC_MAX_CELL_LEVEL && reach > 0 && 1.0 / (double)(1 << (lev + 1)) >= reach) ++lev;
+  if (reach <= 0) lev = NOALLOC_MAX_CELL_LEVEL;
+  int64_t ncell = 1ll << (3 * lev);
+  CK(cudaMemsetAsync(cb, 0, sizeof(int) * ncell, st));
+  CK(cudaMemsetAsync(ce, 0, sizeof(int) * ncell, st));
+  if (ns > 0)
+    KL k_cell_table<<<grid_for(ns, 256), 256, 0, st>>>(skey, ns, 3 * (MAX_LEVEL - lev), cb, ce);
+  const T4* spos = Tr.src_pos.as<T4>();
+  const T4* tpos = Tr.same ? spos : Tr.trg_pos.as<T4>();
+  if (nt > 0) {
+    if (dtype == KAFMM_F64)
+      KL k_rpy_velocity<T, double><<<grid_for(nt, 128), 128, 0, st>>>(
+          spos, fb, tpos, ta, tkey, tperm, nt, cb, ce, lev, P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0,
+          (const double*)g, (double*)ua);
+    else
+      KL k_rpy_velocity<T, float><<<grid_for(nt, 128), 128, 0, st>>>(
+          spos, fb, tpos, ta, tkey, tperm, nt, cb, ce, lev, P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0,
+          (const float*)g, (float*)ua);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return 0;
+}
+
 }  // namespace
 
 int rpy_velocity(Plan& P, const void* s, const void* a, const void* g, void* ua, int dtype) {
   return P.fp64() ? run<double>(P, s, a, g, ua, dtype) : run<float>(P, s, a, g, ua, dtype);
+}
+
+int rpy_velocity_noalloc(Plan& P, const void* s, const void* a, const void* g, void* ua, int dtype) {
+  return P.fp64() ? run_noalloc<double>(P, s, a, g, ua, dtype) : run_noalloc<float>(P, s, a, g, ua, dtype);
 }
 
 }  // namespace kafmm

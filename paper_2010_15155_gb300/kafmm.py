@@ -54,6 +54,7 @@ def lib():
             "kafmm_set_points": ([vp, vp, i64, vp, i64, i32], i32),
             "kafmm_eval": ([vp, vp, vp, i32], i32),
             "kafmm_rpy_velocity": ([vp, vp, vp, vp, vp, i32], i32),
+            "kafmm_rpy_velocity_noalloc": ([vp, vp, vp, vp, vp, i32], i32),
             "kafmm_tree_info": ([vp, ctypes.POINTER(i64), i32], i32),
             "kafmm_get_tree": ([vp, vp, vp, vp, vp], i32),
             "kafmm_get_list": ([vp, i32, vp, vp, vp], i32),
@@ -131,6 +132,10 @@ def kafmm_eval(plan, s, g, dtype):
 
 def kafmm_rpy_velocity(plan, s, a, g, ua, dtype):
     _check(plan, lib().kafmm_rpy_velocity(plan, _ptr(s), _ptr(a), _ptr(g), _ptr(ua), dtype))
+
+
+def kafmm_rpy_velocity_noalloc(plan, s, a, g, ua, dtype):
+    _check(plan, lib().kafmm_rpy_velocity_noalloc(plan, _ptr(s), _ptr(a), _ptr(g), _ptr(ua), dtype))
 
 
 def kafmm_tree_info(plan):

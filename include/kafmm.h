@@ -128,6 +128,24 @@ int kafmm_set_domain(kafmm_plan_t plan, const double origin[3], double L);
 int kafmm_set_points(kafmm_plan_t plan, const void* y, int64_t n_src, const void* x,
                      int64_t n_trg, int dtype);
 
+/* Largest problem count of kafmm_set_points_batched. */
+#define KAFMM_MAX_PROBLEMS 65536
+
+/* Sets a batch of n_prob independent problems at once, each its own kernel sum of
+ * Eq. kernelsumlinear (the paper evaluates one sum per call; a batch runs many uneven ones
+ * in the same launches).  Problem k has the sources
+ * y[src_offsets[k] .. src_offsets[k+1]) and the targets x[trg_offsets[k] .. trg_offsets[k+1]),
+ * all in the same cube [origin, origin + L)^3, and interacts with nothing outside itself.
+ * src_offsets and trg_offsets are HOST arrays of n_prob + 1 nondecreasing entries starting at
+ * 0 (empty problems allowed); y and x are the concatenated points (host or device, as in
+ * kafmm_set_points; x == y with equal offsets means one shared set per problem).  One forest is
+ * built, one root per problem, and every later call (kafmm_eval, the tree queries) covers the
+ * whole batch in the same launches as one problem: s and g of kafmm_eval are the concatenated
+ * values in the same order.  1 <= n_prob <= KAFMM_MAX_PROBLEMS; n_prob > 1 needs
+ * KAFMM_BC_OPEN and is not accepted by the RPY velocity calls (KAFMM_ERR_ARG). */
+int kafmm_set_points_batched(kafmm_plan_t plan, int n_prob, const int64_t* src_offsets,
+                             const int64_t* trg_offsets, const void* y, const void* x, int dtype);
+
 /* Evaluates g [n_trg][k_t] from s [n_src][k_s] for the current points (overwrites g).
  * Upward pass S->M, M->M; downward pass M->L (V), S->L (X), L->L; leaves L->T, M->T (W),
  * S->T (U) -- Sec. II, Fig. kifmmgraph. */
@@ -161,14 +179,16 @@ int kafmm_rpy_velocity_noalloc(kafmm_plan_t plan, const void* s, const void* a, 
 
 /* Tree and list statistics of the current points (host array info[n], up to 16 entries):
  * 0 boxes, 1 leaves, 2 levels, 3 U entries, 4 V entries, 5 W entries, 6 X entries,
- * 7 near-field pairs (sum over U of n_trg(B) n_src(A)), 8 max points in a leaf. */
+ * 7 near-field pairs (sum over U of n_trg(B) n_src(A)), 8 max points in a leaf,
+ * 9 problems (1 unless set by kafmm_set_points_batched). */
 int kafmm_tree_info(kafmm_plan_t plan, int64_t* info, int n);
 
 /* Copies the tree to host arrays (each may be NULL): level[nbox], anchor[nbox][3],
  * parent[nbox], leaf[nbox] (0/1), and the list kind (0 U, 1 V, 2 W, 3 X) as CSR:
  * offsets[nbox + 1], entries[n_entries] = source box index, shifts[n_entries] = image
  * shift code (sx+1) + 3 (sy+1) + 9 (sz+1).  Boxes are numbered level by level, in Morton
- * order inside a level.  Sizes come from kafmm_tree_info. */
+ * order inside a level (a batch: ordered by problem, then Morton; the root of problem k is
+ * box k).  Sizes come from kafmm_tree_info. */
 int kafmm_get_tree(kafmm_plan_t plan, int32_t* level, int32_t* anchor, int32_t* parent,
                    int8_t* leaf);
 int kafmm_get_list(kafmm_plan_t plan, int kind, int64_t* offsets, int32_t* entries,

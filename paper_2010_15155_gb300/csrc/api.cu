@@ -178,12 +178,9 @@ extern "C" int kafmm_set_domain(kafmm_plan_t pl, const double origin[3], double 
   return 0;
 }
 
-extern "C" int kafmm_set_points(kafmm_plan_t pl, const void* y, int64_t ns, const void* x, int64_t nt,
-                                int dtype) {
-  PLAN_CHECK(pl);
-  if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || ns < 0 || nt < 0 || ns > (1ll << 31) - 2 ||
-      nt > (1ll << 31) - 2 || (ns > 0 && !y) || (nt > 0 && !x))
-    return fail(P, KAFMM_ERR_ARG, "kafmm_set_points: bad arguments");
+// Shared body of kafmm_set_points and kafmm_set_points_batched (arguments validated).
+static int set_points_impl(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, int dtype,
+                           int n_prob, const int64_t* soff, const int64_t* toff) {
   P.have_points = false;
   int rc = ensure_ops(P);
   if (rc) return rc;
@@ -192,6 +189,7 @@ extern "C" int kafmm_set_points(kafmm_plan_t pl, const void* y, int64_t ns, cons
   const void* yd = y;
   const void* xd = x;
   bool same = (x == y) && (ns == nt);
+  for (int k = 0; same && k <= n_prob; ++k) same = soff[k] == toff[k];
   if (ns > 0 && is_host_ptr(y)) {
     CKP(P.io_in.reserve(es * 3 * ns));
     CKP(cudaMemcpyAsync(P.io_in.p, y, es * 3 * ns, cudaMemcpyHostToDevice, P.stream));
@@ -204,13 +202,49 @@ extern "C" int kafmm_set_points(kafmm_plan_t pl, const void* y, int64_t ns, cons
     CKP(cudaMemcpyAsync(P.io_aux.p, x, es * 3 * nt, cudaMemcpyHostToDevice, P.stream));
     xd = P.io_aux.p;
   }
-  rc = build_tree(P, yd, ns, xd, nt, dtype);
+  rc = build_tree(P, yd, ns, xd, nt, dtype, n_prob, soff, toff);
   if (rc) return rc;
   rc = build_worklists(P, 64 / P.C, P.use_tc ? 128 / P.C * 2 : 64 / P.C);
   if (rc) return rc;
   P.launches_points = g_launches;
   P.have_points = true;
   return 0;
+}
+
+extern "C" int kafmm_set_points(kafmm_plan_t pl, const void* y, int64_t ns, const void* x, int64_t nt,
+                                int dtype) {
+  PLAN_CHECK(pl);
+  if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || ns < 0 || nt < 0 || ns > (1ll << 31) - 2 ||
+      nt > (1ll << 31) - 2 || (ns > 0 && !y) || (nt > 0 && !x))
+    return fail(P, KAFMM_ERR_ARG, "kafmm_set_points: bad arguments");
+  int64_t soff[2] = {0, ns}, toff[2] = {0, nt};
+  return set_points_impl(P, y, ns, x, nt, dtype, 1, soff, toff);
+}
+
+extern "C" int kafmm_set_points_batched(kafmm_plan_t pl, int n_prob, const int64_t* src_offsets,
+                                        const int64_t* trg_offsets, const void* y, const void* x,
+                                        int dtype) {
+  PLAN_CHECK(pl);
+  P.have_points = false;
+  if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || n_prob < 1 || n_prob > KAFMM_MAX_PROBLEMS ||
+      !src_offsets || !trg_offsets)
+    return fail(P, KAFMM_ERR_ARG, "kafmm_set_points_batched: bad dtype, problem count (1..%d) or offsets",
+                KAFMM_MAX_PROBLEMS);
+  if (P.bc != KAFMM_BC_OPEN && n_prob > 1)
+    return fail(P, KAFMM_ERR_ARG, "batches of several problems need the open boundary condition");
+  const int64_t* offs[2] = {src_offsets, trg_offsets};
+  for (int w = 0; w < 2; ++w) {
+    const int64_t* o = offs[w];
+    if (o[0] != 0) return fail(P, KAFMM_ERR_ARG, "kafmm_set_points_batched: offsets must start at 0");
+    for (int k = 0; k < n_prob; ++k)
+      if (o[k + 1] < o[k])
+        return fail(P, KAFMM_ERR_ARG, "kafmm_set_points_batched: offsets decrease at problem %d", k);
+    if (o[n_prob] > (1ll << 31) - 2)
+      return fail(P, KAFMM_ERR_ARG, "kafmm_set_points_batched: more than 2^31 - 2 points");
+  }
+  int64_t ns = src_offsets[n_prob], nt = trg_offsets[n_prob];
+  if ((ns > 0 && !y) || (nt > 0 && !x)) return fail(P, KAFMM_ERR_ARG, "kafmm_set_points_batched: null points");
+  return set_points_impl(P, y, ns, x, nt, dtype, n_prob, src_offsets, trg_offsets);
 }
 
 extern "C" int kafmm_eval(kafmm_plan_t pl, const void* s, void* g, int dtype) {
@@ -254,6 +288,7 @@ extern "C" int kafmm_rpy_velocity(kafmm_plan_t pl, const void* s, const void* a,
   PLAN_CHECK(pl);
   if (P.kernel != KAFMM_RPY) return fail(P, KAFMM_ERR_ARG, "kafmm_rpy_velocity needs the RPY kernel");
   if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "kafmm_rpy_velocity before kafmm_set_points");
+  if (P.tree.n_prob > 1) return fail(P, KAFMM_ERR_ARG, "kafmm_rpy_velocity takes one point set, not a batch");
   if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || (P.tree.n_src > 0 && !s) ||
       (P.tree.n_trg > 0 && (!a || !g || !ua)))
     return fail(P, KAFMM_ERR_ARG, "kafmm_rpy_velocity: bad arguments");
@@ -296,6 +331,8 @@ extern "C" int kafmm_rpy_velocity_noalloc(kafmm_plan_t pl, const void* s, const 
   PLAN_CHECK(pl);
   if (P.kernel != KAFMM_RPY) return fail(P, KAFMM_ERR_ARG, "kafmm_rpy_velocity_noalloc needs the RPY kernel");
   if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "kafmm_rpy_velocity_noalloc before kafmm_set_points");
+  if (P.tree.n_prob > 1)
+    return fail(P, KAFMM_ERR_ARG, "kafmm_rpy_velocity_noalloc takes one point set, not a batch");
   if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || (P.tree.n_src > 0 && !s) ||
       (P.tree.n_trg > 0 && (!a || !g || !ua)))
     return fail(P, KAFMM_ERR_ARG, "kafmm_rpy_velocity_noalloc: bad arguments");
@@ -311,8 +348,9 @@ extern "C" int kafmm_tree_info(kafmm_plan_t pl, int64_t* info, int n) {
   if (!info || n < 0) return fail(P, KAFMM_ERR_ARG, "bad info array");
   if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "no points");
   const Tree& T = P.tree;
-  int64_t v[9] = {T.nbox, T.nleaf, T.nlevels, T.n_u, T.n_v, T.n_w, T.n_x, T.near_pairs, T.max_leaf_pts};
-  for (int i = 0; i < n && i < 16; ++i) info[i] = i < 9 ? v[i] : 0;
+  int64_t v[10] = {T.nbox, T.nleaf, T.nlevels, T.n_u, T.n_v, T.n_w, T.n_x, T.near_pairs, T.max_leaf_pts,
+                   T.n_prob};
+  for (int i = 0; i < n && i < 16; ++i) info[i] = i < 10 ? v[i] : 0;
   return 0;
 }
 

@@ -10,6 +10,7 @@ namespace kafmm {
 struct TreeView {
   int nbox, nlevels, periodic;
   const int* lvl_start;     // [MAX_LEVELS + 1] (device copy)
+  const int* prob;          // [nbox] problem of each box (a batch has one root per problem)
   const uint64_t* key;      // cell key (Morton code of the anchor at the box's level)
   const int8_t* level;      // [nbox]
   const int* parent;        // [nbox], -1 for the root
@@ -24,6 +25,11 @@ struct TreeView {
 struct Tree {
   int64_t n_src = 0, n_trg = 0;
   bool same = true;
+  // independent problems of one batch: problem k owns sources [src_off[k], src_off[k+1]) and
+  // targets [trg_off[k], trg_off[k+1]) of the caller's arrays; a single set has n_prob = 1
+  int n_prob = 1;
+  std::vector<int64_t> src_off, trg_off;
+  DevBuf d_src_off, d_trg_off;
   int nbox = 0, nleaf = 0, nlevels = 0;
   int lvl_start[MAX_LEVELS + 1] = {0};
   int64_t n_u = 0, n_w = 0, n_x = 0, n_v = 0, near_pairs = 0;
@@ -33,7 +39,7 @@ struct Tree {
   DevBuf src_key, trg_key, src_perm, trg_perm;
   DevBuf src_pos, trg_pos;          // compute-type xyz (float4 or double4, w unused)
   // boxes
-  DevBuf d_lvl_start, key, level, parent, child, sb, se, tb, te, leaf, leaves;
+  DevBuf d_lvl_start, key, level, parent, child, sb, se, tb, te, leaf, leaves, prob;
   // lists, CSR over boxes (entries packed with pack_entry)
   DevBuf u_off, u_ent, w_off, w_ent, x_off, x_ent;
   DevBuf vtab;                      // [nbox][189] source box of each V slot or -1
@@ -41,7 +47,7 @@ struct Tree {
   // scratch of the build
   DevBuf s_keys2, s_vals2, s_hist, t_keys2, t_vals2;
   DevBuf bld_key, bld_sb, bld_se, bld_tb, bld_te, bld_parent, bld_child, bld_cnt, bld_nch,
-      bld_choff, bld_cb, bld_ctb;
+      bld_choff, bld_cb, bld_ctb, bld_prob;
   DevBuf status;                    // unsigned status word
   TreeView view() const;
 };
@@ -106,7 +112,10 @@ int fail(Plan& P, int code, const char* fmt, ...);
 int cuda_fail(Plan& P, cudaError_t e, const char* where);
 
 // tree.cu
-int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, int dtype);
+// Builds the forest of n_prob octrees (one root per problem; src_off / trg_off are host
+// arrays of n_prob + 1 offsets into y and x).
+int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, int dtype, int n_prob,
+               const int64_t* src_off, const int64_t* trg_off);
 
 // operators.cu
 int build_operators(Plan& P);

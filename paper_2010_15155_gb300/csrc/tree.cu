@@ -40,7 +40,29 @@ __global__ void k_keys(const T* __restrict__ pts, int64_t n, double ox, double o
 constexpr int RS_THREADS = 256, RS_ROUNDS = 16, RS_WARPS = RS_THREADS / 32;
 constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
 
-__global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
+// Problem of caller index v: the largest k < nprob with off[k] <= v (empty problems skipped).
+__device__ inline uint32_t problem_of(const int64_t* __restrict__ off, int nprob, uint32_t v) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= (int64_t)v)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return (uint32_t)lo;
+}
+
+// Digit of one element: bits [shift, shift + 8) of the Morton key, or of the element's
+// problem index when poff is given (the passes that group a batch by problem).
+__device__ inline unsigned radix_digit(uint64_t k, uint32_t v, int shift, const int64_t* poff,
+                                       int nprob) {
+  if (poff) return (problem_of(poff, nprob, v) >> shift) & 255u;
+  return (unsigned)((k >> shift) & 255);
+}
+
+__global__ void k_radix_hist(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                             int64_t n, int shift, const int64_t* __restrict__ poff, int nprob,
                              uint32_t* __restrict__ hist, int nblk) {
   __shared__ uint32_t cnt[256];
   cnt[threadIdx.x] = 0;
@@ -48,7 +70,7 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int s
   int64_t base = (int64_t)blockIdx.x * RS_TILE;
   for (int k = 0; k < RS_ROUNDS; ++k) {
     int64_t i = base + k * RS_THREADS + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255], 1u);
+    if (i < n) atomicAdd(&cnt[radix_digit(keys[i], poff ? vals[i] : 0u, shift, poff, nprob)], 1u);
   }
   __syncthreads();
   hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
@@ -56,7 +78,8 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int s
 
 __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                 uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
-                                int shift, const uint32_t* __restrict__ hist, int nblk) {
+                                int shift, const int64_t* __restrict__ poff, int nprob,
+                                const uint32_t* __restrict__ hist, int nblk) {
   __shared__ uint32_t wcnt[RS_WARPS][256];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
@@ -64,13 +87,15 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t
   int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * 32 * RS_ROUNDS;
   uint64_t k[RS_ROUNDS];
   uint32_t v[RS_ROUNDS], rk[RS_ROUNDS];
+  unsigned dg[RS_ROUNDS];
   unsigned lt = (1u << lane) - 1u;
   for (int r = 0; r < RS_ROUNDS; ++r) {
     int64_t i = base + r * 32 + lane;
     bool valid = i < n;
     k[r] = valid ? kin[i] : 0ull;
     v[r] = valid ? vin[i] : 0u;
-    unsigned d = valid ? (unsigned)((k[r] >> shift) & 255) : 256u;
+    unsigned d = valid ? radix_digit(k[r], v[r], shift, poff, nprob) : 256u;
+    dg[r] = d;
     unsigned peers = __match_any_sync(0xffffffffu, d);
     int leader = __ffs(peers) - 1;
     uint32_t cur = 0;
@@ -95,7 +120,7 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t
   for (int r = 0; r < RS_ROUNDS; ++r) {
     int64_t i = base + r * 32 + lane;
     if (i < n) {
-      unsigned d = (unsigned)((k[r] >> shift) & 255);
+      unsigned d = dg[r];
       uint32_t pos = wcnt[w][d] + rk[r];
       kout[pos] = k[r];
       vout[pos] = v[r];
@@ -103,33 +128,43 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t
   }
 }
 
-// Sorts keys/vals in place (ping-pong through k2/v2).  60-bit keys: 8 passes.
+// Sorts keys/vals in place (ping-pong through k2/v2): 8 passes over the 60-bit Morton keys,
+// then, for a batch (nprob > 1), 1 or 2 passes over the problem index of each element's
+// caller index (stable, so each problem's points stay in Morton order).
 static void radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* k2, uint32_t* v2, uint32_t* hist,
-                       int64_t n, cudaStream_t st) {
+                       int64_t n, const int64_t* poff, int nprob, cudaStream_t st) {
   if (n <= 1) return;
   int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
   uint64_t *ka = keys, *kb = k2;
   uint32_t *va = vals, *vb = v2;
-  for (int pass = 0; pass < 8; ++pass) {
-    int shift = pass * 8;
-    KL k_radix_hist<<<nblk, RS_THREADS, 0, st>>>(ka, n, shift, hist, nblk);
+  int npass = 8 + (nprob > 1 ? (nprob > 256 ? 2 : 1) : 0);
+  for (int pass = 0; pass < npass; ++pass) {
+    bool by_prob = pass >= 8;
+    int shift = by_prob ? (pass - 8) * 8 : pass * 8;
+    const int64_t* po = by_prob ? poff : nullptr;
+    KL k_radix_hist<<<nblk, RS_THREADS, 0, st>>>(ka, va, n, shift, po, nprob, hist, nblk);
     scan_excl<uint32_t>(hist, hist, (int64_t)256 * nblk, nullptr, hist + 256 * (int64_t)nblk,
                         nullptr, st);
-    KL k_radix_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, hist, nblk);
+    KL k_radix_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, po, nprob, hist, nblk);
     std::swap(ka, kb);
     std::swap(va, vb);
   }
-  // 8 passes: the result is back in (keys, vals)
+  if (npass & 1) {  // the result sits in (k2, v2)
+    cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
 // Level-by-level refinement.  Level l holds up to cap[l] boxes at bld_* + cap_off[l].
 struct BuildArgs {
   uint64_t* key;
-  int *sb, *se, *tb, *te, *parent, *child, *cnt, *nch, *choff, *cb, *ctb;
+  int *sb, *se, *tb, *te, *parent, *child, *cnt, *nch, *choff, *cb, *ctb, *prob;
   const uint64_t* skey;
   const uint64_t* tkey;
-  int same, q;
+  const int64_t* soff;   // [nprob + 1] source offsets of the problems
+  const int64_t* toff;   // [nprob + 1] target offsets
+  int same, q, nprob;
   int64_t cap_off[MAX_LEVELS + 1];
   int cap[MAX_LEVELS];
 };
@@ -145,16 +180,19 @@ __device__ inline int lower_bound_prefix(const uint64_t* k, int lo, int hi, uint
   return lo;
 }
 
-__global__ void k_root(BuildArgs a, int ns, int nt) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    a.key[0] = 0;
-    a.sb[0] = 0;
-    a.se[0] = ns;
-    a.tb[0] = 0;
-    a.te[0] = nt;
-    a.parent[0] = -1;
-    for (int l = 0; l < MAX_LEVELS; ++l) a.cnt[l] = l == 0 ? 1 : 0;
+// Level 0: one root per problem, holding that problem's slice of the sorted points.
+__global__ void k_root(BuildArgs a) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.nprob; k += gridDim.x * blockDim.x) {
+    a.key[k] = 0;
+    a.sb[k] = (int)a.soff[k];
+    a.se[k] = (int)a.soff[k + 1];
+    a.tb[k] = a.same ? (int)a.soff[k] : (int)a.toff[k];
+    a.te[k] = a.same ? (int)a.soff[k + 1] : (int)a.toff[k + 1];
+    a.parent[k] = -1;
+    a.prob[k] = k;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (int l = 0; l < MAX_LEVELS; ++l) a.cnt[l] = l == 0 ? a.nprob : 0;
 }
 
 __global__ void k_split(BuildArgs a, int lv, unsigned* status) {
@@ -223,6 +261,7 @@ __global__ void k_emit(BuildArgs a, int lv) {
           a.tb[h] = a.same ? b0 : t0;
           a.te[h] = a.same ? b1 : t1;
           a.parent[h] = i;
+          a.prob[h] = a.prob[g];
           c = j;
           ++j;
         }
@@ -239,13 +278,14 @@ struct Layout {
 
 __global__ void k_compact(BuildArgs a, Layout lay, int nbox, uint64_t* key, int8_t* level,
                           int* parent, int* child, int* sb, int* se, int* tb, int* te,
-                          int8_t* leaf) {
+                          int8_t* leaf, int* prob) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nbox; g += gridDim.x * blockDim.x) {
     int lv = 0;
     while (lv + 1 < MAX_LEVELS && g >= lay.lvl_start[lv + 1]) ++lv;
     int i = g - lay.lvl_start[lv];
     int64_t h = lay.cap_off[lv] + i;
     key[g] = a.key[h];
+    prob[g] = a.prob[h];
     level[g] = (int8_t)lv;
     parent[g] = lv > 0 ? lay.lvl_start[lv - 1] + a.parent[h] : -1;
     sb[g] = a.sb[h];
@@ -270,29 +310,33 @@ __device__ inline void anchor_of(uint64_t k, int& x, int& y, int& z) {
   z = (int)compact3(k >> 2);
 }
 
-__device__ inline int find_box(const TreeView& t, int lv, int ax, int ay, int az) {
+// Box of problem pb at level lv with anchor (ax, ay, az), or -1.  A level is ordered by
+// (problem, Morton key).
+__device__ inline int find_box(const TreeView& t, int lv, int pb, int ax, int ay, int az) {
   if (lv >= t.nlevels) return -1;
   uint64_t k = morton3((uint32_t)ax, (uint32_t)ay, (uint32_t)az);
   int lo = t.lvl_start[lv], hi = t.lvl_start[lv + 1], end = hi;
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
-    if (t.key[mid] < k)
+    int pm = t.prob[mid];
+    if (pm < pb || (pm == pb && t.key[mid] < k))
       lo = mid + 1;
     else
       hi = mid;
   }
-  return (lo < end && t.key[lo] == k) ? lo : -1;
+  return (lo < end && t.prob[lo] == pb && t.key[lo] == k) ? lo : -1;
 }
 
-// Deepest existing box at level <= lv that contains cell (lv, a).  The root always exists.
-__device__ inline int deepest_box(const TreeView& t, int lv, int ax, int ay, int az) {
+// Deepest existing box of problem pb at level <= lv that contains cell (lv, a).  The roots
+// always exist: root of problem pb is box pb.
+__device__ inline int deepest_box(const TreeView& t, int lv, int pb, int ax, int ay, int az) {
   int top = lv < t.nlevels - 1 ? lv : t.nlevels - 1;
   for (int l = top; l >= 0; --l) {
     int sh = lv - l;
-    int b = find_box(t, l, ax >> sh, ay >> sh, az >> sh);
+    int b = find_box(t, l, pb, ax >> sh, ay >> sh, az >> sh);
     if (b >= 0) return b;
   }
-  return 0;
+  return pb;
 }
 
 // Neighbour cell a + d at level lv: wraps (periodic) or reports absence.  s: image shift.
@@ -335,6 +379,7 @@ template <bool FILL>
 __global__ void k_lists(TreeView t, ListOut o) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x) {
     int lv = t.level[b];
+    int pb = t.prob[b];
     int ax, ay, az;
     anchor_of(t.key[b], ax, ay, az);
     // ---- V: same-level boxes at the 189 offsets of the parent's neighbourhood
@@ -348,7 +393,7 @@ __global__ void k_lists(TreeView t, ListOut o) {
           int cx, cy, cz, sx, sy, sz;
           if (neighbour(t.periodic, lv, ax, ox, cx, sx) && neighbour(t.periodic, lv, ay, oy, cy, sy) &&
               neighbour(t.periodic, lv, az, oz, cz, sz)) {
-            int s = find_box(t, lv, cx, cy, cz);
+            int s = find_box(t, lv, pb, cx, cy, cz);
             if (s >= 0) e = pack_entry(s, shift_code(sx, sy, sz));
           }
         }
@@ -370,7 +415,7 @@ __global__ void k_lists(TreeView t, ListOut o) {
             !neighbour(t.periodic, lv, az, dz, cz, sz))
           continue;
         int sc = shift_code(sx, sy, sz);
-        int nb = deepest_box(t, lv, cx, cy, cz);
+        int nb = deepest_box(t, lv, pb, cx, cy, cz);
         int nl = t.level[nb];
         if (nl < lv) {  // a coarser box holds the cell: a leaf is a U neighbour
           if (!t.leaf[nb]) continue;
@@ -433,7 +478,7 @@ __global__ void k_lists(TreeView t, ListOut o) {
             !neighbour(t.periodic, lv - 1, py_, dy, cy, sy) ||
             !neighbour(t.periodic, lv - 1, pz_, dz, cz, sz))
           continue;
-        int nb = deepest_box(t, lv - 1, cx, cy, cz);
+        int nb = deepest_box(t, lv - 1, pb, cx, cy, cz);
         if (!t.leaf[nb]) continue;
         int nl = t.level[nb], qx, qy, qz;
         anchor_of(t.key[nb], qx, qy, qz);
@@ -500,6 +545,7 @@ TreeView Tree::view() const {
   v.nlevels = nlevels;
   v.periodic = 0;
   v.lvl_start = d_lvl_start.as<int>();
+  v.prob = prob.as<int>();
   v.key = key.as<uint64_t>();
   v.level = level.as<int8_t>();
   v.parent = parent.as<int>();
@@ -526,8 +572,8 @@ static int grid_for(int64_t n, int threads, int maxb = 152 * 8) {
   } while (0)
 
 // Sorts one point set: keys + permutation, sorted positions in the compute type.
-static int sort_points(Plan& P, const void* pts, int64_t n, int dtype, DevBuf& key, DevBuf& perm,
-                       DevBuf& k2, DevBuf& v2, DevBuf& pos) {
+static int sort_points(Plan& P, const void* pts, int64_t n, int dtype, const int64_t* d_off, int nprob,
+                       DevBuf& key, DevBuf& perm, DevBuf& k2, DevBuf& v2, DevBuf& pos) {
   Tree& T = P.tree;
   cudaStream_t st = P.stream;
   CK(key.reserve(sizeof(uint64_t) * (n + 1)));
@@ -546,7 +592,7 @@ static int sort_points(Plan& P, const void* pts, int64_t n, int dtype, DevBuf& k
       KL k_keys<float><<<g, 256, 0, st>>>((const float*)pts, n, P.origin[0], P.origin[1], P.origin[2],
                                         P.L, key.as<uint64_t>(), perm.as<uint32_t>(), status);
     radix_sort(key.as<uint64_t>(), perm.as<uint32_t>(), k2.as<uint64_t>(), v2.as<uint32_t>(),
-               T.s_hist.as<uint32_t>(), n, st);
+               T.s_hist.as<uint32_t>(), n, d_off, nprob, st);
   }
   size_t esz = P.fp64() ? sizeof(double4) : sizeof(float4);
   CK(pos.reserve(esz * (n + 1)));
@@ -571,31 +617,44 @@ static int sort_points(Plan& P, const void* pts, int64_t n, int dtype, DevBuf& k
   return 0;
 }
 
-int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, int dtype) {
+int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, int dtype, int n_prob,
+               const int64_t* src_off, const int64_t* trg_off) {
   Tree& T = P.tree;
   cudaStream_t st = P.stream;
   T.n_src = ns;
   T.n_trg = nt;
-  T.same = (x == y) && (ns == nt);
+  T.n_prob = n_prob;
+  T.src_off.assign(src_off, src_off + n_prob + 1);
+  T.trg_off.assign(trg_off, trg_off + n_prob + 1);
+  T.same = (x == y) && (ns == nt) && T.src_off == T.trg_off;
   T.dtype_pts = dtype;
   CK(T.status.reserve(64));
   CK(cudaMemsetAsync(T.status.p, 0, 64, st));
+  CK(T.d_src_off.reserve(sizeof(int64_t) * (n_prob + 1)));
+  CK(T.d_trg_off.reserve(sizeof(int64_t) * (n_prob + 1)));
+  CK(cudaMemcpyAsync(T.d_src_off.p, T.src_off.data(), sizeof(int64_t) * (n_prob + 1),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(T.d_trg_off.p, T.trg_off.data(), sizeof(int64_t) * (n_prob + 1),
+                     cudaMemcpyHostToDevice, st));
   cudaEventRecord(P.ev[0], st);
 
-  int rc = sort_points(P, y, ns, dtype, T.src_key, T.src_perm, T.s_keys2, T.s_vals2, T.src_pos);
+  int rc = sort_points(P, y, ns, dtype, T.d_src_off.as<int64_t>(), n_prob, T.src_key, T.src_perm,
+                       T.s_keys2, T.s_vals2, T.src_pos);
   if (rc) return rc;
   if (!T.same) {
-    rc = sort_points(P, x, nt, dtype, T.trg_key, T.trg_perm, T.t_keys2, T.t_vals2, T.trg_pos);
+    rc = sort_points(P, x, nt, dtype, T.d_trg_off.as<int64_t>(), n_prob, T.trg_key, T.trg_perm,
+                     T.t_keys2, T.t_vals2, T.trg_pos);
     if (rc) return rc;
   }
 
-  // per-level capacities: min(8^l, 8 * floor(N / (q + 1)) + 8)
+  // per-level capacities: n_prob roots; below, min(n_prob 8^l, 8 * floor(N / (q + 1)) + 8)
+  // (only a box with more than q points splits, into at most 8 children)
   int64_t npts = T.same ? ns : ns + nt;
   int64_t per = 8 * (npts / (P.q + 1)) + 8;
   BuildArgs a;
   int64_t off = 0;
   for (int l = 0; l < MAX_LEVELS; ++l) {
-    int64_t c = l < 8 ? std::min<int64_t>(per, 1ll << (3 * l)) : per;
+    int64_t c = l == 0 ? n_prob : (l < 8 ? std::min<int64_t>(per, (int64_t)n_prob << (3 * l)) : per);
     a.cap[l] = (int)c;
     a.cap_off[l] = off;
     off += c;
@@ -613,6 +672,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   CK(T.bld_cb.reserve(sizeof(int) * off * 9));
   CK(T.bld_ctb.reserve(sizeof(int) * off * 9));
   CK(T.bld_cnt.reserve(sizeof(int) * (MAX_LEVELS + 8)));
+  CK(T.bld_prob.reserve(sizeof(int) * off));
   a.key = T.bld_key.as<uint64_t>();
   a.sb = T.bld_sb.as<int>();
   a.se = T.bld_se.as<int>();
@@ -625,13 +685,17 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   a.choff = T.bld_choff.as<int>();
   a.cb = T.bld_cb.as<int>();
   a.ctb = T.bld_ctb.as<int>();
+  a.prob = T.bld_prob.as<int>();
+  a.soff = T.d_src_off.as<int64_t>();
+  a.toff = T.d_trg_off.as<int64_t>();
+  a.nprob = n_prob;
   a.skey = T.src_key.as<uint64_t>();
   a.tkey = T.same ? a.skey : T.trg_key.as<uint64_t>();
   a.same = T.same ? 1 : 0;
   a.q = P.q;
   unsigned* status = T.status.as<unsigned>();
   int* d_total = a.cnt + MAX_LEVELS + 1;
-  KL k_root<<<1, 32, 0, st>>>(a, (int)ns, (int)(T.same ? ns : nt));
+  KL k_root<<<grid_for(n_prob, 256), 256, 0, st>>>(a);
   for (int l = 0; l < MAX_LEVEL; ++l) {
     int g = grid_for(a.cap[l], 256);
     KL k_split<<<g, 256, 0, st>>>(a, l, status);
@@ -675,13 +739,14 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   CK(T.tb.reserve(sizeof(int) * nb));
   CK(T.te.reserve(sizeof(int) * nb));
   CK(T.leaf.reserve(nb));
+  CK(T.prob.reserve(sizeof(int) * nb));
   CK(T.d_lvl_start.reserve(sizeof(int) * (MAX_LEVELS + 1)));
   CK(cudaMemcpyAsync(T.d_lvl_start.p, T.lvl_start, sizeof(int) * (MAX_LEVELS + 1),
                      cudaMemcpyHostToDevice, st));
   KL k_compact<<<grid_for(nb, 256), 256, 0, st>>>(a, lay, nb, T.key.as<uint64_t>(), T.level.as<int8_t>(),
                                               T.parent.as<int>(), T.child.as<int>(), T.sb.as<int>(),
                                               T.se.as<int>(), T.tb.as<int>(), T.te.as<int>(),
-                                              T.leaf.as<int8_t>());
+                                              T.leaf.as<int8_t>(), T.prob.as<int>());
   // leaf list (box order)
   CK(T.leaves.reserve(sizeof(int) * (2 * nb + nb / SCAN_TILE + 64)));
   int* lpos = T.leaves.as<int>() + nb;

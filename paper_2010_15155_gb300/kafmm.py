@@ -52,6 +52,7 @@ def lib():
             "kafmm_set_option": ([vp, i32, i64], i32),
             "kafmm_set_domain": ([vp, ctypes.POINTER(dbl), dbl], i32),
             "kafmm_set_points": ([vp, vp, i64, vp, i64, i32], i32),
+            "kafmm_set_points_batched": ([vp, i32, vp, vp, vp, vp, i32], i32),
             "kafmm_eval": ([vp, vp, vp, i32], i32),
             "kafmm_rpy_velocity": ([vp, vp, vp, vp, vp, i32], i32),
             "kafmm_rpy_velocity_noalloc": ([vp, vp, vp, vp, vp, i32], i32),
@@ -126,6 +127,15 @@ def kafmm_set_points(plan, y, n_src, x, n_trg, dtype):
     _check(plan, lib().kafmm_set_points(plan, _ptr(y), n_src, _ptr(x), n_trg, dtype))
 
 
+def kafmm_set_points_batched(plan, n_prob, src_offsets, trg_offsets, y, x, dtype):
+    so = np.ascontiguousarray(src_offsets, dtype=np.int64)
+    to = np.ascontiguousarray(trg_offsets, dtype=np.int64)
+    if so.size != n_prob + 1 or to.size != n_prob + 1:
+        raise ValueError("offsets must have n_prob + 1 entries")
+    _check(plan, lib().kafmm_set_points_batched(plan, n_prob, so.ctypes.data, to.ctypes.data,
+                                                _ptr(y), _ptr(x), dtype))
+
+
 def kafmm_eval(plan, s, g, dtype):
     _check(plan, lib().kafmm_eval(plan, _ptr(s), _ptr(g), dtype))
 
@@ -141,7 +151,8 @@ def kafmm_rpy_velocity_noalloc(plan, s, a, g, ua, dtype):
 def kafmm_tree_info(plan):
     info = (ctypes.c_int64 * 16)()
     _check(plan, lib().kafmm_tree_info(plan, info, 16))
-    keys = ["nbox", "nleaf", "nlevels", "n_u", "n_v", "n_w", "n_x", "near_pairs", "max_leaf_pts"]
+    keys = ["nbox", "nleaf", "nlevels", "n_u", "n_v", "n_w", "n_x", "near_pairs", "max_leaf_pts",
+            "n_prob"]
     return {k: int(info[i]) for i, k in enumerate(keys)}
 
 
@@ -224,6 +235,18 @@ class Plan:
             nt = _numel(x) // 3
         kafmm_set_points(self.h, y, ns, x, nt, dt)
         self.n_src, self.n_trg = ns, nt
+        return self
+
+    def set_points_batched(self, y, offsets, x=None, trg_offsets=None):
+        """Batch of independent problems: problem k owns rows offsets[k]:offsets[k+1]."""
+        dt = _dtype_code(y)
+        offsets = np.asarray(offsets, dtype=np.int64)
+        n_prob = offsets.size - 1
+        if x is None:
+            x, trg_offsets = y, offsets
+        trg_offsets = np.asarray(trg_offsets, dtype=np.int64)
+        kafmm_set_points_batched(self.h, n_prob, offsets, trg_offsets, y, x, dt)
+        self.n_src, self.n_trg = int(offsets[-1]), int(trg_offsets[-1])
         return self
 
     def eval(self, s, g=None):

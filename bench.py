@@ -233,6 +233,7 @@ def run_gpu(args):
 
     info = plan.info()
     ph = {k: float(np.median([p[k] for p in phases])) for k in phases[0]}
+    eval_only = eval_graph_timing(plan, s, g, stream, flush, args.steps)
     peaks, src = _peaks()
     # dominant kernel: M->L.  Algorithmic flops per launch = V translations x 2 n^2 x 4 columns.
     n = 6 * (P_ORDER - 1) ** 2 + 2
@@ -255,6 +256,10 @@ def run_gpu(args):
         achieved = m2l_flops / m2l_s / 1e12
         peak_note = "FP32 CUDA cores, 152 SM x 128 x 2 x max clock"
     st_gflops = info["near_pairs"] * FLOP_ST_PAIR / (ph["leaves"] * 1e-3) / 1e9
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    # tree build + lists: ~48 algorithmic bytes per point (coordinates read 12, keys 8 + 8,
+    # permutation 4 + 4, sorted coordinates 12) against the measured HBM copy bandwidth
+    tree_gbs = N_POINTS * 48 / ((ph["tree"] + ph["lists"]) * 1e-3) / 1e9
     launches = plan_launches(plan)
     line = {
         "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world,
@@ -269,6 +274,14 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "rel_l2_vs_fp64": err,
         "st_gflops": st_gflops,
+        "st_roofline": {"bound": "alu", "achieved": st_gflops / 1e3, "peak": fp32_peak,
+                        "unit": "TFLOP/s", "frac": st_gflops / 1e3 / fp32_peak,
+                        "note": "U-list pairs x 29 flop over the whole leaf phase (which also "
+                                "runs L->T); FP32 peak 152 SM x 128 x 2 x max clock"},
+        "tree_roofline": {"bound": "hbm", "achieved": tree_gbs, "peak": peaks["hbm_gbs"],
+                          "unit": "GB/s", "frac": tree_gbs / peaks["hbm_gbs"],
+                          "note": "48 B/point over tree + lists time; launch-latency bound"},
+        "eval_only": eval_only,
         "phases_ms": ph,
         "tree": info,
         "roofline": {"bound": bound, "kernel": "m2l", "achieved": achieved, "peak": peak,
@@ -426,6 +439,38 @@ def run_gpu_batched(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def eval_graph_timing(plan, s, g, stream, flush, steps):
+    """kafmm_eval alone for the current points, captured once in a CUDA graph (the plan in
+    asynchronous mode) and replayed; per replay CUDA-event time with L2 flushed in between."""
+    import torch
+
+    from paper_2010_15155_gb300 import kafmm as K
+    K.kafmm_set_option(plan.h, K.OPT_SYNC, 0)
+    K.kafmm_eval(plan.h, s, g, K.F32)   # every buffer exists before the capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        K.kafmm_set_option(plan.h, K.OPT_STREAM, torch.cuda.current_stream().cuda_stream)
+        K.kafmm_eval(plan.h, s, g, K.F32)
+    K.kafmm_set_option(plan.h, K.OPT_STREAM, stream.cuda_stream)
+    times = []
+    for i in range(max(3, steps)):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    K.kafmm_status(plan.h)
+    K.kafmm_set_option(plan.h, K.OPT_SYNC, 1)
+    del graph
+    ms = float(np.mean(times))
+    n = g.shape[0]
+    return {"value": n / (ms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms": ms,
+            "how": "kafmm_eval captured once in a CUDA graph and replayed (tree kept)"}
 
 
 def plan_uses_tc(plan):

@@ -87,7 +87,14 @@ enum {
    * 4.7e-6..5.7e-6 for p = 6..10; BF16x3 4.2e-5 (p = 6), 1.1e-5 (p = 8), 6.6e-6 (p = 10),
    * 7e-6 against the direct sum at p = 12, at about 0.7x the time.  AUTO takes BF16x3 for
    * p >= 10 and TF32x3 below. */
-  KAFMM_OPT_TC_SPLIT = 6
+  KAFMM_OPT_TC_SPLIT = 6,
+  /* 1 (default): kafmm_eval synchronises the plan's stream before it returns and reports a
+   * device-side timeout as KAFMM_ERR_TIMEOUT.  0: with device arrays kafmm_eval only enqueues
+   * work on the plan's stream and returns (no host synchronisation, no device allocation after
+   * the first call for the current points), so a second and later call can be captured into a
+   * CUDA graph and replayed; device-side timeouts then accumulate in a status word that
+   * kafmm_status reports.  Host arrays are always handled synchronously. */
+  KAFMM_OPT_SYNC = 7
 };
 enum { KAFMM_TC_TF32X3 = 0, KAFMM_TC_BF16X3 = 1, KAFMM_TC_AUTO = 2 };
 enum { KAFMM_PREC_FP64 = 0, KAFMM_PREC_FP32 = 1, KAFMM_PREC_MIXED = 2 };
@@ -150,6 +157,11 @@ int kafmm_set_points_batched(kafmm_plan_t plan, int n_prob, const int64_t* src_o
  * Upward pass S->M, M->M; downward pass M->L (V), S->L (X), L->L; leaves L->T, M->T (W),
  * S->T (U) -- Sec. II, Fig. kifmmgraph. */
 int kafmm_eval(kafmm_plan_t plan, const void* s, void* g, int dtype);
+
+/* Synchronises the plan's stream and reports (then clears) the device status accumulated by
+ * asynchronous kafmm_eval calls (KAFMM_OPT_SYNC = 0): KAFMM_ERR_TIMEOUT if a bounded device
+ * wait expired in any of them, else 0. */
+int kafmm_status(kafmm_plan_t plan);
 
 /* RPY only (Eq. RPYtrgvel and the overlap post-processing of Sec. II.B): from the kernel
  * sum g = [u, lap u] ([n_trg][6], as returned by kafmm_eval) and the target radii a

@@ -155,6 +155,9 @@ extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
     case KAFMM_OPT_KAHAN:
       P.kahan = value ? 1 : 0;
       return 0;
+    case KAFMM_OPT_SYNC:
+      P.sync = value ? 1 : 0;
+      return 0;
     case KAFMM_OPT_TC_SPLIT:
       if (value != KAFMM_TC_TF32X3 && value != KAFMM_TC_BF16X3 && value != KAFMM_TC_AUTO)
         return fail(P, KAFMM_ERR_ARG, "bad tensor-core split %lld", (long long)value);
@@ -269,15 +272,31 @@ extern "C" int kafmm_eval(kafmm_plan_t pl, const void* s, void* g, int dtype) {
     CKP(P.io_out.reserve(es * P.kt * P.tree.n_trg));
     gd = P.io_out.p;
   }
-  CKP(cudaMemsetAsync(P.tree.status.p, 0, 4, P.stream));
+  // synchronous calls clear the status word and check it at the end; asynchronous ones leave
+  // it sticky for kafmm_status (no host synchronisation, so the call can be stream-captured)
+  bool check = P.sync || host_out;
+  if (check) CKP(cudaMemsetAsync(P.tree.status.p, 0, 4, P.stream));
   long long l0 = g_launches;
   rc = evaluate(P, sd, gd, dtype);
   P.launches_eval = g_launches - l0;
   if (rc) return rc;
   if (host_out)
     CKP(cudaMemcpyAsync(g, gd, es * P.kt * P.tree.n_trg, cudaMemcpyDeviceToHost, P.stream));
+  if (!check) return 0;
   unsigned st = 0;
   CKP(cudaMemcpyAsync(&st, P.tree.status.p, 4, cudaMemcpyDeviceToHost, P.stream));
+  CKP(cudaStreamSynchronize(P.stream));
+  if (st & ST_TIMEOUT) return fail(P, KAFMM_ERR_TIMEOUT, "a bounded device wait expired");
+  return 0;
+}
+
+extern "C" int kafmm_status(kafmm_plan_t pl) {
+  PLAN_CHECK(pl);
+  if (!P.tree.status.p) return 0;
+  unsigned st = 0;
+  CKP(cudaMemcpyAsync(&st, P.tree.status.p, 4, cudaMemcpyDeviceToHost, P.stream));
+  CKP(cudaStreamSynchronize(P.stream));
+  CKP(cudaMemsetAsync(P.tree.status.p, 0, 4, P.stream));
   CKP(cudaStreamSynchronize(P.stream));
   if (st & ST_TIMEOUT) return fail(P, KAFMM_ERR_TIMEOUT, "a bounded device wait expired");
   return 0;

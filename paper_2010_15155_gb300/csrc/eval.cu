@@ -202,6 +202,7 @@ struct GemmArgs {
 
 template <int C>
 struct GemmShape { static constexpr int NB = 64 / C; };
+constexpr int GEMM_BM = 128;   // operator rows per CTA of k_gemm
 
 __device__ inline void m2l_slot_offset(int k, int cls, int& ox, int& oy, int& oz) {
   ox = k % 6 - 2 - (cls & 1);
@@ -209,18 +210,33 @@ __device__ inline void m2l_slot_offset(int k, int cls, int& ox, int& oy, int& oz
   oz = k / 36 - 2 - ((cls >> 2) & 1);
 }
 
-template <class T, int C>
-__global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> a) {
+// Gather-GEMM on the CUDA cores: out[box] (+)= sum over slots of op_slot (R x R) times the
+// slot's source column block (R x C, the four-channel block re-referenced to the target
+// centre).  A CTA owns 128 rows x 64 columns (64 / C boxes of one octant class); each thread
+// an 8 x 4 register tile (8 rows, one box's four channels when C = 4); operator and source
+// chunks of BK k-values are double-buffered in shared memory (loads of chunk c + 1 in flight
+// while chunk c is multiplied).  FP32 M->L: three-level summation (BK-term chunk -> slot ->
+// total), so no single FP32 accumulator runs over all 189 x R terms; the other modes (at most
+// 8 slots) sum BK-term chunks into the total.
+template <class T, int C, bool M2L>
+__global__ void __launch_bounds__(256, M2L ? 1 : 2) k_gemm(GemmArgs<T> a) {
   using T4 = typename V4<T>::type;
-  constexpr int NB = GemmShape<C>::NB, BM = 64, BN = 64, BK = 16;
-  __shared__ T As[BK][BM + 4];
-  __shared__ T Bs[BK][BN + 4];
+  // the per-slot partial level of the summation is kept for the 189-slot M->L sums only; the
+  // other modes have at most 8 slots (and run two CTAs per SM in the registers saved)
+  constexpr bool THREE = sizeof(T) == 4 && M2L;
+  constexpr int NB = GemmShape<C>::NB, BM = GEMM_BM, BN = 64, BK = sizeof(T) == 4 ? 16 : 8, TM = 8,
+                TN = 4;
+  constexpr int AP = BM + 4, BP = BN + 4;               // padded rows (bank spread, 16 B aligned)
+  constexpr int A_PER = BM * BK / 256;                  // operator loads per thread per chunk
+  constexpr int B_PER = C == 4 ? (BK * NB + 255) / 256 : BK * NB / 256;
+  __shared__ __align__(16) T As[2][BK][AP];
+  __shared__ __align__(16) T Bs[2][BK][BP];
   __shared__ int ob[NB], srcb[NB];
   __shared__ T dcx[NB], dcy[NB], dcz[NB], alph[NB];
-  int4 tile = a.tiles[blockIdx.x];
-  int row0 = blockIdx.y * BM;
-  int cls = tile.z;
-  int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int4 tile = a.tiles[blockIdx.x];
+  const int row0 = blockIdx.y * BM;
+  const int cls = tile.z;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   if (tid < NB) {
     int b = tid < tile.y ? a.boxlist[tile.x + tid] : -1;
     ob[tid] = b;
@@ -230,13 +246,14 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> a) {
     alph[tid] = al;
   }
   __syncthreads();
-  T acc[4][4];
+  T acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
-  int nslots = a.mode == GM_M2L ? 216 : (a.mode == GM_M2M ? 8 : 1);
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0;
+  const int nslots = a.mode == GM_M2L ? 216 : (a.mode == GM_M2M ? 8 : 1);
   const int R = a.R;
+  const int nch = (R + BK - 1) / BK;
   for (int k = 0; k < nslots; ++k) {
     int op = 0;
     int ox = 0, oy = 0, oz = 0;
@@ -288,82 +305,138 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> a) {
     }
     if (!__syncthreads_or(has)) continue;
     const T* opp = a.ops + (int64_t)op * R * R;
-    // three-level summation (16-term tile -> slot -> total), so no single FP32 accumulator
-    // runs over all 189 x R terms of an M->L sum
-    T part[4][4];
+    T ra[A_PER];
+    T4 rb4[C == 4 ? B_PER : 1];
+    T rb1[C == 4 ? 1 : B_PER];
+    // global -> registers for chunk ch (zero outside R)
+    auto load = [&](int ch) {
+      int k0 = ch * BK;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) part[i][j] = 0;
-    for (int k0 = 0; k0 < R; k0 += BK) {
-      // A tile: rows row0.., cols k0..  (As[kk][row])
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int e = tid * 4 + q;
+      for (int q = 0; q < A_PER; ++q) {
+        int e = q * 256 + tid;
         int row = e / BK, kk = e % BK;
         int gr = row0 + row, gk = k0 + kk;
-        As[kk][row] = (gr < R && gk < R) ? opp[(int64_t)gr * R + gk] : T(0);
+        ra[q] = (gr < R && gk < R) ? __ldg(opp + (int64_t)gr * R + gk) : T(0);
       }
-      if (C == 4) {
-        int kk = tid / 16, j = tid % 16;
-        int gk = k0 + kk;
-        int s = srcb[j];
-        T4 v;
-        if (s >= 0 && gk < R) {
-          v = reinterpret_cast<const T4*>(a.in)[(int64_t)s * R + gk];
-          v.w = v.w + dcx[j] * v.x + dcy[j] * v.y + dcz[j] * v.z;
-        } else {
-          v.x = v.y = v.z = v.w = 0;
+      if constexpr (C == 4) {
+#pragma unroll
+        for (int q = 0; q < B_PER; ++q) {
+          int e = q * 256 + tid;
+          int kk = e / NB, j = e % NB;
+          int gk = k0 + kk;
+          int sb = (kk < BK) ? srcb[j] : -1;
+          T4 v;
+          if (sb >= 0 && gk < R) {
+            const T4* src = reinterpret_cast<const T4*>(a.in) + (int64_t)sb * R + gk;
+            if constexpr (sizeof(T) == 4)
+              v = __ldg(src);
+            else
+              v = *src;
+            v.w = v.w + dcx[j] * v.x + dcy[j] * v.y + dcz[j] * v.z;
+          } else {
+            v.x = v.y = v.z = v.w = 0;
+          }
+          rb4[q] = v;
         }
-        Bs[kk][j * 4 + 0] = v.x;
-        Bs[kk][j * 4 + 1] = v.y;
-        Bs[kk][j * 4 + 2] = v.z;
-        Bs[kk][j * 4 + 3] = v.w;
       } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          int j = tid & 63, kk = (tid >> 6) + 4 * q;
-          int gk = k0 + kk, s = srcb[j];
-          Bs[kk][j] = (s >= 0 && gk < R) ? a.in[(int64_t)s * R + gk] : T(0);
+        for (int q = 0; q < B_PER; ++q) {
+          int e = q * 256 + tid;
+          int kk = e / NB, j = e % NB;
+          int gk = k0 + kk, sb = srcb[j];
+          rb1[q] = (sb >= 0 && gk < R) ? __ldg(a.in + (int64_t)sb * R + gk) : T(0);
         }
       }
-      __syncthreads();
-      T chunk[4][4];
+    };
+    auto store = [&](int buf) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int q = 0; q < A_PER; ++q) {
+        int e = q * 256 + tid;
+        As[buf][e % BK][e / BK] = ra[q];
+      }
+      if constexpr (C == 4) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) chunk[i][j] = 0;
+        for (int q = 0; q < B_PER; ++q) {
+          int e = q * 256 + tid;
+          int kk = e / NB, j = e % NB;
+          if (kk < BK) *reinterpret_cast<T4*>(&Bs[buf][kk][j * 4]) = rb4[q];
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < B_PER; ++q) {
+          int e = q * 256 + tid;
+          Bs[buf][e / NB][e % NB] = rb1[q];
+        }
+      }
+    };
+    T part[THREE ? TM : 1][THREE ? TN : 1];
+    if constexpr (THREE) {
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) part[i][j] = 0;
+    }
+    load(0);
+    store(0);
+    __syncthreads();
+    for (int ch = 0; ch < nch; ++ch) {
+      const int buf = ch & 1;
+      if (ch + 1 < nch) load(ch + 1);
+      T chunk[TM][TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) chunk[i][j] = 0;
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        T av[4], bv[4];
+        T av[TM], bv[TN];
+        if constexpr (sizeof(T) == 4) {
+          float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * TM]);
+          float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * TM + 4]);
+          float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * TN]);
+          av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
+          av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
+          bv[0] = b0.x; bv[1] = b0.y; bv[2] = b0.z; bv[3] = b0.w;
+        } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+          for (int i = 0; i < TM; ++i) av[i] = As[buf][kk][ty * TM + i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+          for (int j = 0; j < TN; ++j) bv[j] = Bs[buf][kk][tx * TN + j];
+        }
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) chunk[i][j] += av[i] * bv[j];
+          for (int j = 0; j < TN; ++j) chunk[i][j] = fma(av[i], bv[j], chunk[i][j]);
       }
+      if constexpr (THREE) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) part[i][j] += chunk[i][j];
+          for (int j = 0; j < TN; ++j) part[i][j] += chunk[i][j];
+      } else {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] += chunk[i][j];
+      }
+      if (ch + 1 < nch) store(buf ^ 1);
       __syncthreads();
     }
+    if constexpr (THREE) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] += part[i][j];
+        for (int j = 0; j < TN; ++j) acc[i][j] += part[i][j];
+    }
   }
-  bool accumulate = a.mode == GM_M2L || a.mode == GM_L2L;
+  const bool accumulate = a.mode == GM_M2L || a.mode == GM_L2L;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int row = row0 + ty * 4 + i;
+  for (int i = 0; i < TM; ++i) {
+    int row = row0 + ty * TM + i;
     if (row >= R) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int col = tx * 4 + j;
+    for (int j = 0; j < TN; ++j) {
+      int col = tx * TN + j;
       int bj = col / C, c = col % C;
       int b = ob[bj];
       if (b < 0) continue;
@@ -746,10 +819,15 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
   for (int b = 0; b < nb; ++b)
     if (lvl[b] >= vmin) by_cls[cls(b)].push_back(b);
   add_tiles(W, by_cls, NB_TC, W.m2l);
-  // M->M per level: non-leaf boxes (class irrelevant: use class 0 bucket)
+  // M->M per level: non-leaf boxes (class irrelevant: use class 0 bucket).  Multipoles are
+  // read by M->L (levels >= vmin), by M->T over W lists (W entries lie at level >= 2) and, when
+  // periodic, at the root; with the open boundary levels 0 and 1 are never read, so their M->M
+  // is skipped.
   for (int l = 0; l < MAX_LEVELS; ++l) {
-    for (int b = T.lvl_start[l]; b < T.lvl_start[l + 1]; ++b)
-      if (!leaf[b]) by_cls[0].push_back(b);
+    bool needed = l >= vmin || (P.bc == KAFMM_BC_PXYZ && l == 0);
+    if (needed)
+      for (int b = T.lvl_start[l]; b < T.lvl_start[l + 1]; ++b)
+        if (!leaf[b]) by_cls[0].push_back(b);
     add_tiles(W, by_cls, NB, W.m2m[l]);
   }
   // L->L per level (levels >= vmin + 1; and level 1 from the root when periodic)
@@ -867,7 +945,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
     ga.vtab = T_.vtab.as<int32_t>();
     ga.R = R;
     dim3 blk(256);
-    int rb = (R + 63) / 64;
+    int rb = (R + GEMM_BM - 1) / GEMM_BM;
     for (int l = MAX_LEVELS - 1; l >= 0; --l) {
       int n = W.m2m[l][1] - W.m2m[l][0];
       if (n <= 0) continue;
@@ -875,7 +953,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       ga.in = P.up_check.as<T>();
       ga.out = P.up_check.as<T>();
       ga.tiles = P.tiles.as<int4>() + W.m2m[l][0];
-      KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+      KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
     }
     // periodic: far images of the root's multipole density -> root's downward check
     if (W.root[1] > W.root[0]) {
@@ -885,7 +963,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       ga.op = OP_PER;
       ga.scale_r = 0;
       ga.tiles = P.tiles.as<int4>() + W.root[0];
-      KL k_gemm<T, C><<<dim3(1, rb), blk, 0, st>>>(ga);
+      KL k_gemm<T, C, false><<<dim3(1, rb), blk, 0, st>>>(ga);
     }
     cudaEventRecord(P.ev[4], st);
     // M->L over the V lists (all levels)
@@ -899,7 +977,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
         ga.in = P.up_check.as<T>();
         ga.out = P.dn_check.as<T>();
         ga.tiles = P.tiles.as<int4>() + W.m2l[0];
-        KL k_gemm<T, C><<<dim3(nm2l, rb), blk, 0, st>>>(ga);
+        KL k_gemm<T, C, true><<<dim3(nm2l, rb), blk, 0, st>>>(ga);
       }
     }
     cudaEventRecord(P.ev[5], st);
@@ -918,7 +996,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       ga.in = P.dn_check.as<T>();
       ga.out = P.dn_check.as<T>();
       ga.tiles = P.tiles.as<int4>() + W.l2l[l][0];
-      KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+      KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
     }
     // equivalent densities where they are evaluated at targets: r * V * ((S^+ U^T) * check),
     // the two factors applied in turn (tmp = the downward equivalent buffer of the up pass
@@ -931,12 +1009,12 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       ga.out = P.dn_equiv.as<T>();
       ga.op = OP_UP1;
       ga.scale_r = 0;
-      KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+      KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
       ga.in = P.dn_equiv.as<T>();
       ga.out = P.up_equiv.as<T>();
       ga.op = OP_UP2;
       ga.scale_r = 1;
-      KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+      KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
     }
     n = W.pdn[1] - W.pdn[0];
     if (n > 0) {
@@ -946,12 +1024,12 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       ga.out = P.up_check.as<T>();   // up_check is no longer needed here
       ga.op = OP_DN1;
       ga.scale_r = 0;
-      KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+      KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
       ga.in = P.up_check.as<T>();
       ga.out = P.dn_equiv.as<T>();
       ga.op = OP_DN2;
       ga.scale_r = 1;
-      KL k_gemm<T, C><<<dim3(n, rb), blk, 0, st>>>(ga);
+      KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
     }
   }
   cudaEventRecord(P.ev[6], st);

@@ -1,5 +1,5 @@
-// M->L translations on the tcgen05 tensor cores (sm_103a) in split precision (TF32x3 by
-// default, BF16x3 optionally) with FP32 accumulation in tensor memory.
+// M->L translations on the tcgen05 tensor cores (sm_103a) in split precision (BF16x3 or
+// TF32x3) with FP32 accumulation in tensor memory.
 //
 // The V list of a box B (Sec. II: children of the parent's colleagues not adjacent to B) lies
 // at up to 189 of the 316 offsets o in [-3,3]^3 \ [-1,1]^3; with the pseudo-inverse folded in,
@@ -8,8 +8,10 @@
 // class (4 channels each -> N = 256 columns) and accumulates
 //     D[rows, (box, ch)] = sum_o T_o[rows, :] * shift_o(up_check[box + o])[:, ch]
 // over all offsets.  A (the operator) arrives by TMA (128B swizzle, K-major); B (gathered,
-// re-referenced to the target centre and split into bf16 hi/lo) is written to shared memory
-// by producer warps in the same canonical layout.  Each operand is split x = hi + lo in the
+// re-referenced to the target centre and split into hi/lo) is written to shared memory by
+// producer warps in the same canonical layout: one warp per source box and k-chunk, each lane
+// two (bf16) or one (tf32) consecutive k of all four channels, so the gather is coalesced and
+// every 32-bit store instruction fills one whole swizzled 128-byte row (conflict-free).  Each operand is split x = hi + lo in the
 // MMA format (tf32 or bf16) and each product is taken as hi*hi + hi*lo + lo*hi.
 // Each offset is accumulated in a fresh TMEM accumulator and then added into a TMEM sum by
 // the epilogue warps, so no single FP32 accumulation chain spans all offsets.
@@ -182,6 +184,17 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
       : "memory");
 }
 
+// Read-only 256-bit load of two consecutive float4 (address 32-byte aligned).
+__device__ __forceinline__ void ld_nc_v8(const float4* p, float4& a, float4& b) {
+  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+               : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+               : "l"(p));
+}
+
+__device__ __forceinline__ void st_shared_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.b32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&v);
@@ -191,6 +204,7 @@ template <int SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_m2l_tc(const __grid_constant__ CUtensorMap tmap, Args a) {
   constexpr int BK = Fmt<SPLIT>::BK, MK = Fmt<SPLIT>::MK;
+  constexpr int PROD_WARPS = NPROD / 32;
   // offsets accumulated in TMEM before each drain into the running sum: longer chains lose
   // accuracy in TF32x3 (measured 5.4e-6 -> 8.2e-6 at p = 10 with 2), BF16x3 is limited by its
   // operand split instead
@@ -221,7 +235,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     bail = 0;
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], NPROD + 1);
+      mbar_init(&full[s], PROD_WARPS + 1);   // one arrival per producer warp + the TMA's
       mbar_init(&empty[s], 1);
     }
     mbar_init(&acc_full, 1);
@@ -289,79 +303,119 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp >= 4 && warp < W_TMA) {
     // ---------------- B producers: gather, re-reference, split, swizzle ----------------
-    // One item = one 16-byte chunk (KPL consecutive k) of the four channel rows of one box;
-    // the 8 lanes of a quarter warp take the 8 chunks of the same rows, which the 128-byte
-    // swizzle maps to 8 distinct bank groups (conflict-free stores).
-    constexpr int KPL = 16 / Fmt<SPLIT>::ES;  // k values per 16-byte chunk
-    const int pt = threadIdx.x - 128;
-    for (int it = 0; it < total; ++it) {
-      int st = it % STAGES;
-      if (it >= STAGES && !wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail)) break;
+    // Work unit = one target box j of the tile: the BK k-values of this chunk of its source
+    // box's four channels.  Lane l takes EPL consecutive k (two for bf16, one for tf32), i.e.
+    // one 32-bit word of each of the 8 rows (4 channels x hi/lo) at word l of the 128-byte
+    // row: the warp's loads are contiguous and each store instruction writes a full row.
+    constexpr int EPL = 4 / Fmt<SPLIT>::ES;          // k values per lane
+    constexpr int UPW = NB / PROD_WARPS;             // boxes per producer warp per chunk
+    constexpr int UH = UPW / 2;                      // boxes per half stage
+    const int pw = warp - 4;
+    // Box j = pw + 8u has rows n = 4j + ch = (4 pw + ch) + 32u: the 128-byte swizzle row of
+    // (u, ch) sits 4096 u bytes after that of (0, ch), and the chunk swizzle (n & 7) does not
+    // depend on u.  Word `lane` of row n: chunk (lane / 4) ^ (n & 7), word lane & 3.
+    uint32_t roff[4];
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+      int n = 4 * pw + ch;
+      roff[ch] = (uint32_t)((n >> 3) * 1024 + (n & 7) * 128 + ((((lane >> 2) ^ n) & 7) << 4) + (lane & 3) * 4);
+    }
+    // source box (flat index into up) of each of this warp's boxes for the current slot, or -1
+    int srcb[UPW];
+    int cur_slot = -1;
+    auto set_slot = [&](int s) {
+#pragma unroll
+      for (int u = 0; u < UPW; ++u) {
+        int b = sbox[pw + PROD_WARPS * u];
+        int32_t e = b >= 0 ? a.vtab[(int64_t)b * 216 + s] : LIST_EMPTY;
+        srcb[u] = e != LIST_EMPTY ? entry_box(e) : -1;
+      }
+    };
+    // Software pipeline over half stages (UH boxes each): the loads of the next half are in
+    // flight while the current half is converted, including the first half of the next stage
+    // (registers only: no shared-memory stage is needed to issue them).
+    auto load_half = [&](int it, int h, float4 (&q)[UH][EPL]) {
       int s = slot_list[it / nchunk], c = it % nchunk;
+      if (s != cur_slot) {
+        set_slot(s);
+        cur_slot = s;
+      }
+      const int k0 = c * BK + lane * EPL;
+      const bool kin = k0 < R;   // R and k0 even: a bf16 pair is all in or out
+#pragma unroll
+      for (int u = 0; u < UH; ++u) {
+        int sb = srcb[h * UH + u];
+        bool ok = sb >= 0 && kin;
+        const float4* p = reinterpret_cast<const float4*>(a.up) + (int64_t)(ok ? sb : 0) * R + k0;
+        if (EPL == 2) {
+          if (ok) {
+            ld_nc_v8(p, q[u][0], q[u][EPL - 1]);
+          } else {
+            q[u][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+            q[u][EPL - 1] = q[u][0];
+          }
+        } else {
+          q[u][0] = ok ? __ldg(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+    };
+    auto store_half = [&](int it, int h, const float4 (&q)[UH][EPL]) {
+      int s = slot_list[it / nchunk];
       float ox = (float)(s % 6 - 2 - (cls & 1)), oy = (float)((s / 6) % 6 - 2 - ((cls >> 1) & 1)),
             oz = (float)(s / 36 - 2 - ((cls >> 2) & 1));
-      unsigned char* bhi = smem + st * STAGE_BYTES + 2 * A_BYTES;
-      unsigned char* blo = bhi + B_BYTES;
-      constexpr int IPT = NB * 8 / NPROD;  // items per producer thread per chunk
-      float4 q[IPT][KPL];
-      float sh[IPT][3];
-      // issue every gather of this thread before converting (hides the L2 latency)
+      const int st = it % STAGES;
+      const uint32_t bhi = smem_u32(smem + st * STAGE_BYTES + 2 * A_BYTES);
+      const uint32_t blo = bhi + B_BYTES;
 #pragma unroll
-      for (int ii = 0; ii < IPT; ++ii) {
-        int item = pt + ii * NPROD;
-        int j = item >> 3, cidx = item & 7;
-        int b = sbox[j];
-        int32_t src = b >= 0 ? a.vtab[(int64_t)b * 216 + s] : LIST_EMPTY;
-        int k0 = c * BK + cidx * KPL;
-        sh[ii][0] = ox * sside[j];
-        sh[ii][1] = oy * sside[j];
-        sh[ii][2] = oz * sside[j];
-        const float4* p = src != LIST_EMPTY ? reinterpret_cast<const float4*>(a.up) +
-                                                  (int64_t)entry_box(src) * R + k0
-                                            : nullptr;
+      for (int u = 0; u < UH; ++u) {
+        const int uu = h * UH + u;
+        float side = sside[pw + PROD_WARPS * uu];
+        float sx = ox * side, sy = oy * side, sz = oz * side;
+        float v[4][EPL];
 #pragma unroll
-        for (int t = 0; t < KPL; ++t)
-          q[ii][t] = (p && k0 + t < R) ? __ldg(p + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int ii = 0; ii < IPT; ++ii) {
-        int item = pt + ii * NPROD;
-        int j = item >> 3, cidx = item & 7;
-        float v[4][KPL];
-#pragma unroll
-        for (int t = 0; t < KPL; ++t) {
-          v[0][t] = q[ii][t].x;
-          v[1][t] = q[ii][t].y;
-          v[2][t] = q[ii][t].z;
-          v[3][t] = q[ii][t].w + sh[ii][0] * q[ii][t].x + sh[ii][1] * q[ii][t].y + sh[ii][2] * q[ii][t].z;
+        for (int t = 0; t < EPL; ++t) {
+          v[0][t] = q[u][t].x;
+          v[1][t] = q[u][t].y;
+          v[2][t] = q[u][t].z;
+          v[3][t] = q[u][t].w + sx * q[u][t].x + sy * q[u][t].y + sz * q[u][t].z;
         }
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
-          int n = 4 * j + ch;
-          uint32_t off = (uint32_t)((n >> 3) * 1024 + (n & 7) * 128 + ((cidx ^ (n & 7)) << 4));
-          uint32_t hw[4], lw[4];
+          uint32_t hw, lw;
           if (SPLIT == SPLIT_TF32) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-              float h = tf32_rn(v[ch][t]);
-              hw[t] = __float_as_uint(h);
-              lw[t] = __float_as_uint(tf32_rn(v[ch][t] - h));
-            }
+            float hf = tf32_rn(v[ch][0]);
+            hw = __float_as_uint(hf);
+            lw = __float_as_uint(tf32_rn(v[ch][0] - hf));
           } else {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[ch][2 * t], v[ch][(2 * t + 1) % KPL]);
-              float2 hf = __bfloat1622float2(h2);
-              hw[t] = *reinterpret_cast<uint32_t*>(&h2);
-              lw[t] = pack_bf16(v[ch][2 * t] - hf.x, v[ch][(2 * t + 1) % KPL] - hf.y);
-            }
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[ch][0], v[ch][EPL - 1]);
+            float2 hf = __bfloat1622float2(h2);
+            hw = *reinterpret_cast<uint32_t*>(&h2);
+            lw = pack_bf16(v[ch][0] - hf.x, v[ch][EPL - 1] - hf.y);
           }
-          *reinterpret_cast<uint4*>(bhi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          *reinterpret_cast<uint4*>(blo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+          const uint32_t off = roff[ch] + 4096u * uu;
+          st_shared_u32(bhi + off, hw);
+          st_shared_u32(blo + off, lw);
         }
       }
+    };
+    float4 qa[UH][EPL], qb[UH][EPL];
+    if (total > 0) load_half(0, 0, qa);
+    for (int it = 0; it < total; ++it) {
+      int st = it % STAGES;
+      load_half(it, 1, qb);
+      // lane 0 waits for the stage to be free; the warp leaves the loop together on a timeout
+      int ok_wait = 1;
+      if (lane == 0 && it >= STAGES)
+        ok_wait = wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
+      store_half(it, 0, qa);
+      if (it + 1 < total) load_half(it + 1, 0, qa);
+      store_half(it, 1, qb);
+      // each lane orders its shared-memory writes before the async proxy (the MMAs) reads
+      // them; lane 0 then arrives once for the warp
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      arrive(&full[st]);
+      __syncwarp();
+      if (lane == 0) arrive(&full[st]);
     }
   } else if (warp == W_MMA) {
     // ---------------- MMA issue (one thread) ----------------
@@ -405,7 +459,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     float x[32], y[32];
     const int ngroups = (ns + DRAIN - 1) / DRAIN;
     for (int gi = 0; gi < ngroups; ++gi) {
-      if (!wait_parity(&acc_full, gi & 1, a.status, &bail)) break;
+      // lane 0 waits; the warp stays converged for the .sync.aligned TMEM accesses
+      int ok_wait = lane == 0 ? (wait_parity(&acc_full, gi & 1, a.status, &bail) ? 1 : 0) : 0;
+      if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       for (int q = 0; q < BN / 32; ++q) {
         tmem_ld32(tmem + lane_base + q * 32, x);
@@ -557,10 +613,11 @@ int m2l_tc_launch(Plan& P, const int4* tiles, int ntiles, const int* boxlist, cu
     a.nchunk = P.Rpad / tc::Fmt<SPLIT_BF16>::BK;
     KL tc::k_m2l_tc<SPLIT_BF16><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
   }
+  cudaError_t e;
   if (nsplit > 1)
     KL tc::k_combine_parts<<<std::min(ntiles, 152 * 4), 256, 0, st>>>(
         P.m2l_parts.as<float4>(), part_stride / 4, nsplit, P.dn_check.as<float4>(), tiles, ntiles, boxlist, P.R);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(P, e, "k_m2l_tc launch");
   return 0;
 }

@@ -69,6 +69,7 @@ struct Plan {
   // problem
   int kernel = 0, bc = 0, p = 0, q = 0;
   int prec = KAFMM_PREC_MIXED, variant = KAFMM_ML_L4, near_only = 0, kahan = 0;
+  int sync = 1;        // kafmm_eval synchronises and checks the device status (KAFMM_OPT_SYNC)
   cudaStream_t stream = 0;
   double origin[3] = {0, 0, 0}, L = 1.0;
   int ks = 1, kt = 1;

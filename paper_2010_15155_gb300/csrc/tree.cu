@@ -696,17 +696,29 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   unsigned* status = T.status.as<unsigned>();
   int* d_total = a.cnt + MAX_LEVELS + 1;
   KL k_root<<<grid_for(n_prob, 256), 256, 0, st>>>(a);
-  for (int l = 0; l < MAX_LEVEL; ++l) {
-    int g = grid_for(a.cap[l], 256);
-    KL k_split<<<g, 256, 0, st>>>(a, l, status);
-    int* scratch = a.choff + a.cap_off[MAX_LEVELS] + 16;
-    scan_excl<int>(a.nch + a.cap_off[l], a.choff + a.cap_off[l], a.cap[l], a.cnt + l, scratch, d_total,
-                   st);
-    KL k_level_total<<<1, 32, 0, st>>>(a, l, d_total, status);
-    KL k_emit<<<g, 256, 0, st>>>(a, l);
+  // levels in groups of 4; after each group the next level's box count is read back and the
+  // refinement stops once it is zero (a uniform tree of depth 4 takes 8 levels of launches,
+  // not 20)
+  int cnt[MAX_LEVELS];
+  constexpr int LEVEL_GROUP = 4;
+  for (int l0 = 0; l0 < MAX_LEVEL; l0 += LEVEL_GROUP) {
+    int l1 = std::min(MAX_LEVEL, l0 + LEVEL_GROUP);
+    for (int l = l0; l < l1; ++l) {
+      int g = grid_for(a.cap[l], 256);
+      KL k_split<<<g, 256, 0, st>>>(a, l, status);
+      int* scratch = a.choff + a.cap_off[MAX_LEVELS] + 16;
+      scan_excl<int>(a.nch + a.cap_off[l], a.choff + a.cap_off[l], a.cap[l], a.cnt + l, scratch,
+                     d_total, st);
+      KL k_level_total<<<1, 32, 0, st>>>(a, l, d_total, status);
+      KL k_emit<<<g, 256, 0, st>>>(a, l);
+    }
+    if (l1 >= MAX_LEVEL) break;
+    int next = 0;
+    CK(cudaMemcpyAsync(&next, a.cnt + l1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (next == 0) break;
   }
   CK(cudaGetLastError());
-  int cnt[MAX_LEVELS];
   unsigned h_status = 0;
   CK(cudaMemcpyAsync(cnt, a.cnt, sizeof(int) * MAX_LEVELS, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));

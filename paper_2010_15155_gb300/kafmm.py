@@ -22,6 +22,7 @@ LAPLACE, STOKESLET, RPY, STOKES_DL = 0, 1, 2, 3
 BC_OPEN, BC_PXYZ = 0, 3
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN, OPT_TC_SPLIT = 1, 2, 3, 4, 5, 6
+OPT_SYNC = 7
 TC_TF32X3, TC_BF16X3, TC_AUTO = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 ML_G, ML_L4 = 0, 1
@@ -54,6 +55,7 @@ def lib():
             "kafmm_set_points": ([vp, vp, i64, vp, i64, i32], i32),
             "kafmm_set_points_batched": ([vp, i32, vp, vp, vp, vp, i32], i32),
             "kafmm_eval": ([vp, vp, vp, i32], i32),
+            "kafmm_status": ([vp], i32),
             "kafmm_rpy_velocity": ([vp, vp, vp, vp, vp, i32], i32),
             "kafmm_rpy_velocity_noalloc": ([vp, vp, vp, vp, vp, i32], i32),
             "kafmm_tree_info": ([vp, ctypes.POINTER(i64), i32], i32),
@@ -140,6 +142,10 @@ def kafmm_eval(plan, s, g, dtype):
     _check(plan, lib().kafmm_eval(plan, _ptr(s), _ptr(g), dtype))
 
 
+def kafmm_status(plan):
+    _check(plan, lib().kafmm_status(plan))
+
+
 def kafmm_rpy_velocity(plan, s, a, g, ua, dtype):
     _check(plan, lib().kafmm_rpy_velocity(plan, _ptr(s), _ptr(a), _ptr(g), _ptr(ua), dtype))
 
@@ -212,7 +218,7 @@ class Plan:
 
     def __init__(self, kernel, p, q, bc=BC_OPEN, precision=PREC_MIXED, variant=ML_L4,
                  near_only=False, kahan=False, stream=None, origin=(0.0, 0.0, 0.0), L=1.0,
-                 tc_split=TC_AUTO):
+                 tc_split=TC_AUTO, sync=True):
         self.kernel = kernel
         self.ks, self.kt = KDIM[kernel]
         self.h = kafmm_plan(kernel, bc, p, q)
@@ -221,6 +227,7 @@ class Plan:
         kafmm_set_option(self.h, OPT_NEAR_ONLY, int(near_only))
         kafmm_set_option(self.h, OPT_KAHAN, int(kahan))
         kafmm_set_option(self.h, OPT_TC_SPLIT, tc_split)
+        kafmm_set_option(self.h, OPT_SYNC, int(sync))
         if stream is not None:
             kafmm_set_option(self.h, OPT_STREAM, int(stream))
         kafmm_set_domain(self.h, origin, L)

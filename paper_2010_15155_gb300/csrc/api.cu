@@ -207,7 +207,7 @@ static int set_points_impl(Plan& P, const void* y, int64_t ns, const void* x, in
   }
   rc = build_tree(P, yd, ns, xd, nt, dtype, n_prob, soff, toff);
   if (rc) return rc;
-  rc = build_worklists(P, 64 / P.C, P.use_tc ? 128 / P.C * 2 : 64 / P.C);
+  rc = build_worklists(P, 64 / P.C, P.use_tc ? TC_BOXES : 64 / P.C);
   if (rc) return rc;
   P.launches_points = g_launches;
   P.have_points = true;

@@ -16,6 +16,7 @@ extern thread_local long long g_launches;
 #define KL ++::kafmm::g_launches,
 
 constexpr int MAX_LEVEL = 20;        // finest octree level; keys carry 20 bits per axis
+constexpr int TC_BOXES = 32;         // target boxes per tile of the tensor-core M->L
 constexpr int MAX_LEVELS = MAX_LEVEL + 1;
 constexpr double PI = 3.14159265358979323846;
 

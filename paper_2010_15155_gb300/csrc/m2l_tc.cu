@@ -4,8 +4,9 @@
 // The V list of a box B (Sec. II: children of the parent's colleagues not adjacent to B) lies
 // at up to 189 of the 316 offsets o in [-3,3]^3 \ [-1,1]^3; with the pseudo-inverse folded in,
 // each offset is one dense operator T_o (R x R) applied to the check potentials of the source
-// box.  Output-stationary form: a CTA owns 128 check rows x 64 target boxes of one octant
-// class (4 channels each -> N = 256 columns) and accumulates
+// box.  Output-stationary form: a CTA owns 2 x 128 check rows x 32 target boxes of one octant
+// class (4 channels each -> N = 128 columns; one TMEM accumulator per 128-row block) and
+// accumulates
 //     D[rows, (box, ch)] = sum_o T_o[rows, :] * shift_o(up_check[box + o])[:, ch]
 // over all offsets.  A (the operator) arrives by TMA (128B swizzle, K-major); B (gathered,
 // re-referenced to the target centre and split into hi/lo) is written to shared memory by
@@ -30,10 +31,14 @@ namespace kafmm {
 
 namespace tc {
 
-constexpr int BM = 128, BN = 256, NB = 64, STAGES = 2;
-constexpr int A_BYTES = 16384;              // 128 rows x 128 B per split
-constexpr int B_BYTES = 32768;              // 256 rows x 128 B per split
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+// A CTA owns RB = 2 row blocks of BM = 128 operator rows and NB = 32 target boxes (BN = 128
+// columns): both row blocks multiply the same gathered B tile, so every B element the
+// producers build feeds 2 x 3 MMAs.
+constexpr int BM = 128, RB = 2, BN = 128, NB = TC_BOXES, STAGES = 2;
+static_assert(BN == 4 * NB, "four channels per target box");
+constexpr int A_BYTES = 16384;              // 128 rows x 128 B per split and row block
+constexpr int B_BYTES = 16384;              // 128 rows x 128 B per split
+constexpr int STAGE_BYTES = RB * 2 * A_BYTES + 2 * B_BYTES;
 constexpr int THREADS = 448;
 constexpr int NPROD = 256;
 constexpr int W_TMA = 12, W_MMA = 13;
@@ -51,7 +56,8 @@ struct Fmt<SPLIT_BF16> {  // kind::f16 with bf16 operands, K = 16 per instructio
   static constexpr int ES = 2, BK = 64, MK = 16;
   static constexpr uint32_t AB = 1;
 };
-constexpr uint32_t TMEM_COLS = 512;         // [0,256) accumulator, [256,512) running sum
+constexpr uint32_t TMEM_COLS = 512;         // [0,256) accumulators, [256,512) running sums
+constexpr uint32_t SUM_COL = 256;           // row block r: accumulator r*BN, sum SUM_COL + r*BN
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 4096;
 
 struct Args {
@@ -223,8 +229,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int4 tile = a.tiles[blockIdx.x];
   const int cls = tile.z;
-  const int row0 = blockIdx.y * BM;
   const int R = a.R;
+  const int row0 = blockIdx.y * (RB * BM);
+  // row blocks of this CTA that hold operator rows (the last pair may have only one)
+  const int nrb = min(RB, (R - row0 + BM - 1) / BM);
 
   if (threadIdx.x < NB) {
     int b = threadIdx.x < tile.y ? a.boxlist[tile.x + threadIdx.x] : -1;
@@ -288,17 +296,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         unsigned char* base = smem + st * STAGE_BYTES;
         uint32_t bar = smem_u32(&full[st]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
-                     "r"(2 * A_BYTES)
+                     "r"(nrb * 2 * A_BYTES)
                      : "memory");
-        for (int h = 0; h < 2; ++h) {
-          int y = (op * 2 + h) * R + row0;
-          int x = c * BK;
-          asm volatile(
-              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], "
-              "[%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(base + h * A_BYTES)),
-              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x), "r"(y), "r"(bar)
-              : "memory");
-        }
+        for (int r = 0; r < nrb; ++r)
+          for (int h = 0; h < 2; ++h) {
+            int y = (op * 2 + h) * R + row0 + r * BM;
+            int x = c * BK;
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], "
+                "[%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(base + (r * 2 + h) * A_BYTES)),
+                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x), "r"(y), "r"(bar)
+                : "memory");
+          }
       }
     }
   } else if (warp >= 4 && warp < W_TMA) {
@@ -364,7 +373,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       float ox = (float)(s % 6 - 2 - (cls & 1)), oy = (float)((s / 6) % 6 - 2 - ((cls >> 1) & 1)),
             oz = (float)(s / 36 - 2 - ((cls >> 2) & 1));
       const int st = it % STAGES;
-      const uint32_t bhi = smem_u32(smem + st * STAGE_BYTES + 2 * A_BYTES);
+      const uint32_t bhi = smem_u32(smem + st * STAGE_BYTES + RB * 2 * A_BYTES);
       const uint32_t blo = bhi + B_BYTES;
 #pragma unroll
       for (int u = 0; u < UH; ++u) {
@@ -436,15 +445,18 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             uint32_t base = smem_u32(smem + st * STAGE_BYTES);
-            uint32_t ahi = base, alo = base + A_BYTES, bhi = base + 2 * A_BYTES,
-                     blo = base + 2 * A_BYTES + B_BYTES;
+            uint32_t bhi = base + RB * 2 * A_BYTES, blo = bhi + B_BYTES;
             bool first = si == gi * DRAIN && c == 0;
+            for (int r = 0; r < nrb; ++r) {
+              uint32_t ahi = base + r * 2 * A_BYTES, alo = ahi + A_BYTES;
+              uint32_t d = tmem + (uint32_t)(r * BN);
 #pragma unroll
-            for (int kk = 0; kk < BK / MK; ++kk) {
-              uint32_t ko = kk * 32;  // MK elements = 32 bytes in both formats
-              mma<SPLIT>(tmem, sdesc(ahi + ko), sdesc(bhi + ko), (first && kk == 0) ? 0u : 1u);
-              mma<SPLIT>(tmem, sdesc(ahi + ko), sdesc(blo + ko), 1u);
-              mma<SPLIT>(tmem, sdesc(alo + ko), sdesc(bhi + ko), 1u);
+              for (int kk = 0; kk < BK / MK; ++kk) {
+                uint32_t ko = kk * 32;  // MK elements = 32 bytes in both formats
+                mma<SPLIT>(d, sdesc(ahi + ko), sdesc(bhi + ko), (first && kk == 0) ? 0u : 1u);
+                mma<SPLIT>(d, sdesc(ahi + ko), sdesc(blo + ko), 1u);
+                mma<SPLIT>(d, sdesc(alo + ko), sdesc(bhi + ko), 1u);
+              }
             }
             commit(&empty[st]);
           }
@@ -463,29 +475,30 @@ __global__ void __launch_bounds__(THREADS, 1)
       int ok_wait = lane == 0 ? (wait_parity(&acc_full, gi & 1, a.status, &bail) ? 1 : 0) : 0;
       if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      for (int q = 0; q < BN / 32; ++q) {
+      for (int q = 0; q < nrb * (BN / 32); ++q) {   // row block q / 4, columns 32 (q % 4)
         tmem_ld32(tmem + lane_base + q * 32, x);
-        if (gi > 0) tmem_ld32(tmem + lane_base + 256 + q * 32, y);
+        if (gi > 0) tmem_ld32(tmem + lane_base + SUM_COL + q * 32, y);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         if (gi > 0) {
 #pragma unroll
           for (int t = 0; t < 32; ++t) x[t] += y[t];
         }
-        tmem_st32(tmem + lane_base + 256 + q * 32, x);
+        tmem_st32(tmem + lane_base + SUM_COL + q * 32, x);
       }
       asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       arrive(&acc_empty);
     }
-    // write the tile: row = row0 + lane quarter + lane, columns (box j, channel)
-    int row = row0 + (warp & 3) * 32 + lane;
+    // write the tile: row = row0 + 128 r + lane quarter + lane, columns (box j, channel)
     // every CTA writes its partial (zeros when it had no offsets) so the combine is fixed-order
     int do_write = __shfl_sync(0xffffffffu, (!*(volatile int*)&bail) ? 1 : 0, 0);
     float4* dst = reinterpret_cast<float4*>(a.dn + a.part_stride * blockIdx.z);
     if (do_write) {
-      for (int q = 0; q < BN / 32; ++q) {
+      for (int q = 0; q < nrb * (BN / 32); ++q) {
+        int row = row0 + (q / (BN / 32)) * BM + (warp & 3) * 32 + lane;
+        int qc = q % (BN / 32);
         if (ns > 0) {
-          tmem_ld32(tmem + lane_base + 256 + q * 32, x);
+          tmem_ld32(tmem + lane_base + SUM_COL + q * 32, x);
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         } else {
 #pragma unroll
@@ -494,7 +507,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (row < R) {
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
-            int b = sbox[q * 8 + jj];
+            int b = sbox[qc * 8 + jj];
             if (b >= 0)
               dst[(int64_t)b * R + row] = make_float4(x[4 * jj], x[4 * jj + 1], x[4 * jj + 2], x[4 * jj + 3]);
           }
@@ -584,7 +597,7 @@ int m2l_tc_launch(Plan& P, const int4* tiles, int ntiles, const int* boxlist, cu
   }
   const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(P.tmap);
   // offset ranges per tile: enough CTAs to fill the 152 SMs over several waves
-  int rows = (P.R + tc::BM - 1) / tc::BM;
+  int rows = (P.R + tc::RB * tc::BM - 1) / (tc::RB * tc::BM);   // CTAs per tile (row-block pairs)
   int nsplit = 1;
   while (nsplit < 4 && (int64_t)ntiles * rows * nsplit < 152 * 6) nsplit *= 2;
   int64_t part_stride = (int64_t)P.tree.nbox * P.R * 4;

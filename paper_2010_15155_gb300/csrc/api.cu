@@ -207,7 +207,9 @@ static int set_points_impl(Plan& P, const void* y, int64_t ns, const void* x, in
   }
   rc = build_tree(P, yd, ns, xd, nt, dtype, n_prob, soff, toff);
   if (rc) return rc;
-  rc = build_worklists(P, 64 / P.C, P.use_tc ? TC_BOXES : 64 / P.C);
+  // tile sizes: the tensor-core kernels take P.tc_boxes target boxes per tile, k_gemm 64 / C
+  int nb_tile = P.use_tc ? P.tc_boxes : 64 / P.C;
+  rc = build_worklists(P, nb_tile, nb_tile);
   if (rc) return rc;
   P.launches_points = g_launches;
   P.have_points = true;

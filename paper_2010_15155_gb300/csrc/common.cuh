@@ -16,7 +16,6 @@ extern thread_local long long g_launches;
 #define KL ++::kafmm::g_launches,
 
 constexpr int MAX_LEVEL = 20;        // finest octree level; keys carry 20 bits per axis
-constexpr int TC_BOXES = 32;         // target boxes per tile of the tensor-core M->L
 constexpr int MAX_LEVELS = MAX_LEVEL + 1;
 constexpr double PI = 3.14159265358979323846;
 
@@ -43,6 +42,9 @@ constexpr int OP_DN1 = OP_UP2 + 1;
 constexpr int OP_DN2 = OP_DN1 + 1;
 constexpr int OP_PER = OP_DN2 + 1;  // periodic far-image operator of the root (composed)
 constexpr int N_OPS = OP_PER + 1;
+// operators of the non-M->L tensor-core modes (M->M, L->L, pseudo-inverse factors), kept in
+// their own TF32 split array: aux index = slot - OP_M2M
+constexpr int N_AUX = OP_PER - OP_M2M;
 
 // Split formats of the tensor-core M->L.
 enum { SPLIT_TF32 = 0, SPLIT_BF16 = 1 };

@@ -7,7 +7,11 @@
 
 namespace kafmm {
 
-int m2l_tc_launch(Plan& P, const int4* tiles, int ntiles, const int* boxlist, cudaStream_t st);
+int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* boxlist,
+                   const float* in, float* out, int op_slot, int write, cudaStream_t st);
+// modes and output kinds of tc_gemm_launch (m2l_tc.cu)
+constexpr int TCM_M2L = 0, TCM_M2M = 1, TCM_L2L = 2, TCM_APPLY = 3;
+constexpr int TCW_STORE = 0, TCW_ADD = 1, TCW_SCALE = 2;
 
 // ---------------------------------------------------------------------------------------
 // Geometry helpers.
@@ -935,7 +939,10 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       sa.mode = 0;
       KL k_s2check<T, PR><<<n_sleaves, 128, 0, st>>>(sa);
     }
-    // M->M, deepest level first
+    // The gather-GEMMs run on the tensor cores in the mixed form (four-channel table), else on
+    // the CUDA cores (k_gemm).
+    constexpr bool TC_OK = sizeof(T) == 4 && C == 4;
+    const bool tc = TC_OK && P.use_tc;
     GemmArgs<T> ga;
     ga.t = tv;
     ga.geo = geo;
@@ -946,15 +953,31 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
     ga.R = R;
     dim3 blk(256);
     int rb = (R + GEMM_BM - 1) / GEMM_BM;
-    for (int l = MAX_LEVELS - 1; l >= 0; --l) {
-      int n = W.m2m[l][1] - W.m2m[l][0];
-      if (n <= 0) continue;
-      ga.mode = GM_M2M;
-      ga.in = P.up_check.as<T>();
-      ga.out = P.up_check.as<T>();
-      ga.tiles = P.tiles.as<int4>() + W.m2m[l][0];
-      KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
-    }
+    // mode: TCM_*; op: operator slot (TCM_APPLY); write: TCW_*
+    auto gemm = [&](int mode, const int* range, T* in, T* out, int op, int write) -> int {
+      int n = range[1] - range[0];
+      if (n <= 0) return 0;
+      const int4* tiles = P.tiles.as<int4>() + range[0];
+      if (tc)
+        return tc_gemm_launch(P, mode, tiles, n, boxlist, reinterpret_cast<const float*>(in),
+                              reinterpret_cast<float*>(out), op, write, st);
+      ga.mode = mode == TCM_M2L ? GM_M2L : (mode == TCM_M2M ? GM_M2M : (mode == TCM_L2L ? GM_L2L : GM_APPLY));
+      ga.in = in;
+      ga.out = out;
+      ga.op = op;
+      ga.scale_r = write == TCW_SCALE;
+      ga.tiles = tiles;
+      if (mode == TCM_M2L)
+        KL k_gemm<T, C, true><<<dim3(n, rb), blk, 0, st>>>(ga);
+      else
+        KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
+      return 0;
+    };
+    int rc = 0;
+    // M->M, deepest level first
+    for (int l = MAX_LEVELS - 1; l >= 0 && !rc; --l)
+      rc = gemm(TCM_M2M, W.m2m[l], P.up_check.as<T>(), P.up_check.as<T>(), 0, TCW_STORE);
+    if (rc) return rc;
     // periodic: far images of the root's multipole density -> root's downward check
     if (W.root[1] > W.root[0]) {
       ga.mode = GM_APPLY;
@@ -967,19 +990,8 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
     }
     cudaEventRecord(P.ev[4], st);
     // M->L over the V lists (all levels)
-    int nm2l = W.m2l[1] - W.m2l[0];
-    if (nm2l > 0) {
-      if (P.use_tc && !P.fp64() && P.prec == KAFMM_PREC_MIXED && C == 4 && sizeof(T) == 4) {
-        int rc = m2l_tc_launch(P, P.tiles.as<int4>() + W.m2l[0], nm2l, boxlist, st);
-        if (rc) return rc;
-      } else {
-        ga.mode = GM_M2L;
-        ga.in = P.up_check.as<T>();
-        ga.out = P.dn_check.as<T>();
-        ga.tiles = P.tiles.as<int4>() + W.m2l[0];
-        KL k_gemm<T, C, true><<<dim3(nm2l, rb), blk, 0, st>>>(ga);
-      }
-    }
+    rc = gemm(TCM_M2L, W.m2l, P.up_check.as<T>(), P.dn_check.as<T>(), 0, TCW_ADD);
+    if (rc) return rc;
     cudaEventRecord(P.ev[5], st);
     // S->L over the X lists
     if (W.xbox_n > 0) {
@@ -989,48 +1001,18 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       KL k_s2check<T, PR><<<W.xbox_n, 128, 0, st>>>(sa);
     }
     // L->L, coarsest level first
-    for (int l = 0; l < MAX_LEVELS; ++l) {
-      int n = W.l2l[l][1] - W.l2l[l][0];
-      if (n <= 0) continue;
-      ga.mode = GM_L2L;
-      ga.in = P.dn_check.as<T>();
-      ga.out = P.dn_check.as<T>();
-      ga.tiles = P.tiles.as<int4>() + W.l2l[l][0];
-      KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
-    }
+    for (int l = 0; l < MAX_LEVELS && !rc; ++l)
+      rc = gemm(TCM_L2L, W.l2l[l], P.dn_check.as<T>(), P.dn_check.as<T>(), 0, TCW_ADD);
+    if (rc) return rc;
     // equivalent densities where they are evaluated at targets: r * V * ((S^+ U^T) * check),
     // the two factors applied in turn (tmp = the downward equivalent buffer of the up pass
     // is not yet used, so the up pass stages through dn_equiv and vice versa through up_equiv)
-    int n = W.pup[1] - W.pup[0];
-    if (n > 0) {
-      ga.mode = GM_APPLY;
-      ga.tiles = P.tiles.as<int4>() + W.pup[0];
-      ga.in = P.up_check.as<T>();
-      ga.out = P.dn_equiv.as<T>();
-      ga.op = OP_UP1;
-      ga.scale_r = 0;
-      KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
-      ga.in = P.dn_equiv.as<T>();
-      ga.out = P.up_equiv.as<T>();
-      ga.op = OP_UP2;
-      ga.scale_r = 1;
-      KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
-    }
-    n = W.pdn[1] - W.pdn[0];
-    if (n > 0) {
-      ga.mode = GM_APPLY;
-      ga.tiles = P.tiles.as<int4>() + W.pdn[0];
-      ga.in = P.dn_check.as<T>();
-      ga.out = P.up_check.as<T>();   // up_check is no longer needed here
-      ga.op = OP_DN1;
-      ga.scale_r = 0;
-      KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
-      ga.in = P.up_check.as<T>();
-      ga.out = P.dn_equiv.as<T>();
-      ga.op = OP_DN2;
-      ga.scale_r = 1;
-      KL k_gemm<T, C, false><<<dim3(n, rb), blk, 0, st>>>(ga);
-    }
+    rc = gemm(TCM_APPLY, W.pup, P.up_check.as<T>(), P.dn_equiv.as<T>(), OP_UP1, TCW_STORE);
+    if (!rc) rc = gemm(TCM_APPLY, W.pup, P.dn_equiv.as<T>(), P.up_equiv.as<T>(), OP_UP2, TCW_SCALE);
+    // up_check is no longer needed here
+    if (!rc) rc = gemm(TCM_APPLY, W.pdn, P.dn_check.as<T>(), P.up_check.as<T>(), OP_DN1, TCW_STORE);
+    if (!rc) rc = gemm(TCM_APPLY, W.pdn, P.up_check.as<T>(), P.dn_equiv.as<T>(), OP_DN2, TCW_SCALE);
+    if (rc) return rc;
   }
   cudaEventRecord(P.ev[6], st);
   // leaves

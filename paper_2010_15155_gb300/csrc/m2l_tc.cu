@@ -31,14 +31,25 @@ namespace kafmm {
 
 namespace tc {
 
-// A CTA owns RB = 2 row blocks of BM = 128 operator rows and NB = 32 target boxes (BN = 128
-// columns): both row blocks multiply the same gathered B tile, so every B element the
-// producers build feeds 2 x 3 MMAs.
-constexpr int BM = 128, RB = 2, BN = 128, NB = TC_BOXES, STAGES = 2;
-static_assert(BN == 4 * NB, "four channels per target box");
+// A CTA owns RB row blocks of BM = 128 operator rows and NB = 64 / RB target boxes
+// (BN = 256 / RB columns, four channels per box): all row blocks multiply the same gathered B
+// tile, so every B element the producers build feeds RB x 3 MMAs.  RB = 2 when the number of
+// row blocks is even, else 1 (a lone last block would waste a pair's B tile).  Shared memory
+// per stage (96 KB) and TMEM (RB x BN accumulator + running-sum columns) are the same for both.
+constexpr int BM = 128, STAGES = 2;
 constexpr int A_BYTES = 16384;              // 128 rows x 128 B per split and row block
-constexpr int B_BYTES = 16384;              // 128 rows x 128 B per split
-constexpr int STAGE_BYTES = RB * 2 * A_BYTES + 2 * B_BYTES;
+constexpr int STAGE_BYTES = 6 * A_BYTES;   // A hi/lo of RB blocks + B hi/lo: 96 KB (both RB)
+template <int RB>
+struct Shape {
+  static constexpr int BN = 256 / RB, NB = BN / 4;
+  static constexpr int A_STAGE = RB * 2 * A_BYTES;       // A hi/lo of all row blocks
+  static constexpr int B_BYTES = BN * 128;               // BN rows x 128 B per split
+  static_assert(A_STAGE + 2 * B_BYTES == STAGE_BYTES, "96 KB per stage");
+};
+// non-M->L modes drain the TMEM accumulator into the running sum after every k-chunk: the
+// pseudo-inverse factors sum with heavy cancellation, and accumulating two chunks per drain
+// measured 1.3e-5 against the FP64 form at p = 8 (8.7e-6 with one; Stokeslet N = 262144)
+constexpr int AUX_DRAIN = 1;
 constexpr int THREADS = 448;
 constexpr int NPROD = 256;
 constexpr int W_TMA = 12, W_MMA = 13;
@@ -60,11 +71,23 @@ constexpr uint32_t TMEM_COLS = 512;         // [0,256) accumulators, [256,512) r
 constexpr uint32_t SUM_COL = 256;           // row block r: accumulator r*BN, sum SUM_COL + r*BN
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 4096;
 
+// Modes of the gather-GEMM: target box b (of a tile), slots s, out[b] (+)= sum_s
+// T_s * shift_s(in[src(b, s)]):
+//   TC_M2L    s = V slot of the parent's 6^3 neighbourhood, src = V entry, T = M->L(offset)
+//   TC_M2M    s = child octant, src = child s (b a parent), T = M->M(s)
+//   TC_L2L    one slot, src = parent of b, T = L->L(octant class of b)
+//   TC_APPLY  one slot, src = b, T = a fixed operator (pseudo-inverse factor), no shift
+// shift_s re-references the fourth channel from the source box centre to the target's.
+enum TcMode { TC_M2L = 0, TC_M2M = 1, TC_L2L = 2, TC_APPLY = 3 };
+// Output: TC_STORE out = value (or the partial of offset range z), TC_ADD out += value,
+// TC_SCALE out = value x half-width of b.
+enum TcWrite { TC_STORE = 0, TC_ADD = 1, TC_SCALE = 2 };
+
 struct Args {
   TreeView t;
   double L;
-  const float* up;        // [nbox][R][4]
-  float* dn;              // [nsplit][nbox][R][4]: partial sums, one per offset range
+  const float* up;        // input [nbox][R][4]
+  float* dn;              // output [nbox][R][4]; TC_M2L with nsplit > 1: [nsplit] partials
   int64_t part_stride;    // floats between partial buffers
   int nsplit;
   const int4* tiles;
@@ -72,7 +95,53 @@ struct Args {
   const int32_t* vtab;
   unsigned* status;
   int R, nchunk;
+  int mode, write;
+  int op;                 // TC_APPLY: operator index in the tensor map
 };
+
+// Slots of a mode (upper bound of the slot index), the operator of slot s in the tensor map
+// (M->L map for TC_M2L, the auxiliary map otherwise) and the re-reference shift of slot s in
+// units of the target box's side.
+__device__ __forceinline__ int mode_slots(int mode) {
+  return mode == TC_M2L ? 216 : (mode == TC_M2M ? 8 : 1);
+}
+__device__ __forceinline__ int slot_op(const Args& a, int s, int cls) {
+  if (a.mode == TC_M2L) {
+    int ox = s % 6 - 2 - (cls & 1), oy = (s / 6) % 6 - 2 - ((cls >> 1) & 1), oz = s / 36 - 2 - ((cls >> 2) & 1);
+    return m2l_index(ox, oy, oz);
+  }
+  if (a.mode == TC_M2M) return OP_M2M - OP_M2M + s;
+  if (a.mode == TC_L2L) return OP_L2L - OP_M2M + cls;
+  return a.op;
+}
+__device__ __forceinline__ void slot_shift(int mode, int s, int cls, float& fx, float& fy, float& fz) {
+  if (mode == TC_M2L) {
+    fx = (float)(s % 6 - 2 - (cls & 1));
+    fy = (float)((s / 6) % 6 - 2 - ((cls >> 1) & 1));
+    fz = (float)(s / 36 - 2 - ((cls >> 2) & 1));
+  } else if (mode == TC_M2M) {  // child centre - parent centre
+    fx = (s & 1) ? 0.25f : -0.25f;
+    fy = (s & 2) ? 0.25f : -0.25f;
+    fz = (s & 4) ? 0.25f : -0.25f;
+  } else if (mode == TC_L2L) {  // parent centre - child centre
+    fx = (cls & 1) ? -0.5f : 0.5f;
+    fy = (cls & 2) ? -0.5f : 0.5f;
+    fz = (cls & 4) ? -0.5f : 0.5f;
+  } else {
+    fx = fy = fz = 0.f;
+  }
+}
+// Source box of target b at slot s, or -1.
+__device__ __forceinline__ int slot_src(const Args& a, int b, int s) {
+  if (b < 0) return -1;
+  if (a.mode == TC_M2L) {
+    int32_t e = a.vtab[(int64_t)b * 216 + s];
+    return e != LIST_EMPTY ? entry_box(e) : -1;
+  }
+  if (a.mode == TC_M2M) return a.t.child[b * 8 + s];
+  if (a.mode == TC_L2L) return a.t.parent[b];
+  return b;
+}
 
 __device__ __forceinline__ float tf32_rn(float x) {
   uint32_t r;
@@ -135,25 +204,25 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 
 // Instruction descriptor: D = F32, A/B format (bf16 = 1, tf32 = 2), K-major both, N = 256,
 // M = 128.
-template <int SPLIT>
+template <int SPLIT, int BN>
 __device__ __forceinline__ constexpr uint32_t idesc() {
   return (1u << 4) | (Fmt<SPLIT>::AB << 7) | (Fmt<SPLIT>::AB << 10) | ((uint32_t)(BN >> 3) << 17) |
          ((uint32_t)(BM >> 4) << 24);
 }
 
-template <int SPLIT>
+template <int SPLIT, int BN>
 __device__ __forceinline__ void mma(uint32_t dt, uint64_t a, uint64_t b, uint32_t acc) {
   if (SPLIT == SPLIT_TF32)
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-        "l"(a), "l"(b), "r"(idesc<SPLIT>()), "r"(acc)
+        "l"(a), "l"(b), "r"(idesc<SPLIT, BN>()), "r"(acc)
         : "memory");
   else
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-        "l"(a), "l"(b), "r"(idesc<SPLIT>()), "r"(acc)
+        "l"(a), "l"(b), "r"(idesc<SPLIT, BN>()), "r"(acc)
         : "memory");
 }
 
@@ -206,10 +275,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-template <int SPLIT>
+template <int SPLIT, int RB>
 __global__ void __launch_bounds__(THREADS, 1)
     k_m2l_tc(const __grid_constant__ CUtensorMap tmap, Args a) {
   constexpr int BK = Fmt<SPLIT>::BK, MK = Fmt<SPLIT>::MK;
+  constexpr int BN = Shape<RB>::BN, NB = Shape<RB>::NB, B_BYTES = Shape<RB>::B_BYTES,
+                A_STAGE = Shape<RB>::A_STAGE;
   constexpr int PROD_WARPS = NPROD / 32;
   // offsets accumulated in TMEM before each drain into the running sum: longer chains lose
   // accuracy in TF32x3 (measured 5.4e-6 -> 8.2e-6 at p = 10 with 2), BF16x3 is limited by its
@@ -250,13 +321,17 @@ __global__ void __launch_bounds__(THREADS, 1)
     mbar_init(&acc_empty, 128);
   }
   __syncthreads();
-  // active slots: some box of the tile has a V entry there
-  for (int e = threadIdx.x; e < 216 * NB; e += THREADS) {
+  // active slots: some box of the tile has a source there
+  const int nsmax = mode_slots(a.mode);
+  for (int e = threadIdx.x; e < nsmax * NB; e += THREADS) {
     int k = e / NB, j = e % NB;
-    int ox = k % 6 - 2 - (cls & 1), oy = (k / 6) % 6 - 2 - ((cls >> 1) & 1),
-        oz = k / 36 - 2 - ((cls >> 2) & 1);
-    bool inner = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
-    if (!inner && sbox[j] >= 0 && a.vtab[(int64_t)sbox[j] * 216 + k] != LIST_EMPTY) slot_any[k] = 1;
+    bool inner = false;
+    if (a.mode == TC_M2L) {
+      int ox = k % 6 - 2 - (cls & 1), oy = (k / 6) % 6 - 2 - ((cls >> 1) & 1),
+          oz = k / 36 - 2 - ((cls >> 2) & 1);
+      inner = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
+    }
+    if (!inner && slot_src(a, sbox[j], k) >= 0) slot_any[k] = 1;
   }
   if (warp == W_MMA) {  // TMEM allocation (whole warp)
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -268,7 +343,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   if (threadIdx.x == 0) {  // active offsets of this tile, then this CTA's share (blockIdx.z)
     int ns = 0;
-    for (int k = 0; k < 216; ++k)
+    for (int k = 0; k < nsmax; ++k)
       if (slot_any[k]) slot_list[ns++] = k;
     int z = blockIdx.z, nz = a.nsplit;
     int s0 = (int)((int64_t)ns * z / nz), s1 = (int)((int64_t)ns * (z + 1) / nz);
@@ -282,6 +357,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int ns = nslots;
   const int nchunk = a.nchunk;
   const int total = ns * nchunk;
+  // accumulation groups: iterations accumulated in TMEM before the epilogue adds them into the
+  // running sum (M->L: DRAIN whole offsets; other modes: AUX_DRAIN k-chunks)
+  const int GI = a.mode == TC_M2L ? DRAIN * nchunk : AUX_DRAIN;
+  const int ngroups = (total + GI - 1) / GI;
 
   if (warp == W_TMA) {
     // ---------------- TMA producer of A (operator rows, hi and lo) ----------------
@@ -290,9 +369,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         int st = it % STAGES;
         if (it >= STAGES && !wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail)) break;
         int s = slot_list[it / nchunk], c = it % nchunk;
-        int ox = s % 6 - 2 - (cls & 1), oy = (s / 6) % 6 - 2 - ((cls >> 1) & 1),
-            oz = s / 36 - 2 - ((cls >> 2) & 1);
-        int op = m2l_index(ox, oy, oz);
+        int op = slot_op(a, s, cls);
         unsigned char* base = smem + st * STAGE_BYTES;
         uint32_t bar = smem_u32(&full[st]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
@@ -334,11 +411,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     int cur_slot = -1;
     auto set_slot = [&](int s) {
 #pragma unroll
-      for (int u = 0; u < UPW; ++u) {
-        int b = sbox[pw + PROD_WARPS * u];
-        int32_t e = b >= 0 ? a.vtab[(int64_t)b * 216 + s] : LIST_EMPTY;
-        srcb[u] = e != LIST_EMPTY ? entry_box(e) : -1;
-      }
+      for (int u = 0; u < UPW; ++u) srcb[u] = slot_src(a, sbox[pw + PROD_WARPS * u], s);
     };
     // Software pipeline over half stages (UH boxes each): the loads of the next half are in
     // flight while the current half is converted, including the first half of the next stage
@@ -370,10 +443,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     };
     auto store_half = [&](int it, int h, const float4 (&q)[UH][EPL]) {
       int s = slot_list[it / nchunk];
-      float ox = (float)(s % 6 - 2 - (cls & 1)), oy = (float)((s / 6) % 6 - 2 - ((cls >> 1) & 1)),
-            oz = (float)(s / 36 - 2 - ((cls >> 2) & 1));
+      float ox, oy, oz;
+      slot_shift(a.mode, s, cls, ox, oy, oz);
       const int st = it % STAGES;
-      const uint32_t bhi = smem_u32(smem + st * STAGE_BYTES + RB * 2 * A_BYTES);
+      const uint32_t bhi = smem_u32(smem + st * STAGE_BYTES + A_STAGE);
       const uint32_t blo = bhi + B_BYTES;
 #pragma unroll
       for (int u = 0; u < UH; ++u) {
@@ -430,36 +503,33 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- MMA issue (one thread) ----------------
     if (lane == 0) {
       int it = 0;
-      const int ngroups = (ns + DRAIN - 1) / DRAIN;
       for (int gi = 0; gi < ngroups; ++gi) {
         if (gi > 0 && !wait_parity(&acc_empty, (gi - 1) & 1, a.status, &bail)) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         bool ok = true;
-        int s_end = min(ns, (gi + 1) * DRAIN);
-        for (int si = gi * DRAIN; si < s_end && ok; ++si) {
-          for (int c = 0; c < nchunk; ++c, ++it) {
-            int st = it % STAGES;
-            if (!wait_parity(&full[st], (it / STAGES) & 1, a.status, &bail)) {
-              ok = false;
-              break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            uint32_t base = smem_u32(smem + st * STAGE_BYTES);
-            uint32_t bhi = base + RB * 2 * A_BYTES, blo = bhi + B_BYTES;
-            bool first = si == gi * DRAIN && c == 0;
-            for (int r = 0; r < nrb; ++r) {
-              uint32_t ahi = base + r * 2 * A_BYTES, alo = ahi + A_BYTES;
-              uint32_t d = tmem + (uint32_t)(r * BN);
-#pragma unroll
-              for (int kk = 0; kk < BK / MK; ++kk) {
-                uint32_t ko = kk * 32;  // MK elements = 32 bytes in both formats
-                mma<SPLIT>(d, sdesc(ahi + ko), sdesc(bhi + ko), (first && kk == 0) ? 0u : 1u);
-                mma<SPLIT>(d, sdesc(ahi + ko), sdesc(blo + ko), 1u);
-                mma<SPLIT>(d, sdesc(alo + ko), sdesc(bhi + ko), 1u);
-              }
-            }
-            commit(&empty[st]);
+        const int it_end = min(total, (gi + 1) * GI);
+        for (; it < it_end; ++it) {
+          int st = it % STAGES;
+          if (!wait_parity(&full[st], (it / STAGES) & 1, a.status, &bail)) {
+            ok = false;
+            break;
           }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          uint32_t base = smem_u32(smem + st * STAGE_BYTES);
+          uint32_t bhi = base + A_STAGE, blo = bhi + B_BYTES;
+          bool first = it == gi * GI;
+          for (int r = 0; r < nrb; ++r) {
+            uint32_t ahi = base + r * 2 * A_BYTES, alo = ahi + A_BYTES;
+            uint32_t d = tmem + (uint32_t)(r * BN);
+#pragma unroll
+            for (int kk = 0; kk < BK / MK; ++kk) {
+              uint32_t ko = kk * 32;  // MK elements = 32 bytes in both formats
+              mma<SPLIT, BN>(d, sdesc(ahi + ko), sdesc(bhi + ko), (first && kk == 0) ? 0u : 1u);
+              mma<SPLIT, BN>(d, sdesc(ahi + ko), sdesc(blo + ko), 1u);
+              mma<SPLIT, BN>(d, sdesc(alo + ko), sdesc(bhi + ko), 1u);
+            }
+          }
+          commit(&empty[st]);
         }
         if (!ok) break;
         commit(&acc_full);
@@ -469,13 +539,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- epilogue: drain each offset into the running sum ----------------
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     float x[32], y[32];
-    const int ngroups = (ns + DRAIN - 1) / DRAIN;
     for (int gi = 0; gi < ngroups; ++gi) {
       // lane 0 waits; the warp stays converged for the .sync.aligned TMEM accesses
       int ok_wait = lane == 0 ? (wait_parity(&acc_full, gi & 1, a.status, &bail) ? 1 : 0) : 0;
       if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      for (int q = 0; q < nrb * (BN / 32); ++q) {   // row block q / 4, columns 32 (q % 4)
+      for (int q = 0; q < nrb * (BN / 32); ++q) {   // row block q / (BN / 32), 32 columns each
         tmem_ld32(tmem + lane_base + q * 32, x);
         if (gi > 0) tmem_ld32(tmem + lane_base + SUM_COL + q * 32, y);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
@@ -508,8 +577,23 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
             int b = sbox[qc * 8 + jj];
-            if (b >= 0)
-              dst[(int64_t)b * R + row] = make_float4(x[4 * jj], x[4 * jj + 1], x[4 * jj + 2], x[4 * jj + 3]);
+            if (b < 0) continue;
+            float4 v = make_float4(x[4 * jj], x[4 * jj + 1], x[4 * jj + 2], x[4 * jj + 3]);
+            float4* o = dst + (int64_t)b * R + row;
+            if (a.write == TC_ADD) {
+              float4 w = *o;
+              v.x += w.x;
+              v.y += w.y;
+              v.z += w.z;
+              v.w += w.w;
+            } else if (a.write == TC_SCALE) {
+              float al = 0.5f * sside[qc * 8 + jj];
+              v.x *= al;
+              v.y *= al;
+              v.z *= al;
+              v.w *= al;
+            }
+            *o = v;
           }
         }
       }
@@ -524,7 +608,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-// dn[b] = sum of the partial sums over the offset ranges, in range order (boxes of the M->L
+// dn[b] += sum of the partial sums over the offset ranges, in range order (boxes of the M->L
 // tiles only).
 __global__ void k_combine_parts(const float4* __restrict__ parts, int64_t part_stride4, int nsplit,
                                 float4* __restrict__ dn, const int4* __restrict__ tiles, int ntiles,
@@ -542,7 +626,12 @@ __global__ void k_combine_parts(const float4* __restrict__ parts, int64_t part_s
         v.z += w.z;
         v.w += w.w;
       }
-      dn[i] = v;
+      float4 d = dn[i];
+      d.x += v.x;
+      d.y += v.y;
+      d.z += v.z;
+      d.w += v.w;
+      dn[i] = d;
     }
   }
 }
@@ -551,6 +640,9 @@ __global__ void k_combine_parts(const float4* __restrict__ parts, int64_t part_s
 
 bool tc_supported(Plan& P) {
   if (P.prec != KAFMM_PREC_MIXED || P.C != 4 || P.ml_stokes || !P.opstc.p) return false;
+  int rows = (P.R + tc::BM - 1) / tc::BM;
+  P.tc_rb = rows % 2 == 0 ? 2 : 1;
+  P.tc_boxes = 64 / P.tc_rb;
   int dev = 0, major = 0, minor = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
@@ -559,7 +651,9 @@ bool tc_supported(Plan& P) {
   return major == 10 && minor == 3;
 }
 
-static int make_tmap(Plan& P, CUtensorMap* map) {
+// Tensor map over a split operator array [nops][2][R][Rpad] (tf32 or bf16), 128-byte swizzle,
+// boxes of 128 rows x 128 bytes.
+static int make_tmap(Plan& P, CUtensorMap* map, void* base, int nops, bool tf32) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -569,37 +663,48 @@ static int make_tmap(Plan& P, CUtensorMap* map) {
       return fail(P, KAFMM_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  bool tf32 = P.tc_split == SPLIT_TF32;
   int es = tf32 ? 4 : 2;
-  cuuint64_t dims[2] = {(cuuint64_t)P.Rpad, (cuuint64_t)N_M2L * 2 * P.R};
+  cuuint64_t dims[2] = {(cuuint64_t)P.Rpad, (cuuint64_t)nops * 2 * P.R};
   cuuint64_t strides[1] = {(cuuint64_t)P.Rpad * es};
   cuuint32_t box[2] = {(cuuint32_t)(128 / es), tc::BM};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                      2, P.opstc.p, dims, strides, box, estr,
+                      2, base, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(P, KAFMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return 0;
 }
 
-int m2l_tc_launch(Plan& P, const int4* tiles, int ntiles, const int* boxlist, cudaStream_t st) {
-  if (!P.tmap_ready) {
-    int rc = make_tmap(P, reinterpret_cast<CUtensorMap*>(P.tmap));
-    if (rc) return rc;
-    cudaError_t e = cudaFuncSetAttribute(tc::k_m2l_tc<SPLIT_TF32>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(tc::k_m2l_tc<SPLIT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               tc::SMEM_BYTES);
-    if (e != cudaSuccess) return cuda_fail(P, e, "cudaFuncSetAttribute(k_m2l_tc)");
-    P.tmap_ready = true;
-  }
-  const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(P.tmap);
-  // offset ranges per tile: enough CTAs to fill the 152 SMs over several waves
-  int rows = (P.R + tc::RB * tc::BM - 1) / (tc::RB * tc::BM);   // CTAs per tile (row-block pairs)
+static int tc_prepare(Plan& P) {
+  if (P.tmap_ready) return 0;
+  int rc = make_tmap(P, reinterpret_cast<CUtensorMap*>(P.tmap), P.opstc.p, N_M2L, P.tc_split == SPLIT_TF32);
+  if (rc) return rc;
+  rc = make_tmap(P, reinterpret_cast<CUtensorMap*>(P.tmap_aux), P.opstc_aux.p, N_AUX, true);
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  for (auto fn : {tc::k_m2l_tc<SPLIT_TF32, 1>, tc::k_m2l_tc<SPLIT_TF32, 2>, tc::k_m2l_tc<SPLIT_BF16, 1>,
+                  tc::k_m2l_tc<SPLIT_BF16, 2>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+  if (e != cudaSuccess) return cuda_fail(P, e, "cudaFuncSetAttribute(k_m2l_tc)");
+  P.tmap_ready = true;
+  return 0;
+}
+
+// One gather-GEMM on the tensor cores.  TC_M2L: in = up_check, out = dn_check (stored; the
+// operator in the plan's split format, several offset ranges per tile when the grid is small).
+// Other modes: TF32x3 with the auxiliary operators (op = slot for TC_APPLY), one range.
+int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* boxlist,
+                   const float* in, float* out, int op_slot, int write, cudaStream_t st) {
+  int rc = tc_prepare(P);
+  if (rc) return rc;
+  const bool m2l = mode == tc::TC_M2L;
+  const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(m2l ? P.tmap : P.tmap_aux);
+  const int split = m2l ? P.tc_split : SPLIT_TF32;
+  int rows = (P.R + P.tc_rb * tc::BM - 1) / (P.tc_rb * tc::BM);   // CTAs per tile
+  // offset ranges per tile (M->L only): enough CTAs to fill the 152 SMs over several waves
   int nsplit = 1;
-  while (nsplit < 4 && (int64_t)ntiles * rows * nsplit < 152 * 6) nsplit *= 2;
+  while (m2l && nsplit < 4 && (int64_t)ntiles * rows * nsplit < 152 * 6) nsplit *= 2;
   int64_t part_stride = (int64_t)P.tree.nbox * P.R * 4;
   if (nsplit > 1) {
     cudaError_t e = P.m2l_parts.reserve(sizeof(float) * part_stride * nsplit + 256);
@@ -608,9 +713,9 @@ int m2l_tc_launch(Plan& P, const int4* tiles, int ntiles, const int* boxlist, cu
   tc::Args a;
   a.t = P.tree.view();
   a.L = P.L;
-  a.up = P.up_check.as<float>();
-  // one offset range: straight into dn_check; several: partial buffers, combined below
-  a.dn = nsplit > 1 ? P.m2l_parts.as<float>() : P.dn_check.as<float>();
+  a.up = in;
+  // one offset range: straight into the output; several: partial buffers, combined below
+  a.dn = nsplit > 1 ? P.m2l_parts.as<float>() : out;
   a.part_stride = nsplit > 1 ? part_stride : 0;
   a.nsplit = nsplit;
   a.tiles = tiles;
@@ -618,19 +723,24 @@ int m2l_tc_launch(Plan& P, const int4* tiles, int ntiles, const int* boxlist, cu
   a.vtab = P.tree.vtab.as<int32_t>();
   a.status = P.tree.status.as<unsigned>();
   a.R = P.R;
+  a.mode = mode;
+  a.write = nsplit > 1 ? tc::TC_STORE : write;
+  a.op = m2l ? 0 : op_slot - OP_M2M;
   dim3 grid(ntiles, rows, nsplit);
-  if (P.tc_split == SPLIT_TF32) {
-    a.nchunk = P.Rpad / tc::Fmt<SPLIT_TF32>::BK;
-    KL tc::k_m2l_tc<SPLIT_TF32><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
-  } else {
-    a.nchunk = P.Rpad / tc::Fmt<SPLIT_BF16>::BK;
-    KL tc::k_m2l_tc<SPLIT_BF16><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
-  }
-  cudaError_t e;
+  a.nchunk = P.Rpad / (split == SPLIT_TF32 ? tc::Fmt<SPLIT_TF32>::BK : tc::Fmt<SPLIT_BF16>::BK);
+  if (split == SPLIT_TF32 && P.tc_rb == 2)
+    KL tc::k_m2l_tc<SPLIT_TF32, 2><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
+  else if (split == SPLIT_TF32)
+    KL tc::k_m2l_tc<SPLIT_TF32, 1><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
+  else if (P.tc_rb == 2)
+    KL tc::k_m2l_tc<SPLIT_BF16, 2><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
+  else
+    KL tc::k_m2l_tc<SPLIT_BF16, 1><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
   if (nsplit > 1)
     KL tc::k_combine_parts<<<std::min(ntiles, 152 * 4), 256, 0, st>>>(
-        P.m2l_parts.as<float4>(), part_stride / 4, nsplit, P.dn_check.as<float4>(), tiles, ntiles, boxlist, P.R);
-  e = cudaGetLastError();
+        P.m2l_parts.as<float4>(), part_stride / 4, nsplit, reinterpret_cast<float4*>(out), tiles, ntiles,
+        boxlist, P.R);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(P, e, "k_m2l_tc launch");
   return 0;
 }

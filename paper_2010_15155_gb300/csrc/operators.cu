@@ -448,6 +448,9 @@ int build_operators(Plan& P) {
         KL k_split_bf16<<<2048, 256, 0, st>>>(O + RR * OP_M2L, R, P.Rpad, N_M2L,
                                               P.opstc.as<__nv_bfloat16>());
       }
+      // M->M, L->L and the pseudo-inverse factors: TF32 split (about FP32 accuracy)
+      CK(P.opstc_aux.reserve(sizeof(float) * 2 * (size_t)R * P.Rpad * N_AUX));
+      KL k_split_tf32<<<2048, 256, 0, st>>>(O + RR * OP_M2M, R, P.Rpad, N_AUX, P.opstc_aux.as<float>());
     }
   }
   CK(cudaGetLastError());

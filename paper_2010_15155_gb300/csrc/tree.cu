@@ -375,6 +375,31 @@ struct ListOut {
   unsigned long long* near_pairs;
 };
 
+// V: same-level boxes at the 189 offsets of the parent's neighbourhood, one thread per
+// (box, slot k of the parent's 6^3 neighbourhood).
+__global__ void k_vtab(TreeView t, int32_t* __restrict__ vtab) {
+  const int64_t total = (int64_t)t.nbox * 216;
+  for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < total;
+       e0 += (int64_t)gridDim.x * blockDim.x) {
+    int b = (int)(e0 / 216), k = (int)(e0 % 216);
+    int lv = t.level[b];
+    int ax, ay, az;
+    anchor_of(t.key[b], ax, ay, az);
+    int ox = k % 6 - 2 - (ax & 1), oy = (k / 6) % 6 - 2 - (ay & 1), oz = k / 36 - 2 - (az & 1);
+    int32_t e = LIST_EMPTY;
+    bool inner = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
+    if (!inner && (lv >= 2 || (t.periodic && lv >= 1))) {
+      int cx, cy, cz, sx, sy, sz;
+      if (neighbour(t.periodic, lv, ax, ox, cx, sx) && neighbour(t.periodic, lv, ay, oy, cy, sy) &&
+          neighbour(t.periodic, lv, az, oz, cz, sz)) {
+        int s = find_box(t, lv, t.prob[b], cx, cy, cz);
+        if (s >= 0) e = pack_entry(s, shift_code(sx, sy, sz));
+      }
+    }
+    vtab[e0] = e;
+  }
+}
+
 template <bool FILL>
 __global__ void k_lists(TreeView t, ListOut o) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x) {
@@ -382,24 +407,6 @@ __global__ void k_lists(TreeView t, ListOut o) {
     int pb = t.prob[b];
     int ax, ay, az;
     anchor_of(t.key[b], ax, ay, az);
-    // ---- V: same-level boxes at the 189 offsets of the parent's neighbourhood
-    if (FILL) {
-      int bx = ax & 1, by = ay & 1, bz = az & 1;
-      for (int k = 0; k < 216; ++k) {
-        int ox = k % 6 - 2 - bx, oy = (k / 6) % 6 - 2 - by, oz = k / 36 - 2 - bz;
-        int32_t e = LIST_EMPTY;
-        bool inner = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
-        if (!inner && (lv >= 2 || (t.periodic && lv >= 1))) {
-          int cx, cy, cz, sx, sy, sz;
-          if (neighbour(t.periodic, lv, ax, ox, cx, sx) && neighbour(t.periodic, lv, ay, oy, cy, sy) &&
-              neighbour(t.periodic, lv, az, oz, cz, sz)) {
-            int s = find_box(t, lv, pb, cx, cy, cz);
-            if (s >= 0) e = pack_entry(s, shift_code(sx, sy, sz));
-          }
-        }
-        o.vtab[(int64_t)b * 216 + k] = e;
-      }
-    }
     // ---- U and W for leaves
     int64_t nu = 0, nw = 0, nx = 0;
     int64_t pu = FILL ? o.u_cnt[b] : 0, pw = FILL ? o.w_cnt[b] : 0, px = FILL ? o.x_cnt[b] : 0;
@@ -783,8 +790,11 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   lo.u_cnt = T.u_off.as<int64_t>();
   lo.w_cnt = T.w_off.as<int64_t>();
   lo.x_cnt = T.x_off.as<int64_t>();
-  int g = grid_for(nb, 128, 152 * 16);
-  KL k_lists<false><<<g, 128, 0, st>>>(tv, lo);
+  // one warp per block: the per-box work is a long dependent chain of lookups, so spread the
+  // boxes over as many SMs as possible
+  int g = grid_for(nb, 32, 152 * 64);
+  KL k_vtab<<<grid_for((int64_t)nb * 216, 256, 152 * 16), 256, 0, st>>>(tv, T.vtab.as<int32_t>());
+  KL k_lists<false><<<g, 32, 0, st>>>(tv, lo);
   int64_t tot[3];
   int64_t* sc[3] = {lo.u_cnt, lo.w_cnt, lo.x_cnt};
   for (int k = 0; k < 3; ++k) {
@@ -807,7 +817,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   lo.w_flag = T.w_flag.as<int8_t>();
   lo.near_pairs = (unsigned long long*)(T.status.as<unsigned>() + 8);
   CK(cudaMemsetAsync(lo.near_pairs, 0, 8, st));
-  KL k_lists<true><<<g, 128, 0, st>>>(tv, lo);
+  KL k_lists<true><<<g, 32, 0, st>>>(tv, lo);
   unsigned long long pairs = 0;
   CK(cudaMemcpyAsync(&pairs, lo.near_pairs, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaGetLastError());

@@ -486,7 +486,15 @@ __device__ inline void far_eval(T xl, T yl, T zl, const typename V4<T>::type& p,
                                 const typename V4<T>::type& q, T* acc) {
   // p: equivalent point (local coords), q: its density (C = 4: four channels; C = 1 G: q.xyz).
   T r0 = xl - p.x, r1 = yl - p.y, r2 = zl - p.z;
-  if (PR == P_LAP) {
+  if constexpr (PR == P_STK_L4 && sizeof(T) == 4) {
+    // as below; equivalent points lie on surfaces outside the target box, so r > 0
+    float rr = fmaf(r0, r0, fmaf(r1, r1, r2 * r2));
+    float ir = rsqrt_ftz(rr);
+    float tq = (fmaf(xl, q.x, fmaf(yl, q.y, zl * q.z)) - q.w) * (ir * ir * ir);
+    acc[0] = fmaf(r0, tq, fmaf(q.x, ir, acc[0]));
+    acc[1] = fmaf(r1, tq, fmaf(q.y, ir, acc[1]));
+    acc[2] = fmaf(r2, tq, fmaf(q.z, ir, acc[2]));
+  } else if (PR == P_LAP) {
     lap_st<T>(r0, r1, r2, q.x, acc);
   } else if (PR == P_STK_L4 || PR == P_RPY_L4) {
     // 8 pi u_i = 2 [phi_i - x_j d_i phi_j + d_i phi_4] with phi = q/r (reference: leaf centre)
@@ -540,9 +548,12 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
   for (int c0 = t0; c0 < t1; c0 += ntp) {
     int it = c0 + ti;
     bool act = grp >= 0 && it < t1;
-    T xl = 0, yl = 0, zl = 0;
+    T xl = 0, yl = 0, zl = 0, xg = 0, yg = 0, zg = 0;   // target: local and global coordinates
     if (act) {
       T4 x = a.tpos[it];
+      xg = x.x;
+      yg = x.y;
+      zg = x.z;
       xl = x.x - cx;
       yl = x.y - cy;
       zl = x.z - cz;
@@ -666,6 +677,25 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
           T pe[KT];  // partial sum of this entry (plain mode)
 #pragma unroll
           for (int k = 0; k < KT; ++k) pe[k] = 0;
+          if constexpr ((PR == P_STK_L4 || PR == P_STK_G) && sizeof(T) == 4) {
+            if (!a.kahan) {
+              // Stokeslet in FP32: the image shift folded into the target's global coordinates
+              // once per entry (exact for the unshifted entries, so the self pair stays at
+              // r = 0), the pair terms accumulated by FMAs, four sources in flight
+              const float xe = xg - (float)(sx * a.geo.L), ye = yg - (float)(sy * a.geo.L),
+                          ze = zg - (float)(sz * a.geo.L);
+              int j = grp;
+              for (; j + 3 * G < cnt; j += 4 * G) {
+#pragma unroll
+                for (int w = 0; w < 4; ++w) stk_pair_f32(xe, ye, ze, sp[base + j + w * G], sv[base + j + w * G], pe);
+              }
+              for (; j < cnt; j += G) stk_pair_f32(xe, ye, ze, sp[base + j], sv[base + j], pe);
+#pragma unroll
+              for (int k = 0; k < KT; ++k) acc[k] += pe[k];
+              base += cnt;
+              continue;
+            }
+          }
           for (int j = grp; j < cnt; j += G) {
             T4 y = sp[base + j];
             T r0 = xl - (y.x + ox), r1 = yl - (y.y + oy), r2 = zl - (y.z + oz);
@@ -819,9 +849,19 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
     return (int)((k & 1) | ((k >> 1) & 1) << 1 | ((k >> 2) & 1) << 2);
   };
   int vmin = P.bc == KAFMM_BC_PXYZ ? 1 : 2;
-  // M->L: all boxes at levels >= vmin, grouped by class; tensor-core tiles use NB_TC boxes
+  // M->L: all boxes at levels >= vmin, grouped by class; tensor-core tiles use NB_TC boxes.
+  // Inside a class, boxes with the same V slot occupancy are kept together (sorted by its
+  // signature, stable), so a tile's slot union is close to each box's own V list: boxes near
+  // the domain boundary or a coarse neighbour have fewer V entries than interior ones.
+  std::vector<unsigned long long> vsig(nb);
+  CK(cudaMemcpyAsync(vsig.data(), T.vsig.p, sizeof(unsigned long long) * (size_t)nb,
+                     cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   for (int b = 0; b < nb; ++b)
     if (lvl[b] >= vmin) by_cls[cls(b)].push_back(b);
+  for (int c = 0; c < 8; ++c)
+    std::stable_sort(by_cls[c].begin(), by_cls[c].end(),
+                     [&](int x, int y) { return vsig[x] < vsig[y]; });
   add_tiles(W, by_cls, NB_TC, W.m2l);
   // M->M per level: non-leaf boxes (class irrelevant: use class 0 bucket).  Multipoles are
   // read by M->L (levels >= vmin), by M->T over W lists (W entries lie at level >= 2) and, when

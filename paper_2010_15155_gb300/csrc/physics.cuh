@@ -45,6 +45,28 @@ __device__ inline T inv_r(T rr) { return rr > T(0) ? rsqrt_<T>(rr) : T(0); }
 // Source values: v0 = (q | f1 f2 f3 [b]) ; DL: v0 = D00 D01 D02 D10, v1 = D11 D12 D20 D21,
 // v2 = D22.  acc has KT entries.
 
+// 1/sqrt(x) for normal x > 0 in one approximate instruction (inputs here are squared distances
+// between distinct points in the unit cube, far above the subnormal range; zero is tested
+// before the call).
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// One Stokeslet pair in FP32 accumulated into acc[0..2] (scaled by 1/(8 pi) at the end):
+// acc += f / r + r (r.f) / r^3 with r = x - y; zero for r = 0.
+__device__ __forceinline__ void stk_pair_f32(float xe, float ye, float ze, const float4& y,
+                                             const float4& f, float* acc) {
+  float r0 = xe - y.x, r1 = ye - y.y, r2 = ze - y.z;
+  float rr = fmaf(r0, r0, fmaf(r1, r1, r2 * r2));
+  float ir = rr > 0.f ? rsqrt_ftz(rr) : 0.f;
+  float rf = fmaf(r0, f.x, fmaf(r1, f.y, r2 * f.z)) * (ir * ir * ir);
+  acc[0] = fmaf(r0, rf, fmaf(f.x, ir, acc[0]));
+  acc[1] = fmaf(r1, rf, fmaf(f.y, ir, acc[1]));
+  acc[2] = fmaf(r2, rf, fmaf(f.z, ir, acc[2]));
+}
+
 // Laplace L = 1/(4 pi r)
 template <class T>
 __device__ inline void lap_st(T r0, T r1, T r2, T q, T* acc) {

@@ -42,7 +42,8 @@ struct Tree {
   DevBuf d_lvl_start, key, level, parent, child, sb, se, tb, te, leaf, leaves, prob;
   // lists, CSR over boxes (entries packed with pack_entry)
   DevBuf u_off, u_ent, w_off, w_ent, x_off, x_ent;
-  DevBuf vtab;                      // [nbox][189] source box of each V slot or -1
+  DevBuf vtab;                      // [nbox][216] source box of each V slot or LIST_EMPTY
+  DevBuf vsig;                      // [nbox] signature of the box's V slot occupancy
   DevBuf w_flag;                    // [nbox] 1 if the box appears in some W list
   // scratch of the build
   DevBuf s_keys2, s_vals2, s_hist, t_keys2, t_vals2;

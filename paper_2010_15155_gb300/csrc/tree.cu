@@ -530,10 +530,23 @@ __global__ void k_leaf_list(const int8_t* leaf, const int* leaf_pos, int nbox, i
     if (leaf[b]) leaves[leaf_pos[b]] = b;
 }
 
-__global__ void k_tree_stats(TreeView t, const int32_t* vtab, unsigned long long* out) {
+// V entry count and largest leaf; per box a 64-bit signature of its V slot occupancy (boxes
+// with equal signatures are grouped into the same tensor-core tiles).
+__global__ void k_tree_stats(TreeView t, const int32_t* vtab, unsigned long long* out,
+                             unsigned long long* vsig) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x) {
-    unsigned long long nv = 0;
-    for (int k = 0; k < 216; ++k) nv += vtab[(int64_t)b * 216 + k] != LIST_EMPTY;
+    unsigned long long nv = 0, h = 1469598103934665603ull;   // FNV-1a offset basis
+    uint64_t word = 0;
+    for (int k = 0; k < 216; ++k) {
+      bool on = vtab[(int64_t)b * 216 + k] != LIST_EMPTY;
+      nv += on;
+      word |= (uint64_t)on << (k & 63);
+      if ((k & 63) == 63 || k == 215) {
+        h = (h ^ word) * 1099511628211ull;
+        word = 0;
+      }
+    }
+    vsig[b] = h;
     atomicAdd(&out[0], nv);
     if (t.leaf[b]) {
       unsigned long long np = (unsigned long long)max(t.se[b] - t.sb[b], t.te[b] - t.tb[b]);
@@ -827,7 +840,9 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   // V entries and the largest leaf
   unsigned long long* stats = (unsigned long long*)(T.status.as<unsigned>() + 10);
   CK(cudaMemsetAsync(stats, 0, 16, st));
-  KL k_tree_stats<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vtab.as<int32_t>(), stats);
+  CK(T.vsig.reserve(sizeof(unsigned long long) * (nb + 1)));
+  KL k_tree_stats<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vtab.as<int32_t>(), stats,
+                                                   T.vsig.as<unsigned long long>());
   unsigned long long hs[2];
   CK(cudaMemcpyAsync(hs, stats, 16, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -39,11 +39,45 @@ WORKLOAD = "stokeslet_uniform_256k_p10_q128_l4"
 # pair in the leaf kernel (stk_st): 3 sub, r^2 (5), rsqrt, ir^3 (2), r.f (5), scale (1),
 # 3 x (mul + FMA + FMA = 5) -> 29.
 FLOP_ST_PAIR = 29
+# DRAM bytes (read + written) of one M->L launch of this workload in the mixed form, from the ncu
+# capture summarised in profiles/m2l_tc_stokeslet_uniform_256k_p10.md (set to None when the
+# kernel changes until it is captured again)
+M2L_DRAM_BYTES = 5.693392e6 + 137.889280e6
 
 
 def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _dist_init(world, backend="nccl"):
+    """One process per GPU (torchrun): joins the process group when world > 1."""
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend)
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(value, world, device=None):
+    """The slowest rank's time: the whole job's step time."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _rank_seed(base, rank):
+    """Every rank works on its own seeded inputs (replicas, or its own batch of problems): the
+    units are partitioned across ranks and no data crosses them."""
+    return base + rank
 
 
 def _peaks():
@@ -151,14 +185,12 @@ def run_gpu(args):
     from paper_2010_15155_gb300 import kafmm as K
 
     rank, world, local = _env_rank()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    _dist_init(world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    pts, f = workloads.stokes_uniform(N_POINTS, seed=1 + rank, dtype=np.float32)
+    pts, f = workloads.stokes_uniform(N_POINTS, seed=_rank_seed(1, rank), dtype=np.float32)
     y = torch.from_numpy(pts).to(dev)
     s = torch.from_numpy(f).to(dev)
     g = torch.empty((N_POINTS, 3), dtype=torch.float32, device=dev)
@@ -190,8 +222,7 @@ def run_gpu(args):
         flush.fill_(1.0)
         step()
     torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
+    _barrier(world)
     clocks = ClockSampler(local)
     times, phases = [], []
     torch.cuda.synchronize(dev)
@@ -205,14 +236,10 @@ def run_gpu(args):
         times.append(e0.elapsed_time(e1))
         phases.append(plan.phase_times())
     torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
+    _barrier(world)
     clk = clocks.stop()
     ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(ms, world, dev)
     value = world * N_POINTS / (ms * 1e-3) / 1e6
 
     # end to end through the C ABI with pinned host buffers
@@ -285,7 +312,8 @@ def run_gpu(args):
         "phases_ms": ph,
         "tree": info,
         "roofline": {"bound": bound, "kernel": "m2l", "achieved": achieved, "peak": peak,
-                     "unit": unit, "frac": achieved / peak, "traffic": None,
+                     "unit": unit, "frac": achieved / peak,
+                     "traffic": M2L_DRAM_BYTES if args.precision == "mixed" else None,
                      "peak_source": peak_note},
         "e2e": {"value": world * N_POINTS / (e2e_ms * 1e-3) / 1e6, "unit": "Mpoints/s",
                 "h2d_bytes_per_step": int(pts.nbytes + f.nbytes),
@@ -310,15 +338,13 @@ def run_gpu_batched(args):
     from paper_2010_15155_gb300 import kafmm as K
 
     rank, world, local = _env_rank()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    _dist_init(world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     p_ord, q_leaf, n_prob = 8, 64, 512
-    sizes = workloads.batched_sizes(n_prob, seed=3 + rank)
-    pts, f, off = workloads.batched_stokes(sizes, seed=3 + rank)
+    sizes = workloads.batched_sizes(n_prob, seed=_rank_seed(3, rank))
+    pts, f, off = workloads.batched_stokes(sizes, seed=_rank_seed(3, rank))
     ntot = int(off[-1])
     y = torch.from_numpy(pts).to(dev)
     s = torch.from_numpy(f).to(dev)
@@ -353,8 +379,7 @@ def run_gpu_batched(args):
         flush.fill_(1.0)
         step()
     torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
+    _barrier(world)
     clocks = ClockSampler(local)
     times, phases = [], []
     for i in range(args.steps):
@@ -367,14 +392,10 @@ def run_gpu_batched(args):
         times.append(e0.elapsed_time(e1))
         phases.append(plan.phase_times())
     torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
+    _barrier(world)
     clk = clocks.stop()
     ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(ms, world, dev)
     value = world * ntot / (ms * 1e-3) / 1e6
     info = plan.info()
     ph = {k: float(np.median([p[k] for p in phases])) for k in phases[0]}

@@ -94,7 +94,13 @@ enum {
    * the first call for the current points), so a second and later call can be captured into a
    * CUDA graph and replayed; device-side timeouts then accumulate in a status word that
    * kafmm_status reports.  Host arrays are always handled synchronously. */
-  KAFMM_OPT_SYNC = 7
+  KAFMM_OPT_SYNC = 7,
+  /* Pipeline depth of the tensor-core gather-GEMM (mixed form): 2 stages of 96 KB (operand rows
+   * of 128 bytes, 64 bf16 / 32 tf32 k-values per stage) or 4 stages of 48 KB (64-byte rows, half
+   * the k-values per stage).  Both issue the same MMAs in the same order and give bit-identical
+   * results.  Default 2: 4 measured slower on GB300 (Stokeslet N = 262144: M->L 7.1 ms against
+   * 5.3 ms at p = 10, 33 ms against 25 ms at p = 8). */
+  KAFMM_OPT_TC_STAGES = 8
 };
 enum { KAFMM_TC_TF32X3 = 0, KAFMM_TC_BF16X3 = 1, KAFMM_TC_AUTO = 2 };
 enum { KAFMM_PREC_FP64 = 0, KAFMM_PREC_FP32 = 1, KAFMM_PREC_MIXED = 2 };

@@ -158,6 +158,10 @@ extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
     case KAFMM_OPT_SYNC:
       P.sync = value ? 1 : 0;
       return 0;
+    case KAFMM_OPT_TC_STAGES:
+      if (value != 2 && value != 4) return fail(P, KAFMM_ERR_ARG, "tensor-core stages must be 2 or 4");
+      P.tc_stages = (int)value;
+      return 0;
     case KAFMM_OPT_TC_SPLIT:
       if (value != KAFMM_TC_TF32X3 && value != KAFMM_TC_BF16X3 && value != KAFMM_TC_AUTO)
         return fail(P, KAFMM_ERR_ARG, "bad tensor-core split %lld", (long long)value);

@@ -36,40 +36,49 @@ namespace tc {
 // tile, so every B element the producers build feeds RB x 3 MMAs.  RB = 2 when the number of
 // row blocks is even, else 1 (a lone last block would waste a pair's B tile).  Shared memory
 // per stage (96 KB) and TMEM (RB x BN accumulator + running-sum columns) are the same for both.
-constexpr int BM = 128, STAGES = 2;
-constexpr int A_BYTES = 16384;              // 128 rows x 128 B per split and row block
-constexpr int STAGE_BYTES = 6 * A_BYTES;   // A hi/lo of RB blocks + B hi/lo: 96 KB (both RB)
-template <int RB>
+//
+// Pipeline: the operand rows of a stage are SWB bytes wide, stored with the SWB-byte swizzle:
+// SWB = 128 gives two stages of 96 KB, SWB = 64 four stages of 48 KB (half the k per stage,
+// twice the stages in flight, the same MMAs in the same order).
+constexpr int BM = 128;
+template <int RB, int SWB>
 struct Shape {
   static constexpr int BN = 256 / RB, NB = BN / 4;
-  static constexpr int A_STAGE = RB * 2 * A_BYTES;       // A hi/lo of all row blocks
-  static constexpr int B_BYTES = BN * 128;               // BN rows x 128 B per split
-  static_assert(A_STAGE + 2 * B_BYTES == STAGE_BYTES, "96 KB per stage");
+  static constexpr int A_TILE = BM * SWB;                // 128 rows per split and row block
+  static constexpr int A_STAGE = RB * 2 * A_TILE;        // A hi/lo of all row blocks
+  static constexpr int B_TILE = BN * SWB;                // BN rows per split
+  static constexpr int STAGE_BYTES = A_STAGE + 2 * B_TILE;
+  static constexpr int STAGES = 196608 / STAGE_BYTES;
+  static_assert(STAGE_BYTES == 768 * SWB, "96 KB (SWB 128) or 48 KB (SWB 64) per stage");
 };
-// non-M->L modes drain the TMEM accumulator into the running sum after every k-chunk: the
-// pseudo-inverse factors sum with heavy cancellation, and accumulating two chunks per drain
-// measured 1.3e-5 against the FP64 form at p = 8 (8.7e-6 with one; Stokeslet N = 262144)
-constexpr int AUX_DRAIN = 1;
+// dynamic shared memory: 192 KB of stages + alignment and slack
+constexpr int SMEM_BYTES = 196608 + 4096 + 16384;
+// non-M->L modes drain the TMEM accumulator into the running sum after every 64 k-values (one
+// 128-byte chunk): the pseudo-inverse factors sum with heavy cancellation, and accumulating two
+// such chunks per drain measured 1.3e-5 against the FP64 form at p = 8 (8.7e-6 with one;
+// Stokeslet N = 262144)
+template <int SWB>
+constexpr int aux_drain() { return 128 / SWB; }
 constexpr int THREADS = 448;
 constexpr int NPROD = 256;
 constexpr int W_TMA = 12, W_MMA = 13;
 
-// Split formats: a 128-byte swizzle row holds BK elements; one MMA consumes MK of them.
+// Split formats: an SWB-byte swizzle row holds SWB / ES elements; one MMA consumes MK of them
+// (32 bytes in both formats).
 template <int SPLIT>
 struct Fmt;
 template <>
 struct Fmt<SPLIT_TF32> {  // kind::tf32, K = 8 per instruction
-  static constexpr int ES = 4, BK = 32, MK = 8;
+  static constexpr int ES = 4, MK = 8;
   static constexpr uint32_t AB = 2;
 };
 template <>
 struct Fmt<SPLIT_BF16> {  // kind::f16 with bf16 operands, K = 16 per instruction
-  static constexpr int ES = 2, BK = 64, MK = 16;
+  static constexpr int ES = 2, MK = 16;
   static constexpr uint32_t AB = 1;
 };
 constexpr uint32_t TMEM_COLS = 512;         // [0,256) accumulators, [256,512) running sums
 constexpr uint32_t SUM_COL = 256;           // row block r: accumulator r*BN, sum SUM_COL + r*BN
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 4096;
 
 // Modes of the gather-GEMM: target box b (of a tile), slots s, out[b] (+)= sum_s
 // T_s * shift_s(in[src(b, s)]):
@@ -190,15 +199,17 @@ __device__ __forceinline__ void arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// K-major, 128-byte swizzle UMMA shared-memory descriptor (SM100 format, version 1):
-// start >> 4, LBO = 16 B (unused for swizzled K-major), SBO = 1024 B (8-row groups).
+// K-major UMMA shared-memory descriptor (SM100 format, version 1) for SWB-byte swizzled rows:
+// start >> 4, LBO = 16 B (unused for swizzled K-major), SBO = 8 rows x SWB bytes, layout
+// SWIZZLE_128B (2) or SWIZZLE_64B (4).
+template <int SWB>
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);
   d |= (uint64_t)(16 >> 4) << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)((8 * SWB) >> 4) << 32;
   d |= (uint64_t)1 << 46;       // descriptor version
-  d |= (uint64_t)2 << 61;       // SWIZZLE_128B
+  d |= (uint64_t)(SWB == 128 ? 2 : 4) << 61;
   return d;
 }
 
@@ -275,12 +286,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-template <int SPLIT, int RB>
+template <int SPLIT, int RB, int SWB>
 __global__ void __launch_bounds__(THREADS, 1)
     k_m2l_tc(const __grid_constant__ CUtensorMap tmap, Args a) {
-  constexpr int BK = Fmt<SPLIT>::BK, MK = Fmt<SPLIT>::MK;
-  constexpr int BN = Shape<RB>::BN, NB = Shape<RB>::NB, B_BYTES = Shape<RB>::B_BYTES,
-                A_STAGE = Shape<RB>::A_STAGE;
+  constexpr int BK = SWB / Fmt<SPLIT>::ES, MK = Fmt<SPLIT>::MK;
+  using S = Shape<RB, SWB>;
+  constexpr int BN = S::BN, NB = S::NB, B_BYTES = S::B_TILE, A_BYTES = S::A_TILE,
+                A_STAGE = S::A_STAGE, STAGE_BYTES = S::STAGE_BYTES, STAGES = S::STAGES;
   constexpr int PROD_WARPS = NPROD / 32;
   // offsets accumulated in TMEM before each drain into the running sum: longer chains lose
   // accuracy in TF32x3 (measured 5.4e-6 -> 8.2e-6 at p = 10 with 2), BF16x3 is limited by its
@@ -289,7 +301,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full[STAGES], empty[STAGES], acc_full, acc_empty;
+  __shared__ uint64_t full[4], empty[4], acc_full, acc_empty;
   __shared__ uint32_t tmem_base;
   __shared__ int nslots, bail;
   __shared__ int slot_list[216];
@@ -359,7 +371,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int total = ns * nchunk;
   // accumulation groups: iterations accumulated in TMEM before the epilogue adds them into the
   // running sum (M->L: DRAIN whole offsets; other modes: AUX_DRAIN k-chunks)
-  const int GI = a.mode == TC_M2L ? DRAIN * nchunk : AUX_DRAIN;
+  const int GI = a.mode == TC_M2L ? DRAIN * nchunk : aux_drain<SWB>();
   const int ngroups = (total + GI - 1) / GI;
 
   if (warp == W_TMA) {
@@ -393,36 +405,49 @@ __global__ void __launch_bounds__(THREADS, 1)
     // box's four channels.  Lane l takes EPL consecutive k (two for bf16, one for tf32), i.e.
     // one 32-bit word of each of the 8 rows (4 channels x hi/lo) at word l of the 128-byte
     // row: the warp's loads are contiguous and each store instruction writes a full row.
-    constexpr int EPL = 4 / Fmt<SPLIT>::ES;          // k values per lane
-    constexpr int UPW = NB / PROD_WARPS;             // boxes per producer warp per chunk
-    constexpr int UH = UPW / 2;                      // boxes per half stage
+    constexpr int EPL = 4 / Fmt<SPLIT>::ES;          // k values per lane (one 32-bit word)
+    constexpr int WPR = SWB / 4;                     // 32-bit words per operand row
+    constexpr int BPI = 32 / WPR;                    // boxes per warp instruction (1 or 2)
+    constexpr int UPW = NB / PROD_WARPS;             // boxes per producer warp per stage
+    constexpr int LPS = UPW / BPI;                   // boxes per lane per stage
+    constexpr int UH = LPS / 2;                      // boxes per lane per half stage
+    static_assert(UH >= 1 && LPS == 2 * UH, "two half stages");
     const int pw = warp - 4;
-    // Box j = pw + 8u has rows n = 4j + ch = (4 pw + ch) + 32u: the 128-byte swizzle row of
-    // (u, ch) sits 4096 u bytes after that of (0, ch), and the chunk swizzle (n & 7) does not
-    // depend on u.  Word `lane` of row n: chunk (lane / 4) ^ (n & 7), word lane & 3.
+    const int bsel = lane / WPR;                     // which of the BPI boxes the lane serves
+    const int wd = lane % WPR;                       // the lane's word of the row
+    // Lane box ul (0..LPS-1) is u = bsel + BPI ul of the warp's boxes, j = pw + 8u, with rows
+    // n = 4j + ch = (4 pw + ch) + 32u: the swizzled row of (u, ch) sits 32 u SWB bytes after that
+    // of (0, ch), and the chunk swizzle depends on n & 7 only.  With two boxes per instruction
+    // the second writes channel ch ^ 1 (rows of opposite parity: the other 64-byte bank half).
+    auto swz_off = [&](int n) -> uint32_t {
+      int x = SWB == 128 ? (n & 7) : ((n >> 1) & 3);
+      return (uint32_t)((n >> 3) * (8 * SWB) + (n & 7) * SWB + ((((wd >> 2) ^ x) & (SWB / 16 - 1)) << 4) +
+                        (wd & 3) * 4);
+    };
     uint32_t roff[4];
 #pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
-      int n = 4 * pw + ch;
-      roff[ch] = (uint32_t)((n >> 3) * 1024 + (n & 7) * 128 + ((((lane >> 2) ^ n) & 7) << 4) + (lane & 3) * 4);
+    for (int i = 0; i < 4; ++i) {
+      int ch = BPI == 2 ? (i ^ bsel) : i;
+      roff[i] = swz_off(4 * pw + ch) + (uint32_t)(32 * SWB * bsel);
     }
-    // source box (flat index into up) of each of this warp's boxes for the current slot, or -1
-    int srcb[UPW];
+    // source box (flat index into up) of each of this lane's boxes for the current slot, or -1
+    int srcb[LPS];
     int cur_slot = -1;
+    auto box_of = [&](int ul) { return pw + PROD_WARPS * (bsel + BPI * ul); };
     auto set_slot = [&](int s) {
 #pragma unroll
-      for (int u = 0; u < UPW; ++u) srcb[u] = slot_src(a, sbox[pw + PROD_WARPS * u], s);
+      for (int ul = 0; ul < LPS; ++ul) srcb[ul] = slot_src(a, sbox[box_of(ul)], s);
     };
-    // Software pipeline over half stages (UH boxes each): the loads of the next half are in
-    // flight while the current half is converted, including the first half of the next stage
-    // (registers only: no shared-memory stage is needed to issue them).
+    // Software pipeline over half stages (UH boxes per lane each): the loads of the next half
+    // are in flight while the current half is converted, including the first half of the next
+    // stage (registers only: no shared-memory stage is needed to issue them).
     auto load_half = [&](int it, int h, float4 (&q)[UH][EPL]) {
       int s = slot_list[it / nchunk], c = it % nchunk;
       if (s != cur_slot) {
         set_slot(s);
         cur_slot = s;
       }
-      const int k0 = c * BK + lane * EPL;
+      const int k0 = c * BK + wd * EPL;
       const bool kin = k0 < R;   // R and k0 even: a bf16 pair is all in or out
 #pragma unroll
       for (int u = 0; u < UH; ++u) {
@@ -450,8 +475,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t blo = bhi + B_BYTES;
 #pragma unroll
       for (int u = 0; u < UH; ++u) {
-        const int uu = h * UH + u;
-        float side = sside[pw + PROD_WARPS * uu];
+        const int ul = h * UH + u;
+        float side = sside[box_of(ul)];
         float sx = ox * side, sy = oy * side, sz = oz * side;
         float v[4][EPL];
 #pragma unroll
@@ -461,22 +486,30 @@ __global__ void __launch_bounds__(THREADS, 1)
           v[2][t] = q[u][t].z;
           v[3][t] = q[u][t].w + sx * q[u][t].x + sy * q[u][t].y + sz * q[u][t].z;
         }
+        uint32_t hw[4], lw[4];
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
-          uint32_t hw, lw;
           if (SPLIT == SPLIT_TF32) {
             float hf = tf32_rn(v[ch][0]);
-            hw = __float_as_uint(hf);
-            lw = __float_as_uint(tf32_rn(v[ch][0] - hf));
+            hw[ch] = __float_as_uint(hf);
+            lw[ch] = __float_as_uint(tf32_rn(v[ch][0] - hf));
           } else {
             __nv_bfloat162 h2 = __floats2bfloat162_rn(v[ch][0], v[ch][EPL - 1]);
             float2 hf = __bfloat1622float2(h2);
-            hw = *reinterpret_cast<uint32_t*>(&h2);
-            lw = pack_bf16(v[ch][0] - hf.x, v[ch][EPL - 1] - hf.y);
+            hw[ch] = *reinterpret_cast<uint32_t*>(&h2);
+            lw[ch] = pack_bf16(v[ch][0] - hf.x, v[ch][EPL - 1] - hf.y);
           }
-          const uint32_t off = roff[ch] + 4096u * uu;
-          st_shared_u32(bhi + off, hw);
-          st_shared_u32(blo + off, lw);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          uint32_t h_ = hw[i], l_ = lw[i];
+          if (BPI == 2 && bsel) {
+            h_ = hw[i ^ 1];
+            l_ = lw[i ^ 1];
+          }
+          const uint32_t off = roff[i] + (uint32_t)(32 * SWB * BPI) * ul;
+          st_shared_u32(bhi + off, h_);
+          st_shared_u32(blo + off, l_);
         }
       }
     };
@@ -523,10 +556,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t d = tmem + (uint32_t)(r * BN);
 #pragma unroll
             for (int kk = 0; kk < BK / MK; ++kk) {
-              uint32_t ko = kk * 32;  // MK elements = 32 bytes in both formats
-              mma<SPLIT, BN>(d, sdesc(ahi + ko), sdesc(bhi + ko), (first && kk == 0) ? 0u : 1u);
-              mma<SPLIT, BN>(d, sdesc(ahi + ko), sdesc(blo + ko), 1u);
-              mma<SPLIT, BN>(d, sdesc(alo + ko), sdesc(bhi + ko), 1u);
+              uint32_t ko = kk * 32;  // MK elements = 32 bytes in both formats and swizzles
+              mma<SPLIT, BN>(d, sdesc<SWB>(ahi + ko), sdesc<SWB>(bhi + ko), (first && kk == 0) ? 0u : 1u);
+              mma<SPLIT, BN>(d, sdesc<SWB>(ahi + ko), sdesc<SWB>(blo + ko), 1u);
+              mma<SPLIT, BN>(d, sdesc<SWB>(alo + ko), sdesc<SWB>(bhi + ko), 1u);
             }
           }
           commit(&empty[st]);
@@ -608,11 +641,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-// dn[b] += sum of the partial sums over the offset ranges, in range order (boxes of the M->L
-// tiles only).
+// dn[b] (+)= sum of the partial sums over the slot ranges, in range order (boxes of the tiles
+// only); add = 0 stores.
 __global__ void k_combine_parts(const float4* __restrict__ parts, int64_t part_stride4, int nsplit,
                                 float4* __restrict__ dn, const int4* __restrict__ tiles, int ntiles,
-                                const int* __restrict__ boxlist, int R) {
+                                const int* __restrict__ boxlist, int R, int add) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int4 tile = tiles[t];
     for (int e = threadIdx.x; e < tile.y * R; e += blockDim.x) {
@@ -626,12 +659,14 @@ __global__ void k_combine_parts(const float4* __restrict__ parts, int64_t part_s
         v.z += w.z;
         v.w += w.w;
       }
-      float4 d = dn[i];
-      d.x += v.x;
-      d.y += v.y;
-      d.z += v.z;
-      d.w += v.w;
-      dn[i] = d;
+      if (add) {
+        float4 d = dn[i];
+        v.x += d.x;
+        v.y += d.y;
+        v.z += d.z;
+        v.w += d.w;
+      }
+      dn[i] = v;
     }
   }
 }
@@ -651,9 +686,9 @@ bool tc_supported(Plan& P) {
   return major == 10 && minor == 3;
 }
 
-// Tensor map over a split operator array [nops][2][R][Rpad] (tf32 or bf16), 128-byte swizzle,
-// boxes of 128 rows x 128 bytes.
-static int make_tmap(Plan& P, CUtensorMap* map, void* base, int nops, bool tf32) {
+// Tensor map over a split operator array [nops][2][R][Rpad] (tf32 or bf16), swb-byte swizzle,
+// boxes of 128 rows x swb bytes.
+static int make_tmap(Plan& P, CUtensorMap* map, void* base, int nops, bool tf32, int swb) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -666,11 +701,12 @@ static int make_tmap(Plan& P, CUtensorMap* map, void* base, int nops, bool tf32)
   int es = tf32 ? 4 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)P.Rpad, (cuuint64_t)nops * 2 * P.R};
   cuuint64_t strides[1] = {(cuuint64_t)P.Rpad * es};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / es), tc::BM};
+  cuuint32_t box[2] = {(cuuint32_t)(swb / es), tc::BM};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                       2, base, dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      swb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(P, KAFMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return 0;
@@ -678,13 +714,19 @@ static int make_tmap(Plan& P, CUtensorMap* map, void* base, int nops, bool tf32)
 
 static int tc_prepare(Plan& P) {
   if (P.tmap_ready) return 0;
-  int rc = make_tmap(P, reinterpret_cast<CUtensorMap*>(P.tmap), P.opstc.p, N_M2L, P.tc_split == SPLIT_TF32);
-  if (rc) return rc;
-  rc = make_tmap(P, reinterpret_cast<CUtensorMap*>(P.tmap_aux), P.opstc_aux.p, N_AUX, true);
-  if (rc) return rc;
+  for (int sw = 0; sw < 2; ++sw) {   // 128- and 64-byte swizzled rows
+    int swb = sw == 0 ? 128 : 64;
+    int rc = make_tmap(P, reinterpret_cast<CUtensorMap*>(P.tmaps[0][sw]), P.opstc.p, N_M2L,
+                       P.tc_split == SPLIT_TF32, swb);
+    if (rc) return rc;
+    rc = make_tmap(P, reinterpret_cast<CUtensorMap*>(P.tmaps[1][sw]), P.opstc_aux.p, N_AUX, true, swb);
+    if (rc) return rc;
+  }
   cudaError_t e = cudaSuccess;
-  for (auto fn : {tc::k_m2l_tc<SPLIT_TF32, 1>, tc::k_m2l_tc<SPLIT_TF32, 2>, tc::k_m2l_tc<SPLIT_BF16, 1>,
-                  tc::k_m2l_tc<SPLIT_BF16, 2>})
+  for (auto fn : {tc::k_m2l_tc<SPLIT_TF32, 1, 128>, tc::k_m2l_tc<SPLIT_TF32, 2, 128>,
+                  tc::k_m2l_tc<SPLIT_BF16, 1, 128>, tc::k_m2l_tc<SPLIT_BF16, 2, 128>,
+                  tc::k_m2l_tc<SPLIT_TF32, 1, 64>, tc::k_m2l_tc<SPLIT_TF32, 2, 64>,
+                  tc::k_m2l_tc<SPLIT_BF16, 1, 64>, tc::k_m2l_tc<SPLIT_BF16, 2, 64>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
   if (e != cudaSuccess) return cuda_fail(P, e, "cudaFuncSetAttribute(k_m2l_tc)");
   P.tmap_ready = true;
@@ -699,12 +741,15 @@ int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* 
   int rc = tc_prepare(P);
   if (rc) return rc;
   const bool m2l = mode == tc::TC_M2L;
-  const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(m2l ? P.tmap : P.tmap_aux);
+  const int sw = P.tc_stages == 4 ? 1 : 0;   // 64-byte rows, four stages : 128-byte rows, two
+  const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(P.tmaps[m2l ? 0 : 1][sw]);
   const int split = m2l ? P.tc_split : SPLIT_TF32;
   int rows = (P.R + P.tc_rb * tc::BM - 1) / (P.tc_rb * tc::BM);   // CTAs per tile
-  // offset ranges per tile (M->L only): enough CTAs to fill the 152 SMs over several waves
+  // slot ranges per tile (M->L offsets, M->M child octants): enough CTAs to fill the 152 SMs
+  // over several waves; the ranges' partial sums are combined in fixed order
+  const bool splittable = m2l || mode == tc::TC_M2M;
   int nsplit = 1;
-  while (m2l && nsplit < 4 && (int64_t)ntiles * rows * nsplit < 152 * 6) nsplit *= 2;
+  while (splittable && nsplit < 4 && (int64_t)ntiles * rows * nsplit < 152 * 6) nsplit *= 2;
   int64_t part_stride = (int64_t)P.tree.nbox * P.R * 4;
   if (nsplit > 1) {
     cudaError_t e = P.m2l_parts.reserve(sizeof(float) * part_stride * nsplit + 256);
@@ -727,19 +772,26 @@ int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* 
   a.write = nsplit > 1 ? tc::TC_STORE : write;
   a.op = m2l ? 0 : op_slot - OP_M2M;
   dim3 grid(ntiles, rows, nsplit);
-  a.nchunk = P.Rpad / (split == SPLIT_TF32 ? tc::Fmt<SPLIT_TF32>::BK : tc::Fmt<SPLIT_BF16>::BK);
-  if (split == SPLIT_TF32 && P.tc_rb == 2)
-    KL tc::k_m2l_tc<SPLIT_TF32, 2><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
-  else if (split == SPLIT_TF32)
-    KL tc::k_m2l_tc<SPLIT_TF32, 1><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
-  else if (P.tc_rb == 2)
-    KL tc::k_m2l_tc<SPLIT_BF16, 2><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
-  else
-    KL tc::k_m2l_tc<SPLIT_BF16, 1><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a);
+  const int swb = sw ? 64 : 128;
+  a.nchunk = P.Rpad / (swb / (split == SPLIT_TF32 ? tc::Fmt<SPLIT_TF32>::ES : tc::Fmt<SPLIT_BF16>::ES));
+#define KAFMM_TC_LAUNCH(SP, RBv, SW) \
+  KL tc::k_m2l_tc<SP, RBv, SW><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a)
+  if (swb == 128) {
+    if (split == SPLIT_TF32 && P.tc_rb == 2) KAFMM_TC_LAUNCH(SPLIT_TF32, 2, 128);
+    else if (split == SPLIT_TF32) KAFMM_TC_LAUNCH(SPLIT_TF32, 1, 128);
+    else if (P.tc_rb == 2) KAFMM_TC_LAUNCH(SPLIT_BF16, 2, 128);
+    else KAFMM_TC_LAUNCH(SPLIT_BF16, 1, 128);
+  } else {
+    if (split == SPLIT_TF32 && P.tc_rb == 2) KAFMM_TC_LAUNCH(SPLIT_TF32, 2, 64);
+    else if (split == SPLIT_TF32) KAFMM_TC_LAUNCH(SPLIT_TF32, 1, 64);
+    else if (P.tc_rb == 2) KAFMM_TC_LAUNCH(SPLIT_BF16, 2, 64);
+    else KAFMM_TC_LAUNCH(SPLIT_BF16, 1, 64);
+  }
+#undef KAFMM_TC_LAUNCH
   if (nsplit > 1)
     KL tc::k_combine_parts<<<std::min(ntiles, 152 * 4), 256, 0, st>>>(
         P.m2l_parts.as<float4>(), part_stride / 4, nsplit, reinterpret_cast<float4*>(out), tiles, ntiles,
-        boxlist, P.R);
+        boxlist, P.R, write == tc::TC_ADD ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(P, e, "k_m2l_tc launch");
   return 0;

@@ -86,10 +86,11 @@ struct Plan {
   int tc_split = SPLIT_TF32;        // split format of the tensor-core M->L in use
   int tc_split_opt = KAFMM_TC_AUTO; // the requested format (option)
   int tc_rb = 2, tc_boxes = 32;     // row blocks and target boxes per tensor-core CTA
-  alignas(64) unsigned char tmap[128];  // TMA descriptor of opstc
-  bool tmap_ready = false;
   DevBuf opstc_aux;                 // [N_AUX][2][R][Rpad] tf32 hi/lo of M->M, L->L, pinv factors
-  alignas(64) unsigned char tmap_aux[128];
+  // TMA descriptors: [opstc, opstc_aux][128-byte, 64-byte swizzled rows]
+  alignas(64) unsigned char tmaps[2][2][128];
+  bool tmap_ready = false;
+  int tc_stages = 2;                // pipeline depth of the tensor-core kernel (2 or 4)
   DevBuf unit64, unit32;            // unit surface [n][3]
   DevBuf tm2l64, tm2l32;            // periodic far-image operator [R][R]
   // tree + data

@@ -22,7 +22,7 @@ LAPLACE, STOKESLET, RPY, STOKES_DL = 0, 1, 2, 3
 BC_OPEN, BC_PXYZ = 0, 3
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN, OPT_TC_SPLIT = 1, 2, 3, 4, 5, 6
-OPT_SYNC = 7
+OPT_SYNC, OPT_TC_STAGES = 7, 8
 TC_TF32X3, TC_BF16X3, TC_AUTO = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 ML_G, ML_L4 = 0, 1
@@ -218,7 +218,7 @@ class Plan:
 
     def __init__(self, kernel, p, q, bc=BC_OPEN, precision=PREC_MIXED, variant=ML_L4,
                  near_only=False, kahan=False, stream=None, origin=(0.0, 0.0, 0.0), L=1.0,
-                 tc_split=TC_AUTO, sync=True):
+                 tc_split=TC_AUTO, sync=True, tc_stages=None):
         self.kernel = kernel
         self.ks, self.kt = KDIM[kernel]
         self.h = kafmm_plan(kernel, bc, p, q)
@@ -228,6 +228,8 @@ class Plan:
         kafmm_set_option(self.h, OPT_KAHAN, int(kahan))
         kafmm_set_option(self.h, OPT_TC_SPLIT, tc_split)
         kafmm_set_option(self.h, OPT_SYNC, int(sync))
+        if tc_stages is not None:
+            kafmm_set_option(self.h, OPT_TC_STAGES, tc_stages)
         if stream is not None:
             kafmm_set_option(self.h, OPT_STREAM, int(stream))
         kafmm_set_domain(self.h, origin, L)

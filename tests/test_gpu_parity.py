@@ -294,3 +294,21 @@ def test_eval_is_graph_capturable():
     assert torch.equal(g, ref2)
     K.kafmm_status(plan.h)
     plan.close()
+
+
+@pytest.mark.parametrize("p", [6, 8, 10])
+def test_tensor_core_pipeline_depths_agree_bit_for_bit(p):
+    """Two stages of 128-byte operand rows and four stages of 64-byte rows issue the same MMAs
+    in the same order: the mixed form (M->L, M->M, L->L, pseudo-inverse factors on the tensor
+    cores) gives identical bits with either."""
+    pts, f = W.stokes_uniform(30000, seed=9, dtype=np.float32)
+    y = torch.from_numpy(pts).cuda()
+    s = torch.from_numpy(f).cuda()
+    out = {}
+    for stages in (2, 4):
+        plan = K.Plan(K.STOKESLET, p=p, q=64, precision=K.PREC_MIXED, variant=K.ML_L4, tc_stages=stages)
+        plan.set_points(y)
+        out[stages] = plan.eval(s)
+        assert K.kafmm_get_counters(plan.h)["tensor_core_m2l"] == 1
+        plan.close()
+    assert torch.equal(out[2], out[4])

@@ -90,7 +90,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 20 ms during the timed region."""
 
     def __init__(self, index=0):
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
@@ -101,7 +101,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.p = None
@@ -214,6 +214,12 @@ def run_gpu(args):
         ref_plan.close()
         del gref
 
+    # tensor-core kernel configuration picked by the autotuner on these points (untimed setup)
+    tuned = None
+    if args.precision == "mixed":
+        plan.set_points(y)
+        tuned = K.kafmm_autotune(plan.h, s, g, K.F32)
+
     def step():
         plan.set_points(y)
         plan.eval(s, g)
@@ -276,6 +282,12 @@ def run_gpu(args):
         achieved = m2l_flops / m2l_s / 1e12
         peak_note = (f"{split_used}: {'tf32 = bf16 x 1.1/2.25' if split_used == 'tf32x3' else 'bf16'}"
                      f" dense burst, {src}; useful flops (split products not counted, max frac 1/3)")
+    elif args.precision == "fp64":
+        # FP64 on the CUDA cores: GB300's nominal dense FP64 rate (not measured on this machine)
+        bound, unit = "alu", "TFLOP/s"
+        peak = 1.25
+        achieved = m2l_flops / m2l_s / 1e12
+        peak_note = "FP64, nominal 1.25 TFLOP/s (no measured FP64 peak in the peaks file)"
     else:
         # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x max SM clock
         bound, unit = "alu", "TFLOP/s"
@@ -297,6 +309,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "n_points": N_POINTS, "p": P_ORDER, "q": Q_LEAF,
                    "ml_table": "four-channel Laplace", "precision": args.precision,
                    "tc_split": split_used if args.precision == "mixed" else None,
+                   "autotuned": tuned,
                    "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "rel_l2_vs_fp64": err,
@@ -371,6 +384,9 @@ def run_gpu_batched(args):
         ref_plan.close()
         del gref
 
+    plan.set_points_batched(y, off)
+    tuned = K.kafmm_autotune(plan.h, s, g, K.F32)
+
     def step():
         plan.set_points_batched(y, off)
         plan.eval(s, g)
@@ -440,6 +456,7 @@ def run_gpu_batched(args):
         "scaling": "weak", "vs_baseline": None, "dtype": f"f32+{split_used}", "data": "synthetic",
         "config": {"workload": f"stokeslet_batched_{n_prob}x_loguniform_1k_64k_p8_q64_l4",
                    "n_problems": n_prob, "n_points": ntot, "p": p_ord, "q": q_leaf,
+                   "autotuned": tuned,
                    "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": f"one batch per GPU x{world}" if world > 1 else "1 GPU"},
         "max_problem_rel_l2_vs_fp64": err,

@@ -100,7 +100,11 @@ enum {
    * the k-values per stage).  Both issue the same MMAs in the same order and give bit-identical
    * results.  Default 2: 4 measured slower on GB300 (Stokeslet N = 262144: M->L 7.1 ms against
    * 5.3 ms at p = 10, 33 ms against 25 ms at p = 8). */
-  KAFMM_OPT_TC_STAGES = 8
+  KAFMM_OPT_TC_STAGES = 8,
+  /* Most slot ranges a tile of the tensor-core gather-GEMM is split into when the grid would
+   * not fill the GPU (M->L offsets, M->M child octants; partial sums combined in a fixed
+   * order): 1, 2, 4 (default) or 8. */
+  KAFMM_OPT_TC_RANGES = 9
 };
 enum { KAFMM_TC_TF32X3 = 0, KAFMM_TC_BF16X3 = 1, KAFMM_TC_AUTO = 2 };
 enum { KAFMM_PREC_FP64 = 0, KAFMM_PREC_FP32 = 1, KAFMM_PREC_MIXED = 2 };
@@ -163,6 +167,14 @@ int kafmm_set_points_batched(kafmm_plan_t plan, int n_prob, const int64_t* src_o
  * Upward pass S->M, M->M; downward pass M->L (V), S->L (X), L->L; leaves L->T, M->T (W),
  * S->T (U) -- Sec. II, Fig. kifmmgraph. */
 int kafmm_eval(kafmm_plan_t plan, const void* s, void* g, int dtype);
+
+/* Autotuner of the tensor-core kernels: for the current points and the source values s
+ * (device arrays; g receives the values of the last trial), times kafmm_eval for every
+ * combination of KAFMM_OPT_TC_STAGES (2, 4) and KAFMM_OPT_TC_RANGES (1, 2, 4, 8), best of two
+ * runs each, and keeps the fastest in the plan.  chosen (host, may be NULL) receives
+ * {stages, ranges}.  Without tensor cores (FP64 / FP32 forms) it changes nothing.  The work
+ * lists are built for the current points, so call it again when the tree changes much. */
+int kafmm_autotune(kafmm_plan_t plan, const void* s, void* g, int dtype, int64_t* chosen);
 
 /* Synchronises the plan's stream and reports (then clears) the device status accumulated by
  * asynchronous kafmm_eval calls (KAFMM_OPT_SYNC = 0): KAFMM_ERR_TIMEOUT if a bounded device

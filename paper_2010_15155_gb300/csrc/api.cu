@@ -1,4 +1,5 @@
 // C ABI of the evaluator (declared in include/kafmm.h).
+#include <algorithm>
 #include <cstdarg>
 #include <cstring>
 
@@ -162,6 +163,11 @@ extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
       if (value != 2 && value != 4) return fail(P, KAFMM_ERR_ARG, "tensor-core stages must be 2 or 4");
       P.tc_stages = (int)value;
       return 0;
+    case KAFMM_OPT_TC_RANGES:
+      if (value != 1 && value != 2 && value != 4 && value != 8)
+        return fail(P, KAFMM_ERR_ARG, "tensor-core slot ranges must be 1, 2, 4 or 8");
+      P.tc_ranges = (int)value;
+      return 0;
     case KAFMM_OPT_TC_SPLIT:
       if (value != KAFMM_TC_TF32X3 && value != KAFMM_TC_BF16X3 && value != KAFMM_TC_AUTO)
         return fail(P, KAFMM_ERR_ARG, "bad tensor-core split %lld", (long long)value);
@@ -293,6 +299,53 @@ extern "C" int kafmm_eval(kafmm_plan_t pl, const void* s, void* g, int dtype) {
   CKP(cudaMemcpyAsync(&st, P.tree.status.p, 4, cudaMemcpyDeviceToHost, P.stream));
   CKP(cudaStreamSynchronize(P.stream));
   if (st & ST_TIMEOUT) return fail(P, KAFMM_ERR_TIMEOUT, "a bounded device wait expired");
+  return 0;
+}
+
+extern "C" int kafmm_autotune(kafmm_plan_t pl, const void* s, void* g, int dtype, int64_t* chosen) {
+  PLAN_CHECK(pl);
+  if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "kafmm_autotune before kafmm_set_points");
+  if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || (P.tree.n_src > 0 && !s) || (P.tree.n_trg > 0 && !g))
+    return fail(P, KAFMM_ERR_ARG, "kafmm_autotune: bad arguments");
+  if ((P.tree.n_src > 0 && is_host_ptr(s)) || (P.tree.n_trg > 0 && is_host_ptr(g)))
+    return fail(P, KAFMM_ERR_ARG, "kafmm_autotune takes device pointers only");
+  int best_st = P.tc_stages, best_rg = P.tc_ranges;
+  if (P.use_tc) {
+    const int stages[2] = {2, 4}, ranges[4] = {1, 2, 4, 8};
+    const int keep_sync = P.sync;
+    P.sync = 1;
+    int rc = kafmm_eval(pl, s, g, dtype);   // every buffer exists before the timing
+    if (rc) return rc;
+    float best = 3.4e38f;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 4; ++b) {
+        P.tc_stages = stages[a];
+        P.tc_ranges = ranges[b];
+        float t = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {   // best of two evaluations
+          rc = kafmm_eval(pl, s, g, dtype);
+          if (rc) {
+            P.sync = keep_sync;
+            return rc;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, P.ev[3], P.ev[7]);
+          t = rep == 0 ? ms : std::min(t, ms);
+        }
+        if (t < best) {
+          best = t;
+          best_st = stages[a];
+          best_rg = ranges[b];
+        }
+      }
+    P.sync = keep_sync;
+  }
+  P.tc_stages = best_st;
+  P.tc_ranges = best_rg;
+  if (chosen) {
+    chosen[0] = best_st;
+    chosen[1] = best_rg;
+  }
   return 0;
 }
 

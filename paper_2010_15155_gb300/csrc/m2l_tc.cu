@@ -749,7 +749,7 @@ int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* 
   // over several waves; the ranges' partial sums are combined in fixed order
   const bool splittable = m2l || mode == tc::TC_M2M;
   int nsplit = 1;
-  while (splittable && nsplit < 4 && (int64_t)ntiles * rows * nsplit < 152 * 6) nsplit *= 2;
+  while (splittable && nsplit < P.tc_ranges && (int64_t)ntiles * rows * nsplit < 152 * 6) nsplit *= 2;
   int64_t part_stride = (int64_t)P.tree.nbox * P.R * 4;
   if (nsplit > 1) {
     cudaError_t e = P.m2l_parts.reserve(sizeof(float) * part_stride * nsplit + 256);

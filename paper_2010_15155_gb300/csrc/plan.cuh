@@ -91,6 +91,7 @@ struct Plan {
   alignas(64) unsigned char tmaps[2][2][128];
   bool tmap_ready = false;
   int tc_stages = 2;                // pipeline depth of the tensor-core kernel (2 or 4)
+  int tc_ranges = 4;                // most slot ranges (CTAs) per tile of a small grid (1..8)
   DevBuf unit64, unit32;            // unit surface [n][3]
   DevBuf tm2l64, tm2l32;            // periodic far-image operator [R][R]
   // tree + data

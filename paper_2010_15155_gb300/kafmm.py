@@ -22,7 +22,7 @@ LAPLACE, STOKESLET, RPY, STOKES_DL = 0, 1, 2, 3
 BC_OPEN, BC_PXYZ = 0, 3
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN, OPT_TC_SPLIT = 1, 2, 3, 4, 5, 6
-OPT_SYNC, OPT_TC_STAGES = 7, 8
+OPT_SYNC, OPT_TC_STAGES, OPT_TC_RANGES = 7, 8, 9
 TC_TF32X3, TC_BF16X3, TC_AUTO = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 ML_G, ML_L4 = 0, 1
@@ -56,6 +56,7 @@ def lib():
             "kafmm_set_points_batched": ([vp, i32, vp, vp, vp, vp, i32], i32),
             "kafmm_eval": ([vp, vp, vp, i32], i32),
             "kafmm_status": ([vp], i32),
+            "kafmm_autotune": ([vp, vp, vp, i32, ctypes.POINTER(i64)], i32),
             "kafmm_rpy_velocity": ([vp, vp, vp, vp, vp, i32], i32),
             "kafmm_rpy_velocity_noalloc": ([vp, vp, vp, vp, vp, i32], i32),
             "kafmm_tree_info": ([vp, ctypes.POINTER(i64), i32], i32),
@@ -140,6 +141,12 @@ def kafmm_set_points_batched(plan, n_prob, src_offsets, trg_offsets, y, x, dtype
 
 def kafmm_eval(plan, s, g, dtype):
     _check(plan, lib().kafmm_eval(plan, _ptr(s), _ptr(g), dtype))
+
+
+def kafmm_autotune(plan, s, g, dtype):
+    chosen = (ctypes.c_int64 * 2)()
+    _check(plan, lib().kafmm_autotune(plan, _ptr(s), _ptr(g), dtype, chosen))
+    return {"tc_stages": int(chosen[0]), "tc_ranges": int(chosen[1])}
 
 
 def kafmm_status(plan):

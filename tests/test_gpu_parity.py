@@ -312,3 +312,30 @@ def test_tensor_core_pipeline_depths_agree_bit_for_bit(p):
         assert K.kafmm_get_counters(plan.h)["tensor_core_m2l"] == 1
         plan.close()
     assert torch.equal(out[2], out[4])
+
+
+def test_autotune_picks_a_valid_configuration():
+    """kafmm_autotune times the tensor-core pipeline depth and slot-range counts on the current
+    points and keeps the fastest; evaluation afterwards equals an evaluation with those options
+    set by hand and stays within the mixed-form tolerance of the FP64 form."""
+    pts, f = W.stokes_uniform(60000, seed=10, dtype=np.float32)
+    y = torch.from_numpy(pts).cuda()
+    s = torch.from_numpy(f).cuda()
+    g = torch.empty((len(pts), 3), dtype=torch.float32, device="cuda")
+    plan = K.Plan(K.STOKESLET, p=8, q=64, precision=K.PREC_MIXED, variant=K.ML_L4)
+    plan.set_points(y)
+    chosen = K.kafmm_autotune(plan.h, s, g, K.F32)
+    assert chosen["tc_stages"] in (2, 4) and chosen["tc_ranges"] in (1, 2, 4, 8)
+    tuned = plan.eval(s)
+    plan.close()
+    ref = K.Plan(K.STOKESLET, p=8, q=64, precision=K.PREC_MIXED, variant=K.ML_L4,
+                 tc_stages=chosen["tc_stages"])
+    K.kafmm_set_option(ref.h, K.OPT_TC_RANGES, chosen["tc_ranges"])
+    ref.set_points(y)
+    assert torch.equal(ref.eval(s), tuned)
+    ref.close()
+    p64 = K.Plan(K.STOKESLET, p=8, q=64, precision=K.PREC_FP64, variant=K.ML_L4)
+    p64.set_points(y.double())
+    g64 = p64.eval(s.double())
+    p64.close()
+    assert float(torch.linalg.norm(tuned.double() - g64) / torch.linalg.norm(g64)) < 1e-5

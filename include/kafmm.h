@@ -104,7 +104,18 @@ enum {
   /* Most slot ranges a tile of the tensor-core gather-GEMM is split into when the grid would
    * not fill the GPU (M->L offsets, M->M child octants; partial sums combined in a fixed
    * order): 1, 2, 4 (default) or 8. */
-  KAFMM_OPT_TC_RANGES = 9
+  KAFMM_OPT_TC_RANGES = 9,
+  /* RPY with one shared point set: 1 = kafmm_eval leaves the U-list pairs within contact
+   * (r <= b_i + b_j, the radii of the two points) out of the kernel sum and
+   * kafmm_rpy_velocity adds their whole pair mobility; 0 (default) = the kernel sum holds every
+   * pair and kafmm_rpy_velocity corrects contact pairs by (overlap form - far form), as
+   * Sec. II.B describes.  Use 1 for sphere velocities of dense suspensions in the FP32 and
+   * mixed forms: the far form of very close pairs (a^2 / r^3) is orders of magnitude larger
+   * than the velocity and cancels in the correction beyond FP32 precision (2^20 clustered
+   * spheres, mixed form, sampled velocities vs brute force: 2.5e-4 with 0, 1.3e-5 with 1; FP64
+   * form 1.7e-6).  With 1, kafmm_eval's [u, lap u] is the kernel sum without those pairs; set it
+   * before kafmm_eval and keep it for the matching kafmm_rpy_velocity. */
+  KAFMM_OPT_RPY_CONTACT = 10
 };
 enum { KAFMM_TC_TF32X3 = 0, KAFMM_TC_BF16X3 = 1, KAFMM_TC_AUTO = 2 };
 enum { KAFMM_PREC_FP64 = 0, KAFMM_PREC_FP32 = 1, KAFMM_PREC_MIXED = 2 };

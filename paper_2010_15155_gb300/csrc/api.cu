@@ -163,6 +163,10 @@ extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
       if (value != 2 && value != 4) return fail(P, KAFMM_ERR_ARG, "tensor-core stages must be 2 or 4");
       P.tc_stages = (int)value;
       return 0;
+    case KAFMM_OPT_RPY_CONTACT:
+      if (value < 0 || value > 1) return fail(P, KAFMM_ERR_ARG, "bad RPY contact mode %lld", (long long)value);
+      P.rpy_contact = (int)value;
+      return 0;
     case KAFMM_OPT_TC_RANGES:
       if (value != 1 && value != 2 && value != 4 && value != 8)
         return fail(P, KAFMM_ERR_ARG, "tensor-core slot ranges must be 1, 2, 4 or 8");

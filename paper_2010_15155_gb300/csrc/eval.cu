@@ -475,6 +475,7 @@ struct LeafArgs {
   T* g;                              // sorted targets [nt][KT]
   unsigned* status;
   int n, R, near_only, kahan;
+  int contact;                       // RPY: skip U-list pairs within contact (r <= b_i + b_j)
   int cap;                           // staging capacity in sources
 };
 
@@ -558,6 +559,8 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
       yl = x.y - cy;
       zl = x.z - cz;
     }
+    T bi = 0;   // the target's own radius (RPY with one shared point set)
+    if (act && (PR == P_RPY_L4 || PR == P_RPY_G) && a.contact) bi = a.sval[(int64_t)it * NV].w;
     T acc[KT], far[KT], comp[KT];
 #pragma unroll
     for (int k = 0; k < KT; ++k) acc[k] = far[k] = comp[k] = 0;
@@ -708,6 +711,11 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
             } else if (PR == P_STK_L4 || PR == P_STK_G) {
               stk_st<T>(r0, r1, r2, v.x, v.y, v.z, tmp);
             } else if (PR == P_RPY_L4 || PR == P_RPY_G) {
+              // contact pairs are left to the sphere-velocity pass, which adds their whole
+              // mobility (their far form is large and cancels there, beyond FP32 precision)
+              if (a.contact && in_contact<T>(xg, yg, zg, y.x, y.y, y.z, (T)(sx * a.geo.L), (T)(sy * a.geo.L),
+                                              (T)(sz * a.geo.L), bi, v.w))
+                continue;
               rpy_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
             } else {
               T4 v1 = sv[(base + j) * NV + 1], v2 = sv[(base + j) * NV + 2];
@@ -1078,6 +1086,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
     la.R = R;
     la.near_only = P.near_only;
     la.kahan = P.kahan;
+    la.contact = P.contact_split() ? 1 : 0;
     int cap = (int)(40960 / ((1 + NV) * sizeof(T4)));
     if (cap < P.n) cap = P.n;
     la.cap = cap;

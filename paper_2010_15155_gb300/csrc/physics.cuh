@@ -45,6 +45,21 @@ __device__ inline T inv_r(T rr) { return rr > T(0) ? rsqrt_<T>(rr) : T(0); }
 // Source values: v0 = (q | f1 f2 f3 [b]) ; DL: v0 = D00 D01 D02 D10, v1 = D11 D12 D20 D21,
 // v2 = D22.  acc has KT entries.
 
+// r^2 without contracted multiply-adds: the RPY contact test gives the same answer in the leaf
+// kernel and in the sphere-velocity pass.
+__device__ __forceinline__ float rr_exact(float r0, float r1, float r2) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(r0, r0), __fmul_rn(r1, r1)), __fmul_rn(r2, r2));
+}
+__device__ __forceinline__ double rr_exact(double r0, double r1, double r2) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(r0, r0), __dmul_rn(r1, r1)), __dmul_rn(r2, r2));
+}
+// Pair within contact: r^2 <= (bi + bj)^2, from global coordinates x - (y + shift).
+template <class T>
+__device__ __forceinline__ bool in_contact(T x0, T x1, T x2, T y0, T y1, T y2, T s0, T s1, T s2, T bi, T bj) {
+  T cs = bi + bj;
+  return rr_exact(x0 - (y0 + s0), x1 - (y1 + s1), x2 - (y2 + s2)) <= cs * cs;
+}
+
 // 1/sqrt(x) for normal x > 0 in one approximate instruction (inputs here are squared distances
 // between distinct points in the unit cube, far above the subnormal range; zero is tested
 // before the call).

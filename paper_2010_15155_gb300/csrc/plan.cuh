@@ -40,6 +40,7 @@ struct Tree {
   DevBuf src_pos, trg_pos;          // compute-type xyz (float4 or double4, w unused)
   // boxes
   DevBuf d_lvl_start, key, level, parent, child, sb, se, tb, te, leaf, leaves, prob;
+  DevBuf leaf_of;                   // [n_src] leaf box of each sorted source point
   // lists, CSR over boxes (entries packed with pack_entry)
   DevBuf u_off, u_ent, w_off, w_ent, x_off, x_ent;
   DevBuf vtab;                      // [nbox][216] source box of each V slot or LIST_EMPTY
@@ -71,6 +72,7 @@ struct Plan {
   int kernel = 0, bc = 0, p = 0, q = 0;
   int prec = KAFMM_PREC_MIXED, variant = KAFMM_ML_L4, near_only = 0, kahan = 0;
   int sync = 1;        // kafmm_eval synchronises and checks the device status (KAFMM_OPT_SYNC)
+  int rpy_contact = 0; // KAFMM_OPT_RPY_CONTACT: 0 off, 1 on
   cudaStream_t stream = 0;
   double origin[3] = {0, 0, 0}, L = 1.0;
   int ks = 1, kt = 1;
@@ -112,6 +114,10 @@ struct Plan {
   std::string err;
 
   bool fp64() const { return prec == KAFMM_PREC_FP64; }
+  // RPY near field leaves contact pairs to kafmm_rpy_velocity (one shared point set only)
+  bool contact_split() const {
+    return kernel == KAFMM_RPY && tree.same && rpy_contact == 1;
+  }
 };
 
 // Sets plan.err and returns code.

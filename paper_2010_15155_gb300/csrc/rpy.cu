@@ -7,7 +7,8 @@
 //        A = (16 r^3 (a+b) - ((a-b)^2 + 3 r^2)^2) / (32 r^3),  B = 3 ((a-b)^2 - r^2)^2 / (32 r^3)
 //   r <= |a-b|       :  M = I / (6 pi max(a, b))
 // i.e. the pass adds (M_overlap - M_far) f for those pairs (M_far = 0 at r = 0, as the sum
-// skips coincident pairs).  Neighbours come from a dense cell table at a grid level whose cell
+// skips coincident pairs).  With the contact split (FP32 forms, one shared point set) the near
+// field leaves out its pairs within r <= b_i + b_j and this pass adds their whole mobility.  Neighbours come from a dense cell table at a grid level whose cell
 // side is at least a_max + b_max, so every contact partner lies in the 27 surrounding cells.
 #include <algorithm>
 #include <cstring>
@@ -66,6 +67,48 @@ __global__ void k_cell_table(const uint64_t* __restrict__ key, int64_t n, int sh
   }
 }
 
+// Whole pair mobility M(r; ai, aj) f (overlap form within contact, far form outside), added to
+// acc: for contact pairs the near field left out (one shared point set, FP32 forms).
+template <class T>
+__device__ inline void pair_full(T r0, T r1, T r2, T ai, T aj, T f0, T f1, T f2, T* acc) {
+  T rr = r0 * r0 + r1 * r1 + r2 * r2;
+  T rn = sqrt(rr);
+  T s = ai + aj, d = fabs(ai - aj);
+  const T pi = T(PI);
+  T rf = r0 * f0 + r1 * f1 + r2 * f2;
+  T A, Bt;   // M f = A f + Bt r
+  if (rn > s) {   // far form G + (ai^2 + aj^2)/6 lap G
+    T c = ai * ai + aj * aj;
+    A = (T(1) + c / (T(3) * rr)) / (T(8) * pi * rn);
+    Bt = (T(1) - c / rr) / (T(8) * pi * rn) * rf / rr;
+  } else if (rn > d) {
+    T r3 = rr * rn, t = d * d + T(3) * rr, e = d * d - rr;
+    A = (T(16) * r3 * s - t * t) / (T(32) * r3) / (T(6) * pi * ai * aj);
+    Bt = T(3) * e * e / (T(32) * r3) / (T(6) * pi * ai * aj) * rf / rr;
+  } else {
+    A = T(1) / (T(6) * pi * (ai > aj ? ai : aj));
+    Bt = T(0);
+  }
+  acc[0] += A * f0 + Bt * r0;
+  acc[1] += A * f1 + Bt * r1;
+  acc[2] += A * f2 + Bt * r2;
+}
+
+// Closed leaf boxes A and B (B moved by the image shift s, in domains) intersect: the pair is
+// in A's U list.
+__device__ inline bool leaves_adjacent(const int8_t* level, const uint64_t* key, int A, int B, int sx, int sy,
+                                       int sz) {
+  int la = level[A], lb = level[B];
+  int64_t wa = 1ll << (MAX_LEVEL - la), wb = 1ll << (MAX_LEVEL - lb), D = 1ll << MAX_LEVEL;
+  uint64_t ka = key[A], kb = key[B];
+  int64_t a0[3] = {(int64_t)compact3(ka) * wa, (int64_t)compact3(ka >> 1) * wa, (int64_t)compact3(ka >> 2) * wa};
+  int64_t b0[3] = {(int64_t)compact3(kb) * wb + sx * D, (int64_t)compact3(kb >> 1) * wb + sy * D,
+                   (int64_t)compact3(kb >> 2) * wb + sz * D};
+  for (int d = 0; d < 3; ++d)
+    if (a0[d] > b0[d] + wb || b0[d] > a0[d] + wa) return false;
+  return true;
+}
+
 // Pair mobility difference (overlap form minus far form) applied to f, accumulated in acc.
 template <class T>
 __device__ inline void overlap_delta(T r0, T r1, T r2, T ai, T aj, T f0, T f1, T f2, T* acc) {
@@ -99,6 +142,16 @@ __device__ inline void overlap_delta(T r0, T r1, T r2, T ai, T aj, T f0, T f1, T
   acc[2] += u2;
 }
 
+// Contact split (one shared point set): the near field left out the U-list pairs with
+// r <= b_i + b_j, so those get their whole mobility here; contact pairs in the far-field lists
+// keep the overlap-minus-far correction.
+struct ContactInfo {
+  int on;
+  const int* leaf_of;      // [n_src] leaf box of each sorted point
+  const int8_t* level;     // box levels
+  const uint64_t* key;     // box Morton keys
+};
+
 template <class T, class Tio>
 __global__ void k_rpy_velocity(const typename V4<T>::type* __restrict__ spos,
                                const typename V4<T>::type* __restrict__ sfb,
@@ -106,11 +159,12 @@ __global__ void k_rpy_velocity(const typename V4<T>::type* __restrict__ spos,
                                const uint64_t* __restrict__ tkey, const uint32_t* __restrict__ tperm,
                                int64_t nt, const int* __restrict__ cbeg, const int* __restrict__ cend, int g,
                                int periodic, double L, int same, const Tio* __restrict__ gin,
-                               Tio* __restrict__ ua) {
+                               Tio* __restrict__ ua, ContactInfo ci) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
        i += (int64_t)gridDim.x * blockDim.x) {
     typename V4<T>::type x = tpos[i];
     T ai = ta[i];
+    T bi = ci.on ? sfb[i].w : T(0);   // the target's own source radius (shared point set)
     uint64_t ck = tkey[i] >> (3 * (MAX_LEVEL - g));
     int cx = (int)compact3(ck), cy = (int)compact3(ck >> 1), cz = (int)compact3(ck >> 2);
     int n = 1 << g;
@@ -133,8 +187,15 @@ __global__ void k_rpy_velocity(const typename V4<T>::type* __restrict__ spos,
       for (int j = b0; j < b1; ++j) {
         if (same && j == (int)i && sx == 0 && sy == 0 && sz == 0) continue;
         typename V4<T>::type y = spos[j], fb = sfb[j];
-        overlap_delta<T>(x.x - (y.x + ox), x.y - (y.y + oy), x.z - (y.z + oz), ai, fb.w, fb.x, fb.y,
-                         fb.z, acc);
+        T r0 = x.x - (y.x + ox), r1 = x.y - (y.y + oy), r2 = x.z - (y.z + oz);
+        if (ci.on) {   // the near field's contact test (its own radii, the same arithmetic)
+          if (in_contact<T>(x.x, x.y, x.z, y.x, y.y, y.z, ox, oy, oz, bi, fb.w) &&
+              leaves_adjacent(ci.level, ci.key, ci.leaf_of[i], ci.leaf_of[j], sx, sy, sz)) {
+            pair_full<T>(r0, r1, r2, ai, fb.w, fb.x, fb.y, fb.z, acc);
+            continue;
+          }
+        }
+        overlap_delta<T>(r0, r1, r2, ai, fb.w, fb.x, fb.y, fb.z, acc);
       }
     }
     int64_t o = tperm[i];
@@ -142,6 +203,15 @@ __global__ void k_rpy_velocity(const typename V4<T>::type* __restrict__ spos,
     T c6 = ai * ai / T(6);
     for (int k = 0; k < 3; ++k) ua[3 * o + k] = (Tio)((T)gg[k] + c6 * (T)gg[3 + k] + acc[k]);
   }
+}
+
+ContactInfo contact_info(const Plan& P) {
+  ContactInfo ci;
+  ci.on = P.contact_split() ? 1 : 0;
+  ci.leaf_of = P.tree.leaf_of.as<int>();
+  ci.level = P.tree.level.as<int8_t>();
+  ci.key = P.tree.key.as<uint64_t>();
+  return ci;
 }
 
 int grid_for(int64_t n, int threads, int maxb = 152 * 16) {
@@ -187,7 +257,7 @@ int run(Plan& P, const void* s, const void* a, const void* g, void* ua, int dtyp
   float amax, bmax;
   memcpy(&amax, &h[0], 4);
   memcpy(&bmax, &h[1], 4);
-  double reach = ((double)amax + (double)bmax) * (1.0 + 1e-6) / P.L;
+  double reach = (std::max((double)amax, (double)bmax) + (double)bmax) * (1.0 + 1e-6) / P.L;
   int lev = 0;
   while (lev < 8 && reach > 0 && 1.0 / (double)(1 << (lev + 1)) >= reach) ++lev;
   if (reach <= 0) lev = 8;
@@ -204,11 +274,11 @@ int run(Plan& P, const void* s, const void* a, const void* g, void* ua, int dtyp
     if (dtype == KAFMM_F64)
       KL k_rpy_velocity<T, double><<<grid_for(nt, 128), 128, 0, st>>>(
           spos, fb.as<T4>(), tpos, ta.as<T>(), tkey, tperm, nt, cb.as<int>(), ce.as<int>(), lev,
-          P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const double*)g, (double*)ua);
+          P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const double*)g, (double*)ua, contact_info(P));
     else
       KL k_rpy_velocity<T, float><<<grid_for(nt, 128), 128, 0, st>>>(
           spos, fb.as<T4>(), tpos, ta.as<T>(), tkey, tperm, nt, cb.as<int>(), ce.as<int>(), lev,
-          P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const float*)g, (float*)ua);
+          P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const float*)g, (float*)ua, contact_info(P));
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
@@ -293,7 +363,7 @@ int run_noalloc(Plan& P, const void* s, const void* a, const void* g, void* ua, 
   float amax, bmax;
   memcpy(&amax, &h[0], 4);
   memcpy(&bmax, &h[1], 4);
-  double reach = ((double)amax + (double)bmax) * (1.0 + 1e-6) / P.L;
+  double reach = (std::max((double)amax, (double)bmax) + (double)bmax) * (1.0 + 1e-6) / P.L;
   int lev = 0;
   while (lev < NOALLOC_MAX_CELL_LEVEL && reach > 0 && 1.0 / (double)(1 << (lev + 1)) >= reach) ++lev;
   if (reach <= 0) lev = NOALLOC_MAX_CELL_LEVEL;
@@ -308,11 +378,11 @@ int run_noalloc(Plan& P, const void* s, const void* a, const void* g, void* ua, 
     if (dtype == KAFMM_F64)
       KL k_rpy_velocity<T, double><<<grid_for(nt, 128), 128, 0, st>>>(
           spos, fb, tpos, ta, tkey, tperm, nt, cb, ce, lev, P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0,
-          (const double*)g, (double*)ua);
+          (const double*)g, (double*)ua, contact_info(P));
     else
       KL k_rpy_velocity<T, float><<<grid_for(nt, 128), 128, 0, st>>>(
           spos, fb, tpos, ta, tkey, tperm, nt, cb, ce, lev, P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0,
-          (const float*)g, (float*)ua);
+          (const float*)g, (float*)ua, contact_info(P));
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));

@@ -95,11 +95,45 @@ __global__ void k_scan_apply(const T* in, int64_t n, const int* d_len, const T* 
   }
 }
 
+// One block scans up to SCAN_SMALL elements (16 consecutive per thread): the whole scan in one
+// launch.  len = *d_len if d_len else n.
+constexpr int SCAN_SMALL_ITEMS = 16;
+constexpr int64_t SCAN_SMALL = (int64_t)SCAN_THREADS * SCAN_SMALL_ITEMS;
+template <class T>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_small(const T* in, int64_t n, const int* d_len,
+                                                             T* out, T* d_total) {
+  __shared__ T sm[32];
+  int64_t len = d_len ? (int64_t)*d_len : n;
+  if (len > n) len = n;
+  T v[SCAN_SMALL_ITEMS];
+  T s = 0;
+  const int64_t base = (int64_t)threadIdx.x * SCAN_SMALL_ITEMS;
+#pragma unroll
+  for (int k = 0; k < SCAN_SMALL_ITEMS; ++k) {
+    int64_t i = base + k;
+    v[k] = i < len ? in[i] : T(0);
+    s += v[k];
+  }
+  T total;
+  T e = block_excl_scan<T>(s, sm, total);
+#pragma unroll
+  for (int k = 0; k < SCAN_SMALL_ITEMS; ++k) {
+    int64_t i = base + k;
+    if (i < len) out[i] = e;
+    e += v[k];
+  }
+  if (threadIdx.x == 0 && d_total) *d_total = total;
+}
+
 // Exclusive scan of in[0..len) into out (in-place allowed); *d_total receives the sum.
 // cap bounds len; scratch needs (cap / SCAN_TILE + 1) elements.
 template <class T>
 inline void scan_excl(const T* in, T* out, int64_t cap, const int* d_len, T* scratch, T* d_total,
                       cudaStream_t st) {
+  if (cap <= SCAN_SMALL) {
+    KL k_scan_small<T><<<1, SCAN_THREADS, 0, st>>>(in, cap, d_len, out, d_total);
+    return;
+  }
   int ntiles = (int)((cap + SCAN_TILE - 1) / SCAN_TILE);
   if (ntiles < 1) ntiles = 1;
   KL k_scan_tiles<T><<<ntiles, SCAN_THREADS, 0, st>>>(in, cap, d_len, scratch);

@@ -532,6 +532,13 @@ __global__ void k_leaf_list(const int8_t* leaf, const int* leaf_pos, int nbox, i
 
 // V entry count and largest leaf; per box a 64-bit signature of its V slot occupancy (boxes
 // with equal signatures are grouped into the same tensor-core tiles).
+// Leaf box of every sorted source point.
+__global__ void k_leaf_of(TreeView t, int* __restrict__ leaf_of) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x)
+    if (t.leaf[b])
+      for (int i = t.sb[b]; i < t.se[b]; ++i) leaf_of[i] = b;
+}
+
 __global__ void k_tree_stats(TreeView t, const int32_t* vtab, unsigned long long* out,
                              unsigned long long* vsig) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x) {
@@ -787,6 +794,8 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   KL k_i8_to_i32<<<grid_for(nb, 256), 256, 0, st>>>(T.leaf.as<int8_t>(), nb, lpos);
   scan_excl<int>(lpos, lpos, nb, nullptr, lscratch, ltot, st);
   KL k_leaf_list<<<grid_for(nb, 256), 256, 0, st>>>(T.leaf.as<int8_t>(), lpos, nb, T.leaves.as<int>());
+  CK(T.leaf_of.reserve(sizeof(int) * (ns + 1)));
+  KL k_leaf_of<<<grid_for(nb, 128), 128, 0, st>>>(T.view(), T.leaf_of.as<int>());
   CK(cudaMemcpyAsync(&T.nleaf, ltot, sizeof(int), cudaMemcpyDeviceToHost, st));
   cudaEventRecord(P.ev[1], st);
 

@@ -22,7 +22,7 @@ LAPLACE, STOKESLET, RPY, STOKES_DL = 0, 1, 2, 3
 BC_OPEN, BC_PXYZ = 0, 3
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN, OPT_TC_SPLIT = 1, 2, 3, 4, 5, 6
-OPT_SYNC, OPT_TC_STAGES, OPT_TC_RANGES = 7, 8, 9
+OPT_SYNC, OPT_TC_STAGES, OPT_TC_RANGES, OPT_RPY_CONTACT = 7, 8, 9, 10
 TC_TF32X3, TC_BF16X3, TC_AUTO = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 ML_G, ML_L4 = 0, 1

@@ -15,6 +15,9 @@ e2e    = the same through the C ABI with pinned HOST buffers (copies inside the 
          (about 8 million points), p = 8, q = 64, mixed precision, set and evaluated as one
          batch (kafmm_set_points_batched + kafmm_eval) and, for comparison, as 512 sequential
          single-problem calls.
+--workload periodic: triply periodic Stokeslet, 2^22 uniform points, p = 12, q = 128, G table.
+--workload rpy: RPY sphere velocities, 2^20 clustered points, p = 8, q = 128 (set_points +
+         eval + rpy_velocity per step).
 """
 from __future__ import annotations
 
@@ -42,7 +45,7 @@ FLOP_ST_PAIR = 29
 # DRAM bytes (read + written) of one M->L launch of this workload in the mixed form, from the ncu
 # capture summarised in profiles/m2l_tc_stokeslet_uniform_256k_p10.md (set to None when the
 # kernel changes until it is captured again)
-M2L_DRAM_BYTES = 5.693392e6 + 137.889280e6
+M2L_DRAM_BYTES = None
 
 
 def _env_rank():
@@ -198,6 +201,7 @@ def run_gpu(args):
     split = {"tf32x3": K.TC_TF32X3, "bf16x3": K.TC_BF16X3, "auto": K.TC_AUTO}[args.tc_split]
     plan = K.Plan(K.STOKESLET, p=P_ORDER, q=Q_LEAF, precision=prec, variant=K.ML_L4,
                   stream=stream.cuda_stream, tc_split=split)
+    K.kafmm_set_option(plan.h, K.OPT_TC_TILING, args.tc_tiling)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     # accuracy against the plain FP64 GPU form (outside the timed region)
@@ -216,7 +220,7 @@ def run_gpu(args):
 
     # tensor-core kernel configuration picked by the autotuner on these points (untimed setup)
     tuned = None
-    if args.precision == "mixed":
+    if args.precision == "mixed" and args.tc_tiling == 0:
         plan.set_points(y)
         tuned = K.kafmm_autotune(plan.h, s, g, K.F32)
 
@@ -310,6 +314,7 @@ def run_gpu(args):
                    "ml_table": "four-channel Laplace", "precision": args.precision,
                    "tc_split": split_used if args.precision == "mixed" else None,
                    "autotuned": tuned,
+                   "m2l_tiling": K.kafmm_get_counters(plan.h)["m2l_tiling"],
                    "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "rel_l2_vs_fp64": err,
@@ -364,6 +369,7 @@ def run_gpu_batched(args):
     g = torch.empty((ntot, 3), dtype=torch.float32, device=dev)
     plan = K.Plan(K.STOKESLET, p=p_ord, q=q_leaf, precision=K.PREC_MIXED, variant=K.ML_L4,
                   stream=stream.cuda_stream)
+    K.kafmm_set_option(plan.h, K.OPT_TC_TILING, args.tc_tiling)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     err = None
@@ -385,7 +391,7 @@ def run_gpu_batched(args):
         del gref
 
     plan.set_points_batched(y, off)
-    tuned = K.kafmm_autotune(plan.h, s, g, K.F32)
+    tuned = K.kafmm_autotune(plan.h, s, g, K.F32) if args.tc_tiling == 0 else None
 
     def step():
         plan.set_points_batched(y, off)
@@ -417,6 +423,7 @@ def run_gpu_batched(args):
     ph = {k: float(np.median([p[k] for p in phases])) for k in phases[0]}
     launches = plan_launches(plan)
     split_used = K.kafmm_get_counters(plan.h)["tc_split"]
+    tiling = K.kafmm_get_counters(plan.h)["m2l_tiling"]
     plan.close()
 
     # the same 512 problems as sequential single-problem calls (one plan, one stream)
@@ -456,7 +463,7 @@ def run_gpu_batched(args):
         "scaling": "weak", "vs_baseline": None, "dtype": f"f32+{split_used}", "data": "synthetic",
         "config": {"workload": f"stokeslet_batched_{n_prob}x_loguniform_1k_64k_p8_q64_l4",
                    "n_problems": n_prob, "n_points": ntot, "p": p_ord, "q": q_leaf,
-                   "autotuned": tuned,
+                   "autotuned": tuned, "m2l_tiling": tiling,
                    "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": f"one batch per GPU x{world}" if world > 1 else "1 GPU"},
         "max_problem_rel_l2_vs_fp64": err,
@@ -472,6 +479,189 @@ def run_gpu_batched(args):
         "clocks": clk,
         "gpu_launches": launches * args.steps if launches is not None else None,
     }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _timed_steps(step, plan, args, world, dev, stream, flush, local):
+    """W untimed warm-up steps, then K steps timed one by one with CUDA events (L2 flushed in
+    between), clocks sampled meanwhile; returns (mean ms max over ranks, median phases, clocks)."""
+    import torch
+    for i in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize(dev)
+    _barrier(world)
+    clocks = ClockSampler(local)
+    times, phases = [], []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        phases.append(plan.phase_times())
+    torch.cuda.synchronize(dev)
+    _barrier(world)
+    clk = clocks.stop()
+    ms = _max_over_ranks(float(np.mean(times)), world, dev)
+    ph = {k: float(np.median([p[k] for p in phases])) for k in phases[0]}
+    return ms, ph, clk
+
+
+def _m2l_roofline(K, plan, flops, m2l_ms):
+    peaks, src = _peaks()
+    split_used = K.kafmm_get_counters(plan.h)["tc_split"]
+    tiling = K.kafmm_get_counters(plan.h)["m2l_tiling"]
+    tf32 = split_used == "tf32x3"
+    peak = peaks["bf16_tflops"] * (1.1 / 2.25) if tf32 else peaks["bf16_tflops"]
+    achieved = flops / (m2l_ms * 1e-3) / 1e12
+    return split_used, {"bound": "tensor", "kernel": "m2l", "achieved": achieved, "peak": peak,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                        "peak_source": f"{split_used} dense burst, {src}; useful flops",
+                        "m2l_tiling": tiling}
+
+
+def run_gpu_periodic(args):
+    """Triply periodic Stokeslet: 2^22 uniform points, forces minus their mean, p = 12,
+    q = 128, G table (the periodic far field acts on the root's G multipole), mixed form."""
+    import torch
+
+    from paper_2010_15155_gb300 import kafmm as K
+
+    rank, world, local = _env_rank()
+    _dist_init(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n_pts, p_ord, q_leaf = 1 << 22, 12, 128
+    pts, f = workloads.stokes_uniform(n_pts, seed=_rank_seed(4, rank), zero_mean=True)
+    y = torch.from_numpy(pts).to(dev)
+    s = torch.from_numpy(f).to(dev)
+    g = torch.empty((n_pts, 3), dtype=torch.float32, device=dev)
+    plan = K.Plan(K.STOKESLET, p=p_ord, q=q_leaf, bc=K.BC_PXYZ, precision=K.PREC_MIXED,
+                  variant=K.ML_G, stream=stream.cuda_stream)
+    K.kafmm_set_option(plan.h, K.OPT_TC_TILING, args.tc_tiling)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    plan.set_points(y)
+    plan.eval(s, g)
+    acc = None
+    if rank == 0 and not args.skip_check:
+        # a rigid shift modulo the cell (Sec. III.B) and the FP32 CUDA-core form
+        sh = ((pts.astype(np.float64) + np.array([0.4173, 0.2281, 0.9011])) % 1.0).astype(np.float32)
+        sh = np.minimum(sh, np.float32(1) - np.float32(2 ** -24))
+        g0 = g.clone()
+        plan.set_points(torch.from_numpy(sh).to(dev))
+        g1 = plan.eval(s)
+        p32 = K.Plan(K.STOKESLET, p=p_ord, q=q_leaf, bc=K.BC_PXYZ, precision=K.PREC_FP32,
+                     variant=K.ML_G, stream=stream.cuda_stream)
+        p32.set_points(y)
+        g32 = p32.eval(s)
+        torch.cuda.synchronize(dev)
+        p32.close()
+
+        def rel(a, b):
+            return float(torch.linalg.norm(a.double() - b.double()) / torch.linalg.norm(b.double()))
+        acc = {"translation_rel_l2": rel(g1, g0), "rel_l2_vs_fp32_form": rel(g0, g32)}
+        del g0, g1, g32
+
+    def step():
+        plan.set_points(y)
+        plan.eval(s, g)
+
+    ms, ph, clk = _timed_steps(step, plan, args, world, dev, stream, flush, local)
+    info = plan.info()
+    n = 6 * (p_ord - 1) ** 2 + 2
+    split_used, roof = _m2l_roofline(K, plan, info["n_v"] * 2.0 * (3 * n) ** 2, ph["m2l"])
+    launches = plan_launches(plan)
+    line = {
+        "metric": METRIC, "value": world * n_pts / (ms * 1e-3) / 1e6, "unit": "Mpoints/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"f32+{split_used}", "data": "synthetic",
+        "config": {"workload": "stokeslet_periodic_4m_p12_q128_g", "n_points": n_pts, "p": p_ord,
+                   "q": q_leaf, "bc": "pxyz", "ml_table": "G",
+                   "l2": "inputs larger than L2; flushed (256 MiB write) between timed steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "accuracy": acc, "phases_ms": ph, "tree": info, "roofline": roof, "clocks": clk,
+        "gpu_launches": launches * args.steps if launches is not None else None,
+    }
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_gpu_rpy(args):
+    """RPY sphere velocities: 2^20 points in 64 Gaussian clusters, radii U(0.002, 0.006),
+    p = 8, q = 128, four-channel table, mixed form with the contact split; a step is
+    kafmm_set_points + kafmm_eval + kafmm_rpy_velocity (overlap pass and assembly)."""
+    import torch
+
+    from oracle import direct as D
+    from paper_2010_15155_gb300 import kafmm as K
+
+    rank, world, local = _env_rank()
+    _dist_init(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n_pts, p_ord, q_leaf = 1 << 20, 8, 128
+    pts, f, a = workloads.rpy_clusters(n_pts, seed=_rank_seed(2, rank))
+    fb = np.concatenate([f, a[:, None]], axis=1).astype(np.float32)
+    y = torch.from_numpy(pts).to(dev)
+    s = torch.from_numpy(fb).to(dev)
+    rad = torch.from_numpy(a).to(dev)
+    g = torch.empty((n_pts, 6), dtype=torch.float32, device=dev)
+    ua = torch.empty((n_pts, 3), dtype=torch.float32, device=dev)
+    plan = K.Plan(K.RPY, p=p_ord, q=q_leaf, precision=K.PREC_MIXED, variant=K.ML_L4,
+                  stream=stream.cuda_stream)
+    K.kafmm_set_option(plan.h, K.OPT_RPY_CONTACT, 1)
+    K.kafmm_set_option(plan.h, K.OPT_TC_TILING, args.tc_tiling)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        plan.set_points(y)
+        plan.eval(s, g)
+        K.kafmm_rpy_velocity(plan.h, s, rad, g, ua, K.F32)
+
+    step()
+    torch.cuda.synchronize(dev)
+    err = None
+    if rank == 0 and not args.skip_check:
+        # brute-force pair mobilities (FP64 oracle) at 1024 sampled spheres
+        idx = workloads.sample_targets(n_pts, 1024)
+        p64, fb64, a64 = pts.astype(np.float64), fb.astype(np.float64), a.astype(np.float64)
+        ref = D.rpy_velocity(p64[idx], a64[idx], p64, fb64, same_set=False)
+        ref -= fb64[idx, :3] / (6 * np.pi * a64[idx, None])
+        err = D.rel_l2(ua.double().cpu().numpy()[idx], ref)
+    ms, ph, clk = _timed_steps(step, plan, args, world, dev, stream, flush, local)
+    info = plan.info()
+    n = 6 * (p_ord - 1) ** 2 + 2
+    split_used, roof = _m2l_roofline(K, plan, info["n_v"] * 2.0 * n * n * 4, ph["m2l"])
+    launches = plan_launches(plan)
+    line = {
+        "metric": METRIC, "value": world * n_pts / (ms * 1e-3) / 1e6, "unit": "Mpoints/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"f32+{split_used}", "data": "synthetic",
+        "config": {"workload": "rpy_clusters_1m_64c_p8_q128_l4", "n_points": n_pts, "p": p_ord,
+                   "q": q_leaf, "ml_table": "four-channel Laplace", "contact_split": True,
+                   "l2": "flushed (256 MiB write) between timed steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "velocity_rel_l2_vs_brute_force_1024_sampled": err,
+        "phases_ms": ph, "tree": info, "roofline": roof, "clocks": clk,
+        "gpu_launches": launches * args.steps if launches is not None else None,
+        "gpu_launches_note": "set_points + eval launches; the velocity pass adds its own",
+    }
+    plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -529,7 +719,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
     ap.add_argument("--tc-split", default="auto", choices=["auto", "tf32x3", "bf16x3"])
-    ap.add_argument("--workload", default="stokeslet", choices=["stokeslet", "batched"])
+    ap.add_argument("--workload", default="stokeslet",
+                    choices=["stokeslet", "batched", "periodic", "rpy"])
+    ap.add_argument("--tc-tiling", type=int, default=0, choices=[0, 1, 2],
+                    help="M->L tiling: 0 automatic, 1 whole V lists, 2 per parent neighbour")
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -537,6 +730,10 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_gpu_batched(args)
+    if args.workload == "periodic":
+        return run_gpu_periodic(args)
+    if args.workload == "rpy":
+        return run_gpu_rpy(args)
     return run_gpu(args)
 
 

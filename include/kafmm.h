@@ -115,7 +115,19 @@ enum {
    * spheres, mixed form, sampled velocities vs brute force: 2.5e-4 with 0, 1.3e-5 with 1; FP64
    * form 1.7e-6).  With 1, kafmm_eval's [u, lap u] is the kernel sum without those pairs; set it
    * before kafmm_eval and keep it for the matching kafmm_rpy_velocity. */
-  KAFMM_OPT_RPY_CONTACT = 10
+  KAFMM_OPT_RPY_CONTACT = 10,
+  /* How the tensor-core M->L groups target boxes into tiles (applied at the next
+   * kafmm_set_points): 1 = tiles of one octant class carry whole V lists (every offset any of
+   * their boxes has); 2 = tiles of one octant class and one neighbour of the parent (the 8
+   * children of that colleague, Sec. II), each box's result a partial sum added to its
+   * downward check in neighbour order by a combine pass; 0 (default) = 2 when the partials
+   * (R x C floats per box and neighbour) fit in a quarter of the device memory, else 1.
+   * Adaptive V lists are sparse and differ from box to box (2^18 clustered points: 45 of 189
+   * offsets per box on average, 5735 distinct occupancies in 8810 boxes), so whole-list tiles
+   * compute mostly empty columns (M->L of 2^20 clustered RPY points: 44.7 ms with 1, 22.6 ms
+   * with 2; Stokeslet N = 262144 uniform, p = 10: 5.39 -> 4.42 ms).  kafmm_autotune times
+   * both. */
+  KAFMM_OPT_TC_TILING = 11
 };
 enum { KAFMM_TC_TF32X3 = 0, KAFMM_TC_BF16X3 = 1, KAFMM_TC_AUTO = 2 };
 enum { KAFMM_PREC_FP64 = 0, KAFMM_PREC_FP32 = 1, KAFMM_PREC_MIXED = 2 };
@@ -181,10 +193,11 @@ int kafmm_eval(kafmm_plan_t plan, const void* s, void* g, int dtype);
 
 /* Autotuner of the tensor-core kernels: for the current points and the source values s
  * (device arrays; g receives the values of the last trial), times kafmm_eval for every
- * combination of KAFMM_OPT_TC_STAGES (2, 4) and KAFMM_OPT_TC_RANGES (1, 2, 4, 8), best of two
- * runs each, and keeps the fastest in the plan.  chosen (host, may be NULL) receives
- * {stages, ranges}.  Without tensor cores (FP64 / FP32 forms) it changes nothing.  The work
- * lists are built for the current points, so call it again when the tree changes much. */
+ * combination of KAFMM_OPT_TC_TILING (2, 1; the work lists are rebuilt for each and the host
+ * time of that build is added to the score), KAFMM_OPT_TC_STAGES (2, 4) and
+ * KAFMM_OPT_TC_RANGES (1, 2, 4, 8), best of two runs each, and keeps the fastest in the plan.
+ * chosen (host, may be NULL) receives {stages, ranges, tiling}.  Without tensor cores (FP64 /
+ * FP32 forms) it changes nothing.  Call it again when the tree changes much. */
 int kafmm_autotune(kafmm_plan_t plan, const void* s, void* g, int dtype, int64_t* chosen);
 
 /* Synchronises the plan's stream and reports (then clears) the device status accumulated by
@@ -237,13 +250,16 @@ int kafmm_get_list(kafmm_plan_t plan, int kind, int64_t* offsets, int32_t* entri
 
 /* Times of the phases of the last set_points + eval, in milliseconds (CUDA events on the
  * plan's stream): 0 tree, 1 lists, 2 upward, 3 M->L, 4 downward rest, 5 near field,
- * 6 whole eval.  Host array t[n], up to 8 entries. */
+ * 6 whole eval; 7 host time of set_points' work-list build (tiles of the gather-GEMMs, read
+ * back from the tree; the device waits meanwhile).  Host array t[n], up to 8 entries. */
 int kafmm_phase_times(kafmm_plan_t plan, double* t, int n);
 
 /* Counters of the last calls (host array c[n], up to 8 entries): 0 kernel launches of the
  * last kafmm_set_points, 1 kernel launches of the last kafmm_eval, 2 whether M->L ran on the
  * tcgen05 tensor cores (0/1), 3 launches of set_points + eval, 4 the split format in use
- * (KAFMM_TC_TF32X3 or KAFMM_TC_BF16X3; -1 without tensor cores). */
+ * (KAFMM_TC_TF32X3 or KAFMM_TC_BF16X3; -1 without tensor cores), 5 the M->L tiling of the
+ * current points (1 whole V lists, 2 per parent neighbour; see KAFMM_OPT_TC_TILING), 6 the
+ * number of M->L tiles. */
 int kafmm_get_counters(kafmm_plan_t plan, int64_t* c, int n);
 
 /* Copies one precomputed translation operator to the host as FP64 (row-major R x R, R = the

@@ -1,5 +1,6 @@
 // C ABI of the evaluator (declared in include/kafmm.h).
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstring>
 
@@ -77,6 +78,12 @@ static int ensure_ops(Plan& P) {
   if (rc) return rc;
   extern bool tc_supported(Plan & P);
   P.use_tc = tc_supported(P);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    total_b = 0;
+  }
+  P.dev_mem = total_b;
   return 0;
 }
 
@@ -163,6 +170,10 @@ extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
       if (value != 2 && value != 4) return fail(P, KAFMM_ERR_ARG, "tensor-core stages must be 2 or 4");
       P.tc_stages = (int)value;
       return 0;
+    case KAFMM_OPT_TC_TILING:
+      if (value < 0 || value > 2) return fail(P, KAFMM_ERR_ARG, "bad M->L tiling %lld", (long long)value);
+      P.tc_tiling = (int)value;
+      return 0;
     case KAFMM_OPT_RPY_CONTACT:
       if (value < 0 || value > 1) return fail(P, KAFMM_ERR_ARG, "bad RPY contact mode %lld", (long long)value);
       P.rpy_contact = (int)value;
@@ -223,7 +234,9 @@ static int set_points_impl(Plan& P, const void* y, int64_t ns, const void* x, in
   if (rc) return rc;
   // tile sizes: the tensor-core kernels take P.tc_boxes target boxes per tile, k_gemm 64 / C
   int nb_tile = P.use_tc ? P.tc_boxes : 64 / P.C;
+  auto t0 = std::chrono::steady_clock::now();
   rc = build_worklists(P, nb_tile, nb_tile);
+  P.host_wl_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (rc) return rc;
   P.launches_points = g_launches;
   P.have_points = true;
@@ -313,42 +326,57 @@ extern "C" int kafmm_autotune(kafmm_plan_t pl, const void* s, void* g, int dtype
     return fail(P, KAFMM_ERR_ARG, "kafmm_autotune: bad arguments");
   if ((P.tree.n_src > 0 && is_host_ptr(s)) || (P.tree.n_trg > 0 && is_host_ptr(g)))
     return fail(P, KAFMM_ERR_ARG, "kafmm_autotune takes device pointers only");
-  int best_st = P.tc_stages, best_rg = P.tc_ranges;
+  int best_st = P.tc_stages, best_rg = P.tc_ranges, best_tl = P.wl.m2l_grouped ? 2 : 1;
   if (P.use_tc) {
-    const int stages[2] = {2, 4}, ranges[4] = {1, 2, 4, 8};
+    const int stages[2] = {2, 4}, ranges[4] = {1, 2, 4, 8}, tilings[2] = {2, 1};
     const int keep_sync = P.sync;
     P.sync = 1;
-    int rc = kafmm_eval(pl, s, g, dtype);   // every buffer exists before the timing
-    if (rc) return rc;
     float best = 3.4e38f;
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 4; ++b) {
-        P.tc_stages = stages[a];
-        P.tc_ranges = ranges[b];
-        float t = 0.f;
-        for (int rep = 0; rep < 2; ++rep) {   // best of two evaluations
-          rc = kafmm_eval(pl, s, g, dtype);
-          if (rc) {
-            P.sync = keep_sync;
-            return rc;
+    const int n_stages = P.C == 4 ? 2 : 1;   // single-column tables: two stages only
+    int built = -1;
+    int rc = 0;
+    for (int ti = 0; ti < 2 && !rc; ++ti) {
+      // the tiling is fixed by the work lists: rebuild them; the host time of the build is
+      // part of every set_points, so it counts towards the score
+      P.tc_tiling = tilings[ti];
+      auto t0 = std::chrono::steady_clock::now();
+      rc = build_worklists(P, P.tc_boxes, P.tc_boxes);
+      double host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (rc) break;
+      built = tilings[ti];
+      if (tilings[ti] == 2 && !P.wl.m2l_grouped) continue;   // partials do not fit
+      rc = kafmm_eval(pl, s, g, dtype);   // every buffer exists before the timing
+      for (int a = 0; a < n_stages && !rc; ++a)
+        for (int b = 0; b < 4 && !rc; ++b) {
+          P.tc_stages = stages[a];
+          P.tc_ranges = ranges[b];
+          float t = 0.f;
+          for (int rep = 0; rep < 2 && !rc; ++rep) {   // best of two evaluations
+            rc = kafmm_eval(pl, s, g, dtype);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, P.ev[3], P.ev[7]);
+            t = rep == 0 ? ms : std::min(t, ms);
           }
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, P.ev[3], P.ev[7]);
-          t = rep == 0 ? ms : std::min(t, ms);
+          t += (float)host_ms;
+          if (!rc && t < best) {
+            best = t;
+            best_st = stages[a];
+            best_rg = ranges[b];
+            best_tl = tilings[ti];
+          }
         }
-        if (t < best) {
-          best = t;
-          best_st = stages[a];
-          best_rg = ranges[b];
-        }
-      }
+    }
     P.sync = keep_sync;
+    P.tc_tiling = best_tl;
+    if (!rc && built != best_tl) rc = build_worklists(P, P.tc_boxes, P.tc_boxes);
+    if (rc) return rc;
   }
   P.tc_stages = best_st;
   P.tc_ranges = best_rg;
   if (chosen) {
     chosen[0] = best_st;
     chosen[1] = best_rg;
+    chosen[2] = best_tl;
   }
   return 0;
 }
@@ -550,17 +578,18 @@ extern "C" int kafmm_phase_times(kafmm_plan_t pl, double* t, int n) {
     }
     ms[i] = v;
   }
-  for (int i = 0; i < n && i < 8; ++i) t[i] = i < 7 ? ms[i] : 0.0;
+  for (int i = 0; i < n && i < 8; ++i) t[i] = i < 7 ? ms[i] : P.host_wl_ms;
   return 0;
 }
 
 extern "C" int kafmm_get_counters(kafmm_plan_t pl, int64_t* c, int n) {
   PLAN_CHECK(pl);
   if (!c || n < 0) return fail(P, KAFMM_ERR_ARG, "null array");
-  int64_t v[5] = {P.launches_points, P.launches_eval, P.use_tc ? 1 : 0,
+  int64_t v[7] = {P.launches_points, P.launches_eval, P.use_tc ? 1 : 0,
                   P.launches_points + P.launches_eval,
-                  P.use_tc ? (P.tc_split == SPLIT_BF16 ? KAFMM_TC_BF16X3 : KAFMM_TC_TF32X3) : -1};
-  for (int i = 0; i < n && i < 8; ++i) c[i] = i < 5 ? v[i] : 0;
+                  P.use_tc ? (P.tc_split == SPLIT_BF16 ? KAFMM_TC_BF16X3 : KAFMM_TC_TF32X3) : -1,
+                  P.wl.m2l_grouped ? 2 : 1, P.wl.m2l[1] - P.wl.m2l[0]};
+  for (int i = 0; i < n && i < 8; ++i) c[i] = i < 7 ? v[i] : 0;
   return 0;
 }
 

@@ -120,6 +120,32 @@ struct DevBuf {
   T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// Page-locked host staging buffer (grows, never shrinks; contents not preserved on growth).
+struct HostBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~HostBuf() { release(); }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t reserve(size_t nbytes) {
+    if (nbytes <= bytes && p) return cudaSuccess;
+    release();
+    size_t nb = nbytes < 4096 ? 4096 : nbytes + nbytes / 4;
+    cudaError_t e = cudaMallocHost(&p, nb);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = nb;
+    return cudaSuccess;
+  }
+  template <class T>
+  T* as(size_t byte_off = 0) const { return reinterpret_cast<T*>(static_cast<char*>(p) + byte_off); }
+};
+
 // Status word written by kernels (never trapped on): bit 0 domain error, bit 1 timeout,
 // bit 2 capacity overflow, bit 3 non-finite value.
 enum { ST_DOMAIN = 1, ST_TIMEOUT = 2, ST_OVERFLOW = 4, ST_NONFINITE = 8 };

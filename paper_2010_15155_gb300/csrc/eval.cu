@@ -836,19 +836,31 @@ static void add_tiles(WorkLists& W, std::vector<int>* by_cls, int NB, int range[
 int build_worklists(Plan& P, int NB, int NB_TC) {
   Tree& T = P.tree;
   cudaStream_t st = P.stream;
-  int nb = T.nbox;
-  std::vector<uint64_t> key(nb);
-  std::vector<int8_t> lvl(nb), leaf(nb), wflag(nb);
-  std::vector<int64_t> xoff(nb + 1);
-  std::vector<int> tb(nb), te(nb);
-  CK(cudaMemcpyAsync(key.data(), T.key.p, 8 * (size_t)nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(lvl.data(), T.level.p, nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(leaf.data(), T.leaf.p, nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(wflag.data(), T.w_flag.p, nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(xoff.data(), T.x_off.p, 8 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(tb.data(), T.tb.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(te.data(), T.te.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  const int nb = T.nbox;
+  // the tree's per-box fields, copied once into page-locked memory
+  const size_t o_key = 0, o_xoff = o_key + 8 * (size_t)nb, o_vocc = o_xoff + 8 * (size_t)(nb + 1),
+               o_tb = o_vocc + 32 * (size_t)nb, o_te = o_tb + 4 * (size_t)nb,
+               o_lvl = o_te + 4 * (size_t)nb, o_leaf = o_lvl + nb, o_wflag = o_leaf + nb,
+               down_bytes = o_wflag + nb;
+  CK(P.wl_down.reserve(down_bytes));
+  HostBuf& H = P.wl_down;
+  CK(cudaMemcpyAsync(H.as<void>(o_key), T.key.p, 8 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o_xoff), T.x_off.p, 8 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o_vocc), T.vocc.p, 32 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o_tb), T.tb.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o_te), T.te.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o_lvl), T.level.p, nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o_leaf), T.leaf.p, nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o_wflag), T.w_flag.p, nb, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  const uint64_t* key = H.as<uint64_t>(o_key);
+  const int64_t* xoff = H.as<int64_t>(o_xoff);
+  const uint8_t* oc = H.as<uint8_t>(o_vocc);
+  const int* tb = H.as<int>(o_tb);
+  const int* te = H.as<int>(o_te);
+  const int8_t* lvl = H.as<int8_t>(o_lvl);
+  const int8_t* leaf = H.as<int8_t>(o_leaf);
+  const int8_t* wflag = H.as<int8_t>(o_wflag);
   WorkLists& W = P.wl;
   W = WorkLists();
   std::vector<int> by_cls[8];
@@ -857,20 +869,95 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
     return (int)((k & 1) | ((k >> 1) & 1) << 1 | ((k >> 2) & 1) << 2);
   };
   int vmin = P.bc == KAFMM_BC_PXYZ ? 1 : 2;
-  // M->L: all boxes at levels >= vmin, grouped by class; tensor-core tiles use NB_TC boxes.
-  // Inside a class, boxes with the same V slot occupancy are kept together (sorted by its
-  // signature, stable), so a tile's slot union is close to each box's own V list: boxes near
-  // the domain boundary or a coarse neighbour have fewer V entries than interior ones.
-  std::vector<unsigned long long> vsig(nb);
-  CK(cudaMemcpyAsync(vsig.data(), T.vsig.p, sizeof(unsigned long long) * (size_t)nb,
-                     cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  // M->L: all boxes at levels >= vmin, by octant class (the class fixes the offset of each V
+  // slot).  Tensor-core tiles take NB_TC boxes.
   for (int b = 0; b < nb; ++b)
     if (lvl[b] >= vmin) by_cls[cls(b)].push_back(b);
-  for (int c = 0; c < 8; ++c)
-    std::stable_sort(by_cls[c].begin(), by_cls[c].end(),
-                     [&](int x, int y) { return vsig[x] < vsig[y]; });
-  add_tiles(W, by_cls, NB_TC, W.m2l);
+  // Per parent neighbour g (the 8 children of one colleague of the parent: Sec. II builds V
+  // lists from such children): a tile holds boxes of one class with entries from g, sorted by
+  // their 8-bit occupancy of g, and each box's result is a partial sum added to its downward
+  // check in neighbour order.  Adaptive V lists are sparse and differ from box to box, so
+  // tiles carrying whole V lists compute mostly empty columns; this is the default whenever
+  // the partials (R x C floats per box and neighbour) fit in a quarter of the device memory.
+  bool grouped = false;
+  if (P.use_tc && P.tc_tiling != 1) {
+    int64_t npart = 0;
+    for (int c = 0; c < 8; ++c)
+      for (int b : by_cls[c]) {
+        const uint64_t* o = reinterpret_cast<const uint64_t*>(oc + (size_t)b * 32);
+        for (int w = 0; w < 4; ++w) {   // nonzero bytes of each word
+          uint64_t x = o[w];
+          x |= x >> 4;
+          x |= x >> 2;
+          x |= x >> 1;
+          npart += __builtin_popcountll(x & 0x0101010101010101ull);
+        }
+      }
+    const double part_bytes = (double)npart * P.R * P.C * 4;
+    grouped = part_bytes < (double)P.dev_mem / 4 && npart < INT32_MAX;
+    if (grouped) {
+      // one counting sort per class over the keys (g, occupancy byte of g) of the class's
+      // (box, neighbour) pairs; the partial of (b, g) is b's running pair count
+      W.m2l[0] = (int)W.tiles.size();
+      W.m2l_part.reserve((size_t)npart);
+      W.boxlist.reserve((size_t)npart + 3 * (size_t)nb);
+      std::vector<int> cnt(27 * 256 + 1), pbox, ppart;
+      int run = 0;
+      for (int c = 0; c < 8; ++c) {
+        const std::vector<int>& v = by_cls[c];
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int b : v) {
+          const uint8_t* o = oc + (size_t)b * 32;
+          for (int g = 0; g < 27; ++g)
+            if (o[g]) ++cnt[g * 256 + o[g] + 1];
+        }
+        for (int k = 1; k <= 27 * 256; ++k) cnt[k] += cnt[k - 1];
+        int gs[28];
+        for (int g = 0; g <= 27; ++g) gs[g] = cnt[g * 256];
+        pbox.resize(gs[27]);
+        ppart.resize(gs[27]);
+        for (int b : v) {
+          const uint8_t* o = oc + (size_t)b * 32;
+          const int first = run;
+          for (int g = 0; g < 27; ++g)
+            if (o[g]) {
+              int pos = cnt[g * 256 + o[g]]++;
+              pbox[pos] = b;
+              ppart[pos] = run++;
+            }
+          if (run > first) W.m2l_comb.push_back(make_int4(b, first, run - first, 0));
+        }
+        for (int g = 0; g < 27; ++g)
+          for (int i = gs[g]; i < gs[g + 1]; i += NB_TC) {
+            int k = std::min(NB_TC, gs[g + 1] - i);
+            W.tiles.push_back(make_int4((int)W.boxlist.size(), k, c, g + 1));
+            W.boxlist.insert(W.boxlist.end(), pbox.begin() + i, pbox.begin() + i + k);
+            W.m2l_part.insert(W.m2l_part.end(), ppart.begin() + i, ppart.begin() + i + k);
+          }
+        by_cls[c].clear();
+      }
+      W.m2l[1] = (int)W.tiles.size();
+      W.m2l_nparts = run;
+    }
+  }
+  W.m2l_grouped = grouped;
+  if (!grouped) {
+    // whole V lists: boxes with the same occupancy kept together (sorted by a hash of it,
+    // ties in box order), so a tile's offset union stays close to each box's own V list
+    std::vector<std::pair<uint64_t, int>> kv;
+    for (int c = 0; c < 8; ++c) {
+      kv.clear();
+      for (int b : by_cls[c]) {
+        unsigned long long h = 1469598103934665603ull;   // FNV-1a over the occupancy words
+        const uint64_t* o = reinterpret_cast<const uint64_t*>(oc + (size_t)b * 32);
+        for (int w = 0; w < 4; ++w) h = (h ^ o[w]) * 1099511628211ull;
+        kv.emplace_back(h, b);
+      }
+      std::sort(kv.begin(), kv.end());
+      for (size_t i = 0; i < kv.size(); ++i) by_cls[c][i] = kv[i].second;
+    }
+    add_tiles(W, by_cls, NB_TC, W.m2l);
+  }
   // M->M per level: non-leaf boxes (class irrelevant: use class 0 bucket).  Multipoles are
   // read by M->L (levels >= vmin), by M->T over W lists (W entries lie at level >= 2) and, when
   // periodic, at the root; with the open boundary levels 0 and 1 are never read, so their M->M
@@ -899,7 +986,7 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
   for (int b = 0; b < nb; ++b)
     if (leaf[b] && te[b] > tb[b]) by_cls[0].push_back(b);
   add_tiles(W, by_cls, NB, W.pdn);
-  // plain lists: leaves (with targets) and boxes with X entries
+  // plain lists: leaves (with targets), boxes with X entries, leaves (S->M, last)
   W.leafbox_off = (int)W.boxlist.size();
   for (int b = 0; b < nb; ++b)
     if (leaf[b] && te[b] > tb[b]) W.boxlist.push_back(b);
@@ -908,24 +995,34 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
   for (int b = 0; b < nb; ++b)
     if (xoff[b + 1] > xoff[b]) W.boxlist.push_back(b);
   W.xbox_n = (int)W.boxlist.size() - W.xbox_off;
-  // S->M work: leaves (with sources)
-  CK(P.tiles.reserve(sizeof(int4) * (W.tiles.size() + 1)));
-  CK(P.tile_meta.reserve(sizeof(int) * (W.boxlist.size() + nb + 1)));
-  CK(cudaMemcpyAsync(P.tiles.p, W.tiles.data(), sizeof(int4) * W.tiles.size(), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(P.tile_meta.p, W.boxlist.data(), sizeof(int) * W.boxlist.size(),
-                     cudaMemcpyHostToDevice, st));
-  // leaves with sources (for S->M) appended after boxlist
-  std::vector<int> sleaves;
-  std::vector<int> sb(nb), se(nb);
-  CK(cudaMemcpyAsync(sb.data(), T.sb.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(se.data(), T.se.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
   for (int b = 0; b < nb; ++b)
-    if (leaf[b]) sleaves.push_back(b);
-  W.boxlist.insert(W.boxlist.end(), sleaves.begin(), sleaves.end());
-  CK(cudaMemcpyAsync(P.tile_meta.as<int>() + (W.boxlist.size() - sleaves.size()), sleaves.data(),
-                     sizeof(int) * sleaves.size(), cudaMemcpyHostToDevice, st));
-  CK(cudaStreamSynchronize(st));
+    if (leaf[b]) W.boxlist.push_back(b);
+  // upload through page-locked staging: tiles, box lists, grouped M->L partial indices and
+  // combine list
+  const size_t u_tiles = 0, u_box = u_tiles + sizeof(int4) * W.tiles.size(),
+               u_part = u_box + sizeof(int) * W.boxlist.size(),
+               u_comb = (u_part + sizeof(int) * W.m2l_part.size() + 15) / 16 * 16,
+               up_bytes = u_comb + sizeof(int4) * W.m2l_comb.size();
+  CK(P.wl_up.reserve(up_bytes));
+  HostBuf& U = P.wl_up;
+  std::copy(W.tiles.begin(), W.tiles.end(), U.as<int4>(u_tiles));
+  std::copy(W.boxlist.begin(), W.boxlist.end(), U.as<int>(u_box));
+  std::copy(W.m2l_part.begin(), W.m2l_part.end(), U.as<int>(u_part));
+  std::copy(W.m2l_comb.begin(), W.m2l_comb.end(), U.as<int4>(u_comb));
+  CK(P.tiles.reserve(sizeof(int4) * (W.tiles.size() + 1)));
+  CK(P.tile_meta.reserve(sizeof(int) * (W.boxlist.size() + 1)));
+  CK(cudaMemcpyAsync(P.tiles.p, U.as<void>(u_tiles), sizeof(int4) * W.tiles.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(P.tile_meta.p, U.as<void>(u_box), sizeof(int) * W.boxlist.size(),
+                     cudaMemcpyHostToDevice, st));
+  if (W.m2l_grouped) {
+    CK(P.m2l_part_idx.reserve(sizeof(int) * (W.m2l_part.size() + 1)));
+    CK(P.m2l_comb.reserve(sizeof(int4) * (W.m2l_comb.size() + 1)));
+    CK(cudaMemcpyAsync(P.m2l_part_idx.p, U.as<void>(u_part), sizeof(int) * W.m2l_part.size(),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(P.m2l_comb.p, U.as<void>(u_comb), sizeof(int4) * W.m2l_comb.size(),
+                       cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaStreamSynchronize(st));   // the staging buffers are reused by the next build
   return 0;
 }
 
@@ -987,9 +1084,9 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       sa.mode = 0;
       KL k_s2check<T, PR><<<n_sleaves, 128, 0, st>>>(sa);
     }
-    // The gather-GEMMs run on the tensor cores in the mixed form (four-channel table), else on
-    // the CUDA cores (k_gemm).
-    constexpr bool TC_OK = sizeof(T) == 4 && C == 4;
+    // The gather-GEMMs run on the tensor cores in the mixed form (four-channel and
+    // single-column tables), else on the CUDA cores (k_gemm).
+    constexpr bool TC_OK = sizeof(T) == 4 && (C == 4 || C == 1);
     const bool tc = TC_OK && P.use_tc;
     GemmArgs<T> ga;
     ga.t = tv;

@@ -14,8 +14,10 @@
 // two (bf16) or one (tf32) consecutive k of all four channels, so the gather is coalesced and
 // every 32-bit store instruction fills one whole swizzled 128-byte row (conflict-free).  Each operand is split x = hi + lo in the
 // MMA format (tf32 or bf16) and each product is taken as hi*hi + hi*lo + lo*hi.
-// Each offset is accumulated in a fresh TMEM accumulator and then added into a TMEM sum by
-// the epilogue warps, so no single FP32 accumulation chain spans all offsets.
+// A group of k-values (counted over the tile's offsets in order; its length is chosen per
+// table on the host) is accumulated in a fresh TMEM accumulator and then added into a TMEM sum
+// by the epilogue warps, so no FP32 accumulation chain inside the tensor core is longer than
+// one group.
 //
 // Warp roles (448 threads): 0-3 epilogue (TMEM lane quarters), 4-11 B producers, 12 TMA,
 // 13 TMEM allocation + MMA issue.  Every wait is bounded (2 s of %globaltimer); on expiry the
@@ -40,10 +42,14 @@ namespace tc {
 // Pipeline: the operand rows of a stage are SWB bytes wide, stored with the SWB-byte swizzle:
 // SWB = 128 gives two stages of 96 KB, SWB = 64 four stages of 48 KB (half the k per stage,
 // twice the stages in flight, the same MMAs in the same order).
+//
+// Single-column tables (the Stokeslet G table and the Laplace table, CH = 1): a CTA owns
+// BN = 256 / RB target boxes, one column each, and the B producers copy contiguous k-runs of
+// each source box (no re-reference: those tables have no centre-dependent channel).
 constexpr int BM = 128;
-template <int RB, int SWB>
+template <int RB, int SWB, int CH>
 struct Shape {
-  static constexpr int BN = 256 / RB, NB = BN / 4;
+  static constexpr int BN = 256 / RB, NB = BN / CH;
   static constexpr int A_TILE = BM * SWB;                // 128 rows per split and row block
   static constexpr int A_STAGE = RB * 2 * A_TILE;        // A hi/lo of all row blocks
   static constexpr int B_TILE = BN * SWB;                // BN rows per split
@@ -59,6 +65,15 @@ constexpr int SMEM_BYTES = 196608 + 4096 + 16384;
 // Stokeslet N = 262144)
 template <int SWB>
 constexpr int aux_drain() { return 128 / SWB; }
+// M->L accumulation groups.  The tensor core's FP32 accumulation loses accuracy over long
+// chains of these cancelling sums.  Single-column tables drain every 256 k-values: the
+// Stokeslet G table at p = 12 (2184 k per offset), TF32x3, measured 1.5e-5 against the FP32
+// CUDA-core form with one drain per offset, 2.2e-6 with one per 256 k (1 % slower) and 1.3e-6
+// with one per 64 k.  The four-channel table (488 k per offset at p = 10) drains after one
+// offset in TF32x3 and after two in BF16x3 (measured 7.6e-6 against the FP64 form at p = 10;
+// one drain per 256 k gives 6.1e-6 but costs 5 % of the M->L time).  A group may span two
+// offsets (the sum is linear).
+constexpr int M2L_GROUP_K = 256;
 constexpr int THREADS = 448;
 constexpr int NPROD = 256;
 constexpr int W_TMA = 12, W_MMA = 13;
@@ -95,8 +110,8 @@ enum TcWrite { TC_STORE = 0, TC_ADD = 1, TC_SCALE = 2 };
 struct Args {
   TreeView t;
   double L;
-  const float* up;        // input [nbox][R][4]
-  float* dn;              // output [nbox][R][4]; TC_M2L with nsplit > 1: [nsplit] partials
+  const float* up;        // input [nbox][R][CH]
+  float* dn;              // output [nbox][R][CH]; with nsplit > 1: [nsplit] partials
   int64_t part_stride;    // floats between partial buffers
   int nsplit;
   const int4* tiles;
@@ -106,6 +121,10 @@ struct Args {
   int R, nchunk;
   int mode, write;
   int op;                 // TC_APPLY: operator index in the tensor map
+  int group;              // TC_M2L: k-chunks per TMEM accumulation group
+  // TC_M2L tiles of one parent neighbour (tile.w = g + 1): box j of the tile writes partial
+  // part[tile.x + j] of dn (R x CH floats each) instead of its own box
+  const int* part;
 };
 
 // Slots of a mode (upper bound of the slot index), the operator of slot s in the tensor map
@@ -281,23 +300,25 @@ __device__ __forceinline__ void st_shared_u32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared.b32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, const uint32_t (&v)[4]) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "r"(v[0]), "r"(v[1]), "r"(v[2]),
+               "r"(v[3])
+               : "memory");
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-template <int SPLIT, int RB, int SWB>
+template <int SPLIT, int RB, int SWB, int CH>
 __global__ void __launch_bounds__(THREADS, 1)
     k_m2l_tc(const __grid_constant__ CUtensorMap tmap, Args a) {
   constexpr int BK = SWB / Fmt<SPLIT>::ES, MK = Fmt<SPLIT>::MK;
-  using S = Shape<RB, SWB>;
+  using S = Shape<RB, SWB, CH>;
   constexpr int BN = S::BN, NB = S::NB, B_BYTES = S::B_TILE, A_BYTES = S::A_TILE,
                 A_STAGE = S::A_STAGE, STAGE_BYTES = S::STAGE_BYTES, STAGES = S::STAGES;
   constexpr int PROD_WARPS = NPROD / 32;
-  // offsets accumulated in TMEM before each drain into the running sum: longer chains lose
-  // accuracy in TF32x3 (measured 5.4e-6 -> 8.2e-6 at p = 10 with 2), BF16x3 is limited by its
-  // operand split instead
-  constexpr int DRAIN = SPLIT == SPLIT_TF32 ? 1 : 2;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -306,12 +327,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   __shared__ int nslots, bail;
   __shared__ int slot_list[216];
   __shared__ int sbox[NB];
+  __shared__ int sout[NB];          // output record of box j (its box, or its partial)
   __shared__ float sside[NB];
   __shared__ int slot_any[216];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int4 tile = a.tiles[blockIdx.x];
   const int cls = tile.z;
+  const int grp = a.mode == TC_M2L ? tile.w - 1 : -1;   // parent neighbour, -1 = whole V lists
   const int R = a.R;
   const int row0 = blockIdx.y * (RB * BM);
   // row blocks of this CTA that hold operator rows (the last pair may have only one)
@@ -320,6 +343,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x < NB) {
     int b = threadIdx.x < tile.y ? a.boxlist[tile.x + threadIdx.x] : -1;
     sbox[threadIdx.x] = b;
+    sout[threadIdx.x] = grp >= 0 && b >= 0 ? a.part[tile.x + threadIdx.x] : b;
     sside[threadIdx.x] = b >= 0 ? (float)(a.L / (double)(1 << a.t.level[b])) : 0.f;
   }
   for (int k = threadIdx.x; k < 216; k += THREADS) slot_any[k] = 0;
@@ -335,8 +359,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   // active slots: some box of the tile has a source there
   const int nsmax = mode_slots(a.mode);
-  for (int e = threadIdx.x; e < nsmax * NB; e += THREADS) {
+  // candidate slots: the 8 children of parent neighbour grp, or all slots of the mode
+  const int ncand = grp >= 0 ? 8 : nsmax;
+  for (int e = threadIdx.x; e < ncand * NB; e += THREADS) {
     int k = e / NB, j = e % NB;
+    if (grp >= 0)
+      k = (2 * (grp % 3) + (k & 1)) + 6 * (2 * ((grp / 3) % 3) + ((k >> 1) & 1)) +
+          36 * (2 * (grp / 9) + (k >> 2));
     bool inner = false;
     if (a.mode == TC_M2L) {
       int ox = k % 6 - 2 - (cls & 1), oy = (k / 6) % 6 - 2 - ((cls >> 1) & 1),
@@ -370,8 +399,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int nchunk = a.nchunk;
   const int total = ns * nchunk;
   // accumulation groups: iterations accumulated in TMEM before the epilogue adds them into the
-  // running sum (M->L: DRAIN whole offsets; other modes: AUX_DRAIN k-chunks)
-  const int GI = a.mode == TC_M2L ? DRAIN * nchunk : aux_drain<SWB>();
+  // running sum (M->L: a.group chunks; other modes: one 128-byte chunk)
+  const int GI = a.mode == TC_M2L ? a.group : aux_drain<SWB>();
   const int ngroups = (total + GI - 1) / GI;
 
   if (warp == W_TMA) {
@@ -400,6 +429,101 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else if (warp >= 4 && warp < W_TMA) {
+   if constexpr (CH == 1) {
+    // ---------------- B producers, single-column tables: gather, split, swizzle ----------------
+    // Row n of B = target box n of the tile: the BK k-values of this chunk of its source box,
+    // contiguous in memory.  LPR lanes share a row, each loading 8 consecutive k (32 bytes)
+    // and writing its 16-byte chunk(s) of the swizzled row (one per 8 bf16, two per 8 tf32);
+    // a warp instruction covers BPI boxes, so the loads are contiguous runs and each
+    // shared-memory phase of 8 lanes fills whole 128-byte rows (conflict-free).
+    static_assert(SWB == 128, "single-column tables use 128-byte rows");
+    constexpr int LPR = BK / 8;                      // lanes per row
+    constexpr int BPI = 32 / LPR;                    // boxes per warp instruction (4 or 8)
+    constexpr int UPW = NB / PROD_WARPS;             // boxes per producer warp per stage
+    constexpr int LPS = UPW / BPI;                   // boxes per lane per stage
+    constexpr int UH = LPS / 2;                      // boxes per lane per half stage
+    static_assert(UH >= 1 && LPS == 2 * UH, "two half stages");
+    const int pw = warp - 4;
+    const int bsel = lane / LPR, wd = lane % LPR;
+    auto box_of = [&](int ul) { return pw * UPW + ul * BPI + bsel; };
+    int srcb[LPS];
+    int cur_slot = -1;
+    auto load_half = [&](int it, int h, float4 (&q)[UH][2]) {
+      int s = slot_list[it / nchunk], c = it % nchunk;
+      if (s != cur_slot) {
+#pragma unroll
+        for (int ul = 0; ul < LPS; ++ul) srcb[ul] = slot_src(a, sbox[box_of(ul)], s);
+        cur_slot = s;
+      }
+      const int k0 = c * BK + wd * 8;
+      const bool kin = k0 < R;   // R a multiple of 8: a lane's 8 k are all in or all out
+#pragma unroll
+      for (int u = 0; u < UH; ++u) {
+        int sb = srcb[h * UH + u];
+        if (sb >= 0 && kin) {
+          ld_nc_v8(reinterpret_cast<const float4*>(a.up + (int64_t)sb * R + k0), q[u][0], q[u][1]);
+        } else {
+          q[u][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+          q[u][1] = q[u][0];
+        }
+      }
+    };
+    auto store_half = [&](int it, int h, const float4 (&q)[UH][2]) {
+      const int st = it % STAGES;
+      const uint32_t bhi = smem_u32(smem + st * STAGE_BYTES + A_STAGE);
+      const uint32_t blo = bhi + B_BYTES;
+#pragma unroll
+      for (int u = 0; u < UH; ++u) {
+        const int n = box_of(h * UH + u);
+        const uint32_t row = (uint32_t)(n * SWB);
+        const float v[8] = {q[u][0].x, q[u][0].y, q[u][0].z, q[u][0].w,
+                            q[u][1].x, q[u][1].y, q[u][1].z, q[u][1].w};
+        if (SPLIT == SPLIT_TF32) {
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              float hf = tf32_rn(v[4 * g + t]);
+              hw[t] = __float_as_uint(hf);
+              lw[t] = __float_as_uint(tf32_rn(v[4 * g + t] - hf));
+            }
+            const uint32_t off = row + ((uint32_t)((2 * wd + g) ^ (n & 7)) << 4);
+            st_shared_v4(bhi + off, hw);
+            st_shared_v4(blo + off, lw);
+          }
+        } else {
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * t], v[2 * t + 1]);
+            float2 hf = __bfloat1622float2(h2);
+            hw[t] = *reinterpret_cast<uint32_t*>(&h2);
+            lw[t] = pack_bf16(v[2 * t] - hf.x, v[2 * t + 1] - hf.y);
+          }
+          const uint32_t off = row + ((uint32_t)(wd ^ (n & 7)) << 4);
+          st_shared_v4(bhi + off, hw);
+          st_shared_v4(blo + off, lw);
+        }
+      }
+    };
+    float4 qa[UH][2], qb[UH][2];
+    if (total > 0) load_half(0, 0, qa);
+    for (int it = 0; it < total; ++it) {
+      int st = it % STAGES;
+      load_half(it, 1, qb);
+      int ok_wait = 1;
+      if (lane == 0 && it >= STAGES)
+        ok_wait = wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
+      store_half(it, 0, qa);
+      if (it + 1 < total) load_half(it + 1, 0, qa);
+      store_half(it, 1, qb);
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) arrive(&full[st]);
+    }
+   } else {
     // ---------------- B producers: gather, re-reference, split, swizzle ----------------
     // Work unit = one target box j of the tile: the BK k-values of this chunk of its source
     // box's four channels.  Lane l takes EPL consecutive k (two for bf16, one for tf32), i.e.
@@ -532,6 +656,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       __syncwarp();
       if (lane == 0) arrive(&full[st]);
     }
+   }
   } else if (warp == W_MMA) {
     // ---------------- MMA issue (one thread) ----------------
     if (lane == 0) {
@@ -606,13 +731,26 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int t = 0; t < 32; ++t) x[t] = 0.f;
         }
-        if (row < R) {
+        if constexpr (CH == 1) {
+         if (row < R) {
+          // column t = box 32 qc + t; a warp writes 32 consecutive rows of one box per store
+          float* dst1 = a.dn + a.part_stride * blockIdx.z;
+#pragma unroll
+          for (int t = 0; t < 32; ++t) {
+            if (sbox[qc * 32 + t] < 0) continue;
+            float* o = dst1 + (int64_t)sout[qc * 32 + t] * R + row;
+            float v = x[t];
+            if (a.write == TC_ADD) v += *o;
+            else if (a.write == TC_SCALE) v *= 0.5f * sside[qc * 32 + t];
+            *o = v;
+          }
+         }
+        } else if (row < R) {
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
-            int b = sbox[qc * 8 + jj];
-            if (b < 0) continue;
+            if (sbox[qc * 8 + jj] < 0) continue;
             float4 v = make_float4(x[4 * jj], x[4 * jj + 1], x[4 * jj + 2], x[4 * jj + 3]);
-            float4* o = dst + (int64_t)b * R + row;
+            float4* o = dst + (int64_t)sout[qc * 8 + jj] * R + row;
             if (a.write == TC_ADD) {
               float4 w = *o;
               v.x += w.x;
@@ -671,13 +809,48 @@ __global__ void k_combine_parts(const float4* __restrict__ parts, int64_t part_s
   }
 }
 
+// Grouped M->L: dn[box] (+)= sum of the box's partials (one per parent neighbour, in
+// neighbour order).  comb = (box, first partial, count); R4 = float4 per box.
+__global__ void k_combine_groups(const float4* __restrict__ parts, const int4* __restrict__ comb,
+                                 int ncomb, float4* __restrict__ dn, int R4, int add) {
+  for (int i = blockIdx.x; i < ncomb; i += gridDim.x) {
+    const int4 c = comb[i];
+    for (int r = threadIdx.x; r < R4; r += blockDim.x) {
+      const float4* p = parts + (int64_t)c.y * R4 + r;
+      float4 v = p[0];
+      for (int k = 1; k < c.z; ++k) {
+        float4 w = p[(int64_t)k * R4];
+        v.x += w.x;
+        v.y += w.y;
+        v.z += w.z;
+        v.w += w.w;
+      }
+      float4* o = dn + (int64_t)c.x * R4 + r;
+      if (add) {
+        float4 d = *o;
+        v.x += d.x;
+        v.y += d.y;
+        v.z += d.z;
+        v.w += d.w;
+      }
+      *o = v;
+    }
+  }
+}
+
 }  // namespace tc
 
+// Tables on the tensor cores: the four-channel Laplace table (Laplace ML kernel, C = 4) and
+// the single-column tables (C = 1) whose rows per box are a multiple of 8 (32-byte loads).
+bool tc_table(const Plan& P) {
+  return (P.C == 4 && !P.ml_stokes) || (P.C == 1 && P.R % 8 == 0);
+}
+
 bool tc_supported(Plan& P) {
-  if (P.prec != KAFMM_PREC_MIXED || P.C != 4 || P.ml_stokes || !P.opstc.p) return false;
+  if (P.prec != KAFMM_PREC_MIXED || !tc_table(P) || !P.opstc.p) return false;
   int rows = (P.R + tc::BM - 1) / tc::BM;
   P.tc_rb = rows % 2 == 0 ? 2 : 1;
-  P.tc_boxes = 64 / P.tc_rb;
+  P.tc_boxes = 256 / P.tc_rb / P.C;
   int dev = 0, major = 0, minor = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
@@ -723,10 +896,12 @@ static int tc_prepare(Plan& P) {
     if (rc) return rc;
   }
   cudaError_t e = cudaSuccess;
-  for (auto fn : {tc::k_m2l_tc<SPLIT_TF32, 1, 128>, tc::k_m2l_tc<SPLIT_TF32, 2, 128>,
-                  tc::k_m2l_tc<SPLIT_BF16, 1, 128>, tc::k_m2l_tc<SPLIT_BF16, 2, 128>,
-                  tc::k_m2l_tc<SPLIT_TF32, 1, 64>, tc::k_m2l_tc<SPLIT_TF32, 2, 64>,
-                  tc::k_m2l_tc<SPLIT_BF16, 1, 64>, tc::k_m2l_tc<SPLIT_BF16, 2, 64>})
+  for (auto fn : {tc::k_m2l_tc<SPLIT_TF32, 1, 128, 4>, tc::k_m2l_tc<SPLIT_TF32, 2, 128, 4>,
+                  tc::k_m2l_tc<SPLIT_BF16, 1, 128, 4>, tc::k_m2l_tc<SPLIT_BF16, 2, 128, 4>,
+                  tc::k_m2l_tc<SPLIT_TF32, 1, 64, 4>, tc::k_m2l_tc<SPLIT_TF32, 2, 64, 4>,
+                  tc::k_m2l_tc<SPLIT_BF16, 1, 64, 4>, tc::k_m2l_tc<SPLIT_BF16, 2, 64, 4>,
+                  tc::k_m2l_tc<SPLIT_TF32, 1, 128, 1>, tc::k_m2l_tc<SPLIT_TF32, 2, 128, 1>,
+                  tc::k_m2l_tc<SPLIT_BF16, 1, 128, 1>, tc::k_m2l_tc<SPLIT_BF16, 2, 128, 1>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
   if (e != cudaSuccess) return cuda_fail(P, e, "cudaFuncSetAttribute(k_m2l_tc)");
   P.tmap_ready = true;
@@ -741,18 +916,23 @@ int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* 
   int rc = tc_prepare(P);
   if (rc) return rc;
   const bool m2l = mode == tc::TC_M2L;
-  const int sw = P.tc_stages == 4 ? 1 : 0;   // 64-byte rows, four stages : 128-byte rows, two
+  // 64-byte rows, four stages : 128-byte rows, two (single-column tables: always two)
+  const int sw = P.tc_stages == 4 && P.C == 4 ? 1 : 0;
   const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(P.tmaps[m2l ? 0 : 1][sw]);
   const int split = m2l ? P.tc_split : SPLIT_TF32;
   int rows = (P.R + P.tc_rb * tc::BM - 1) / (P.tc_rb * tc::BM);   // CTAs per tile
   // slot ranges per tile (M->L offsets, M->M child octants): enough CTAs to fill the 152 SMs
   // over several waves; the ranges' partial sums are combined in fixed order
-  const bool splittable = m2l || mode == tc::TC_M2M;
+  // grouped M->L tiles (one parent neighbour each) write per-box partials, combined below
+  const bool grouped = m2l && P.wl.m2l_grouped;
+  const bool splittable = (m2l && !grouped) || mode == tc::TC_M2M;
   int nsplit = 1;
   while (splittable && nsplit < P.tc_ranges && (int64_t)ntiles * rows * nsplit < 152 * 6) nsplit *= 2;
-  int64_t part_stride = (int64_t)P.tree.nbox * P.R * 4;
-  if (nsplit > 1) {
-    cudaError_t e = P.m2l_parts.reserve(sizeof(float) * part_stride * nsplit + 256);
+  int64_t part_stride = (int64_t)P.tree.nbox * P.R * P.C;
+  if (nsplit > 1 || grouped) {
+    size_t bytes = grouped ? sizeof(float) * (size_t)P.wl.m2l_nparts * P.R * P.C + 256
+                           : sizeof(float) * part_stride * nsplit + 256;
+    cudaError_t e = P.m2l_parts.reserve(bytes);
     if (e != cudaSuccess) return cuda_fail(P, e, "M->L partial buffers");
   }
   tc::Args a;
@@ -760,23 +940,33 @@ int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* 
   a.L = P.L;
   a.up = in;
   // one offset range: straight into the output; several: partial buffers, combined below
-  a.dn = nsplit > 1 ? P.m2l_parts.as<float>() : out;
+  a.dn = nsplit > 1 || grouped ? P.m2l_parts.as<float>() : out;
   a.part_stride = nsplit > 1 ? part_stride : 0;
   a.nsplit = nsplit;
+  a.part = grouped ? P.m2l_part_idx.as<int>() : nullptr;
   a.tiles = tiles;
   a.boxlist = boxlist;
   a.vtab = P.tree.vtab.as<int32_t>();
   a.status = P.tree.status.as<unsigned>();
   a.R = P.R;
   a.mode = mode;
-  a.write = nsplit > 1 ? tc::TC_STORE : write;
+  a.write = nsplit > 1 || grouped ? tc::TC_STORE : write;
   a.op = m2l ? 0 : op_slot - OP_M2M;
   dim3 grid(ntiles, rows, nsplit);
   const int swb = sw ? 64 : 128;
-  a.nchunk = P.Rpad / (swb / (split == SPLIT_TF32 ? tc::Fmt<SPLIT_TF32>::ES : tc::Fmt<SPLIT_BF16>::ES));
+  const int bk = swb / (split == SPLIT_TF32 ? tc::Fmt<SPLIT_TF32>::ES : tc::Fmt<SPLIT_BF16>::ES);
+  a.nchunk = P.Rpad / bk;
+  a.group = P.C == 1 ? tc::M2L_GROUP_K / bk : (split == SPLIT_BF16 ? 2 : 1) * a.nchunk;
 #define KAFMM_TC_LAUNCH(SP, RBv, SW) \
-  KL tc::k_m2l_tc<SP, RBv, SW><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a)
-  if (swb == 128) {
+  KL tc::k_m2l_tc<SP, RBv, SW, 4><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a)
+#define KAFMM_TC_LAUNCH1(SP, RBv) \
+  KL tc::k_m2l_tc<SP, RBv, 128, 1><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a)
+  if (P.C == 1) {
+    if (split == SPLIT_TF32 && P.tc_rb == 2) KAFMM_TC_LAUNCH1(SPLIT_TF32, 2);
+    else if (split == SPLIT_TF32) KAFMM_TC_LAUNCH1(SPLIT_TF32, 1);
+    else if (P.tc_rb == 2) KAFMM_TC_LAUNCH1(SPLIT_BF16, 2);
+    else KAFMM_TC_LAUNCH1(SPLIT_BF16, 1);
+  } else if (swb == 128) {
     if (split == SPLIT_TF32 && P.tc_rb == 2) KAFMM_TC_LAUNCH(SPLIT_TF32, 2, 128);
     else if (split == SPLIT_TF32) KAFMM_TC_LAUNCH(SPLIT_TF32, 1, 128);
     else if (P.tc_rb == 2) KAFMM_TC_LAUNCH(SPLIT_BF16, 2, 128);
@@ -788,10 +978,15 @@ int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* 
     else KAFMM_TC_LAUNCH(SPLIT_BF16, 1, 64);
   }
 #undef KAFMM_TC_LAUNCH
-  if (nsplit > 1)
+#undef KAFMM_TC_LAUNCH1
+  if (grouped && !P.wl.m2l_comb.empty())
+    KL tc::k_combine_groups<<<std::min((int)P.wl.m2l_comb.size(), 152 * 8), 128, 0, st>>>(
+        P.m2l_parts.as<float4>(), P.m2l_comb.as<int4>(), (int)P.wl.m2l_comb.size(),
+        reinterpret_cast<float4*>(out), P.R * P.C / 4, write == tc::TC_ADD ? 1 : 0);
+  if (nsplit > 1)   // a box holds R * C floats = R * C / 4 float4 (R * C a multiple of 8)
     KL tc::k_combine_parts<<<std::min(ntiles, 152 * 4), 256, 0, st>>>(
         P.m2l_parts.as<float4>(), part_stride / 4, nsplit, reinterpret_cast<float4*>(out), tiles, ntiles,
-        boxlist, P.R, write == tc::TC_ADD ? 1 : 0);
+        boxlist, P.R * P.C / 4, write == tc::TC_ADD ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(P, e, "k_m2l_tc launch");
   return 0;

@@ -437,7 +437,8 @@ int build_operators(Plan& P) {
   } else {
     CK(P.ops32.reserve(sizeof(float) * RR * N_OPS));
     KL k_round32<<<2048, 256, 0, st>>>(O, (int64_t)RR * N_OPS, P.ops32.as<float>());
-    if (P.prec == KAFMM_PREC_MIXED && P.C == 4) {
+    extern bool tc_table(const Plan& P);
+    if (P.prec == KAFMM_PREC_MIXED && tc_table(P)) {
       P.Rpad = (R + 63) / 64 * 64;
       P.tmap_ready = false;
       if (P.tc_split == SPLIT_TF32) {

@@ -44,7 +44,7 @@ struct Tree {
   // lists, CSR over boxes (entries packed with pack_entry)
   DevBuf u_off, u_ent, w_off, w_ent, x_off, x_ent;
   DevBuf vtab;                      // [nbox][216] source box of each V slot or LIST_EMPTY
-  DevBuf vsig;                      // [nbox] signature of the box's V slot occupancy
+  DevBuf vocc;                      // [nbox][32] bytes: V slot occupancy per parent neighbour
   DevBuf w_flag;                    // [nbox] 1 if the box appears in some W list
   // scratch of the build
   DevBuf s_keys2, s_vals2, s_hist, t_keys2, t_vals2;
@@ -60,6 +60,13 @@ struct WorkLists {
   std::vector<int> boxlist;
   std::vector<int4> tiles;
   int m2l[2] = {0, 0};                       // tile ranges
+  // tensor-core M->L tiled per (octant class, parent neighbour g): tile.w = g + 1, each box's
+  // result goes to its own partial (index m2l_part[boxlist position]) and the partials of a
+  // box are added in order by the combine list (box, first partial, count)
+  bool m2l_grouped = false;
+  int64_t m2l_nparts = 0;
+  std::vector<int> m2l_part;
+  std::vector<int4> m2l_comb;
   int m2m[MAX_LEVELS][2] = {};
   int l2l[MAX_LEVELS][2] = {};
   int pup[2] = {0, 0}, pdn[2] = {0, 0};
@@ -94,6 +101,8 @@ struct Plan {
   bool tmap_ready = false;
   int tc_stages = 2;                // pipeline depth of the tensor-core kernel (2 or 4)
   int tc_ranges = 4;                // most slot ranges (CTAs) per tile of a small grid (1..8)
+  int tc_tiling = 0;                // M->L tiles: 0 automatic, 1 whole V lists, 2 per neighbour
+  size_t dev_mem = 0;               // device memory in bytes (read when the operators are built)
   DevBuf unit64, unit32;            // unit surface [n][3]
   DevBuf tm2l64, tm2l32;            // periodic far-image operator [R][R]
   // tree + data
@@ -104,7 +113,10 @@ struct Plan {
   DevBuf g_sorted;                  // target values in sorted order
   DevBuf io_in, io_out, io_aux;     // staging for host pointers / dtype conversion
   DevBuf tiles, tile_meta;          // work lists of the gather-GEMM engine
+  HostBuf wl_down, wl_up;           // pinned staging of the work-list build (tree in, lists out)
+  double host_wl_ms = 0;            // host time of the last work-list build
   DevBuf m2l_parts;                 // partial M->L sums per offset range (tensor-core path)
+  DevBuf m2l_part_idx, m2l_comb;    // grouped M->L: partial index per tile entry, combine list
   int64_t tiles_cap = 0;
   WorkLists wl;
   bool use_tc = false;              // tensor-core M->L available for this plan

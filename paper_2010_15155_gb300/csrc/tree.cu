@@ -539,21 +539,29 @@ __global__ void k_leaf_of(TreeView t, int* __restrict__ leaf_of) {
       for (int i = t.sb[b]; i < t.se[b]; ++i) leaf_of[i] = b;
 }
 
-__global__ void k_tree_stats(TreeView t, const int32_t* vtab, unsigned long long* out,
-                             unsigned long long* vsig) {
+// V-list count, largest leaf, and the V slot occupancy of every box as 27 bytes (padded to 32):
+// byte g = (gx, gy, gz) in [0,3)^3 is the neighbour of the parent at offset (g - 1), bit
+// d = (dx, dy, dz) its child, i.e. slot (2gx + dx) + 6 (2gy + dy) + 36 (2gz + dz) of the 6^3
+// table.
+__global__ void k_tree_stats(TreeView t, const int32_t* vtab, unsigned long long* out, uint4* vocc) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x) {
-    unsigned long long nv = 0, h = 1469598103934665603ull;   // FNV-1a offset basis
-    uint64_t word = 0;
-    for (int k = 0; k < 216; ++k) {
-      bool on = vtab[(int64_t)b * 216 + k] != LIST_EMPTY;
-      nv += on;
-      word |= (uint64_t)on << (k & 63);
-      if ((k & 63) == 63 || k == 215) {
-        h = (h ^ word) * 1099511628211ull;
-        word = 0;
+    unsigned long long nv = 0;
+    uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int32_t* vt = vtab + (int64_t)b * 216;
+#pragma unroll
+    for (int g = 0; g < 27; ++g) {
+      const int gx = g % 3, gy = (g / 3) % 3, gz = g / 9;
+      uint32_t byte = 0;
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        int k = (2 * gx + (d & 1)) + 6 * (2 * gy + ((d >> 1) & 1)) + 36 * (2 * gz + (d >> 2));
+        byte |= (uint32_t)(vt[k] != LIST_EMPTY) << d;
       }
+      nv += __popc(byte);
+      w[g >> 2] |= byte << (8 * (g & 3));
     }
-    vsig[b] = h;
+    vocc[2 * (int64_t)b] = make_uint4(w[0], w[1], w[2], w[3]);
+    vocc[2 * (int64_t)b + 1] = make_uint4(w[4], w[5], w[6], w[7]);
     atomicAdd(&out[0], nv);
     if (t.leaf[b]) {
       unsigned long long np = (unsigned long long)max(t.se[b] - t.sb[b], t.te[b] - t.tb[b]);
@@ -849,9 +857,8 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   // V entries and the largest leaf
   unsigned long long* stats = (unsigned long long*)(T.status.as<unsigned>() + 10);
   CK(cudaMemsetAsync(stats, 0, 16, st));
-  CK(T.vsig.reserve(sizeof(unsigned long long) * (nb + 1)));
-  KL k_tree_stats<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vtab.as<int32_t>(), stats,
-                                                   T.vsig.as<unsigned long long>());
+  CK(T.vocc.reserve(32 * (size_t)(nb + 1)));
+  KL k_tree_stats<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vtab.as<int32_t>(), stats, T.vocc.as<uint4>());
   unsigned long long hs[2];
   CK(cudaMemcpyAsync(hs, stats, 16, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -22,7 +22,7 @@ LAPLACE, STOKESLET, RPY, STOKES_DL = 0, 1, 2, 3
 BC_OPEN, BC_PXYZ = 0, 3
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN, OPT_TC_SPLIT = 1, 2, 3, 4, 5, 6
-OPT_SYNC, OPT_TC_STAGES, OPT_TC_RANGES, OPT_RPY_CONTACT = 7, 8, 9, 10
+OPT_SYNC, OPT_TC_STAGES, OPT_TC_RANGES, OPT_RPY_CONTACT, OPT_TC_TILING = 7, 8, 9, 10, 11
 TC_TF32X3, TC_BF16X3, TC_AUTO = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 ML_G, ML_L4 = 0, 1
@@ -144,9 +144,9 @@ def kafmm_eval(plan, s, g, dtype):
 
 
 def kafmm_autotune(plan, s, g, dtype):
-    chosen = (ctypes.c_int64 * 2)()
+    chosen = (ctypes.c_int64 * 3)()
     _check(plan, lib().kafmm_autotune(plan, _ptr(s), _ptr(g), dtype, chosen))
-    return {"tc_stages": int(chosen[0]), "tc_ranges": int(chosen[1])}
+    return {"tc_stages": int(chosen[0]), "tc_ranges": int(chosen[1]), "tc_tiling": int(chosen[2])}
 
 
 def kafmm_status(plan):
@@ -191,7 +191,7 @@ def kafmm_get_list(plan, kind, nbox):
 def kafmm_phase_times(plan):
     t = (ctypes.c_double * 8)()
     _check(plan, lib().kafmm_phase_times(plan, t, 8))
-    names = ["tree", "lists", "upward", "m2l", "downward", "leaves", "eval"]
+    names = ["tree", "lists", "upward", "m2l", "downward", "leaves", "eval", "host_worklists"]
     return {k: float(t[i]) for i, k in enumerate(names)}
 
 
@@ -200,7 +200,9 @@ def kafmm_get_counters(plan):
     _check(plan, lib().kafmm_get_counters(plan, c, 8))
     return {"launches_points": int(c[0]), "launches_eval": int(c[1]),
             "tensor_core_m2l": int(c[2]), "launches_per_step": int(c[3]),
-            "tc_split": {0: "tf32x3", 1: "bf16x3"}.get(int(c[4]))}
+            "tc_split": {0: "tf32x3", 1: "bf16x3"}.get(int(c[4])),
+            "m2l_tiling": {1: "whole V lists", 2: "per parent neighbour"}.get(int(c[5])),
+            "m2l_tiles": int(c[6])}
 
 
 def kafmm_get_operator(plan, slot, R):

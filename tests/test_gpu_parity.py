@@ -193,6 +193,73 @@ def test_mixed_tensor_core_form_matches_fp64_form(n, p, q):
     assert D.rel_l2(out[K.PREC_MIXED], out[K.PREC_FP64]) < 1e-5
 
 
+@pytest.mark.parametrize("kernel,bc,p,split", [
+    ("laplace", "open", 8, K.TC_TF32X3),      # R = 296: one 128-row block per CTA
+    ("stokeslet", "open", 6, K.TC_TF32X3),    # G table, R = 456: two row blocks per CTA
+    ("stokeslet", "open", 8, K.TC_BF16X3),    # G table, R = 888
+    ("stokeslet", "pxyz", 8, K.TC_AUTO),      # periodic G table (root operator on CUDA cores)
+    ("rpy", "open", 6, K.TC_AUTO),            # RPY on the G table
+])
+def test_mixed_tensor_core_single_column_tables_match_fp64_form(kernel, bc, p, split):
+    """Single-column ML tables (Laplace; the Stokeslet G table, open and periodic) with the
+    M->L, M->M, L->L and pseudo-inverse gather-GEMMs on the tensor cores: within 1e-5 of the
+    FP32 form (same rounded operators on the CUDA cores), and no further from the plain FP64
+    form than the FP32 form is, plus 1e-5.  (At p = 6 the FP32 form itself differs from the
+    FP64 form by about 1e-4: its pseudo-inverse cutoff, 1e-7, drops more singular values.)"""
+    n = 30000
+    pts, s = _neutral(kernel, n, seed=41) if bc == "pxyz" else _inputs(kernel, n, seed=41)
+    pts = np.minimum(pts, 1.0 - 2.0 ** -24)   # below 1 after rounding to FP32
+    out = {}
+    for prec in (K.PREC_FP64, K.PREC_FP32, K.PREC_MIXED):
+        dt = torch.float64 if prec == K.PREC_FP64 else torch.float32
+        plan = K.Plan(KERN[kernel], p=p, q=64, bc=K.BC_PXYZ if bc == "pxyz" else K.BC_OPEN,
+                      precision=prec, variant=K.ML_G, tc_split=split)
+        plan.set_points(torch.from_numpy(pts).to(dt).cuda())
+        out[prec] = plan.eval(torch.from_numpy(s).to(dt).cuda()).double().cpu().numpy()
+        if prec == K.PREC_MIXED:
+            assert K.kafmm_get_counters(plan.h)["tensor_core_m2l"] == 1
+        plan.close()
+    tc_err = D.rel_l2(out[K.PREC_MIXED], out[K.PREC_FP32])
+    err = D.rel_l2(out[K.PREC_MIXED], out[K.PREC_FP64])
+    assert tc_err < 1e-5
+    assert err < D.rel_l2(out[K.PREC_FP32], out[K.PREC_FP64]) + 1e-5
+
+
+@pytest.mark.parametrize("workload", ["uniform_l4", "clusters_l4", "uniform_g"])
+def test_m2l_tilings_agree(workload):
+    """Tensor-core M->L tiled per parent neighbour (per-box partials, combined in neighbour
+    order) and with whole V lists per tile compute the same translations: equal up to the
+    summation order of the split products (2.6e-6 measured, uniform, p = 8), each within 1e-5
+    of the FP64 form; both are deterministic."""
+    if workload == "clusters_l4":
+        pts, f, _ = W.rpy_clusters(100000, seed=7, n_clusters=16)
+        kern, variant, p = K.STOKESLET, K.ML_L4, 8
+    else:
+        pts, f = W.stokes_uniform(60000, seed=8, dtype=np.float32)
+        kern, variant, p = K.STOKESLET, (K.ML_L4 if workload == "uniform_l4" else K.ML_G), 8
+    y = torch.from_numpy(pts).cuda()
+    s = torch.from_numpy(f).cuda()
+    out = {}
+    for tiling in (1, 2):
+        plan = K.Plan(kern, p=p, q=64, precision=K.PREC_MIXED, variant=variant)
+        K.kafmm_set_option(plan.h, K.OPT_TC_TILING, tiling)
+        plan.set_points(y)
+        g = plan.eval(s)
+        assert torch.equal(plan.eval(s), g)
+        c = K.kafmm_get_counters(plan.h)
+        assert c["tensor_core_m2l"] == 1
+        assert c["m2l_tiling"] == ("whole V lists" if tiling == 1 else "per parent neighbour")
+        out[tiling] = g.double().cpu().numpy()
+        plan.close()
+    p64 = K.Plan(kern, p=p, q=64, precision=K.PREC_FP64, variant=variant)
+    p64.set_points(y.double())
+    ref = p64.eval(s.double()).cpu().numpy()
+    p64.close()
+    print("tilings", workload, D.rel_l2(out[2], out[1]), D.rel_l2(out[1], ref), D.rel_l2(out[2], ref))
+    assert D.rel_l2(out[2], out[1]) < 1e-5
+    assert D.rel_l2(out[1], ref) < 1e-5 and D.rel_l2(out[2], ref) < 1e-5
+
+
 @pytest.mark.parametrize("prec,tol", [(K.PREC_FP64, 1e-6), (K.PREC_FP32, 2e-5)])
 def test_rpy_sphere_velocities_with_overlap_match_brute_force(prec, tol):
     """kafmm_eval ([u, lap u]) + kafmm_rpy_velocity (assembly u + a^2/6 lap u and the overlap
@@ -262,6 +329,36 @@ def test_periodic_fp32_gpu_kafmm_against_ewald_and_translation():
 
 
 
+def test_periodic_full_size_mixed_form():
+    """Triply periodic Stokeslet at full size (2^22 uniform points, forces minus their mean,
+    p = 12, q = 128) in the mixed form (G table on the tensor cores): within 1e-5 of the FP32
+    CUDA-core form (pinned to the Ewald sum and the oracle's periodic KAFMM at small sizes by
+    the tests above), and a rigid shift modulo the cell (Sec. III.B) changes the result by less
+    than 1e-5 (measured 2.9e-6 and 6.5e-6)."""
+    n = 1 << 22
+    pts, f = W.stokes_uniform(n, seed=4, zero_mean=True)
+    y = torch.from_numpy(pts).cuda()
+    s = torch.from_numpy(f).cuda()
+    plan = K.Plan(K.STOKESLET, p=12, q=128, bc=K.BC_PXYZ, precision=K.PREC_MIXED, variant=K.ML_G)
+    plan.set_points(y)
+    g0 = plan.eval(s)
+    assert K.kafmm_get_counters(plan.h)["tensor_core_m2l"] == 1
+    sh = ((pts.astype(np.float64) + np.array([0.4173, 0.2281, 0.9011])) % 1.0).astype(np.float32)
+    sh = np.minimum(sh, np.float32(1) - np.float32(2 ** -24))
+    plan.set_points(torch.from_numpy(sh).cuda())
+    g1 = plan.eval(s)
+    plan.close()
+    p32 = K.Plan(K.STOKESLET, p=12, q=128, bc=K.BC_PXYZ, precision=K.PREC_FP32, variant=K.ML_G)
+    p32.set_points(y)
+    g32 = p32.eval(s)
+    p32.close()
+
+    def rel(a, b):
+        return float(torch.linalg.norm(a.double() - b.double()) / torch.linalg.norm(b.double()))
+    assert rel(g0, g32) < 1e-5
+    assert rel(g1, g0) < 1e-5
+
+
 def test_eval_is_graph_capturable():
     """With KAFMM_OPT_SYNC = 0 a kafmm_eval after the first one enqueues work only: captured in
     a CUDA graph and replayed it reproduces the eager result bit for bit, for new source values
@@ -326,11 +423,13 @@ def test_autotune_picks_a_valid_configuration():
     plan.set_points(y)
     chosen = K.kafmm_autotune(plan.h, s, g, K.F32)
     assert chosen["tc_stages"] in (2, 4) and chosen["tc_ranges"] in (1, 2, 4, 8)
+    assert chosen["tc_tiling"] in (1, 2)
     tuned = plan.eval(s)
     plan.close()
     ref = K.Plan(K.STOKESLET, p=8, q=64, precision=K.PREC_MIXED, variant=K.ML_L4,
                  tc_stages=chosen["tc_stages"])
     K.kafmm_set_option(ref.h, K.OPT_TC_RANGES, chosen["tc_ranges"])
+    K.kafmm_set_option(ref.h, K.OPT_TC_TILING, chosen["tc_tiling"])
     ref.set_points(y)
     assert torch.equal(ref.eval(s), tuned)
     ref.close()

@@ -881,63 +881,25 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
   // the partials (R x C floats per box and neighbour) fit in a quarter of the device memory.
   bool grouped = false;
   if (P.use_tc && P.tc_tiling != 1) {
-    int64_t npart = 0;
-    for (int c = 0; c < 8; ++c)
-      for (int b : by_cls[c]) {
-        const uint64_t* o = reinterpret_cast<const uint64_t*>(oc + (size_t)b * 32);
-        for (int w = 0; w < 4; ++w) {   // nonzero bytes of each word
-          uint64_t x = o[w];
-          x |= x >> 4;
-          x |= x >> 2;
-          x |= x >> 1;
-          npart += __builtin_popcountll(x & 0x0101010101010101ull);
-        }
-      }
+    // the pairs were counted with the tree (Tree::m2l_hist); they are sorted on the device and
+    // the tiles laid out here: runs of one (class, neighbour) in key order, NB_TC pairs a tile
+    const int64_t npart = T.m2l_npairs;
     const double part_bytes = (double)npart * P.R * P.C * 4;
     grouped = part_bytes < (double)P.dev_mem / 4 && npart < INT32_MAX;
     if (grouped) {
-      // one counting sort per class over the keys (g, occupancy byte of g) of the class's
-      // (box, neighbour) pairs; the partial of (b, g) is b's running pair count
+      int rc = m2l_pairs_sort(P);
+      if (rc) return rc;
       W.m2l[0] = (int)W.tiles.size();
-      W.m2l_part.reserve((size_t)npart);
-      W.boxlist.reserve((size_t)npart + 3 * (size_t)nb);
-      std::vector<int> cnt(27 * 256 + 1), pbox, ppart;
       int run = 0;
-      for (int c = 0; c < 8; ++c) {
-        const std::vector<int>& v = by_cls[c];
-        std::fill(cnt.begin(), cnt.end(), 0);
-        for (int b : v) {
-          const uint8_t* o = oc + (size_t)b * 32;
-          for (int g = 0; g < 27; ++g)
-            if (o[g]) ++cnt[g * 256 + o[g] + 1];
-        }
-        for (int k = 1; k <= 27 * 256; ++k) cnt[k] += cnt[k - 1];
-        int gs[28];
-        for (int g = 0; g <= 27; ++g) gs[g] = cnt[g * 256];
-        pbox.resize(gs[27]);
-        ppart.resize(gs[27]);
-        for (int b : v) {
-          const uint8_t* o = oc + (size_t)b * 32;
-          const int first = run;
-          for (int g = 0; g < 27; ++g)
-            if (o[g]) {
-              int pos = cnt[g * 256 + o[g]]++;
-              pbox[pos] = b;
-              ppart[pos] = run++;
-            }
-          if (run > first) W.m2l_comb.push_back(make_int4(b, first, run - first, 0));
-        }
-        for (int g = 0; g < 27; ++g)
-          for (int i = gs[g]; i < gs[g + 1]; i += NB_TC) {
-            int k = std::min(NB_TC, gs[g + 1] - i);
-            W.tiles.push_back(make_int4((int)W.boxlist.size(), k, c, g + 1));
-            W.boxlist.insert(W.boxlist.end(), pbox.begin() + i, pbox.begin() + i + k);
-            W.m2l_part.insert(W.m2l_part.end(), ppart.begin() + i, ppart.begin() + i + k);
-          }
-        by_cls[c].clear();
+      for (int cg = 0; cg < 216; ++cg) {
+        const int cnt = (int)T.m2l_hist[cg];
+        for (int i = 0; i < cnt; i += NB_TC)
+          W.tiles.push_back(make_int4(run + i, std::min(NB_TC, cnt - i), cg / 27, cg % 27 + 1));
+        run += cnt;
       }
       W.m2l[1] = (int)W.tiles.size();
-      W.m2l_nparts = run;
+      W.m2l_nparts = npart;
+      for (int c = 0; c < 8; ++c) by_cls[c].clear();
     }
   }
   W.m2l_grouped = grouped;
@@ -997,31 +959,18 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
   W.xbox_n = (int)W.boxlist.size() - W.xbox_off;
   for (int b = 0; b < nb; ++b)
     if (leaf[b]) W.boxlist.push_back(b);
-  // upload through page-locked staging: tiles, box lists, grouped M->L partial indices and
-  // combine list
+  // upload through page-locked staging: tiles and box lists
   const size_t u_tiles = 0, u_box = u_tiles + sizeof(int4) * W.tiles.size(),
-               u_part = u_box + sizeof(int) * W.boxlist.size(),
-               u_comb = (u_part + sizeof(int) * W.m2l_part.size() + 15) / 16 * 16,
-               up_bytes = u_comb + sizeof(int4) * W.m2l_comb.size();
+               up_bytes = u_box + sizeof(int) * W.boxlist.size();
   CK(P.wl_up.reserve(up_bytes));
   HostBuf& U = P.wl_up;
   std::copy(W.tiles.begin(), W.tiles.end(), U.as<int4>(u_tiles));
   std::copy(W.boxlist.begin(), W.boxlist.end(), U.as<int>(u_box));
-  std::copy(W.m2l_part.begin(), W.m2l_part.end(), U.as<int>(u_part));
-  std::copy(W.m2l_comb.begin(), W.m2l_comb.end(), U.as<int4>(u_comb));
   CK(P.tiles.reserve(sizeof(int4) * (W.tiles.size() + 1)));
   CK(P.tile_meta.reserve(sizeof(int) * (W.boxlist.size() + 1)));
   CK(cudaMemcpyAsync(P.tiles.p, U.as<void>(u_tiles), sizeof(int4) * W.tiles.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(P.tile_meta.p, U.as<void>(u_box), sizeof(int) * W.boxlist.size(),
                      cudaMemcpyHostToDevice, st));
-  if (W.m2l_grouped) {
-    CK(P.m2l_part_idx.reserve(sizeof(int) * (W.m2l_part.size() + 1)));
-    CK(P.m2l_comb.reserve(sizeof(int4) * (W.m2l_comb.size() + 1)));
-    CK(cudaMemcpyAsync(P.m2l_part_idx.p, U.as<void>(u_part), sizeof(int) * W.m2l_part.size(),
-                       cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(P.m2l_comb.p, U.as<void>(u_comb), sizeof(int4) * W.m2l_comb.size(),
-                       cudaMemcpyHostToDevice, st));
-  }
   CK(cudaStreamSynchronize(st));   // the staging buffers are reused by the next build
   return 0;
 }
@@ -1103,8 +1052,10 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       int n = range[1] - range[0];
       if (n <= 0) return 0;
       const int4* tiles = P.tiles.as<int4>() + range[0];
+      // grouped M->L tiles index the sorted pair arrays
+      const int* bl = mode == TCM_M2L && P.wl.m2l_grouped ? P.m2l_box.as<int>() : boxlist;
       if (tc)
-        return tc_gemm_launch(P, mode, tiles, n, boxlist, reinterpret_cast<const float*>(in),
+        return tc_gemm_launch(P, mode, tiles, n, bl, reinterpret_cast<const float*>(in),
                               reinterpret_cast<float*>(out), op, write, st);
       ga.mode = mode == TCM_M2L ? GM_M2L : (mode == TCM_M2M ? GM_M2M : (mode == TCM_L2L ? GM_L2L : GM_APPLY));
       ga.in = in;

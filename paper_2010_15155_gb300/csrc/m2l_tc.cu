@@ -810,11 +810,12 @@ __global__ void k_combine_parts(const float4* __restrict__ parts, int64_t part_s
 }
 
 // Grouped M->L: dn[box] (+)= sum of the box's partials (one per parent neighbour, in
-// neighbour order).  comb = (box, first partial, count); R4 = float4 per box.
+// neighbour order).  comb = (box, first partial, count) for every box; R4 = float4 per box.
 __global__ void k_combine_groups(const float4* __restrict__ parts, const int4* __restrict__ comb,
                                  int ncomb, float4* __restrict__ dn, int R4, int add) {
   for (int i = blockIdx.x; i < ncomb; i += gridDim.x) {
     const int4 c = comb[i];
+    if (c.z == 0) continue;   // a box without V entries (or below the M->L levels)
     for (int r = threadIdx.x; r < R4; r += blockDim.x) {
       const float4* p = parts + (int64_t)c.y * R4 + r;
       float4 v = p[0];
@@ -943,7 +944,7 @@ int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* 
   a.dn = nsplit > 1 || grouped ? P.m2l_parts.as<float>() : out;
   a.part_stride = nsplit > 1 ? part_stride : 0;
   a.nsplit = nsplit;
-  a.part = grouped ? P.m2l_part_idx.as<int>() : nullptr;
+  a.part = grouped ? reinterpret_cast<const int*>(P.m2l_part_sorted) : nullptr;
   a.tiles = tiles;
   a.boxlist = boxlist;
   a.vtab = P.tree.vtab.as<int32_t>();
@@ -979,9 +980,9 @@ int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* 
   }
 #undef KAFMM_TC_LAUNCH
 #undef KAFMM_TC_LAUNCH1
-  if (grouped && !P.wl.m2l_comb.empty())
-    KL tc::k_combine_groups<<<std::min((int)P.wl.m2l_comb.size(), 152 * 8), 128, 0, st>>>(
-        P.m2l_parts.as<float4>(), P.m2l_comb.as<int4>(), (int)P.wl.m2l_comb.size(),
+  if (grouped && P.tree.nbox > 0)
+    KL tc::k_combine_groups<<<std::min(P.tree.nbox, 152 * 8), 128, 0, st>>>(
+        P.m2l_parts.as<float4>(), P.m2l_comb.as<int4>(), P.tree.nbox,
         reinterpret_cast<float4*>(out), P.R * P.C / 4, write == tc::TC_ADD ? 1 : 0);
   if (nsplit > 1)   // a box holds R * C floats = R * C / 4 float4 (R * C a multiple of 8)
     KL tc::k_combine_parts<<<std::min(ntiles, 152 * 4), 256, 0, st>>>(

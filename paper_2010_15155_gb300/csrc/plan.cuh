@@ -45,6 +45,11 @@ struct Tree {
   DevBuf u_off, u_ent, w_off, w_ent, x_off, x_ent;
   DevBuf vtab;                      // [nbox][216] source box of each V slot or LIST_EMPTY
   DevBuf vocc;                      // [nbox][32] bytes: V slot occupancy per parent neighbour
+  // grouped M->L pairs (box, parent neighbour with V entries) of boxes at levels >= vmin:
+  // count and first pair per box, per (octant class, neighbour) totals and their sum
+  DevBuf m2l_cnt, m2l_base, m2l_meta;
+  unsigned m2l_hist[217] = {0};
+  int64_t m2l_npairs = 0;
   DevBuf w_flag;                    // [nbox] 1 if the box appears in some W list
   // scratch of the build
   DevBuf s_keys2, s_vals2, s_hist, t_keys2, t_vals2;
@@ -60,13 +65,11 @@ struct WorkLists {
   std::vector<int> boxlist;
   std::vector<int4> tiles;
   int m2l[2] = {0, 0};                       // tile ranges
-  // tensor-core M->L tiled per (octant class, parent neighbour g): tile.w = g + 1, each box's
-  // result goes to its own partial (index m2l_part[boxlist position]) and the partials of a
-  // box are added in order by the combine list (box, first partial, count)
+  // tensor-core M->L tiled per (octant class, parent neighbour g): tile.w = g + 1, tile.x
+  // indexes the sorted pair arrays (Plan::m2l_box, m2l_part_sorted); each box's result goes to
+  // its own partial and the partials of a box are added in order by Plan::m2l_comb
   bool m2l_grouped = false;
   int64_t m2l_nparts = 0;
-  std::vector<int> m2l_part;
-  std::vector<int4> m2l_comb;
   int m2m[MAX_LEVELS][2] = {};
   int l2l[MAX_LEVELS][2] = {};
   int pup[2] = {0, 0}, pdn[2] = {0, 0};
@@ -116,7 +119,10 @@ struct Plan {
   HostBuf wl_down, wl_up;           // pinned staging of the work-list build (tree in, lists out)
   double host_wl_ms = 0;            // host time of the last work-list build
   DevBuf m2l_parts;                 // partial M->L sums per offset range (tensor-core path)
-  DevBuf m2l_part_idx, m2l_comb;    // grouped M->L: partial index per tile entry, combine list
+  // grouped M->L: sorted pairs (keys, partial indices, ping-pong halves), pair boxes before
+  // and after sorting, radix histograms, combine list [nbox] (box, first partial, count)
+  DevBuf m2l_keys, m2l_vals, m2l_pbox, m2l_box, m2l_hist, m2l_comb;
+  const uint32_t* m2l_part_sorted = nullptr;
   int64_t tiles_cap = 0;
   WorkLists wl;
   bool use_tc = false;              // tensor-core M->L available for this plan
@@ -144,6 +150,9 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
 
 // operators.cu
 int build_operators(Plan& P);
+
+// Sorts the grouped M->L pairs of the current tree (device; see WorkLists::m2l_grouped).
+int m2l_pairs_sort(Plan& P);
 
 // eval.cu
 int evaluate(Plan& P, const void* s_dev, void* g_dev, int dtype);

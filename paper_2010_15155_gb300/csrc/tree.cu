@@ -132,15 +132,15 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t
 // then, for a batch (nprob > 1), 1 or 2 passes over the problem index of each element's
 // caller index (stable, so each problem's points stay in Morton order).
 static void radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* k2, uint32_t* v2, uint32_t* hist,
-                       int64_t n, const int64_t* poff, int nprob, cudaStream_t st) {
+                       int64_t n, const int64_t* poff, int nprob, cudaStream_t st, int key_passes = 8) {
   if (n <= 1) return;
   int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
   uint64_t *ka = keys, *kb = k2;
   uint32_t *va = vals, *vb = v2;
-  int npass = 8 + (nprob > 1 ? (nprob > 256 ? 2 : 1) : 0);
+  int npass = key_passes + (nprob > 1 ? (nprob > 256 ? 2 : 1) : 0);
   for (int pass = 0; pass < npass; ++pass) {
-    bool by_prob = pass >= 8;
-    int shift = by_prob ? (pass - 8) * 8 : pass * 8;
+    bool by_prob = pass >= key_passes;
+    int shift = by_prob ? (pass - key_passes) * 8 : pass * 8;
     const int64_t* po = by_prob ? poff : nullptr;
     KL k_radix_hist<<<nblk, RS_THREADS, 0, st>>>(ka, va, n, shift, po, nprob, hist, nblk);
     scan_excl<uint32_t>(hist, hist, (int64_t)256 * nblk, nullptr, hist + 256 * (int64_t)nblk,
@@ -543,7 +543,32 @@ __global__ void k_leaf_of(TreeView t, int* __restrict__ leaf_of) {
 // byte g = (gx, gy, gz) in [0,3)^3 is the neighbour of the parent at offset (g - 1), bit
 // d = (dx, dy, dz) its child, i.e. slot (2gx + dx) + 6 (2gy + dy) + 36 (2gz + dz) of the 6^3
 // table.
-__global__ void k_tree_stats(TreeView t, const int32_t* vtab, unsigned long long* out, uint4* vocc) {
+// Parent neighbours of box b with V entries (bit g of the result): bytes of its occupancy
+// record that are nonzero.
+__device__ inline uint32_t vocc_neighbours(const uint4* vocc, int64_t b, uint64_t (&w)[4]) {
+  const uint4 a = vocc[2 * b], c = vocc[2 * b + 1];
+  w[0] = a.x | (uint64_t)a.y << 32;
+  w[1] = a.z | (uint64_t)a.w << 32;
+  w[2] = c.x | (uint64_t)c.y << 32;
+  w[3] = c.z | (uint64_t)c.w << 32;
+  uint32_t m = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    uint64_t x = w[k];
+    x |= x >> 4;
+    x |= x >> 2;
+    x |= x >> 1;
+    x &= 0x0101010101010101ull;   // bit 0 of each byte: byte nonzero
+    m |= (uint32_t)((x * 0x0102040810204080ull) >> 56) << (8 * k);   // gather to bits 0..7
+  }
+  return m & ((1u << 27) - 1);
+}
+
+__global__ void k_tree_stats(TreeView t, const int32_t* vtab, unsigned long long* out, uint4* vocc,
+                             int vmin, int* m2l_cnt, unsigned* m2l_hist) {
+  __shared__ unsigned hist[216];
+  for (int k = threadIdx.x; k < 216; k += blockDim.x) hist[k] = 0;
+  __syncthreads();
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x) {
     unsigned long long nv = 0;
     uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -567,7 +592,48 @@ __global__ void k_tree_stats(TreeView t, const int32_t* vtab, unsigned long long
       unsigned long long np = (unsigned long long)max(t.se[b] - t.sb[b], t.te[b] - t.tb[b]);
       atomicMax(&out[1], np);
     }
+    // grouped M->L: (box, parent neighbour) pairs of the boxes at levels >= vmin
+    uint32_t m = 0;
+    if (t.level[b] >= vmin) {
+      uint64_t wd[4];
+      m = vocc_neighbours(vocc, b, wd);
+      const int c = (int)(t.key[b] & 7);
+      for (uint32_t r = m; r; r &= r - 1) atomicAdd(&hist[c * 27 + __ffs(r) - 1], 1u);
+    }
+    m2l_cnt[b] = __popc(m);
   }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 216; k += blockDim.x)
+    if (hist[k]) atomicAdd(&m2l_hist[k], hist[k]);
+}
+
+// Grouped M->L pairs in box order: pair i = (box, neighbour g) has the sort key (octant class,
+// g, occupancy byte of g), its partial index i, and its box; comb[b] = (b, first pair, count).
+__global__ void k_m2l_pair_emit(TreeView t, const uint4* vocc, int vmin, const int* base,
+                                uint64_t* keys, uint32_t* vals, int* pbox, int4* comb) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x) {
+    int n = 0;
+    const int first = base[b];
+    if (t.level[b] >= vmin) {
+      uint64_t w[4];
+      const uint32_t m = vocc_neighbours(vocc, b, w);
+      const int c = (int)(t.key[b] & 7);
+      for (uint32_t r = m; r; r &= r - 1) {
+        const int g = __ffs(r) - 1;
+        const unsigned byte = (unsigned)(w[g >> 3] >> (8 * (g & 7))) & 255u;
+        const int pos = first + n++;
+        keys[pos] = (uint64_t)((c * 27 + g) << 8 | byte);
+        vals[pos] = (uint32_t)pos;
+        pbox[pos] = b;
+      }
+    }
+    comb[b] = make_int4(b, first, n, 0);
+  }
+}
+
+__global__ void k_m2l_pair_box(const uint32_t* vals, const int* pbox, int64_t n, int* box) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    box[i] = pbox[vals[i]];
 }
 
 __global__ void k_i8_to_i32(const int8_t* a, int n, int* b) {
@@ -854,16 +920,57 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   cudaEventRecord(P.ev[2], st);
   CK(cudaStreamSynchronize(st));
   T.near_pairs = (int64_t)pairs;
-  // V entries and the largest leaf
+  // V entries, the largest leaf, and the pairs of the grouped M->L (count per box, then their
+  // offsets by a scan; per (class, neighbour) totals for the tile layout)
   unsigned long long* stats = (unsigned long long*)(T.status.as<unsigned>() + 10);
   CK(cudaMemsetAsync(stats, 0, 16, st));
   CK(T.vocc.reserve(32 * (size_t)(nb + 1)));
-  KL k_tree_stats<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vtab.as<int32_t>(), stats, T.vocc.as<uint4>());
+  CK(T.m2l_cnt.reserve(sizeof(int) * (nb + 1)));
+  CK(T.m2l_base.reserve(sizeof(int) * (nb + 1)));
+  CK(T.m2l_meta.reserve(sizeof(int) * (216 + 1 + nb / SCAN_TILE + 64)));
+  unsigned* meta = T.m2l_meta.as<unsigned>();   // [0..216) per (class, neighbour), [216] total
+  CK(cudaMemsetAsync(meta, 0, sizeof(unsigned) * 217, st));
+  const int vmin = P.bc == KAFMM_BC_PXYZ ? 1 : 2;
+  KL k_tree_stats<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vtab.as<int32_t>(), stats, T.vocc.as<uint4>(),
+                                                   vmin, T.m2l_cnt.as<int>(), meta);
+  scan_excl<int>(T.m2l_cnt.as<int>(), T.m2l_base.as<int>(), nb, nullptr,
+                 reinterpret_cast<int*>(meta) + 217, reinterpret_cast<int*>(meta) + 216, st);
   unsigned long long hs[2];
   CK(cudaMemcpyAsync(hs, stats, 16, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(T.m2l_hist, meta, sizeof(unsigned) * 217, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   T.n_v = (int64_t)hs[0];
   T.max_leaf_pts = (int)hs[1];
+  T.m2l_npairs = (int64_t)T.m2l_hist[216];
+  return 0;
+}
+
+// Sorted pairs of the grouped M->L: P.m2l_box[i] and P.m2l_part_sorted[i] for the pairs ordered by
+// (octant class, parent neighbour, occupancy byte), boxes in box order within equal keys;
+// P.m2l_comb[b] = (b, first partial, count) for every box.
+int m2l_pairs_sort(Plan& P) {
+  Tree& T = P.tree;
+  cudaStream_t st = P.stream;
+  const int nb = T.nbox;
+  const int64_t n = T.m2l_npairs;
+  const int vmin = P.bc == KAFMM_BC_PXYZ ? 1 : 2;
+  CK(P.m2l_keys.reserve(sizeof(uint64_t) * 2 * (n + 1)));
+  CK(P.m2l_vals.reserve(sizeof(uint32_t) * 2 * (n + 1)));
+  CK(P.m2l_pbox.reserve(sizeof(int) * (n + 1)));
+  CK(P.m2l_box.reserve(sizeof(int) * (n + 1)));
+  CK(P.m2l_comb.reserve(sizeof(int4) * (nb + 1)));
+  const int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
+  CK(P.m2l_hist.reserve(sizeof(uint32_t) * (256 * (size_t)nblk + 256 * (size_t)nblk / SCAN_TILE + 64)));
+  uint64_t* k1 = P.m2l_keys.as<uint64_t>();
+  uint32_t* v1 = P.m2l_vals.as<uint32_t>();
+  TreeView tv = T.view();
+  KL k_m2l_pair_emit<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vocc.as<uint4>(), vmin, T.m2l_base.as<int>(), k1,
+                                                      v1, P.m2l_pbox.as<int>(), P.m2l_comb.as<int4>());
+  // two 8-bit passes over the 16-bit keys (stable): the sorted values are the partial indices
+  radix_sort(k1, v1, k1 + n + 1, v1 + n + 1, P.m2l_hist.as<uint32_t>(), n, nullptr, 1, st, 2);
+  KL k_m2l_pair_box<<<grid_for(n, 256), 256, 0, st>>>(v1, P.m2l_pbox.as<int>(), n, P.m2l_box.as<int>());
+  P.m2l_part_sorted = v1;
+  CK(cudaGetLastError());
   return 0;
 }
 

@@ -45,7 +45,7 @@ FLOP_ST_PAIR = 29
 # DRAM bytes (read + written) of one M->L launch of this workload in the mixed form, from the ncu
 # capture summarised in profiles/m2l_tc_stokeslet_uniform_256k_p10.md (set to None when the
 # kernel changes until it is captured again)
-M2L_DRAM_BYTES = None
+M2L_DRAM_BYTES = 878.991872e6 + 672.660736e6
 
 
 def _env_rank():

@@ -882,7 +882,7 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
   bool grouped = false;
   if (P.use_tc && P.tc_tiling != 1) {
     // the pairs were counted with the tree (Tree::m2l_hist); they are sorted on the device and
-    // the tiles laid out here: runs of one (class, neighbour) in key order, NB_TC pairs a tile
+    // the tiles laid out here: runs of one (neighbour, class) in key order, NB_TC pairs a tile
     const int64_t npart = T.m2l_npairs;
     const double part_bytes = (double)npart * P.R * P.C * 4;
     grouped = part_bytes < (double)P.dev_mem / 4 && npart < INT32_MAX;
@@ -891,10 +891,10 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
       if (rc) return rc;
       W.m2l[0] = (int)W.tiles.size();
       int run = 0;
-      for (int cg = 0; cg < 216; ++cg) {
-        const int cnt = (int)T.m2l_hist[cg];
+      for (int gc = 0; gc < 216; ++gc) {   // key order: neighbour g = gc / 8, class gc % 8
+        const int cnt = (int)T.m2l_hist[gc];
         for (int i = 0; i < cnt; i += NB_TC)
-          W.tiles.push_back(make_int4(run + i, std::min(NB_TC, cnt - i), cg / 27, cg % 27 + 1));
+          W.tiles.push_back(make_int4(run + i, std::min(NB_TC, cnt - i), gc % 8, gc / 8 + 1));
         run += cnt;
       }
       W.m2l[1] = (int)W.tiles.size();

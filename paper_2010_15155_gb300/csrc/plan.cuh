@@ -46,7 +46,7 @@ struct Tree {
   DevBuf vtab;                      // [nbox][216] source box of each V slot or LIST_EMPTY
   DevBuf vocc;                      // [nbox][32] bytes: V slot occupancy per parent neighbour
   // grouped M->L pairs (box, parent neighbour with V entries) of boxes at levels >= vmin:
-  // count and first pair per box, per (octant class, neighbour) totals and their sum
+  // count and first pair per box, per (neighbour, octant class) totals and their sum
   DevBuf m2l_cnt, m2l_base, m2l_meta;
   unsigned m2l_hist[217] = {0};
   int64_t m2l_npairs = 0;

@@ -530,8 +530,6 @@ __global__ void k_leaf_list(const int8_t* leaf, const int* leaf_pos, int nbox, i
     if (leaf[b]) leaves[leaf_pos[b]] = b;
 }
 
-// V entry count and largest leaf; per box a 64-bit signature of its V slot occupancy (boxes
-// with equal signatures are grouped into the same tensor-core tiles).
 // Leaf box of every sorted source point.
 __global__ void k_leaf_of(TreeView t, int* __restrict__ leaf_of) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x)
@@ -598,7 +596,7 @@ __global__ void k_tree_stats(TreeView t, const int32_t* vtab, unsigned long long
       uint64_t wd[4];
       m = vocc_neighbours(vocc, b, wd);
       const int c = (int)(t.key[b] & 7);
-      for (uint32_t r = m; r; r &= r - 1) atomicAdd(&hist[c * 27 + __ffs(r) - 1], 1u);
+      for (uint32_t r = m; r; r &= r - 1) atomicAdd(&hist[(__ffs(r) - 1) * 8 + c], 1u);
     }
     m2l_cnt[b] = __popc(m);
   }
@@ -607,8 +605,11 @@ __global__ void k_tree_stats(TreeView t, const int32_t* vtab, unsigned long long
     if (hist[k]) atomicAdd(&m2l_hist[k], hist[k]);
 }
 
-// Grouped M->L pairs in box order: pair i = (box, neighbour g) has the sort key (octant class,
-// g, occupancy byte of g), its partial index i, and its box; comb[b] = (b, first pair, count).
+// Grouped M->L pairs in box order: pair i = (box, neighbour g) has the sort key (g, octant
+// class, occupancy byte of g), its partial index i, and its box; comb[b] = (b, first pair,
+// count).  Neighbour-major order keeps the 27 offsets of one neighbour (over all classes) in
+// L2 while its tiles run: class-major order re-read every operator from DRAM once per class
+// (2.4 GB per M->L launch, Stokeslet N = 262144, p = 10).
 __global__ void k_m2l_pair_emit(TreeView t, const uint4* vocc, int vmin, const int* base,
                                 uint64_t* keys, uint32_t* vals, int* pbox, int4* comb) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x) {
@@ -622,7 +623,7 @@ __global__ void k_m2l_pair_emit(TreeView t, const uint4* vocc, int vmin, const i
         const int g = __ffs(r) - 1;
         const unsigned byte = (unsigned)(w[g >> 3] >> (8 * (g & 7))) & 255u;
         const int pos = first + n++;
-        keys[pos] = (uint64_t)((c * 27 + g) << 8 | byte);
+        keys[pos] = (uint64_t)((g * 8 + c) << 8 | byte);
         vals[pos] = (uint32_t)pos;
         pbox[pos] = b;
       }
@@ -928,7 +929,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   CK(T.m2l_cnt.reserve(sizeof(int) * (nb + 1)));
   CK(T.m2l_base.reserve(sizeof(int) * (nb + 1)));
   CK(T.m2l_meta.reserve(sizeof(int) * (216 + 1 + nb / SCAN_TILE + 64)));
-  unsigned* meta = T.m2l_meta.as<unsigned>();   // [0..216) per (class, neighbour), [216] total
+  unsigned* meta = T.m2l_meta.as<unsigned>();   // [0..216) per (neighbour, class), [216] total
   CK(cudaMemsetAsync(meta, 0, sizeof(unsigned) * 217, st));
   const int vmin = P.bc == KAFMM_BC_PXYZ ? 1 : 2;
   KL k_tree_stats<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vtab.as<int32_t>(), stats, T.vocc.as<uint4>(),
@@ -946,7 +947,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
 }
 
 // Sorted pairs of the grouped M->L: P.m2l_box[i] and P.m2l_part_sorted[i] for the pairs ordered by
-// (octant class, parent neighbour, occupancy byte), boxes in box order within equal keys;
+// (parent neighbour, octant class, occupancy byte), boxes in box order within equal keys;
 // P.m2l_comb[b] = (b, first partial, count) for every box.
 int m2l_pairs_sort(Plan& P) {
   Tree& T = P.tree;

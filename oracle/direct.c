@@ -100,6 +100,30 @@ void orc_stokeslet(const double* x, int64_t nt, const double* y, int64_t ns,
   }
 }
 
+/* Regularized Stokeslet, Sec. II.B (Table tab:ktab_reg): the flow of the force f spread by
+ * the blob psi(r) = 15 eps^4 / (8 pi (r^2 + eps^2)^{7/2}) around the source,
+ *   G^eps_ij = [ (r^2 + 2 eps^2) delta_ij + r_i r_j ] / (8 pi (r^2 + eps^2)^{3/2}),
+ * eps per source.  s: [f1 f2 f3 eps] (4), g: u (3).  eps = 0 gives the Stokeslet. */
+void orc_stokeslet_reg(const double* x, int64_t nt, const double* y, int64_t ns,
+                       const double* s, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double u[3] = {0, 0, 0};
+    for (int64_t b = 0; b < ns; ++b) {
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1],
+                     x[3 * a + 2] - y[3 * b + 2]};
+      double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (rr == 0.0) continue;
+      const double* f = s + 4 * b;
+      double ee = f[3] * f[3];
+      double d = rr + ee, d3 = d * sqrt(d);
+      double rf = r[0] * f[0] + r[1] * f[1] + r[2] * f[2];
+      for (int i = 0; i < 3; ++i) u[i] += ((rr + 2.0 * ee) * f[i] + r[i] * rf) / (8.0 * PI * d3);
+    }
+    for (int i = 0; i < 3; ++i) g[3 * a + i] += u[i];
+  }
+}
+
 /* RPY flow field and its Laplacian, Eqs. RPYflow/RPYkernel and Table tab:ktab_rpy:
  *   u = G f + (b^2/6) lap(G) f,   lap(u) = lap(G) f   (lap lap G = 0),
  *   lap(G)_ij = (delta_ij / r^3 - 3 r_i r_j / r^5) / (4 pi).

@@ -54,6 +54,9 @@ PROBLEMS = {
     "stokeslet_l4": (3, 3, "laplace", 4),
     "rpy_g": (4, 6, "stokeslet", 1),
     "rpy_l4": (4, 6, "laplace", 4),
+    # regularized Stokeslet [f, eps] -> u, Table tab:ktab_reg: G^eps from S (to M, L and T),
+    # the singular Stokeslet G between equivalent surfaces and from them to T
+    "stokeslet_reg_g": (4, 3, "stokeslet", 1),
 }
 
 
@@ -136,8 +139,8 @@ class KAFMM:
         pr = self.problem
         if pr == "laplace":
             return D.direct("laplace", chk, y, s)
-        if pr in ("stokeslet_g", "rpy_g"):
-            kern = "stokeslet" if pr == "stokeslet_g" else "rpy"
+        if pr in ("stokeslet_g", "rpy_g", "stokeslet_reg_g"):
+            kern = {"stokeslet_g": "stokeslet", "rpy_g": "rpy", "stokeslet_reg_g": "stokeslet_reg"}[pr]
             g = D.direct(kern, chk, y, s)
             return g[:, :3].reshape(-1, 1)
         f = s[:, :3]
@@ -155,7 +158,7 @@ class KAFMM:
         pr = self.problem
         if pr == "laplace":
             return D.direct("laplace", x, eq, dens[:, 0])
-        if pr == "stokeslet_g":
+        if pr in ("stokeslet_g", "stokeslet_reg_g"):
             return D.direct("stokeslet", x, eq, dens.reshape(-1, 3))
         if pr == "rpy_g":
             fb = np.concatenate([dens.reshape(-1, 3), np.zeros((len(eq), 1))], axis=1)
@@ -176,7 +179,7 @@ class KAFMM:
 
     def _src_to_targets(self, x, y, s) -> np.ndarray:
         kern = {"laplace": "laplace", "stokeslet_g": "stokeslet", "stokeslet_l4": "stokeslet",
-                "rpy_g": "rpy", "rpy_l4": "rpy"}[self.problem]
+                "rpy_g": "rpy", "rpy_l4": "rpy", "stokeslet_reg_g": "stokeslet_reg"}[self.problem]
         return D.direct(kern, x, y, s)
 
     def _shift(self, dens, c_from, c_to) -> np.ndarray:

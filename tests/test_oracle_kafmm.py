@@ -69,8 +69,7 @@ def test_kafmm_without_far_field_is_the_direct_sum(problem):
     s = rng.standard_normal((50, ks))
     if ks == 4:
         s[:, 3] = rng.uniform(0.001, 0.01, 50)
-    kern = {"laplace": "laplace", "stokeslet_g": "stokeslet", "stokeslet_l4": "stokeslet",
-            "rpy_g": "rpy", "rpy_l4": "rpy"}[problem]
+    kern = KERNEL_OF[problem]
     g = KAFMM(problem, 4, q=64).evaluate(pts, s)
     assert D.rel_l2(g, D.direct(kern, pts, pts, s)) < 1e-14
 
@@ -94,6 +93,10 @@ def test_l4_aggregation_reproduces_stokeslet_exactly():
     assert np.allclose(F._shift(q0, c0, c1), q1, rtol=1e-13, atol=1e-14)
 
 
+KERNEL_OF = {"laplace": "laplace", "stokeslet_g": "stokeslet", "stokeslet_l4": "stokeslet",
+             "rpy_g": "rpy", "rpy_l4": "rpy", "stokeslet_reg_g": "stokeslet_reg"}
+
+
 def _inputs(problem, n, seed=0):
     rng = np.random.default_rng(seed)
     pts = rng.random((n, 3))
@@ -110,12 +113,12 @@ def _inputs(problem, n, seed=0):
     ("stokeslet_g", 1200, 40, (4, 6), 1e-3),
     ("rpy_l4", 2000, 40, (4, 6, 8), 1e-5),
     ("rpy_g", 1200, 40, (4, 6), 1e-3),
+    ("stokeslet_reg_g", 1200, 40, (4, 6), 1e-3),
 ])
 def test_kafmm_converges_to_direct_sum(problem, n, q, orders, bound):
     """eps_L2 against the direct sum falls exponentially with the order m (Sec. III)."""
     pts, s = _inputs(problem, n)
-    kern = {"laplace": "laplace", "stokeslet_g": "stokeslet", "stokeslet_l4": "stokeslet",
-            "rpy_g": "rpy", "rpy_l4": "rpy"}[problem]
+    kern = KERNEL_OF[problem]
     ref = D.direct(kern, pts, pts, s)
     errs = []
     for m in orders:

@@ -265,3 +265,74 @@ def test_two_point_roundoff_under_translation():
         u1 = D.direct("stokeslet", x + t, y + t, f)
         errs.append(D.rel_l2(u1, u0))
     assert 1e-15 < np.median(errs) < 1e-10
+
+
+def _blob(rr, eps):
+    """Spreading function of the regularized Stokeslet (Sec. II.B), integral 1."""
+    return 15 * eps ** 4 / (8 * PI * (rr + eps * eps) ** 3.5)
+
+
+def test_regularized_stokeslet_limits_and_divergence():
+    """eps = 0 gives the Stokeslet; the regularized flow is divergence-free (it is the Stokes
+    flow of a spread force); far from the blob G^eps = G + (eps^2/4) lap G + O(eps^4 / r^5):
+    with b^2 / 6 = eps^2 / 4 the oracle's RPY field is G + (eps^2/4) lap G, and the
+    remainder drops 16-fold when eps halves."""
+    rng = np.random.default_rng(31)
+    y = rng.random((4, 3))
+    f = rng.standard_normal((4, 3))
+    x = rng.random((5, 3)) + 1.0
+    s0 = np.concatenate([f, np.zeros((4, 1))], axis=1)
+    assert np.allclose(D.direct("stokeslet_reg", x, y, s0), D.direct("stokeslet", x, y, f),
+                       rtol=1e-13, atol=0)
+    eps = np.array([0.3, 0.5, 0.2, 0.7])
+    s = np.concatenate([f, eps[:, None]], axis=1)
+    xt = np.array([0.6, 0.4, 0.7])   # within a blob width of the sources
+    J = fd_grad(lambda z: D.direct("stokeslet_reg", z[None], y, s)[0], xt, h=1e-5)
+    assert abs(np.trace(J)) < 1e-8 * np.abs(J).max()
+    one = np.array([[0.0, 0.0, 0.0]])
+    xr = np.array([[0.6, -0.5, 0.62]])   # |r| = 1
+    res = []
+    for e in (0.02, 0.01):
+        ureg = D.direct("stokeslet_reg", xr, one, np.array([[0.3, -1.1, 0.7, e]]))
+        urpy = D.direct("rpy", xr, one, np.array([[0.3, -1.1, 0.7, np.sqrt(1.5) * e]]))[:, :3]
+        res.append(np.abs(ureg - urpy).max())
+    assert 15.5 < res[0] / res[1] < 16.5, res
+
+
+@pytest.mark.parametrize("eps,xt", [(0.5, (0.5, 0.4, -0.3)), (0.2, (0.1, -0.25, 0.12))])
+def test_regularized_stokeslet_is_the_flow_of_the_blob_force(eps, xt):
+    """u(x) = int G(x - y) psi_eps(y) dy f (Sec. II.B: the force f spread by the blob psi_eps
+    around the source), by quadrature in spherical coordinates about the target: with z =
+    x - y = rho n, G(z) dz = (I + n n^T) rho / (8 pi) drho dOmega, a smooth integrand.
+    Panels of Gauss-Legendre in rho (tail rho > 6 mapped to (0, 1]), Gauss-Legendre in the
+    cosine of the angle to x and trapezoid in the azimuth."""
+    x = np.array(xt)
+    f = np.array([0.4, -0.9, 1.3])
+    ez = x / np.linalg.norm(x)
+    ex = np.cross(ez, [0.3, 0.5, 0.8])
+    ex /= np.linalg.norm(ex)
+    ey = np.cross(ez, ex)
+    ct, wt = np.polynomial.legendre.leggauss(96)
+    phi = np.arange(64) * 2 * PI / 64
+    st = np.sqrt(1 - ct ** 2)
+    n = (ct[:, None, None] * ez + (st[:, None] * np.cos(phi))[:, :, None] * ex
+         + (st[:, None] * np.sin(phi))[:, :, None] * ey).reshape(-1, 3)
+    wang = np.outer(wt, np.full(64, 2 * PI / 64)).reshape(-1)
+    gl, gw = np.polynomial.legendre.leggauss(24)
+    edges = np.concatenate([np.linspace(0, 2, 21), [3, 4, 6]])
+    rho, wr = [], []
+    for a, b in zip(edges[:-1], edges[1:]):
+        rho.append(0.5 * (b - a) * gl + 0.5 * (a + b))
+        wr.append(0.5 * (b - a) * gw)
+    t = 0.5 * gl + 0.5                                # rho = 6 / t on (0, 1]
+    rho.append(6 / t)
+    wr.append(0.5 * gw * 6 / t ** 2)
+    rho, wr = np.concatenate(rho), np.concatenate(wr)
+    u = np.zeros(3)
+    for rk, wk in zip(rho, wr):
+        y = x - rk * n                                  # source points of this shell
+        psi = _blob(np.sum(y * y, axis=1), eps)
+        nf = n @ f
+        u += wk * rk / (8 * PI) * ((wang * psi) @ (f[None, :] + n * nf[:, None]))
+    ref = D.direct("stokeslet_reg", x[None], np.zeros((1, 3)), np.concatenate([f, [eps]])[None])[0]
+    assert np.allclose(u, ref, rtol=1e-8, atol=1e-10), (u, ref)

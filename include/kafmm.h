@@ -44,12 +44,22 @@ typedef struct kafmm_plan_s* kafmm_plan_t;
  *                    (Eqs. RPYflow, RPYkernel; source radius b per point; Table tab:ktab_rpy)
  *   KAFMM_STOKES_DL  D -> [p, u],            Eqs. stkdlp, stkdlvel, D_jk at 3j+k k_s=9, k_t=4
  *                    (Sec. II.C).  Only the near field (U list) is evaluated for this kernel:
- *                    kafmm_eval requires KAFMM_OPT_NEAR_ONLY = 1, otherwise KAFMM_ERR_ARG. */
+ *                    kafmm_eval requires KAFMM_OPT_NEAR_ONLY = 1, otherwise KAFMM_ERR_ARG.
+ *   KAFMM_STOKES_REG [f, eps] -> u,          regularized Stokeslet               k_s=4, k_t=3
+ *                    (Sec. II.B, Table tab:ktab_reg): the flow of f spread by the blob
+ *                    15 eps^4 / (8 pi (r^2 + eps^2)^{7/2}),
+ *                    8 pi G^eps = [(r^2 + 2 eps^2) I + r r^T] / (r^2 + eps^2)^{3/2}, eps per
+ *                    source.  G^eps from the sources (S->M, S->L, S->T), the singular
+ *                    Stokeslet elsewhere, always on the G table (KAFMM_OPT_ML_VARIANT is
+ *                    ignored).  eps must be far below the smallest leaf box (Sec. II.B).
+ *                    Pairs at r = 0 are skipped as for the other kernels; a caller wanting a
+ *                    blob's own velocity adds G^eps(0) f = f / (4 pi eps). */
 typedef enum {
   KAFMM_LAPLACE = 0,
   KAFMM_STOKESLET = 1,
   KAFMM_RPY = 2,
-  KAFMM_STOKES_DL = 3
+  KAFMM_STOKES_DL = 3,
+  KAFMM_STOKES_REG = 4
 } kafmm_kernel;
 
 /* Boundary conditions (Sec. III.B).  KAFMM_BC_PXYZ: triply periodic in the cube

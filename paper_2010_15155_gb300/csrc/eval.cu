@@ -38,7 +38,8 @@ template <class Tin, class T, int PR>
 __global__ void k_prep_src(const Tin* __restrict__ s, const uint32_t* __restrict__ perm, int64_t n,
                            typename V4<T>::type* __restrict__ out) {
   using T4 = typename V4<T>::type;
-  constexpr int KS = PR == P_LAP ? 1 : (PR == P_DL ? 9 : ((PR == P_RPY_L4 || PR == P_RPY_G) ? 4 : 3));
+  constexpr int KS =
+      PR == P_LAP ? 1 : (PR == P_DL ? 9 : ((PR == P_RPY_L4 || PR == P_RPY_G || PR == P_REG_G) ? 4 : 3));
   constexpr int NV = ProbInfo<PR>::NV;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -152,6 +153,8 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
               acc[3] += q4 * ir;
             } else if (PR == P_STK_G) {
               stk_st<T>(r0, r1, r2, v.x, v.y, v.z, acc);
+            } else if (PR == P_REG_G) {   // S->M, S->L: the regularized kernel (Table tab:ktab_reg)
+              reg_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, acc);
             } else if (PR == P_RPY_G) {
               T tmp[6] = {0, 0, 0, 0, 0, 0};
               rpy_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
       }
     }
     if (i < a.n) {
-      T sc = (PR == P_STK_G || PR == P_RPY_G) ? T(1.0 / (8.0 * PI)) : T(1.0 / (4.0 * PI));
+      T sc = (PR == P_STK_G || PR == P_RPY_G || PR == P_REG_G) ? T(1.0 / (8.0 * PI)) : T(1.0 / (4.0 * PI));
       T* out = a.check + (int64_t)b * a.R * C;
 #pragma unroll
       for (int d = 0; d < D; ++d)
@@ -512,7 +515,7 @@ __device__ inline void far_eval(T xl, T yl, T zl, const typename V4<T>::type& p,
       acc[4] += (q.y - r1 * c3) * ir3;
       acc[5] += (q.z - r2 * c3) * ir3;
     }
-  } else if (PR == P_STK_G) {
+  } else if (PR == P_STK_G || PR == P_REG_G) {   // M->T, L->T: the singular Stokeslet
     stk_st<T>(r0, r1, r2, q.x, q.y, q.z, acc);
   } else if (PR == P_RPY_G) {
     rpy_st<T>(r0, r1, r2, q.x, q.y, q.z, T(0), acc);
@@ -710,6 +713,8 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
               lap_st<T>(r0, r1, r2, v.x, tmp);
             } else if (PR == P_STK_L4 || PR == P_STK_G) {
               stk_st<T>(r0, r1, r2, v.x, v.y, v.z, tmp);
+            } else if (PR == P_REG_G) {   // S->T: the regularized kernel of the source's eps
+              reg_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
             } else if (PR == P_RPY_L4 || PR == P_RPY_G) {
               // contact pairs are left to the sphere-velocity pass, which adds their whole
               // mobility (their far form is large and cancels there, beyond FP32 precision)
@@ -1170,6 +1175,8 @@ int evaluate(Plan& P, const void* s, void* g, int dtype) {
     pr = P.C == 4 ? P_STK_L4 : P_STK_G;
   else if (P.kernel == KAFMM_RPY)
     pr = P.C == 4 ? P_RPY_L4 : P_RPY_G;
+  else if (P.kernel == KAFMM_STOKES_REG)
+    pr = P_REG_G;
   else
     pr = P_DL;
   (void)dtype;
@@ -1181,6 +1188,7 @@ int evaluate(Plan& P, const void* s, void* g, int dtype) {
     case P_STK_G: return run_eval<T, P_STK_G>(P, s, sd, g);  \
     case P_RPY_L4: return run_eval<T, P_RPY_L4>(P, s, sd, g); \
     case P_RPY_G: return run_eval<T, P_RPY_G>(P, s, sd, g);  \
+    case P_REG_G: return run_eval<T, P_REG_G>(P, s, sd, g);  \
     default: return run_eval<T, P_DL>(P, s, sd, g);          \
   }
   if (P.fp64()) {

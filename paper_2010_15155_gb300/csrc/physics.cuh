@@ -6,7 +6,7 @@
 namespace kafmm {
 
 // Problem = kernel + ML-tree table.
-enum Prob { P_LAP = 0, P_STK_L4 = 1, P_STK_G = 2, P_RPY_L4 = 3, P_RPY_G = 4, P_DL = 5 };
+enum Prob { P_LAP = 0, P_STK_L4 = 1, P_STK_G = 2, P_RPY_L4 = 3, P_RPY_G = 4, P_DL = 5, P_REG_G = 6 };
 
 template <int PR>
 struct ProbInfo;
@@ -22,6 +22,8 @@ template <>
 struct ProbInfo<P_RPY_G> { static constexpr int KT = 6, C = 1, D = 3, NV = 1; };
 template <>
 struct ProbInfo<P_DL> { static constexpr int KT = 4, C = 1, D = 1, NV = 3; };
+template <>
+struct ProbInfo<P_REG_G> { static constexpr int KT = 3, C = 1, D = 3, NV = 1; };
 
 template <class T>
 struct V4;
@@ -100,6 +102,22 @@ __device__ inline void stk_st(T r0, T r1, T r2, T f0, T f1, T f2, T* acc) {
   acc[2] += f2 * ir + r2 * rf;
 }
 
+// Regularized Stokeslet (Sec. II.B, force f spread over the blob of width eps):
+//   8 pi u = [(r^2 + 2 eps^2) f + r (r.f)] / (r^2 + eps^2)^{3/2}; the pair at r = 0 is skipped.
+template <class T>
+__device__ inline void reg_st(T r0, T r1, T r2, T f0, T f1, T f2, T eps, T* acc) {
+  T rr = r0 * r0 + r1 * r1 + r2 * r2;
+  if (rr == T(0)) return;
+  T ee = eps * eps;
+  T id = rsqrt_<T>(rr + ee);
+  T id3 = id * id * id;
+  T h1 = (rr + T(2) * ee) * id3;
+  T rf = (r0 * f0 + r1 * f1 + r2 * f2) * id3;
+  acc[0] += h1 * f0 + r0 * rf;
+  acc[1] += h1 * f1 + r1 * rf;
+  acc[2] += h1 * f2 + r2 * rf;
+}
+
 // RPY: u = G f + b^2/6 lap G f, lap u = lap G f with lap G = (I/r^3 - 3 r r^T / r^5)/(4 pi).
 // acc[0..2] scaled by 1/(8 pi), acc[3..5] by 1/(4 pi) at the end:
 //   8 pi u   = f/r + r (r.f)/r^3 + b^2/3 (f/r^3 - 3 r (r.f)/r^5)
@@ -142,7 +160,7 @@ template <int PR, class T>
 __device__ inline T out_scale(int k) {
   const T f4 = T(1.0 / (4.0 * PI)), f8 = T(1.0 / (8.0 * PI));
   if (PR == P_LAP) return f4;
-  if (PR == P_STK_L4 || PR == P_STK_G) return f8;
+  if (PR == P_STK_L4 || PR == P_STK_G || PR == P_REG_G) return f8;
   if (PR == P_RPY_L4 || PR == P_RPY_G) return k < 3 ? f8 : f4;
   return k == 0 ? f4 : f8;  // DL
 }

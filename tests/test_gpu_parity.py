@@ -18,7 +18,8 @@ from oracle.kafmm import KAFMM  # noqa: E402
 from oracle.tree import Tree  # noqa: E402
 from paper_2010_15155_gb300 import kafmm as K  # noqa: E402
 
-KERN = {"laplace": K.LAPLACE, "stokeslet": K.STOKESLET, "rpy": K.RPY, "stokes_dl": K.STOKES_DL}
+KERN = {"laplace": K.LAPLACE, "stokeslet": K.STOKESLET, "rpy": K.RPY, "stokes_dl": K.STOKES_DL,
+        "stokeslet_reg": K.STOKES_REG}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -81,7 +82,7 @@ def _inputs(kernel, n, seed, dtype=np.float64):
     pts = rng.random((n, 3))
     ks = K.KDIM[KERN[kernel]][0]
     s = rng.standard_normal((n, ks))
-    if kernel == "rpy":
+    if kernel in ("rpy", "stokeslet_reg"):   # radius b / blob width eps per source
         s[:, 3] = rng.uniform(0.0, 2e-3, n)
     return pts.astype(dtype), s.astype(dtype)
 
@@ -98,7 +99,7 @@ def _near_oracle(kernel, pts, s, q):
     return g
 
 
-@pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "rpy", "stokes_dl"])
+@pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "rpy", "stokes_dl", "stokeslet_reg"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_near_field_matches_oracle(kernel, prec):
     n, q = 3000, 50
@@ -120,6 +121,7 @@ def test_near_field_matches_oracle(kernel, prec):
     ("stokeslet_g", "stokeslet", K.ML_G, 1500, 4, 32),
     ("rpy_l4", "rpy", K.ML_L4, 2500, 6, 40),
     ("rpy_g", "rpy", K.ML_G, 1500, 4, 32),
+    ("stokeslet_reg_g", "stokeslet_reg", K.ML_G, 1500, 4, 32),
 ])
 def test_fp64_gpu_kafmm_matches_cpu_kafmm(problem, kernel, variant, n, p, q):
     if problem == "laplace":
@@ -260,6 +262,32 @@ def test_m2l_tilings_agree(workload):
     assert D.rel_l2(out[1], ref) < 1e-5 and D.rel_l2(out[2], ref) < 1e-5
 
 
+@pytest.mark.parametrize("p", [8, 10])
+def test_regularized_stokeslet_mixed_form(p):
+    """Regularized Stokeslet, blob widths eps ~ U(0, 1e-4) per source as in the paper's
+    benchmark (Sec. III.A), 60000 uniform points: the mixed form (G table on the tensor cores)
+    within 1e-5 of the plain FP64 GPU form, and both forms within their FMM error of the FP64
+    direct sum on sampled targets."""
+    rng = np.random.default_rng(44)
+    n = 60000
+    pts = np.minimum(rng.random((n, 3)), 1.0 - 2.0 ** -24)
+    s = np.concatenate([rng.standard_normal((n, 3)), rng.uniform(0.0, 1e-4, (n, 1))], axis=1)
+    idx = W.sample_targets(n, 1024)
+    ref = D.direct("stokeslet_reg", pts[idx], pts, s)
+    out = {}
+    for prec in (K.PREC_FP64, K.PREC_MIXED):
+        dt = torch.float64 if prec == K.PREC_FP64 else torch.float32
+        plan = K.Plan(K.STOKES_REG, p=p, q=64, precision=prec)
+        plan.set_points(torch.from_numpy(pts).to(dt).cuda())
+        out[prec] = plan.eval(torch.from_numpy(s).to(dt).cuda()).double().cpu().numpy()
+        if prec == K.PREC_MIXED:
+            assert K.kafmm_get_counters(plan.h)["tensor_core_m2l"] == 1
+        plan.close()
+    assert D.rel_l2(out[K.PREC_MIXED], out[K.PREC_FP64]) < 1e-5
+    assert D.rel_l2(out[K.PREC_FP64][idx], ref) < (1e-5 if p == 8 else 1e-6)
+    assert D.rel_l2(out[K.PREC_MIXED][idx], ref) < 2e-5
+
+
 @pytest.mark.parametrize("prec,tol", [(K.PREC_FP64, 1e-6), (K.PREC_FP32, 2e-5)])
 def test_rpy_sphere_velocities_with_overlap_match_brute_force(prec, tol):
     """kafmm_eval ([u, lap u]) + kafmm_rpy_velocity (assembly u + a^2/6 lap u and the overlap
@@ -287,21 +315,28 @@ def test_rpy_sphere_velocities_with_overlap_match_brute_force(prec, tol):
 
 
 def _neutral(kernel, n, seed, dtype=np.float64):
+    """Zero net source (periodic sums): charges or forces minus their mean; the regularized
+    Stokeslet's blob widths eps ~ U(0, 2e-3) in the fourth column."""
     rng = np.random.default_rng(seed)
     pts = rng.random((n, 3))
     kt = 1 if kernel == "laplace" else 3
     s = rng.standard_normal((n, kt))
-    return pts.astype(dtype), (s - s.mean(axis=0)).astype(dtype)
+    s = s - s.mean(axis=0)
+    if kernel == "stokeslet_reg":
+        s = np.concatenate([s, rng.uniform(0.0, 2e-3, (n, 1))], axis=1)
+    return pts.astype(dtype), s.astype(dtype)
 
 
-@pytest.mark.parametrize("problem,kernel", [("laplace", "laplace"), ("stokeslet_g", "stokeslet")])
+@pytest.mark.parametrize("problem,kernel", [("laplace", "laplace"), ("stokeslet_g", "stokeslet"),
+                                            ("stokeslet_reg_g", "stokeslet_reg")])
 def test_periodic_fp64_gpu_kafmm_matches_cpu_kafmm(problem, kernel):
     """Triply periodic KAFMM (far images through the root operator) vs the oracle's periodic
     plain KAFMM, FP64 both: rel L2 <= 1e-7."""
     from oracle import periodic as Pd
     pts, s = _neutral(kernel, 1500, seed=21)
     p, q = 6, 32
-    ref = KAFMM(problem, p, q, bc="pxyz", t_m2l=Pd.t_m2l(kernel, p)).evaluate(pts, s)
+    ml = "laplace" if kernel == "laplace" else "stokeslet"   # the ML-tree kernel of the table
+    ref = KAFMM(problem, p, q, bc="pxyz", t_m2l=Pd.t_m2l(ml, p)).evaluate(pts, s)
     plan = K.Plan(KERN[kernel], p=p, q=q, bc=K.BC_PXYZ, precision=K.PREC_FP64, variant=K.ML_G)
     plan.set_points(torch.from_numpy(pts).cuda())
     g = plan.eval(torch.from_numpy(s).cuda()).cpu().numpy()

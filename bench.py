@@ -18,6 +18,8 @@ e2e    = the same through the C ABI with pinned HOST buffers (copies inside the 
 --workload periodic: triply periodic Stokeslet, 2^22 uniform points, p = 12, q = 128, G table.
 --workload rpy: RPY sphere velocities, 2^20 clustered points, p = 8, q = 128 (set_points +
          eval + rpy_velocity per step).
+--workload convergence: the paper's convergence benchmark (10^6 log-normal points, L = 32,
+         q = 2000, m = 6..16 relative to m = 16, FP64), Laplace and Stokeslet.
 """
 from __future__ import annotations
 
@@ -669,6 +671,58 @@ def run_gpu_rpy(args):
     return 0
 
 
+def run_convergence(args):
+    """The paper's convergence benchmark (Sec. III.A): 10^6 points with log-normal coordinates
+    (Eq. ptdist, m = -1, s = 0.5) in [0, 32)^3, source values U(-1, 1), leaves of at most 2000
+    points, orders m = 6..16, eps_L2 of every target value relative to m = 16; plain FP64
+    form.  Laplace and Stokeslet (four-channel table).  The m = 16 result is also checked
+    against the oracle's direct FP64 sum on 256 sampled targets."""
+    import torch
+
+    from oracle import direct as D
+    from paper_2010_15155_gb300 import kafmm as K
+
+    rank, world, local = _env_rank()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    n, L, q = 1000000, 32.0, 2000
+    orders = (6, 8, 10, 12, 14, 16)
+    pts = workloads.lognormal_points(n, seed=5) * L
+    rng = np.random.default_rng(6)
+    y = torch.from_numpy(pts).cuda()
+    idx = workloads.sample_targets(n, 256)
+    out = {"metric": "eps_L2 relative to m = 16 (Sec. III.A)", "impl": "gb300",
+           "data": "synthetic", "dtype": "f64",
+           "config": {"workload": "lognormal_1m_L32_q2000", "n_points": n, "L": L, "q": q,
+                      "orders": list(orders), "precision": "fp64"}, "kernels": {}}
+    for name, kern, ks in (("laplace", K.LAPLACE, 1), ("stokeslet", K.STOKESLET, 3)):
+        sv = rng.uniform(-1.0, 1.0, (n, ks))
+        s = torch.from_numpy(sv).cuda()
+        g, ms, info = {}, {}, None
+        for m in orders:
+            plan = K.Plan(kern, p=m, q=q, precision=K.PREC_FP64, variant=K.ML_L4,
+                          origin=(0.0, 0.0, 0.0), L=L)
+            plan.set_points(y)
+            g[m] = plan.eval(s).cpu().numpy()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.set_points(y)
+            plan.eval(s)
+            e1.record()
+            e1.synchronize()
+            ms[m] = e0.elapsed_time(e1)
+            info = plan.info()
+            plan.close()
+        ref = D.direct(name, pts[idx], pts, sv)
+        out["kernels"][name] = {
+            "eps_l2_vs_m16": {m: D.rel_l2(g[m], g[16]) for m in orders[:-1]},
+            "m16_vs_direct_256_sampled": D.rel_l2(g[16][idx], ref),
+            "ms_per_step": ms, "tree": {k: info[k] for k in ("nbox", "nleaf", "nlevels", "n_v")}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def eval_graph_timing(plan, s, g, stream, flush, steps):
     """kafmm_eval alone for the current points, captured once in a CUDA graph (the plan in
     asynchronous mode) and replayed; per replay CUDA-event time with L2 flushed in between."""
@@ -720,7 +774,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
     ap.add_argument("--tc-split", default="auto", choices=["auto", "tf32x3", "bf16x3"])
     ap.add_argument("--workload", default="stokeslet",
-                    choices=["stokeslet", "batched", "periodic", "rpy"])
+                    choices=["stokeslet", "batched", "periodic", "rpy", "convergence"])
     ap.add_argument("--tc-tiling", type=int, default=0, choices=[0, 1, 2],
                     help="M->L tiling: 0 automatic, 1 whole V lists, 2 per parent neighbour")
     ap.add_argument("--skip-check", action="store_true")
@@ -734,6 +788,8 @@ def main():
         return run_gpu_periodic(args)
     if args.workload == "rpy":
         return run_gpu_rpy(args)
+    if args.workload == "convergence":
+        return run_convergence(args)
     return run_gpu(args)
 
 

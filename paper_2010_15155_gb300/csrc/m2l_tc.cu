@@ -429,234 +429,234 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else if (warp >= 4 && warp < W_TMA) {
-   if constexpr (CH == 1) {
-    // ---------------- B producers, single-column tables: gather, split, swizzle ----------------
-    // Row n of B = target box n of the tile: the BK k-values of this chunk of its source box,
-    // contiguous in memory.  LPR lanes share a row, each loading 8 consecutive k (32 bytes)
-    // and writing its 16-byte chunk(s) of the swizzled row (one per 8 bf16, two per 8 tf32);
-    // a warp instruction covers BPI boxes, so the loads are contiguous runs and each
-    // shared-memory phase of 8 lanes fills whole 128-byte rows (conflict-free).
-    static_assert(SWB == 128, "single-column tables use 128-byte rows");
-    constexpr int LPR = BK / 8;                      // lanes per row
-    constexpr int BPI = 32 / LPR;                    // boxes per warp instruction (4 or 8)
-    constexpr int UPW = NB / PROD_WARPS;             // boxes per producer warp per stage
-    constexpr int LPS = UPW / BPI;                   // boxes per lane per stage
-    constexpr int UH = LPS / 2;                      // boxes per lane per half stage
-    static_assert(UH >= 1 && LPS == 2 * UH, "two half stages");
-    const int pw = warp - 4;
-    const int bsel = lane / LPR, wd = lane % LPR;
-    auto box_of = [&](int ul) { return pw * UPW + ul * BPI + bsel; };
-    int srcb[LPS];
-    int cur_slot = -1;
-    auto load_half = [&](int it, int h, float4 (&q)[UH][2]) {
-      int s = slot_list[it / nchunk], c = it % nchunk;
-      if (s != cur_slot) {
+    if constexpr (CH == 1) {
+      // ---------------- B producers, single-column tables: gather, split, swizzle ----------------
+      // Row n of B = target box n of the tile: the BK k-values of this chunk of its source box,
+      // contiguous in memory.  LPR lanes share a row, each loading 8 consecutive k (32 bytes)
+      // and writing its 16-byte chunk(s) of the swizzled row (one per 8 bf16, two per 8 tf32);
+      // a warp instruction covers BPI boxes, so the loads are contiguous runs and each
+      // shared-memory phase of 8 lanes fills whole 128-byte rows (conflict-free).
+      static_assert(SWB == 128, "single-column tables use 128-byte rows");
+      constexpr int LPR = BK / 8;                      // lanes per row
+      constexpr int BPI = 32 / LPR;                    // boxes per warp instruction (4 or 8)
+      constexpr int UPW = NB / PROD_WARPS;             // boxes per producer warp per stage
+      constexpr int LPS = UPW / BPI;                   // boxes per lane per stage
+      constexpr int UH = LPS / 2;                      // boxes per lane per half stage
+      static_assert(UH >= 1 && LPS == 2 * UH, "two half stages");
+      const int pw = warp - 4;
+      const int bsel = lane / LPR, wd = lane % LPR;
+      auto box_of = [&](int ul) { return pw * UPW + ul * BPI + bsel; };
+      int srcb[LPS];
+      int cur_slot = -1;
+      auto load_half = [&](int it, int h, float4 (&q)[UH][2]) {
+        int s = slot_list[it / nchunk], c = it % nchunk;
+        if (s != cur_slot) {
 #pragma unroll
-        for (int ul = 0; ul < LPS; ++ul) srcb[ul] = slot_src(a, sbox[box_of(ul)], s);
-        cur_slot = s;
-      }
-      const int k0 = c * BK + wd * 8;
-      const bool kin = k0 < R;   // R a multiple of 8: a lane's 8 k are all in or all out
-#pragma unroll
-      for (int u = 0; u < UH; ++u) {
-        int sb = srcb[h * UH + u];
-        if (sb >= 0 && kin) {
-          ld_nc_v8(reinterpret_cast<const float4*>(a.up + (int64_t)sb * R + k0), q[u][0], q[u][1]);
-        } else {
-          q[u][0] = make_float4(0.f, 0.f, 0.f, 0.f);
-          q[u][1] = q[u][0];
+          for (int ul = 0; ul < LPS; ++ul) srcb[ul] = slot_src(a, sbox[box_of(ul)], s);
+          cur_slot = s;
         }
-      }
-    };
-    auto store_half = [&](int it, int h, const float4 (&q)[UH][2]) {
-      const int st = it % STAGES;
-      const uint32_t bhi = smem_u32(smem + st * STAGE_BYTES + A_STAGE);
-      const uint32_t blo = bhi + B_BYTES;
+        const int k0 = c * BK + wd * 8;
+        const bool kin = k0 < R;   // R a multiple of 8: a lane's 8 k are all in or all out
 #pragma unroll
-      for (int u = 0; u < UH; ++u) {
-        const int n = box_of(h * UH + u);
-        const uint32_t row = (uint32_t)(n * SWB);
-        const float v[8] = {q[u][0].x, q[u][0].y, q[u][0].z, q[u][0].w,
-                            q[u][1].x, q[u][1].y, q[u][1].z, q[u][1].w};
-        if (SPLIT == SPLIT_TF32) {
+        for (int u = 0; u < UH; ++u) {
+          int sb = srcb[h * UH + u];
+          if (sb >= 0 && kin) {
+            ld_nc_v8(reinterpret_cast<const float4*>(a.up + (int64_t)sb * R + k0), q[u][0], q[u][1]);
+          } else {
+            q[u][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+            q[u][1] = q[u][0];
+          }
+        }
+      };
+      auto store_half = [&](int it, int h, const float4 (&q)[UH][2]) {
+        const int st = it % STAGES;
+        const uint32_t bhi = smem_u32(smem + st * STAGE_BYTES + A_STAGE);
+        const uint32_t blo = bhi + B_BYTES;
 #pragma unroll
-          for (int g = 0; g < 2; ++g) {
+        for (int u = 0; u < UH; ++u) {
+          const int n = box_of(h * UH + u);
+          const uint32_t row = (uint32_t)(n * SWB);
+          const float v[8] = {q[u][0].x, q[u][0].y, q[u][0].z, q[u][0].w,
+                              q[u][1].x, q[u][1].y, q[u][1].z, q[u][1].w};
+          if (SPLIT == SPLIT_TF32) {
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                float hf = tf32_rn(v[4 * g + t]);
+                hw[t] = __float_as_uint(hf);
+                lw[t] = __float_as_uint(tf32_rn(v[4 * g + t] - hf));
+              }
+              const uint32_t off = row + ((uint32_t)((2 * wd + g) ^ (n & 7)) << 4);
+              st_shared_v4(bhi + off, hw);
+              st_shared_v4(blo + off, lw);
+            }
+          } else {
             uint32_t hw[4], lw[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-              float hf = tf32_rn(v[4 * g + t]);
-              hw[t] = __float_as_uint(hf);
-              lw[t] = __float_as_uint(tf32_rn(v[4 * g + t] - hf));
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * t], v[2 * t + 1]);
+              float2 hf = __bfloat1622float2(h2);
+              hw[t] = *reinterpret_cast<uint32_t*>(&h2);
+              lw[t] = pack_bf16(v[2 * t] - hf.x, v[2 * t + 1] - hf.y);
             }
-            const uint32_t off = row + ((uint32_t)((2 * wd + g) ^ (n & 7)) << 4);
+            const uint32_t off = row + ((uint32_t)(wd ^ (n & 7)) << 4);
             st_shared_v4(bhi + off, hw);
             st_shared_v4(blo + off, lw);
           }
-        } else {
+        }
+      };
+      float4 qa[UH][2], qb[UH][2];
+      if (total > 0) load_half(0, 0, qa);
+      for (int it = 0; it < total; ++it) {
+        int st = it % STAGES;
+        load_half(it, 1, qb);
+        int ok_wait = 1;
+        if (lane == 0 && it >= STAGES)
+          ok_wait = wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail) ? 1 : 0;
+        if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
+        store_half(it, 0, qa);
+        if (it + 1 < total) load_half(it + 1, 0, qa);
+        store_half(it, 1, qb);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncwarp();
+        if (lane == 0) arrive(&full[st]);
+      }
+    } else {
+      // ---------------- B producers: gather, re-reference, split, swizzle ----------------
+      // Work unit = one target box j of the tile: the BK k-values of this chunk of its source
+      // box's four channels.  Lane l takes EPL consecutive k (two for bf16, one for tf32), i.e.
+      // one 32-bit word of each of the 8 rows (4 channels x hi/lo) at word l of the 128-byte
+      // row: the warp's loads are contiguous and each store instruction writes a full row.
+      constexpr int EPL = 4 / Fmt<SPLIT>::ES;          // k values per lane (one 32-bit word)
+      constexpr int WPR = SWB / 4;                     // 32-bit words per operand row
+      constexpr int BPI = 32 / WPR;                    // boxes per warp instruction (1 or 2)
+      constexpr int UPW = NB / PROD_WARPS;             // boxes per producer warp per stage
+      constexpr int LPS = UPW / BPI;                   // boxes per lane per stage
+      constexpr int UH = LPS / 2;                      // boxes per lane per half stage
+      static_assert(UH >= 1 && LPS == 2 * UH, "two half stages");
+      const int pw = warp - 4;
+      const int bsel = lane / WPR;                     // which of the BPI boxes the lane serves
+      const int wd = lane % WPR;                       // the lane's word of the row
+      // Lane box ul (0..LPS-1) is u = bsel + BPI ul of the warp's boxes, j = pw + 8u, with rows
+      // n = 4j + ch = (4 pw + ch) + 32u: the swizzled row of (u, ch) sits 32 u SWB bytes after that
+      // of (0, ch), and the chunk swizzle depends on n & 7 only.  With two boxes per instruction
+      // the second writes channel ch ^ 1 (rows of opposite parity: the other 64-byte bank half).
+      auto swz_off = [&](int n) -> uint32_t {
+        int x = SWB == 128 ? (n & 7) : ((n >> 1) & 3);
+        return (uint32_t)((n >> 3) * (8 * SWB) + (n & 7) * SWB + ((((wd >> 2) ^ x) & (SWB / 16 - 1)) << 4) +
+                          (wd & 3) * 4);
+      };
+      uint32_t roff[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        int ch = BPI == 2 ? (i ^ bsel) : i;
+        roff[i] = swz_off(4 * pw + ch) + (uint32_t)(32 * SWB * bsel);
+      }
+      // source box (flat index into up) of each of this lane's boxes for the current slot, or -1
+      int srcb[LPS];
+      int cur_slot = -1;
+      auto box_of = [&](int ul) { return pw + PROD_WARPS * (bsel + BPI * ul); };
+      auto set_slot = [&](int s) {
+#pragma unroll
+        for (int ul = 0; ul < LPS; ++ul) srcb[ul] = slot_src(a, sbox[box_of(ul)], s);
+      };
+      // Software pipeline over half stages (UH boxes per lane each): the loads of the next half
+      // are in flight while the current half is converted, including the first half of the next
+      // stage (registers only: no shared-memory stage is needed to issue them).
+      auto load_half = [&](int it, int h, float4 (&q)[UH][EPL]) {
+        int s = slot_list[it / nchunk], c = it % nchunk;
+        if (s != cur_slot) {
+          set_slot(s);
+          cur_slot = s;
+        }
+        const int k0 = c * BK + wd * EPL;
+        const bool kin = k0 < R;   // R and k0 even: a bf16 pair is all in or out
+#pragma unroll
+        for (int u = 0; u < UH; ++u) {
+          int sb = srcb[h * UH + u];
+          bool ok = sb >= 0 && kin;
+          const float4* p = reinterpret_cast<const float4*>(a.up) + (int64_t)(ok ? sb : 0) * R + k0;
+          if (EPL == 2) {
+            if (ok) {
+              ld_nc_v8(p, q[u][0], q[u][EPL - 1]);
+            } else {
+              q[u][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+              q[u][EPL - 1] = q[u][0];
+            }
+          } else {
+            q[u][0] = ok ? __ldg(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+      };
+      auto store_half = [&](int it, int h, const float4 (&q)[UH][EPL]) {
+        int s = slot_list[it / nchunk];
+        float ox, oy, oz;
+        slot_shift(a.mode, s, cls, ox, oy, oz);
+        const int st = it % STAGES;
+        const uint32_t bhi = smem_u32(smem + st * STAGE_BYTES + A_STAGE);
+        const uint32_t blo = bhi + B_BYTES;
+#pragma unroll
+        for (int u = 0; u < UH; ++u) {
+          const int ul = h * UH + u;
+          float side = sside[box_of(ul)];
+          float sx = ox * side, sy = oy * side, sz = oz * side;
+          float v[4][EPL];
+#pragma unroll
+          for (int t = 0; t < EPL; ++t) {
+            v[0][t] = q[u][t].x;
+            v[1][t] = q[u][t].y;
+            v[2][t] = q[u][t].z;
+            v[3][t] = q[u][t].w + sx * q[u][t].x + sy * q[u][t].y + sz * q[u][t].z;
+          }
           uint32_t hw[4], lw[4];
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * t], v[2 * t + 1]);
-            float2 hf = __bfloat1622float2(h2);
-            hw[t] = *reinterpret_cast<uint32_t*>(&h2);
-            lw[t] = pack_bf16(v[2 * t] - hf.x, v[2 * t + 1] - hf.y);
+          for (int ch = 0; ch < 4; ++ch) {
+            if (SPLIT == SPLIT_TF32) {
+              float hf = tf32_rn(v[ch][0]);
+              hw[ch] = __float_as_uint(hf);
+              lw[ch] = __float_as_uint(tf32_rn(v[ch][0] - hf));
+            } else {
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[ch][0], v[ch][EPL - 1]);
+              float2 hf = __bfloat1622float2(h2);
+              hw[ch] = *reinterpret_cast<uint32_t*>(&h2);
+              lw[ch] = pack_bf16(v[ch][0] - hf.x, v[ch][EPL - 1] - hf.y);
+            }
           }
-          const uint32_t off = row + ((uint32_t)(wd ^ (n & 7)) << 4);
-          st_shared_v4(bhi + off, hw);
-          st_shared_v4(blo + off, lw);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            uint32_t h_ = hw[i], l_ = lw[i];
+            if (BPI == 2 && bsel) {
+              h_ = hw[i ^ 1];
+              l_ = lw[i ^ 1];
+            }
+            const uint32_t off = roff[i] + (uint32_t)(32 * SWB * BPI) * ul;
+            st_shared_u32(bhi + off, h_);
+            st_shared_u32(blo + off, l_);
+          }
         }
+      };
+      float4 qa[UH][EPL], qb[UH][EPL];
+      if (total > 0) load_half(0, 0, qa);
+      for (int it = 0; it < total; ++it) {
+        int st = it % STAGES;
+        load_half(it, 1, qb);
+        // lane 0 waits for the stage to be free; the warp leaves the loop together on a timeout
+        int ok_wait = 1;
+        if (lane == 0 && it >= STAGES)
+          ok_wait = wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail) ? 1 : 0;
+        if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
+        store_half(it, 0, qa);
+        if (it + 1 < total) load_half(it + 1, 0, qa);
+        store_half(it, 1, qb);
+        // each lane orders its shared-memory writes before the async proxy (the MMAs) reads
+        // them; lane 0 then arrives once for the warp
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncwarp();
+        if (lane == 0) arrive(&full[st]);
       }
-    };
-    float4 qa[UH][2], qb[UH][2];
-    if (total > 0) load_half(0, 0, qa);
-    for (int it = 0; it < total; ++it) {
-      int st = it % STAGES;
-      load_half(it, 1, qb);
-      int ok_wait = 1;
-      if (lane == 0 && it >= STAGES)
-        ok_wait = wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail) ? 1 : 0;
-      if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
-      store_half(it, 0, qa);
-      if (it + 1 < total) load_half(it + 1, 0, qa);
-      store_half(it, 1, qb);
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      __syncwarp();
-      if (lane == 0) arrive(&full[st]);
     }
-   } else {
-    // ---------------- B producers: gather, re-reference, split, swizzle ----------------
-    // Work unit = one target box j of the tile: the BK k-values of this chunk of its source
-    // box's four channels.  Lane l takes EPL consecutive k (two for bf16, one for tf32), i.e.
-    // one 32-bit word of each of the 8 rows (4 channels x hi/lo) at word l of the 128-byte
-    // row: the warp's loads are contiguous and each store instruction writes a full row.
-    constexpr int EPL = 4 / Fmt<SPLIT>::ES;          // k values per lane (one 32-bit word)
-    constexpr int WPR = SWB / 4;                     // 32-bit words per operand row
-    constexpr int BPI = 32 / WPR;                    // boxes per warp instruction (1 or 2)
-    constexpr int UPW = NB / PROD_WARPS;             // boxes per producer warp per stage
-    constexpr int LPS = UPW / BPI;                   // boxes per lane per stage
-    constexpr int UH = LPS / 2;                      // boxes per lane per half stage
-    static_assert(UH >= 1 && LPS == 2 * UH, "two half stages");
-    const int pw = warp - 4;
-    const int bsel = lane / WPR;                     // which of the BPI boxes the lane serves
-    const int wd = lane % WPR;                       // the lane's word of the row
-    // Lane box ul (0..LPS-1) is u = bsel + BPI ul of the warp's boxes, j = pw + 8u, with rows
-    // n = 4j + ch = (4 pw + ch) + 32u: the swizzled row of (u, ch) sits 32 u SWB bytes after that
-    // of (0, ch), and the chunk swizzle depends on n & 7 only.  With two boxes per instruction
-    // the second writes channel ch ^ 1 (rows of opposite parity: the other 64-byte bank half).
-    auto swz_off = [&](int n) -> uint32_t {
-      int x = SWB == 128 ? (n & 7) : ((n >> 1) & 3);
-      return (uint32_t)((n >> 3) * (8 * SWB) + (n & 7) * SWB + ((((wd >> 2) ^ x) & (SWB / 16 - 1)) << 4) +
-                        (wd & 3) * 4);
-    };
-    uint32_t roff[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      int ch = BPI == 2 ? (i ^ bsel) : i;
-      roff[i] = swz_off(4 * pw + ch) + (uint32_t)(32 * SWB * bsel);
-    }
-    // source box (flat index into up) of each of this lane's boxes for the current slot, or -1
-    int srcb[LPS];
-    int cur_slot = -1;
-    auto box_of = [&](int ul) { return pw + PROD_WARPS * (bsel + BPI * ul); };
-    auto set_slot = [&](int s) {
-#pragma unroll
-      for (int ul = 0; ul < LPS; ++ul) srcb[ul] = slot_src(a, sbox[box_of(ul)], s);
-    };
-    // Software pipeline over half stages (UH boxes per lane each): the loads of the next half
-    // are in flight while the current half is converted, including the first half of the next
-    // stage (registers only: no shared-memory stage is needed to issue them).
-    auto load_half = [&](int it, int h, float4 (&q)[UH][EPL]) {
-      int s = slot_list[it / nchunk], c = it % nchunk;
-      if (s != cur_slot) {
-        set_slot(s);
-        cur_slot = s;
-      }
-      const int k0 = c * BK + wd * EPL;
-      const bool kin = k0 < R;   // R and k0 even: a bf16 pair is all in or out
-#pragma unroll
-      for (int u = 0; u < UH; ++u) {
-        int sb = srcb[h * UH + u];
-        bool ok = sb >= 0 && kin;
-        const float4* p = reinterpret_cast<const float4*>(a.up) + (int64_t)(ok ? sb : 0) * R + k0;
-        if (EPL == 2) {
-          if (ok) {
-            ld_nc_v8(p, q[u][0], q[u][EPL - 1]);
-          } else {
-            q[u][0] = make_float4(0.f, 0.f, 0.f, 0.f);
-            q[u][EPL - 1] = q[u][0];
-          }
-        } else {
-          q[u][0] = ok ? __ldg(p) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      }
-    };
-    auto store_half = [&](int it, int h, const float4 (&q)[UH][EPL]) {
-      int s = slot_list[it / nchunk];
-      float ox, oy, oz;
-      slot_shift(a.mode, s, cls, ox, oy, oz);
-      const int st = it % STAGES;
-      const uint32_t bhi = smem_u32(smem + st * STAGE_BYTES + A_STAGE);
-      const uint32_t blo = bhi + B_BYTES;
-#pragma unroll
-      for (int u = 0; u < UH; ++u) {
-        const int ul = h * UH + u;
-        float side = sside[box_of(ul)];
-        float sx = ox * side, sy = oy * side, sz = oz * side;
-        float v[4][EPL];
-#pragma unroll
-        for (int t = 0; t < EPL; ++t) {
-          v[0][t] = q[u][t].x;
-          v[1][t] = q[u][t].y;
-          v[2][t] = q[u][t].z;
-          v[3][t] = q[u][t].w + sx * q[u][t].x + sy * q[u][t].y + sz * q[u][t].z;
-        }
-        uint32_t hw[4], lw[4];
-#pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-          if (SPLIT == SPLIT_TF32) {
-            float hf = tf32_rn(v[ch][0]);
-            hw[ch] = __float_as_uint(hf);
-            lw[ch] = __float_as_uint(tf32_rn(v[ch][0] - hf));
-          } else {
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[ch][0], v[ch][EPL - 1]);
-            float2 hf = __bfloat1622float2(h2);
-            hw[ch] = *reinterpret_cast<uint32_t*>(&h2);
-            lw[ch] = pack_bf16(v[ch][0] - hf.x, v[ch][EPL - 1] - hf.y);
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          uint32_t h_ = hw[i], l_ = lw[i];
-          if (BPI == 2 && bsel) {
-            h_ = hw[i ^ 1];
-            l_ = lw[i ^ 1];
-          }
-          const uint32_t off = roff[i] + (uint32_t)(32 * SWB * BPI) * ul;
-          st_shared_u32(bhi + off, h_);
-          st_shared_u32(blo + off, l_);
-        }
-      }
-    };
-    float4 qa[UH][EPL], qb[UH][EPL];
-    if (total > 0) load_half(0, 0, qa);
-    for (int it = 0; it < total; ++it) {
-      int st = it % STAGES;
-      load_half(it, 1, qb);
-      // lane 0 waits for the stage to be free; the warp leaves the loop together on a timeout
-      int ok_wait = 1;
-      if (lane == 0 && it >= STAGES)
-        ok_wait = wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail) ? 1 : 0;
-      if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
-      store_half(it, 0, qa);
-      if (it + 1 < total) load_half(it + 1, 0, qa);
-      store_half(it, 1, qb);
-      // each lane orders its shared-memory writes before the async proxy (the MMAs) reads
-      // them; lane 0 then arrives once for the warp
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      __syncwarp();
-      if (lane == 0) arrive(&full[st]);
-    }
-   }
   } else if (warp == W_MMA) {
     // ---------------- MMA issue (one thread) ----------------
     if (lane == 0) {
@@ -732,19 +732,19 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int t = 0; t < 32; ++t) x[t] = 0.f;
         }
         if constexpr (CH == 1) {
-         if (row < R) {
-          // column t = box 32 qc + t; a warp writes 32 consecutive rows of one box per store
-          float* dst1 = a.dn + a.part_stride * blockIdx.z;
+          if (row < R) {
+            // column t = box 32 qc + t; a warp writes 32 consecutive rows of one box per store
+            float* dst1 = a.dn + a.part_stride * blockIdx.z;
 #pragma unroll
-          for (int t = 0; t < 32; ++t) {
-            if (sbox[qc * 32 + t] < 0) continue;
-            float* o = dst1 + (int64_t)sout[qc * 32 + t] * R + row;
-            float v = x[t];
-            if (a.write == TC_ADD) v += *o;
-            else if (a.write == TC_SCALE) v *= 0.5f * sside[qc * 32 + t];
-            *o = v;
+            for (int t = 0; t < 32; ++t) {
+              if (sbox[qc * 32 + t] < 0) continue;
+              float* o = dst1 + (int64_t)sout[qc * 32 + t] * R + row;
+              float v = x[t];
+              if (a.write == TC_ADD) v += *o;
+              else if (a.write == TC_SCALE) v *= 0.5f * sside[qc * 32 + t];
+              *o = v;
+            }
           }
-         }
         } else if (row < R) {
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {

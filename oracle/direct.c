@@ -79,6 +79,43 @@ void orc_laplace_dipole(const double* x, int64_t nt, const double* y, int64_t ns
   }
 }
 
+/* Charges and dipoles to potential, gradient and Hessian, Sec. II.A (Table
+ * tab:ktab_lapqdpgradgrad): phi = L q + L^D_j d_j with L^D_j = -dL/dx_j, so with r = x - y
+ *   4 pi phi         = q / r + (d.r) / r^3,
+ *   4 pi d_i phi     = -q r_i / r^3 + d_i / r^3 - 3 (d.r) r_i / r^5,
+ *   4 pi d_i d_j phi = q (3 r_i r_j - delta_ij r^2) / r^5
+ *                      - 3 (d_i r_j + d_j r_i + (d.r) delta_ij) / r^5 + 15 (d.r) r_i r_j / r^7.
+ * s: [q d1 d2 d3] (4), g: [phi, grad (3), Hessian xx xy xz yy yz zz (6)] (10). */
+void orc_laplace_qd(const double* x, int64_t nt, const double* y, int64_t ns,
+                    const double* s, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double acc[10] = {0};
+    for (int64_t b = 0; b < ns; ++b) {
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1],
+                     x[3 * a + 2] - y[3 * b + 2]};
+      double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (rr == 0.0) continue;
+      const double* v = s + 4 * b;
+      double q = v[0], d[3] = {v[1], v[2], v[3]};
+      double rn = sqrt(rr), r3 = rr * rn, r5 = r3 * rr, r7 = r5 * rr;
+      double dr = d[0] * r[0] + d[1] * r[1] + d[2] * r[2];
+      acc[0] += (q / rn + dr / r3) / (4.0 * PI);
+      for (int i = 0; i < 3; ++i)
+        acc[1 + i] += (-q * r[i] / r3 + d[i] / r3 - 3.0 * dr * r[i] / r5) / (4.0 * PI);
+      int c = 4;
+      for (int i = 0; i < 3; ++i)
+        for (int j = i; j < 3; ++j) {
+          double dij = i == j ? 1.0 : 0.0;
+          double h = q * (3.0 * r[i] * r[j] - dij * rr) / r5 -
+                     3.0 * (d[i] * r[j] + d[j] * r[i] + dr * dij) / r5 + 15.0 * dr * r[i] * r[j] / r7;
+          acc[c++] += h / (4.0 * PI);
+        }
+    }
+    for (int k = 0; k < 10; ++k) g[10 * a + k] += acc[k];
+  }
+}
+
 /* Stokeslet, Sec. II.B: G_ij = (delta_ij / r + r_i r_j / r^3) / (8 pi).  s: f (3), g: u (3). */
 void orc_stokeslet(const double* x, int64_t nt, const double* y, int64_t ns,
                    const double* s, double* g) {

@@ -8,6 +8,7 @@ Kernels (dimensions k_s x k_t, Table tab:implement):
   laplace            q -> phi                     1 x 1   (Sec. II.A)
   laplace_pgradgrad  q -> phi, grad, grad grad    1 x 10  (Table tab:ktab_lapqdpgradgrad)
   laplace_dipole     d -> phi                     3 x 1   (Sec. II.A)
+  laplace_qd         [q, d] -> phi, grad, grad grad  4 x 10  (Table tab:ktab_lapqdpgradgrad)
   stokeslet          f -> u                       3 x 3   (Sec. II.B)
   stokeslet_reg      [f, eps] -> u                4 x 3   (regularized Stokeslet, Table tab:ktab_reg)
   rpy                [f, b] -> [u, lap u]         4 x 6   (Eqs. RPYflow, RPYkernel)
@@ -27,6 +28,7 @@ KDIM = {  # kernel -> (k_s, k_t)
     "laplace": (1, 1),
     "laplace_pgradgrad": (1, 10),
     "laplace_dipole": (3, 1),
+    "laplace_qd": (4, 10),
     "stokeslet": (3, 3),
     "stokeslet_reg": (4, 3),
     "rpy": (4, 6),

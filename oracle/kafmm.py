@@ -57,6 +57,9 @@ PROBLEMS = {
     # regularized Stokeslet [f, eps] -> u, Table tab:ktab_reg: G^eps from S (to M, L and T),
     # the singular Stokeslet G between equivalent surfaces and from them to T
     "stokeslet_reg_g": (4, 3, "stokeslet", 1),
+    # charges and dipoles to potential, gradient and Hessian, Table tab:ktab_lapqdpgradgrad:
+    # L and L^D from S, charges on M and L, L + grad L + grad grad L to T
+    "laplace_qd": (4, 10, "laplace", 1),
 }
 
 
@@ -139,6 +142,8 @@ class KAFMM:
         pr = self.problem
         if pr == "laplace":
             return D.direct("laplace", chk, y, s)
+        if pr == "laplace_qd":
+            return D.direct("laplace", chk, y, s[:, :1]) + D.direct("laplace_dipole", chk, y, s[:, 1:])
         if pr in ("stokeslet_g", "rpy_g", "stokeslet_reg_g"):
             kern = {"stokeslet_g": "stokeslet", "rpy_g": "rpy", "stokeslet_reg_g": "stokeslet_reg"}[pr]
             g = D.direct(kern, chk, y, s)
@@ -158,6 +163,8 @@ class KAFMM:
         pr = self.problem
         if pr == "laplace":
             return D.direct("laplace", x, eq, dens[:, 0])
+        if pr == "laplace_qd":
+            return D.direct("laplace_pgradgrad", x, eq, dens[:, 0])
         if pr in ("stokeslet_g", "stokeslet_reg_g"):
             return D.direct("stokeslet", x, eq, dens.reshape(-1, 3))
         if pr == "rpy_g":
@@ -179,7 +186,8 @@ class KAFMM:
 
     def _src_to_targets(self, x, y, s) -> np.ndarray:
         kern = {"laplace": "laplace", "stokeslet_g": "stokeslet", "stokeslet_l4": "stokeslet",
-                "rpy_g": "rpy", "rpy_l4": "rpy", "stokeslet_reg_g": "stokeslet_reg"}[self.problem]
+                "rpy_g": "rpy", "rpy_l4": "rpy", "stokeslet_reg_g": "stokeslet_reg",
+                "laplace_qd": "laplace_qd"}[self.problem]
         return D.direct(kern, x, y, s)
 
     def _shift(self, dens, c_from, c_to) -> np.ndarray:

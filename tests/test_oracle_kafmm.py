@@ -67,7 +67,7 @@ def test_kafmm_without_far_field_is_the_direct_sum(problem):
     ks, kt, _, _ = PROBLEMS[problem]
     pts = rng.random((50, 3))
     s = rng.standard_normal((50, ks))
-    if ks == 4:
+    if problem in WIDTH_PROBLEMS:   # radius b / blob width eps in the fourth column
         s[:, 3] = rng.uniform(0.001, 0.01, 50)
     kern = KERNEL_OF[problem]
     g = KAFMM(problem, 4, q=64).evaluate(pts, s)
@@ -93,8 +93,10 @@ def test_l4_aggregation_reproduces_stokeslet_exactly():
     assert np.allclose(F._shift(q0, c0, c1), q1, rtol=1e-13, atol=1e-14)
 
 
+WIDTH_PROBLEMS = ("rpy_g", "rpy_l4", "stokeslet_reg_g")
 KERNEL_OF = {"laplace": "laplace", "stokeslet_g": "stokeslet", "stokeslet_l4": "stokeslet",
-             "rpy_g": "rpy", "rpy_l4": "rpy", "stokeslet_reg_g": "stokeslet_reg"}
+             "rpy_g": "rpy", "rpy_l4": "rpy", "stokeslet_reg_g": "stokeslet_reg",
+             "laplace_qd": "laplace_qd"}
 
 
 def _inputs(problem, n, seed=0):
@@ -102,7 +104,7 @@ def _inputs(problem, n, seed=0):
     pts = rng.random((n, 3))
     ks = PROBLEMS[problem][0]
     s = rng.standard_normal((n, ks))
-    if ks == 4:
+    if problem in WIDTH_PROBLEMS:
         s[:, 3] = rng.uniform(0.0, 2e-3, n)
     return pts, s
 
@@ -114,6 +116,7 @@ def _inputs(problem, n, seed=0):
     ("rpy_l4", 2000, 40, (4, 6, 8), 1e-5),
     ("rpy_g", 1200, 40, (4, 6), 1e-3),
     ("stokeslet_reg_g", 1200, 40, (4, 6), 1e-3),
+    ("laplace_qd", 2000, 48, (4, 6, 8), 1e-5),
 ])
 def test_kafmm_converges_to_direct_sum(problem, n, q, orders, bound):
     """eps_L2 against the direct sum falls exponentially with the order m (Sec. III)."""

@@ -336,3 +336,32 @@ def test_regularized_stokeslet_is_the_flow_of_the_blob_force(eps, xt):
         u += wk * rk / (8 * PI) * ((wang * psi) @ (f[None, :] + n * nf[:, None]))
     ref = D.direct("stokeslet_reg", x[None], np.zeros((1, 3)), np.concatenate([f, [eps]])[None])[0]
     assert np.allclose(u, ref, rtol=1e-8, atol=1e-10), (u, ref)
+
+
+def test_laplace_charge_dipole_gradients_and_hessian():
+    """[q, d] -> [phi, grad phi, grad grad phi] (Table tab:ktab_lapqdpgradgrad): charges alone
+    equal the charge routine, the potential of dipoles alone equals the (separately pinned)
+    dipole potential, the gradient and Hessian equal central differences of the potential
+    and of the gradient, and the Hessian is trace-free (phi is harmonic off the sources)."""
+    rng = np.random.default_rng(41)
+    y = rng.random((5, 3))
+    sv = rng.standard_normal((5, 4))
+    x = np.array([[1.3, 0.7, -0.4], [0.2, 1.9, 1.1]])
+    q_only = sv.copy()
+    q_only[:, 1:] = 0
+    assert np.allclose(D.direct("laplace_qd", x, y, q_only), D.direct("laplace_pgradgrad", x, y, sv[:, :1]),
+                       rtol=1e-13, atol=0)
+    d_only = sv.copy()
+    d_only[:, 0] = 0
+    assert np.allclose(D.direct("laplace_qd", x, y, d_only)[:, 0],
+                       D.direct("laplace_dipole", x, y, sv[:, 1:])[:, 0], rtol=1e-13, atol=0)
+    hidx = {(0, 0): 4, (0, 1): 5, (0, 2): 6, (1, 1): 7, (1, 2): 8, (2, 2): 9}
+    for xt in x:
+        g = D.direct("laplace_qd", xt[None], y, sv)[0]
+        phi = lambda z: D.direct("laplace_qd", z[None], y, sv)[0, :1]
+        grad = lambda z: D.direct("laplace_qd", z[None], y, sv)[0, 1:4]
+        assert np.allclose(fd_grad(phi, xt, h=1e-5)[0], g[1:4], rtol=1e-7, atol=1e-9)
+        H = fd_grad(grad, xt, h=1e-5)
+        for (i, j), k in hidx.items():
+            assert np.isclose(H[i, j], g[k], rtol=1e-6, atol=1e-8)
+        assert abs(g[4] + g[7] + g[9]) < 1e-12 * np.abs(g[4:]).max()

@@ -53,13 +53,20 @@ typedef struct kafmm_plan_s* kafmm_plan_t;
  *                    Stokeslet elsewhere, always on the G table (KAFMM_OPT_ML_VARIANT is
  *                    ignored).  eps must be far below the smallest leaf box (Sec. II.B).
  *                    Pairs at r = 0 are skipped as for the other kernels; a caller wanting a
- *                    blob's own velocity adds G^eps(0) f = f / (4 pi eps). */
+ *                    blob's own velocity adds G^eps(0) f = f / (4 pi eps).
+ *   KAFMM_LAPLACE_QD [q, d] -> [phi, grad phi, grad grad phi]                     k_s=4, k_t=10
+ *                    (Sec. II.A, Table tab:ktab_lapqdpgradgrad): charge q and dipole d per
+ *                    source, phi = q/(4 pi r) + d.r/(4 pi r^3); outputs phi, d_x phi, d_y phi,
+ *                    d_z phi, then the Hessian xx xy xz yy yz zz.  L and L^D from the sources,
+ *                    charges on the equivalent surfaces (Laplace table).  Open boundary only
+ *                    (KAFMM_ERR_ARG with KAFMM_BC_PXYZ). */
 typedef enum {
   KAFMM_LAPLACE = 0,
   KAFMM_STOKESLET = 1,
   KAFMM_RPY = 2,
   KAFMM_STOKES_DL = 3,
-  KAFMM_STOKES_REG = 4
+  KAFMM_STOKES_REG = 4,
+  KAFMM_LAPLACE_QD = 5
 } kafmm_kernel;
 
 /* Boundary conditions (Sec. III.B).  KAFMM_BC_PXYZ: triply periodic in the cube

@@ -49,6 +49,10 @@ static void configure(Plan& P) {
         P.D = 3;
       }
       break;
+    case KAFMM_LAPLACE_QD:  // [q, d] -> [phi, grad, grad grad] on the Laplace table
+      P.ks = 4;
+      P.kt = 10;
+      break;
     case KAFMM_STOKES_REG:  // [f, eps] -> u on the G table (Table tab:ktab_reg)
       P.ks = 4;
       P.kt = 3;
@@ -118,7 +122,7 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
     return KAFMM_ERR_ARG;
   }
   *out = nullptr;
-  if ((int)kernel < 0 || (int)kernel > 4 || (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ) || p < 2 ||
+  if ((int)kernel < 0 || (int)kernel > 5 || (kernel == KAFMM_LAPLACE_QD && bc == KAFMM_BC_PXYZ) || (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ) || p < 2 ||
       p > 16 || q < 1 || q > 4096) {
     g_err = "kafmm_plan: invalid kernel, boundary condition, order (2..16) or leaf size (1..4096)";
     return KAFMM_ERR_ARG;

@@ -39,7 +39,8 @@ __global__ void k_prep_src(const Tin* __restrict__ s, const uint32_t* __restrict
                            typename V4<T>::type* __restrict__ out) {
   using T4 = typename V4<T>::type;
   constexpr int KS =
-      PR == P_LAP ? 1 : (PR == P_DL ? 9 : ((PR == P_RPY_L4 || PR == P_RPY_G || PR == P_REG_G) ? 4 : 3));
+      PR == P_LAP ? 1
+                  : (PR == P_DL ? 9 : ((PR == P_RPY_L4 || PR == P_RPY_G || PR == P_REG_G || PR == P_LAPQD) ? 4 : 3));
   constexpr int NV = ProbInfo<PR>::NV;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -142,6 +143,10 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
             T r0 = px - y.x, r1 = py - y.y, r2 = pz - y.z;
             if (PR == P_LAP) {
               lap_st<T>(r0, r1, r2, v.x, acc);
+            } else if (PR == P_LAPQD) {   // S->M, S->L: L for the charge, L^D for the dipole
+              T rr = r0 * r0 + r1 * r1 + r2 * r2;
+              T ir = inv_r(rr);
+              acc[0] += v.x * ir + (v.y * r0 + v.z * r1 + v.w * r2) * ir * ir * ir;
             } else if (PR == P_STK_L4 || PR == P_RPY_L4) {
               T rr = r0 * r0 + r1 * r1 + r2 * r2;
               T ir = inv_r(rr);
@@ -500,6 +505,8 @@ __device__ inline void far_eval(T xl, T yl, T zl, const typename V4<T>::type& p,
     acc[2] = fmaf(r2, tq, fmaf(q.z, ir, acc[2]));
   } else if (PR == P_LAP) {
     lap_st<T>(r0, r1, r2, q.x, acc);
+  } else if (PR == P_LAPQD) {   // M->T, L->T: equivalent charges, L + grad L + grad grad L
+    lapqd_st<T, false>(r0, r1, r2, q.x, T(0), T(0), T(0), acc);
   } else if (PR == P_STK_L4 || PR == P_RPY_L4) {
     // 8 pi u_i = 2 [phi_i - x_j d_i phi_j + d_i phi_4] with phi = q/r (reference: leaf centre)
     T rr = r0 * r0 + r1 * r1 + r2 * r2;
@@ -711,6 +718,8 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
             T4 v = sv[(base + j) * NV];
             if (PR == P_LAP) {
               lap_st<T>(r0, r1, r2, v.x, tmp);
+            } else if (PR == P_LAPQD) {
+              lapqd_st<T, true>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
             } else if (PR == P_STK_L4 || PR == P_STK_G) {
               stk_st<T>(r0, r1, r2, v.x, v.y, v.z, tmp);
             } else if (PR == P_REG_G) {   // S->T: the regularized kernel of the source's eps
@@ -1177,6 +1186,8 @@ int evaluate(Plan& P, const void* s, void* g, int dtype) {
     pr = P.C == 4 ? P_RPY_L4 : P_RPY_G;
   else if (P.kernel == KAFMM_STOKES_REG)
     pr = P_REG_G;
+  else if (P.kernel == KAFMM_LAPLACE_QD)
+    pr = P_LAPQD;
   else
     pr = P_DL;
   (void)dtype;
@@ -1189,6 +1200,7 @@ int evaluate(Plan& P, const void* s, void* g, int dtype) {
     case P_RPY_L4: return run_eval<T, P_RPY_L4>(P, s, sd, g); \
     case P_RPY_G: return run_eval<T, P_RPY_G>(P, s, sd, g);  \
     case P_REG_G: return run_eval<T, P_REG_G>(P, s, sd, g);  \
+    case P_LAPQD: return run_eval<T, P_LAPQD>(P, s, sd, g);  \
     default: return run_eval<T, P_DL>(P, s, sd, g);          \
   }
   if (P.fp64()) {

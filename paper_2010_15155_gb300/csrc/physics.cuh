@@ -6,7 +6,8 @@
 namespace kafmm {
 
 // Problem = kernel + ML-tree table.
-enum Prob { P_LAP = 0, P_STK_L4 = 1, P_STK_G = 2, P_RPY_L4 = 3, P_RPY_G = 4, P_DL = 5, P_REG_G = 6 };
+enum Prob { P_LAP = 0, P_STK_L4 = 1, P_STK_G = 2, P_RPY_L4 = 3, P_RPY_G = 4, P_DL = 5, P_REG_G = 6,
+            P_LAPQD = 7 };
 
 template <int PR>
 struct ProbInfo;
@@ -24,6 +25,8 @@ template <>
 struct ProbInfo<P_DL> { static constexpr int KT = 4, C = 1, D = 1, NV = 3; };
 template <>
 struct ProbInfo<P_REG_G> { static constexpr int KT = 3, C = 1, D = 3, NV = 1; };
+template <>
+struct ProbInfo<P_LAPQD> { static constexpr int KT = 10, C = 1, D = 1, NV = 1; };
 
 template <class T>
 struct V4;
@@ -89,6 +92,35 @@ template <class T>
 __device__ inline void lap_st(T r0, T r1, T r2, T q, T* acc) {
   T ir = inv_r(r0 * r0 + r1 * r1 + r2 * r2);
   acc[0] += q * ir;  // scaled by 1/(4 pi) at the end
+}
+
+// Charges and dipoles to potential, gradient and Hessian (Sec. II.A, Table
+// tab:ktab_lapqdpgradgrad), all scaled by 1/(4 pi) at the end; r = x - y:
+//   phi = q/r + (d.r)/r^3,  d_i phi = -q r_i/r^3 + d_i/r^3 - 3 (d.r) r_i/r^5,
+//   d_i d_j phi = q (3 r_i r_j - delta_ij r^2)/r^5 - 3 (d_i r_j + d_j r_i + (d.r) delta_ij)/r^5
+//                 + 15 (d.r) r_i r_j / r^7;   Hessian order xx xy xz yy yz zz.
+template <class T, bool DIPOLE>
+__device__ inline void lapqd_st(T r0, T r1, T r2, T q, T d0, T d1, T d2, T* acc) {
+  T ir = inv_r(r0 * r0 + r1 * r1 + r2 * r2);
+  T ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+  const T r[3] = {r0, r1, r2};
+  const T d[3] = {d0, d1, d2};
+  T dr = DIPOLE ? (d0 * r0 + d1 * r1 + d2 * r2) : T(0);
+  T a3 = T(3) * ir5 * q;                      // charge Hessian: a3 r_i r_j - q ir3 delta_ij
+  T c5 = DIPOLE ? T(15) * dr * ir5 * ir2 : T(0);
+  T m3 = DIPOLE ? T(3) * ir5 : T(0);
+  acc[0] += q * ir + dr * ir3;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) acc[1 + i] += -q * r[i] * ir3 + (DIPOLE ? d[i] * ir3 - T(3) * dr * r[i] * ir5 : T(0));
+  int c = 4;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      T h = a3 * r[i] * r[j] + (DIPOLE ? c5 * r[i] * r[j] - m3 * (d[i] * r[j] + d[j] * r[i]) : T(0));
+      if (i == j) h -= q * ir3 + (DIPOLE ? m3 * dr : T(0));
+      acc[c++] += h;
+    }
 }
 
 // Stokeslet u = (f / r + r (r.f) / r^3): scaled by 1/(8 pi) at the end
@@ -159,7 +191,7 @@ __device__ inline void dl_st(T r0, T r1, T r2, const T* Dm, T* acc) {
 template <int PR, class T>
 __device__ inline T out_scale(int k) {
   const T f4 = T(1.0 / (4.0 * PI)), f8 = T(1.0 / (8.0 * PI));
-  if (PR == P_LAP) return f4;
+  if (PR == P_LAP || PR == P_LAPQD) return f4;
   if (PR == P_STK_L4 || PR == P_STK_G || PR == P_REG_G) return f8;
   if (PR == P_RPY_L4 || PR == P_RPY_G) return k < 3 ? f8 : f4;
   return k == 0 ? f4 : f8;  // DL

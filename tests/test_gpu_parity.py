@@ -19,7 +19,7 @@ from oracle.tree import Tree  # noqa: E402
 from paper_2010_15155_gb300 import kafmm as K  # noqa: E402
 
 KERN = {"laplace": K.LAPLACE, "stokeslet": K.STOKESLET, "rpy": K.RPY, "stokes_dl": K.STOKES_DL,
-        "stokeslet_reg": K.STOKES_REG}
+        "stokeslet_reg": K.STOKES_REG, "laplace_qd": K.LAPLACE_QD}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -99,11 +99,15 @@ def _near_oracle(kernel, pts, s, q):
     return g
 
 
-@pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "rpy", "stokes_dl", "stokeslet_reg"])
+@pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "rpy", "stokes_dl", "stokeslet_reg",
+                                    "laplace_qd"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_near_field_matches_oracle(kernel, prec):
     n, q = 3000, 50
     pts, s = _inputs(kernel, n, seed=7)
+    if prec == "fp32":   # the oracle sees the points and values the FP32 form computes with
+        pts = pts.astype(np.float32).astype(np.float64)
+        s = s.astype(np.float32).astype(np.float64)
     ref = _near_oracle(kernel, pts, s, q)
     dt = torch.float64 if prec == "fp64" else torch.float32
     plan = K.Plan(KERN[kernel], p=4, q=q, precision=K.PREC_FP64 if prec == "fp64" else K.PREC_FP32,
@@ -122,6 +126,7 @@ def test_near_field_matches_oracle(kernel, prec):
     ("rpy_l4", "rpy", K.ML_L4, 2500, 6, 40),
     ("rpy_g", "rpy", K.ML_G, 1500, 4, 32),
     ("stokeslet_reg_g", "stokeslet_reg", K.ML_G, 1500, 4, 32),
+    ("laplace_qd", "laplace_qd", K.ML_L4, 3000, 6, 40),
 ])
 def test_fp64_gpu_kafmm_matches_cpu_kafmm(problem, kernel, variant, n, p, q):
     if problem == "laplace":
@@ -168,6 +173,9 @@ def test_fp32_form_matches_fp64_form(kernel, variant):
 
 
 def test_errors_are_reported_not_trapped():
+    with pytest.raises(K.KafmmError) as e:   # dipole sums need a surface term when periodic
+        K.Plan(K.LAPLACE_QD, p=4, q=32, bc=K.BC_PXYZ)
+    assert e.value.code == -1
     plan = K.Plan(K.STOKESLET, p=4, q=32, precision=K.PREC_FP32)
     bad = torch.tensor([[0.5, 0.5, 1.5], [0.1, 0.2, 0.3]], dtype=torch.float32, device="cuda")
     with pytest.raises(K.KafmmError) as e:
@@ -201,6 +209,7 @@ def test_mixed_tensor_core_form_matches_fp64_form(n, p, q):
     ("stokeslet", "open", 8, K.TC_BF16X3),    # G table, R = 888
     ("stokeslet", "pxyz", 8, K.TC_AUTO),      # periodic G table (root operator on CUDA cores)
     ("rpy", "open", 6, K.TC_AUTO),            # RPY on the G table
+    ("laplace_qd", "open", 8, K.TC_AUTO),     # charges + dipoles -> phi, grad, Hessian
 ])
 def test_mixed_tensor_core_single_column_tables_match_fp64_form(kernel, bc, p, split):
     """Single-column ML tables (Laplace; the Stokeslet G table, open and periodic) with the

@@ -137,6 +137,30 @@ void orc_stokeslet(const double* x, int64_t nt, const double* y, int64_t ns,
   }
 }
 
+/* StokesPVel, Sec. II.C (Eqs. stkslp, stkslvel): [p, u] = G^P [f, q],
+ *   p = r.f / (4 pi r^3),  u_i = (delta_ij / r + r_i r_j / r^3) f_j / (8 pi) - r_i q / (8 pi r^3),
+ * q twice the fluid removed (a sink for q > 0).  s: [f1 f2 f3 q] (4), g: [p, u] (4). */
+void orc_stokes_pvel(const double* x, int64_t nt, const double* y, int64_t ns,
+                     const double* s, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double acc[4] = {0, 0, 0, 0};
+    for (int64_t b = 0; b < ns; ++b) {
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1],
+                     x[3 * a + 2] - y[3 * b + 2]};
+      double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (rr == 0.0) continue;
+      const double* v = s + 4 * b;
+      double rn = sqrt(rr), r3 = rr * rn;
+      double rf = r[0] * v[0] + r[1] * v[1] + r[2] * v[2];
+      acc[0] += rf / (4.0 * PI * r3);
+      for (int i = 0; i < 3; ++i)
+        acc[1 + i] += (v[i] / rn + r[i] * rf / r3 - r[i] * v[3] / r3) / (8.0 * PI);
+    }
+    for (int k = 0; k < 4; ++k) g[4 * a + k] += acc[k];
+  }
+}
+
 /* Regularized Stokeslet, Sec. II.B (Table tab:ktab_reg): the flow of the force f spread by
  * the blob psi(r) = 15 eps^4 / (8 pi (r^2 + eps^2)^{7/2}) around the source,
  *   G^eps_ij = [ (r^2 + 2 eps^2) delta_ij + r_i r_j ] / (8 pi (r^2 + eps^2)^{3/2}),

@@ -11,6 +11,7 @@ Kernels (dimensions k_s x k_t, Table tab:implement):
   laplace_qd         [q, d] -> phi, grad, grad grad  4 x 10  (Table tab:ktab_lapqdpgradgrad)
   stokeslet          f -> u                       3 x 3   (Sec. II.B)
   stokeslet_reg      [f, eps] -> u                4 x 3   (regularized Stokeslet, Table tab:ktab_reg)
+  stokes_pvel        [f, q] -> [p, u]             4 x 4   (StokesPVel, Eqs. stkslp, stkslvel)
   rpy                [f, b] -> [u, lap u]         4 x 6   (Eqs. RPYflow, RPYkernel)
   stokes_dl          D -> [p, u]                  9 x 4   (Eqs. stkdlp, stkdlvel)
 """
@@ -31,6 +32,7 @@ KDIM = {  # kernel -> (k_s, k_t)
     "laplace_qd": (4, 10),
     "stokeslet": (3, 3),
     "stokeslet_reg": (4, 3),
+    "stokes_pvel": (4, 4),
     "rpy": (4, 6),
     "stokes_dl": (9, 4),
 }

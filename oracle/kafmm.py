@@ -60,6 +60,9 @@ PROBLEMS = {
     # charges and dipoles to potential, gradient and Hessian, Table tab:ktab_lapqdpgradgrad:
     # L and L^D from S, charges on M and L, L + grad L + grad grad L to T
     "laplace_qd": (4, 10, "laplace", 1),
+    # Stokes double layer D -> [p, u], Table tab:ktab_stkdlpvelgrad: K from S, the StokesPVel
+    # kernel G^P ([f, q] -> [p, u]) between and from the equivalent surfaces
+    "stokes_dl_pv": (9, 4, "stokes_pvel", 1),
 }
 
 
@@ -72,12 +75,23 @@ def surface(m: int) -> np.ndarray:
 
 
 def ml_matrix(ml: str, trg: np.ndarray, src: np.ndarray) -> np.ndarray:
-    """Kernel matrix of the ML-tree kernel: Laplace [nt, ns] or Stokeslet [3nt, 3ns]."""
+    """Kernel matrix of the ML-tree kernel: Laplace [nt, ns], Stokeslet [3nt, 3ns] or
+    StokesPVel [4nt, 4ns] (rows p, u per target point; columns f, q per source point)."""
     r = trg[:, None, :] - src[None, :, :]
     rn = np.sqrt(np.sum(r * r, axis=2))
     if ml == "laplace":
         return 1.0 / (4.0 * PI * rn)
     nt, ns = rn.shape
+    if ml == "stokes_pvel":
+        K = np.zeros((nt, 4, ns, 4))
+        for b in range(3):
+            K[:, 0, :, b] = r[:, :, b] / (4.0 * PI * rn ** 3)
+        for a in range(3):
+            for b in range(3):
+                K[:, 1 + a, :, b] = ((1.0 if a == b else 0.0) / rn
+                                     + r[:, :, a] * r[:, :, b] / rn ** 3) / (8.0 * PI)
+            K[:, 1 + a, :, 3] = -r[:, :, a] / (8.0 * PI * rn ** 3)
+        return K.reshape(4 * nt, 4 * ns)
     K = np.zeros((nt, 3, ns, 3))
     for a in range(3):
         for b in range(3):
@@ -97,7 +111,7 @@ class KAFMM:
         self.bc, self.origin, self.L = bc, float(origin), float(L)
         self.unit = surface(self.p)
         self.n = len(self.unit)
-        self.dim = 1 if self.ml == "laplace" else 3  # rows per surface point
+        self.dim = {"laplace": 1, "stokeslet": 3, "stokes_pvel": 4}[self.ml]  # rows per point
         self.t_m2l = t_m2l
         self._cache = {}
 
@@ -108,6 +122,19 @@ class KAFMM:
 
     def _pinv(self, kind: str, lv: int) -> np.ndarray:
         key = ("pinv", kind, lv)
+        if key not in self._cache and self.ml == "stokes_pvel":
+            # StokesPVel mixes degrees (p and the q-term of u fall as 1/r^2, the f-term of u as
+            # 1/r): the pseudo-inverse is taken for the unit box in scaled units, check values
+            # [h p, u] times h and equivalent densities [f, q / h] (h: half-width at level lv),
+            # so its cutoff does not depend on the level
+            h = self.L / float(1 << (lv + 1))
+            z = np.zeros(3)
+            ck, ek = ("uc", "ue") if kind == "up" else ("dc", "de")
+            Ku = ml_matrix(self.ml, ALPHA[ck] * self.unit, ALPHA[ek] * self.unit)
+            P = np.linalg.pinv(Ku, rcond=self.rcond)
+            chk_scale = np.tile([h, 1.0, 1.0, 1.0], self.n)
+            eq_scale = np.tile([1.0, 1.0, 1.0, h], self.n)
+            self._cache[key] = h * eq_scale[:, None] * P * chk_scale[None, :]
         if key not in self._cache:
             z = np.zeros(3)
             if kind == "up":
@@ -148,6 +175,8 @@ class KAFMM:
             kern = {"stokeslet_g": "stokeslet", "rpy_g": "rpy", "stokeslet_reg_g": "stokeslet_reg"}[pr]
             g = D.direct(kern, chk, y, s)
             return g[:, :3].reshape(-1, 1)
+        if pr == "stokes_dl_pv":
+            return D.direct("stokes_dl", chk, y, s).reshape(-1, 1)
         f = s[:, :3]
         out = np.zeros((len(chk), 4))
         for j in range(3):
@@ -165,6 +194,8 @@ class KAFMM:
             return D.direct("laplace", x, eq, dens[:, 0])
         if pr == "laplace_qd":
             return D.direct("laplace_pgradgrad", x, eq, dens[:, 0])
+        if pr == "stokes_dl_pv":
+            return D.direct("stokes_pvel", x, eq, dens.reshape(-1, 4))
         if pr in ("stokeslet_g", "stokeslet_reg_g"):
             return D.direct("stokeslet", x, eq, dens.reshape(-1, 3))
         if pr == "rpy_g":
@@ -187,7 +218,7 @@ class KAFMM:
     def _src_to_targets(self, x, y, s) -> np.ndarray:
         kern = {"laplace": "laplace", "stokeslet_g": "stokeslet", "stokeslet_l4": "stokeslet",
                 "rpy_g": "rpy", "rpy_l4": "rpy", "stokeslet_reg_g": "stokeslet_reg",
-                "laplace_qd": "laplace_qd"}[self.problem]
+                "laplace_qd": "laplace_qd", "stokes_dl_pv": "stokes_dl"}[self.problem]
         return D.direct(kern, x, y, s)
 
     def _shift(self, dens, c_from, c_to) -> np.ndarray:

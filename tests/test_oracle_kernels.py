@@ -365,3 +365,34 @@ def test_laplace_charge_dipole_gradients_and_hessian():
         for (i, j), k in hidx.items():
             assert np.isclose(H[i, j], g[k], rtol=1e-6, atol=1e-8)
         assert abs(g[4] + g[7] + g[9]) < 1e-12 * np.abs(g[4:]).max()
+
+
+def test_stokes_pvel_pressure_source_and_stokes_equation():
+    """StokesPVel [f, q] -> [p, u] (Eqs. stkslp, stkslvel): with q = 0 the velocity is the
+    Stokeslet's and the pressure is -sum_j d_j (f_j / (4 pi r)) (from the Laplace oracle);
+    the flow out of any sphere around the source is -q / 2 (the net flow a double layer
+    leaves, -1/2 tr D, is matched by q = tr D); lap u = grad p and div u = 0 off the source."""
+    rng = np.random.default_rng(51)
+    y = rng.random((3, 3))
+    sv = rng.standard_normal((3, 4))
+    x = np.array([[1.4, 0.9, -0.5], [-0.3, 1.7, 0.8]])
+    f_only = sv.copy()
+    f_only[:, 3] = 0
+    g = D.direct("stokes_pvel", x, y, f_only)
+    assert np.allclose(g[:, 1:], D.direct("stokeslet", x, y, sv[:, :3]), rtol=1e-13, atol=0)
+    for k, xt in enumerate(x):
+        p_ref = -sum(D.direct("laplace_pgradgrad", xt[None], y, sv[:, j])[0, 1 + j] for j in range(3))
+        assert np.isclose(g[k, 0], p_ref, rtol=1e-13)
+    one = np.zeros((1, 3))
+    src = np.array([[0.7, -0.4, 1.1, 2.3]])
+    for R in (0.3, 2.5):
+        pts, n, w = sphere_quadrature(R)
+        u = D.direct("stokes_pvel", pts, one, src)[:, 1:]
+        assert abs(np.sum(w * np.sum(u * n, axis=1)) + 0.5 * src[0, 3]) < 1e-10
+    xt = np.array([0.5, -0.3, 0.4])
+    fun = lambda z: D.direct("stokes_pvel", z[None], y, sv)[0]
+    lap = fd_laplacian(lambda z: fun(z)[1:], xt)
+    gp = fd_grad(lambda z: fun(z)[:1], xt)[0]
+    assert np.allclose(lap, gp, rtol=1e-5, atol=1e-6)
+    J = fd_grad(lambda z: fun(z)[1:], xt)
+    assert abs(np.trace(J)) < 1e-6 * np.abs(J).max()

@@ -43,8 +43,13 @@ typedef struct kafmm_plan_s* kafmm_plan_t;
  *   KAFMM_RPY        [f, b] -> [u, lap u],   u = (1 + b^2/6 lap) G f             k_s=4, k_t=6
  *                    (Eqs. RPYflow, RPYkernel; source radius b per point; Table tab:ktab_rpy)
  *   KAFMM_STOKES_DL  D -> [p, u],            Eqs. stkdlp, stkdlvel, D_jk at 3j+k k_s=9, k_t=4
- *                    (Sec. II.C).  Only the near field (U list) is evaluated for this kernel:
- *                    kafmm_eval requires KAFMM_OPT_NEAR_ONLY = 1, otherwise KAFMM_ERR_ARG.
+ *                    (Sec. II.C, Table tab:ktab_stkdlpvelgrad): the double-layer kernel from
+ *                    the sources; the StokesPVel kernel G^P ([f, q] -> [p, u], Eqs. stkslp,
+ *                    stkslvel: the fluid source q carries the net flow -1/2 tr D) between and
+ *                    from the equivalent surfaces (4 values per surface point).  Check values
+ *                    are kept as [h p, u] per box of half-width h, so the translations stay
+ *                    level-independent.  Open boundary only (KAFMM_ERR_ARG with
+ *                    KAFMM_BC_PXYZ).
  *   KAFMM_STOKES_REG [f, eps] -> u,          regularized Stokeslet               k_s=4, k_t=3
  *                    (Sec. II.B, Table tab:ktab_reg): the flow of f spread by the blob
  *                    15 eps^4 / (8 pi (r^2 + eps^2)^{7/2}),

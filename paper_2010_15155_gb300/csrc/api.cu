@@ -59,9 +59,11 @@ static void configure(Plan& P) {
       P.ml_stokes = 1;
       P.D = 3;
       break;
-    default:  // double layer: near field only
+    default:  // double layer D -> [p, u] on the StokesPVel table (Table tab:ktab_stkdlpvelgrad)
       P.ks = 9;
       P.kt = 4;
+      P.ml_stokes = 2;
+      P.D = 4;
       break;
   }
   P.n = 6 * (P.p - 1) * (P.p - 1) + 2;
@@ -83,7 +85,7 @@ static bool is_host_ptr(const void* p) {
 }
 
 static int ensure_ops(Plan& P) {
-  if (P.ops_ready || P.kernel == KAFMM_STOKES_DL) return 0;
+  if (P.ops_ready) return 0;
   int rc = build_operators(P);
   if (rc) return rc;
   extern bool tc_supported(Plan & P);
@@ -122,7 +124,8 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
     return KAFMM_ERR_ARG;
   }
   *out = nullptr;
-  if ((int)kernel < 0 || (int)kernel > 5 || (kernel == KAFMM_LAPLACE_QD && bc == KAFMM_BC_PXYZ) || (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ) || p < 2 ||
+  if ((int)kernel < 0 || (int)kernel > 5 ||
+      ((kernel == KAFMM_LAPLACE_QD || kernel == KAFMM_STOKES_DL) && bc == KAFMM_BC_PXYZ) || (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ) || p < 2 ||
       p > 16 || q < 1 || q > 4096) {
     g_err = "kafmm_plan: invalid kernel, boundary condition, order (2..16) or leaf size (1..4096)";
     return KAFMM_ERR_ARG;
@@ -294,8 +297,6 @@ extern "C" int kafmm_eval(kafmm_plan_t pl, const void* s, void* g, int dtype) {
   if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "kafmm_eval before kafmm_set_points");
   if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || (P.tree.n_src > 0 && !s) || (P.tree.n_trg > 0 && !g))
     return fail(P, KAFMM_ERR_ARG, "kafmm_eval: bad arguments");
-  if (P.kernel == KAFMM_STOKES_DL && !P.near_only)
-    return fail(P, KAFMM_ERR_ARG, "the double-layer kernel is evaluated with KAFMM_OPT_NEAR_ONLY = 1");
   int rc = ensure_ops(P);
   if (rc) return rc;
   size_t es = dtype == KAFMM_F64 ? 8 : 4;
@@ -608,7 +609,6 @@ extern "C" int kafmm_get_operator(kafmm_plan_t pl, int slot, double* out) {
   if (!out || slot < 0 || slot >= N_OPS) return fail(P, KAFMM_ERR_ARG, "bad operator slot");
   int rc = ensure_ops(P);
   if (rc) return rc;
-  if (P.kernel == KAFMM_STOKES_DL) return fail(P, KAFMM_ERR_STATE, "no operators for this kernel");
   size_t RR = (size_t)P.R * P.R;
   if (P.fp64()) {
     CKP(cudaMemcpy(out, P.ops64.as<double>() + RR * slot, sizeof(double) * RR, cudaMemcpyDeviceToHost));

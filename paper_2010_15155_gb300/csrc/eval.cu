@@ -95,9 +95,9 @@ struct S2CArgs {
 template <class T, int PR>
 __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
   using T4 = typename V4<T>::type;
-  constexpr int C = ProbInfo<PR>::C, D = ProbInfo<PR>::D;
+  constexpr int C = ProbInfo<PR>::C, D = ProbInfo<PR>::D, NV = ProbInfo<PR>::NV;
   constexpr int CH = 256;
-  __shared__ T4 sp[CH], sv[CH];
+  __shared__ T4 sp[CH], sv[CH * NV];
   int b = a.boxes[blockIdx.x];
   T cx, cy, cz, r;
   box_centre<T>(a.t, b, a.geo.L, a.geo.org, cx, cy, cz, r);
@@ -134,14 +134,24 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
           p.y = p.y + oy;
           p.z = p.z + oz;
           sp[j] = p;
-          sv[j] = a.val[c0 + j];
+#pragma unroll
+          for (int qv = 0; qv < NV; ++qv) sv[j * NV + qv] = a.val[(int64_t)(c0 + j) * NV + qv];
         }
         __syncthreads();
         if (i < a.n) {
           for (int j = 0; j < cn; ++j) {
-            T4 y = sp[j], v = sv[j];
+            T4 y = sp[j], v = sv[j * NV];
             T r0 = px - y.x, r1 = py - y.y, r2 = pz - y.z;
-            if (PR == P_LAP) {
+            if (PR == P_DL) {   // S->M, S->L: the double-layer kernel K, [p, u] (p doubled: 1/(8 pi) below)
+              T4 v1 = sv[j * NV + 1], v2 = sv[j * NV + 2];
+              T Dm[9] = {v.x, v.y, v.z, v.w, v1.x, v1.y, v1.z, v1.w, v2.x};
+              T tmp[4] = {0, 0, 0, 0};
+              dl_st<T>(r0, r1, r2, Dm, tmp);
+              acc[0] += T(2) * tmp[0];
+              acc[1] += tmp[1];
+              acc[2] += tmp[2];
+              acc[3] += tmp[3];
+            } else if (PR == P_LAP) {
               lap_st<T>(r0, r1, r2, v.x, acc);
             } else if (PR == P_LAPQD) {   // S->M, S->L: L for the charge, L^D for the dipole
               T rr = r0 * r0 + r1 * r1 + r2 * r2;
@@ -172,7 +182,8 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
       }
     }
     if (i < a.n) {
-      T sc = (PR == P_STK_G || PR == P_RPY_G || PR == P_REG_G) ? T(1.0 / (8.0 * PI)) : T(1.0 / (4.0 * PI));
+      T sc = (PR == P_STK_G || PR == P_RPY_G || PR == P_REG_G || PR == P_DL) ? T(1.0 / (8.0 * PI))
+                                                                             : T(1.0 / (4.0 * PI));
       T* out = a.check + (int64_t)b * a.R * C;
 #pragma unroll
       for (int d = 0; d < D; ++d)
@@ -180,6 +191,9 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
         for (int c = 0; c < C; ++c) {
           int64_t idx = (int64_t)(i * D + d) * C + c;
           T v = acc[d * C + c] * sc;
+          // StokesPVel check values are stored as [h p, u] (h: box half-width), which makes
+          // the translations level-independent (p falls as 1/r^2, u as 1/r)
+          if (PR == P_DL && d == 0) v *= r;
           if (a.mode == 0)
             out[idx] = v;
           else
@@ -210,6 +224,7 @@ struct GemmArgs {
   const int32_t* vtab;
   int mode, R;
   int op, scale_r;
+  int qscale4;         // StokesPVel table: rows 4k+3 (q) of a scaled apply get the half-width again
 };
 
 template <int C>
@@ -454,6 +469,7 @@ __global__ void __launch_bounds__(256, M2L ? 1 : 2) k_gemm(GemmArgs<T> a) {
       if (b < 0) continue;
       T* o = a.out + ((int64_t)b * R + row) * C + c;
       T v = alph[bj] * acc[i][j];
+      if (a.qscale4 && (row & 3) == 3) v *= alph[bj];
       if (accumulate)
         *o += v;
       else
@@ -505,6 +521,8 @@ __device__ inline void far_eval(T xl, T yl, T zl, const typename V4<T>::type& p,
     acc[2] = fmaf(r2, tq, fmaf(q.z, ir, acc[2]));
   } else if (PR == P_LAP) {
     lap_st<T>(r0, r1, r2, q.x, acc);
+  } else if (PR == P_DL) {   // M->T, L->T: StokesPVel from the equivalent [f, q]
+    pvel_st<T>(r0, r1, r2, q.x, q.y, q.z, q.w, acc);
   } else if (PR == P_LAPQD) {   // M->T, L->T: equivalent charges, L + grad L + grad grad L
     lapqd_st<T, false>(r0, r1, r2, q.x, T(0), T(0), T(0), acc);
   } else if (PR == P_STK_L4 || PR == P_RPY_L4) {
@@ -612,6 +630,11 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
             q.y = dp[1];
             q.z = dp[2];
             q.w = 0;
+          } else if (D == 4) {   // StokesPVel: [f, q]
+            q.x = dp[0];
+            q.y = dp[1];
+            q.z = dp[2];
+            q.w = dp[3];
           } else {
             q.x = dp[0];
             q.y = q.z = q.w = 0;
@@ -992,7 +1015,7 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
 template <class T, int PR>
 static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
   using T4 = typename V4<T>::type;
-  constexpr int KT = ProbInfo<PR>::KT, C = ProbInfo<PR>::C, NV = ProbInfo<PR>::NV;
+  constexpr int KT = ProbInfo<PR>::KT, C = ProbInfo<PR>::C, D = ProbInfo<PR>::D, NV = ProbInfo<PR>::NV;
   Tree& T_ = P.tree;
   cudaStream_t st = P.stream;
   WorkLists& W = P.wl;
@@ -1052,6 +1075,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
     constexpr bool TC_OK = sizeof(T) == 4 && (C == 4 || C == 1);
     const bool tc = TC_OK && P.use_tc;
     GemmArgs<T> ga;
+    ga.qscale4 = 0;
     ga.t = tv;
     ga.geo = geo;
     ga.ops = ops;
@@ -1076,6 +1100,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       ga.out = out;
       ga.op = op;
       ga.scale_r = write == TCW_SCALE;
+      ga.qscale4 = write == TCW_SCALE && D == 4;
       ga.tiles = tiles;
       if (mode == TCM_M2L)
         KL k_gemm<T, C, true><<<dim3(n, rb), blk, 0, st>>>(ga);
@@ -1095,6 +1120,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       ga.out = P.dn_check.as<T>();
       ga.op = OP_PER;
       ga.scale_r = 0;
+      ga.qscale4 = 0;
       ga.tiles = P.tiles.as<int4>() + W.root[0];
       KL k_gemm<T, C, false><<<dim3(1, rb), blk, 0, st>>>(ga);
     }

@@ -125,6 +125,7 @@ struct Args {
   // TC_M2L tiles of one parent neighbour (tile.w = g + 1): box j of the tile writes partial
   // part[tile.x + j] of dn (R x CH floats each) instead of its own box
   const int* part;
+  int qrow4;              // StokesPVel table, TC_SCALE: rows 4k+3 (q) take the half-width twice
 };
 
 // Slots of a mode (upper bound of the slot index), the operator of slot s in the tensor map
@@ -740,8 +741,12 @@ __global__ void __launch_bounds__(THREADS, 1)
               if (sbox[qc * 32 + t] < 0) continue;
               float* o = dst1 + (int64_t)sout[qc * 32 + t] * R + row;
               float v = x[t];
-              if (a.write == TC_ADD) v += *o;
-              else if (a.write == TC_SCALE) v *= 0.5f * sside[qc * 32 + t];
+              if (a.write == TC_ADD) {
+                v += *o;
+              } else if (a.write == TC_SCALE) {
+                const float h = 0.5f * sside[qc * 32 + t];
+                v *= (a.qrow4 && (row & 3) == 3) ? h * h : h;
+              }
               *o = v;
             }
           }
@@ -945,6 +950,7 @@ int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* 
   a.part_stride = nsplit > 1 ? part_stride : 0;
   a.nsplit = nsplit;
   a.part = grouped ? reinterpret_cast<const int*>(P.m2l_part_sorted) : nullptr;
+  a.qrow4 = P.D == 4 ? 1 : 0;
   a.tiles = tiles;
   a.boxlist = boxlist;
   a.vtab = P.tree.vtab.as<int32_t>();

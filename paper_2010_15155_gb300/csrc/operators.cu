@@ -36,10 +36,12 @@ std::vector<double> unit_surface(int m) {
 }
 
 // K[i][j] (R x R): target points ct + at * s_i, source points cs + as * s_j.
+// ML kernels: stokes = 0 Laplace (1 x 1 per point pair), 1 Stokeslet G (3 x 3), 2 StokesPVel
+// G^P (4 x 4: rows p, u; columns f, q; Eqs. stkslp, stkslvel).
 __global__ void k_fill_kernel_matrix(const double* __restrict__ unit, int n, int stokes, double ctx,
                                      double cty, double ctz, double at, double csx, double csy,
                                      double csz, double as, double* __restrict__ K) {
-  int R = stokes ? 3 * n : n;
+  int R = stokes == 2 ? 4 * n : (stokes ? 3 * n : n);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
        e += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(e / n), j = (int)(e % n);
@@ -50,6 +52,16 @@ __global__ void k_fill_kernel_matrix(const double* __restrict__ unit, int n, int
     double rn = sqrt(rr);
     if (!stokes) {
       K[(int64_t)i * R + j] = 1.0 / (4.0 * PI * rn);
+    } else if (stokes == 2) {
+      double r[3] = {r0, r1, r2};
+      double inv = 1.0 / (8.0 * PI * rn), inv3 = inv / rr;
+      for (int b = 0; b < 3; ++b) K[(int64_t)(4 * i) * R + 4 * j + b] = 2.0 * r[b] * inv3;
+      K[(int64_t)(4 * i) * R + 4 * j + 3] = 0.0;
+      for (int a2 = 0; a2 < 3; ++a2) {
+        for (int b = 0; b < 3; ++b)
+          K[(int64_t)(4 * i + 1 + a2) * R + 4 * j + b] = (a2 == b ? inv : 0.0) + r[a2] * r[b] * inv3;
+        K[(int64_t)(4 * i + 1 + a2) * R + 4 * j + 3] = -r[a2] * inv3;
+      }
     } else {
       double r[3] = {r0, r1, r2};
       double inv = 1.0 / (8.0 * PI * rn), inv3 = inv / rr;
@@ -57,6 +69,16 @@ __global__ void k_fill_kernel_matrix(const double* __restrict__ unit, int n, int
         for (int b = 0; b < 3; ++b)
           K[(int64_t)(3 * i + a) * R + 3 * j + b] = (a == b ? inv : 0.0) + r[a] * r[b] * inv3;
     }
+  }
+}
+
+// Multiplies every 4th row (rows = 1, starting at first) or column (rows = 0) of the R x R
+// matrix K by f: the StokesPVel p rows or q columns.
+__global__ void k_scale_every4(double* __restrict__ K, int R, int rows, int first, double f) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)R * R;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / R), j = (int)(e % R);
+    if (((rows ? i : j) & 3) == first) K[e] *= f;
   }
 }
 
@@ -419,9 +441,14 @@ int build_operators(Plan& P) {
     double cx = (c & 1) ? 1.0 : -1.0, cy = (c & 2) ? 1.0 : -1.0, cz = (c & 4) ? 1.0 : -1.0;
     KL k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, 2.0 * ALPHA_UC, cx, cy, cz,
                                             ALPHA_UE, K);
+    // StokesPVel, check values stored as [h p, u]: the parent's p rows carry h = 2 (the
+    // child's h = 1 cancels in its pseudo-inverse)
+    if (stokes == 2) KL k_scale_every4<<<g, 256, 0, st>>>(K, R, 1, 0, 2.0);
     compose(OP_UP1, OP_UP2, 1.0, O + RR * (OP_M2M + c));
     KL k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, cx, cy, cz, ALPHA_DC, 0, 0, 0,
                                             2.0 * ALPHA_DE, K);
+    // StokesPVel: the parent's equivalent q is its scaled q times h = 2
+    if (stokes == 2) KL k_scale_every4<<<g, 256, 0, st>>>(K, R, 0, 3, 2.0);
     compose(OP_DN1, OP_DN2, 2.0, O + RR * (OP_L2L + c));
   }
   if (P.bc == KAFMM_BC_PXYZ) {  // root far images, composed with the upward pseudo-inverse

@@ -21,8 +21,10 @@ template <>
 struct ProbInfo<P_RPY_L4> { static constexpr int KT = 6, C = 4, D = 1, NV = 1; };
 template <>
 struct ProbInfo<P_RPY_G> { static constexpr int KT = 6, C = 1, D = 3, NV = 1; };
+// The double layer runs on the StokesPVel table: [f, q] per equivalent point, [p, u] per check
+// point (D = 4 rows per surface point).
 template <>
-struct ProbInfo<P_DL> { static constexpr int KT = 4, C = 1, D = 1, NV = 3; };
+struct ProbInfo<P_DL> { static constexpr int KT = 4, C = 1, D = 4, NV = 3; };
 template <>
 struct ProbInfo<P_REG_G> { static constexpr int KT = 3, C = 1, D = 3, NV = 1; };
 template <>
@@ -169,6 +171,20 @@ __device__ inline void rpy_st(T r0, T r1, T r2, T f0, T f1, T f2, T b, T* acc) {
   acc[3] += l0;
   acc[4] += l1;
   acc[5] += l2;
+}
+
+// StokesPVel (Eqs. stkslp, stkslvel) from an equivalent point's [f, q]:
+//   4 pi p = (r.f) / r^3 (acc[0]),  8 pi u = f / r + r (r.f) / r^3 - r q / r^3 (acc[1..3]).
+template <class T>
+__device__ inline void pvel_st(T r0, T r1, T r2, T f0, T f1, T f2, T q, T* acc) {
+  T ir = inv_r(r0 * r0 + r1 * r1 + r2 * r2);
+  T ir3 = ir * ir * ir;
+  T rf = (r0 * f0 + r1 * f1 + r2 * f2) * ir3;
+  T g = rf - q * ir3;
+  acc[0] += rf;
+  acc[1] += f0 * ir + r0 * g;
+  acc[2] += f1 * ir + r1 * g;
+  acc[3] += f2 * ir + r2 * g;
 }
 
 // Stokes double layer: 4 pi p = -3 (r.D.r)/r^5 + tr D / r^3 ; 8 pi u = -3 r (r.D.r) / r^5.

@@ -127,6 +127,7 @@ def test_near_field_matches_oracle(kernel, prec):
     ("rpy_g", "rpy", K.ML_G, 1500, 4, 32),
     ("stokeslet_reg_g", "stokeslet_reg", K.ML_G, 1500, 4, 32),
     ("laplace_qd", "laplace_qd", K.ML_L4, 3000, 6, 40),
+    ("stokes_dl_pv", "stokes_dl", K.ML_L4, 1500, 6, 40),
 ])
 def test_fp64_gpu_kafmm_matches_cpu_kafmm(problem, kernel, variant, n, p, q):
     if problem == "laplace":
@@ -210,6 +211,7 @@ def test_mixed_tensor_core_form_matches_fp64_form(n, p, q):
     ("stokeslet", "pxyz", 8, K.TC_AUTO),      # periodic G table (root operator on CUDA cores)
     ("rpy", "open", 6, K.TC_AUTO),            # RPY on the G table
     ("laplace_qd", "open", 8, K.TC_AUTO),     # charges + dipoles -> phi, grad, Hessian
+    ("stokes_dl", "open", 8, K.TC_AUTO),      # double layer on the StokesPVel table, R = 4n
 ])
 def test_mixed_tensor_core_single_column_tables_match_fp64_form(kernel, bc, p, split):
     """Single-column ML tables (Laplace; the Stokeslet G table, open and periodic) with the

@@ -64,14 +64,21 @@ typedef struct kafmm_plan_s* kafmm_plan_t;
  *                    source, phi = q/(4 pi r) + d.r/(4 pi r^3); outputs phi, d_x phi, d_y phi,
  *                    d_z phi, then the Hessian xx xy xz yy yz zz.  L and L^D from the sources,
  *                    charges on the equivalent surfaces (Laplace table).  Open boundary only
- *                    (KAFMM_ERR_ARG with KAFMM_BC_PXYZ). */
+ *                    (KAFMM_ERR_ARG with KAFMM_BC_PXYZ).
+ *   KAFMM_STOKES_PVEL [f, q] -> [p, u],      StokesPVel G^P                      k_s=4, k_t=4
+ *                    (Sec. II.C, Eqs. stkslp, stkslvel): force f and fluid source q (twice
+ *                    the fluid removed) to pressure and velocity,
+ *                    p = r.f/(4 pi r^3), u = G f - r q/(8 pi r^3); G^P for all interactions,
+ *                    check values kept as [h p, u] as for KAFMM_STOKES_DL.  Open boundary
+ *                    only. */
 typedef enum {
   KAFMM_LAPLACE = 0,
   KAFMM_STOKESLET = 1,
   KAFMM_RPY = 2,
   KAFMM_STOKES_DL = 3,
   KAFMM_STOKES_REG = 4,
-  KAFMM_LAPLACE_QD = 5
+  KAFMM_LAPLACE_QD = 5,
+  KAFMM_STOKES_PVEL = 6
 } kafmm_kernel;
 
 /* Boundary conditions (Sec. III.B).  KAFMM_BC_PXYZ: triply periodic in the cube

@@ -63,6 +63,8 @@ PROBLEMS = {
     # Stokes double layer D -> [p, u], Table tab:ktab_stkdlpvelgrad: K from S, the StokesPVel
     # kernel G^P ([f, q] -> [p, u]) between and from the equivalent surfaces
     "stokes_dl_pv": (9, 4, "stokes_pvel", 1),
+    # StokesPVel [f, q] -> [p, u] (Sec. II.C): G^P for all interactions
+    "stokes_pvel": (4, 4, "stokes_pvel", 1),
 }
 
 
@@ -175,8 +177,9 @@ class KAFMM:
             kern = {"stokeslet_g": "stokeslet", "rpy_g": "rpy", "stokeslet_reg_g": "stokeslet_reg"}[pr]
             g = D.direct(kern, chk, y, s)
             return g[:, :3].reshape(-1, 1)
-        if pr == "stokes_dl_pv":
-            return D.direct("stokes_dl", chk, y, s).reshape(-1, 1)
+        if pr in ("stokes_dl_pv", "stokes_pvel"):
+            kern = "stokes_dl" if pr == "stokes_dl_pv" else "stokes_pvel"
+            return D.direct(kern, chk, y, s).reshape(-1, 1)
         f = s[:, :3]
         out = np.zeros((len(chk), 4))
         for j in range(3):
@@ -194,7 +197,7 @@ class KAFMM:
             return D.direct("laplace", x, eq, dens[:, 0])
         if pr == "laplace_qd":
             return D.direct("laplace_pgradgrad", x, eq, dens[:, 0])
-        if pr == "stokes_dl_pv":
+        if pr in ("stokes_dl_pv", "stokes_pvel"):
             return D.direct("stokes_pvel", x, eq, dens.reshape(-1, 4))
         if pr in ("stokeslet_g", "stokeslet_reg_g"):
             return D.direct("stokeslet", x, eq, dens.reshape(-1, 3))
@@ -218,7 +221,8 @@ class KAFMM:
     def _src_to_targets(self, x, y, s) -> np.ndarray:
         kern = {"laplace": "laplace", "stokeslet_g": "stokeslet", "stokeslet_l4": "stokeslet",
                 "rpy_g": "rpy", "rpy_l4": "rpy", "stokeslet_reg_g": "stokeslet_reg",
-                "laplace_qd": "laplace_qd", "stokes_dl_pv": "stokes_dl"}[self.problem]
+                "laplace_qd": "laplace_qd", "stokes_dl_pv": "stokes_dl",
+                "stokes_pvel": "stokes_pvel"}[self.problem]
         return D.direct(kern, x, y, s)
 
     def _shift(self, dens, c_from, c_to) -> np.ndarray:

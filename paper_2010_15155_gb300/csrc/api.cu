@@ -53,6 +53,12 @@ static void configure(Plan& P) {
       P.ks = 4;
       P.kt = 10;
       break;
+    case KAFMM_STOKES_PVEL:  // [f, q] -> [p, u], G^P for every interaction (Sec. II.C)
+      P.ks = 4;
+      P.kt = 4;
+      P.ml_stokes = 2;
+      P.D = 4;
+      break;
     case KAFMM_STOKES_REG:  // [f, eps] -> u on the G table (Table tab:ktab_reg)
       P.ks = 4;
       P.kt = 3;
@@ -124,8 +130,9 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
     return KAFMM_ERR_ARG;
   }
   *out = nullptr;
-  if ((int)kernel < 0 || (int)kernel > 5 ||
-      ((kernel == KAFMM_LAPLACE_QD || kernel == KAFMM_STOKES_DL) && bc == KAFMM_BC_PXYZ) || (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ) || p < 2 ||
+  if ((int)kernel < 0 || (int)kernel > 6 ||
+      ((kernel == KAFMM_LAPLACE_QD || kernel == KAFMM_STOKES_DL || kernel == KAFMM_STOKES_PVEL) &&
+       bc == KAFMM_BC_PXYZ) || (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ) || p < 2 ||
       p > 16 || q < 1 || q > 4096) {
     g_err = "kafmm_plan: invalid kernel, boundary condition, order (2..16) or leaf size (1..4096)";
     return KAFMM_ERR_ARG;

@@ -40,7 +40,10 @@ __global__ void k_prep_src(const Tin* __restrict__ s, const uint32_t* __restrict
   using T4 = typename V4<T>::type;
   constexpr int KS =
       PR == P_LAP ? 1
-                  : (PR == P_DL ? 9 : ((PR == P_RPY_L4 || PR == P_RPY_G || PR == P_REG_G || PR == P_LAPQD) ? 4 : 3));
+                  : (PR == P_DL ? 9
+                                : ((PR == P_RPY_L4 || PR == P_RPY_G || PR == P_REG_G || PR == P_LAPQD || PR == P_PVEL)
+                                       ? 4
+                                       : 3));
   constexpr int NV = ProbInfo<PR>::NV;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -151,6 +154,13 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
               acc[1] += tmp[1];
               acc[2] += tmp[2];
               acc[3] += tmp[3];
+            } else if (PR == P_PVEL) {   // S->M, S->L: G^P, [p, u] (p doubled: 1/(8 pi) below)
+              T tmp[4] = {0, 0, 0, 0};
+              pvel_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
+              acc[0] += T(2) * tmp[0];
+              acc[1] += tmp[1];
+              acc[2] += tmp[2];
+              acc[3] += tmp[3];
             } else if (PR == P_LAP) {
               lap_st<T>(r0, r1, r2, v.x, acc);
             } else if (PR == P_LAPQD) {   // S->M, S->L: L for the charge, L^D for the dipole
@@ -182,8 +192,9 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
       }
     }
     if (i < a.n) {
-      T sc = (PR == P_STK_G || PR == P_RPY_G || PR == P_REG_G || PR == P_DL) ? T(1.0 / (8.0 * PI))
-                                                                             : T(1.0 / (4.0 * PI));
+      T sc = (PR == P_STK_G || PR == P_RPY_G || PR == P_REG_G || PR == P_DL || PR == P_PVEL)
+                 ? T(1.0 / (8.0 * PI))
+                 : T(1.0 / (4.0 * PI));
       T* out = a.check + (int64_t)b * a.R * C;
 #pragma unroll
       for (int d = 0; d < D; ++d)
@@ -193,7 +204,7 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
           T v = acc[d * C + c] * sc;
           // StokesPVel check values are stored as [h p, u] (h: box half-width), which makes
           // the translations level-independent (p falls as 1/r^2, u as 1/r)
-          if (PR == P_DL && d == 0) v *= r;
+          if ((PR == P_DL || PR == P_PVEL) && d == 0) v *= r;
           if (a.mode == 0)
             out[idx] = v;
           else
@@ -521,7 +532,7 @@ __device__ inline void far_eval(T xl, T yl, T zl, const typename V4<T>::type& p,
     acc[2] = fmaf(r2, tq, fmaf(q.z, ir, acc[2]));
   } else if (PR == P_LAP) {
     lap_st<T>(r0, r1, r2, q.x, acc);
-  } else if (PR == P_DL) {   // M->T, L->T: StokesPVel from the equivalent [f, q]
+  } else if (PR == P_DL || PR == P_PVEL) {   // M->T, L->T: StokesPVel from the equivalent [f, q]
     pvel_st<T>(r0, r1, r2, q.x, q.y, q.z, q.w, acc);
   } else if (PR == P_LAPQD) {   // M->T, L->T: equivalent charges, L + grad L + grad grad L
     lapqd_st<T, false>(r0, r1, r2, q.x, T(0), T(0), T(0), acc);
@@ -743,6 +754,8 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
               lap_st<T>(r0, r1, r2, v.x, tmp);
             } else if (PR == P_LAPQD) {
               lapqd_st<T, true>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
+            } else if (PR == P_PVEL) {
+              pvel_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
             } else if (PR == P_STK_L4 || PR == P_STK_G) {
               stk_st<T>(r0, r1, r2, v.x, v.y, v.z, tmp);
             } else if (PR == P_REG_G) {   // S->T: the regularized kernel of the source's eps
@@ -1214,6 +1227,8 @@ int evaluate(Plan& P, const void* s, void* g, int dtype) {
     pr = P_REG_G;
   else if (P.kernel == KAFMM_LAPLACE_QD)
     pr = P_LAPQD;
+  else if (P.kernel == KAFMM_STOKES_PVEL)
+    pr = P_PVEL;
   else
     pr = P_DL;
   (void)dtype;
@@ -1227,6 +1242,7 @@ int evaluate(Plan& P, const void* s, void* g, int dtype) {
     case P_RPY_G: return run_eval<T, P_RPY_G>(P, s, sd, g);  \
     case P_REG_G: return run_eval<T, P_REG_G>(P, s, sd, g);  \
     case P_LAPQD: return run_eval<T, P_LAPQD>(P, s, sd, g);  \
+    case P_PVEL: return run_eval<T, P_PVEL>(P, s, sd, g);    \
     default: return run_eval<T, P_DL>(P, s, sd, g);          \
   }
   if (P.fp64()) {

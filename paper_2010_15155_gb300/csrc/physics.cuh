@@ -7,7 +7,7 @@ namespace kafmm {
 
 // Problem = kernel + ML-tree table.
 enum Prob { P_LAP = 0, P_STK_L4 = 1, P_STK_G = 2, P_RPY_L4 = 3, P_RPY_G = 4, P_DL = 5, P_REG_G = 6,
-            P_LAPQD = 7 };
+            P_LAPQD = 7, P_PVEL = 8 };
 
 template <int PR>
 struct ProbInfo;
@@ -29,6 +29,8 @@ template <>
 struct ProbInfo<P_REG_G> { static constexpr int KT = 3, C = 1, D = 3, NV = 1; };
 template <>
 struct ProbInfo<P_LAPQD> { static constexpr int KT = 10, C = 1, D = 1, NV = 1; };
+template <>
+struct ProbInfo<P_PVEL> { static constexpr int KT = 4, C = 1, D = 4, NV = 1; };
 
 template <class T>
 struct V4;
@@ -210,7 +212,7 @@ __device__ inline T out_scale(int k) {
   if (PR == P_LAP || PR == P_LAPQD) return f4;
   if (PR == P_STK_L4 || PR == P_STK_G || PR == P_REG_G) return f8;
   if (PR == P_RPY_L4 || PR == P_RPY_G) return k < 3 ? f8 : f4;
-  return k == 0 ? f4 : f8;  // DL
+  return k == 0 ? f4 : f8;  // DL, StokesPVel: [p, u]
 }
 
 }  // namespace kafmm

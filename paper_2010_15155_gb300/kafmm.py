@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkafmm.so")
 
 # enums of include/kafmm.h
-LAPLACE, STOKESLET, RPY, STOKES_DL, STOKES_REG, LAPLACE_QD = 0, 1, 2, 3, 4, 5
+LAPLACE, STOKESLET, RPY, STOKES_DL, STOKES_REG, LAPLACE_QD, STOKES_PVEL = 0, 1, 2, 3, 4, 5, 6
 BC_OPEN, BC_PXYZ = 0, 3
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN, OPT_TC_SPLIT = 1, 2, 3, 4, 5, 6
@@ -26,7 +26,7 @@ OPT_SYNC, OPT_TC_STAGES, OPT_TC_RANGES, OPT_RPY_CONTACT, OPT_TC_TILING = 7, 8, 9
 TC_TF32X3, TC_BF16X3, TC_AUTO = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 ML_G, ML_L4 = 0, 1
-KDIM = {LAPLACE: (1, 1), STOKESLET: (3, 3), RPY: (4, 6), STOKES_DL: (9, 4), STOKES_REG: (4, 3), LAPLACE_QD: (4, 10)}
+KDIM = {LAPLACE: (1, 1), STOKESLET: (3, 3), RPY: (4, 6), STOKES_DL: (9, 4), STOKES_REG: (4, 3), LAPLACE_QD: (4, 10), STOKES_PVEL: (4, 4)}
 ERRORS = {-1: "KAFMM_ERR_ARG", -2: "KAFMM_ERR_DOMAIN", -3: "KAFMM_ERR_CUDA",
           -4: "KAFMM_ERR_TIMEOUT", -5: "KAFMM_ERR_NOMEM", -6: "KAFMM_ERR_STATE"}
 

@@ -19,7 +19,7 @@ from oracle.tree import Tree  # noqa: E402
 from paper_2010_15155_gb300 import kafmm as K  # noqa: E402
 
 KERN = {"laplace": K.LAPLACE, "stokeslet": K.STOKESLET, "rpy": K.RPY, "stokes_dl": K.STOKES_DL,
-        "stokeslet_reg": K.STOKES_REG, "laplace_qd": K.LAPLACE_QD}
+        "stokeslet_reg": K.STOKES_REG, "laplace_qd": K.LAPLACE_QD, "stokes_pvel": K.STOKES_PVEL}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -100,7 +100,7 @@ def _near_oracle(kernel, pts, s, q):
 
 
 @pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "rpy", "stokes_dl", "stokeslet_reg",
-                                    "laplace_qd"])
+                                    "laplace_qd", "stokes_pvel"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_near_field_matches_oracle(kernel, prec):
     n, q = 3000, 50
@@ -128,6 +128,7 @@ def test_near_field_matches_oracle(kernel, prec):
     ("stokeslet_reg_g", "stokeslet_reg", K.ML_G, 1500, 4, 32),
     ("laplace_qd", "laplace_qd", K.ML_L4, 3000, 6, 40),
     ("stokes_dl_pv", "stokes_dl", K.ML_L4, 1500, 6, 40),
+    ("stokes_pvel", "stokes_pvel", K.ML_L4, 1500, 6, 40),
 ])
 def test_fp64_gpu_kafmm_matches_cpu_kafmm(problem, kernel, variant, n, p, q):
     if problem == "laplace":
@@ -174,9 +175,10 @@ def test_fp32_form_matches_fp64_form(kernel, variant):
 
 
 def test_errors_are_reported_not_trapped():
-    with pytest.raises(K.KafmmError) as e:   # dipole sums need a surface term when periodic
-        K.Plan(K.LAPLACE_QD, p=4, q=32, bc=K.BC_PXYZ)
-    assert e.value.code == -1
+    for kern in (K.LAPLACE_QD, K.STOKES_DL, K.STOKES_PVEL):   # open boundary only
+        with pytest.raises(K.KafmmError) as e:
+            K.Plan(kern, p=4, q=32, bc=K.BC_PXYZ)
+        assert e.value.code == -1
     plan = K.Plan(K.STOKESLET, p=4, q=32, precision=K.PREC_FP32)
     bad = torch.tensor([[0.5, 0.5, 1.5], [0.1, 0.2, 0.3]], dtype=torch.float32, device="cuda")
     with pytest.raises(K.KafmmError) as e:
@@ -212,6 +214,7 @@ def test_mixed_tensor_core_form_matches_fp64_form(n, p, q):
     ("rpy", "open", 6, K.TC_AUTO),            # RPY on the G table
     ("laplace_qd", "open", 8, K.TC_AUTO),     # charges + dipoles -> phi, grad, Hessian
     ("stokes_dl", "open", 8, K.TC_AUTO),      # double layer on the StokesPVel table, R = 4n
+    ("stokes_pvel", "open", 10, K.TC_AUTO),   # [f, q] -> [p, u], BF16x3
 ])
 def test_mixed_tensor_core_single_column_tables_match_fp64_form(kernel, bc, p, split):
     """Single-column ML tables (Laplace; the Stokeslet G table, open and periodic) with the

@@ -94,9 +94,13 @@ typedef enum { KAFMM_F32 = 0, KAFMM_F64 = 1 } kafmm_dtype;
 enum {
   /* Arithmetic of the evaluation (default KAFMM_PREC_MIXED):
    *   KAFMM_PREC_FP64  -- every step in FP64 (the plain reference form);
-   *   KAFMM_PREC_FP32  -- FP32 everywhere, M->L on CUDA cores;
-   *   KAFMM_PREC_MIXED -- FP32 near field and surface matvecs, M->L on tcgen05 tensor
-   *                       cores in split BF16x3 with FP32 accumulation. */
+   *   KAFMM_PREC_FP32  -- FP32 everywhere, every gather-GEMM on CUDA cores;
+   *   KAFMM_PREC_MIXED -- FP32 near field and source/target kernels; the gather-GEMMs on
+   *                       tcgen05 tensor cores with FP32 accumulation: M->L in split BF16x3
+   *                       or TF32x3 (KAFMM_OPT_TC_SPLIT), M->M, L->L and the pseudo-inverse
+   *                       factors in TF32x3.  Tables on the tensor cores: the four-channel
+   *                       Laplace table and single-column tables with rows per box a multiple
+   *                       of 8 (G, Laplace, StokesPVel for even p); others stay on CUDA cores. */
   KAFMM_OPT_PRECISION = 1,
   /* ML-tree kernel table of the Stokeslet and RPY problems (default KAFMM_ML_L4):
    *   KAFMM_ML_G  -- the Stokeslet G on M and L points (Tables tab:ktab_rpy, tab:ktab_reg);
@@ -292,7 +296,8 @@ int kafmm_phase_times(kafmm_plan_t plan, double* t, int n);
 int kafmm_get_counters(kafmm_plan_t plan, int64_t* c, int n);
 
 /* Copies one precomputed translation operator to the host as FP64 (row-major R x R, R = the
- * ML rows of the plan: 6(p-1)^2+2, times 3 for the Stokeslet table).  slot: 0..342 M->L by
+ * ML rows of the plan: 6(p-1)^2+2, times 3 for the Stokeslet G table, times 4 for the
+ * StokesPVel table).  slot: 0..342 M->L by
  * offset (ox+3) + 7(oy+3) + 49(oz+3); 343..350 M->M by child octant; 351..358 L->L by child
  * octant; 359/360 the upward pseudo-inverse factors S^+U^T and V; 361/362 the downward ones;
  * 363 the periodic far-image operator.  All are composed with the pseudo-inverse and

@@ -34,7 +34,10 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     lib.kafmm_last_error.restype = ctypes.c_char_p
     lib.kafmm_last_error.argtypes = [ctypes.c_void_p]
     out = ctypes.c_void_p(1)
-    for args in [(7, 0, 8, 64), (1, 1, 8, 64), (1, 0, 1, 64), (1, 0, 8, 0), (1, 0, 17, 64)]:
+    # kernel out of range, PX boundary, p or q out of range, and the open-boundary-only
+    # kernels (double layer, charges + dipoles, StokesPVel) with the triply periodic one
+    for args in [(7, 0, 8, 64), (1, 1, 8, 64), (1, 0, 1, 64), (1, 0, 8, 0), (1, 0, 17, 64),
+                 (3, 3, 8, 64), (5, 3, 8, 64), (6, 3, 8, 64)]:
         assert lib.kafmm_plan(*args, ctypes.byref(out)) == -1
         assert out.value is None
         assert len(lib.kafmm_last_error(None)) > 0
@@ -48,3 +51,25 @@ def test_python_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(kafmm, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         kafmm.lib()
+
+
+def test_python_constants_match_the_header():
+    """Every KAFMM_* enum value the header declares equals the binding's constant."""
+    from paper_2010_15155_gb300 import kafmm
+    src = open(os.path.join(ROOT, "include", "kafmm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    values = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(KAFMM_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    assert len(values) > 30
+    errors = {v: k for k, v in kafmm.ERRORS.items()}
+    for name, v in values.items():
+        short = name[len("KAFMM_"):]
+        if short.startswith("ERR_"):
+            assert errors[name] == v, name
+        elif short == "OK":
+            assert v == 0
+        elif short in ("LAPLACE", "STOKESLET", "RPY", "STOKES_DL", "STOKES_REG", "LAPLACE_QD",
+                       "STOKES_PVEL"):
+            assert getattr(kafmm, short) == v, name
+            assert v in kafmm.KDIM, name
+        else:
+            assert getattr(kafmm, short) == v, name

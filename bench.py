@@ -155,9 +155,20 @@ def cpu_baseline(max_seconds=15.0):
         if dt > max_seconds / 4 or nt >= N_POINTS:
             break
         nt = min(N_POINTS, int(nt * max(2.0, (max_seconds / 4) / max(dt, 1e-3))))
+    # the same sums on one thread, a sample sized for about min(3 s, max_seconds / 4)
+    t1 = min(3.0, max_seconds / 4)
+    nt1 = int(min(N_POINTS, max(4, nt / dt / max(cores, 1) * t1)))
+    prev = direct.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        direct.direct("stokeslet", pts64[:nt1], pts64, f64)
+        dt1 = time.perf_counter() - t0
+    finally:
+        direct.set_threads(prev)
     return {"value": nt / dt / 1e6, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+            "value_1thread": nt1 / dt1 / 1e6,
             "sample": f"O1 direct FP64 sum, {nt} of {N_POINTS} targets x all sources, "
-                      f"{dt:.2f} s"}
+                      f"{dt:.2f} s on {cores} threads; {nt1} targets in {dt1:.2f} s on 1 thread"}
 
 
 def run_reference(args):
@@ -177,6 +188,7 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "n_points": N_POINTS, "p": P_ORDER, "q": Q_LEAF,
                        "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": v, "unit": "Mpoints/s", "cores": res[-1]["cores"],
+                             "value_1thread": float(np.median([r["value_1thread"] for r in res])),
                              "kind": "oracle", "sample": res[-1]["sample"]},
             "e2e": {"value": v, "unit": "Mpoints/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}

@@ -12,8 +12,24 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define PI 3.14159265358979323846
+
+/* Threads of the OpenMP loops below (n > 0), for timing the sums on one core and on all of
+ * them; returns the previous maximum. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  int prev = omp_get_max_threads();
+  if (n > 0) omp_set_num_threads(n);
+  return prev;
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 /* Laplace single layer, Sec. II.A: L = 1/(4 pi r).  s: [q], g: [phi]. */
 void orc_laplace(const double* x, int64_t nt, const double* y, int64_t ns,

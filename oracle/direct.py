@@ -54,7 +54,14 @@ def lib():
             fn.restype = None
         _lib.orc_rpy_pair.argtypes = [p, ctypes.c_double, ctypes.c_double, p]
         _lib.orc_rpy_pair.restype = None
+        _lib.orc_set_threads.argtypes = [ctypes.c_int]
+        _lib.orc_set_threads.restype = ctypes.c_int
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the direct sums (n > 0); returns the previous maximum."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _f64(a, shape1=None):

@@ -396,3 +396,18 @@ def test_stokes_pvel_pressure_source_and_stokes_equation():
     assert np.allclose(lap, gp, rtol=1e-5, atol=1e-6)
     J = fd_grad(lambda z: fun(z)[1:], xt)
     assert abs(np.trace(J)) < 1e-6 * np.abs(J).max()
+
+
+def test_direct_sums_do_not_depend_on_the_thread_count():
+    """The OpenMP loops split targets only: one thread and all threads give the same bits."""
+    rng = np.random.default_rng(61)
+    y = rng.random((500, 3))
+    f = rng.standard_normal((500, 3))
+    x = rng.random((64, 3))
+    g_all = D.direct("stokeslet", x, y, f)
+    prev = D.set_threads(1)
+    try:
+        g_one = D.direct("stokeslet", x, y, f)
+    finally:
+        D.set_threads(prev)
+    assert np.array_equal(g_all, g_one)

@@ -469,3 +469,38 @@ void orc_ewald_matrix(int kernel, const double* x, int64_t nt, const double* y, 
     }
   }
 }
+
+/* Real-space part of the Ewald sum with the minimum-image convention: for every pair the image
+ * difference d (each component of r moved into [-L/2, L/2]) contributes its erfc term when
+ * |d| < rc <= L/2; every other image lies at least L/2 away, beyond the cutoff.  d = 0 (the
+ * target is the source) takes the regular limit of the n = 0 term, as in the blocks above.
+ * g += sum over such pairs; kernel 0 = Laplace (no constant term here), 1 = Stokeslet. */
+void orc_ewald_real_mi(int kernel, const double* x, int64_t nt, const double* y, int64_t ns,
+                       const double* s, double L, double xi, double rc, double* g) {
+  const double sp = 2.0 * xi / sqrt(PI), rc2 = rc * rc;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t a = 0; a < nt; ++a) {
+    double acc[3] = {0, 0, 0};
+    for (int64_t b = 0; b < ns; ++b) {
+      double d[3];
+      for (int q = 0; q < 3; ++q) {   /* points in one cell: differences in (-L, L) */
+        double r = x[3 * a + q] - y[3 * b + q];
+        d[q] = r > 0.5 * L ? r - L : (r < -0.5 * L ? r + L : r);
+      }
+      double rr = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (rr >= rc2) continue;
+      if (kernel == 0) {
+        acc[0] += s[b] * (rr == 0.0 ? -xi / (2.0 * PI * sqrt(PI)) : erfc(xi * sqrt(rr)) / (4.0 * PI * sqrt(rr)));
+      } else if (rr == 0.0) {
+        for (int p = 0; p < 3; ++p) acc[p] += -2.0 * sp / (8.0 * PI) * s[3 * b + p];
+      } else {
+        double rn = sqrt(rr), e = exp(-xi * xi * rr), ec = erfc(xi * rn);
+        double A = (ec / rn - sp * e) / (8.0 * PI), B = (ec / rn + sp * e) / (8.0 * PI) / rr;
+        double df = d[0] * s[3 * b] + d[1] * s[3 * b + 1] + d[2] * s[3 * b + 2];
+        for (int p = 0; p < 3; ++p) acc[p] += A * s[3 * b + p] + B * d[p] * df;
+      }
+    }
+    int kt = kernel == 0 ? 1 : 3;
+    for (int p = 0; p < kt; ++p) g[kt * a + p] += acc[p];
+  }
+}

@@ -85,3 +85,27 @@ def test_periodic_kafmm_translation_invariance():
     ref = Pd.ewald_sum("stokeslet", pts, pts, s)
     e_fmm = D.rel_l2(g0, ref)
     assert D.rel_l2(g1, g0) < 3 * e_fmm + 1e-12
+
+
+@pytest.mark.parametrize("kernel", ["laplace", "stokeslet"])
+def test_sampled_ewald_equals_converged_ewald_sum(kernel):
+    """The structure-factor Ewald evaluation (used at full size, many sources, few targets)
+    equals the pairwise Ewald sum converged to FP64 round-off, on targets that are sources
+    (self images by the regular limit) and on targets that are not."""
+    rng = np.random.default_rng(17)
+    n = 300
+    y = rng.random((n, 3))
+    kq = 1 if kernel == "laplace" else 3
+    s = rng.standard_normal((n, kq))
+    s -= s.mean(axis=0)
+    x = np.concatenate([y[:40], rng.random((40, 3))])
+    ref = Pd.ewald_sum(kernel, x, y, s)
+    got = Pd.ewald_sum_sampled(kernel, x, y, s, chunk=64)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-11
+    # a different cell size and split parameter give the same sum (scale and split invariance)
+    got2 = Pd.ewald_sum_sampled(kernel, 2.0 * x, 2.0 * y, s, L=2.0, xi_l=11.0, kmax=18)
+    scale = 0.5   # both kernels are homogeneous of degree -1
+    assert np.linalg.norm(got2 - scale * ref) / np.linalg.norm(ref) < 1e-11
+    # the cheaper split of the full-size checks: truncation erfc(4) ~ 1.5e-8
+    got3 = Pd.ewald_sum_sampled(kernel, x, y, s, xi_l=8.0, kmax=12)
+    assert np.linalg.norm(got3 - ref) / np.linalg.norm(ref) < 1e-7

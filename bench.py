@@ -45,10 +45,9 @@ WORKLOAD = "stokeslet_uniform_256k_p10_q128_l4"
 # pair in the leaf kernel (stk_st): 3 sub, r^2 (5), rsqrt, ir^3 (2), r.f (5), scale (1),
 # 3 x (mul + FMA + FMA = 5) -> 29.
 FLOP_ST_PAIR = 29
-# DRAM bytes (read + written) of one M->L launch of this workload in the mixed form, from the ncu
-# capture summarised in profiles/m2l_tc_stokeslet_uniform_256k_p10.md (set to None when the
-# kernel changes until it is captured again)
-M2L_DRAM_BYTES = 878.991872e6 + 672.660736e6
+# DRAM bytes (read + written) of one M->L launch of this workload in the mixed form, taken from
+# an ncu capture of the current kernel; None until the kernel in use has been captured
+M2L_DRAM_BYTES = None
 
 
 def _env_rank():
@@ -139,6 +138,36 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_peaks():
+    """Rates measured on this GPU by the library's micro-benchmarks (kafmm_measure_peak)."""
+    from paper_2010_15155_gb300 import kafmm as K
+    out = {}
+    for what, name in ((K.PEAK_FFMA, "fp32_fma_tflops"), (K.PEAK_RSQRT, "mufu_rsqrt_tops"),
+                       (K.PEAK_DFMA, "fp64_fma_tflops"), (K.PEAK_MMA_TF32, "tf32_mma_tflops"),
+                       (K.PEAK_MMA_BF16, "bf16_mma_tflops")):
+        out[name] = K.kafmm_measure_peak(what)[0] / 1e12
+    return out
+
+
+def cpu_baseline_o2(n=32768):
+    """The oracle's plain CPU KAFMM (numpy, FP64) on a bounded problem of the same kind:
+    n uniform points, the same order, leaf size and table; the operator precompute runs first
+    and is not timed."""
+    from oracle.kafmm import KAFMM
+    pts, f = workloads.stokes_uniform(n, seed=1, dtype=np.float32)
+    p64, f64 = pts.astype(np.float64), f.astype(np.float64)
+    F = KAFMM("stokeslet_l4", P_ORDER, Q_LEAF)
+    t0 = time.perf_counter()
+    F.evaluate(p64[:2048], f64[:2048])   # builds and caches the operators
+    t_ops = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    F.evaluate(p64, f64)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt / 1e6, "unit": "Mpoints/s", "kind": "oracle O2 (plain CPU KAFMM, numpy)",
+            "sample": f"{n} uniform points, p = {P_ORDER}, q = {Q_LEAF}, four-channel table: "
+                      f"{dt:.1f} s per evaluation (operators cached; their build took {t_ops:.1f} s)"}
+
+
 def cpu_baseline(max_seconds=15.0):
     """The oracle's direct FP64 sum on the host cores over a bounded sample of targets of the
     same workload (all sources); scaled to Mpoints/s (targets per second)."""
@@ -183,7 +212,10 @@ def run_reference(args):
     v = float(np.median([r["value"] for r in res]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpoints/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": N_POINTS / (v * 1e6) * 1e3, "higher_is_better": True,
+            "ms_per_step": N_POINTS / (v * 1e6) * 1e3,
+            "ms_per_step_note": "extrapolated: N divided by the rate measured on the sampled "
+                                "targets of each step (see cpu_baseline.sample)",
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_points": N_POINTS, "p": P_ORDER, "q": Q_LEAF,
                        "l2": "n/a (CPU)"},
@@ -213,14 +245,24 @@ def run_gpu(args):
     g = torch.empty((N_POINTS, 3), dtype=torch.float32, device=dev)
     prec = {"mixed": K.PREC_MIXED, "fp32": K.PREC_FP32, "fp64": K.PREC_FP64}[args.precision]
     split = {"tf32x3": K.TC_TF32X3, "bf16x3": K.TC_BF16X3, "auto": K.TC_AUTO}[args.tc_split]
+    mpk = measured_peaks()
+    # plan: operator precompute (SVD pseudo-inverses, translation operators), not in a step
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
     plan = K.Plan(K.STOKESLET, p=P_ORDER, q=Q_LEAF, precision=prec, variant=K.ML_L4,
-                  stream=stream.cuda_stream, tc_split=split)
+                  stream=stream.cuda_stream, tc_split=split, compress=not args.no_compress)
+    R = 6 * (P_ORDER - 1) ** 2 + 2
+    K.kafmm_get_operator(plan.h, 0, R)   # builds the operators
+    torch.cuda.synchronize(dev)
+    plan_ms = (time.perf_counter() - t0) * 1e3
     K.kafmm_set_option(plan.h, K.OPT_TC_TILING, args.tc_tiling)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    # accuracy against the plain FP64 GPU form (outside the timed region)
-    err = None
+    # accuracy against the plain FP64 GPU form and against the oracle's direct FP64 sum on
+    # 4096 sampled targets (outside the timed region)
+    err, err_o1 = None, None
     if rank == 0 and not args.skip_check:
+        from oracle import direct as D
         ref_plan = K.Plan(K.STOKESLET, p=P_ORDER, q=Q_LEAF, precision=K.PREC_FP64,
                           variant=K.ML_L4, stream=stream.cuda_stream)
         ref_plan.set_points(y.double())
@@ -229,6 +271,12 @@ def run_gpu(args):
         plan.eval(s, g)
         torch.cuda.synchronize(dev)
         err = float(torch.linalg.norm(g.double() - gref) / torch.linalg.norm(gref))
+        idx = workloads.sample_targets(N_POINTS, 4096)
+        p64, f64 = pts.astype(np.float64), f.astype(np.float64)
+        o1 = D.direct("stokeslet", p64[idx], p64, f64)
+        err_o1 = {"form": D.rel_l2(g.double().cpu().numpy()[idx], o1),
+                  "fp64_form": D.rel_l2(gref.cpu().numpy()[idx], o1),
+                  "targets": "4096 sampled (oracle O1, direct FP64 sum over all sources)"}
         ref_plan.close()
         del gref
 
@@ -285,35 +333,51 @@ def run_gpu(args):
     info = plan.info()
     ph = {k: float(np.median([p[k] for p in phases])) for k in phases[0]}
     eval_only = eval_graph_timing(plan, s, g, stream, flush, args.steps)
+    st_ms = near_only_timing(plan, s, g, flush)
     peaks, src = _peaks()
-    # dominant kernel: M->L.  Algorithmic flops per launch = V translations x 2 n^2 x 4 columns.
+    cnt = K.kafmm_get_counters(plan.h)
+    # dominant kernel: M->L.  Algorithmic flops per launch = V translations x 2 rows x k x 4
+    # channels: rows x k = r_dn x r_up in compressed coordinates (the singular values the two
+    # pseudo-inverses keep), n x n on check potentials.
     n = 6 * (P_ORDER - 1) ** 2 + 2
-    m2l_flops = info["n_v"] * 2.0 * n * n * 4
-    m2l_s = ph["m2l"] * 1e-3
-    split_used = K.kafmm_get_counters(plan.h)["tc_split"]
-    if args.precision == "mixed" and plan_uses_tc(plan):
-        # TF32 dense peak = measured bf16 burst x nominal tf32/bf16 ratio (1.1 / 2.25 PFLOP/s);
-        # achieved counts useful flops only (the three split products are not counted).
-        bound, unit = "tensor", "TFLOP/s"
-        peak = peaks["bf16_tflops"] * (1.1 / 2.25) if split_used == "tf32x3" else \
-            peaks["bf16_tflops"]
-        achieved = m2l_flops / m2l_s / 1e12
-        peak_note = (f"{split_used}: {'tf32 = bf16 x 1.1/2.25' if split_used == 'tf32x3' else 'bf16'}"
-                     f" dense burst, {src}; useful flops (split products not counted, max frac 1/3)")
-    elif args.precision == "fp64":
-        # FP64 on the CUDA cores: GB300's nominal dense FP64 rate (not measured on this machine)
-        bound, unit = "alu", "TFLOP/s"
-        peak = 1.25
-        achieved = m2l_flops / m2l_s / 1e12
-        peak_note = "FP64, nominal 1.25 TFLOP/s (no measured FP64 peak in the peaks file)"
+    if cnt["compressed_rows"]:
+        m2l_flops = info["n_v"] * 2.0 * cnt["rank_dn"] * cnt["rank_up"] * 4
+        m2l_exec = info["n_v"] * 2.0 * cnt["compressed_rows"] ** 2 * 4 * 3
+        coords = (f"compressed coordinates: {cnt['rank_dn']} x {cnt['rank_up']} per translation "
+                  f"(padded {cnt['compressed_rows']})")
     else:
-        # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x max SM clock
-        bound, unit = "alu", "TFLOP/s"
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        m2l_flops = info["n_v"] * 2.0 * n * n * 4
+        m2l_exec = info["n_v"] * 2.0 * n * ((n + 63) // 64 * 64) * 4 * 3
+        coords = f"check potentials: {n} x {n} per translation"
+    m2l_s = ph["m2l"] * 1e-3
+    split_used = cnt["tc_split"]
+    if args.precision == "mixed" and plan_uses_tc(plan):
+        # achieved counts useful flops only (the three split products and the padding are not
+        # counted); tf32x3 is measured against the TF32 MMA rate of kafmm_measure_peak
+        bound, unit = "tensor", "TFLOP/s"
+        if split_used == "tf32x3":
+            peak = mpk["tf32_mma_tflops"]
+            pk = "tf32 tcgen05 MMA rate measured by kafmm_measure_peak"
+        else:
+            peak = peaks["bf16_tflops"]
+            pk = f"bf16 dense burst (cuBLAS), {src}"
         achieved = m2l_flops / m2l_s / 1e12
-        peak_note = "FP32 CUDA cores, 152 SM x 128 x 2 x max clock"
-    st_gflops = info["near_pairs"] * FLOP_ST_PAIR / (ph["leaves"] * 1e-3) / 1e9
-    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        peak_note = (f"{split_used}: {pk}; useful flops ({coords}; split products not counted, "
+                     f"max frac 1/3); executed incl. padding {m2l_exec / m2l_s / 1e12:.0f} TFLOP/s")
+    elif args.precision == "fp64":
+        bound, unit = "alu", "TFLOP/s"
+        peak = mpk["fp64_fma_tflops"]
+        achieved = m2l_flops / m2l_s / 1e12
+        peak_note = "FP64 FMA rate measured by kafmm_measure_peak"
+    else:
+        bound, unit = "alu", "TFLOP/s"
+        peak = mpk["fp32_fma_tflops"]
+        achieved = m2l_flops / m2l_s / 1e12
+        peak_note = "FP32 FMA rate measured by kafmm_measure_peak"
+    # near field alone (the leaf kernel in near-only mode: U-list S->T, no L->T)
+    st_gflops = info["near_pairs"] * FLOP_ST_PAIR / (st_ms * 1e-3) / 1e9
+    fp32_peak = mpk["fp32_fma_tflops"]
+    rsqrt_frac = info["near_pairs"] / (st_ms * 1e-3) / (mpk["mufu_rsqrt_tops"] * 1e12)
     # tree build + lists: ~48 algorithmic bytes per point (coordinates read 12, keys 8 + 8,
     # permutation 4 + 4, sorted coordinates 12) against the measured HBM copy bandwidth
     tree_gbs = N_POINTS * 48 / ((ph["tree"] + ph["lists"]) * 1e-3) / 1e9
@@ -332,11 +396,17 @@ def run_gpu(args):
                    "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "rel_l2_vs_fp64": err,
+        "rel_l2_vs_o1": err_o1,
+        "plan_ms": plan_ms,
         "st_gflops": st_gflops,
         "st_roofline": {"bound": "alu", "achieved": st_gflops / 1e3, "peak": fp32_peak,
                         "unit": "TFLOP/s", "frac": st_gflops / 1e3 / fp32_peak,
-                        "note": "U-list pairs x 29 flop over the whole leaf phase (which also "
-                                "runs L->T); FP32 peak 152 SM x 128 x 2 x max clock"},
+                        "ms": st_ms, "rsqrt_frac": rsqrt_frac,
+                        "note": "U-list pairs x 29 flop over the near-field-only leaf kernel "
+                                "(CUDA events); peak = FP32 FMA rate measured by "
+                                "kafmm_measure_peak; rsqrt_frac = pairs/s over the measured "
+                                "MUFU rsqrt rate (one per pair)"},
+        "measured_peaks": mpk,
         "tree_roofline": {"bound": "hbm", "achieved": tree_gbs, "peak": peaks["hbm_gbs"],
                           "unit": "GB/s", "frac": tree_gbs / peaks["hbm_gbs"],
                           "note": "48 B/point over tree + lists time; launch-latency bound"},
@@ -346,6 +416,9 @@ def run_gpu(args):
         "roofline": {"bound": bound, "kernel": "m2l", "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak,
                      "traffic": M2L_DRAM_BYTES if args.precision == "mixed" else None,
+                     "traffic_source": "DRAM bytes of one M->L launch from an ncu capture of the "
+                                       "current kernel" if M2L_DRAM_BYTES else
+                                       "not captured for the current kernel",
                      "peak_source": peak_note},
         "e2e": {"value": world * N_POINTS / (e2e_ms * 1e-3) / 1e6, "unit": "Mpoints/s",
                 "h2d_bytes_per_step": int(pts.nbytes + f.nbytes),
@@ -355,6 +428,7 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"]["o2"] = cpu_baseline_o2()
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -767,6 +841,23 @@ def eval_graph_timing(plan, s, g, stream, flush, steps):
             "how": "kafmm_eval captured once in a CUDA graph and replayed (tree kept)"}
 
 
+def near_only_timing(plan, s, g, flush, reps=5):
+    """The leaf kernel alone in near-only mode (U-list S->T, no far field): median of its
+    CUDA-event phase time over reps evaluations, L2 flushed before each."""
+    import torch
+
+    from paper_2010_15155_gb300 import kafmm as K
+    K.kafmm_set_option(plan.h, K.OPT_NEAR_ONLY, 1)
+    t = []
+    for i in range(reps):
+        flush.fill_(float(i))
+        K.kafmm_eval(plan.h, s, g, K.F32)
+        t.append(K.kafmm_phase_times(plan.h)["leaves"])
+    torch.cuda.synchronize()
+    K.kafmm_set_option(plan.h, K.OPT_NEAR_ONLY, 0)
+    return float(np.median(t))
+
+
 def plan_uses_tc(plan):
     from paper_2010_15155_gb300 import kafmm as K
     return bool(K.kafmm_get_counters(plan.h)["tensor_core_m2l"])
@@ -789,6 +880,8 @@ def main():
                     choices=["stokeslet", "batched", "periodic", "rpy", "convergence"])
     ap.add_argument("--tc-tiling", type=int, default=0, choices=[0, 1, 2],
                     help="M->L tiling: 0 automatic, 1 whole V lists, 2 per parent neighbour")
+    ap.add_argument("--no-compress", action="store_true",
+                    help="mixed form in check potentials instead of compressed coordinates")
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -160,7 +160,32 @@ enum {
    * compute mostly empty columns (M->L of 2^20 clustered RPY points: 44.7 ms with 1, 22.6 ms
    * with 2; Stokeslet N = 262144 uniform, p = 10: 5.39 -> 4.42 ms).  kafmm_autotune times
    * both. */
-  KAFMM_OPT_TC_TILING = 11
+  KAFMM_OPT_TC_TILING = 11,
+  /* Limit of every device-side wait on an asynchronous copy or a pipeline stage, in
+   * microseconds (default 2,000,000 = 2 s; 1 .. 60,000,000).  A wait that runs out records a
+   * timeout (KAFMM_ERR_TIMEOUT from kafmm_eval or kafmm_status); the kernel then issues no
+   * further copy, waits once more (same limit) for its copies in flight, skips the rest of its
+   * work and returns, so the device stays usable.  No kernel traps. */
+  KAFMM_OPT_WAIT_LIMIT_US = 12,
+  /* Test aid (default -1 = off): a device-side wait that lasted at least this many
+   * microseconds (0: every wait) records a timeout as above but completes normally, so the
+   * results are unchanged while the status reaches the host. */
+  KAFMM_OPT_WAIT_REPORT_US = 13,
+  /* Test aid (default 0): 1 makes every block of the near-field kernel first wait on a barrier
+   * that nothing completes, so the wait runs out after KAFMM_OPT_WAIT_LIMIT_US and the block
+   * takes the wind-down path above (kafmm_eval returns KAFMM_ERR_TIMEOUT; the results of that
+   * call are not valid). */
+  KAFMM_OPT_TEST_STALL = 14,
+  /* Mixed form on the tensor cores (default 1): 1 runs the ML tree in compressed coordinates,
+   * 0 in check potentials (R rows per box).  The pseudo-inverse of Sec. II keeps the r singular
+   * values above its cutoff, and every use of a check potential passes through it, so a box's
+   * state can be its projection on the r leading left singular vectors (U^T times the check
+   * potential) without changing the result in exact arithmetic: M->L, M->M, L->L and the
+   * periodic operator become r x r matrices (r padded to 64; p = 10, Laplace table: 256 instead
+   * of 488 rows, 256 instead of 512 k-values), the leaves' S->M potentials and the X-list
+   * potentials are projected once, and the equivalent densities come from V S^+ applied to the
+   * projections.  Applied at the next kafmm_set_points (operators rebuilt). */
+  KAFMM_OPT_COMPRESS = 15
 };
 enum { KAFMM_TC_TF32X3 = 0, KAFMM_TC_BF16X3 = 1, KAFMM_TC_AUTO = 2 };
 enum { KAFMM_PREC_FP64 = 0, KAFMM_PREC_FP32 = 1, KAFMM_PREC_MIXED = 2 };
@@ -251,16 +276,17 @@ int kafmm_rpy_velocity(kafmm_plan_t plan, const void* s, const void* a, const vo
  * the call: for instance an application whose own pool allocator has reserved the device
  * memory up front, or one that must not trigger the implicit device-wide synchronisation of
  * cudaMalloc / cudaFree while other streams run.  The paper has no counterpart: this is a
- * library convenience.  It calls no cudaMalloc, cudaFree or allocating library routine; its
- * work arrays live in one fixed 32 MiB device array that every GPU loading the library holds
- * until the process exits.  Limit: the work arrays take 32 bytes per source and 8 per target
- * in FP64 (16 and 4 in FP32) plus 2 MiB of cell table, so about 780,000 points of one shared
- * set in FP64 and 1.5 million in FP32; larger sets return KAFMM_ERR_ARG with the sizes in the
- * message (use
- * kafmm_rpy_velocity).  All pointers must be device pointers (host arrays would need staging
- * copies).  The first call on a device looks the array up (once per device, that device
- * current); make that first call before any stream capture.  Every call uses the same array,
- * so calls that overlap on the GPU (other threads, other streams) race. */
+ * library convenience.  It calls no cudaMalloc, cudaFree or allocating library routine
+ * (counter 7 of kafmm_get_counters does not move); its work arrays live in one fixed 32 MiB
+ * device array that every GPU loading the library holds until the process exits.  Limit: the
+ * work arrays take 32 bytes per source and 8 per target in FP64 (16 and 4 in FP32) plus 2 MiB
+ * of cell table, so about 780,000 points of one shared set in FP64 and 1.5 million in FP32;
+ * larger sets return KAFMM_ERR_ARG with the sizes in the message (use kafmm_rpy_velocity).
+ * All pointers must be device pointers (host arrays would need staging copies).  The first
+ * call in a CUDA context (once per device, and again after cudaDeviceReset replaced the
+ * context) looks the array up with that device current; make that first call before any
+ * stream capture.  Every call uses the same array and keeps its contents, so calls that
+ * overlap on the GPU (other threads, other streams) race. */
 int kafmm_rpy_velocity_noalloc(kafmm_plan_t plan, const void* s, const void* a, const void* g,
                                void* ua, int dtype);
 
@@ -287,12 +313,15 @@ int kafmm_get_list(kafmm_plan_t plan, int kind, int64_t* offsets, int32_t* entri
  * back from the tree; the device waits meanwhile).  Host array t[n], up to 8 entries. */
 int kafmm_phase_times(kafmm_plan_t plan, double* t, int n);
 
-/* Counters of the last calls (host array c[n], up to 8 entries): 0 kernel launches of the
+/* Counters of the last calls (host array c[n], up to 12 entries): 0 kernel launches of the
  * last kafmm_set_points, 1 kernel launches of the last kafmm_eval, 2 whether M->L ran on the
  * tcgen05 tensor cores (0/1), 3 launches of set_points + eval, 4 the split format in use
  * (KAFMM_TC_TF32X3 or KAFMM_TC_BF16X3; -1 without tensor cores), 5 the M->L tiling of the
  * current points (1 whole V lists, 2 per parent neighbour; see KAFMM_OPT_TC_TILING), 6 the
- * number of M->L tiles. */
+ * number of M->L tiles, 7 device allocations (cudaMalloc) the library has made in this process
+ * so far, over all plans, 8 rows of the compressed coordinates (0: check potentials; see
+ * KAFMM_OPT_COMPRESS), 9 and 10 the singular values kept by the upward and downward
+ * pseudo-inverses. */
 int kafmm_get_counters(kafmm_plan_t plan, int64_t* c, int n);
 
 /* Copies one precomputed translation operator to the host as FP64 (row-major R x R, R = the
@@ -304,6 +333,15 @@ int kafmm_get_counters(kafmm_plan_t plan, int64_t* c, int n);
  * described in units of the box half-width.  Values come from the plan's precision (FP32
  * plans return their FP32 operators widened). */
 int kafmm_get_operator(kafmm_plan_t plan, int slot, double* out);
+
+/* Measurement aid, not part of the method (the paper has no counterpart): runs one
+ * micro-benchmark on the current CUDA device and writes its rate to *rate (operations per
+ * second) and the duration of the timed launch to *ms (may be NULL).  what: 0 FP32 FMA
+ * (2 flop each), 1 MUFU reciprocal square root (one operation each), 2 FP64 FMA (2 flop each),
+ * 3 tcgen05 MMA kind::tf32 and 4 kind::f16 with bf16 operands (dense flops, M = 128, N = 256,
+ * one CTA per SM).  These are the denominators of the near-field, FP64 and TF32 rooflines.
+ * Returns KAFMM_ERR_ARG for another value of what. */
+int kafmm_measure_peak(int what, double* rate, double* ms);
 
 /* Releases the plan and all device memory it owns. */
 int kafmm_destroy(kafmm_plan_t plan);

@@ -1,5 +1,6 @@
 // C ABI of the evaluator (declared in include/kafmm.h).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdarg>
 #include <cstring>
@@ -9,6 +10,10 @@
 namespace kafmm {
 
 thread_local long long g_launches = 0;
+
+static std::atomic<long long> g_device_allocs{0};
+void count_device_allocation() { g_device_allocs.fetch_add(1, std::memory_order_relaxed); }
+long long device_allocations() { return g_device_allocs.load(std::memory_order_relaxed); }
 
 int fail(Plan& P, int code, const char* fmt, ...) {
   char buf[512];
@@ -202,6 +207,28 @@ extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
       if (value != 1 && value != 2 && value != 4 && value != 8)
         return fail(P, KAFMM_ERR_ARG, "tensor-core slot ranges must be 1, 2, 4 or 8");
       P.tc_ranges = (int)value;
+      return 0;
+    case KAFMM_OPT_WAIT_LIMIT_US:
+      if (value < 1 || value > 60000000)
+        return fail(P, KAFMM_ERR_ARG, "wait limit must be 1 .. 60,000,000 microseconds");
+      P.wait.hard_ns = (unsigned long long)value * 1000ull;
+      return 0;
+    case KAFMM_OPT_WAIT_REPORT_US:
+      if (value < -1 || value > 60000000)
+        return fail(P, KAFMM_ERR_ARG, "wait report threshold must be -1 .. 60,000,000 microseconds");
+      P.wait.report_ns = value < 0 ? ~0ull : (unsigned long long)value * 1000ull;
+      return 0;
+    case KAFMM_OPT_TEST_STALL:
+      if (value < 0 || value > 1) return fail(P, KAFMM_ERR_ARG, "test stall must be 0 or 1");
+      P.stall_test = (int)value;
+      return 0;
+    case KAFMM_OPT_COMPRESS:
+      if (value < 0 || value > 1) return fail(P, KAFMM_ERR_ARG, "compress must be 0 or 1");
+      if (P.compress_opt != (int)value) {
+        P.compress_opt = (int)value;
+        configure(P);
+        P.have_points = false;
+      }
       return 0;
     case KAFMM_OPT_TC_SPLIT:
       if (value != KAFMM_TC_TF32X3 && value != KAFMM_TC_BF16X3 && value != KAFMM_TC_AUTO)
@@ -603,11 +630,15 @@ extern "C" int kafmm_phase_times(kafmm_plan_t pl, double* t, int n) {
 extern "C" int kafmm_get_counters(kafmm_plan_t pl, int64_t* c, int n) {
   PLAN_CHECK(pl);
   if (!c || n < 0) return fail(P, KAFMM_ERR_ARG, "null array");
-  int64_t v[7] = {P.launches_points, P.launches_eval, P.use_tc ? 1 : 0,
-                  P.launches_points + P.launches_eval,
-                  P.use_tc ? (P.tc_split == SPLIT_BF16 ? KAFMM_TC_BF16X3 : KAFMM_TC_TF32X3) : -1,
-                  P.wl.m2l_grouped ? 2 : 1, P.wl.m2l[1] - P.wl.m2l[0]};
-  for (int i = 0; i < n && i < 8; ++i) c[i] = i < 7 ? v[i] : 0;
+  const bool cm = P.use_tc && P.cmp;
+  int64_t v[11] = {P.launches_points, P.launches_eval, P.use_tc ? 1 : 0,
+                   P.launches_points + P.launches_eval,
+                   P.use_tc ? ((cm ? P.tc_split_cm : P.tc_split) == SPLIT_BF16 ? KAFMM_TC_BF16X3
+                                                                               : KAFMM_TC_TF32X3)
+                            : -1,
+                   P.wl.m2l_grouped ? 2 : 1, P.wl.m2l[1] - P.wl.m2l[0], device_allocations(),
+                   cm ? P.rp : 0, cm ? P.r_up : 0, cm ? P.r_dn : 0};
+  for (int i = 0; i < n && i < 12; ++i) c[i] = i < 11 ? v[i] : 0;
   return 0;
 }
 

@@ -14,6 +14,9 @@ namespace kafmm {
 // Count of kernel launches issued by this thread (reported per set_points + eval).
 extern thread_local long long g_launches;
 #define KL ++::kafmm::g_launches,
+// Count of device allocations (cudaMalloc) made by the library in this process.
+long long device_allocations();
+void count_device_allocation();
 
 constexpr int MAX_LEVEL = 20;        // finest octree level; keys carry 20 bits per axis
 constexpr int MAX_LEVELS = MAX_LEVEL + 1;
@@ -45,6 +48,13 @@ constexpr int N_OPS = OP_PER + 1;
 // operators of the non-M->L tensor-core modes (M->M, L->L, pseudo-inverse factors), kept in
 // their own TF32 split array: aux index = slot - OP_M2M
 constexpr int N_AUX = OP_PER - OP_M2M;
+
+// Operators of the compressed coordinates besides M->L: 8 M->M, 8 L->L, the periodic one.
+constexpr int N_CAUX = 17, CAUX_PER = 16;
+
+// Operator sets of the tensor-core gather-GEMM: the dense operators (R x R), the translations
+// between compressed coordinates (rp x rp), compress (rp x R) and decompress (R x rp).
+enum { TCO_DENSE = 0, TCO_CMP = 1, TCO_CIN = 2, TCO_COUT = 3 };
 
 // Split formats of the tensor-core M->L.
 enum { SPLIT_TF32 = 0, SPLIT_BF16 = 1 };
@@ -108,6 +118,7 @@ struct DevBuf {
     if (nbytes <= bytes && p) return cudaSuccess;
     release();
     size_t nb = nbytes < 256 ? 256 : nbytes;
+    count_device_allocation();
     cudaError_t e = cudaMalloc(&p, nb);
     if (e != cudaSuccess) {
       p = nullptr;
@@ -150,21 +161,49 @@ struct HostBuf {
 // bit 2 capacity overflow, bit 3 non-finite value.
 enum { ST_DOMAIN = 1, ST_TIMEOUT = 2, ST_OVERFLOW = 4, ST_NONFINITE = 8 };
 
-// Bounded mbarrier wait used by every kernel that waits on an asynchronous copy.
-__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, unsigned* status) {
+// Limits of the device-side waits (nanoseconds of %globaltimer).  A wait that has not
+// completed after hard_ns gives up: the kernel records ST_TIMEOUT and winds down.  report_ns
+// only reports: a wait that took report_ns or longer records ST_TIMEOUT and still completes
+// normally (a test sets it to 0 to see the status reach the host without changing what runs).
+struct WaitLimits {
+  unsigned long long hard_ns = 2000000000ull;
+  unsigned long long report_ns = ~0ull;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(phase), "r"(100000u)  // suspend up to 0.1 ms per try (woken on completion)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded mbarrier wait: true once the phase completed, false (ST_TIMEOUT recorded) when
+// lim.hard_ns passed first.
+__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, unsigned* status,
+                                         const WaitLimits& lim) {
   uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
-  for (long it = 0; it < (1L << 26); ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(addr), "r"(phase)
-        : "memory");
-    if (ok) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(addr, phase)) {
+      if (lim.report_ns != ~0ull && global_ns() - t0 >= lim.report_ns)
+        atomicOr(status, (unsigned)ST_TIMEOUT);
+      return true;
+    }
+    if (global_ns() - t0 > lim.hard_ns) {
+      atomicOr(status, (unsigned)ST_TIMEOUT);
+      return false;
+    }
   }
-  atomicOr(status, (unsigned)ST_TIMEOUT);
-  return false;
 }
 
 __device__ inline void mbar_init(uint64_t* bar, unsigned count) {

@@ -7,8 +7,8 @@
 
 namespace kafmm {
 
-int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* boxlist,
-                   const float* in, float* out, int op_slot, int write, cudaStream_t st);
+int tc_gemm_launch(Plan& P, int mode, int opset, const int4* tiles, int ntiles, const int* boxlist,
+                   const float* in, float* out, int op, int write, cudaStream_t st);
 // modes and output kinds of tc_gemm_launch (m2l_tc.cu)
 constexpr int TCM_M2L = 0, TCM_M2M = 1, TCM_L2L = 2, TCM_APPLY = 3;
 constexpr int TCW_STORE = 0, TCW_ADD = 1, TCW_SCALE = 2;
@@ -509,6 +509,8 @@ struct LeafArgs {
   const int32_t* w_ent;
   T* g;                              // sorted targets [nt][KT]
   unsigned* status;
+  WaitLimits lim;                    // bounds of the mbarrier waits
+  int stall_test;                    // test aid: first wait on a barrier nothing completes
   int n, R, near_only, kahan;
   int contact;                       // RPY: skip U-list pairs within contact (r <= b_i + b_j)
   int cap;                           // staging capacity in sources
@@ -566,9 +568,9 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
   T4* sp = reinterpret_cast<T4*>(smem_raw);          // [cap]
   T4* sv = sp + a.cap;                                // [cap * NV]
   T* red = reinterpret_cast<T*>(sv + a.cap * NV);     // [LEAF_THREADS * KT]
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar, stall_bar;
   __shared__ int ent_n, ent_cnt[LEAF_MAX_ENT], ent_sc[LEAF_MAX_ENT];
-  __shared__ int next_e, next_s, done;
+  __shared__ int next_e, next_s, done, bail;
 
   int b = a.leaves[blockIdx.x];
   T cx, cy, cz, r;
@@ -576,8 +578,19 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
   int t0 = a.t.tb[b], t1 = a.t.te[b];
   int nt = t1 - t0;
   if (nt <= 0) return;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    if (a.stall_test) mbar_init(&stall_bar, 1);
+    bail = 0;
+  }
   __syncthreads();
+  if (a.stall_test) {
+    // test aid: a wait that nothing completes runs out after the wait limit; the block then
+    // takes the wind-down path (no copy has been issued yet) and leaves without output
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&stall_bar, 0, a.status, a.lim)) bail = 1;
+    __syncthreads();
+    if (bail) return;
+  }
   uint32_t phase = 0;
   int ntp = ((nt + 31) / 32) * 32;
   if (ntp > LEAF_THREADS) ntp = LEAF_THREADS;
@@ -711,8 +724,16 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
       }
       __syncthreads();
       if (done) break;
-      // wait for this batch (bounded)
-      mbar_wait_bounded(&bar, phase, a.status);
+      // wait for this batch (bounded).  On expiry the block issues no further copy, skips the
+      // compute and the output, waits once more (bounded) for the copies of this batch still
+      // in flight, and leaves; the status word carries ST_TIMEOUT to the host.
+      if (!mbar_wait_bounded(&bar, phase, a.status, a.lim)) bail = 1;
+      __syncthreads();
+      if (bail) {
+        if (threadIdx.x == 0) mbar_wait_bounded(&bar, phase, a.status, a.lim);
+        __syncthreads();
+        return;
+      }
       phase ^= 1;
       if (act) {
         int base = 0;
@@ -998,6 +1019,14 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
   for (int b = 0; b < nb; ++b)
     if (leaf[b] && te[b] > tb[b]) by_cls[0].push_back(b);
   add_tiles(W, by_cls, NB, W.pdn);
+  if (P.cmp && P.use_tc) {   // compressed coordinates: S->M results of the leaves, X-list sums
+    for (int b = 0; b < nb; ++b)
+      if (leaf[b]) by_cls[0].push_back(b);
+    add_tiles(W, by_cls, NB, W.cup);
+    for (int b = 0; b < nb; ++b)
+      if (xoff[b + 1] > xoff[b]) by_cls[0].push_back(b);
+    add_tiles(W, by_cls, NB, W.cx);
+  }
   // plain lists: leaves (with targets), boxes with X entries, leaves (S->M, last)
   W.leafbox_off = (int)W.boxlist.size();
   for (int b = 0; b < nb; ++b)
@@ -1023,6 +1052,60 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
                      cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));   // the staging buffers are reused by the next build
   return 0;
+}
+
+// The ML tree in compressed coordinates (mixed form, tensor cores): the upward and downward
+// state of a box is its check potential projected on the leading left singular vectors of the
+// check-to-equivalent matrix, which carries all the pseudo-inverse uses of it (Sec. II: the
+// equivalent density is pinv x check, and every translation starts from an equivalent
+// density).  S->M check potentials of the leaves (already in up_check) are compressed; M->M,
+// the periodic root operator, M->L and L->L act between compressed coordinates; X-list S->L
+// check potentials are compressed and added; the equivalent densities of the W-list boxes and
+// of the leaves come from V S^+ applied to the coordinates (scaled by the half-width).
+template <int PR>
+static int run_compressed(Plan& P, S2CArgs<float, PR>& sa, WorkLists& W, const int* boxlist, int n_sleaves,
+                          const int* sleaves) {
+  cudaStream_t st = P.stream;
+  const int nb = P.tree.nbox;
+  const size_t hat_bytes = sizeof(float) * (size_t)P.rp * P.C * nb;
+  CK(P.up_hat.reserve(hat_bytes));
+  CK(P.dn_hat.reserve(hat_bytes));
+  CK(cudaMemsetAsync(P.dn_hat.p, 0, hat_bytes, st));
+  float* up_check = P.up_check.as<float>();
+  float* dn_check = P.dn_check.as<float>();
+  float* up_hat = P.up_hat.as<float>();
+  float* dn_hat = P.dn_hat.as<float>();
+  auto tcg = [&](int mode, int opset, const int* range, const float* in, float* out, int op, int write) -> int {
+    const int n = range[1] - range[0];
+    if (n <= 0) return 0;
+    const int* bl = mode == TCM_M2L && W.m2l_grouped ? P.m2l_box.as<int>() : boxlist;
+    return tc_gemm_launch(P, mode, opset, P.tiles.as<int4>() + range[0], n, bl, in, out, op, write, st);
+  };
+  (void)n_sleaves;
+  (void)sleaves;
+  int rc = tcg(TCM_APPLY, TCO_CIN, W.cup, up_check, up_hat, 0, TCW_STORE);
+  for (int l = MAX_LEVELS - 1; l >= 0 && !rc; --l)
+    rc = tcg(TCM_M2M, TCO_CMP, W.m2m[l], up_hat, up_hat, 0, TCW_STORE);
+  if (!rc) rc = tcg(TCM_APPLY, TCO_CMP, W.root, up_hat, dn_hat, CAUX_PER, TCW_ADD);
+  if (rc) return rc;
+  cudaEventRecord(P.ev[4], st);
+  rc = tcg(TCM_M2L, TCO_CMP, W.m2l, up_hat, dn_hat, 0, TCW_ADD);
+  if (rc) return rc;
+  cudaEventRecord(P.ev[5], st);
+  if (W.xbox_n > 0) {   // S->L over the X lists on the check surface, then compressed and added
+    CK(cudaMemsetAsync(dn_check, 0, sizeof(float) * (size_t)P.R * P.C * nb, st));
+    sa.boxes = boxlist + W.xbox_off;
+    sa.check = dn_check;
+    sa.mode = 1;
+    KL k_s2check<float, PR><<<W.xbox_n, 128, 0, st>>>(sa);
+    rc = tcg(TCM_APPLY, TCO_CIN, W.cx, dn_check, dn_hat, 1, TCW_ADD);
+  }
+  for (int l = 0; l < MAX_LEVELS && !rc; ++l)
+    rc = tcg(TCM_L2L, TCO_CMP, W.l2l[l], dn_hat, dn_hat, 0, TCW_ADD);
+  if (!rc) rc = tcg(TCM_APPLY, TCO_COUT, W.pup, up_hat, P.up_equiv.as<float>(), 0, TCW_SCALE);
+  if (!rc) rc = tcg(TCM_APPLY, TCO_COUT, W.pdn, dn_hat, P.dn_equiv.as<float>(), 1, TCW_SCALE);
+  CK(cudaGetLastError());
+  return rc;
 }
 
 template <class T, int PR>
@@ -1106,8 +1189,8 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       // grouped M->L tiles index the sorted pair arrays
       const int* bl = mode == TCM_M2L && P.wl.m2l_grouped ? P.m2l_box.as<int>() : boxlist;
       if (tc)
-        return tc_gemm_launch(P, mode, tiles, n, bl, reinterpret_cast<const float*>(in),
-                              reinterpret_cast<float*>(out), op, write, st);
+        return tc_gemm_launch(P, mode, TCO_DENSE, tiles, n, bl, reinterpret_cast<const float*>(in),
+                              reinterpret_cast<float*>(out), op - OP_M2M, write, st);
       ga.mode = mode == TCM_M2L ? GM_M2L : (mode == TCM_M2M ? GM_M2M : (mode == TCM_L2L ? GM_L2L : GM_APPLY));
       ga.in = in;
       ga.out = out;
@@ -1122,46 +1205,56 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       return 0;
     };
     int rc = 0;
-    // M->M, deepest level first
-    for (int l = MAX_LEVELS - 1; l >= 0 && !rc; --l)
-      rc = gemm(TCM_M2M, W.m2m[l], P.up_check.as<T>(), P.up_check.as<T>(), 0, TCW_STORE);
-    if (rc) return rc;
-    // periodic: far images of the root's multipole density -> root's downward check
-    if (W.root[1] > W.root[0]) {
-      ga.mode = GM_APPLY;
-      ga.in = P.up_check.as<T>();
-      ga.out = P.dn_check.as<T>();
-      ga.op = OP_PER;
-      ga.scale_r = 0;
-      ga.qscale4 = 0;
-      ga.tiles = P.tiles.as<int4>() + W.root[0];
-      KL k_gemm<T, C, false><<<dim3(1, rb), blk, 0, st>>>(ga);
+    bool compressed = false;
+    if constexpr (TC_OK) {
+      if (tc && P.cmp) {
+        rc = run_compressed<PR>(P, sa, W, boxlist, n_sleaves, sleaves);
+        if (rc) return rc;
+        compressed = true;
+      }
     }
-    cudaEventRecord(P.ev[4], st);
-    // M->L over the V lists (all levels)
-    rc = gemm(TCM_M2L, W.m2l, P.up_check.as<T>(), P.dn_check.as<T>(), 0, TCW_ADD);
-    if (rc) return rc;
-    cudaEventRecord(P.ev[5], st);
-    // S->L over the X lists
-    if (W.xbox_n > 0) {
-      sa.boxes = boxlist + W.xbox_off;
-      sa.check = P.dn_check.as<T>();
-      sa.mode = 1;
-      KL k_s2check<T, PR><<<W.xbox_n, 128, 0, st>>>(sa);
+    if (!compressed) {
+      // M->M, deepest level first
+      for (int l = MAX_LEVELS - 1; l >= 0 && !rc; --l)
+        rc = gemm(TCM_M2M, W.m2m[l], P.up_check.as<T>(), P.up_check.as<T>(), 0, TCW_STORE);
+      if (rc) return rc;
+      // periodic: far images of the root's multipole density -> root's downward check
+      if (W.root[1] > W.root[0]) {
+        ga.mode = GM_APPLY;
+        ga.in = P.up_check.as<T>();
+        ga.out = P.dn_check.as<T>();
+        ga.op = OP_PER;
+        ga.scale_r = 0;
+        ga.qscale4 = 0;
+        ga.tiles = P.tiles.as<int4>() + W.root[0];
+        KL k_gemm<T, C, false><<<dim3(1, rb), blk, 0, st>>>(ga);
+      }
+      cudaEventRecord(P.ev[4], st);
+      // M->L over the V lists (all levels)
+      rc = gemm(TCM_M2L, W.m2l, P.up_check.as<T>(), P.dn_check.as<T>(), 0, TCW_ADD);
+      if (rc) return rc;
+      cudaEventRecord(P.ev[5], st);
+      // S->L over the X lists
+      if (W.xbox_n > 0) {
+        sa.boxes = boxlist + W.xbox_off;
+        sa.check = P.dn_check.as<T>();
+        sa.mode = 1;
+        KL k_s2check<T, PR><<<W.xbox_n, 128, 0, st>>>(sa);
+      }
+      // L->L, coarsest level first
+      for (int l = 0; l < MAX_LEVELS && !rc; ++l)
+        rc = gemm(TCM_L2L, W.l2l[l], P.dn_check.as<T>(), P.dn_check.as<T>(), 0, TCW_ADD);
+      if (rc) return rc;
+      // equivalent densities where they are evaluated at targets: r * V * ((S^+ U^T) * check),
+      // the two factors applied in turn (tmp = the downward equivalent buffer of the up pass
+      // is not yet used, so the up pass stages through dn_equiv and vice versa through up_equiv)
+      rc = gemm(TCM_APPLY, W.pup, P.up_check.as<T>(), P.dn_equiv.as<T>(), OP_UP1, TCW_STORE);
+      if (!rc) rc = gemm(TCM_APPLY, W.pup, P.dn_equiv.as<T>(), P.up_equiv.as<T>(), OP_UP2, TCW_SCALE);
+      // up_check is no longer needed here
+      if (!rc) rc = gemm(TCM_APPLY, W.pdn, P.dn_check.as<T>(), P.up_check.as<T>(), OP_DN1, TCW_STORE);
+      if (!rc) rc = gemm(TCM_APPLY, W.pdn, P.up_check.as<T>(), P.dn_equiv.as<T>(), OP_DN2, TCW_SCALE);
+      if (rc) return rc;
     }
-    // L->L, coarsest level first
-    for (int l = 0; l < MAX_LEVELS && !rc; ++l)
-      rc = gemm(TCM_L2L, W.l2l[l], P.dn_check.as<T>(), P.dn_check.as<T>(), 0, TCW_ADD);
-    if (rc) return rc;
-    // equivalent densities where they are evaluated at targets: r * V * ((S^+ U^T) * check),
-    // the two factors applied in turn (tmp = the downward equivalent buffer of the up pass
-    // is not yet used, so the up pass stages through dn_equiv and vice versa through up_equiv)
-    rc = gemm(TCM_APPLY, W.pup, P.up_check.as<T>(), P.dn_equiv.as<T>(), OP_UP1, TCW_STORE);
-    if (!rc) rc = gemm(TCM_APPLY, W.pup, P.dn_equiv.as<T>(), P.up_equiv.as<T>(), OP_UP2, TCW_SCALE);
-    // up_check is no longer needed here
-    if (!rc) rc = gemm(TCM_APPLY, W.pdn, P.dn_check.as<T>(), P.up_check.as<T>(), OP_DN1, TCW_STORE);
-    if (!rc) rc = gemm(TCM_APPLY, W.pdn, P.up_check.as<T>(), P.dn_equiv.as<T>(), OP_DN2, TCW_SCALE);
-    if (rc) return rc;
   }
   cudaEventRecord(P.ev[6], st);
   // leaves
@@ -1183,6 +1276,8 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
     la.w_ent = T_.w_ent.as<int32_t>();
     la.g = P.g_sorted.as<T>();
     la.status = T_.status.as<unsigned>();
+    la.lim = P.wait;
+    la.stall_test = P.stall_test;
     la.n = P.n;
     la.R = R;
     la.near_only = P.near_only;

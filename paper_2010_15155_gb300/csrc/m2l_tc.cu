@@ -20,14 +20,15 @@
 // one group.
 //
 // Warp roles (448 threads): 0-3 epilogue (TMEM lane quarters), 4-11 B producers, 12 TMA,
-// 13 TMEM allocation + MMA issue.  Every wait is bounded (2 s of %globaltimer); on expiry the
-// kernel records ST_TIMEOUT and winds down without trapping.
+// 13 TMEM allocation + MMA issue.  Every wait is bounded (%globaltimer, 2 s by default); on
+// expiry the kernel records ST_TIMEOUT and winds down without trapping.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
 
 #include "plan.cuh"
+#include "tcgen05.cuh"
 
 namespace kafmm {
 
@@ -46,7 +47,6 @@ namespace tc {
 // Single-column tables (the Stokeslet G table and the Laplace table, CH = 1): a CTA owns
 // BN = 256 / RB target boxes, one column each, and the B producers copy contiguous k-runs of
 // each source box (no re-reference: those tables have no centre-dependent channel).
-constexpr int BM = 128;
 template <int RB, int SWB, int CH>
 struct Shape {
   static constexpr int BN = 256 / RB, NB = BN / CH;
@@ -78,20 +78,6 @@ constexpr int THREADS = 448;
 constexpr int NPROD = 256;
 constexpr int W_TMA = 12, W_MMA = 13;
 
-// Split formats: an SWB-byte swizzle row holds SWB / ES elements; one MMA consumes MK of them
-// (32 bytes in both formats).
-template <int SPLIT>
-struct Fmt;
-template <>
-struct Fmt<SPLIT_TF32> {  // kind::tf32, K = 8 per instruction
-  static constexpr int ES = 4, MK = 8;
-  static constexpr uint32_t AB = 2;
-};
-template <>
-struct Fmt<SPLIT_BF16> {  // kind::f16 with bf16 operands, K = 16 per instruction
-  static constexpr int ES = 2, MK = 16;
-  static constexpr uint32_t AB = 1;
-};
 constexpr uint32_t TMEM_COLS = 512;         // [0,256) accumulators, [256,512) running sums
 constexpr uint32_t SUM_COL = 256;           // row block r: accumulator r*BN, sum SUM_COL + r*BN
 
@@ -118,7 +104,10 @@ struct Args {
   const int* boxlist;
   const int32_t* vtab;
   unsigned* status;
-  int R, nchunk;
+  WaitLimits lim;
+  // Rout: operator rows = output rows per box; Rin: input rows per box (the k extent); Rop:
+  // rows per operator in the tensor map (Rout, or more with padding)
+  int Rout, Rin, Rop, nchunk;
   int mode, write;
   int op;                 // TC_APPLY: operator index in the tensor map
   int group;              // TC_M2L: k-chunks per TMEM accumulation group
@@ -178,116 +167,30 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float(r);
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded parity wait; returns false (and flags the status word) after ~2 s.
+// Bounded parity wait: false (ST_TIMEOUT recorded, the CTA's bail flag set) once lim.hard_ns
+// passed, or when another warp has already bailed; a wait of lim.report_ns or longer that
+// completes records ST_TIMEOUT too (report only).
 __device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity, unsigned* status,
-                                            int* bail) {
-  uint32_t addr = smem_u32(bar);
-  uint64_t t0 = 0;
-  for (uint32_t it = 0;; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity), "r"(1000000u)  // suspend up to 1 ms per try (woken on completion)
-        : "memory");
-    if (ok) return true;
-    if (*(volatile int*)bail) return false;
-    if ((it & 63) == 0) {
-      uint64_t t = gtimer();
-      if (t0 == 0) t0 = t;
-      if (t - t0 > 2000000000ull) {
+                                            int* bail, const WaitLimits& lim) {
+  const uint32_t addr = smem_u32(bar);
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(addr, parity)) {
+      if (lim.report_ns != ~0ull && global_ns() - t0 >= lim.report_ns)
         atomicOr(status, (unsigned)ST_TIMEOUT);
-        *(volatile int*)bail = 1;
-        return false;
-      }
+      return true;
+    }
+    if (*(volatile int*)bail) return false;
+    if (global_ns() - t0 > lim.hard_ns) {
+      atomicOr(status, (unsigned)ST_TIMEOUT);
+      *(volatile int*)bail = 1;
+      return false;
     }
   }
 }
 
 __device__ __forceinline__ void arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// K-major UMMA shared-memory descriptor (SM100 format, version 1) for SWB-byte swizzled rows:
-// start >> 4, LBO = 16 B (unused for swizzled K-major), SBO = 8 rows x SWB bytes, layout
-// SWIZZLE_128B (2) or SWIZZLE_64B (4).
-template <int SWB>
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)(16 >> 4) << 16;
-  d |= (uint64_t)((8 * SWB) >> 4) << 32;
-  d |= (uint64_t)1 << 46;       // descriptor version
-  d |= (uint64_t)(SWB == 128 ? 2 : 4) << 61;
-  return d;
-}
-
-// Instruction descriptor: D = F32, A/B format (bf16 = 1, tf32 = 2), K-major both, N = 256,
-// M = 128.
-template <int SPLIT, int BN>
-__device__ __forceinline__ constexpr uint32_t idesc() {
-  return (1u << 4) | (Fmt<SPLIT>::AB << 7) | (Fmt<SPLIT>::AB << 10) | ((uint32_t)(BN >> 3) << 17) |
-         ((uint32_t)(BM >> 4) << 24);
-}
-
-template <int SPLIT, int BN>
-__device__ __forceinline__ void mma(uint32_t dt, uint64_t a, uint64_t b, uint32_t acc) {
-  if (SPLIT == SPLIT_TF32)
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-        "l"(a), "l"(b), "r"(idesc<SPLIT, BN>()), "r"(acc)
-        : "memory");
-  else
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-        "l"(a), "l"(b), "r"(idesc<SPLIT, BN>()), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t* r = reinterpret_cast<uint32_t*>(v);
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
-  const uint32_t* r = reinterpret_cast<const uint32_t*>(v);
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
-      "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]),
-      "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]),
-      "r"(r[30]), "r"(r[31])
-      : "memory");
 }
 
 // Read-only 256-bit load of two consecutive float4 (address 32-byte aligned).
@@ -336,7 +239,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int4 tile = a.tiles[blockIdx.x];
   const int cls = tile.z;
   const int grp = a.mode == TC_M2L ? tile.w - 1 : -1;   // parent neighbour, -1 = whole V lists
-  const int R = a.R;
+  const int R = a.Rout, Rin = a.Rin;
   const int row0 = blockIdx.y * (RB * BM);
   // row blocks of this CTA that hold operator rows (the last pair may have only one)
   const int nrb = min(RB, (R - row0 + BM - 1) / BM);
@@ -409,7 +312,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       for (int it = 0; it < total; ++it) {
         int st = it % STAGES;
-        if (it >= STAGES && !wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail)) break;
+        if (it >= STAGES && !wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail, a.lim)) break;
         int s = slot_list[it / nchunk], c = it % nchunk;
         int op = slot_op(a, s, cls);
         unsigned char* base = smem + st * STAGE_BYTES;
@@ -419,7 +322,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                      : "memory");
         for (int r = 0; r < nrb; ++r)
           for (int h = 0; h < 2; ++h) {
-            int y = (op * 2 + h) * R + row0 + r * BM;
+            int y = (op * 2 + h) * a.Rop + row0 + r * BM;
             int x = c * BK;
             asm volatile(
                 "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], "
@@ -457,12 +360,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           cur_slot = s;
         }
         const int k0 = c * BK + wd * 8;
-        const bool kin = k0 < R;   // R a multiple of 8: a lane's 8 k are all in or all out
+        const bool kin = k0 < Rin;   // Rin a multiple of 8: a lane's 8 k are all in or all out
 #pragma unroll
         for (int u = 0; u < UH; ++u) {
           int sb = srcb[h * UH + u];
           if (sb >= 0 && kin) {
-            ld_nc_v8(reinterpret_cast<const float4*>(a.up + (int64_t)sb * R + k0), q[u][0], q[u][1]);
+            ld_nc_v8(reinterpret_cast<const float4*>(a.up + (int64_t)sb * Rin + k0), q[u][0], q[u][1]);
           } else {
             q[u][0] = make_float4(0.f, 0.f, 0.f, 0.f);
             q[u][1] = q[u][0];
@@ -515,7 +418,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         load_half(it, 1, qb);
         int ok_wait = 1;
         if (lane == 0 && it >= STAGES)
-          ok_wait = wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail) ? 1 : 0;
+          ok_wait = wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail, a.lim) ? 1 : 0;
         if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
         store_half(it, 0, qa);
         if (it + 1 < total) load_half(it + 1, 0, qa);
@@ -573,12 +476,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           cur_slot = s;
         }
         const int k0 = c * BK + wd * EPL;
-        const bool kin = k0 < R;   // R and k0 even: a bf16 pair is all in or out
+        const bool kin = k0 < Rin;   // Rin and k0 even: a bf16 pair is all in or out
 #pragma unroll
         for (int u = 0; u < UH; ++u) {
           int sb = srcb[h * UH + u];
           bool ok = sb >= 0 && kin;
-          const float4* p = reinterpret_cast<const float4*>(a.up) + (int64_t)(ok ? sb : 0) * R + k0;
+          const float4* p = reinterpret_cast<const float4*>(a.up) + (int64_t)(ok ? sb : 0) * Rin + k0;
           if (EPL == 2) {
             if (ok) {
               ld_nc_v8(p, q[u][0], q[u][EPL - 1]);
@@ -646,7 +549,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         // lane 0 waits for the stage to be free; the warp leaves the loop together on a timeout
         int ok_wait = 1;
         if (lane == 0 && it >= STAGES)
-          ok_wait = wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail) ? 1 : 0;
+          ok_wait = wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail, a.lim) ? 1 : 0;
         if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
         store_half(it, 0, qa);
         if (it + 1 < total) load_half(it + 1, 0, qa);
@@ -663,13 +566,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       int it = 0;
       for (int gi = 0; gi < ngroups; ++gi) {
-        if (gi > 0 && !wait_parity(&acc_empty, (gi - 1) & 1, a.status, &bail)) break;
+        if (gi > 0 && !wait_parity(&acc_empty, (gi - 1) & 1, a.status, &bail, a.lim)) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         bool ok = true;
         const int it_end = min(total, (gi + 1) * GI);
         for (; it < it_end; ++it) {
           int st = it % STAGES;
-          if (!wait_parity(&full[st], (it / STAGES) & 1, a.status, &bail)) {
+          if (!wait_parity(&full[st], (it / STAGES) & 1, a.status, &bail, a.lim)) {
             ok = false;
             break;
           }
@@ -700,7 +603,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     float x[32], y[32];
     for (int gi = 0; gi < ngroups; ++gi) {
       // lane 0 waits; the warp stays converged for the .sync.aligned TMEM accesses
-      int ok_wait = lane == 0 ? (wait_parity(&acc_full, gi & 1, a.status, &bail) ? 1 : 0) : 0;
+      int ok_wait = lane == 0 ? (wait_parity(&acc_full, gi & 1, a.status, &bail, a.lim) ? 1 : 0) : 0;
       if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       for (int q = 0; q < nrb * (BN / 32); ++q) {   // row block q / (BN / 32), 32 columns each
@@ -855,7 +758,9 @@ bool tc_table(const Plan& P) {
 bool tc_supported(Plan& P) {
   if (P.prec != KAFMM_PREC_MIXED || !tc_table(P) || !P.opstc.p) return false;
   int rows = (P.R + tc::BM - 1) / tc::BM;
-  P.tc_rb = rows % 2 == 0 ? 2 : 1;
+  // compressed coordinates: every operator set shares the tiles, so a CTA always owns two
+  // 128-row blocks (the last CTA of an odd block count runs one)
+  P.tc_rb = P.cmp ? 2 : (rows % 2 == 0 ? 2 : 1);
   P.tc_boxes = 256 / P.tc_rb / P.C;
   int dev = 0, major = 0, minor = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -865,9 +770,10 @@ bool tc_supported(Plan& P) {
   return major == 10 && minor == 3;
 }
 
-// Tensor map over a split operator array [nops][2][R][Rpad] (tf32 or bf16), swb-byte swizzle,
-// boxes of 128 rows x swb bytes.
-static int make_tmap(Plan& P, CUtensorMap* map, void* base, int nops, bool tf32, int swb) {
+// Tensor map over a split operator array of total_rows rows ([op][2][rows][colpad], tf32 or
+// bf16), swb-byte swizzle, boxes of 128 rows x swb bytes.
+static int make_tmap(Plan& P, CUtensorMap* map, void* base, int64_t total_rows, int colpad, bool tf32,
+                     int swb) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -878,8 +784,8 @@ static int make_tmap(Plan& P, CUtensorMap* map, void* base, int nops, bool tf32,
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   int es = tf32 ? 4 : 2;
-  cuuint64_t dims[2] = {(cuuint64_t)P.Rpad, (cuuint64_t)nops * 2 * P.R};
-  cuuint64_t strides[1] = {(cuuint64_t)P.Rpad * es};
+  cuuint64_t dims[2] = {(cuuint64_t)colpad, (cuuint64_t)total_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)colpad * es};
   cuuint32_t box[2] = {(cuuint32_t)(swb / es), tc::BM};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
@@ -891,14 +797,34 @@ static int make_tmap(Plan& P, CUtensorMap* map, void* base, int nops, bool tf32,
   return 0;
 }
 
+// Operator sets of the tensor-core gather-GEMM: the map, the rows per operator, the padded k
+// extent, the input rows per box and the output rows per box.
+struct OpSet {
+  int map, rop, kpad, rin, rout;
+};
+static OpSet op_set(const Plan& P, int opset, bool m2l) {
+  switch (opset) {
+    case TCO_CMP: return {m2l ? 2 : 3, P.rp, P.rp, P.rp, P.rp};
+    case TCO_CIN: return {4, P.rp, P.Rpad, P.R, P.rp};
+    case TCO_COUT: return {5, P.R, P.rp, P.rp, P.R};
+    default: return {m2l ? 0 : 1, P.R, P.Rpad, P.R, P.R};
+  }
+}
+
 static int tc_prepare(Plan& P) {
   if (P.tmap_ready) return 0;
+  const bool ml_tf32 = P.tc_split == SPLIT_TF32, cm_tf32 = P.tc_split_cm == SPLIT_TF32;
   for (int sw = 0; sw < 2; ++sw) {   // 128- and 64-byte swizzled rows
     int swb = sw == 0 ? 128 : 64;
-    int rc = make_tmap(P, reinterpret_cast<CUtensorMap*>(P.tmaps[0][sw]), P.opstc.p, N_M2L,
-                       P.tc_split == SPLIT_TF32, swb);
-    if (rc) return rc;
-    rc = make_tmap(P, reinterpret_cast<CUtensorMap*>(P.tmaps[1][sw]), P.opstc_aux.p, N_AUX, true, swb);
+    auto map = [&](int k) { return reinterpret_cast<CUtensorMap*>(P.tmaps[k][sw]); };
+    int rc = make_tmap(P, map(0), P.opstc.p, (int64_t)N_M2L * 2 * P.R, P.Rpad, ml_tf32, swb);
+    if (!rc) rc = make_tmap(P, map(1), P.opstc_aux.p, (int64_t)N_AUX * 2 * P.R, P.Rpad, true, swb);
+    if (!rc && P.cmp) {
+      rc = make_tmap(P, map(2), P.opstc_cm2l.p, (int64_t)N_M2L * 2 * P.rp, P.rp, cm_tf32, swb);
+      if (!rc) rc = make_tmap(P, map(3), P.opstc_caux.p, (int64_t)N_CAUX * 2 * P.rp, P.rp, true, swb);
+      if (!rc) rc = make_tmap(P, map(4), P.opstc_cin.p, (int64_t)2 * 2 * P.rp, P.Rpad, true, swb);
+      if (!rc) rc = make_tmap(P, map(5), P.opstc_cout.p, (int64_t)2 * 2 * P.R, P.rp, true, swb);
+    }
     if (rc) return rc;
   }
   cudaError_t e = cudaSuccess;
@@ -914,19 +840,20 @@ static int tc_prepare(Plan& P) {
   return 0;
 }
 
-// One gather-GEMM on the tensor cores.  TC_M2L: in = up_check, out = dn_check (stored; the
-// operator in the plan's split format, several offset ranges per tile when the grid is small).
-// Other modes: TF32x3 with the auxiliary operators (op = slot for TC_APPLY), one range.
-int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* boxlist,
-                   const float* in, float* out, int op_slot, int write, cudaStream_t st) {
+// One gather-GEMM on the tensor cores over the operator set opset (TCO_*).  TC_M2L: the
+// operator in the plan's split format, several offset ranges per tile when the grid is small.
+// Other modes: TF32x3 (op = index of the operator in its set for TC_APPLY), one range.
+int tc_gemm_launch(Plan& P, int mode, int opset, const int4* tiles, int ntiles, const int* boxlist,
+                   const float* in, float* out, int op, int write, cudaStream_t st) {
   int rc = tc_prepare(P);
   if (rc) return rc;
   const bool m2l = mode == tc::TC_M2L;
+  const OpSet os = op_set(P, opset, m2l);
   // 64-byte rows, four stages : 128-byte rows, two (single-column tables: always two)
   const int sw = P.tc_stages == 4 && P.C == 4 ? 1 : 0;
-  const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(P.tmaps[m2l ? 0 : 1][sw]);
-  const int split = m2l ? P.tc_split : SPLIT_TF32;
-  int rows = (P.R + P.tc_rb * tc::BM - 1) / (P.tc_rb * tc::BM);   // CTAs per tile
+  const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(P.tmaps[os.map][sw]);
+  const int split = m2l ? (opset == TCO_CMP ? P.tc_split_cm : P.tc_split) : SPLIT_TF32;
+  int rows = (os.rout + P.tc_rb * tc::BM - 1) / (P.tc_rb * tc::BM);   // CTAs per tile
   // slot ranges per tile (M->L offsets, M->M child octants): enough CTAs to fill the 152 SMs
   // over several waves; the ranges' partial sums are combined in fixed order
   // grouped M->L tiles (one parent neighbour each) write per-box partials, combined below
@@ -934,9 +861,9 @@ int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* 
   const bool splittable = (m2l && !grouped) || mode == tc::TC_M2M;
   int nsplit = 1;
   while (splittable && nsplit < P.tc_ranges && (int64_t)ntiles * rows * nsplit < 152 * 6) nsplit *= 2;
-  int64_t part_stride = (int64_t)P.tree.nbox * P.R * P.C;
+  int64_t part_stride = (int64_t)P.tree.nbox * os.rout * P.C;
   if (nsplit > 1 || grouped) {
-    size_t bytes = grouped ? sizeof(float) * (size_t)P.wl.m2l_nparts * P.R * P.C + 256
+    size_t bytes = grouped ? sizeof(float) * (size_t)P.wl.m2l_nparts * os.rout * P.C + 256
                            : sizeof(float) * part_stride * nsplit + 256;
     cudaError_t e = P.m2l_parts.reserve(bytes);
     if (e != cudaSuccess) return cuda_fail(P, e, "M->L partial buffers");
@@ -950,20 +877,25 @@ int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* 
   a.part_stride = nsplit > 1 ? part_stride : 0;
   a.nsplit = nsplit;
   a.part = grouped ? reinterpret_cast<const int*>(P.m2l_part_sorted) : nullptr;
-  a.qrow4 = P.D == 4 ? 1 : 0;
+  // StokesPVel table: the q rows of an equivalent density take the half-width twice
+  a.qrow4 = P.D == 4 && os.rout == P.R ? 1 : 0;
   a.tiles = tiles;
   a.boxlist = boxlist;
   a.vtab = P.tree.vtab.as<int32_t>();
   a.status = P.tree.status.as<unsigned>();
-  a.R = P.R;
+  a.lim = P.wait;
+  a.Rout = os.rout;
+  a.Rin = os.rin;
+  a.Rop = os.rop;
   a.mode = mode;
   a.write = nsplit > 1 || grouped ? tc::TC_STORE : write;
-  a.op = m2l ? 0 : op_slot - OP_M2M;
+  a.op = m2l ? 0 : op;
   dim3 grid(ntiles, rows, nsplit);
   const int swb = sw ? 64 : 128;
   const int bk = swb / (split == SPLIT_TF32 ? tc::Fmt<SPLIT_TF32>::ES : tc::Fmt<SPLIT_BF16>::ES);
-  a.nchunk = P.Rpad / bk;
+  a.nchunk = os.kpad / bk;
   a.group = P.C == 1 ? tc::M2L_GROUP_K / bk : (split == SPLIT_BF16 ? 2 : 1) * a.nchunk;
+  if (a.group < 1) a.group = 1;
 #define KAFMM_TC_LAUNCH(SP, RBv, SW) \
   KL tc::k_m2l_tc<SP, RBv, SW, 4><<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(map, a)
 #define KAFMM_TC_LAUNCH1(SP, RBv) \
@@ -989,11 +921,11 @@ int tc_gemm_launch(Plan& P, int mode, const int4* tiles, int ntiles, const int* 
   if (grouped && P.tree.nbox > 0)
     KL tc::k_combine_groups<<<std::min(P.tree.nbox, 152 * 8), 128, 0, st>>>(
         P.m2l_parts.as<float4>(), P.m2l_comb.as<int4>(), P.tree.nbox,
-        reinterpret_cast<float4*>(out), P.R * P.C / 4, write == tc::TC_ADD ? 1 : 0);
-  if (nsplit > 1)   // a box holds R * C floats = R * C / 4 float4 (R * C a multiple of 8)
+        reinterpret_cast<float4*>(out), os.rout * P.C / 4, write == tc::TC_ADD ? 1 : 0);
+  if (nsplit > 1)   // a box holds Rout * C floats = Rout * C / 4 float4 (Rout * C a multiple of 8)
     KL tc::k_combine_parts<<<std::min(ntiles, 152 * 4), 256, 0, st>>>(
         P.m2l_parts.as<float4>(), part_stride / 4, nsplit, reinterpret_cast<float4*>(out), tiles, ntiles,
-        boxlist, P.R * P.C / 4, write == tc::TC_ADD ? 1 : 0);
+        boxlist, os.rout * P.C / 4, write == tc::TC_ADD ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(P, e, "k_m2l_tc launch");
   return 0;

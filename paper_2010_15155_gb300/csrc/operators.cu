@@ -13,6 +13,7 @@
 // pseudo-inverse never meet the rounding of the product.
 // (geometry in units of the half-width of the child / of the box), which equals the paper's
 // sequence "equivalent density = pinv * check, then translate" up to rounding.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -97,71 +98,123 @@ __global__ void k_identity(double* V, int n) {
     V[e] = (e / n == e % n) ? 1.0 : 0.0;
 }
 
-// One round of one-sided (Hestenes) Jacobi on the rows of At (= columns of A): the n/2
-// disjoint pairs of the round-robin schedule, one block per pair.
-__global__ void k_jacobi_round(double* __restrict__ At, double* __restrict__ Vt, int n, int round,
-                               int* rotated, double tol, unsigned* worst) {
-  __shared__ double red[3][32];
-  __shared__ double cs[2];
-  int p = blockIdx.x;
-  auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + round) % (n - 1)) + 1; };
-  int i = player(p), j = player(n - 1 - p);
-  double* ai = At + (int64_t)i * n;
-  double* aj = At + (int64_t)j * n;
-  double a = 0, b = 0, g = 0;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    double x = ai[k], y = aj[k];
-    a += x * x;
-    b += y * y;
-    g += x * y;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-    g += __shfl_down_sync(0xffffffffu, g, o);
-  }
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[0][w] = a;
-    red[1][w] = b;
-    red[2][w] = g;
-  }
+// Grid-wide barrier of a cooperative launch (every block resident): sense by generation
+// counter, the wait bounded by %globaltimer.  Returns false (ST_TIMEOUT in *status) when the
+// other blocks did not arrive within limit_ns.
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, unsigned* status,
+                             unsigned long long limit_ns) {
+  __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    a = b = g = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-      a += red[0][k];
-      b += red[1][k];
-      g += red[2][k];
+    ok = 1;
+    const unsigned g = *(volatile unsigned*)gen;
+    __threadfence();
+    if (atomicAdd(count, 1u) + 1u == nblocks) {
+      *(volatile unsigned*)count = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*(volatile unsigned*)gen == g) {
+        if (global_ns() - t0 > limit_ns) {
+          atomicOr(status, (unsigned)ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
     }
-    double c = 1.0, s = 0.0;
-    if (a > 0 && b > 0) {  // largest relative off-orthogonality of the sweep (float bits)
-      float rel = (float)(fabs(g) / sqrt(a * b));
-      atomicMax(worst, __float_as_uint(rel));
-    }
-    if (fabs(g) > tol * sqrt(a * b) && a > 0 && b > 0) {
-      double zeta = (b - a) / (2.0 * g);
-      double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-      c = 1.0 / sqrt(1.0 + t * t);
-      s = c * t;
-      *rotated = 1;
-    }
-    cs[0] = c;
-    cs[1] = s;
+    __threadfence();
   }
   __syncthreads();
-  double c = cs[0], s = cs[1];
-  if (s == 0.0) return;
-  double* vi = Vt + (int64_t)i * n;
-  double* vj = Vt + (int64_t)j * n;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    double x = ai[k], y = aj[k];
-    ai[k] = c * x - s * y;
-    aj[k] = s * x + c * y;
-    x = vi[k];
-    y = vj[k];
-    vi[k] = c * x - s * y;
-    vj[k] = s * x + c * y;
+  return ok != 0;
+}
+
+// One-sided (Hestenes) Jacobi SVD of the rows of At (= columns of A), whole decomposition in one
+// cooperative launch: per sweep the n - 1 rounds of the round-robin schedule, each round's n/2
+// disjoint pairs spread over the blocks, a grid barrier after every round.  A sweep that rotates
+// no pair (|a_i . a_j| <= tol |a_i| |a_j| for all pairs) ends the iteration.  st (device ints):
+// [0..2] rotated flag of sweep s at s % 3, [3..5] largest relative off-orthogonality of sweep s
+// (float bits), [6] sweeps done, [7] barrier count, [8] barrier generation.
+__global__ void __launch_bounds__(256) k_jacobi_svd(double* __restrict__ At, double* __restrict__ Vt, int n,
+                                                    double tol, int max_sweeps, unsigned* st,
+                                                    unsigned* status, unsigned long long limit_ns) {
+  __shared__ double red[3][8];
+  __shared__ double cs[2];
+  const unsigned nb = gridDim.x;
+  auto player = [&](int pos, int round) { return pos == 0 ? 0 : ((pos - 1 + round) % (n - 1)) + 1; };
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    unsigned* rotated = st + sweep % 3;
+    unsigned* worst = st + 3 + sweep % 3;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // nobody touches the next sweep's slots now
+      st[(sweep + 1) % 3] = 0u;
+      st[3 + (sweep + 1) % 3] = 0u;
+    }
+    for (int round = 0; round < n - 1; ++round) {
+      for (int pr = blockIdx.x; pr < n / 2; pr += nb) {
+        const int i = player(pr, round), j = player(n - 1 - pr, round);
+        double* ai = At + (int64_t)i * n;
+        double* aj = At + (int64_t)j * n;
+        double a = 0, b = 0, g = 0;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+          double x = ai[k], y = aj[k];
+          a += x * x;
+          b += y * y;
+          g += x * y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_down_sync(0xffffffffu, a, o);
+          b += __shfl_down_sync(0xffffffffu, b, o);
+          g += __shfl_down_sync(0xffffffffu, g, o);
+        }
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) {
+          red[0][w] = a;
+          red[1][w] = b;
+          red[2][w] = g;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          a = b = g = 0;
+          for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            a += red[0][k];
+            b += red[1][k];
+            g += red[2][k];
+          }
+          double c = 1.0, s = 0.0;
+          if (a > 0 && b > 0) atomicMax(worst, __float_as_uint((float)(fabs(g) / sqrt(a * b))));
+          if (fabs(g) > tol * sqrt(a * b) && a > 0 && b > 0) {
+            double zeta = (b - a) / (2.0 * g);
+            double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = c * t;
+            *(volatile unsigned*)rotated = 1u;
+          }
+          cs[0] = c;
+          cs[1] = s;
+        }
+        __syncthreads();
+        const double c = cs[0], s = cs[1];
+        if (s != 0.0) {
+          double* vi = Vt + (int64_t)i * n;
+          double* vj = Vt + (int64_t)j * n;
+          for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            double x = ai[k], y = aj[k];
+            ai[k] = c * x - s * y;
+            aj[k] = s * x + c * y;
+            x = vi[k];
+            y = vj[k];
+            vi[k] = c * x - s * y;
+            vj[k] = s * x + c * y;
+          }
+        }
+        __syncthreads();
+      }
+      if (!grid_barrier(st + 7, st + 8, nb, status, limit_ns)) return;
+    }
+    const bool again = *(volatile unsigned*)rotated != 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st[6] = (unsigned)(sweep + 1);
+    if (!again) return;
   }
 }
 
@@ -309,37 +362,95 @@ __global__ void k_round32(const double* in, int64_t n, float* out) {
     out[e] = (float)in[e];
 }
 
-// Split into tf32 hi + lo (stored as fp32) with K padded to Rpad: out[(op*2 + h)][i][Rpad].
-__global__ void k_split_tf32(const double* in, int R, int Rpad, int64_t nops, float* out) {
-  int64_t total = nops * R * (int64_t)Rpad;
+// Split into tf32 hi + lo (stored as fp32), columns padded with zeros: operator op has rows x
+// cols entries at in[(op * rows + i) * ld + j]; out[(op * 2 + h)][i][colpad].
+__global__ void k_split_tf32(const double* in, int rows, int cols, int ld, int colpad, int64_t nops,
+                             float* out) {
+  int64_t total = nops * rows * (int64_t)colpad;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t op = e / ((int64_t)R * Rpad);
-    int64_t rem = e % ((int64_t)R * Rpad);
-    int i = (int)(rem / Rpad), j = (int)(rem % Rpad);
-    float v = j < R ? (float)in[(op * R + i) * R + j] : 0.f;
+    int64_t op = e / ((int64_t)rows * colpad);
+    int64_t rem = e % ((int64_t)rows * colpad);
+    int i = (int)(rem / colpad), j = (int)(rem % colpad);
+    float v = j < cols ? (float)in[(op * rows + i) * ld + j] : 0.f;
     uint32_t hb, lb;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
     float hi = __uint_as_float(hb);
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(v - hi));
-    out[((op * 2 + 0) * R + i) * Rpad + j] = hi;
-    out[((op * 2 + 1) * R + i) * Rpad + j] = __uint_as_float(lb);
+    out[((op * 2 + 0) * rows + i) * colpad + j] = hi;
+    out[((op * 2 + 1) * rows + i) * colpad + j] = __uint_as_float(lb);
   }
 }
 
-// Split into bf16 hi + lo with K padded to Rpad: out[(op*2 + h)][i][Rpad].
-__global__ void k_split_bf16(const double* in, int R, int Rpad, int64_t nops, __nv_bfloat16* out) {
-  int64_t total = nops * R * (int64_t)Rpad;
+// Split into bf16 hi + lo, the same layout as k_split_tf32.
+__global__ void k_split_bf16(const double* in, int rows, int cols, int ld, int colpad, int64_t nops,
+                             __nv_bfloat16* out) {
+  int64_t total = nops * rows * (int64_t)colpad;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t op = e / ((int64_t)R * Rpad);
-    int64_t rem = e % ((int64_t)R * Rpad);
-    int i = (int)(rem / Rpad), j = (int)(rem % Rpad);
-    float v = j < R ? (float)in[(op * R + i) * R + j] : 0.f;
+    int64_t op = e / ((int64_t)rows * colpad);
+    int64_t rem = e % ((int64_t)rows * colpad);
+    int i = (int)(rem / colpad), j = (int)(rem % colpad);
+    float v = j < cols ? (float)in[(op * rows + i) * ld + j] : 0.f;
     __nv_bfloat16 hi = __float2bfloat16_rn(v);
     __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    out[((op * 2 + 0) * R + i) * Rpad + j] = hi;
-    out[((op * 2 + 1) * R + i) * Rpad + j] = lo;
+    out[((op * 2 + 0) * rows + i) * colpad + j] = hi;
+    out[((op * 2 + 1) * rows + i) * colpad + j] = lo;
+  }
+}
+
+// General FP64 GEMM, C[M][N] (row stride ldc) = alpha op(A) op(B), op(A)[i][k] = A[i lda + k]
+// (ta = 0) or A[k lda + i] (ta = 1), op(B)[k][j] = B[k ldb + j] (tb = 0) or B[j ldb + k].
+// 32 x 32 tiles; plan time only.
+__global__ void k_gemm64g(const double* __restrict__ A, int lda, int ta, const double* __restrict__ B,
+                          int ldb, int tb, double* __restrict__ Cm, int ldc, int M, int N, int K,
+                          double alpha) {
+  __shared__ double As[32][33], Bs[32][33];
+  int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  double acc[4] = {0, 0, 0, 0};
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      // As[i][k], Bs[k][j]
+      int i = i0 + r, k = k0 + tx;
+      As[r][tx] = (i < M && k < K) ? (ta ? A[(int64_t)k * lda + i] : A[(int64_t)i * lda + k]) : 0.0;
+      int kb = k0 + r, j = j0 + tx;
+      Bs[r][tx] = (kb < K && j < N) ? (tb ? B[(int64_t)j * ldb + kb] : B[(int64_t)kb * ldb + j]) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      double b = Bs[k][tx];
+      for (int q = 0; q < 4; ++q) acc[q] += As[ty + 8 * q][k] * b;
+    }
+    __syncthreads();
+  }
+  for (int q = 0; q < 4; ++q) {
+    int i = i0 + ty + 8 * q, j = j0 + tx;
+    if (i < M && j < N) Cm[(int64_t)i * ldc + j] = alpha * acc[q];
+  }
+}
+
+// dst[i][0..n) = scale[i] * src[idx[i]][0..n) for i < nsel, zero rows for nsel <= i < rows.
+__global__ void k_select_rows(const double* __restrict__ src, int n, const int* __restrict__ idx,
+                              const double* __restrict__ scale, int nsel, int rows,
+                              double* __restrict__ dst) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)rows * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / n), j = (int)(e % n);
+    dst[e] = i < nsel ? scale[i] * src[(int64_t)idx[i] * n + j] : 0.0;
+  }
+}
+
+// dst[j][0..cols) (row stride cols) = scale[i] * src[j][idx[i]] in column i < nsel, zero columns
+// for nsel <= i < cols; src is n x n.
+__global__ void k_select_cols(const double* __restrict__ src, int n, const int* __restrict__ idx,
+                              const double* __restrict__ scale, int nsel, int cols,
+                              double* __restrict__ dst) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * cols;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int j = (int)(e / cols), i = (int)(e % cols);
+    dst[e] = i < nsel ? scale[i] * src[(int64_t)j * n + idx[i]] : 0.0;
   }
 }
 
@@ -352,7 +463,7 @@ __global__ void k_split_bf16(const double* in, int R, int Rpad, int64_t nops, __
 // Factored pinv of K (R x R) via one-sided Jacobi SVD: K = W V^T with orthogonal columns
 // W = U S.  out1 = S^+ U^T = diag(w) W^T (w_k = 1/sigma_k^2 above the cutoff), out2 = V.
 static int pinv64(Plan& P, const double* K, double* out1, double* out2, double* At, double* Vt,
-                  double* w, int* flag) {
+                  double* w, int* flag, std::vector<double>* w_host = nullptr) {
   int R = P.R;
   cudaStream_t st = P.stream;
   int g = 512;
@@ -360,21 +471,30 @@ static int pinv64(Plan& P, const double* K, double* out1, double* out2, double* 
   KL k_identity<<<g, 256, 0, st>>>(Vt, R);
   // stop when a sweep rotates no pair: |a_i . a_j| <= tol |a_i| |a_j| with tol = 4 R eps, the
   // level FP64 rounding of a length-R dot product can resolve
-  const double tol = 4.0 * R * 2.220446049250313e-16;
-  unsigned* worst = (unsigned*)(flag + 1);
-  int sweeps = 0;
-  float last = 1.f;
-  for (; sweeps < 80; ++sweeps) {
-    CK(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
-    for (int r = 0; r < R - 1; ++r)
-      KL k_jacobi_round<<<R / 2, 256, 0, st>>>(At, Vt, R, r, flag, tol, worst);
-    int h[2] = {0, 0};
-    CK(cudaMemcpyAsync(h, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    memcpy(&last, &h[1], sizeof(float));
-    if (!h[0]) break;
-  }
-  if (sweeps >= 80 && last > 1e-11f)
+  double tol = 4.0 * R * 2.220446049250313e-16;
+  int max_sweeps = 80;
+  unsigned* jst = reinterpret_cast<unsigned*>(flag);   // 9 words, see k_jacobi_svd
+  unsigned* status = jst + 12;
+  CK(cudaMemsetAsync(jst, 0, 16 * sizeof(unsigned), st));
+  // one cooperative launch: as many blocks as can be resident at once, at most one per pair
+  int dev = 0, nsm = 0, per_sm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_svd, 256, 0));
+  int blocks = std::max(1, std::min(R / 2, std::max(1, per_sm) * nsm));
+  // one round between barriers takes microseconds: the wait limit, at least the 2 s default
+  unsigned long long limit = std::max(P.wait.hard_ns, 2000000000ull);
+  void* args[] = {&At, &Vt, &R, &tol, &max_sweeps, &jst, &status, &limit};
+  ++g_launches;
+  CK(cudaLaunchCooperativeKernel((const void*)k_jacobi_svd, dim3(blocks), dim3(256), args, 0, st));
+  unsigned h[16];
+  CK(cudaMemcpyAsync(h, jst, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h[12] & ST_TIMEOUT) return fail(P, KAFMM_ERR_TIMEOUT, "Jacobi SVD: a grid barrier timed out");
+  const int sweeps = (int)h[6];
+  float last = 0.f;
+  memcpy(&last, &h[3 + (sweeps + 2) % 3], sizeof(float));   // the last sweep's slot
+  if (sweeps >= max_sweeps && h[(sweeps + 2) % 3] && last > 1e-11f)
     return fail(P, KAFMM_ERR_CUDA, "Jacobi SVD did not converge (off-orthogonality %.3g)", last);
   KL k_row_norms<<<R, 256, 0, st>>>(At, R, w);
   KL k_pinv_weights<<<1, 256, 0, st>>>(w, R, P.fp64() ? PINV_RCOND_FP64 : PINV_RCOND_FP32);
@@ -382,10 +502,112 @@ static int pinv64(Plan& P, const double* K, double* out1, double* out2, double* 
   KL k_scale_rows<<<512, 256, 0, st>>>(At, w, R, out1);
   KL k_transpose<<<512, 256, 0, st>>>(Vt, R, out2);
   CK(cudaGetLastError());
+  if (w_host) {   // the weights 1 / sigma_k^2 of the kept singular values (0: dropped)
+    w_host->resize(R);
+    CK(cudaMemcpyAsync(w_host->data(), w, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return 0;
+}
+
+// The operators of the compressed coordinates (see Plan::cmp) from the dense FP64 operators O
+// and the kept singular values (w = 1 / sigma^2, 0 where dropped) of the two pseudo-inverses.
+// Row k of the factor S^+ U^T is u_k^T / sigma_k and column k of V is v_k, so the projection
+// rows are u_k^T = sigma_k (S^+ U^T)_k and the decompression columns v_k / sigma_k.
+static int build_compressed(Plan& P, const double* O, const std::vector<double>& w_up,
+                            const std::vector<double>& w_dn) {
+  cudaStream_t st = P.stream;
+  const int R = P.R;
+  const size_t RR = (size_t)R * R;
+  std::vector<int> idx[2];
+  std::vector<double> sig[2], isig[2];
+  for (int h = 0; h < 2; ++h) {
+    const std::vector<double>& w = h == 0 ? w_up : w_dn;
+    for (int k = 0; k < R; ++k)
+      if (w[k] > 0) {
+        idx[h].push_back(k);
+        sig[h].push_back(1.0 / std::sqrt(w[k]));
+        isig[h].push_back(std::sqrt(w[k]));
+      }
+  }
+  const int ru = (int)idx[0].size(), rd = (int)idx[1].size();
+  const int rp = std::max(64, (std::max(ru, rd) + 63) / 64 * 64);
+  if (rp >= P.Rpad) return 0;   // nothing to gain: keep the dense coordinates
+  const size_t rr = (size_t)rp * rp, rR = (size_t)rp * R;
+  DevBuf d_idx, d_sc, cin, cout, cops, X;
+  CK(d_idx.reserve(sizeof(int) * 2 * R));
+  CK(d_sc.reserve(sizeof(double) * 4 * R));
+  CK(cin.reserve(sizeof(double) * 2 * rR));     // U_u^T, U_d^T  [rp][R] each
+  CK(cout.reserve(sizeof(double) * 2 * rR));    // V_u S_u^+, V_d S_d^+  [R][rp] each
+  CK(cops.reserve(sizeof(double) * rr * (N_M2L + N_CAUX)));
+  CK(X.reserve(sizeof(double) * rR));
+  int* di = d_idx.as<int>();
+  double* ds = d_sc.as<double>();
+  for (int h = 0; h < 2; ++h) {
+    const int r = h == 0 ? ru : rd;
+    CK(cudaMemcpyAsync(di + h * R, idx[h].data(), sizeof(int) * r, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ds + (2 * h) * R, sig[h].data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ds + (2 * h + 1) * R, isig[h].data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
+    const double* f1 = O + RR * (h == 0 ? OP_UP1 : OP_DN1);
+    const double* f2 = O + RR * (h == 0 ? OP_UP2 : OP_DN2);
+    KL k_select_rows<<<1024, 256, 0, st>>>(f1, R, di + h * R, ds + (2 * h) * R, r, rp, cin.as<double>() + h * rR);
+    KL k_select_cols<<<1024, 256, 0, st>>>(f2, R, di + h * R, ds + (2 * h + 1) * R, r, rp,
+                                           cout.as<double>() + h * rR);
+  }
+  const double* PuT = cin.as<double>();
+  const double* PdT = PuT + rR;
+  // dst (rp x rp) = A^T T B with A^T, B^T given as [rp][R] projection rows
+  auto sandwich = [&](const double* T, const double* AT, const double* BT, double* dst) {
+    KL k_gemm64g<<<dim3((rp + 31) / 32, (R + 31) / 32), 256, 0, st>>>(T, R, 0, BT, R, 1, X.as<double>(), rp,
+                                                                      R, rp, R, 1.0);
+    KL k_gemm64g<<<dim3((rp + 31) / 32, (rp + 31) / 32), 256, 0, st>>>(AT, R, 0, X.as<double>(), rp, 0,
+                                                                       dst, rp, rp, rp, R, 1.0);
+  };
+  double* C = cops.as<double>();
+  for (int o = 0; o < N_M2L; ++o) {
+    int ox = o % 7 - 3, oy = (o / 7) % 7 - 3, oz = o / 49 - 3;
+    if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) {
+      CK(cudaMemsetAsync(C + rr * o, 0, sizeof(double) * rr, st));
+      continue;
+    }
+    sandwich(O + RR * (OP_M2L + o), PdT, PuT, C + rr * o);
+  }
+  double* CA = C + rr * N_M2L;
+  for (int c = 0; c < 8; ++c) {
+    sandwich(O + RR * (OP_M2M + c), PuT, PuT, CA + rr * c);
+    sandwich(O + RR * (OP_L2L + c), PdT, PdT, CA + rr * (8 + c));
+  }
+  sandwich(O + RR * OP_PER, PdT, PuT, CA + rr * CAUX_PER);
+  CK(cudaGetLastError());
+  // split format: the plan's, except that the automatic choice takes TF32x3 when the
+  // compressed rows exceed 512 (the Stokeslet G table at p = 12, rp = 896: BF16x3 measured
+  // 2.6e-5 against the Ewald sum on 2^22 periodic points, TF32x3 below 1e-5)
+  P.tc_split_cm = P.tc_split;
+  if (P.tc_split_opt == KAFMM_TC_AUTO && rp > 512) P.tc_split_cm = SPLIT_TF32;
+  if (P.tc_split_cm == SPLIT_TF32) {
+    CK(P.opstc_cm2l.reserve(sizeof(float) * 2 * rr * N_M2L));
+    KL k_split_tf32<<<2048, 256, 0, st>>>(C, rp, rp, rp, rp, N_M2L, P.opstc_cm2l.as<float>());
+  } else {
+    CK(P.opstc_cm2l.reserve(sizeof(__nv_bfloat16) * 2 * rr * N_M2L));
+    KL k_split_bf16<<<2048, 256, 0, st>>>(C, rp, rp, rp, rp, N_M2L, P.opstc_cm2l.as<__nv_bfloat16>());
+  }
+  CK(P.opstc_caux.reserve(sizeof(float) * 2 * rr * N_CAUX));
+  KL k_split_tf32<<<2048, 256, 0, st>>>(CA, rp, rp, rp, rp, N_CAUX, P.opstc_caux.as<float>());
+  CK(P.opstc_cin.reserve(sizeof(float) * 2 * 2 * (size_t)rp * P.Rpad));
+  KL k_split_tf32<<<2048, 256, 0, st>>>(cin.as<double>(), rp, R, R, P.Rpad, 2, P.opstc_cin.as<float>());
+  CK(P.opstc_cout.reserve(sizeof(float) * 2 * 2 * rR));
+  KL k_split_tf32<<<2048, 256, 0, st>>>(cout.as<double>(), R, rp, rp, rp, 2, P.opstc_cout.as<float>());
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));   // the temporaries are released on return
+  P.rp = rp;
+  P.r_up = ru;
+  P.r_dn = rd;
+  P.cmp = true;
   return 0;
 }
 
 int build_operators(Plan& P) {
+  P.cmp = false;
   cudaStream_t st = P.stream;
   int n = P.n, R = P.R;
   std::vector<double> us = unit_surface(P.p);
@@ -398,7 +620,7 @@ int build_operators(Plan& P) {
   size_t RR = (size_t)R * R;
   DevBuf ops, scratch;
   CK(ops.reserve(sizeof(double) * RR * N_OPS));
-  CK(scratch.reserve(sizeof(double) * (RR * 4 + R + 64)));
+  CK(scratch.reserve(sizeof(double) * (RR * 4 + R + 64)));   // the tail holds 16 status words
   double* O = ops.as<double>();
   double* K = scratch.as<double>();
   double* At = K + RR;
@@ -411,10 +633,11 @@ int build_operators(Plan& P) {
   int stokes = P.ml_stokes;
   // pseudo-inverses at half-width 1 (factored)
   KL k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, ALPHA_UC, 0, 0, 0, ALPHA_UE, K);
-  int rc = pinv64(P, K, O + RR * OP_UP1, O + RR * OP_UP2, At, Vt, w, flag);
+  std::vector<double> w_up, w_dn;
+  int rc = pinv64(P, K, O + RR * OP_UP1, O + RR * OP_UP2, At, Vt, w, flag, &w_up);
   if (rc) return rc;
   KL k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, ALPHA_DC, 0, 0, 0, ALPHA_DE, K);
-  rc = pinv64(P, K, O + RR * OP_DN1, O + RR * OP_DN2, At, Vt, w, flag);
+  rc = pinv64(P, K, O + RR * OP_DN1, O + RR * OP_DN2, At, Vt, w, flag, &w_dn);
   if (rc) return rc;
   dim3 gg((R + 31) / 32, (R + 31) / 32);
   // Op = alpha * (K * V) * (S^+ U^T): the product through the factors
@@ -470,15 +693,20 @@ int build_operators(Plan& P) {
       P.tmap_ready = false;
       if (P.tc_split == SPLIT_TF32) {
         CK(P.opstc.reserve(sizeof(float) * 2 * (size_t)R * P.Rpad * N_M2L));
-        KL k_split_tf32<<<2048, 256, 0, st>>>(O + RR * OP_M2L, R, P.Rpad, N_M2L, P.opstc.as<float>());
+        KL k_split_tf32<<<2048, 256, 0, st>>>(O + RR * OP_M2L, R, R, R, P.Rpad, N_M2L, P.opstc.as<float>());
       } else {
         CK(P.opstc.reserve(sizeof(__nv_bfloat16) * 2 * (size_t)R * P.Rpad * N_M2L));
-        KL k_split_bf16<<<2048, 256, 0, st>>>(O + RR * OP_M2L, R, P.Rpad, N_M2L,
+        KL k_split_bf16<<<2048, 256, 0, st>>>(O + RR * OP_M2L, R, R, R, P.Rpad, N_M2L,
                                               P.opstc.as<__nv_bfloat16>());
       }
       // M->M, L->L and the pseudo-inverse factors: TF32 split (about FP32 accuracy)
       CK(P.opstc_aux.reserve(sizeof(float) * 2 * (size_t)R * P.Rpad * N_AUX));
-      KL k_split_tf32<<<2048, 256, 0, st>>>(O + RR * OP_M2M, R, P.Rpad, N_AUX, P.opstc_aux.as<float>());
+      KL k_split_tf32<<<2048, 256, 0, st>>>(O + RR * OP_M2M, R, R, R, P.Rpad, N_AUX, P.opstc_aux.as<float>());
+      P.cmp = false;
+      if (P.compress_opt) {
+        rc = build_compressed(P, O, w_up, w_dn);
+        if (rc) return rc;
+      }
     }
   }
   CK(cudaGetLastError());

@@ -74,6 +74,7 @@ struct WorkLists {
   int l2l[MAX_LEVELS][2] = {};
   int pup[2] = {0, 0}, pdn[2] = {0, 0};
   int root[2] = {0, 0};                      // the root alone (periodic far images)
+  int cup[2] = {0, 0}, cx[2] = {0, 0};       // compressed coordinates: leaves, boxes with X entries
   int leaves_n = 0, xbox_off = 0, xbox_n = 0, leafbox_off = 0;  // plain box lists
 };
 
@@ -83,6 +84,8 @@ struct Plan {
   int prec = KAFMM_PREC_MIXED, variant = KAFMM_ML_L4, near_only = 0, kahan = 0;
   int sync = 1;        // kafmm_eval synchronises and checks the device status (KAFMM_OPT_SYNC)
   int rpy_contact = 0; // KAFMM_OPT_RPY_CONTACT: 0 off, 1 on
+  WaitLimits wait;     // KAFMM_OPT_WAIT_LIMIT_US, KAFMM_OPT_WAIT_REPORT_US
+  int stall_test = 0;  // KAFMM_OPT_TEST_STALL
   cudaStream_t stream = 0;
   double origin[3] = {0, 0, 0}, L = 1.0;
   int ks = 1, kt = 1;
@@ -99,8 +102,24 @@ struct Plan {
   int tc_split_opt = KAFMM_TC_AUTO; // the requested format (option)
   int tc_rb = 2, tc_boxes = 32;     // row blocks and target boxes per tensor-core CTA
   DevBuf opstc_aux;                 // [N_AUX][2][R][Rpad] tf32 hi/lo of M->M, L->L, pinv factors
-  // TMA descriptors: [opstc, opstc_aux][128-byte, 64-byte swizzled rows]
-  alignas(64) unsigned char tmaps[2][2][128];
+  // Compressed coordinates of the mixed form (KAFMM_OPT_COMPRESS): the ML-tree state of a box
+  // is its check potential projected on the r leading left singular vectors of the
+  // check-to-equivalent matrix (upward U_u, downward U_d; r = singular values above the
+  // pseudo-inverse cutoff), every translation P^T T P between those coordinates (rp x rp,
+  // rp = max(r_up, r_dn) rounded up to 64); leaves compress their S->M check potentials, and
+  // equivalent densities come from V S^+ applied to the coordinates.
+  int compress_opt = 1;             // option: use compressed coordinates when the table allows
+  bool cmp = false;                 // compressed operators built for this plan
+  int rp = 0, r_up = 0, r_dn = 0;
+  int tc_split_cm = SPLIT_TF32;     // split format of the compressed M->L
+  DevBuf opstc_cm2l;                // [N_M2L][2][rp][rp] M->L in the plan's split format
+  DevBuf opstc_caux;                // [N_CAUX][2][rp][rp] tf32: M->M (8), L->L (8), periodic (1)
+  DevBuf opstc_cin;                 // [2][2][rp][Rpad] tf32: U_u^T, U_d^T (compress)
+  DevBuf opstc_cout;                // [2][2][R][rp] tf32: V_u S_u^+, V_d S_d^+ (decompress)
+  DevBuf up_hat, dn_hat;            // [nbox][rp][C] compressed upward / downward state
+  // TMA descriptors: [operator set][128-byte, 64-byte swizzled rows]; sets: dense M->L, dense
+  // aux, compressed M->L, compressed aux, compress, decompress
+  alignas(64) unsigned char tmaps[6][2][128];
   bool tmap_ready = false;
   int tc_stages = 2;                // pipeline depth of the tensor-core kernel (2 or 4)
   int tc_ranges = 4;                // most slot ranges (CTAs) per tile of a small grid (1..8)

@@ -10,6 +10,8 @@
 // skips coincident pairs).  With the contact split (FP32 forms, one shared point set) the near
 // field leaves out its pairs within r <= b_i + b_j and this pass adds their whole mobility.  Neighbours come from a dense cell table at a grid level whose cell
 // side is at least a_max + b_max, so every contact partner lies in the 27 surrounding cells.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -296,28 +298,63 @@ constexpr size_t NOALLOC_BYTES = (size_t)32 << 20;   // 32 MiB
 constexpr int NOALLOC_MAX_CELL_LEVEL = 6;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
+// Host-side address of the array in the CUDA context current on this thread.  A module's
+// device variables live per context, and cudaDeviceReset replaces the device's primary context,
+// so the address is looked up once per context (keyed by the driver's context id, which a new
+// context never reuses), with that context current.
 static unsigned char* noalloc_base(Plan& P, int* rc) {
-  // host-side address of the array on the current device, looked up once per device
+  typedef CUresult (*CtxCurrentFn)(CUcontext*);
+  typedef CUresult (*CtxIdFn)(CUcontext, unsigned long long*);
   static std::mutex mu;
+  static CtxCurrentFn ctx_current = nullptr;
+  static CtxIdFn ctx_id = nullptr;
+  static unsigned long long ids[64] = {0};
   static unsigned char* addr[64] = {nullptr};
+  static int n_cached = 0, next_evict = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64) {
-    *rc = cuda_fail(P, e == cudaSuccess ? cudaErrorInvalidDevice : e, "cudaGetDevice");
+  if (e == cudaSuccess) e = cudaSetDevice(dev);   // makes the device's primary context current
+  if (e != cudaSuccess) {
+    *rc = cuda_fail(P, e, "cudaGetDevice / cudaSetDevice");
     return nullptr;
   }
   std::lock_guard<std::mutex> lk(mu);
-  if (!addr[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr) {
-      *rc = cuda_fail(P, e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress(scratch)");
+  if (!ctx_current || !ctx_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &f1, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPoint("cuCtxGetId", &f2, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+      cudaGetLastError();
+      *rc = fail(P, KAFMM_ERR_CUDA, "cuCtxGetCurrent / cuCtxGetId are unavailable");
       return nullptr;
     }
-    addr[dev] = reinterpret_cast<unsigned char*>(ptr);
+    ctx_current = reinterpret_cast<CtxCurrentFn>(f1);
+    ctx_id = reinterpret_cast<CtxIdFn>(f2);
   }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (ctx_current(&ctx) != CUDA_SUCCESS || !ctx || ctx_id(ctx, &id) != CUDA_SUCCESS) {
+    *rc = fail(P, KAFMM_ERR_CUDA, "no current CUDA context");
+    return nullptr;
+  }
+  for (int i = 0; i < n_cached; ++i)
+    if (ids[i] == id) {
+      *rc = 0;
+      return addr[i];
+    }
+  void* ptr = nullptr;
+  e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr) {
+    *rc = cuda_fail(P, e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress(scratch)");
+    return nullptr;
+  }
+  int slot = n_cached < 64 ? n_cached++ : (next_evict++ % 64);   // a full table reuses slots in turn
+  ids[slot] = id;
+  addr[slot] = reinterpret_cast<unsigned char*>(ptr);
   *rc = 0;
-  return addr[dev];
+  return addr[slot];
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -23,6 +23,7 @@ BC_OPEN, BC_PXYZ = 0, 3
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN, OPT_TC_SPLIT = 1, 2, 3, 4, 5, 6
 OPT_SYNC, OPT_TC_STAGES, OPT_TC_RANGES, OPT_RPY_CONTACT, OPT_TC_TILING = 7, 8, 9, 10, 11
+OPT_WAIT_LIMIT_US, OPT_WAIT_REPORT_US, OPT_TEST_STALL, OPT_COMPRESS = 12, 13, 14, 15
 TC_TF32X3, TC_BF16X3, TC_AUTO = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 ML_G, ML_L4 = 0, 1
@@ -65,6 +66,7 @@ def lib():
             "kafmm_phase_times": ([vp, ctypes.POINTER(dbl), i32], i32),
             "kafmm_get_counters": ([vp, ctypes.POINTER(i64), i32], i32),
             "kafmm_get_operator": ([vp, i32, vp], i32),
+            "kafmm_measure_peak": ([i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)], i32),
             "kafmm_destroy": ([vp], i32),
             "kafmm_last_error": ([vp], ctypes.c_char_p),
         }
@@ -196,19 +198,30 @@ def kafmm_phase_times(plan):
 
 
 def kafmm_get_counters(plan):
-    c = (ctypes.c_int64 * 8)()
-    _check(plan, lib().kafmm_get_counters(plan, c, 8))
+    c = (ctypes.c_int64 * 12)()
+    _check(plan, lib().kafmm_get_counters(plan, c, 12))
     return {"launches_points": int(c[0]), "launches_eval": int(c[1]),
             "tensor_core_m2l": int(c[2]), "launches_per_step": int(c[3]),
             "tc_split": {0: "tf32x3", 1: "bf16x3"}.get(int(c[4])),
             "m2l_tiling": {1: "whole V lists", 2: "per parent neighbour"}.get(int(c[5])),
-            "m2l_tiles": int(c[6])}
+            "m2l_tiles": int(c[6]), "device_allocations": int(c[7]),
+            "compressed_rows": int(c[8]), "rank_up": int(c[9]), "rank_dn": int(c[10])}
 
 
 def kafmm_get_operator(plan, slot, R):
     out = np.zeros((R, R))
     _check(plan, lib().kafmm_get_operator(plan, slot, out.ctypes.data))
     return out
+
+
+PEAK_FFMA, PEAK_RSQRT, PEAK_DFMA, PEAK_MMA_TF32, PEAK_MMA_BF16 = 0, 1, 2, 3, 4
+
+
+def kafmm_measure_peak(what):
+    """(operations per second, ms of the timed launch) of one micro-benchmark."""
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    _check(None, lib().kafmm_measure_peak(what, ctypes.byref(rate), ctypes.byref(ms)))
+    return rate.value, ms.value
 
 
 def kafmm_destroy(plan):
@@ -227,7 +240,7 @@ class Plan:
 
     def __init__(self, kernel, p, q, bc=BC_OPEN, precision=PREC_MIXED, variant=ML_L4,
                  near_only=False, kahan=False, stream=None, origin=(0.0, 0.0, 0.0), L=1.0,
-                 tc_split=TC_AUTO, sync=True, tc_stages=None):
+                 tc_split=TC_AUTO, sync=True, tc_stages=None, compress=True):
         self.kernel = kernel
         self.ks, self.kt = KDIM[kernel]
         self.h = kafmm_plan(kernel, bc, p, q)
@@ -237,6 +250,7 @@ class Plan:
         kafmm_set_option(self.h, OPT_KAHAN, int(kahan))
         kafmm_set_option(self.h, OPT_TC_SPLIT, tc_split)
         kafmm_set_option(self.h, OPT_SYNC, int(sync))
+        kafmm_set_option(self.h, OPT_COMPRESS, int(compress))
         if tc_stages is not None:
             kafmm_set_option(self.h, OPT_TC_STAGES, tc_stages)
         if stream is not None:

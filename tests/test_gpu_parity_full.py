@@ -1,0 +1,226 @@
+"""GPU parity at the benchmark sizes and on the edge cases of the tree.
+
+* The Stokeslet workload at full size (N = 262144 uniform, p = 10, q = 128, four-channel
+  table): the plain FP64 form and the mixed form against the oracle's direct FP64 sum on 4096
+  sampled targets (Sec. III.A's eps_L2 on a sample).  The FP64 form's error is the FMM
+  truncation error at p = 10 (about 1e-7 on the paper's convergence study); the mixed form
+  adds its rounding, within the 1e-5 of the metric.
+* The triply periodic Stokeslet at full size (2^22 points, p = 12, mixed) against the Ewald
+  sum on 1024 sampled targets (Sec. III.B).
+* Coincident points: more than q points on one spot force leaves at the depth cap (level 20);
+  the tree and lists stay integer-equal to the oracle's and the FP64 KAFMM to the CPU KAFMM.
+* Separate source and target sets (x != y), FP64 and mixed.
+* The Kahan-compensated FP32 near field (KAFMM_OPT_KAHAN) against the oracle's U-list sums.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads as W  # noqa: E402
+from oracle import direct as D  # noqa: E402
+from oracle.kafmm import KAFMM  # noqa: E402
+from oracle.tree import Tree  # noqa: E402
+from paper_2010_15155_gb300 import kafmm as K  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_15155_gb300 import build
+    build.build()
+
+
+def _eval(kernel, pts, s, prec, p, q, variant=K.ML_L4, trg=None, bc=K.BC_OPEN, **kw):
+    dt = torch.float64 if prec == K.PREC_FP64 else torch.float32
+    plan = K.Plan(kernel, p=p, q=q, precision=prec, variant=variant, bc=bc, **kw)
+    y = torch.from_numpy(np.ascontiguousarray(pts)).to(dt).cuda()
+    x = None if trg is None else torch.from_numpy(np.ascontiguousarray(trg)).to(dt).cuda()
+    plan.set_points(y, x)
+    g = plan.eval(torch.from_numpy(np.ascontiguousarray(s)).to(dt).cuda()).double().cpu().numpy()
+    counters = K.kafmm_get_counters(plan.h)
+    plan.close()
+    return g, counters
+
+
+def test_stokeslet_full_size_forms_against_direct_sum():
+    n, p, q = 262144, 10, 128
+    pts, f = W.stokes_uniform(n, seed=1, dtype=np.float32)
+    p64, f64 = pts.astype(np.float64), f.astype(np.float64)
+    idx = W.sample_targets(n, 4096)
+    ref = D.direct("stokeslet", p64[idx], p64, f64)
+    g64, _ = _eval(K.STOKESLET, p64, f64, K.PREC_FP64, p, q)
+    gmx, c = _eval(K.STOKESLET, pts, f, K.PREC_MIXED, p, q)
+    assert c["tensor_core_m2l"] == 1
+    e64 = D.rel_l2(g64[idx], ref)
+    emx = D.rel_l2(gmx[idx], ref)
+    print("full size vs direct: fp64", e64, "mixed", emx, "mixed vs fp64", D.rel_l2(gmx, g64))
+    assert e64 < 5e-7
+    assert emx < 1e-5
+    assert D.rel_l2(gmx, g64) < 1e-5
+
+
+def test_periodic_full_size_against_ewald_sum():
+    from oracle import periodic as Pd
+    n = 1 << 22
+    pts, f = W.stokes_uniform(n, seed=4, zero_mean=True)
+    idx = W.sample_targets(n, 1024)
+    g, c = _eval(K.STOKESLET, pts, f, K.PREC_MIXED, 12, 128, variant=K.ML_G, bc=K.BC_PXYZ)
+    assert c["tensor_core_m2l"] == 1
+    # the Ewald sum of the points and forces the mixed form computes with (FP32 inputs)
+    ref = Pd.ewald_sum_sampled("stokeslet", pts[idx].astype(np.float64), pts.astype(np.float64),
+                               f.astype(np.float64), xi_l=8.0, kmax=12)
+    err = D.rel_l2(g[idx], ref)
+    print("periodic full size vs Ewald (1024 sampled)", err)
+    assert err < 1e-5
+
+
+def _coincident(n_bg=3000, n_spot=150, seed=5):
+    rng = np.random.default_rng(seed)
+    bg = rng.random((n_bg, 3))
+    spot = np.tile(np.array([[0.3141592, 0.7182818, 0.1414213]]), (n_spot, 1))
+    near = spot[:40] + rng.uniform(-1, 1, (40, 3)) * 2.0 ** -22   # a cluster around the spot
+    return np.concatenate([bg, spot, near])
+
+
+def test_coincident_points_reach_the_depth_cap():
+    pts = _coincident()
+    q = 32
+    T = Tree(pts, q=q)
+    assert T.nlevels == 21   # leaves at level 20 hold the coincident points
+    plan = K.Plan(K.LAPLACE, p=4, q=q, precision=K.PREC_FP64, near_only=True)
+    plan.set_points(torch.from_numpy(pts).cuda())
+    info = plan.info()
+    nb = info["nbox"]
+    level, anchor, parent, leaf = K.kafmm_get_tree(plan.h, nb)
+    assert info["nbox"] == T.nbox and info["nlevels"] == T.nlevels
+    assert info["max_leaf_pts"] > q
+    assert np.array_equal(level, T.level) and np.array_equal(anchor, T.anchor)
+    assert np.array_equal(parent, T.parent) and np.array_equal(leaf.astype(bool), T.is_leaf)
+    for kind, name in enumerate("UVWX"):
+        off, ent, sh = K.kafmm_get_list(plan.h, kind, nb)
+        ref = getattr(T, name)
+        for b in range(nb):
+            got = set(zip(ent[off[b]:off[b + 1]].tolist(), sh[off[b]:off[b + 1]].tolist()))
+            assert got == {(a, 13) for (a, _) in ref[b]}, (name, b)
+    plan.close()
+
+
+@pytest.mark.parametrize("problem,kernel", [("laplace", K.LAPLACE), ("stokeslet_l4", K.STOKESLET)])
+def test_coincident_points_fp64_kafmm_matches_cpu_kafmm(problem, kernel):
+    pts = _coincident()
+    rng = np.random.default_rng(9)
+    s = rng.standard_normal((len(pts), 1 if kernel == K.LAPLACE else 3))
+    ref = KAFMM(problem, 6, 32).evaluate(pts, s)
+    g, _ = _eval(kernel, pts, s, K.PREC_FP64, 6, 32)
+    assert np.all(np.isfinite(g))
+    assert D.rel_l2(g, ref) < 1e-7
+
+
+@pytest.mark.parametrize("problem,kernel,variant", [("laplace", K.LAPLACE, K.ML_L4),
+                                                    ("stokeslet_l4", K.STOKESLET, K.ML_L4),
+                                                    ("stokeslet_g", K.STOKESLET, K.ML_G)])
+def test_separate_targets_fp64_kafmm_matches_cpu_kafmm(problem, kernel, variant):
+    rng = np.random.default_rng(12)
+    src = rng.random((2500, 3))
+    trg = np.concatenate([rng.random((1500, 3)), src[:200]])   # some targets on sources
+    s = rng.standard_normal((len(src), 1 if kernel == K.LAPLACE else 3))
+    ref = KAFMM(problem, 6, 40).evaluate(src, s, trg=trg)
+    g, _ = _eval(kernel, src, s, K.PREC_FP64, 6, 40, variant=variant, trg=trg)
+    assert g.shape == ref.shape
+    assert D.rel_l2(g, ref) < 1e-7
+
+
+def test_separate_targets_mixed_form_against_direct_sum():
+    rng = np.random.default_rng(13)
+    src = rng.random((60000, 3)).astype(np.float32)
+    trg = rng.random((20000, 3)).astype(np.float32)
+    f = rng.standard_normal((60000, 3)).astype(np.float32)
+    ref = D.direct("stokeslet", trg.astype(np.float64), src.astype(np.float64), f.astype(np.float64))
+    g64, _ = _eval(K.STOKESLET, src.astype(np.float64), f.astype(np.float64), K.PREC_FP64, 8, 64,
+                   trg=trg.astype(np.float64))
+    gmx, c = _eval(K.STOKESLET, src, f, K.PREC_MIXED, 8, 64, trg=trg)
+    assert c["tensor_core_m2l"] == 1
+    assert D.rel_l2(g64, ref) < 2e-6
+    assert D.rel_l2(gmx, ref) < 1e-5
+
+
+def _near_oracle(kernel, pts, s, q):
+    T = Tree(pts, q=q)
+    g = np.zeros((len(pts), K.KDIM[{"laplace": K.LAPLACE, "stokeslet": K.STOKESLET,
+                                     "rpy": K.RPY}[kernel]][1]))
+    for b in T.leaves():
+        ti = T.trg_idx[b]
+        for (a, _) in T.U[b]:
+            si = T.src_idx[a]
+            g[ti] += D.direct(kernel, pts[ti], pts[si], s[si])
+    return g
+
+
+@pytest.mark.parametrize("kernel,code", [("laplace", K.LAPLACE), ("stokeslet", K.STOKESLET),
+                                         ("rpy", K.RPY)])
+def test_kahan_near_field_matches_oracle(kernel, code):
+    rng = np.random.default_rng(14)
+    n, q = 4000, 60
+    pts = rng.random((n, 3)).astype(np.float32).astype(np.float64)
+    ks = K.KDIM[code][0]
+    s = rng.standard_normal((n, ks))
+    if kernel == "rpy":
+        s[:, 3] = rng.uniform(0.0, 2e-3, n)
+    s = s.astype(np.float32).astype(np.float64)
+    ref = _near_oracle(kernel, pts, s, q)
+    out = {}
+    for kahan in (False, True):
+        out[kahan], _ = _eval(code, pts.astype(np.float32), s.astype(np.float32), K.PREC_FP32, 4, q,
+                              near_only=True, kahan=kahan)
+    ek, ep = D.rel_l2(out[True], ref), D.rel_l2(out[False], ref)
+    print("near field", kernel, "kahan", ek, "plain", ep)
+    assert ek < 1e-5
+    assert ek <= ep * 1.5 + 1e-7   # compensation does not make it worse
+
+
+@pytest.mark.parametrize("kernel,variant,bc,p,split", [
+    ("stokeslet", K.ML_L4, "open", 10, K.TC_AUTO),     # four-channel table, BF16x3
+    ("stokeslet", K.ML_L4, "open", 8, K.TC_TF32X3),    # four-channel table, TF32x3
+    ("laplace", K.ML_L4, "open", 8, K.TC_AUTO),        # Laplace, single column
+    ("stokeslet", K.ML_G, "open", 8, K.TC_BF16X3),     # G table
+    ("stokeslet", K.ML_G, "pxyz", 8, K.TC_AUTO),       # periodic G table (root operator)
+    ("stokes_dl", K.ML_L4, "open", 8, K.TC_AUTO),      # StokesPVel table ([h p, u] scaling)
+    ("rpy", K.ML_L4, "open", 8, K.TC_AUTO),            # RPY on the four-channel table
+])
+def test_compressed_coordinates_match_dense_mixed_form(kernel, variant, bc, p, split):
+    """The ML tree in compressed coordinates (KAFMM_OPT_COMPRESS, the default) computes the
+    same sums as in check potentials: both mixed forms within 1e-5 of the plain FP64 form, and
+    of each other; clustered points so the tree has W and X lists."""
+    code = {"laplace": K.LAPLACE, "stokeslet": K.STOKESLET, "stokes_dl": K.STOKES_DL, "rpy": K.RPY}[kernel]
+    if bc == "pxyz":
+        rng = np.random.default_rng(51)
+        pts = rng.random((30000, 3))
+        s = rng.standard_normal((30000, 3))
+        s -= s.mean(axis=0)
+    else:
+        pts, _, a = W.rpy_clusters(40000, seed=52, n_clusters=12, sigma=0.04, dtype=np.float64)
+        rng = np.random.default_rng(53)
+        s = rng.standard_normal((len(pts), K.KDIM[code][0]))
+        if kernel == "rpy":
+            s[:, 3] = rng.uniform(0.0, 1e-3, len(pts))
+    # both forms see the same FP32-rounded inputs (close clustered pairs are sensitive to them)
+    pts = np.minimum(pts, 1.0 - 2.0 ** -24).astype(np.float32).astype(np.float64)
+    s = s.astype(np.float32).astype(np.float64)
+    bcc = K.BC_PXYZ if bc == "pxyz" else K.BC_OPEN
+    g64, _ = _eval(code, pts, s, K.PREC_FP64, p, 64, variant=variant, bc=bcc)
+    out = {}
+    for cmp in (False, True):
+        out[cmp], c = _eval(code, pts.astype(np.float32), s.astype(np.float32), K.PREC_MIXED, p, 64,
+                            variant=variant, bc=bcc, tc_split=split, compress=cmp)
+        assert c["tensor_core_m2l"] == 1
+        if cmp:
+            assert 0 < c["rank_up"] <= c["compressed_rows"] and 0 < c["rank_dn"] <= c["compressed_rows"]
+        else:
+            assert c["compressed_rows"] == 0
+    e_c, e_d = D.rel_l2(out[True], g64), D.rel_l2(out[False], g64)
+    print("compressed", kernel, variant, bc, p, "vs fp64", e_c, "dense", e_d, "ranks", c["rank_up"], c["rank_dn"])
+    assert e_c < 1e-5 and e_d < 1e-5
+    assert D.rel_l2(out[True], out[False]) < 1e-5

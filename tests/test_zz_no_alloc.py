@@ -41,8 +41,11 @@ def test_noalloc_velocity_equals_allocating_entry_point(prec):
         ref = torch.empty((len(pts), 3), dtype=dt, device="cuda")
         K.kafmm_rpy_velocity(plan.h, s, ac, g, ref, code)
         ua = torch.full((len(pts), 3), float("nan"), dtype=dt, device="cuda")
+        allocs = K.kafmm_get_counters(plan.h)["device_allocations"]
         K.kafmm_rpy_velocity_noalloc(plan.h, s, ac, g, ua, code)
         torch.cuda.synchronize()
+        # the library made no device allocation during the call
+        assert K.kafmm_get_counters(plan.h)["device_allocations"] == allocs
         r, u = ref.double().cpu().numpy(), ua.double().cpu().numpy()
         assert np.all(np.isfinite(u))
         assert D.rel_l2(u, r) < (1e-12 if prec == K.PREC_FP64 else 1e-6)

@@ -504,3 +504,52 @@ void orc_ewald_real_mi(int kernel, const double* x, int64_t nt, const double* y,
     for (int p = 0; p < kt; ++p) g[kt * a + p] += acc[p];
   }
 }
+
+/* ---------------------------------------------------------------------------------------
+ * Stokeslet above a no-slip wall (the plane x_3 = zw), Blake's image system: for a source at
+ * y with height h = y_3 - zw and its image y^I = (y_1, y_2, zw - h), r = x - y, R = x - y^I,
+ *   8 pi u_i = [S_ij(r) - S_ij(R)] f_j + 2 h sum_k (M f)_k d/dR_k D_i(R),
+ *   S_ij(r) = delta_ij / r + r_i r_j / r^3,  M = diag(1, 1, -1),
+ *   D_i(R) = h R_i / R^3 - delta_i3 / R - R_i R_3 / R^3.
+ * The field vanishes on the wall and equals the free-space Stokeslet plus a regular field near
+ * the source.  Sources and targets must lie above the wall; at r = 0 (a target on its source)
+ * the free-space term is skipped and the image terms are kept.
+ * ------------------------------------------------------------------------------------- */
+void orc_stokeslet_wall(const double* x, int64_t nt, const double* y, int64_t ns, const double* f,
+                        double zw, double* g) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t a = 0; a < nt; ++a) {
+    double acc[3] = {0, 0, 0};
+    for (int64_t b = 0; b < ns; ++b) {
+      const double h = y[3 * b + 2] - zw;
+      double r[3], R[3];
+      for (int q = 0; q < 3; ++q) r[q] = x[3 * a + q] - y[3 * b + q];
+      R[0] = r[0];
+      R[1] = r[1];
+      R[2] = x[3 * a + 2] - (zw - h);
+      const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      const double rn = sqrt(rr), Rn = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+      const double* fb = f + 3 * b;
+      const double Mf[3] = {fb[0], fb[1], -fb[2]};
+      double rf = 0, Rf = 0;
+      for (int q = 0; q < 3; ++q) {
+        rf += r[q] * fb[q];
+        Rf += R[q] * fb[q];
+      }
+      for (int i = 0; i < 3; ++i) {
+        /* r = 0 (the target is the source): the free-space part is skipped, the image part kept */
+        double u = (rr > 0.0 ? fb[i] / rn + r[i] * rf / (rn * rn * rn) : 0.0) - fb[i] / Rn -
+                   R[i] * Rf / (Rn * Rn * Rn);
+        double d = 0;
+        for (int k = 0; k < 3; ++k) {
+          const double dik = i == k ? 1.0 : 0.0, di3 = i == 2 ? 1.0 : 0.0, d3k = k == 2 ? 1.0 : 0.0;
+          const double R3 = Rn * Rn * Rn, R5 = R3 * Rn * Rn;
+          d += Mf[k] * (h * (dik / R3 - 3.0 * R[i] * R[k] / R5) + di3 * R[k] / R3 -
+                        (dik * R[2] + R[i] * d3k) / R3 + 3.0 * R[i] * R[2] * R[k] / R5);
+        }
+        acc[i] += u + 2.0 * h * d;
+      }
+    }
+    for (int i = 0; i < 3; ++i) g[3 * a + i] += acc[i] / (8.0 * PI);
+  }
+}

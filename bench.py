@@ -20,6 +20,10 @@ e2e    = the same through the C ABI with pinned HOST buffers (copies inside the 
          eval + rpy_velocity per step).
 --workload convergence: the paper's convergence benchmark (10^6 log-normal points, L = 32,
          q = 2000, m = 6..16 relative to m = 16, FP64), Laplace and Stokeslet.
+--workload leafsweep: the leaf-size trade-off on the paper's log-normal cloud (10^6 points,
+         p = 10, mixed form, q = 32 .. 2000): step time and error against the direct sum.
+--workload errors: error of every form (FP64, FP32, mixed) against the direct FP64 sum per
+         kernel and order (65536 uniform points, 512 sampled targets).
 """
 from __future__ import annotations
 
@@ -250,7 +254,7 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     plan = K.Plan(K.STOKESLET, p=P_ORDER, q=Q_LEAF, precision=prec, variant=K.ML_L4,
-                  stream=stream.cuda_stream, tc_split=split, compress=not args.no_compress)
+                  stream=stream.cuda_stream, tc_split=split, compress=args.compress)
     R = 6 * (P_ORDER - 1) ** 2 + 2
     K.kafmm_get_operator(plan.h, 0, R)   # builds the operators
     torch.cuda.synchronize(dev)
@@ -390,6 +394,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_points": N_POINTS, "p": P_ORDER, "q": Q_LEAF,
                    "ml_table": "four-channel Laplace", "precision": args.precision,
+                   "compress": args.compress,
                    "tc_split": split_used if args.precision == "mixed" else None,
                    "autotuned": tuned,
                    "m2l_tiling": K.kafmm_get_counters(plan.h)["m2l_tiling"],
@@ -809,6 +814,115 @@ def run_convergence(args):
     return 0
 
 
+def run_errors(args):
+    """FMM error of every form against the oracle's direct FP64 sum (O1), per kernel and order:
+    N = 65536 uniform points, q = 64, 512 sampled targets (Sec. III.A's eps_L2 on a sample).
+    Forms: plain FP64, FP32 on CUDA cores, mixed (tensor cores, compressed coordinates)."""
+    import torch
+
+    from oracle import direct as D
+    from paper_2010_15155_gb300 import kafmm as K
+
+    rank, world, local = _env_rank()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    n, q = 65536, 64
+    rng = np.random.default_rng(7)
+    pts = np.minimum(rng.random((n, 3)), 1.0 - 2.0 ** -24)
+    p32 = pts.astype(np.float32).astype(np.float64)
+    idx = workloads.sample_targets(n, 512)
+    cases = [  # name, kernel, ML variant, oracle kernel, orders
+        ("laplace", K.LAPLACE, K.ML_L4, "laplace", (6, 8, 10, 12)),
+        ("stokeslet_four_channel", K.STOKESLET, K.ML_L4, "stokeslet", (6, 8, 10, 12)),
+        ("stokeslet_g_table", K.STOKESLET, K.ML_G, "stokeslet", (6, 8, 10)),
+        ("rpy_four_channel", K.RPY, K.ML_L4, "rpy", (6, 8, 10, 12)),
+        ("regularized_stokeslet", K.STOKES_REG, K.ML_G, "stokeslet_reg", (6, 8, 10)),
+        ("laplace_charge_dipole", K.LAPLACE_QD, K.ML_L4, "laplace_qd", (6, 8, 10, 12)),
+        ("stokes_double_layer", K.STOKES_DL, K.ML_L4, "stokes_dl", (6, 8, 10)),
+    ]
+    forms = (("fp64", K.PREC_FP64), ("fp32", K.PREC_FP32), ("mixed", K.PREC_MIXED))
+    out = {"metric": "relative L2 error against the direct FP64 sum (O1), 512 sampled targets",
+           "impl": "gb300", "data": "synthetic",
+           "config": {"workload": "errors_uniform_64k_q64", "n_points": n, "q": q,
+                      "targets": "512 sampled"}, "table": {}}
+    for name, kern, var, okern, orders in cases:
+        ks = K.KDIM[kern][0]
+        s = rng.standard_normal((n, ks))
+        if kern == K.RPY:
+            s[:, 3] = rng.uniform(0.0, 2e-3, n)
+        if kern == K.STOKES_REG:
+            s[:, 3] = rng.uniform(0.0, 1e-4, n)
+        s32 = s.astype(np.float32).astype(np.float64)
+        ref = {"fp64": D.direct(okern, pts[idx], pts, s),
+               "f32in": D.direct(okern, p32[idx], p32, s32)}
+        row = {}
+        for p in orders:
+            cell = {}
+            for fname, prec in forms:
+                dt = torch.float64 if prec == K.PREC_FP64 else torch.float32
+                plan = K.Plan(kern, p=p, q=q, precision=prec, variant=var)
+                src = pts if prec == K.PREC_FP64 else p32
+                plan.set_points(torch.from_numpy(src).to(dt).cuda())
+                sv = s if prec == K.PREC_FP64 else s32
+                g = plan.eval(torch.from_numpy(sv).to(dt).cuda()).double().cpu().numpy()
+                plan.close()
+                cell[fname] = D.rel_l2(g[idx], ref["fp64" if prec == K.PREC_FP64 else "f32in"])
+            row[p] = cell
+        out["table"][name] = row
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_leafsweep(args):
+    """The leaf-size trade-off (Sec. III.A uses at most 2000 points per leaf): the paper's
+    log-normal cloud (10^6 points, Eq. ptdist, m = -1, s = 0.5, L = 32), Stokeslet, p = 10,
+    mixed form, q = 32 .. 2000: step time (set_points + eval, CUDA events, L2 flushed between
+    steps) and the error against the direct FP64 sum on 512 sampled targets."""
+    import torch
+
+    from oracle import direct as D
+    from paper_2010_15155_gb300 import kafmm as K
+
+    rank, world, local = _env_rank()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n, L = 1000000, 32.0
+    pts = (workloads.lognormal_points(n, seed=5) * L).astype(np.float32)
+    f = np.random.default_rng(6).uniform(-1.0, 1.0, (n, 3)).astype(np.float32)
+    idx = workloads.sample_targets(n, 512)
+    ref = D.direct("stokeslet", pts[idx].astype(np.float64), pts.astype(np.float64), f.astype(np.float64))
+    y = torch.from_numpy(pts).to(dev)
+    s = torch.from_numpy(f).to(dev)
+    g = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    rows = {}
+    for q in (32, 64, 128, 256, 512, 1000, 2000):
+        plan = K.Plan(K.STOKESLET, p=10, q=q, precision=K.PREC_MIXED, variant=K.ML_L4,
+                      origin=(0.0, 0.0, 0.0), L=L, stream=stream.cuda_stream)
+
+        def step():
+            plan.set_points(y)
+            plan.eval(s, g)
+        ms, ph, _ = _timed_steps(step, plan, argparse.Namespace(warmup=2, steps=5), 1, dev, stream, flush, local)
+        err = D.rel_l2(g.double().cpu().numpy()[idx], ref)
+        info = plan.info()
+        rows[q] = {"ms_per_step": ms, "mpoints_s": n / (ms * 1e-3) / 1e6, "rel_l2_vs_o1": err,
+                   "phases_ms": ph, "nleaf": info["nleaf"], "nlevels": info["nlevels"],
+                   "near_pairs": info["near_pairs"], "n_v": info["n_v"]}
+        plan.close()
+    out = {"metric": "Stokeslet KAFMM step time and error vs leaf size q (Sec. III.A cloud)",
+           "impl": "gb300", "data": "synthetic", "dtype": "f32+bf16x3",
+           "config": {"workload": "lognormal_1m_L32_p10_leafsweep", "n_points": n, "L": L, "p": 10,
+                      "precision": "mixed", "l2": "flushed (256 MiB write) between timed steps"},
+           "by_q": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def eval_graph_timing(plan, s, g, stream, flush, steps):
     """kafmm_eval alone for the current points, captured once in a CUDA graph (the plan in
     asynchronous mode) and replayed; per replay CUDA-event time with L2 flushed in between."""
@@ -877,11 +991,13 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
     ap.add_argument("--tc-split", default="auto", choices=["auto", "tf32x3", "bf16x3"])
     ap.add_argument("--workload", default="stokeslet",
-                    choices=["stokeslet", "batched", "periodic", "rpy", "convergence"])
+                    choices=["stokeslet", "batched", "periodic", "rpy", "convergence", "errors",
+                             "leafsweep"])
     ap.add_argument("--tc-tiling", type=int, default=0, choices=[0, 1, 2],
                     help="M->L tiling: 0 automatic, 1 whole V lists, 2 per parent neighbour")
-    ap.add_argument("--no-compress", action="store_true",
-                    help="mixed form in check potentials instead of compressed coordinates")
+    ap.add_argument("--compress", type=int, default=1, choices=[0, 1, 2],
+                    help="mixed form: 0 check potentials, 1 compressed coordinates, 2 compressed "
+                         "with the rank rounded down to a multiple of 64")
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -895,6 +1011,10 @@ def main():
         return run_gpu_rpy(args)
     if args.workload == "convergence":
         return run_convergence(args)
+    if args.workload == "errors":
+        return run_errors(args)
+    if args.workload == "leafsweep":
+        return run_leafsweep(args)
     return run_gpu(args)
 
 

@@ -85,8 +85,22 @@ typedef enum {
  * [origin, origin + L)^3; the far images enter through a precomputed operator on the
  * root's multipole density (Sec. III, App. B).  Periodic sums need a zero net source
  * (sum of f = 0 for the Stokeslet, sum of q = 0 for Laplace); the k = 0 Fourier mode is
- * dropped (zero-mean field).  PX and PXY are not provided. */
-typedef enum { KAFMM_BC_OPEN = 0, KAFMM_BC_PXYZ = 3 } kafmm_bc;
+ * dropped (zero-mean field).  PX and PXY are not provided.
+ * KAFMM_BC_WALL (KAFMM_STOKESLET only): a no-slip wall on the plane z = origin_z + L / 2,
+ * open elsewhere (Sec. III.C).  Every source and target must lie above it (z in
+ * [origin_z + L/2, origin_z + L)), else KAFMM_ERR_DOMAIN; their mirror images fill the lower
+ * half of the cube.  The flow is Blake's image system, evaluated as one Stokeslet and two
+ * Laplace charge + dipole KAFMM sums over the sources and their images and assembled at the
+ * targets (Table tab:rpywall with b = 0):
+ *   u = u^S + grad phi^SDZ + x_3 grad phi^SD - [0, 0, phi^SD],  x_3 = height above the wall,
+ *   u^S: (f_1, f_2, 0) at y and its negative at the image; phi^SD: charge -f_3/2 at y, charge
+ *   f_3/2 and dipole h (-f_1, -f_2, f_3) at the image; phi^SDZ: charge h f_3/2 at y, -h f_3/2
+ *   at the image (h: the source's height).  A target on a source gets that source's image
+ *   field, not its own.  The plan keeps two child plans (Stokeslet and Laplace charges +
+ *   dipoles, open boundary, the same p, q and options); kafmm_tree_info, kafmm_phase_times
+ *   and kafmm_get_counters report the Stokeslet child; batches, kafmm_autotune, the tree
+ *   queries, kafmm_get_operator and the RPY calls answer KAFMM_ERR_ARG. */
+typedef enum { KAFMM_BC_OPEN = 0, KAFMM_BC_PXYZ = 3, KAFMM_BC_WALL = 4 } kafmm_bc;
 
 typedef enum { KAFMM_F32 = 0, KAFMM_F64 = 1 } kafmm_dtype;
 
@@ -184,8 +198,16 @@ enum {
    * periodic operator become r x r matrices (r padded to 64; p = 10, Laplace table: 256 instead
    * of 488 rows, 256 instead of 512 k-values), the leaves' S->M potentials and the X-list
    * potentials are projected once, and the equivalent densities come from V S^+ applied to the
-   * projections.  Applied at the next kafmm_set_points (operators rebuilt). */
-  KAFMM_OPT_COMPRESS = 15
+   * projections.  2: as 1, and when rounding the larger rank down to a multiple of 64 keeps at
+   * least 90 % of it, only that many leading singular vectors are kept (p = 10: 192 of 202), so
+   * no row or k-value of the tensor-core tiles is padding.  Applied at the next
+   * kafmm_set_points (operators rebuilt). */
+  KAFMM_OPT_COMPRESS = 15,
+  /* Sources per staging buffer of the near-field kernel (two buffers: the copies of one batch
+   * of U-list sources are in flight while the previous batch is evaluated).  0 (default): 20 KB
+   * per buffer (640 FP32 Stokeslet sources); 64 .. 4096 otherwise; never fewer than the points
+   * of one equivalent surface.  kafmm_autotune times 256, 640 and 1280. */
+  KAFMM_OPT_LEAF_STAGE = 16
 };
 enum { KAFMM_TC_TF32X3 = 0, KAFMM_TC_BF16X3 = 1, KAFMM_TC_AUTO = 2 };
 enum { KAFMM_PREC_FP64 = 0, KAFMM_PREC_FP32 = 1, KAFMM_PREC_MIXED = 2 };
@@ -249,13 +271,14 @@ int kafmm_set_points_batched(kafmm_plan_t plan, int n_prob, const int64_t* src_o
  * S->T (U) -- Sec. II, Fig. kifmmgraph. */
 int kafmm_eval(kafmm_plan_t plan, const void* s, void* g, int dtype);
 
-/* Autotuner of the tensor-core kernels: for the current points and the source values s
- * (device arrays; g receives the values of the last trial), times kafmm_eval for every
- * combination of KAFMM_OPT_TC_TILING (2, 1; the work lists are rebuilt for each and the host
- * time of that build is added to the score), KAFMM_OPT_TC_STAGES (2, 4) and
- * KAFMM_OPT_TC_RANGES (1, 2, 4, 8), best of two runs each, and keeps the fastest in the plan.
- * chosen (host, may be NULL) receives {stages, ranges, tiling}.  Without tensor cores (FP64 /
- * FP32 forms) it changes nothing.  Call it again when the tree changes much. */
+/* Autotuner: for the current points and the source values s (device arrays; g receives the
+ * values of the last trial), times kafmm_eval for every combination of KAFMM_OPT_TC_TILING
+ * (2, 1; the work lists are rebuilt for each and the host time of that build is added to the
+ * score), KAFMM_OPT_TC_STAGES (2, 4) and KAFMM_OPT_TC_RANGES (1, 2, 4, 8), best of two runs
+ * each (tensor-core plans only), then the near-field staging KAFMM_OPT_LEAF_STAGE (256, 640,
+ * 1280 sources per buffer) on the leaf phase alone, and keeps the fastest in the plan.  chosen
+ * (host, may be NULL, 4 entries) receives {stages, ranges, tiling, leaf stage}.  Call it again
+ * when the tree changes much. */
 int kafmm_autotune(kafmm_plan_t plan, const void* s, void* g, int dtype, int64_t* chosen);
 
 /* Synchronises the plan's stream and reports (then clears) the device status accumulated by

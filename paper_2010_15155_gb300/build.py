@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkafmm.so")
-SOURCES = ["api.cu", "tree.cu", "operators.cu", "eval.cu", "m2l_tc.cu", "rpy.cu", "peaks.cu"]
+SOURCES = ["api.cu", "tree.cu", "operators.cu", "eval.cu", "m2l_tc.cu", "rpy.cu", "peaks.cu", "wall.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

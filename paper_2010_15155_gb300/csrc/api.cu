@@ -123,6 +123,10 @@ static thread_local std::string g_err;
   }                                                            \
   Plan& P = *reinterpret_cast<Plan*>(pl);
 
+// Wall plans: queries of the tree, the operators, the autotuner and the RPY calls do not apply.
+#define NOT_FOR_WALL(name)                                                             \
+  if (P.wall_child[0]) return fail(P, KAFMM_ERR_ARG, name " is not available for a wall plan");
+
 #define CKP(call)                                          \
   do {                                                     \
     cudaError_t e_ = (call);                               \
@@ -137,8 +141,9 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
   *out = nullptr;
   if ((int)kernel < 0 || (int)kernel > 6 ||
       ((kernel == KAFMM_LAPLACE_QD || kernel == KAFMM_STOKES_DL || kernel == KAFMM_STOKES_PVEL) &&
-       bc == KAFMM_BC_PXYZ) || (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ) || p < 2 ||
-      p > 16 || q < 1 || q > 4096) {
+       bc == KAFMM_BC_PXYZ) ||
+      (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ && bc != KAFMM_BC_WALL) ||
+      (bc == KAFMM_BC_WALL && kernel != KAFMM_STOKESLET) || p < 2 || p > 16 || q < 1 || q > 4096) {
     g_err = "kafmm_plan: invalid kernel, boundary condition, order (2..16) or leaf size (1..4096)";
     return KAFMM_ERR_ARG;
   }
@@ -156,12 +161,29 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
       return KAFMM_ERR_CUDA;
     }
   }
+  if (bc == KAFMM_BC_WALL) {   // the sums of the image system: Stokeslet, Laplace charges + dipoles
+    const kafmm_kernel kk[2] = {KAFMM_STOKESLET, KAFMM_LAPLACE_QD};
+    for (int c = 0; c < 2; ++c) {
+      int rc = kafmm_plan(kk[c], KAFMM_BC_OPEN, p, q, &P->wall_child[c]);
+      if (rc) {
+        for (int d = 0; d < c; ++d) kafmm_destroy(P->wall_child[d]);
+        for (int i = 0; i < 8; ++i) cudaEventDestroy(P->ev[i]);
+        delete P;
+        return rc;
+      }
+    }
+  }
   *out = reinterpret_cast<kafmm_plan_t>(P);
   return 0;
 }
 
 extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
   PLAN_CHECK(pl);
+  for (int c = 0; c < 2; ++c)   // a wall plan's sums take the same options
+    if (P.wall_child[c]) {
+      int rc = kafmm_set_option(P.wall_child[c], key, value);
+      if (rc) return fail(P, rc, "%s", kafmm_last_error(P.wall_child[c]));
+    }
   switch (key) {
     case KAFMM_OPT_PRECISION:
       if (value < 0 || value > 2) return fail(P, KAFMM_ERR_ARG, "bad precision %lld", (long long)value);
@@ -222,8 +244,13 @@ extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
       if (value < 0 || value > 1) return fail(P, KAFMM_ERR_ARG, "test stall must be 0 or 1");
       P.stall_test = (int)value;
       return 0;
+    case KAFMM_OPT_LEAF_STAGE:
+      if (value != 0 && (value < 64 || value > 4096))
+        return fail(P, KAFMM_ERR_ARG, "leaf staging must be 0 (default) or 64 .. 4096 sources");
+      P.leaf_stage = (int)value;
+      return 0;
     case KAFMM_OPT_COMPRESS:
-      if (value < 0 || value > 1) return fail(P, KAFMM_ERR_ARG, "compress must be 0 or 1");
+      if (value < 0 || value > 2) return fail(P, KAFMM_ERR_ARG, "compress must be 0, 1 or 2");
       if (P.compress_opt != (int)value) {
         P.compress_opt = (int)value;
         configure(P);
@@ -250,6 +277,8 @@ extern "C" int kafmm_set_domain(kafmm_plan_t pl, const double origin[3], double 
   for (int d = 0; d < 3; ++d) P.origin[d] = origin[d];
   P.L = L;
   P.have_points = false;
+  for (int c = 0; c < 2; ++c)
+    if (P.wall_child[c]) kafmm_set_domain(P.wall_child[c], origin, L);
   return 0;
 }
 
@@ -257,7 +286,8 @@ extern "C" int kafmm_set_domain(kafmm_plan_t pl, const double origin[3], double 
 static int set_points_impl(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, int dtype,
                            int n_prob, const int64_t* soff, const int64_t* toff) {
   P.have_points = false;
-  int rc = ensure_ops(P);
+  const bool wall = P.wall_child[0] != nullptr;
+  int rc = wall ? 0 : ensure_ops(P);
   if (rc) return rc;
   g_launches = 0;
   size_t es = dtype == KAFMM_F64 ? 8 : 4;
@@ -276,6 +306,13 @@ static int set_points_impl(Plan& P, const void* y, int64_t ns, const void* x, in
     CKP(P.io_aux.reserve(es * 3 * nt));
     CKP(cudaMemcpyAsync(P.io_aux.p, x, es * 3 * nt, cudaMemcpyHostToDevice, P.stream));
     xd = P.io_aux.p;
+  }
+  if (wall) {
+    rc = wall_set_points(P, yd, ns, xd, nt, dtype);
+    if (rc) return rc;
+    P.launches_points = g_launches;
+    P.have_points = true;
+    return 0;
   }
   rc = build_tree(P, yd, ns, xd, nt, dtype, n_prob, soff, toff);
   if (rc) return rc;
@@ -304,6 +341,7 @@ extern "C" int kafmm_set_points_batched(kafmm_plan_t pl, int n_prob, const int64
                                         const int64_t* trg_offsets, const void* y, const void* x,
                                         int dtype) {
   PLAN_CHECK(pl);
+  NOT_FOR_WALL("kafmm_set_points_batched")
   P.have_points = false;
   if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || n_prob < 1 || n_prob > KAFMM_MAX_PROBLEMS ||
       !src_offsets || !trg_offsets)
@@ -331,7 +369,7 @@ extern "C" int kafmm_eval(kafmm_plan_t pl, const void* s, void* g, int dtype) {
   if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "kafmm_eval before kafmm_set_points");
   if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || (P.tree.n_src > 0 && !s) || (P.tree.n_trg > 0 && !g))
     return fail(P, KAFMM_ERR_ARG, "kafmm_eval: bad arguments");
-  int rc = ensure_ops(P);
+  int rc = P.wall_child[0] ? 0 : ensure_ops(P);
   if (rc) return rc;
   size_t es = dtype == KAFMM_F64 ? 8 : 4;
   const void* sd = s;
@@ -351,7 +389,7 @@ extern "C" int kafmm_eval(kafmm_plan_t pl, const void* s, void* g, int dtype) {
   bool check = P.sync || host_out;
   if (check) CKP(cudaMemsetAsync(P.tree.status.p, 0, 4, P.stream));
   long long l0 = g_launches;
-  rc = evaluate(P, sd, gd, dtype);
+  rc = P.wall_child[0] ? wall_eval(P, sd, gd, dtype) : evaluate(P, sd, gd, dtype);
   P.launches_eval = g_launches - l0;
   if (rc) return rc;
   if (host_out)
@@ -366,6 +404,7 @@ extern "C" int kafmm_eval(kafmm_plan_t pl, const void* s, void* g, int dtype) {
 
 extern "C" int kafmm_autotune(kafmm_plan_t pl, const void* s, void* g, int dtype, int64_t* chosen) {
   PLAN_CHECK(pl);
+  NOT_FOR_WALL("kafmm_autotune")
   if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "kafmm_autotune before kafmm_set_points");
   if ((dtype != KAFMM_F32 && dtype != KAFMM_F64) || (P.tree.n_src > 0 && !s) || (P.tree.n_trg > 0 && !g))
     return fail(P, KAFMM_ERR_ARG, "kafmm_autotune: bad arguments");
@@ -418,16 +457,48 @@ extern "C" int kafmm_autotune(kafmm_plan_t pl, const void* s, void* g, int dtype
   }
   P.tc_stages = best_st;
   P.tc_ranges = best_rg;
+  // near field: sources per staging buffer, timed on the leaf phase alone
+  int best_ls = P.leaf_stage;
+  {
+    const int stages_leaf[3] = {256, 640, 1280};
+    const int keep_sync = P.sync;
+    P.sync = 1;
+    float best = 3.4e38f;
+    int rc = 0;
+    for (int i = 0; i < 3 && !rc; ++i) {
+      P.leaf_stage = stages_leaf[i];
+      float t = 0.f;
+      for (int rep = 0; rep < 3 && !rc; ++rep) {   // first run warms the configuration
+        rc = kafmm_eval(pl, s, g, dtype);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, P.ev[6], P.ev[7]);
+        if (rep == 1 || (rep == 2 && ms < t)) t = ms;
+      }
+      if (!rc && t < best) {
+        best = t;
+        best_ls = stages_leaf[i];
+      }
+    }
+    P.sync = keep_sync;
+    if (rc) return rc;
+    P.leaf_stage = best_ls;
+  }
   if (chosen) {
     chosen[0] = best_st;
     chosen[1] = best_rg;
     chosen[2] = best_tl;
+    chosen[3] = best_ls;
   }
   return 0;
 }
 
 extern "C" int kafmm_status(kafmm_plan_t pl) {
   PLAN_CHECK(pl);
+  for (int c = 0; c < 2; ++c)
+    if (P.wall_child[c]) {
+      int rc = kafmm_status(P.wall_child[c]);
+      if (rc) return fail(P, rc, "%s", kafmm_last_error(P.wall_child[c]));
+    }
   if (!P.tree.status.p) return 0;
   unsigned st = 0;
   CKP(cudaMemcpyAsync(&st, P.tree.status.p, 4, cudaMemcpyDeviceToHost, P.stream));
@@ -500,6 +571,7 @@ extern "C" int kafmm_rpy_velocity_noalloc(kafmm_plan_t pl, const void* s, const 
 
 extern "C" int kafmm_tree_info(kafmm_plan_t pl, int64_t* info, int n) {
   PLAN_CHECK(pl);
+  if (P.wall_child[0]) return kafmm_tree_info(P.wall_child[0], info, n);
   if (!info || n < 0) return fail(P, KAFMM_ERR_ARG, "bad info array");
   if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "no points");
   const Tree& T = P.tree;
@@ -539,6 +611,7 @@ __global__ void k_vtab_count(const int32_t* vtab, int nbox, int64_t* cnt) {
 extern "C" int kafmm_get_tree(kafmm_plan_t pl, int32_t* level, int32_t* anchor, int32_t* parent,
                               int8_t* leaf) {
   PLAN_CHECK(pl);
+  NOT_FOR_WALL("kafmm_get_tree")
   if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "no points");
   Tree& T = P.tree;
   int nb = T.nbox;
@@ -565,6 +638,7 @@ extern "C" int kafmm_get_tree(kafmm_plan_t pl, int32_t* level, int32_t* anchor, 
 extern "C" int kafmm_get_list(kafmm_plan_t pl, int kind, int64_t* offsets, int32_t* entries,
                               int8_t* shifts) {
   PLAN_CHECK(pl);
+  NOT_FOR_WALL("kafmm_get_list")
   if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "no points");
   if (kind < 0 || kind > 3) return fail(P, KAFMM_ERR_ARG, "bad list kind");
   Tree& T = P.tree;
@@ -610,6 +684,7 @@ extern "C" int kafmm_get_list(kafmm_plan_t pl, int kind, int64_t* offsets, int32
 
 extern "C" int kafmm_phase_times(kafmm_plan_t pl, double* t, int n) {
   PLAN_CHECK(pl);
+  if (P.wall_child[0]) return kafmm_phase_times(P.wall_child[0], t, n);
   if (!t) return fail(P, KAFMM_ERR_ARG, "null array");
   // ev: 0 start of set_points, 1 tree done, 2 lists done, 3 eval start, 4 upward done,
   //     5 M->L done, 6 downward done, 7 eval done
@@ -629,6 +704,7 @@ extern "C" int kafmm_phase_times(kafmm_plan_t pl, double* t, int n) {
 
 extern "C" int kafmm_get_counters(kafmm_plan_t pl, int64_t* c, int n) {
   PLAN_CHECK(pl);
+  if (P.wall_child[0]) return kafmm_get_counters(P.wall_child[0], c, n);
   if (!c || n < 0) return fail(P, KAFMM_ERR_ARG, "null array");
   const bool cm = P.use_tc && P.cmp;
   int64_t v[11] = {P.launches_points, P.launches_eval, P.use_tc ? 1 : 0,
@@ -644,6 +720,7 @@ extern "C" int kafmm_get_counters(kafmm_plan_t pl, int64_t* c, int n) {
 
 extern "C" int kafmm_get_operator(kafmm_plan_t pl, int slot, double* out) {
   PLAN_CHECK(pl);
+  NOT_FOR_WALL("kafmm_get_operator")
   if (!out || slot < 0 || slot >= N_OPS) return fail(P, KAFMM_ERR_ARG, "bad operator slot");
   int rc = ensure_ops(P);
   if (rc) return rc;
@@ -661,8 +738,14 @@ extern "C" int kafmm_get_operator(kafmm_plan_t pl, int slot, double* out) {
 extern "C" int kafmm_destroy(kafmm_plan_t pl) {
   if (!pl) return 0;
   Plan* P = reinterpret_cast<Plan*>(pl);
+  for (int c = 0; c < 2; ++c)
+    if (P->wall_child[c]) kafmm_destroy(P->wall_child[c]);
   for (int i = 0; i < 8; ++i)
     if (P->ev[i]) cudaEventDestroy(P->ev[i]);
+  if (P->wl_event) {
+    cudaEventSynchronize(P->wl_event);
+    cudaEventDestroy(P->wl_event);
+  }
   delete P;
   return 0;
 }

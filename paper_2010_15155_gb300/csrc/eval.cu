@@ -1,6 +1,7 @@
 // The KAFMM evaluation (Sec. II, Fig. kifmmgraph): S->M, M->M, M->L, S->L, L->L, and at the
 // leaves L->T, M->T, S->T; CUDA-core kernels in FP32 or FP64.
 #include <algorithm>
+#include <cstring>
 
 #include "physics.cuh"
 #include "plan.cuh"
@@ -560,26 +561,43 @@ __device__ inline void far_eval(T xl, T yl, T zl, const typename V4<T>::type& p,
   }
 }
 
+// Targets per thread of the leaf kernel: two in the FP32 form for tables of at most six
+// outputs (each staged source or equivalent point then feeds two targets), one otherwise.
+template <class T, int PR>
+struct LeafTT { static constexpr int V = (sizeof(T) == 4 && ProbInfo<PR>::KT <= 6) ? 2 : 1; };
+
+// Leaf kernel, one block per target leaf.  Work split: a pass takes up to LEAF_THREADS x tt
+// targets (tt = 2 when the leaf holds more than 64 and the table allows it); its targets are
+// dealt to S slots of tt targets each, and the G = LEAF_THREADS / S threads of a slot (lane-major:
+// consecutive lanes) split the sources of every interaction list among themselves; the G
+// partial sums of a target are combined by warp shuffles when G divides 32, else through
+// shared memory.  Far field first (L->T from the leaf's own downward equivalent density, M->T
+// over the W list; equivalent points generated in shared memory), then the U list S->T with the
+// sources staged by cp.async.bulk into two buffers: the copies of batch i + 1 are in flight while
+// batch i is evaluated.
 template <class T, int PR>
 __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
   using T4 = typename V4<T>::type;
   constexpr int KT = ProbInfo<PR>::KT, C = ProbInfo<PR>::C, D = ProbInfo<PR>::D, NV = ProbInfo<PR>::NV;
+  constexpr int TT = LeafTT<T, PR>::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T4* sp = reinterpret_cast<T4*>(smem_raw);          // [cap]
-  T4* sv = sp + a.cap;                                // [cap * NV]
-  T* red = reinterpret_cast<T*>(sv + a.cap * NV);     // [LEAF_THREADS * KT]
-  __shared__ uint64_t bar, stall_bar;
-  __shared__ int ent_n, ent_cnt[LEAF_MAX_ENT], ent_sc[LEAF_MAX_ENT];
-  __shared__ int next_e, next_s, done, bail;
+  T4* sp = reinterpret_cast<T4*>(smem_raw);          // [2][cap] source / equivalent positions
+  T4* sv = sp + 2 * a.cap;                            // [2][cap * NV] their values
+  T* red = reinterpret_cast<T*>(sv + 2 * a.cap * NV); // [LEAF_THREADS][TT][KT]
+  __shared__ uint64_t bar[2], stall_bar;
+  __shared__ int ent_n[2], ent_cnt[2][LEAF_MAX_ENT], ent_sc[2][LEAF_MAX_ENT], have[2];
+  __shared__ int next_e, next_s, bail;
 
-  int b = a.leaves[blockIdx.x];
+  const int b = a.leaves[blockIdx.x];
   T cx, cy, cz, r;
   box_centre<T>(a.t, b, a.geo.L, a.geo.org, cx, cy, cz, r);
-  int t0 = a.t.tb[b], t1 = a.t.te[b];
-  int nt = t1 - t0;
+  const int t0 = a.t.tb[b], t1 = a.t.te[b];
+  const int nt = t1 - t0;
   if (nt <= 0) return;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     if (a.stall_test) mbar_init(&stall_bar, 1);
     bail = 0;
   }
@@ -587,39 +605,49 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
   if (a.stall_test) {
     // test aid: a wait that nothing completes runs out after the wait limit; the block then
     // takes the wind-down path (no copy has been issued yet) and leaves without output
-    if (threadIdx.x == 0 && !mbar_wait_bounded(&stall_bar, 0, a.status, a.lim)) bail = 1;
+    if (tid == 0 && !mbar_wait_bounded(&stall_bar, 0, a.status, a.lim)) bail = 1;
     __syncthreads();
     if (bail) return;
   }
-  uint32_t phase = 0;
-  int ntp = ((nt + 31) / 32) * 32;
-  if (ntp > LEAF_THREADS) ntp = LEAF_THREADS;
-  int G = LEAF_THREADS / ntp;
-  int grp = threadIdx.x / ntp, ti = threadIdx.x % ntp;
-  if (grp >= G) grp = -1;
-  int64_t u0 = a.u_off[b], u1 = a.u_off[b + 1];
-  for (int c0 = t0; c0 < t1; c0 += ntp) {
-    int it = c0 + ti;
-    bool act = grp >= 0 && it < t1;
-    T xl = 0, yl = 0, zl = 0, xg = 0, yg = 0, zg = 0;   // target: local and global coordinates
-    if (act) {
-      T4 x = a.tpos[it];
-      xg = x.x;
-      yg = x.y;
-      zg = x.z;
-      xl = x.x - cx;
-      yl = x.y - cy;
-      zl = x.z - cz;
-    }
-    T bi = 0;   // the target's own radius (RPY with one shared point set)
-    if (act && (PR == P_RPY_L4 || PR == P_RPY_G) && a.contact) bi = a.sval[(int64_t)it * NV].w;
-    T acc[KT], far[KT], comp[KT];
+  const int tt = (TT == 2 && nt > 64) ? 2 : 1;
+  const int per_pass = min(nt, LEAF_THREADS * tt);
+  const int S = (per_pass + tt - 1) / tt;            // slots
+  const int G = max(1, LEAF_THREADS / S);            // threads per slot
+  const int slot = tid / G, grp = tid % G;
+  const bool in_slot = slot < S;
+  const bool shfl = G <= 32 && (32 % G) == 0;
+  const int64_t u0 = a.u_off[b], u1 = a.u_off[b + 1];
+  uint32_t ph[2] = {0u, 0u};
+
+  for (int p0 = t0; p0 < t1; p0 += per_pass) {
+    const int p1 = min(t1, p0 + per_pass);
+    int it[TT];
+    bool act[TT];
+    T xl[TT], yl[TT], zl[TT], xg[TT], yg[TT], zg[TT], bi[TT];
+    T acc[TT][KT], comp[TT][KT];
 #pragma unroll
-    for (int k = 0; k < KT; ++k) acc[k] = far[k] = comp[k] = 0;
+    for (int u = 0; u < TT; ++u) {
+      it[u] = p0 + slot + u * S;
+      act[u] = in_slot && u < tt && it[u] < p1;
+      xl[u] = yl[u] = zl[u] = xg[u] = yg[u] = zg[u] = bi[u] = 0;
+      if (act[u]) {
+        T4 x = a.tpos[it[u]];
+        xg[u] = x.x;
+        yg[u] = x.y;
+        zg[u] = x.z;
+        xl[u] = x.x - cx;
+        yl[u] = x.y - cy;
+        zl[u] = x.z - cz;
+        // the target's own radius (RPY with one shared point set)
+        if ((PR == P_RPY_L4 || PR == P_RPY_G) && a.contact) bi[u] = a.sval[(int64_t)it[u] * NV].w;
+      }
+#pragma unroll
+      for (int k = 0; k < KT; ++k) acc[u][k] = comp[u][k] = 0;
+    }
 
     if (!a.near_only) {
       // ---- L->T and M->T: equivalent points staged (local coordinates, reference c_B)
-      int nw = (int)(a.w_off[b + 1] - a.w_off[b]);
+      const int nw = (int)(a.w_off[b + 1] - a.w_off[b]);
       for (int e = -1; e < nw; ++e) {
         int sbx = b, sc = 13;
         T alpha = T(ALPHA_DE);
@@ -635,10 +663,9 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
         shift_decode(sc, sx, sy, sz);
         T ax, ay, az, ar;
         box_centre<T>(a.t, sbx, a.geo.L, a.geo.org, ax, ay, az, ar);
-        T ox = ax + (T)(sx * a.geo.L) - cx, oy = ay + (T)(sy * a.geo.L) - cy,
-          oz = az + (T)(sz * a.geo.L) - cz;
+        T ox = ax + (T)(sx * a.geo.L) - cx, oy = ay + (T)(sy * a.geo.L) - cy, oz = az + (T)(sz * a.geo.L) - cz;
         __syncthreads();
-        for (int k = threadIdx.x; k < a.n; k += blockDim.x) {
+        for (int k = tid; k < a.n; k += blockDim.x) {
           T4 p;
           p.x = ox + alpha * ar * a.unit[3 * k];
           p.y = oy + alpha * ar * a.unit[3 * k + 1];
@@ -667,173 +694,241 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
           sv[k] = q;
         }
         __syncthreads();
-        if (act) {  // partial sums per 32 equivalent points, then per surface
-          T fs[KT];
+        if (act[0]) {  // partial sums per 32 equivalent points of a group, then per surface
+          T fs[TT][KT];
 #pragma unroll
-          for (int q = 0; q < KT; ++q) fs[q] = 0;
+          for (int u = 0; u < TT; ++u)
+#pragma unroll
+            for (int q = 0; q < KT; ++q) fs[u][q] = 0;
           for (int k0 = grp; k0 < a.n; k0 += 32 * G) {
-            T fp[KT];
+            T fp[TT][KT];
 #pragma unroll
-            for (int q = 0; q < KT; ++q) fp[q] = 0;
-            int kend = min(a.n, k0 + 32 * G);
-            for (int k = k0; k < kend; k += G) far_eval<T, PR>(xl, yl, zl, sp[k], sv[k], fp);
+            for (int u = 0; u < TT; ++u)
 #pragma unroll
-            for (int q = 0; q < KT; ++q) fs[q] += fp[q];
+              for (int q = 0; q < KT; ++q) fp[u][q] = 0;
+            const int kend = min(a.n, k0 + 32 * G);
+            for (int k = k0; k < kend; k += G) {
+              const T4 pk = sp[k], qk = sv[k];
+#pragma unroll
+              for (int u = 0; u < TT; ++u)
+                if (u < tt) far_eval<T, PR>(xl[u], yl[u], zl[u], pk, qk, fp[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < TT; ++u)
+#pragma unroll
+              for (int q = 0; q < KT; ++q) fs[u][q] += fp[u][q];
           }
 #pragma unroll
-          for (int q = 0; q < KT; ++q) far[q] += fs[q];
+          for (int u = 0; u < TT; ++u)
+#pragma unroll
+            for (int q = 0; q < KT; ++q) acc[u][q] += fs[u][q];
         }
       }
     }
 
-    // ---- S->T over the U list, staged in batches of whole (or split) entries
-    if (threadIdx.x == 0) {
+    // ---- S->T over the U list: batches of whole (or split) entries, two staging buffers
+    // (thread 0 composes a batch: bulk copies of its sources and values completing on the
+    // buffer's mbarrier)
+    auto compose = [&](int bf) -> int {
+      T4* dp = sp + bf * a.cap;
+      T4* dv = sv + bf * a.cap * NV;
+      int used = 0, ne = 0;
+      uint32_t bytes = 0;
+      while (next_e < u1 && ne < LEAF_MAX_ENT && used < a.cap) {
+        int32_t ent = a.u_ent[next_e];
+        int sbx = entry_box(ent);
+        int s0 = a.t.sb[sbx] + next_s, s1 = a.t.se[sbx];
+        int take = min(s1 - s0, a.cap - used);
+        if (take > 0) {
+          bulk_g2s(dp + used, a.spos + s0, (uint32_t)(take * sizeof(T4)), &bar[bf]);
+          bulk_g2s(dv + used * NV, a.sval + (int64_t)s0 * NV, (uint32_t)(take * NV * sizeof(T4)), &bar[bf]);
+          bytes += (uint32_t)(take * (1 + NV) * sizeof(T4));
+          ent_cnt[bf][ne] = take;
+          ent_sc[bf][ne] = entry_shift(ent);
+          ++ne;
+          used += take;
+        }
+        if (s0 + take >= s1) {
+          ++next_e;
+          next_s = 0;
+        } else {
+          next_s += take;
+        }
+      }
+      ent_n[bf] = ne;
+      return ne > 0 ? (int)bytes : 0;
+    };
+    __syncthreads();   // the far field has finished reading buffer 0 (its equivalent points)
+    if (tid == 0) {
       next_e = (int)u0;
       next_s = 0;
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      for (int bf = 0; bf < 2; ++bf) {
+        const int bytes = compose(bf);
+        have[bf] = bytes > 0;
+        if (bytes) mbar_expect_tx(&bar[bf], (uint32_t)bytes);
+      }
     }
     __syncthreads();
-    while (true) {
-      if (threadIdx.x == 0) {
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        int used = 0, ne = 0;
-        uint32_t bytes = 0;
-        while (next_e < u1 && ne < LEAF_MAX_ENT && used < a.cap) {
-          int32_t ent = a.u_ent[next_e];
-          int sbx = entry_box(ent);
-          int s0 = a.t.sb[sbx] + next_s, s1 = a.t.se[sbx];
-          int take = min(s1 - s0, a.cap - used);
-          if (take > 0) {
-            bulk_g2s(sp + used, a.spos + s0, (uint32_t)(take * sizeof(T4)), &bar);
-            bulk_g2s(sv + used * NV, a.sval + (int64_t)s0 * NV, (uint32_t)(take * NV * sizeof(T4)), &bar);
-            bytes += (uint32_t)(take * (1 + NV) * sizeof(T4));
-            ent_cnt[ne] = take;
-            ent_sc[ne] = entry_shift(ent);
-            ++ne;
-            used += take;
-          }
-          if (s0 + take >= s1) {
-            ++next_e;
-            next_s = 0;
-          } else {
-            next_s += take;
-          }
-        }
-        ent_n = ne;
-        done = ne == 0;
-        if (ne > 0) mbar_expect_tx(&bar, bytes);
-      }
-      __syncthreads();
-      if (done) break;
+    for (int itb = 0;; ++itb) {
+      const int bf = itb & 1;
+      if (!have[bf]) break;
       // wait for this batch (bounded).  On expiry the block issues no further copy, skips the
-      // compute and the output, waits once more (bounded) for the copies of this batch still
-      // in flight, and leaves; the status word carries ST_TIMEOUT to the host.
-      if (!mbar_wait_bounded(&bar, phase, a.status, a.lim)) bail = 1;
+      // compute and the output, waits once more (bounded) for the copies still in flight, and
+      // leaves; the status word carries ST_TIMEOUT to the host.
+      if (!mbar_wait_bounded(&bar[bf], ph[bf], a.status, a.lim)) bail = 1;
       __syncthreads();
       if (bail) {
-        if (threadIdx.x == 0) mbar_wait_bounded(&bar, phase, a.status, a.lim);
+        if (tid == 0) {
+          mbar_wait_bounded(&bar[bf], ph[bf], a.status, a.lim);
+          if (have[bf ^ 1]) mbar_wait_bounded(&bar[bf ^ 1], ph[bf ^ 1], a.status, a.lim);
+        }
         __syncthreads();
         return;
       }
-      phase ^= 1;
-      if (act) {
+      ph[bf] ^= 1u;
+      const T4* bp = sp + bf * a.cap;
+      const T4* bv = sv + bf * a.cap * NV;
+      if (act[0]) {
         int base = 0;
-        for (int e = 0; e < ent_n; ++e) {
+        for (int e = 0; e < ent_n[bf]; ++e) {
           int sx, sy, sz;
-          shift_decode(ent_sc[e], sx, sy, sz);
-          T ox = (T)(sx * a.geo.L) - cx, oy = (T)(sy * a.geo.L) - cy, oz = (T)(sz * a.geo.L) - cz;
-          int cnt = ent_cnt[e];
-          T pe[KT];  // partial sum of this entry (plain mode)
+          shift_decode(ent_sc[bf][e], sx, sy, sz);
+          const T ox = (T)(sx * a.geo.L) - cx, oy = (T)(sy * a.geo.L) - cy, oz = (T)(sz * a.geo.L) - cz;
+          const int cnt = ent_cnt[bf][e];
+          T pe[TT][KT];  // partial sums of this entry (plain mode)
 #pragma unroll
-          for (int k = 0; k < KT; ++k) pe[k] = 0;
+          for (int u = 0; u < TT; ++u)
+#pragma unroll
+            for (int k = 0; k < KT; ++k) pe[u][k] = 0;
+          bool done_fast = false;
           if constexpr ((PR == P_STK_L4 || PR == P_STK_G) && sizeof(T) == 4) {
             if (!a.kahan) {
-              // Stokeslet in FP32: the image shift folded into the target's global coordinates
-              // once per entry (exact for the unshifted entries, so the self pair stays at
-              // r = 0), the pair terms accumulated by FMAs, four sources in flight
-              const float xe = xg - (float)(sx * a.geo.L), ye = yg - (float)(sy * a.geo.L),
-                          ze = zg - (float)(sz * a.geo.L);
-              int j = grp;
-              for (; j + 3 * G < cnt; j += 4 * G) {
+              // Stokeslet in FP32: the image shift folded into the targets' global
+              // coordinates once per entry (exact for the unshifted entries, so the self pair
+              // stays at r = 0), every staged source feeding the thread's targets by FMAs
+              float xe[TT], ye[TT], ze[TT];
 #pragma unroll
-                for (int w = 0; w < 4; ++w) stk_pair_f32(xe, ye, ze, sp[base + j + w * G], sv[base + j + w * G], pe);
+              for (int u = 0; u < TT; ++u) {
+                xe[u] = xg[u] - (float)(sx * a.geo.L);
+                ye[u] = yg[u] - (float)(sy * a.geo.L);
+                ze[u] = zg[u] - (float)(sz * a.geo.L);
               }
-              for (; j < cnt; j += G) stk_pair_f32(xe, ye, ze, sp[base + j], sv[base + j], pe);
-#pragma unroll
-              for (int k = 0; k < KT; ++k) acc[k] += pe[k];
-              base += cnt;
-              continue;
+              if (tt == 2) {
+                for (int j = grp; j < cnt; j += G) {
+                  const float4 y = bp[base + j], f = bv[base + j];
+                  stk_pair_f32(xe[0], ye[0], ze[0], y, f, pe[0]);
+                  stk_pair_f32(xe[TT - 1], ye[TT - 1], ze[TT - 1], y, f, pe[TT - 1]);
+                }
+              } else {
+                int j = grp;
+                for (; j + G < cnt; j += 2 * G) {
+                  stk_pair_f32(xe[0], ye[0], ze[0], bp[base + j], bv[base + j], pe[0]);
+                  stk_pair_f32(xe[0], ye[0], ze[0], bp[base + j + G], bv[base + j + G], pe[0]);
+                }
+                if (j < cnt) stk_pair_f32(xe[0], ye[0], ze[0], bp[base + j], bv[base + j], pe[0]);
+              }
+              done_fast = true;
             }
           }
-          for (int j = grp; j < cnt; j += G) {
-            T4 y = sp[base + j];
-            T r0 = xl - (y.x + ox), r1 = yl - (y.y + oy), r2 = zl - (y.z + oz);
-            T tmp[KT];
+          if (!done_fast) {
+            for (int j = grp; j < cnt; j += G) {
+              const T4 y = bp[base + j];
+              const T4 v = bv[(base + j) * NV];
 #pragma unroll
-            for (int k = 0; k < KT; ++k) tmp[k] = 0;
-            T4 v = sv[(base + j) * NV];
-            if (PR == P_LAP) {
-              lap_st<T>(r0, r1, r2, v.x, tmp);
-            } else if (PR == P_LAPQD) {
-              lapqd_st<T, true>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
-            } else if (PR == P_PVEL) {
-              pvel_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
-            } else if (PR == P_STK_L4 || PR == P_STK_G) {
-              stk_st<T>(r0, r1, r2, v.x, v.y, v.z, tmp);
-            } else if (PR == P_REG_G) {   // S->T: the regularized kernel of the source's eps
-              reg_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
-            } else if (PR == P_RPY_L4 || PR == P_RPY_G) {
-              // contact pairs are left to the sphere-velocity pass, which adds their whole
-              // mobility (their far form is large and cancels there, beyond FP32 precision)
-              if (a.contact && in_contact<T>(xg, yg, zg, y.x, y.y, y.z, (T)(sx * a.geo.L), (T)(sy * a.geo.L),
-                                              (T)(sz * a.geo.L), bi, v.w))
-                continue;
-              rpy_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
-            } else {
-              T4 v1 = sv[(base + j) * NV + 1], v2 = sv[(base + j) * NV + 2];
-              T Dm[9] = {v.x, v.y, v.z, v.w, v1.x, v1.y, v1.z, v1.w, v2.x};
-              dl_st<T>(r0, r1, r2, Dm, tmp);
-            }
-            if (a.kahan) {
+              for (int u = 0; u < TT; ++u) {
+                if (u >= tt) continue;
+                T r0 = xl[u] - (y.x + ox), r1 = yl[u] - (y.y + oy), r2 = zl[u] - (y.z + oz);
+                T tmp[KT];
 #pragma unroll
-              for (int k = 0; k < KT; ++k) {
-                T yk = tmp[k] - comp[k];
-                T tk = acc[k] + yk;
-                comp[k] = (tk - acc[k]) - yk;
-                acc[k] = tk;
+                for (int k = 0; k < KT; ++k) tmp[k] = 0;
+                if (PR == P_LAP) {
+                  lap_st<T>(r0, r1, r2, v.x, tmp);
+                } else if (PR == P_LAPQD) {
+                  lapqd_st<T, true>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
+                } else if (PR == P_PVEL) {
+                  pvel_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
+                } else if (PR == P_STK_L4 || PR == P_STK_G) {
+                  stk_st<T>(r0, r1, r2, v.x, v.y, v.z, tmp);
+                } else if (PR == P_REG_G) {   // S->T: the regularized kernel of the source's eps
+                  reg_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
+                } else if (PR == P_RPY_L4 || PR == P_RPY_G) {
+                  // contact pairs are left to the sphere-velocity pass, which adds their whole
+                  // mobility (their far form is large and cancels there, beyond FP32 precision)
+                  if (a.contact && in_contact<T>(xg[u], yg[u], zg[u], y.x, y.y, y.z, (T)(sx * a.geo.L),
+                                                  (T)(sy * a.geo.L), (T)(sz * a.geo.L), bi[u], v.w))
+                    continue;
+                  rpy_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
+                } else {
+                  const T4 v1 = bv[(base + j) * NV + 1], v2 = bv[(base + j) * NV + 2];
+                  T Dm[9] = {v.x, v.y, v.z, v.w, v1.x, v1.y, v1.z, v1.w, v2.x};
+                  dl_st<T>(r0, r1, r2, Dm, tmp);
+                }
+                if (a.kahan) {
+#pragma unroll
+                  for (int k = 0; k < KT; ++k) {
+                    T yk = tmp[k] - comp[u][k];
+                    T tk = acc[u][k] + yk;
+                    comp[u][k] = (tk - acc[u][k]) - yk;
+                    acc[u][k] = tk;
+                  }
+                } else {
+#pragma unroll
+                  for (int k = 0; k < KT; ++k) pe[u][k] += tmp[k];
+                }
               }
-            } else {
-#pragma unroll
-              for (int k = 0; k < KT; ++k) pe[k] += tmp[k];
             }
           }
           if (!a.kahan) {
 #pragma unroll
-            for (int k = 0; k < KT; ++k) acc[k] += pe[k];
+            for (int u = 0; u < TT; ++u)
+#pragma unroll
+              for (int k = 0; k < KT; ++k) acc[u][k] += pe[u][k];
           }
           base += cnt;
         }
       }
-      __syncthreads();
-    }
-    // ---- combine the thread groups and write
-#pragma unroll
-    for (int k = 0; k < KT; ++k) acc[k] += far[k];
-    if (G > 1) {
-      if (grp >= 0)
-#pragma unroll
-        for (int k = 0; k < KT; ++k) red[(grp * ntp + ti) * KT + k] = acc[k];
-      __syncthreads();
-      if (grp == 0) {
-        for (int q = 1; q < G; ++q)
-#pragma unroll
-          for (int k = 0; k < KT; ++k) acc[k] += red[(q * ntp + ti) * KT + k];
+      __syncthreads();   // every read of buffer bf is done: it takes batch itb + 2
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        const int bytes = compose(bf);
+        have[bf] = bytes > 0;
+        if (bytes) mbar_expect_tx(&bar[bf], (uint32_t)bytes);
       }
-      __syncthreads();
     }
-    if (grp == 0 && it < t1) {
+    // ---- combine the G partial sums of each target and write
+    if (G > 1) {
+      if (shfl) {
 #pragma unroll
-      for (int k = 0; k < KT; ++k) a.g[(int64_t)it * KT + k] = acc[k] * out_scale<PR, T>(k);
+        for (int u = 0; u < TT; ++u)
+#pragma unroll
+          for (int k = 0; k < KT; ++k)
+            for (int o = G >> 1; o > 0; o >>= 1) acc[u][k] += __shfl_xor_sync(0xffffffffu, acc[u][k], o);
+      } else {
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < TT; ++u)
+#pragma unroll
+          for (int k = 0; k < KT; ++k) red[((int64_t)tid * TT + u) * KT + k] = acc[u][k];
+        __syncthreads();
+        if (grp == 0 && in_slot) {
+          for (int q = 1; q < G; ++q)
+#pragma unroll
+            for (int u = 0; u < TT; ++u)
+#pragma unroll
+              for (int k = 0; k < KT; ++k) acc[u][k] += red[((int64_t)(tid + q) * TT + u) * KT + k];
+        }
+      }
     }
+    if (grp == 0) {
+#pragma unroll
+      for (int u = 0; u < TT; ++u)
+        if (act[u]) {
+#pragma unroll
+          for (int k = 0; k < KT; ++k) a.g[(int64_t)it[u] * KT + k] = acc[u][k] * out_scale<PR, T>(k);
+        }
+    }
+    __syncthreads();   // the next pass reuses the staging buffers
   }
 }
 
@@ -912,7 +1007,10 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
   const size_t o_key = 0, o_xoff = o_key + 8 * (size_t)nb, o_vocc = o_xoff + 8 * (size_t)(nb + 1),
                o_tb = o_vocc + 32 * (size_t)nb, o_te = o_tb + 4 * (size_t)nb,
                o_lvl = o_te + 4 * (size_t)nb, o_leaf = o_lvl + nb, o_wflag = o_leaf + nb,
-               down_bytes = o_wflag + nb;
+               o_stats = (o_wflag + nb + 7) / 8 * 8, o_meta = o_stats + 24,
+               down_bytes = o_meta + 4 * 217;
+  // the previous build's uploads read the staging buffers: wait for them before refilling
+  if (P.wl_event) CK(cudaEventSynchronize(P.wl_event));
   CK(P.wl_down.reserve(down_bytes));
   HostBuf& H = P.wl_down;
   CK(cudaMemcpyAsync(H.as<void>(o_key), T.key.p, 8 * (size_t)nb, cudaMemcpyDeviceToHost, st));
@@ -923,7 +1021,19 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
   CK(cudaMemcpyAsync(H.as<void>(o_lvl), T.level.p, nb, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(H.as<void>(o_leaf), T.leaf.p, nb, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(H.as<void>(o_wflag), T.w_flag.p, nb, cudaMemcpyDeviceToHost, st));
+  // near-field pairs (status words 8-9), V entries and largest leaf (10-13), the grouped M->L
+  // pair histogram (216 counts and their total)
+  CK(cudaMemcpyAsync(H.as<void>(o_stats), T.status.as<unsigned>() + 8, 24, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o_meta), T.m2l_meta.p, 4 * 217, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  {
+    const unsigned long long* hs = H.as<unsigned long long>(o_stats);
+    T.near_pairs = (int64_t)hs[0];
+    T.n_v = (int64_t)hs[1];
+    T.max_leaf_pts = (int)hs[2];
+    memcpy(T.m2l_hist, H.as<unsigned>(o_meta), sizeof(unsigned) * 217);
+    T.m2l_npairs = (int64_t)T.m2l_hist[216];
+  }
   const uint64_t* key = H.as<uint64_t>(o_key);
   const int64_t* xoff = H.as<int64_t>(o_xoff);
   const uint8_t* oc = H.as<uint8_t>(o_vocc);
@@ -1050,7 +1160,9 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
   CK(cudaMemcpyAsync(P.tiles.p, U.as<void>(u_tiles), sizeof(int4) * W.tiles.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(P.tile_meta.p, U.as<void>(u_box), sizeof(int) * W.boxlist.size(),
                      cudaMemcpyHostToDevice, st));
-  CK(cudaStreamSynchronize(st));   // the staging buffers are reused by the next build
+  // the staging buffers are reused by the next build, which waits for this event first
+  if (!P.wl_event) CK(cudaEventCreateWithFlags(&P.wl_event, cudaEventDisableTiming));
+  CK(cudaEventRecord(P.wl_event, st));
   return 0;
 }
 
@@ -1283,10 +1395,12 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
     la.near_only = P.near_only;
     la.kahan = P.kahan;
     la.contact = P.contact_split() ? 1 : 0;
-    int cap = (int)(40960 / ((1 + NV) * sizeof(T4)));
+    // sources per staging buffer (two buffers): 20 KB each by default (640 FP32 Stokeslet
+    // sources), KAFMM_OPT_LEAF_STAGE otherwise; at least the equivalent points of a surface
+    int cap = P.leaf_stage > 0 ? P.leaf_stage : (int)(20480 / ((1 + NV) * sizeof(T4)));
     if (cap < P.n) cap = P.n;
     la.cap = cap;
-    size_t smem = (size_t)cap * (1 + NV) * sizeof(T4) + sizeof(T) * LEAF_THREADS * KT;
+    size_t smem = 2 * (size_t)cap * (1 + NV) * sizeof(T4) + sizeof(T) * LEAF_THREADS * LeafTT<T, PR>::V * KT;
     CK(cudaFuncSetAttribute(k_leaf<T, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     KL k_leaf<T, PR><<<W.leaves_n, LEAF_THREADS, smem, st>>>(la);
   }

@@ -530,6 +530,30 @@ static int build_compressed(Plan& P, const double* O, const std::vector<double>&
         isig[h].push_back(std::sqrt(w[k]));
       }
   }
+  // compress option 2: when rounding the larger rank down to a multiple of 64 keeps at least
+  // 90 % of it, keep only that many leading singular vectors (largest sigma) on both sides, so no
+  // row or k-value of the tensor-core tiles is padding
+  if (P.compress_opt == 2) {
+    const int rmax = (int)std::max(idx[0].size(), idx[1].size());
+    const int rdown = rmax / 64 * 64;
+    if (rdown >= 64 && 10 * rdown >= 9 * rmax)
+      for (int h = 0; h < 2; ++h) {
+        std::vector<int> ord(idx[h].size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return sig[h][a] > sig[h][b]; });
+        ord.resize(std::min<size_t>(ord.size(), (size_t)rdown));
+        std::vector<int> i2;
+        std::vector<double> s2, is2;
+        for (int o : ord) {
+          i2.push_back(idx[h][o]);
+          s2.push_back(sig[h][o]);
+          is2.push_back(isig[h][o]);
+        }
+        idx[h] = i2;
+        sig[h] = s2;
+        isig[h] = is2;
+      }
+  }
   const int ru = (int)idx[0].size(), rd = (int)idx[1].size();
   const int rp = std::max(64, (std::max(ru, rd) + 63) / 64 * 64);
   if (rp >= P.Rpad) return 0;   // nothing to gain: keep the dense coordinates

@@ -86,6 +86,7 @@ struct Plan {
   int rpy_contact = 0; // KAFMM_OPT_RPY_CONTACT: 0 off, 1 on
   WaitLimits wait;     // KAFMM_OPT_WAIT_LIMIT_US, KAFMM_OPT_WAIT_REPORT_US
   int stall_test = 0;  // KAFMM_OPT_TEST_STALL
+  int leaf_stage = 0;  // KAFMM_OPT_LEAF_STAGE: sources per staging buffer of the leaf kernel
   cudaStream_t stream = 0;
   double origin[3] = {0, 0, 0}, L = 1.0;
   int ks = 1, kt = 1;
@@ -136,6 +137,7 @@ struct Plan {
   DevBuf io_in, io_out, io_aux;     // staging for host pointers / dtype conversion
   DevBuf tiles, tile_meta;          // work lists of the gather-GEMM engine
   HostBuf wl_down, wl_up;           // pinned staging of the work-list build (tree in, lists out)
+  cudaEvent_t wl_event = nullptr;   // the last work-list upload (the staging buffers are free after it)
   double host_wl_ms = 0;            // host time of the last work-list build
   DevBuf m2l_parts;                 // partial M->L sums per offset range (tensor-core path)
   // grouped M->L: sorted pairs (keys, partial indices, ping-pong halves), pair boxes before
@@ -146,6 +148,10 @@ struct Plan {
   WorkLists wl;
   bool use_tc = false;              // tensor-core M->L available for this plan
   long long launches_points = 0, launches_eval = 0;  // kernel launches of the last calls
+  // no-slip wall (KAFMM_BC_WALL): the Stokeslet and Laplace charge + dipole child plans over
+  // the sources and their images, and the work arrays of the assembly
+  kafmm_plan_t wall_child[2] = {nullptr, nullptr};
+  DevBuf wall_buf[8];
   cudaEvent_t ev[8] = {0};
   double phase_ms[8] = {0};
   std::string err;
@@ -180,5 +186,9 @@ int rpy_velocity(Plan& P, const void* s_dev, const void* a_dev, const void* g_de
                  int dtype);
 int rpy_velocity_noalloc(Plan& P, const void* s_dev, const void* a_dev, const void* g_dev,
                          void* ua_dev, int dtype);
+
+// wall.cu
+int wall_set_points(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, int dtype);
+int wall_eval(Plan& P, const void* s, void* g, int dtype);
 
 }  // namespace kafmm

@@ -798,13 +798,17 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   unsigned* status = T.status.as<unsigned>();
   int* d_total = a.cnt + MAX_LEVELS + 1;
   KL k_root<<<grid_for(n_prob, 256), 256, 0, st>>>(a);
-  // levels in groups of 4; after each group the next level's box count is read back and the
-  // refinement stops once it is zero (a uniform tree of depth 4 takes 8 levels of launches,
-  // not 20)
-  int cnt[MAX_LEVELS];
-  constexpr int LEVEL_GROUP = 4;
-  for (int l0 = 0; l0 < MAX_LEVEL; l0 += LEVEL_GROUP) {
-    int l1 = std::min(MAX_LEVEL, l0 + LEVEL_GROUP);
+  // levels in groups: the first covers the depth a uniform tree of these points would have
+  // (ceil(log8(points / q)) + 1 levels below the root), later ones 4 levels each; after each
+  // group every level's box count and the status are read back at once and the refinement
+  // stops when the next level is empty (a uniform tree of depth 4: one group, one read-back)
+  int cnt[MAX_LEVELS + 1];
+  unsigned h_status = 0;
+  int est = 1;
+  for (double m = (double)npts / (double)(P.q > 0 ? P.q : 1) / std::max(1, n_prob); m > 1.0 && est < MAX_LEVEL; m /= 8.0)
+    ++est;
+  for (int l0 = 0, group = est + 1;; group = 4) {
+    int l1 = std::min(MAX_LEVEL, l0 + group);
     for (int l = l0; l < l1; ++l) {
       int g = grid_for(a.cap[l], 256);
       KL k_split<<<g, 256, 0, st>>>(a, l, status);
@@ -814,17 +818,13 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
       KL k_level_total<<<1, 32, 0, st>>>(a, l, d_total, status);
       KL k_emit<<<g, 256, 0, st>>>(a, l);
     }
-    if (l1 >= MAX_LEVEL) break;
-    int next = 0;
-    CK(cudaMemcpyAsync(&next, a.cnt + l1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(cnt, a.cnt, sizeof(int) * MAX_LEVELS, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (next == 0) break;
+    if (l1 >= MAX_LEVEL || cnt[l1] == 0 || (h_status & (ST_DOMAIN | ST_OVERFLOW))) break;
+    l0 = l1;
   }
   CK(cudaGetLastError());
-  unsigned h_status = 0;
-  CK(cudaMemcpyAsync(cnt, a.cnt, sizeof(int) * MAX_LEVELS, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
   if (h_status & ST_DOMAIN)
     return fail(P, KAFMM_ERR_DOMAIN, "a point lies outside [origin, origin + L)^3 or is not finite");
   if (h_status & ST_OVERFLOW) return fail(P, KAFMM_ERR_NOMEM, "octree level capacity exceeded");
@@ -915,12 +915,8 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   lo.near_pairs = (unsigned long long*)(T.status.as<unsigned>() + 8);
   CK(cudaMemsetAsync(lo.near_pairs, 0, 8, st));
   KL k_lists<true><<<g, 32, 0, st>>>(tv, lo);
-  unsigned long long pairs = 0;
-  CK(cudaMemcpyAsync(&pairs, lo.near_pairs, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaGetLastError());
   cudaEventRecord(P.ev[2], st);
-  CK(cudaStreamSynchronize(st));
-  T.near_pairs = (int64_t)pairs;
   // V entries, the largest leaf, and the pairs of the grouped M->L (count per box, then their
   // offsets by a scan; per (class, neighbour) totals for the tile layout)
   unsigned long long* stats = (unsigned long long*)(T.status.as<unsigned>() + 10);
@@ -936,13 +932,9 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
                                                    vmin, T.m2l_cnt.as<int>(), meta);
   scan_excl<int>(T.m2l_cnt.as<int>(), T.m2l_base.as<int>(), nb, nullptr,
                  reinterpret_cast<int*>(meta) + 217, reinterpret_cast<int*>(meta) + 216, st);
-  unsigned long long hs[2];
-  CK(cudaMemcpyAsync(hs, stats, 16, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(T.m2l_hist, meta, sizeof(unsigned) * 217, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  T.n_v = (int64_t)hs[0];
-  T.max_leaf_pts = (int)hs[1];
-  T.m2l_npairs = (int64_t)T.m2l_hist[216];
+  // the V entry count, the largest leaf, the near-field pair count and the grouped M->L pair
+  // histogram are read back with the work lists (build_worklists), in the same copy
+  CK(cudaGetLastError());
   return 0;
 }
 

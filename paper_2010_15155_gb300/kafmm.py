@@ -19,11 +19,11 @@ LIB_PATH = os.path.join(HERE, "libkafmm.so")
 
 # enums of include/kafmm.h
 LAPLACE, STOKESLET, RPY, STOKES_DL, STOKES_REG, LAPLACE_QD, STOKES_PVEL = 0, 1, 2, 3, 4, 5, 6
-BC_OPEN, BC_PXYZ = 0, 3
+BC_OPEN, BC_PXYZ, BC_WALL = 0, 3, 4
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN, OPT_TC_SPLIT = 1, 2, 3, 4, 5, 6
 OPT_SYNC, OPT_TC_STAGES, OPT_TC_RANGES, OPT_RPY_CONTACT, OPT_TC_TILING = 7, 8, 9, 10, 11
-OPT_WAIT_LIMIT_US, OPT_WAIT_REPORT_US, OPT_TEST_STALL, OPT_COMPRESS = 12, 13, 14, 15
+OPT_WAIT_LIMIT_US, OPT_WAIT_REPORT_US, OPT_TEST_STALL, OPT_COMPRESS, OPT_LEAF_STAGE = 12, 13, 14, 15, 16
 TC_TF32X3, TC_BF16X3, TC_AUTO = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 ML_G, ML_L4 = 0, 1
@@ -146,9 +146,10 @@ def kafmm_eval(plan, s, g, dtype):
 
 
 def kafmm_autotune(plan, s, g, dtype):
-    chosen = (ctypes.c_int64 * 3)()
+    chosen = (ctypes.c_int64 * 4)()
     _check(plan, lib().kafmm_autotune(plan, _ptr(s), _ptr(g), dtype, chosen))
-    return {"tc_stages": int(chosen[0]), "tc_ranges": int(chosen[1]), "tc_tiling": int(chosen[2])}
+    return {"tc_stages": int(chosen[0]), "tc_ranges": int(chosen[1]), "tc_tiling": int(chosen[2]),
+            "leaf_stage": int(chosen[3])}
 
 
 def kafmm_status(plan):

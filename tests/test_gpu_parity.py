@@ -474,13 +474,14 @@ def test_autotune_picks_a_valid_configuration():
     plan.set_points(y)
     chosen = K.kafmm_autotune(plan.h, s, g, K.F32)
     assert chosen["tc_stages"] in (2, 4) and chosen["tc_ranges"] in (1, 2, 4, 8)
-    assert chosen["tc_tiling"] in (1, 2)
+    assert chosen["tc_tiling"] in (1, 2) and chosen["leaf_stage"] in (256, 640, 1280)
     tuned = plan.eval(s)
     plan.close()
     ref = K.Plan(K.STOKESLET, p=8, q=64, precision=K.PREC_MIXED, variant=K.ML_L4,
                  tc_stages=chosen["tc_stages"])
     K.kafmm_set_option(ref.h, K.OPT_TC_RANGES, chosen["tc_ranges"])
     K.kafmm_set_option(ref.h, K.OPT_TC_TILING, chosen["tc_tiling"])
+    K.kafmm_set_option(ref.h, K.OPT_LEAF_STAGE, chosen["leaf_stage"])
     ref.set_points(y)
     assert torch.equal(ref.eval(s), tuned)
     ref.close()

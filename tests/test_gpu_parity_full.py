@@ -224,3 +224,17 @@ def test_compressed_coordinates_match_dense_mixed_form(kernel, variant, bc, p, s
     print("compressed", kernel, variant, bc, p, "vs fp64", e_c, "dense", e_d, "ranks", c["rank_up"], c["rank_dn"])
     assert e_c < 1e-5 and e_d < 1e-5
     assert D.rel_l2(out[True], out[False]) < 1e-5
+
+
+@pytest.mark.parametrize("problem,kernel", [("stokeslet_l4", K.STOKESLET), ("laplace", K.LAPLACE)])
+def test_fp64_gpu_kafmm_matches_cpu_kafmm_at_p10(problem, kernel):
+    """The plain FP64 GPU form at the order of the benchmark (p = 10, q = 128) against the
+    oracle's plain CPU KAFMM: relative L2 <= 1e-7 (the bar stated for p = 10)."""
+    n = 8192
+    pts, f = W.stokes_uniform(n, seed=21, dtype=np.float64)
+    s = f if kernel == K.STOKESLET else f[:, :1].copy()
+    ref = KAFMM(problem, 10, 128).evaluate(pts, s)
+    g, _ = _eval(kernel, pts, s, K.PREC_FP64, 10, 128)
+    err = D.rel_l2(g, ref)
+    print("fp64 gpu vs cpu kafmm p = 10", problem, err)
+    assert err < 1e-7

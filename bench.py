@@ -995,7 +995,7 @@ def main():
                              "leafsweep"])
     ap.add_argument("--tc-tiling", type=int, default=0, choices=[0, 1, 2],
                     help="M->L tiling: 0 automatic, 1 whole V lists, 2 per parent neighbour")
-    ap.add_argument("--compress", type=int, default=1, choices=[0, 1, 2],
+    ap.add_argument("--compress", type=int, default=2, choices=[0, 1, 2],
                     help="mixed form: 0 check potentials, 1 compressed coordinates, 2 compressed "
                          "with the rank rounded down to a multiple of 64")
     ap.add_argument("--skip-check", action="store_true")

@@ -96,6 +96,9 @@ struct S2CArgs {
   int mode;                          // 0: S->M (overwrite), 1: S->L over X lists (accumulate)
 };
 
+// Check points per thread of k_s2check: each staged source feeds CPT check points.
+constexpr int S2C_CPT = 4;
+
 template <class T, int PR>
 __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
   using T4 = typename V4<T>::type;
@@ -107,17 +110,24 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
   box_centre<T>(a.t, b, a.geo.L, a.geo.org, cx, cy, cz, r);
   T alpha = a.mode == 0 ? T(ALPHA_UC) : T(ALPHA_DC);
   int nent = a.mode == 0 ? 1 : (int)(a.x_off[b + 1] - a.x_off[b]);
-  for (int i0 = 0; i0 < a.n; i0 += blockDim.x) {
-    int i = i0 + threadIdx.x;
-    T px = 0, py = 0, pz = 0;
-    if (i < a.n) {
-      px = alpha * r * a.unit[3 * i];
-      py = alpha * r * a.unit[3 * i + 1];
-      pz = alpha * r * a.unit[3 * i + 2];
-    }
-    T acc[C * D];
+  // check points i0 + threadIdx.x + 128 u (u < S2C_CPT) of this pass
+  for (int i0 = 0; i0 < a.n; i0 += 128 * S2C_CPT) {
+    T px[S2C_CPT], py[S2C_CPT], pz[S2C_CPT];
+    bool on[S2C_CPT];
+    T acc[S2C_CPT][C * D];
 #pragma unroll
-    for (int k = 0; k < C * D; ++k) acc[k] = 0;
+    for (int u = 0; u < S2C_CPT; ++u) {
+      const int i = i0 + threadIdx.x + 128 * u;
+      on[u] = i < a.n;
+      px[u] = py[u] = pz[u] = 0;
+      if (on[u]) {
+        px[u] = alpha * r * a.unit[3 * i];
+        py[u] = alpha * r * a.unit[3 * i + 1];
+        pz[u] = alpha * r * a.unit[3 * i + 2];
+      }
+#pragma unroll
+      for (int k = 0; k < C * D; ++k) acc[u][k] = 0;
+    }
     for (int e = 0; e < nent; ++e) {
       int src = b, sc = 13;
       if (a.mode == 1) {
@@ -142,67 +152,74 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
           for (int qv = 0; qv < NV; ++qv) sv[j * NV + qv] = a.val[(int64_t)(c0 + j) * NV + qv];
         }
         __syncthreads();
-        if (i < a.n) {
-          for (int j = 0; j < cn; ++j) {
-            T4 y = sp[j], v = sv[j * NV];
-            T r0 = px - y.x, r1 = py - y.y, r2 = pz - y.z;
+        if (!on[0]) continue;
+        for (int j = 0; j < cn; ++j) {
+          const T4 y = sp[j], v = sv[j * NV];
+#pragma unroll
+          for (int u = 0; u < S2C_CPT; ++u) {
+            if (!on[u]) continue;
+            T r0 = px[u] - y.x, r1 = py[u] - y.y, r2 = pz[u] - y.z;
+            T* ac = acc[u];
             if (PR == P_DL) {   // S->M, S->L: the double-layer kernel K, [p, u] (p doubled: 1/(8 pi) below)
               T4 v1 = sv[j * NV + 1], v2 = sv[j * NV + 2];
               T Dm[9] = {v.x, v.y, v.z, v.w, v1.x, v1.y, v1.z, v1.w, v2.x};
               T tmp[4] = {0, 0, 0, 0};
               dl_st<T>(r0, r1, r2, Dm, tmp);
-              acc[0] += T(2) * tmp[0];
-              acc[1] += tmp[1];
-              acc[2] += tmp[2];
-              acc[3] += tmp[3];
+              ac[0] += T(2) * tmp[0];
+              ac[1] += tmp[1];
+              ac[2] += tmp[2];
+              ac[3] += tmp[3];
             } else if (PR == P_PVEL) {   // S->M, S->L: G^P, [p, u] (p doubled: 1/(8 pi) below)
               T tmp[4] = {0, 0, 0, 0};
               pvel_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
-              acc[0] += T(2) * tmp[0];
-              acc[1] += tmp[1];
-              acc[2] += tmp[2];
-              acc[3] += tmp[3];
+              ac[0] += T(2) * tmp[0];
+              ac[1] += tmp[1];
+              ac[2] += tmp[2];
+              ac[3] += tmp[3];
             } else if (PR == P_LAP) {
-              lap_st<T>(r0, r1, r2, v.x, acc);
+              lap_st<T>(r0, r1, r2, v.x, ac);
             } else if (PR == P_LAPQD) {   // S->M, S->L: L for the charge, L^D for the dipole
               T rr = r0 * r0 + r1 * r1 + r2 * r2;
               T ir = inv_r(rr);
-              acc[0] += v.x * ir + (v.y * r0 + v.z * r1 + v.w * r2) * ir * ir * ir;
+              ac[0] += v.x * ir + (v.y * r0 + v.z * r1 + v.w * r2) * ir * ir * ir;
             } else if (PR == P_STK_L4 || PR == P_RPY_L4) {
               T rr = r0 * r0 + r1 * r1 + r2 * r2;
               T ir = inv_r(rr);
-              acc[0] += v.x * ir;
-              acc[1] += v.y * ir;
-              acc[2] += v.z * ir;
+              ac[0] += v.x * ir;
+              ac[1] += v.y * ir;
+              ac[2] += v.z * ir;
               T q4 = y.x * v.x + y.y * v.y + y.z * v.z;  // (y - c) . f
               if (PR == P_RPY_L4) q4 = q4 + v.w * v.w * T(1.0 / 3.0) * (r0 * v.x + r1 * v.y + r2 * v.z) * ir * ir;
-              acc[3] += q4 * ir;
+              ac[3] += q4 * ir;
             } else if (PR == P_STK_G) {
-              stk_st<T>(r0, r1, r2, v.x, v.y, v.z, acc);
+              stk_st<T>(r0, r1, r2, v.x, v.y, v.z, ac);
             } else if (PR == P_REG_G) {   // S->M, S->L: the regularized kernel (Table tab:ktab_reg)
-              reg_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, acc);
+              reg_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, ac);
             } else if (PR == P_RPY_G) {
               T tmp[6] = {0, 0, 0, 0, 0, 0};
               rpy_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
-              acc[0] += tmp[0];
-              acc[1] += tmp[1];
-              acc[2] += tmp[2];
+              ac[0] += tmp[0];
+              ac[1] += tmp[1];
+              ac[2] += tmp[2];
             }
           }
         }
       }
     }
-    if (i < a.n) {
-      T sc = (PR == P_STK_G || PR == P_RPY_G || PR == P_REG_G || PR == P_DL || PR == P_PVEL)
-                 ? T(1.0 / (8.0 * PI))
-                 : T(1.0 / (4.0 * PI));
-      T* out = a.check + (int64_t)b * a.R * C;
+    T sc = (PR == P_STK_G || PR == P_RPY_G || PR == P_REG_G || PR == P_DL || PR == P_PVEL)
+               ? T(1.0 / (8.0 * PI))
+               : T(1.0 / (4.0 * PI));
+    T* out = a.check + (int64_t)b * a.R * C;
+#pragma unroll
+    for (int u = 0; u < S2C_CPT; ++u) {
+      if (!on[u]) continue;
+      const int i = i0 + threadIdx.x + 128 * u;
 #pragma unroll
       for (int d = 0; d < D; ++d)
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           int64_t idx = (int64_t)(i * D + d) * C + c;
-          T v = acc[d * C + c] * sc;
+          T v = acc[u][d * C + c] * sc;
           // StokesPVel check values are stored as [h p, u] (h: box half-width), which makes
           // the translations level-independent (p falls as 1/r^2, u as 1/r)
           if ((PR == P_DL || PR == P_PVEL) && d == 0) v *= r;
@@ -567,7 +584,7 @@ template <class T, int PR>
 struct LeafTT { static constexpr int V = (sizeof(T) == 4 && ProbInfo<PR>::KT <= 6) ? 2 : 1; };
 
 // Leaf kernel, one block per target leaf.  Work split: a pass takes up to LEAF_THREADS x tt
-// targets (tt = 2 when the leaf holds more than 64 and the table allows it); its targets are
+// targets (tt = 2 when the leaf holds more than 16 and the table allows it); its targets are
 // dealt to S slots of tt targets each, and the G = LEAF_THREADS / S threads of a slot (lane-major:
 // consecutive lanes) split the sources of every interaction list among themselves; the G
 // partial sums of a target are combined by warp shuffles when G divides 32, else through
@@ -609,7 +626,7 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
     __syncthreads();
     if (bail) return;
   }
-  const int tt = (TT == 2 && nt > 64) ? 2 : 1;
+  const int tt = (TT == 2 && nt > 16) ? 2 : 1;
   const int per_pass = min(nt, LEAF_THREADS * tt);
   const int S = (per_pass + tt - 1) / tt;            // slots
   const int G = max(1, LEAF_THREADS / S);            // threads per slot

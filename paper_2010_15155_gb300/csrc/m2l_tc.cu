@@ -286,14 +286,25 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   __syncthreads();
-  if (threadIdx.x == 0) {  // active offsets of this tile, then this CTA's share (blockIdx.z)
+  if (warp == 0) {  // active offsets of this tile (ballot compaction), then this CTA's share
     int ns = 0;
-    for (int k = 0; k < nsmax; ++k)
-      if (slot_any[k]) slot_list[ns++] = k;
-    int z = blockIdx.z, nz = a.nsplit;
-    int s0 = (int)((int64_t)ns * z / nz), s1 = (int)((int64_t)ns * (z + 1) / nz);
-    for (int k = s0; k < s1; ++k) slot_list[k - s0] = slot_list[k];
-    nslots = s1 - s0;
+    for (int k0 = 0; k0 < nsmax; k0 += 32) {
+      const int k = k0 + lane;
+      const bool on = k < nsmax && slot_any[k];
+      const unsigned m = __ballot_sync(0xffffffffu, on);
+      if (on) slot_list[ns + __popc(m & ((1u << lane) - 1u))] = k;
+      ns += __popc(m);
+    }
+    __syncwarp();
+    const int z = blockIdx.z, nz = a.nsplit;
+    const int s0 = (int)((int64_t)ns * z / nz), s1 = (int)((int64_t)ns * (z + 1) / nz);
+    int tmp[7];   // the share moves to the front of the list (at most 216 entries, 7 per lane)
+    int cnt = 0;
+    for (int k = s0 + lane; k < s1; k += 32) tmp[cnt++] = slot_list[k];
+    __syncwarp();
+    cnt = 0;
+    for (int k = s0 + lane; k < s1; k += 32) slot_list[k - s0] = tmp[cnt++];
+    if (lane == 0) nslots = s1 - s0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();

@@ -109,7 +109,7 @@ struct Plan {
   // pseudo-inverse cutoff), every translation P^T T P between those coordinates (rp x rp,
   // rp = max(r_up, r_dn) rounded up to 64); leaves compress their S->M check potentials, and
   // equivalent densities come from V S^+ applied to the coordinates.
-  int compress_opt = 1;             // option: use compressed coordinates when the table allows
+  int compress_opt = 2;             // option: use compressed coordinates when the table allows
   bool cmp = false;                 // compressed operators built for this plan
   int rp = 0, r_up = 0, r_dn = 0;
   int tc_split_cm = SPLIT_TF32;     // split format of the compressed M->L

@@ -95,34 +95,55 @@ __global__ void k_scan_apply(const T* in, int64_t n, const int* d_len, const T* 
   }
 }
 
-// One block scans up to SCAN_SMALL elements (16 consecutive per thread): the whole scan in one
-// launch.  len = *d_len if d_len else n.
+// One block scans up to SCAN_SMALL elements in one launch: warp w owns the contiguous chunk
+// [512 w, 512 (w + 1)), read and written in rows of 32 consecutive elements (coalesced); each row
+// is scanned across the lanes with a running carry, then the warps' totals are scanned.
+// len = *d_len if d_len else n.
 constexpr int SCAN_SMALL_ITEMS = 16;
 constexpr int64_t SCAN_SMALL = (int64_t)SCAN_THREADS * SCAN_SMALL_ITEMS;
 template <class T>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_small(const T* in, int64_t n, const int* d_len,
                                                              T* out, T* d_total) {
-  __shared__ T sm[32];
+  __shared__ T wsum[32];
   int64_t len = d_len ? (int64_t)*d_len : n;
   if (len > n) len = n;
-  T v[SCAN_SMALL_ITEMS];
-  T s = 0;
-  const int64_t base = (int64_t)threadIdx.x * SCAN_SMALL_ITEMS;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t chunk = (int64_t)w * 32 * SCAN_SMALL_ITEMS;
+  T ex[SCAN_SMALL_ITEMS];
+  T carry = 0;
 #pragma unroll
   for (int k = 0; k < SCAN_SMALL_ITEMS; ++k) {
-    int64_t i = base + k;
-    v[k] = i < len ? in[i] : T(0);
-    s += v[k];
+    const int64_t i = chunk + 32 * k + lane;
+    const T v = i < len ? in[i] : T(0);
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    ex[k] = carry + x - v;
+    carry += __shfl_sync(0xffffffffu, x, 31);
   }
-  T total;
-  T e = block_excl_scan<T>(s, sm, total);
+  if (lane == 0) wsum[w] = carry;
+  __syncthreads();
+  if (w == 0) {
+    const T t = lane < (int)(blockDim.x >> 5) ? wsum[lane] : T(0);
+    T x = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    wsum[lane] = x - t;   // exclusive offsets of the warps
+    if (lane == 31 && d_total) *d_total = x;
+  }
+  __syncthreads();
+  const T off = wsum[w];
 #pragma unroll
   for (int k = 0; k < SCAN_SMALL_ITEMS; ++k) {
-    int64_t i = base + k;
-    if (i < len) out[i] = e;
-    e += v[k];
+    const int64_t i = chunk + 32 * k + lane;
+    if (i < len) out[i] = off + ex[k];
   }
-  if (threadIdx.x == 0 && d_total) *d_total = total;
 }
 
 // Exclusive scan of in[0..len) into out (in-place allowed); *d_total receives the sum.

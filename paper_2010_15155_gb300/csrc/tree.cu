@@ -195,32 +195,44 @@ __global__ void k_root(BuildArgs a) {
     for (int l = 0; l < MAX_LEVELS; ++l) a.cnt[l] = l == 0 ? a.nprob : 0;
 }
 
+// One warp per box: a box with more than q points splits; lanes 0-7 find the start of child o in
+// the sorted source keys and lanes 8-15 in the target keys (binary searches in parallel, so
+// the root's eight searches over all points are one chain of dependent loads, not eight).
 __global__ void k_split(BuildArgs a, int lv, unsigned* status) {
-  int n = a.cnt[lv];
-  int64_t o0 = a.cap_off[lv];
-  int sh = 3 * (MAX_LEVEL - lv - 1);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int64_t g = o0 + i;
-    int sb = a.sb[g], se = a.se[g], tb = a.tb[g], te = a.te[g];
-    int count = (se - sb) + (a.same ? 0 : (te - tb));
+  const int n = a.cnt[lv];
+  const int64_t o0 = a.cap_off[lv];
+  const int sh = 3 * (MAX_LEVEL - lv - 1);
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
+    const int64_t g = o0 + i;
+    const int sb = a.sb[g], se = a.se[g], tb = a.tb[g], te = a.te[g];
+    const int count = (se - sb) + (a.same ? 0 : (te - tb));
     int nch = 0;
-    if (count > a.q && lv < MAX_LEVEL) {
-      uint64_t k = a.key[g];
+    if (count > a.q && lv < MAX_LEVEL) {   // warp-uniform
+      const uint64_t k = a.key[g];
+      int v = 0;
+      if (lane < 8)
+        v = lower_bound_prefix(a.skey, sb, se, k * 8 + lane, sh);
+      else if (lane < 16 && !a.same)
+        v = lower_bound_prefix(a.tkey, tb, te, k * 8 + (lane - 8), sh);
       int cb[9], ctb[9];
+#pragma unroll
       for (int o = 0; o < 8; ++o) {
-        cb[o] = lower_bound_prefix(a.skey, sb, se, k * 8 + o, sh);
-        ctb[o] = a.same ? cb[o] : lower_bound_prefix(a.tkey, tb, te, k * 8 + o, sh);
+        cb[o] = __shfl_sync(0xffffffffu, v, o);
+        ctb[o] = __shfl_sync(0xffffffffu, v, 8 + o);
+        if (a.same) ctb[o] = cb[o];
       }
       cb[8] = se;
       ctb[8] = a.same ? se : te;
-      for (int o = 0; o < 9; ++o) {
-        a.cb[g * 9 + o] = cb[o];
-        a.ctb[g * 9 + o] = ctb[o];
+      if (lane < 9) {
+        a.cb[g * 9 + lane] = cb[lane];
+        a.ctb[g * 9 + lane] = ctb[lane];
       }
+#pragma unroll
       for (int o = 0; o < 8; ++o)
         nch += ((cb[o + 1] - cb[o]) + (a.same ? 0 : (ctb[o + 1] - ctb[o]))) > 0;
     }
-    a.nch[g] = nch;
+    if (lane == 0) a.nch[g] = nch;
   }
 }
 
@@ -400,60 +412,79 @@ __global__ void k_vtab(TreeView t, int32_t* __restrict__ vtab) {
   }
 }
 
+// Warp-level exclusive scan of per-lane counts; total in *tot.
+__device__ __forceinline__ int64_t warp_excl(int64_t v, int lane, int64_t* tot) {
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  *tot = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
+}
+
+// U, W and X lists, one warp per box: lane d < 27 takes neighbour direction d of the box (U and
+// W, leaves only), lane d < 27 also direction d of the parent (X, d != 13).  A coarse U or X
+// entry reached from several directions is kept by its lowest lane (__match_any_sync); each
+// lane's entries go to its place in the box's list by a warp scan of the counts (direction
+// order, then descent order within a direction).
 template <bool FILL>
 __global__ void k_lists(TreeView t, ListOut o) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nbox; b += gridDim.x * blockDim.x) {
-    int lv = t.level[b];
-    int pb = t.prob[b];
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < t.nbox; b += gridDim.x * wpb) {
+    const int lv = t.level[b];
+    const int pb = t.prob[b];
     int ax, ay, az;
     anchor_of(t.key[b], ax, ay, az);
-    // ---- U and W for leaves
+    const bool is_leaf = t.leaf[b] != 0;
+    const int ntb = t.te[b] - t.tb[b];
     int64_t nu = 0, nw = 0, nx = 0;
-    int64_t pu = FILL ? o.u_cnt[b] : 0, pw = FILL ? o.w_cnt[b] : 0, px = FILL ? o.x_cnt[b] : 0;
     unsigned long long pairs = 0;
-    if (t.leaf[b]) {
-      int coarse[27];
-      int ncoarse = 0;
-      int ntb = t.te[b] - t.tb[b];
-      for (int d = 0; d < 27; ++d) {
-        int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-        int cx, cy, cz, sx, sy, sz;
-        if (!neighbour(t.periodic, lv, ax, dx, cx, sx) || !neighbour(t.periodic, lv, ay, dy, cy, sy) ||
-            !neighbour(t.periodic, lv, az, dz, cz, sz))
-          continue;
-        int sc = shift_code(sx, sy, sz);
-        int nb = deepest_box(t, lv, pb, cx, cy, cz);
-        int nl = t.level[nb];
-        if (nl < lv) {  // a coarser box holds the cell: a leaf is a U neighbour
-          if (!t.leaf[nb]) continue;
-          int32_t e = pack_entry(nb, sc);
-          bool dup = false;
-          for (int j = 0; j < ncoarse; ++j) dup = dup || coarse[j] == e;
-          if (dup) continue;
-          coarse[ncoarse++] = e;
-          if (FILL) o.u_ent[pu + nu] = e;
-          ++nu;
-          pairs += (unsigned long long)ntb * (t.se[nb] - t.sb[nb]);
-          continue;
-        }
-        if (t.leaf[nb]) {
-          if (FILL) o.u_ent[pu + nu] = pack_entry(nb, sc);
-          ++nu;
-          pairs += (unsigned long long)ntb * (t.se[nb] - t.sb[nb]);
-          continue;
-        }
+    // ---- U and W (leaves): direction d = lane
+    int sx = 0, sy = 0, sz = 0, sc = 13, nb = -1, kind = 0;   // kind 1: coarse leaf, 2: leaf, 3: descend
+    if (is_leaf && lane < 27) {
+      const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+      int cx, cy, cz;
+      if (neighbour(t.periodic, lv, ax, dx, cx, sx) && neighbour(t.periodic, lv, ay, dy, cy, sy) &&
+          neighbour(t.periodic, lv, az, dz, cz, sz)) {
+        sc = shift_code(sx, sy, sz);
+        nb = deepest_box(t, lv, pb, cx, cy, cz);
+        const int nl = t.level[nb];
+        if (nl < lv)
+          kind = t.leaf[nb] ? 1 : 0;   // a coarser box holds the cell: only a leaf is a U neighbour
+        else
+          kind = t.leaf[nb] ? 2 : 3;
+      }
+    }
+    // coarse entries reached from several directions: the lowest lane keeps it
+    const int32_t ce = kind == 1 ? pack_entry(nb, sc) : LIST_EMPTY;
+    const unsigned peers = __match_any_sync(0xffffffffu, ce);
+    if (kind == 1 && (__ffs(peers) - 1) != lane) kind = 0;
+    // two rounds: count, then (FILL) write at the scanned offsets
+    int64_t u_base = 0, w_base = 0;
+    for (int round = 0; round < (FILL ? 2 : 1); ++round) {
+      nu = nw = 0;
+      pairs = 0;
+      const bool write = FILL && round == 1;
+      if (kind == 1 || kind == 2) {
+        if (write) o.u_ent[u_base + nu] = pack_entry(nb, sc);
+        ++nu;
+        pairs += (unsigned long long)ntb * (t.se[nb] - t.sb[nb]);
+      } else if (kind == 3) {
         // non-leaf colleague: descend; adjacent leaves -> U, non-adjacent boxes -> W
         int stack[8 * MAX_LEVELS];
         int sp = 0;
         for (int c = 0; c < 8; ++c)
           if (t.child[nb * 8 + c] >= 0) stack[sp++] = t.child[nb * 8 + c];
         while (sp > 0) {
-          int dd = stack[--sp];
-          int dl = t.level[dd], qx, qy, qz;
+          const int dd = stack[--sp];
+          const int dl = t.level[dd];
+          int qx, qy, qz;
           anchor_of(t.key[dd], qx, qy, qz);
           if (adjacent(dl, qx, qy, qz, sx, sy, sz, lv, ax, ay, az)) {
             if (t.leaf[dd]) {
-              if (FILL) o.u_ent[pu + nu] = pack_entry(dd, sc);
+              if (write) o.u_ent[u_base + nu] = pack_entry(dd, sc);
               ++nu;
               pairs += (unsigned long long)ntb * (t.se[dd] - t.sb[dd]);
             } else {
@@ -461,50 +492,58 @@ __global__ void k_lists(TreeView t, ListOut o) {
                 if (t.child[dd * 8 + c] >= 0 && sp < 8 * MAX_LEVELS) stack[sp++] = t.child[dd * 8 + c];
             }
           } else {
-            if (FILL) {
-              o.w_ent[pw + nw] = pack_entry(dd, sc);
+            if (write) {
+              o.w_ent[w_base + nw] = pack_entry(dd, sc);
               o.w_flag[dd] = 1;
             }
             ++nw;
           }
         }
       }
-    }
-    // ---- X: coarser leaves adjacent to the parent but not to b
-    if (lv >= 1) {
-      int p = t.parent[b];
-      int px_, py_, pz_;
-      anchor_of(t.key[p], px_, py_, pz_);
-      int found[27];
-      int nf = 0;
-      for (int d = 0; d < 27; ++d) {
-        if (d == 13) continue;
-        int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-        int cx, cy, cz, sx, sy, sz;
-        if (!neighbour(t.periodic, lv - 1, px_, dx, cx, sx) ||
-            !neighbour(t.periodic, lv - 1, py_, dy, cy, sy) ||
-            !neighbour(t.periodic, lv - 1, pz_, dz, cz, sz))
-          continue;
-        int nb = deepest_box(t, lv - 1, pb, cx, cy, cz);
-        if (!t.leaf[nb]) continue;
-        int nl = t.level[nb], qx, qy, qz;
-        anchor_of(t.key[nb], qx, qy, qz);
-        if (adjacent(nl, qx, qy, qz, sx, sy, sz, lv, ax, ay, az)) continue;
-        int32_t e = pack_entry(nb, shift_code(sx, sy, sz));
-        bool dup = false;
-        for (int j = 0; j < nf; ++j) dup = dup || found[j] == e;
-        if (dup) continue;
-        found[nf++] = e;
-        if (FILL) o.x_ent[px + nx] = e;
-        ++nx;
+      if (FILL && round == 0) {   // this lane's first entry in the box's lists
+        int64_t tu, tw;
+        u_base = o.u_cnt[b] + warp_excl(nu, lane, &tu);
+        w_base = o.w_cnt[b] + warp_excl(nw, lane, &tw);
       }
     }
+    // ---- X: coarser leaves adjacent to the parent but not to b; direction d = lane != 13
+    int32_t xe = LIST_EMPTY;
+    if (lv >= 1 && lane < 27 && lane != 13) {
+      const int p = t.parent[b];
+      int px_, py_, pz_;
+      anchor_of(t.key[p], px_, py_, pz_);
+      const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+      int cx, cy, cz, xsx, xsy, xsz;
+      if (neighbour(t.periodic, lv - 1, px_, dx, cx, xsx) && neighbour(t.periodic, lv - 1, py_, dy, cy, xsy) &&
+          neighbour(t.periodic, lv - 1, pz_, dz, cz, xsz)) {
+        const int xb = deepest_box(t, lv - 1, pb, cx, cy, cz);
+        if (t.leaf[xb]) {
+          const int nl = t.level[xb];
+          int qx, qy, qz;
+          anchor_of(t.key[xb], qx, qy, qz);
+          if (!adjacent(nl, qx, qy, qz, xsx, xsy, xsz, lv, ax, ay, az)) xe = pack_entry(xb, shift_code(xsx, xsy, xsz));
+        }
+      }
+    }
+    const unsigned xpeers = __match_any_sync(0xffffffffu, xe);
+    nx = (xe != LIST_EMPTY && (__ffs(xpeers) - 1) == lane) ? 1 : 0;
+    int64_t tx;
+    const int64_t xoff = warp_excl(nx, lane, &tx);
+    if (FILL && nx) o.x_ent[o.x_cnt[b] + xoff] = xe;
+    // ---- totals
+    int64_t tu, tw;
+    warp_excl(nu, lane, &tu);
+    warp_excl(nw, lane, &tw);
     if (!FILL) {
-      o.u_cnt[b] = nu;
-      o.w_cnt[b] = nw;
-      o.x_cnt[b] = nx;
-    } else if (pairs) {
-      atomicAdd(o.near_pairs, pairs);
+      if (lane == 0) {
+        o.u_cnt[b] = tu;
+        o.w_cnt[b] = tw;
+        o.x_cnt[b] = tx;
+      }
+    } else {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, off);
+      if (lane == 0 && pairs) atomicAdd(o.near_pairs, pairs);
     }
   }
 }
@@ -811,7 +850,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
     int l1 = std::min(MAX_LEVEL, l0 + group);
     for (int l = l0; l < l1; ++l) {
       int g = grid_for(a.cap[l], 256);
-      KL k_split<<<g, 256, 0, st>>>(a, l, status);
+      KL k_split<<<grid_for((int64_t)a.cap[l] * 32, 256), 256, 0, st>>>(a, l, status);
       int* scratch = a.choff + a.cap_off[MAX_LEVELS] + 16;
       scan_excl<int>(a.nch + a.cap_off[l], a.choff + a.cap_off[l], a.cap[l], a.cnt + l, scratch,
                      d_total, st);
@@ -887,11 +926,10 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   lo.u_cnt = T.u_off.as<int64_t>();
   lo.w_cnt = T.w_off.as<int64_t>();
   lo.x_cnt = T.x_off.as<int64_t>();
-  // one warp per block: the per-box work is a long dependent chain of lookups, so spread the
-  // boxes over as many SMs as possible
-  int g = grid_for(nb, 32, 152 * 64);
+  // one warp per box (lanes take the neighbour directions), 8 boxes per block
+  int g = grid_for((int64_t)nb * 32, 256, 152 * 16);
   KL k_vtab<<<grid_for((int64_t)nb * 216, 256, 152 * 16), 256, 0, st>>>(tv, T.vtab.as<int32_t>());
-  KL k_lists<false><<<g, 32, 0, st>>>(tv, lo);
+  KL k_lists<false><<<g, 256, 0, st>>>(tv, lo);
   int64_t tot[3];
   int64_t* sc[3] = {lo.u_cnt, lo.w_cnt, lo.x_cnt};
   for (int k = 0; k < 3; ++k) {
@@ -914,7 +952,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   lo.w_flag = T.w_flag.as<int8_t>();
   lo.near_pairs = (unsigned long long*)(T.status.as<unsigned>() + 8);
   CK(cudaMemsetAsync(lo.near_pairs, 0, 8, st));
-  KL k_lists<true><<<g, 32, 0, st>>>(tv, lo);
+  KL k_lists<true><<<g, 256, 0, st>>>(tv, lo);
   CK(cudaGetLastError());
   cudaEventRecord(P.ev[2], st);
   // V entries, the largest leaf, and the pairs of the grouped M->L (count per box, then their

@@ -241,7 +241,7 @@ class Plan:
 
     def __init__(self, kernel, p, q, bc=BC_OPEN, precision=PREC_MIXED, variant=ML_L4,
                  near_only=False, kahan=False, stream=None, origin=(0.0, 0.0, 0.0), L=1.0,
-                 tc_split=TC_AUTO, sync=True, tc_stages=None, compress=True):
+                 tc_split=TC_AUTO, sync=True, tc_stages=None, compress=2):
         self.kernel = kernel
         self.ks, self.kt = KDIM[kernel]
         self.h = kafmm_plan(kernel, bc, p, q)

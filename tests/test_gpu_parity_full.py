@@ -212,7 +212,7 @@ def test_compressed_coordinates_match_dense_mixed_form(kernel, variant, bc, p, s
     bcc = K.BC_PXYZ if bc == "pxyz" else K.BC_OPEN
     g64, _ = _eval(code, pts, s, K.PREC_FP64, p, 64, variant=variant, bc=bcc)
     out = {}
-    for cmp in (False, True):
+    for cmp in (0, 1, 2):   # check potentials; compressed; compressed with the rank rounded down
         out[cmp], c = _eval(code, pts.astype(np.float32), s.astype(np.float32), K.PREC_MIXED, p, 64,
                             variant=variant, bc=bcc, tc_split=split, compress=cmp)
         assert c["tensor_core_m2l"] == 1
@@ -220,10 +220,10 @@ def test_compressed_coordinates_match_dense_mixed_form(kernel, variant, bc, p, s
             assert 0 < c["rank_up"] <= c["compressed_rows"] and 0 < c["rank_dn"] <= c["compressed_rows"]
         else:
             assert c["compressed_rows"] == 0
-    e_c, e_d = D.rel_l2(out[True], g64), D.rel_l2(out[False], g64)
-    print("compressed", kernel, variant, bc, p, "vs fp64", e_c, "dense", e_d, "ranks", c["rank_up"], c["rank_dn"])
-    assert e_c < 1e-5 and e_d < 1e-5
-    assert D.rel_l2(out[True], out[False]) < 1e-5
+    errs = {cmp: D.rel_l2(out[cmp], g64) for cmp in out}
+    print("compressed", kernel, variant, bc, p, "vs fp64", errs, "ranks", c["rank_up"], c["rank_dn"])
+    assert all(e < 1e-5 for e in errs.values())
+    assert D.rel_l2(out[1], out[0]) < 1e-5 and D.rel_l2(out[2], out[0]) < 1e-5
 
 
 @pytest.mark.parametrize("problem,kernel", [("stokeslet_l4", K.STOKESLET), ("laplace", K.LAPLACE)])

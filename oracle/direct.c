@@ -259,6 +259,147 @@ void orc_stokes_dl(const double* x, int64_t nt, const double* y, int64_t ns,
   }
 }
 
+/* ---------------------------------------------------------------------------------------
+ * Derivatives of the StokesPVel and double-layer fields at the targets (the T column of
+ * Tables tab:ktab_stkslpvelgrad and tab:ktab_stkdlpvelgrad; target values of PVelGrad,
+ * PVelLaplacian and Traction in Table tab:implement).  Layouts of the target values:
+ *   grad:      [p, u_1..3, d p / d x_1..3, d u_i / d x_j at 7 + 3 i + j]          (16)
+ *   laplacian: [p, u_1..3, lap u_1..3]                                             (7)
+ *   traction:  sigma_ij = -p delta_ij + d u_i / d x_j + d u_j / d x_i at 3 i + j   (9)
+ * (Eq. stressdef with mu = 1). */
+
+/* One StokesPVel pair (Eqs. stkslp, stkslvel differentiated in x), r = x - y, v = [f, q]:
+ *   4 pi d_j p   = f_j / r^3 - 3 (r.f) r_j / r^5,
+ *   8 pi d_j u_i = [delta_ij (r.f) + r_i f_j - f_i r_j - q delta_ij] / r^3
+ *                  + 3 r_i r_j (q - r.f) / r^5. */
+static void pvel_pair_grad(const double r[3], const double* v, double* o) {
+  double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  double rn = sqrt(rr), r3 = rr * rn, r5 = r3 * rr;
+  double rf = r[0] * v[0] + r[1] * v[1] + r[2] * v[2], q = v[3];
+  o[0] = rf / (4.0 * PI * r3);
+  for (int i = 0; i < 3; ++i) o[1 + i] = (v[i] / rn + r[i] * rf / r3 - r[i] * q / r3) / (8.0 * PI);
+  for (int j = 0; j < 3; ++j) o[4 + j] = (v[j] / r3 - 3.0 * rf * r[j] / r5) / (4.0 * PI);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double dij = i == j ? 1.0 : 0.0;
+      o[7 + 3 * i + j] = ((dij * rf + r[i] * v[j] - v[i] * r[j] - q * dij) / r3 +
+                          3.0 * r[i] * r[j] * (q - rf) / r5) / (8.0 * PI);
+    }
+}
+
+/* One double-layer pair (Eqs. stkdlp, stkdlvel differentiated in x), D_jk at 3 j + k, with
+ * rDr = r_j D_jk r_k, a_j = d(rDr)/d r_j = D_jk r_k + r_k D_kj, t = tr D:
+ *   4 pi d_j p   = -3 a_j / r^5 + 15 rDr r_j / r^7 - 3 t r_j / r^5,
+ *   8 pi d_j u_i = -3 [delta_ij rDr / r^5 + r_i a_j / r^5 - 5 r_i r_j rDr / r^7]. */
+static void dl_pair_grad(const double r[3], const double* D, double* o) {
+  double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  double rn = sqrt(rr), r3 = rr * rn, r5 = r3 * rr, r7 = r5 * rr;
+  double rDr = 0.0, t = D[0] + D[4] + D[8], a[3];
+  for (int j = 0; j < 3; ++j) {
+    a[j] = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      rDr += r[j] * D[3 * j + k] * r[k];
+      a[j] += D[3 * j + k] * r[k] + r[k] * D[3 * k + j];
+    }
+  }
+  o[0] = (-3.0 * rDr / r5 + t / r3) / (4.0 * PI);
+  for (int i = 0; i < 3; ++i) o[1 + i] = -3.0 / (8.0 * PI) * r[i] * rDr / r5;
+  for (int j = 0; j < 3; ++j) o[4 + j] = (-3.0 * a[j] / r5 + 15.0 * rDr * r[j] / r7 - 3.0 * t * r[j] / r5) / (4.0 * PI);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      o[7 + 3 * i + j] = -3.0 / (8.0 * PI) *
+                         ((i == j ? rDr / r5 : 0.0) + r[i] * a[j] / r5 - 5.0 * r[i] * r[j] * rDr / r7);
+}
+
+/* Laplacian of the velocity, worked out from the velocities themselves (not from the pressure):
+ * StokesPVel: the source term -q r / r^3 is a gradient of 1/r (harmonic away from the source),
+ * and lap (f / r + r (r.f) / r^3) = 2 f / r^3 - 6 r (r.f) / r^5, so
+ *   8 pi lap u_i = 2 f_i / r^3 - 6 r_i (r.f) / r^5;
+ * double layer: lap (r_i rDr / r^5) = 2 a_i / r^5 + 2 t r_i / r^5 - 10 r_i rDr / r^7, so
+ *   8 pi lap u_i = -3 [2 a_i / r^5 + 2 t r_i / r^5 - 10 r_i rDr / r^7]. */
+static void pvel_pair_lapl(const double r[3], const double* v, double* o) {
+  double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  double rn = sqrt(rr), r3 = rr * rn, r5 = r3 * rr;
+  double rf = r[0] * v[0] + r[1] * v[1] + r[2] * v[2], q = v[3];
+  o[0] = rf / (4.0 * PI * r3);
+  for (int i = 0; i < 3; ++i) {
+    o[1 + i] = (v[i] / rn + r[i] * rf / r3 - r[i] * q / r3) / (8.0 * PI);
+    o[4 + i] = (2.0 * v[i] / r3 - 6.0 * r[i] * rf / r5) / (8.0 * PI);
+  }
+}
+
+static void dl_pair_lapl(const double r[3], const double* D, double* o) {
+  double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  double rn = sqrt(rr), r3 = rr * rn, r5 = r3 * rr, r7 = r5 * rr;
+  double rDr = 0.0, t = D[0] + D[4] + D[8], a[3];
+  for (int j = 0; j < 3; ++j) {
+    a[j] = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      rDr += r[j] * D[3 * j + k] * r[k];
+      a[j] += D[3 * j + k] * r[k] + r[k] * D[3 * k + j];
+    }
+  }
+  o[0] = (-3.0 * rDr / r5 + t / r3) / (4.0 * PI);
+  for (int i = 0; i < 3; ++i) {
+    o[1 + i] = -3.0 / (8.0 * PI) * r[i] * rDr / r5;
+    o[4 + i] = -3.0 / (8.0 * PI) * (2.0 * a[i] / r5 + 2.0 * t * r[i] / r5 - 10.0 * r[i] * rDr / r7);
+  }
+}
+
+/* Shared loop of the derivative kernels: mode 0 grad (16), 1 laplacian (7), 2 traction (9);
+ * dl selects the double-layer sources (9 per source) over [f, q] (4). */
+static void deriv_sum(int dl, int mode, const double* x, int64_t nt, const double* y, int64_t ns,
+                      const double* s, double* g) {
+  const int ks = dl ? 9 : 4, kt = mode == 0 ? 16 : (mode == 1 ? 7 : 9);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double acc[16] = {0};
+    for (int64_t b = 0; b < ns; ++b) {
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1], x[3 * a + 2] - y[3 * b + 2]};
+      if (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] == 0.0) continue;
+      double o[16];
+      const double* v = s + ks * b;
+      if (mode == 1) {
+        if (dl) dl_pair_lapl(r, v, o);
+        else pvel_pair_lapl(r, v, o);
+        for (int k = 0; k < 7; ++k) acc[k] += o[k];
+      } else {
+        if (dl) dl_pair_grad(r, v, o);
+        else pvel_pair_grad(r, v, o);
+        if (mode == 0) {
+          for (int k = 0; k < 16; ++k) acc[k] += o[k];
+        } else {
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+              acc[3 * i + j] += (i == j ? -o[0] : 0.0) + o[7 + 3 * i + j] + o[7 + 3 * j + i];
+        }
+      }
+    }
+    for (int k = 0; k < kt; ++k) g[kt * a + k] += acc[k];
+  }
+}
+
+void orc_stokes_pvel_grad(const double* x, int64_t nt, const double* y, int64_t ns, const double* s, double* g) {
+  deriv_sum(0, 0, x, nt, y, ns, s, g);
+}
+void orc_stokes_pvel_lapl(const double* x, int64_t nt, const double* y, int64_t ns, const double* s, double* g) {
+  deriv_sum(0, 1, x, nt, y, ns, s, g);
+}
+void orc_stokes_pvel_traction(const double* x, int64_t nt, const double* y, int64_t ns, const double* s,
+                              double* g) {
+  deriv_sum(0, 2, x, nt, y, ns, s, g);
+}
+void orc_stokes_dl_grad(const double* x, int64_t nt, const double* y, int64_t ns, const double* s, double* g) {
+  deriv_sum(1, 0, x, nt, y, ns, s, g);
+}
+void orc_stokes_dl_lapl(const double* x, int64_t nt, const double* y, int64_t ns, const double* s, double* g) {
+  deriv_sum(1, 1, x, nt, y, ns, s, g);
+}
+void orc_stokes_dl_traction(const double* x, int64_t nt, const double* y, int64_t ns, const double* s,
+                            double* g) {
+  deriv_sum(1, 2, x, nt, y, ns, s, g);
+}
+
 /* Pair mobility of two spheres (radii ai at the target, aj at the source), r = x - y.
  * Far form (r > ai + aj): the assembled RPY tensor of Eqs. RPYkernel/RPYtrgvel,
  *   M = G + (ai^2 + aj^2)/6 lap G.

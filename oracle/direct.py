@@ -14,6 +14,13 @@ Kernels (dimensions k_s x k_t, Table tab:implement):
   stokes_pvel        [f, q] -> [p, u]             4 x 4   (StokesPVel, Eqs. stkslp, stkslvel)
   rpy                [f, b] -> [u, lap u]         4 x 6   (Eqs. RPYflow, RPYkernel)
   stokes_dl          D -> [p, u]                  9 x 4   (Eqs. stkdlp, stkdlvel)
+  stokes_pvel_grad   [f, q] -> [p, u, grad p, grad u]  4 x 16  (Table tab:ktab_stkslpvelgrad)
+  stokes_pvel_lapl   [f, q] -> [p, u, lap u]      4 x 7   (Table tab:ktab_stkslpvelgrad)
+  stokes_pvel_traction [f, q] -> sigma            4 x 9   (Eq. stressdef, mu = 1)
+  stokes_dl_grad     D -> [p, u, grad p, grad u]  9 x 16  (Table tab:ktab_stkdlpvelgrad)
+  stokes_dl_lapl     D -> [p, u, lap u]           9 x 7   (Table tab:ktab_stkdlpvelgrad)
+  stokes_dl_traction D -> sigma                   9 x 9   (Eq. stressdef, mu = 1)
+grad u is d u_i / d x_j at 3 i + j; sigma_ij = -p delta_ij + d_j u_i + d_i u_j at 3 i + j.
 """
 from __future__ import annotations
 
@@ -35,6 +42,12 @@ KDIM = {  # kernel -> (k_s, k_t)
     "stokes_pvel": (4, 4),
     "rpy": (4, 6),
     "stokes_dl": (9, 4),
+    "stokes_pvel_grad": (4, 16),
+    "stokes_pvel_lapl": (4, 7),
+    "stokes_pvel_traction": (4, 9),
+    "stokes_dl_grad": (9, 16),
+    "stokes_dl_lapl": (9, 7),
+    "stokes_dl_traction": (9, 9),
 }
 
 

@@ -65,7 +65,20 @@ PROBLEMS = {
     "stokes_dl_pv": (9, 4, "stokes_pvel", 1),
     # StokesPVel [f, q] -> [p, u] (Sec. II.C): G^P for all interactions
     "stokes_pvel": (4, 4, "stokes_pvel", 1),
+    # the same ML tree with derivative target values (the T column of Tables
+    # tab:ktab_stkslpvelgrad and tab:ktab_stkdlpvelgrad): G^P + grad G^P (16), G^P + lap G^P
+    # (7), and the traction (9, Eq. stressdef) from [f, q] or from D sources
+    "stokes_pvel_grad": (4, 16, "stokes_pvel", 1),
+    "stokes_pvel_lapl": (4, 7, "stokes_pvel", 1),
+    "stokes_pvel_traction": (4, 9, "stokes_pvel", 1),
+    "stokes_dl_grad": (9, 16, "stokes_pvel", 1),
+    "stokes_dl_lapl": (9, 7, "stokes_pvel", 1),
+    "stokes_dl_traction": (9, 9, "stokes_pvel", 1),
 }
+
+# target value kind of the derivative problems (suffix of the direct-sum kernel names)
+_DERIV = {"stokes_pvel_grad": "grad", "stokes_pvel_lapl": "lapl", "stokes_pvel_traction": "traction",
+          "stokes_dl_grad": "grad", "stokes_dl_lapl": "lapl", "stokes_dl_traction": "traction"}
 
 
 def surface(m: int) -> np.ndarray:
@@ -177,8 +190,8 @@ class KAFMM:
             kern = {"stokeslet_g": "stokeslet", "rpy_g": "rpy", "stokeslet_reg_g": "stokeslet_reg"}[pr]
             g = D.direct(kern, chk, y, s)
             return g[:, :3].reshape(-1, 1)
-        if pr in ("stokes_dl_pv", "stokes_pvel"):
-            kern = "stokes_dl" if pr == "stokes_dl_pv" else "stokes_pvel"
+        if pr in ("stokes_dl_pv", "stokes_pvel") or pr in _DERIV:
+            kern = "stokes_dl" if pr == "stokes_dl_pv" or pr.startswith("stokes_dl_") else "stokes_pvel"
             return D.direct(kern, chk, y, s).reshape(-1, 1)
         f = s[:, :3]
         out = np.zeros((len(chk), 4))
@@ -199,6 +212,8 @@ class KAFMM:
             return D.direct("laplace_pgradgrad", x, eq, dens[:, 0])
         if pr in ("stokes_dl_pv", "stokes_pvel"):
             return D.direct("stokes_pvel", x, eq, dens.reshape(-1, 4))
+        if pr in _DERIV:
+            return D.direct("stokes_pvel_" + _DERIV[pr], x, eq, dens.reshape(-1, 4))
         if pr in ("stokeslet_g", "stokeslet_reg_g"):
             return D.direct("stokeslet", x, eq, dens.reshape(-1, 3))
         if pr == "rpy_g":
@@ -219,6 +234,8 @@ class KAFMM:
         return np.concatenate([u, lap], axis=1)
 
     def _src_to_targets(self, x, y, s) -> np.ndarray:
+        if self.problem in _DERIV:
+            return D.direct(self.problem, x, y, s)
         kern = {"laplace": "laplace", "stokeslet_g": "stokeslet", "stokeslet_l4": "stokeslet",
                 "rpy_g": "rpy", "rpy_l4": "rpy", "stokeslet_reg_g": "stokeslet_reg",
                 "laplace_qd": "laplace_qd", "stokes_dl_pv": "stokes_dl",

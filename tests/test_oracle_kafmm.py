@@ -96,7 +96,10 @@ def test_l4_aggregation_reproduces_stokeslet_exactly():
 WIDTH_PROBLEMS = ("rpy_g", "rpy_l4", "stokeslet_reg_g")
 KERNEL_OF = {"laplace": "laplace", "stokeslet_g": "stokeslet", "stokeslet_l4": "stokeslet",
              "rpy_g": "rpy", "rpy_l4": "rpy", "stokeslet_reg_g": "stokeslet_reg",
-             "laplace_qd": "laplace_qd", "stokes_dl_pv": "stokes_dl", "stokes_pvel": "stokes_pvel"}
+             "laplace_qd": "laplace_qd", "stokes_dl_pv": "stokes_dl", "stokes_pvel": "stokes_pvel",
+             "stokes_pvel_grad": "stokes_pvel_grad", "stokes_pvel_lapl": "stokes_pvel_lapl",
+             "stokes_pvel_traction": "stokes_pvel_traction", "stokes_dl_grad": "stokes_dl_grad",
+             "stokes_dl_lapl": "stokes_dl_lapl", "stokes_dl_traction": "stokes_dl_traction"}
 
 
 def _inputs(problem, n, seed=0):
@@ -119,6 +122,8 @@ def _inputs(problem, n, seed=0):
     ("laplace_qd", 2000, 48, (4, 6, 8), 1e-5),
     ("stokes_dl_pv", 1200, 40, (4, 6), 1e-3),
     ("stokes_pvel", 1200, 40, (4, 6), 1e-3),
+    ("stokes_pvel_grad", 1200, 40, (4, 6), 3e-3),
+    ("stokes_dl_traction", 1200, 40, (4, 6), 3e-3),
 ])
 def test_kafmm_converges_to_direct_sum(problem, n, q, orders, bound):
     """eps_L2 against the direct sum falls exponentially with the order m (Sec. III)."""

@@ -411,3 +411,54 @@ def test_direct_sums_do_not_depend_on_the_thread_count():
     finally:
         D.set_threads(prev)
     assert np.array_equal(g_all, g_one)
+
+
+@pytest.mark.parametrize("base,ks", [("stokes_pvel", 4), ("stokes_dl", 9)])
+def test_derivative_kernels_against_finite_differences(base, ks):
+    """PVelGrad / PVelLaplacian / Traction target values (Tables tab:ktab_stkslpvelgrad,
+    tab:ktab_stkdlpvelgrad, Eq. stressdef) against central differences of the [p, u] kernel
+    (pinned above): grad p, grad u and lap u by finite differences, [p, u] unchanged; the
+    traction assembled from those differences."""
+    rng = np.random.default_rng(61 if ks == 4 else 62)
+    y = rng.random((4, 3))
+    sv = rng.standard_normal((4, ks))
+    fun = lambda z: D.direct(base, z[None], y, sv)[0]
+    for xt in (np.array([1.3, 0.2, -0.6]), np.array([0.45, 0.5, 0.55]), np.array([-0.7, 1.9, 0.9])):
+        pu = fun(xt)
+        gr = D.direct(base + "_grad", xt[None], y, sv)[0]
+        lp = D.direct(base + "_lapl", xt[None], y, sv)[0]
+        tr = D.direct(base + "_traction", xt[None], y, sv)[0]
+        assert np.allclose(gr[:4], pu, rtol=1e-13, atol=1e-15)
+        assert np.allclose(lp[:4], pu, rtol=1e-13, atol=1e-15)
+        J = fd_grad(fun, xt, h=1e-5)                       # [component, direction]
+        scale = np.abs(J).max()
+        assert np.allclose(gr[4:7], J[0], rtol=1e-6, atol=1e-7 * scale)
+        assert np.allclose(gr[7:].reshape(3, 3), J[1:], rtol=1e-6, atol=1e-7 * scale)
+        # Richardson-extrapolated 7-point Laplacian (error O(h^4))
+        l1 = fd_laplacian(lambda z: fun(z)[1:], xt, h=2e-3)
+        l2 = fd_laplacian(lambda z: fun(z)[1:], xt, h=1e-3)
+        lap = (4.0 * l2 - l1) / 3.0
+        assert np.allclose(lp[4:], lap, rtol=1e-6, atol=1e-6 * np.abs(lap).max())
+        sig = -pu[0] * np.eye(3) + J[1:] + J[1:].T
+        assert np.allclose(tr.reshape(3, 3), sig, rtol=1e-6, atol=1e-7 * scale)
+
+
+@pytest.mark.parametrize("base,ks", [("stokes_pvel", 4), ("stokes_dl", 9)])
+def test_derivative_kernels_solve_stokes(base, ks):
+    """Off the sources the fields are Stokes flows: lap u (worked out from the velocity) equals
+    grad p (worked out from the pressure), div u = tr grad u = 0 (the PVel source term q is a
+    potential flow), and the traction is symmetric with trace -3 p."""
+    rng = np.random.default_rng(63 if ks == 4 else 64)
+    y = rng.random((6, 3))
+    sv = rng.standard_normal((6, ks))
+    x = rng.random((20, 3)) * 3 - 1
+    gr = D.direct(base + "_grad", x, y, sv)
+    lp = D.direct(base + "_lapl", x, y, sv)
+    tr = D.direct(base + "_traction", x, y, sv).reshape(-1, 3, 3)
+    scale = np.abs(gr[:, 4:7]).max()
+    assert np.allclose(lp[:, 4:], gr[:, 4:7], rtol=1e-11, atol=1e-12 * scale)
+    G = gr[:, 7:].reshape(-1, 3, 3)
+    assert np.abs(np.trace(G, axis1=1, axis2=2)).max() < 1e-12 * np.abs(G).max()
+    assert np.allclose(tr, np.transpose(tr, (0, 2, 1)), rtol=0, atol=1e-13 * np.abs(tr).max())
+    assert np.allclose(np.trace(tr, axis1=1, axis2=2), -3 * gr[:, 0], rtol=1e-11,
+                       atol=1e-12 * np.abs(gr[:, 0]).max())

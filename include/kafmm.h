@@ -70,7 +70,16 @@ typedef struct kafmm_plan_s* kafmm_plan_t;
  *                    the fluid removed) to pressure and velocity,
  *                    p = r.f/(4 pi r^3), u = G f - r q/(8 pi r^3); G^P for all interactions,
  *                    check values kept as [h p, u] as for KAFMM_STOKES_DL.  Open boundary
- *                    only. */
+ *                    only.
+ *   Derivative target values (PVelGrad, PVelLaplacian and Traction of Table tab:implement;
+ *   the T column of Tables tab:ktab_stkslpvelgrad and tab:ktab_stkdlpvelgrad), from [f, q]
+ *   sources (KAFMM_STOKES_PVEL_*, k_s=4) or double-layer D sources (KAFMM_STOKES_DL_*, k_s=9),
+ *   on the same StokesPVel ML table, open boundary only:
+ *     *_GRAD      [p, u, d p / d x_1..3, d u_i / d x_j at 7 + 3 i + j]                 k_t=16
+ *     *_LAPL      [p, u, lap u]; lap u is evaluated as grad p (the Stokes equation off the
+ *                 sources, mu = 1)                                                       k_t=7
+ *     *_TRACTION  sigma_ij = -p delta_ij + d u_i / d x_j + d u_j / d x_i at 3 i + j
+ *                 (Eq. stressdef, mu = 1)                                                k_t=9 */
 typedef enum {
   KAFMM_LAPLACE = 0,
   KAFMM_STOKESLET = 1,
@@ -78,7 +87,13 @@ typedef enum {
   KAFMM_STOKES_DL = 3,
   KAFMM_STOKES_REG = 4,
   KAFMM_LAPLACE_QD = 5,
-  KAFMM_STOKES_PVEL = 6
+  KAFMM_STOKES_PVEL = 6,
+  KAFMM_STOKES_PVEL_GRAD = 7,
+  KAFMM_STOKES_PVEL_LAPL = 8,
+  KAFMM_STOKES_PVEL_TRACTION = 9,
+  KAFMM_STOKES_DL_GRAD = 10,
+  KAFMM_STOKES_DL_LAPL = 11,
+  KAFMM_STOKES_DL_TRACTION = 12
 } kafmm_kernel;
 
 /* Boundary conditions (Sec. III.B).  KAFMM_BC_PXYZ: triply periodic in the cube
@@ -208,7 +223,13 @@ enum {
    * of U-list sources are in flight while the previous batch is evaluated).  0 (default): 20 KB
    * per buffer (640 FP32 Stokeslet sources); 64 .. 4096 otherwise; never fewer than the points
    * of one equivalent surface.  kafmm_autotune times 256, 640 and 1280. */
-  KAFMM_OPT_LEAF_STAGE = 16
+  KAFMM_OPT_LEAF_STAGE = 16,
+  /* Consecutive tiles one CTA of the tensor-core gather-GEMM processes in turn: 1 (default),
+   * 2 or 4.  With more than one, the TMEM allocation and barrier set-up are paid once per CTA
+   * and a tile's output writes overlap the next tile's MMAs; fewer are used when the grid would
+   * no longer fill the GPU twice.  Results are bit-identical for every value.
+   * kafmm_autotune times all three. */
+  KAFMM_OPT_TC_TILES = 17
 };
 enum { KAFMM_TC_TF32X3 = 0, KAFMM_TC_BF16X3 = 1, KAFMM_TC_AUTO = 2 };
 enum { KAFMM_PREC_FP64 = 0, KAFMM_PREC_FP32 = 1, KAFMM_PREC_MIXED = 2 };
@@ -277,8 +298,9 @@ int kafmm_eval(kafmm_plan_t plan, const void* s, void* g, int dtype);
  * (2, 1; the work lists are rebuilt for each and the host time of that build is added to the
  * score), KAFMM_OPT_TC_STAGES (2, 4) and KAFMM_OPT_TC_RANGES (1, 2, 4, 8), best of two runs
  * each (tensor-core plans only), then the near-field staging KAFMM_OPT_LEAF_STAGE (256, 640,
- * 1280 sources per buffer) on the leaf phase alone, and keeps the fastest in the plan.  chosen
- * (host, may be NULL, 4 entries) receives {stages, ranges, tiling, leaf stage}.  Call it again
+ * 1280 sources per buffer) on the leaf phase alone, and keeps the fastest in the plan; with
+ * KAFMM_OPT_TC_TILES (1, 2, 4) in the tensor-core combinations.  chosen (host, may be NULL,
+ * 5 entries) receives {stages, ranges, tiling, leaf stage, tiles per CTA}.  Call it again
  * when the tree changes much. */
 int kafmm_autotune(kafmm_plan_t plan, const void* s, void* g, int dtype, int64_t* chosen);
 

@@ -70,6 +70,23 @@ static void configure(Plan& P) {
       P.ml_stokes = 1;
       P.D = 3;
       break;
+    case KAFMM_STOKES_PVEL_GRAD:       // [f, q] or D -> derivative target values on the
+    case KAFMM_STOKES_PVEL_LAPL:       // StokesPVel table (Tables tab:ktab_stkslpvelgrad,
+    case KAFMM_STOKES_PVEL_TRACTION:   // tab:ktab_stkdlpvelgrad)
+    case KAFMM_STOKES_DL_GRAD:
+    case KAFMM_STOKES_DL_LAPL:
+    case KAFMM_STOKES_DL_TRACTION: {
+      const int k = P.kernel;
+      const bool dl = k == KAFMM_STOKES_DL_GRAD || k == KAFMM_STOKES_DL_LAPL || k == KAFMM_STOKES_DL_TRACTION;
+      P.deriv_mode = (k == KAFMM_STOKES_PVEL_GRAD || k == KAFMM_STOKES_DL_GRAD)
+                         ? 0
+                         : ((k == KAFMM_STOKES_PVEL_LAPL || k == KAFMM_STOKES_DL_LAPL) ? 1 : 2);
+      P.ks = dl ? 9 : 4;
+      P.kt = P.deriv_mode == 0 ? 16 : (P.deriv_mode == 1 ? 7 : 9);
+      P.ml_stokes = 2;
+      P.D = 4;
+      break;
+    }
     default:  // double layer D -> [p, u] on the StokesPVel table (Table tab:ktab_stkdlpvelgrad)
       P.ks = 9;
       P.kt = 4;
@@ -139,8 +156,8 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
     return KAFMM_ERR_ARG;
   }
   *out = nullptr;
-  if ((int)kernel < 0 || (int)kernel > 6 ||
-      ((kernel == KAFMM_LAPLACE_QD || kernel == KAFMM_STOKES_DL || kernel == KAFMM_STOKES_PVEL) &&
+  if ((int)kernel < 0 || (int)kernel > 12 ||
+      ((kernel == KAFMM_LAPLACE_QD || kernel >= KAFMM_STOKES_PVEL || kernel == KAFMM_STOKES_DL) &&
        bc == KAFMM_BC_PXYZ) ||
       (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ && bc != KAFMM_BC_WALL) ||
       (bc == KAFMM_BC_WALL && kernel != KAFMM_STOKESLET) || p < 2 || p > 16 || q < 1 || q > 4096) {
@@ -244,6 +261,11 @@ extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
       if (value < 0 || value > 1) return fail(P, KAFMM_ERR_ARG, "test stall must be 0 or 1");
       P.stall_test = (int)value;
       return 0;
+    case KAFMM_OPT_TC_TILES:
+      if (value != 1 && value != 2 && value != 4)
+        return fail(P, KAFMM_ERR_ARG, "tensor-core tiles per CTA must be 1, 2 or 4");
+      P.tc_tiles = (int)value;
+      return 0;
     case KAFMM_OPT_LEAF_STAGE:
       if (value != 0 && (value < 64 || value > 4096))
         return fail(P, KAFMM_ERR_ARG, "leaf staging must be 0 (default) or 64 .. 4096 sources");
@@ -317,10 +339,9 @@ static int set_points_impl(Plan& P, const void* y, int64_t ns, const void* x, in
   rc = build_tree(P, yd, ns, xd, nt, dtype, n_prob, soff, toff);
   if (rc) return rc;
   // tile sizes: the tensor-core kernels take P.tc_boxes target boxes per tile, k_gemm 64 / C
+  // (the work lists are laid out on the host by the first evaluation, while S->M runs)
   int nb_tile = P.use_tc ? P.tc_boxes : 64 / P.C;
-  auto t0 = std::chrono::steady_clock::now();
-  rc = build_worklists(P, nb_tile, nb_tile);
-  P.host_wl_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  rc = worklists_download(P, nb_tile, nb_tile);
   if (rc) return rc;
   P.launches_points = g_launches;
   P.have_points = true;
@@ -410,9 +431,11 @@ extern "C" int kafmm_autotune(kafmm_plan_t pl, const void* s, void* g, int dtype
     return fail(P, KAFMM_ERR_ARG, "kafmm_autotune: bad arguments");
   if ((P.tree.n_src > 0 && is_host_ptr(s)) || (P.tree.n_trg > 0 && is_host_ptr(g)))
     return fail(P, KAFMM_ERR_ARG, "kafmm_autotune takes device pointers only");
-  int best_st = P.tc_stages, best_rg = P.tc_ranges, best_tl = P.wl.m2l_grouped ? 2 : 1;
+  if (int rw = worklists_finish(P)) return rw;
+  int best_st = P.tc_stages, best_rg = P.tc_ranges, best_tl = P.wl.m2l_grouped ? 2 : 1,
+      best_tp = P.tc_tiles;
   if (P.use_tc) {
-    const int stages[2] = {2, 4}, ranges[4] = {1, 2, 4, 8}, tilings[2] = {2, 1};
+    const int stages[2] = {2, 4}, ranges[4] = {1, 2, 4, 8}, tilings[2] = {2, 1}, tiles[3] = {1, 2, 4};
     const int keep_sync = P.sync;
     P.sync = 1;
     float best = 3.4e38f;
@@ -431,24 +454,27 @@ extern "C" int kafmm_autotune(kafmm_plan_t pl, const void* s, void* g, int dtype
       if (tilings[ti] == 2 && !P.wl.m2l_grouped) continue;   // partials do not fit
       rc = kafmm_eval(pl, s, g, dtype);   // every buffer exists before the timing
       for (int a = 0; a < n_stages && !rc; ++a)
-        for (int b = 0; b < 4 && !rc; ++b) {
-          P.tc_stages = stages[a];
-          P.tc_ranges = ranges[b];
-          float t = 0.f;
-          for (int rep = 0; rep < 2 && !rc; ++rep) {   // best of two evaluations
-            rc = kafmm_eval(pl, s, g, dtype);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, P.ev[3], P.ev[7]);
-            t = rep == 0 ? ms : std::min(t, ms);
+        for (int b = 0; b < 4 && !rc; ++b)
+          for (int c = 0; c < 3 && !rc; ++c) {
+            P.tc_stages = stages[a];
+            P.tc_ranges = ranges[b];
+            P.tc_tiles = tiles[c];
+            float t = 0.f;
+            for (int rep = 0; rep < 2 && !rc; ++rep) {   // best of two evaluations
+              rc = kafmm_eval(pl, s, g, dtype);
+              float ms = 0.f;
+              cudaEventElapsedTime(&ms, P.ev[3], P.ev[7]);
+              t = rep == 0 ? ms : std::min(t, ms);
+            }
+            t += (float)host_ms;
+            if (!rc && t < best) {
+              best = t;
+              best_st = stages[a];
+              best_rg = ranges[b];
+              best_tl = tilings[ti];
+              best_tp = tiles[c];
+            }
           }
-          t += (float)host_ms;
-          if (!rc && t < best) {
-            best = t;
-            best_st = stages[a];
-            best_rg = ranges[b];
-            best_tl = tilings[ti];
-          }
-        }
     }
     P.sync = keep_sync;
     P.tc_tiling = best_tl;
@@ -457,6 +483,7 @@ extern "C" int kafmm_autotune(kafmm_plan_t pl, const void* s, void* g, int dtype
   }
   P.tc_stages = best_st;
   P.tc_ranges = best_rg;
+  P.tc_tiles = best_tp;
   // near field: sources per staging buffer, timed on the leaf phase alone
   int best_ls = P.leaf_stage;
   {
@@ -488,6 +515,7 @@ extern "C" int kafmm_autotune(kafmm_plan_t pl, const void* s, void* g, int dtype
     chosen[1] = best_rg;
     chosen[2] = best_tl;
     chosen[3] = best_ls;
+    chosen[4] = best_tp;
   }
   return 0;
 }
@@ -574,6 +602,7 @@ extern "C" int kafmm_tree_info(kafmm_plan_t pl, int64_t* info, int n) {
   if (P.wall_child[0]) return kafmm_tree_info(P.wall_child[0], info, n);
   if (!info || n < 0) return fail(P, KAFMM_ERR_ARG, "bad info array");
   if (!P.have_points) return fail(P, KAFMM_ERR_STATE, "no points");
+  if (int rw = worklists_finish(P)) return rw;   // the pair counts come with the work lists
   const Tree& T = P.tree;
   int64_t v[10] = {T.nbox, T.nleaf, T.nlevels, T.n_u, T.n_v, T.n_w, T.n_x, T.near_pairs, T.max_leaf_pts,
                    T.n_prob};
@@ -706,6 +735,8 @@ extern "C" int kafmm_get_counters(kafmm_plan_t pl, int64_t* c, int n) {
   PLAN_CHECK(pl);
   if (P.wall_child[0]) return kafmm_get_counters(P.wall_child[0], c, n);
   if (!c || n < 0) return fail(P, KAFMM_ERR_ARG, "null array");
+  if (P.have_points)
+    if (int rw = worklists_finish(P)) return rw;
   const bool cm = P.use_tc && P.cmp;
   int64_t v[11] = {P.launches_points, P.launches_eval, P.use_tc ? 1 : 0,
                    P.launches_points + P.launches_eval,
@@ -745,6 +776,10 @@ extern "C" int kafmm_destroy(kafmm_plan_t pl) {
   if (P->wl_event) {
     cudaEventSynchronize(P->wl_event);
     cudaEventDestroy(P->wl_event);
+  }
+  if (P->wl_dl_event) {   // copies into the page-locked staging buffer may still be landing
+    cudaEventSynchronize(P->wl_dl_event);
+    cudaEventDestroy(P->wl_dl_event);
   }
   delete P;
   return 0;

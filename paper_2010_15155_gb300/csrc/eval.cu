@@ -1,6 +1,7 @@
 // The KAFMM evaluation (Sec. II, Fig. kifmmgraph): S->M, M->M, M->L, S->L, L->L, and at the
 // leaves L->T, M->T, S->T; CUDA-core kernels in FP32 or FP64.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 
 #include "physics.cuh"
@@ -41,8 +42,8 @@ __global__ void k_prep_src(const Tin* __restrict__ s, const uint32_t* __restrict
   using T4 = typename V4<T>::type;
   constexpr int KS =
       PR == P_LAP ? 1
-                  : (PR == P_DL ? 9
-                                : ((PR == P_RPY_L4 || PR == P_RPY_G || PR == P_REG_G || PR == P_LAPQD || PR == P_PVEL)
+                  : (dl_src(PR) ? 9
+                                : ((PR == P_RPY_L4 || PR == P_RPY_G || PR == P_REG_G || PR == P_LAPQD || pvel_src(PR))
                                        ? 4
                                        : 3));
   constexpr int NV = ProbInfo<PR>::NV;
@@ -61,6 +62,30 @@ __global__ void k_prep_src(const Tin* __restrict__ s, const uint32_t* __restrict
       r.w = v[4 * q + 3];
       out[i * NV + q] = r;
     }
+  }
+}
+
+// Derivative target values back to the caller's order and dtype, from [p, u, grad p, grad u]
+// per sorted target: mode 0 all 16; mode 1 [p, u, lap u] with lap u = grad p (the Stokes
+// equation off the sources, mu = 1, which every source and equivalent point's field solves);
+// mode 2 the traction sigma_ij = -p delta_ij + d_j u_i + d_i u_j at 3 i + j (Eq. stressdef).
+template <class T, class Tout>
+__global__ void k_unperm_deriv(const T* __restrict__ g, const uint32_t* __restrict__ perm, int64_t n, int mode,
+                               Tout* __restrict__ out) {
+  const int kt = mode == 0 ? 16 : (mode == 1 ? 7 : 9);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * kt;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / kt;
+    const int k = (int)(e % kt);
+    const T* v = g + 16 * i;
+    T o;
+    if (mode == 2) {
+      const int a = k / 3, b = k % 3;
+      o = v[7 + 3 * a + b] + v[7 + 3 * b + a] - (a == b ? v[0] : T(0));
+    } else {
+      o = v[k];   // mode 1: lap u_i = d_i p are entries 4..6
+    }
+    out[(int64_t)perm[i] * kt + k] = (Tout)o;
   }
 }
 
@@ -160,7 +185,7 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
             if (!on[u]) continue;
             T r0 = px[u] - y.x, r1 = py[u] - y.y, r2 = pz[u] - y.z;
             T* ac = acc[u];
-            if (PR == P_DL) {   // S->M, S->L: the double-layer kernel K, [p, u] (p doubled: 1/(8 pi) below)
+            if (dl_src(PR)) {   // S->M, S->L: the double-layer kernel K, [p, u] (p doubled: 1/(8 pi) below)
               T4 v1 = sv[j * NV + 1], v2 = sv[j * NV + 2];
               T Dm[9] = {v.x, v.y, v.z, v.w, v1.x, v1.y, v1.z, v1.w, v2.x};
               T tmp[4] = {0, 0, 0, 0};
@@ -169,7 +194,7 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
               ac[1] += tmp[1];
               ac[2] += tmp[2];
               ac[3] += tmp[3];
-            } else if (PR == P_PVEL) {   // S->M, S->L: G^P, [p, u] (p doubled: 1/(8 pi) below)
+            } else if (pvel_src(PR)) {   // S->M, S->L: G^P, [p, u] (p doubled: 1/(8 pi) below)
               T tmp[4] = {0, 0, 0, 0};
               pvel_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
               ac[0] += T(2) * tmp[0];
@@ -206,7 +231,7 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
         }
       }
     }
-    T sc = (PR == P_STK_G || PR == P_RPY_G || PR == P_REG_G || PR == P_DL || PR == P_PVEL)
+    T sc = (PR == P_STK_G || PR == P_RPY_G || PR == P_REG_G || pvel_table(PR))
                ? T(1.0 / (8.0 * PI))
                : T(1.0 / (4.0 * PI));
     T* out = a.check + (int64_t)b * a.R * C;
@@ -222,7 +247,7 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
           T v = acc[u][d * C + c] * sc;
           // StokesPVel check values are stored as [h p, u] (h: box half-width), which makes
           // the translations level-independent (p falls as 1/r^2, u as 1/r)
-          if ((PR == P_DL || PR == P_PVEL) && d == 0) v *= r;
+          if (pvel_table(PR) && d == 0) v *= r;
           if (a.mode == 0)
             out[idx] = v;
           else
@@ -554,6 +579,8 @@ __device__ inline void far_eval(T xl, T yl, T zl, const typename V4<T>::type& p,
     lap_st<T>(r0, r1, r2, q.x, acc);
   } else if (PR == P_DL || PR == P_PVEL) {   // M->T, L->T: StokesPVel from the equivalent [f, q]
     pvel_st<T>(r0, r1, r2, q.x, q.y, q.z, q.w, acc);
+  } else if (deriv_out(PR)) {   // M->T, L->T: G^P + grad G^P from the equivalent [f, q]
+    pvel_grad_st<T>(r0, r1, r2, q.x, q.y, q.z, q.w, acc);
   } else if (PR == P_LAPQD) {   // M->T, L->T: equivalent charges, L + grad L + grad grad L
     lapqd_st<T, false>(r0, r1, r2, q.x, T(0), T(0), T(0), acc);
   } else if (PR == P_STK_L4 || PR == P_RPY_L4) {
@@ -865,6 +892,8 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
                   lapqd_st<T, true>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
                 } else if (PR == P_PVEL) {
                   pvel_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
+                } else if (PR == P_PVEL_D) {
+                  pvel_grad_st<T>(r0, r1, r2, v.x, v.y, v.z, v.w, tmp);
                 } else if (PR == P_STK_L4 || PR == P_STK_G) {
                   stk_st<T>(r0, r1, r2, v.x, v.y, v.z, tmp);
                 } else if (PR == P_REG_G) {   // S->T: the regularized kernel of the source's eps
@@ -879,7 +908,10 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
                 } else {
                   const T4 v1 = bv[(base + j) * NV + 1], v2 = bv[(base + j) * NV + 2];
                   T Dm[9] = {v.x, v.y, v.z, v.w, v1.x, v1.y, v1.z, v1.w, v2.x};
-                  dl_st<T>(r0, r1, r2, Dm, tmp);
+                  if constexpr (PR == P_DL_D)
+                    dl_grad_st<T>(r0, r1, r2, Dm, tmp);
+                  else
+                    dl_st<T>(r0, r1, r2, Dm, tmp);
                 }
                 if (a.kahan) {
 #pragma unroll
@@ -1016,35 +1048,79 @@ static void add_tiles(WorkLists& W, std::vector<int>* by_cls, int NB, int range[
   range[1] = (int)W.tiles.size();
 }
 
-int build_worklists(Plan& P, int NB, int NB_TC) {
+// Offsets of the tree's per-box fields in the page-locked download buffer.
+struct WlDown {
+  size_t key, xoff, vocc, tb, te, lvl, leaf, wflag, stats, meta, bytes;
+  explicit WlDown(int nb) {
+    key = 0;
+    xoff = key + 8 * (size_t)nb;
+    vocc = xoff + 8 * (size_t)(nb + 1);
+    tb = vocc + 32 * (size_t)nb;
+    te = tb + 4 * (size_t)nb;
+    lvl = te + 4 * (size_t)nb;
+    leaf = lvl + nb;
+    wflag = leaf + nb;
+    stats = (wflag + nb + 7) / 8 * 8;
+    meta = stats + 24;
+    bytes = meta + 4 * 217;
+  }
+};
+
+// Enqueues the copy of the tree's per-box fields into page-locked memory (no wait): the work
+// lists are laid out from them by worklists_finish, which the evaluation calls after enqueuing
+// S->M, so the host work overlaps the upward pass.
+int worklists_download(Plan& P, int NB, int NB_TC) {
   Tree& T = P.tree;
   cudaStream_t st = P.stream;
   const int nb = T.nbox;
-  // the tree's per-box fields, copied once into page-locked memory
-  const size_t o_key = 0, o_xoff = o_key + 8 * (size_t)nb, o_vocc = o_xoff + 8 * (size_t)(nb + 1),
-               o_tb = o_vocc + 32 * (size_t)nb, o_te = o_tb + 4 * (size_t)nb,
-               o_lvl = o_te + 4 * (size_t)nb, o_leaf = o_lvl + nb, o_wflag = o_leaf + nb,
-               o_stats = (o_wflag + nb + 7) / 8 * 8, o_meta = o_stats + 24,
-               down_bytes = o_meta + 4 * 217;
-  // the previous build's uploads read the staging buffers: wait for them before refilling
-  if (P.wl_event) CK(cudaEventSynchronize(P.wl_event));
-  CK(P.wl_down.reserve(down_bytes));
+  const WlDown o(nb);
+  // copies of an earlier download may still be landing in the staging buffer
+  if (P.wl_pending && P.wl_dl_event) CK(cudaEventSynchronize(P.wl_dl_event));
+  P.wl_pending = false;
+  CK(P.wl_down.reserve(o.bytes));
   HostBuf& H = P.wl_down;
-  CK(cudaMemcpyAsync(H.as<void>(o_key), T.key.p, 8 * (size_t)nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(H.as<void>(o_xoff), T.x_off.p, 8 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(H.as<void>(o_vocc), T.vocc.p, 32 * (size_t)nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(H.as<void>(o_tb), T.tb.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(H.as<void>(o_te), T.te.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(H.as<void>(o_lvl), T.level.p, nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(H.as<void>(o_leaf), T.leaf.p, nb, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(H.as<void>(o_wflag), T.w_flag.p, nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o.key), T.key.p, 8 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o.xoff), T.x_off.p, 8 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o.vocc), T.vocc.p, 32 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o.tb), T.tb.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o.te), T.te.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o.lvl), T.level.p, nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o.leaf), T.leaf.p, nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o.wflag), T.w_flag.p, nb, cudaMemcpyDeviceToHost, st));
   // near-field pairs (status words 8-9), V entries and largest leaf (10-13), the grouped M->L
   // pair histogram (216 counts and their total)
-  CK(cudaMemcpyAsync(H.as<void>(o_stats), T.status.as<unsigned>() + 8, 24, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(H.as<void>(o_meta), T.m2l_meta.p, 4 * 217, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpyAsync(H.as<void>(o.stats), T.status.as<unsigned>() + 8, 24, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(H.as<void>(o.meta), T.m2l_meta.p, 4 * 217, cudaMemcpyDeviceToHost, st));
+  if (!P.wl_dl_event) CK(cudaEventCreateWithFlags(&P.wl_dl_event, cudaEventDisableTiming));
+  CK(cudaEventRecord(P.wl_dl_event, st));
+  P.wl_nb = NB;
+  P.wl_nb_tc = NB_TC;
+  P.wl_pending = true;
+  return 0;
+}
+
+int build_worklists(Plan& P, int NB, int NB_TC) {
+  int rc = worklists_download(P, NB, NB_TC);
+  return rc ? rc : worklists_finish(P);
+}
+
+// Lays out the work lists of the downloaded tree on the host and uploads them (no-op unless a
+// download is pending).
+int worklists_finish(Plan& P) {
+  if (!P.wl_pending) return 0;
+  auto t0 = std::chrono::steady_clock::now();
+  Tree& T = P.tree;
+  cudaStream_t st = P.stream;
+  const int nb = T.nbox;
+  const int NB = P.wl_nb, NB_TC = P.wl_nb_tc;
+  const WlDown wd(nb);
+  const size_t o_key = wd.key, o_xoff = wd.xoff, o_vocc = wd.vocc, o_tb = wd.tb, o_te = wd.te, o_lvl = wd.lvl,
+               o_leaf = wd.leaf, o_wflag = wd.wflag, o_stats = wd.stats, o_meta = wd.meta;
+  CK(cudaEventSynchronize(P.wl_dl_event));
+  P.wl_pending = false;
+  HostBuf& H = P.wl_down;
   {
-    const unsigned long long* hs = H.as<unsigned long long>(o_stats);
+  const unsigned long long* hs = H.as<unsigned long long>(o_stats);
     T.near_pairs = (int64_t)hs[0];
     T.n_v = (int64_t)hs[1];
     T.max_leaf_pts = (int)hs[2];
@@ -1165,9 +1241,11 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
   W.xbox_n = (int)W.boxlist.size() - W.xbox_off;
   for (int b = 0; b < nb; ++b)
     if (leaf[b]) W.boxlist.push_back(b);
-  // upload through page-locked staging: tiles and box lists
+  // upload through page-locked staging: tiles and box lists; the previous upload read the
+  // staging buffer, so wait for it before refilling
   const size_t u_tiles = 0, u_box = u_tiles + sizeof(int4) * W.tiles.size(),
                up_bytes = u_box + sizeof(int) * W.boxlist.size();
+  if (P.wl_event) CK(cudaEventSynchronize(P.wl_event));
   CK(P.wl_up.reserve(up_bytes));
   HostBuf& U = P.wl_up;
   std::copy(W.tiles.begin(), W.tiles.end(), U.as<int4>(u_tiles));
@@ -1180,6 +1258,7 @@ int build_worklists(Plan& P, int NB, int NB_TC) {
   // the staging buffers are reused by the next build, which waits for this event first
   if (!P.wl_event) CK(cudaEventCreateWithFlags(&P.wl_event, cudaEventDisableTiming));
   CK(cudaEventRecord(P.wl_event, st));
+  P.host_wl_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return 0;
 }
 
@@ -1269,9 +1348,16 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
   const T4* spos = T_.src_pos.as<T4>();
   const T4* tpos = T_.same ? spos : T_.trg_pos.as<T4>();
   size_t box_bytes = sizeof(T) * (size_t)R * C;
-  int* boxlist = P.tile_meta.as<int>();
-  int n_sleaves = (int)(W.boxlist.size()) - (W.xbox_off + W.xbox_n);
-  const int* sleaves = boxlist + W.xbox_off + W.xbox_n;
+  // S->M runs over the tree's leaf list (box order); the work lists are laid out on the host
+  // while it runs
+  const int n_sleaves = T_.nleaf;
+  const int* sleaves = T_.leaves.as<int>();
+  int* boxlist = nullptr;
+  if (P.near_only) {
+    int rc = worklists_finish(P);
+    if (rc) return rc;
+    boxlist = P.tile_meta.as<int>();
+  }
   if (!P.near_only) {
     CK(P.up_check.reserve(box_bytes * nb));
     CK(P.dn_check.reserve(box_bytes * nb));
@@ -1295,6 +1381,9 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
       sa.mode = 0;
       KL k_s2check<T, PR><<<n_sleaves, 128, 0, st>>>(sa);
     }
+    int rcw = worklists_finish(P);
+    if (rcw) return rcw;
+    boxlist = P.tile_meta.as<int>();
     // The gather-GEMMs run on the tensor cores in the mixed form (four-channel and
     // single-column tables), else on the CUDA cores (k_gemm).
     constexpr bool TC_OK = sizeof(T) == 4 && (C == 4 || C == 1);
@@ -1429,7 +1518,15 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
   // back to the caller's order and dtype
   if (nt > 0) {
     const uint32_t* tperm = T_.same ? T_.src_perm.as<uint32_t>() : T_.trg_perm.as<uint32_t>();
-    if (s_dtype == KAFMM_F64)
+    if constexpr (deriv_out(PR)) {
+      const int kto = P.kt;
+      if (s_dtype == KAFMM_F64)
+        KL k_unperm_deriv<T, double><<<grid_for(nt * kto, 256), 256, 0, st>>>(P.g_sorted.as<T>(), tperm, nt,
+                                                                           P.deriv_mode, (double*)g_out);
+      else
+        KL k_unperm_deriv<T, float><<<grid_for(nt * kto, 256), 256, 0, st>>>(P.g_sorted.as<T>(), tperm, nt,
+                                                                          P.deriv_mode, (float*)g_out);
+    } else if (s_dtype == KAFMM_F64)
       KL k_unperm<T, double><<<grid_for(nt * KT, 256), 256, 0, st>>>(P.g_sorted.as<T>(), tperm, nt, KT,
                                                                 (double*)g_out);
     else
@@ -1455,8 +1552,13 @@ int evaluate(Plan& P, const void* s, void* g, int dtype) {
     pr = P_LAPQD;
   else if (P.kernel == KAFMM_STOKES_PVEL)
     pr = P_PVEL;
-  else
+  else if (P.kernel == KAFMM_STOKES_DL)
     pr = P_DL;
+  else if (P.kernel == KAFMM_STOKES_PVEL_GRAD || P.kernel == KAFMM_STOKES_PVEL_LAPL ||
+           P.kernel == KAFMM_STOKES_PVEL_TRACTION)
+    pr = P_PVEL_D;
+  else
+    pr = P_DL_D;
   (void)dtype;
   int sd = dtype;
 #define DISPATCH(T)                                          \
@@ -1469,7 +1571,9 @@ int evaluate(Plan& P, const void* s, void* g, int dtype) {
     case P_REG_G: return run_eval<T, P_REG_G>(P, s, sd, g);  \
     case P_LAPQD: return run_eval<T, P_LAPQD>(P, s, sd, g);  \
     case P_PVEL: return run_eval<T, P_PVEL>(P, s, sd, g);    \
-    default: return run_eval<T, P_DL>(P, s, sd, g);          \
+    case P_DL: return run_eval<T, P_DL>(P, s, sd, g);        \
+    case P_PVEL_D: return run_eval<T, P_PVEL_D>(P, s, sd, g); \
+    default: return run_eval<T, P_DL_D>(P, s, sd, g);        \
   }
   if (P.fp64()) {
     DISPATCH(double)

@@ -57,8 +57,8 @@ struct Shape {
   static constexpr int STAGES = 196608 / STAGE_BYTES;
   static_assert(STAGE_BYTES == 768 * SWB, "96 KB (SWB 128) or 48 KB (SWB 64) per stage");
 };
-// dynamic shared memory: 192 KB of stages + alignment and slack
-constexpr int SMEM_BYTES = 196608 + 4096 + 16384;
+// dynamic shared memory: 192 KB of stages + alignment
+constexpr int SMEM_BYTES = 196608 + 1024;   // stages + alignment to 1024 bytes
 // non-M->L modes drain the TMEM accumulator into the running sum after every 64 k-values (one
 // 128-byte chunk): the pseudo-inverse factors sum with heavy cancellation, and accumulating two
 // such chunks per drain measured 1.3e-5 against the FP64 form at p = 8 (8.7e-6 with one;
@@ -74,6 +74,9 @@ constexpr int aux_drain() { return 128 / SWB; }
 // one drain per 256 k gives 6.1e-6 but costs 5 % of the M->L time).  A group may span two
 // offsets (the sum is linear).
 constexpr int M2L_GROUP_K = 256;
+// Most tiles one CTA processes in turn (KAFMM_OPT_TC_TILES): the TMEM allocation and barrier
+// set-up are paid once, and a tile's output writes overlap the next tile's MMAs.
+constexpr int TC_TMAX = 4;
 constexpr int THREADS = 448;
 constexpr int NPROD = 256;
 constexpr int W_TMA = 12, W_MMA = 13;
@@ -115,6 +118,8 @@ struct Args {
   // part[tile.x + j] of dn (R x CH floats each) instead of its own box
   const int* part;
   int qrow4;              // StokesPVel table, TC_SCALE: rows 4k+3 (q) take the half-width twice
+  int ntiles;             // tiles of the launch
+  int tpc;                // consecutive tiles per CTA (1 .. TC_TMAX)
 };
 
 // Slots of a mode (upper bound of the slot index), the operator of slot s in the tensor map
@@ -228,55 +233,106 @@ __global__ void __launch_bounds__(THREADS, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t full[4], empty[4], acc_full, acc_empty;
   __shared__ uint32_t tmem_base;
-  __shared__ int nslots, bail;
-  __shared__ int slot_list[216];
-  __shared__ int sbox[NB];
-  __shared__ int sout[NB];          // output record of box j (its box, or its partial)
-  __shared__ float sside[NB];
+  __shared__ int bail;
+  // the CTA's tiles (a.tpc consecutive tiles): box records, active slots and the prefix tables
+  // that map the CTA's iteration index (tile after tile, slot after slot, k-chunk after k-chunk)
+  // and its accumulation groups to their tile
+  __shared__ int sbox[TC_TMAX][NB];
+  __shared__ int sout[TC_TMAX][NB];          // output record of box j (its box, or its partial)
+  __shared__ float sside[TC_TMAX][NB];
+  __shared__ int slots_all[TC_TMAX * 216];
   __shared__ int slot_any[216];
+  __shared__ int t_n[TC_TMAX], t_s0[TC_TMAX], t_cls[TC_TMAX], t_it0[TC_TMAX + 1], t_g0[TC_TMAX + 1];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int4 tile = a.tiles[blockIdx.x];
-  const int cls = tile.z;
-  const int grp = a.mode == TC_M2L ? tile.w - 1 : -1;   // parent neighbour, -1 = whole V lists
   const int R = a.Rout, Rin = a.Rin;
   const int row0 = blockIdx.y * (RB * BM);
   // row blocks of this CTA that hold operator rows (the last pair may have only one)
   const int nrb = min(RB, (R - row0 + BM - 1) / BM);
+  const int T = min(a.tpc, TC_TMAX);
+  const int nchunk = a.nchunk;
+  // accumulation groups: iterations accumulated in TMEM before the epilogue adds them into the
+  // running sum (M->L: a.group chunks; other modes: one 128-byte chunk); a group never spans
+  // two tiles
+  const int GI = a.mode == TC_M2L ? a.group : aux_drain<SWB>();
+  const int nsmax = mode_slots(a.mode);
 
-  if (threadIdx.x < NB) {
-    int b = threadIdx.x < tile.y ? a.boxlist[tile.x + threadIdx.x] : -1;
-    sbox[threadIdx.x] = b;
-    sout[threadIdx.x] = grp >= 0 && b >= 0 ? a.part[tile.x + threadIdx.x] : b;
-    sside[threadIdx.x] = b >= 0 ? (float)(a.L / (double)(1 << a.t.level[b])) : 0.f;
-  }
-  for (int k = threadIdx.x; k < 216; k += THREADS) slot_any[k] = 0;
   if (threadIdx.x == 0) {
     bail = 0;
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], PROD_WARPS + 1);   // one arrival per producer warp + the TMA's
-      mbar_init(&empty[s], 1);
+    for (int st = 0; st < STAGES; ++st) {
+      mbar_init(&full[st], PROD_WARPS + 1);   // one arrival per producer warp + the TMA's
+      mbar_init(&empty[st], 1);
     }
     mbar_init(&acc_full, 1);
     mbar_init(&acc_empty, 128);
   }
-  __syncthreads();
-  // active slots: some box of the tile has a source there
-  const int nsmax = mode_slots(a.mode);
-  // candidate slots: the 8 children of parent neighbour grp, or all slots of the mode
-  const int ncand = grp >= 0 ? 8 : nsmax;
-  for (int e = threadIdx.x; e < ncand * NB; e += THREADS) {
-    int k = e / NB, j = e % NB;
-    if (grp >= 0)
-      k = (2 * (grp % 3) + (k & 1)) + 6 * (2 * ((grp / 3) % 3) + ((k >> 1) & 1)) +
-          36 * (2 * (grp / 9) + (k >> 2));
-    bool inner = false;
-    if (a.mode == TC_M2L) {
-      int ox = k % 6 - 2 - (cls & 1), oy = (k / 6) % 6 - 2 - ((cls >> 1) & 1),
-          oz = k / 36 - 2 - ((cls >> 2) & 1);
-      inner = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
+  int s_run = 0;   // entries of slots_all used so far (warp 0)
+  for (int t = 0; t < T; ++t) {
+    const int ti = blockIdx.x * T + t;
+    const int4 tile = ti < a.ntiles ? a.tiles[ti] : make_int4(0, 0, 0, 0);
+    const int cls = tile.z;
+    const int grp = a.mode == TC_M2L ? tile.w - 1 : -1;   // parent neighbour, -1 = whole V lists
+    for (int j = threadIdx.x; j < NB; j += THREADS) {
+      int b = j < tile.y ? a.boxlist[tile.x + j] : -1;
+      sbox[t][j] = b;
+      sout[t][j] = grp >= 0 && b >= 0 ? a.part[tile.x + j] : b;
+      sside[t][j] = b >= 0 ? (float)(a.L / (double)(1 << a.t.level[b])) : 0.f;
     }
-    if (!inner && slot_src(a, sbox[j], k) >= 0) slot_any[k] = 1;
+    for (int k = threadIdx.x; k < 216; k += THREADS) slot_any[k] = 0;
+    if (threadIdx.x == 0) t_cls[t] = cls;
+    __syncthreads();
+    // active slots: some box of the tile has a source there; candidates: the 8 children of
+    // parent neighbour grp, or all slots of the mode
+    const int ncand = grp >= 0 ? 8 : nsmax;
+    for (int e = threadIdx.x; e < ncand * NB; e += THREADS) {
+      int k = e / NB, j = e % NB;
+      if (grp >= 0)
+        k = (2 * (grp % 3) + (k & 1)) + 6 * (2 * ((grp / 3) % 3) + ((k >> 1) & 1)) +
+            36 * (2 * (grp / 9) + (k >> 2));
+      bool inner = false;
+      if (a.mode == TC_M2L) {
+        int ox = k % 6 - 2 - (cls & 1), oy = (k / 6) % 6 - 2 - ((cls >> 1) & 1),
+            oz = k / 36 - 2 - ((cls >> 2) & 1);
+        inner = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
+      }
+      if (!inner && slot_src(a, sbox[t][j], k) >= 0) slot_any[k] = 1;
+    }
+    __syncthreads();
+    if (warp == 0) {  // active offsets (ballot compaction), then this CTA's share (blockIdx.z)
+      int* list = slots_all + s_run;
+      int ns = 0;
+      for (int k0 = 0; k0 < nsmax; k0 += 32) {
+        const int k = k0 + lane;
+        const bool on = k < nsmax && slot_any[k];
+        const unsigned m = __ballot_sync(0xffffffffu, on);
+        if (on) list[ns + __popc(m & ((1u << lane) - 1u))] = k;
+        ns += __popc(m);
+      }
+      __syncwarp();
+      const int z = blockIdx.z, nz = a.nsplit;
+      const int q0 = (int)((int64_t)ns * z / nz), q1 = (int)((int64_t)ns * (z + 1) / nz);
+      int tmp[7];   // the share moves to the front (at most 216 entries, 7 per lane)
+      int cnt = 0;
+      for (int k = q0 + lane; k < q1; k += 32) tmp[cnt++] = list[k];
+      __syncwarp();
+      cnt = 0;
+      for (int k = q0 + lane; k < q1; k += 32) list[k - q0] = tmp[cnt++];
+      if (lane == 0) {
+        t_n[t] = q1 - q0;
+        t_s0[t] = s_run;
+      }
+      s_run += q1 - q0;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    t_it0[0] = 0;
+    t_g0[0] = 0;
+    for (int t = 0; t < T; ++t) {
+      const int n_it = t_n[t] * nchunk;
+      t_it0[t + 1] = t_it0[t] + n_it;
+      t_g0[t + 1] = t_g0[t] + (n_it + GI - 1) / GI;
+    }
   }
   if (warp == W_MMA) {  // TMEM allocation (whole warp)
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -285,38 +341,19 @@ __global__ void __launch_bounds__(THREADS, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
-  __syncthreads();
-  if (warp == 0) {  // active offsets of this tile (ballot compaction), then this CTA's share
-    int ns = 0;
-    for (int k0 = 0; k0 < nsmax; k0 += 32) {
-      const int k = k0 + lane;
-      const bool on = k < nsmax && slot_any[k];
-      const unsigned m = __ballot_sync(0xffffffffu, on);
-      if (on) slot_list[ns + __popc(m & ((1u << lane) - 1u))] = k;
-      ns += __popc(m);
-    }
-    __syncwarp();
-    const int z = blockIdx.z, nz = a.nsplit;
-    const int s0 = (int)((int64_t)ns * z / nz), s1 = (int)((int64_t)ns * (z + 1) / nz);
-    int tmp[7];   // the share moves to the front of the list (at most 216 entries, 7 per lane)
-    int cnt = 0;
-    for (int k = s0 + lane; k < s1; k += 32) tmp[cnt++] = slot_list[k];
-    __syncwarp();
-    cnt = 0;
-    for (int k = s0 + lane; k < s1; k += 32) slot_list[k - s0] = tmp[cnt++];
-    if (lane == 0) nslots = s1 - s0;
-  }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const int ns = nslots;
-  const int nchunk = a.nchunk;
-  const int total = ns * nchunk;
-  // accumulation groups: iterations accumulated in TMEM before the epilogue adds them into the
-  // running sum (M->L: a.group chunks; other modes: one 128-byte chunk)
-  const int GI = a.mode == TC_M2L ? a.group : aux_drain<SWB>();
-  const int ngroups = (total + GI - 1) / GI;
+  const int total = t_it0[T];
+  // tile of iteration it (iterations run tile after tile), its slot and its k-chunk
+  auto tile_of = [&](int it) {
+    int t = 0;
+    while (t + 1 < T && it >= t_it0[t + 1]) ++t;
+    return t;
+  };
+  auto slot_of = [&](int t, int it) { return slots_all[t_s0[t] + (it - t_it0[t]) / nchunk]; };
+  auto chunk_of = [&](int t, int it) { return (it - t_it0[t]) % nchunk; };
 
   if (warp == W_TMA) {
     // ---------------- TMA producer of A (operator rows, hi and lo) ----------------
@@ -324,8 +361,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int it = 0; it < total; ++it) {
         int st = it % STAGES;
         if (it >= STAGES && !wait_parity(&empty[st], ((it / STAGES) - 1) & 1, a.status, &bail, a.lim)) break;
-        int s = slot_list[it / nchunk], c = it % nchunk;
-        int op = slot_op(a, s, cls);
+        const int t = tile_of(it);
+        int s = slot_of(t, it), c = chunk_of(t, it);
+        int op = slot_op(a, s, t_cls[t]);
         unsigned char* base = smem + st * STAGE_BYTES;
         uint32_t bar = smem_u32(&full[st]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
@@ -364,11 +402,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       int srcb[LPS];
       int cur_slot = -1;
       auto load_half = [&](int it, int h, float4 (&q)[UH][2]) {
-        int s = slot_list[it / nchunk], c = it % nchunk;
-        if (s != cur_slot) {
+        const int t = tile_of(it);
+        int s = slot_of(t, it), c = chunk_of(t, it);
+        if (t * 256 + s != cur_slot) {
 #pragma unroll
-          for (int ul = 0; ul < LPS; ++ul) srcb[ul] = slot_src(a, sbox[box_of(ul)], s);
-          cur_slot = s;
+          for (int ul = 0; ul < LPS; ++ul) srcb[ul] = slot_src(a, sbox[t][box_of(ul)], s);
+          cur_slot = t * 256 + s;
         }
         const int k0 = c * BK + wd * 8;
         const bool kin = k0 < Rin;   // Rin a multiple of 8: a lane's 8 k are all in or all out
@@ -473,18 +512,19 @@ __global__ void __launch_bounds__(THREADS, 1)
       int srcb[LPS];
       int cur_slot = -1;
       auto box_of = [&](int ul) { return pw + PROD_WARPS * (bsel + BPI * ul); };
-      auto set_slot = [&](int s) {
+      auto set_slot = [&](int t, int s) {
 #pragma unroll
-        for (int ul = 0; ul < LPS; ++ul) srcb[ul] = slot_src(a, sbox[box_of(ul)], s);
+        for (int ul = 0; ul < LPS; ++ul) srcb[ul] = slot_src(a, sbox[t][box_of(ul)], s);
       };
       // Software pipeline over half stages (UH boxes per lane each): the loads of the next half
       // are in flight while the current half is converted, including the first half of the next
       // stage (registers only: no shared-memory stage is needed to issue them).
       auto load_half = [&](int it, int h, float4 (&q)[UH][EPL]) {
-        int s = slot_list[it / nchunk], c = it % nchunk;
-        if (s != cur_slot) {
-          set_slot(s);
-          cur_slot = s;
+        const int t = tile_of(it);
+        int s = slot_of(t, it), c = chunk_of(t, it);
+        if (t * 256 + s != cur_slot) {
+          set_slot(t, s);
+          cur_slot = t * 256 + s;
         }
         const int k0 = c * BK + wd * EPL;
         const bool kin = k0 < Rin;   // Rin and k0 even: a bf16 pair is all in or out
@@ -506,16 +546,17 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       };
       auto store_half = [&](int it, int h, const float4 (&q)[UH][EPL]) {
-        int s = slot_list[it / nchunk];
+        const int t = tile_of(it);
+        int s = slot_of(t, it);
         float ox, oy, oz;
-        slot_shift(a.mode, s, cls, ox, oy, oz);
+        slot_shift(a.mode, s, t_cls[t], ox, oy, oz);
         const int st = it % STAGES;
         const uint32_t bhi = smem_u32(smem + st * STAGE_BYTES + A_STAGE);
         const uint32_t blo = bhi + B_BYTES;
 #pragma unroll
         for (int u = 0; u < UH; ++u) {
           const int ul = h * UH + u;
-          float side = sside[box_of(ul)];
+          float side = sside[t][box_of(ul)];
           float sx = ox * side, sy = oy * side, sz = oz * side;
           float v[4][EPL];
 #pragma unroll
@@ -575,90 +616,104 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == W_MMA) {
     // ---------------- MMA issue (one thread) ----------------
     if (lane == 0) {
-      int it = 0;
-      for (int gi = 0; gi < ngroups; ++gi) {
-        if (gi > 0 && !wait_parity(&acc_empty, (gi - 1) & 1, a.status, &bail, a.lim)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        bool ok = true;
-        const int it_end = min(total, (gi + 1) * GI);
-        for (; it < it_end; ++it) {
-          int st = it % STAGES;
-          if (!wait_parity(&full[st], (it / STAGES) & 1, a.status, &bail, a.lim)) {
+      bool ok = true;
+      for (int t = 0; t < T && ok; ++t) {
+        for (int G = t_g0[t]; G < t_g0[t + 1]; ++G) {
+          if (G > 0 && !wait_parity(&acc_empty, (G - 1) & 1, a.status, &bail, a.lim)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-          uint32_t base = smem_u32(smem + st * STAGE_BYTES);
-          uint32_t bhi = base + A_STAGE, blo = bhi + B_BYTES;
-          bool first = it == gi * GI;
-          for (int r = 0; r < nrb; ++r) {
-            uint32_t ahi = base + r * 2 * A_BYTES, alo = ahi + A_BYTES;
-            uint32_t d = tmem + (uint32_t)(r * BN);
-#pragma unroll
-            for (int kk = 0; kk < BK / MK; ++kk) {
-              uint32_t ko = kk * 32;  // MK elements = 32 bytes in both formats and swizzles
-              mma<SPLIT, BN>(d, sdesc<SWB>(ahi + ko), sdesc<SWB>(bhi + ko), (first && kk == 0) ? 0u : 1u);
-              mma<SPLIT, BN>(d, sdesc<SWB>(ahi + ko), sdesc<SWB>(blo + ko), 1u);
-              mma<SPLIT, BN>(d, sdesc<SWB>(alo + ko), sdesc<SWB>(bhi + ko), 1u);
+          const int it_beg = t_it0[t] + (G - t_g0[t]) * GI, it_end = min(t_it0[t + 1], it_beg + GI);
+          for (int it = it_beg; it < it_end; ++it) {
+            int st = it % STAGES;
+            if (!wait_parity(&full[st], (it / STAGES) & 1, a.status, &bail, a.lim)) {
+              ok = false;
+              break;
             }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            uint32_t base = smem_u32(smem + st * STAGE_BYTES);
+            uint32_t bhi = base + A_STAGE, blo = bhi + B_BYTES;
+            bool first = it == it_beg;
+            for (int r = 0; r < nrb; ++r) {
+              uint32_t ahi = base + r * 2 * A_BYTES, alo = ahi + A_BYTES;
+              uint32_t d = tmem + (uint32_t)(r * BN);
+#pragma unroll
+              for (int kk = 0; kk < BK / MK; ++kk) {
+                uint32_t ko = kk * 32;  // MK elements = 32 bytes in both formats and swizzles
+                mma<SPLIT, BN>(d, sdesc<SWB>(ahi + ko), sdesc<SWB>(bhi + ko), (first && kk == 0) ? 0u : 1u);
+                mma<SPLIT, BN>(d, sdesc<SWB>(ahi + ko), sdesc<SWB>(blo + ko), 1u);
+                mma<SPLIT, BN>(d, sdesc<SWB>(alo + ko), sdesc<SWB>(bhi + ko), 1u);
+              }
+            }
+            commit(&empty[st]);
           }
-          commit(&empty[st]);
+          if (!ok) break;
+          commit(&acc_full);
         }
-        if (!ok) break;
-        commit(&acc_full);
       }
     }
   } else {
     // ---------------- epilogue: drain each offset into the running sum ----------------
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     float x[32], y[32];
-    for (int gi = 0; gi < ngroups; ++gi) {
-      // lane 0 waits; the warp stays converged for the .sync.aligned TMEM accesses
-      int ok_wait = lane == 0 ? (wait_parity(&acc_full, gi & 1, a.status, &bail, a.lim) ? 1 : 0) : 0;
-      if (!__shfl_sync(0xffffffffu, ok_wait, 0)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      for (int q = 0; q < nrb * (BN / 32); ++q) {   // row block q / (BN / 32), 32 columns each
-        tmem_ld32(tmem + lane_base + q * 32, x);
-        if (gi > 0) tmem_ld32(tmem + lane_base + SUM_COL + q * 32, y);
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (gi > 0) {
-#pragma unroll
-          for (int t = 0; t < 32; ++t) x[t] += y[t];
-        }
-        tmem_st32(tmem + lane_base + SUM_COL + q * 32, x);
-      }
-      asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      arrive(&acc_empty);
-    }
-    // write the tile: row = row0 + 128 r + lane quarter + lane, columns (box j, channel)
-    // every CTA writes its partial (zeros when it had no offsets) so the combine is fixed-order
-    int do_write = __shfl_sync(0xffffffffu, (!*(volatile int*)&bail) ? 1 : 0, 0);
     float4* dst = reinterpret_cast<float4*>(a.dn + a.part_stride * blockIdx.z);
-    if (do_write) {
+    bool stop = false;
+    for (int t = 0; t < T && !stop; ++t) {
+      for (int G = t_g0[t]; G < t_g0[t + 1]; ++G) {
+        // lane 0 waits; the warp stays converged for the .sync.aligned TMEM accesses
+        int ok_wait = lane == 0 ? (wait_parity(&acc_full, G & 1, a.status, &bail, a.lim) ? 1 : 0) : 0;
+        if (!__shfl_sync(0xffffffffu, ok_wait, 0)) {
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const bool first = G == t_g0[t];   // the tile's first group starts its running sum
+        for (int q = 0; q < nrb * (BN / 32); ++q) {   // row block q / (BN / 32), 32 columns each
+          tmem_ld32(tmem + lane_base + q * 32, x);
+          if (!first) tmem_ld32(tmem + lane_base + SUM_COL + q * 32, y);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          if (!first) {
+#pragma unroll
+            for (int u = 0; u < 32; ++u) x[u] += y[u];
+          }
+          tmem_st32(tmem + lane_base + SUM_COL + q * 32, x);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        arrive(&acc_empty);   // the MMAs of the next group (this or the next tile) may start
+      }
+      if (stop) break;
+      // write tile t (the MMAs of tile t + 1 proceed meanwhile): row = row0 + 128 r + lane
+      // quarter + lane, columns (box j, channel); every CTA writes its partial (zeros when it had
+      // no offsets) so the combine is fixed-order
+      if (blockIdx.x * T + t >= a.ntiles) continue;
+      const int do_write = __shfl_sync(0xffffffffu, (!*(volatile int*)&bail) ? 1 : 0, 0);
+      if (!do_write) break;
+      const bool has = t_n[t] > 0;
       for (int q = 0; q < nrb * (BN / 32); ++q) {
         int row = row0 + (q / (BN / 32)) * BM + (warp & 3) * 32 + lane;
         int qc = q % (BN / 32);
-        if (ns > 0) {
+        if (has) {
           tmem_ld32(tmem + lane_base + SUM_COL + q * 32, x);
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         } else {
 #pragma unroll
-          for (int t = 0; t < 32; ++t) x[t] = 0.f;
+          for (int u = 0; u < 32; ++u) x[u] = 0.f;
         }
         if constexpr (CH == 1) {
           if (row < R) {
-            // column t = box 32 qc + t; a warp writes 32 consecutive rows of one box per store
+            // column u = box 32 qc + u; a warp writes 32 consecutive rows of one box per store
             float* dst1 = a.dn + a.part_stride * blockIdx.z;
 #pragma unroll
-            for (int t = 0; t < 32; ++t) {
-              if (sbox[qc * 32 + t] < 0) continue;
-              float* o = dst1 + (int64_t)sout[qc * 32 + t] * R + row;
-              float v = x[t];
+            for (int u = 0; u < 32; ++u) {
+              if (sbox[t][qc * 32 + u] < 0) continue;
+              float* o = dst1 + (int64_t)sout[t][qc * 32 + u] * R + row;
+              float v = x[u];
               if (a.write == TC_ADD) {
                 v += *o;
               } else if (a.write == TC_SCALE) {
-                const float h = 0.5f * sside[qc * 32 + t];
+                const float h = 0.5f * sside[t][qc * 32 + u];
                 v *= (a.qrow4 && (row & 3) == 3) ? h * h : h;
               }
               *o = v;
@@ -667,9 +722,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         } else if (row < R) {
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
-            if (sbox[qc * 8 + jj] < 0) continue;
+            if (sbox[t][qc * 8 + jj] < 0) continue;
             float4 v = make_float4(x[4 * jj], x[4 * jj + 1], x[4 * jj + 2], x[4 * jj + 3]);
-            float4* o = dst + (int64_t)sout[qc * 8 + jj] * R + row;
+            float4* o = dst + (int64_t)sout[t][qc * 8 + jj] * R + row;
             if (a.write == TC_ADD) {
               float4 w = *o;
               v.x += w.x;
@@ -677,7 +732,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               v.z += w.z;
               v.w += w.w;
             } else if (a.write == TC_SCALE) {
-              float al = 0.5f * sside[qc * 8 + jj];
+              float al = 0.5f * sside[t][qc * 8 + jj];
               v.x *= al;
               v.y *= al;
               v.z *= al;
@@ -687,6 +742,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       }
+      // the next tile's first drain overwrites the running sum: its reads above are complete
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -901,7 +958,12 @@ int tc_gemm_launch(Plan& P, int mode, int opset, const int4* tiles, int ntiles, 
   a.mode = mode;
   a.write = nsplit > 1 || grouped ? tc::TC_STORE : write;
   a.op = m2l ? 0 : op;
-  dim3 grid(ntiles, rows, nsplit);
+  // consecutive tiles per CTA: the option, kept while the grid still fills the 152 SMs twice
+  int tpc = std::max(1, std::min(P.tc_tiles, tc::TC_TMAX));
+  while (tpc > 1 && (int64_t)((ntiles + tpc - 1) / tpc) * rows * nsplit < 152 * 2) tpc /= 2;
+  a.ntiles = ntiles;
+  a.tpc = tpc;
+  dim3 grid((ntiles + tpc - 1) / tpc, rows, nsplit);
   const int swb = sw ? 64 : 128;
   const int bk = swb / (split == SPLIT_TF32 ? tc::Fmt<SPLIT_TF32>::ES : tc::Fmt<SPLIT_BF16>::ES);
   a.nchunk = os.kpad / bk;

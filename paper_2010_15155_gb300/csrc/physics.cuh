@@ -6,8 +6,17 @@
 namespace kafmm {
 
 // Problem = kernel + ML-tree table.
+// P_PVEL_D / P_DL_D: the StokesPVel and double-layer problems with derivative target values
+// (Tables tab:ktab_stkslpvelgrad, tab:ktab_stkdlpvelgrad): [p, u, grad p, grad u] at every
+// target, from which the Laplacian and traction forms are taken.
 enum Prob { P_LAP = 0, P_STK_L4 = 1, P_STK_G = 2, P_RPY_L4 = 3, P_RPY_G = 4, P_DL = 5, P_REG_G = 6,
-            P_LAPQD = 7, P_PVEL = 8 };
+            P_LAPQD = 7, P_PVEL = 8, P_PVEL_D = 9, P_DL_D = 10 };
+
+// [f, q] sources, double-layer D sources, and the StokesPVel ML table shared by all four.
+__host__ __device__ constexpr bool pvel_src(int pr) { return pr == P_PVEL || pr == P_PVEL_D; }
+__host__ __device__ constexpr bool dl_src(int pr) { return pr == P_DL || pr == P_DL_D; }
+__host__ __device__ constexpr bool pvel_table(int pr) { return pvel_src(pr) || dl_src(pr); }
+__host__ __device__ constexpr bool deriv_out(int pr) { return pr == P_PVEL_D || pr == P_DL_D; }
 
 template <int PR>
 struct ProbInfo;
@@ -31,6 +40,10 @@ template <>
 struct ProbInfo<P_LAPQD> { static constexpr int KT = 10, C = 1, D = 1, NV = 1; };
 template <>
 struct ProbInfo<P_PVEL> { static constexpr int KT = 4, C = 1, D = 4, NV = 1; };
+template <>
+struct ProbInfo<P_PVEL_D> { static constexpr int KT = 16, C = 1, D = 4, NV = 1; };
+template <>
+struct ProbInfo<P_DL_D> { static constexpr int KT = 16, C = 1, D = 4, NV = 3; };
 
 template <class T>
 struct V4;
@@ -205,6 +218,63 @@ __device__ inline void dl_st(T r0, T r1, T r2, const T* Dm, T* acc) {
   acc[3] += c * r2;
 }
 
+// StokesPVel with its derivatives (Eqs. stkslp, stkslvel differentiated in x) from [f, q]:
+// [p, u, grad p, grad u] with grad u = d u_i / d x_j at 7 + 3 i + j; acc[0] and acc[4..6] are
+// scaled by 1/(4 pi), the rest by 1/(8 pi) at the end:
+//   4 pi d_j p   = f_j / r^3 - 3 (r.f) r_j / r^5,
+//   8 pi d_j u_i = [delta_ij (r.f - q) + r_i f_j - f_i r_j] / r^3 + 3 r_i r_j (q - r.f) / r^5.
+template <class T>
+__device__ inline void pvel_grad_st(T r0, T r1, T r2, T f0, T f1, T f2, T q, T* acc) {
+  T ir = inv_r(r0 * r0 + r1 * r1 + r2 * r2);
+  T ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+  const T r[3] = {r0, r1, r2}, f[3] = {f0, f1, f2};
+  T rf = r0 * f0 + r1 * f1 + r2 * f2;
+  T g = (rf - q) * ir3;
+  T c = T(3) * rf * ir5;
+  T e = T(3) * (q - rf) * ir5;
+  acc[0] += rf * ir3;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    acc[1 + i] += f[i] * ir + r[i] * g;
+    acc[4 + i] += f[i] * ir3 - c * r[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      acc[7 + 3 * i + j] += (r[i] * f[j] - f[i] * r[j]) * ir3 + r[i] * r[j] * e + (i == j ? g : T(0));
+}
+
+// Double layer with its derivatives (Eqs. stkdlp, stkdlvel differentiated in x), same layout
+// and scaling; rDr = r.D.r, a_j = (D r)_j + (D^T r)_j, t = tr D:
+//   4 pi d_j p   = -3 a_j / r^5 + 15 rDr r_j / r^7 - 3 t r_j / r^5,
+//   8 pi d_j u_i = -3 [delta_ij rDr / r^5 + r_i a_j / r^5 - 5 r_i r_j rDr / r^7].
+template <class T>
+__device__ inline void dl_grad_st(T r0, T r1, T r2, const T* Dm, T* acc) {
+  T ir = inv_r(r0 * r0 + r1 * r1 + r2 * r2);
+  T ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2, ir7 = ir5 * ir2;
+  const T r[3] = {r0, r1, r2};
+  T dr[3], a[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) dr[j] = Dm[3 * j] * r0 + Dm[3 * j + 1] * r1 + Dm[3 * j + 2] * r2;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) a[j] = dr[j] + Dm[j] * r0 + Dm[3 + j] * r1 + Dm[6 + j] * r2;
+  T rDr = r0 * dr[0] + r1 * dr[1] + r2 * dr[2];
+  T t = Dm[0] + Dm[4] + Dm[8];
+  T c5 = rDr * ir5, c7 = T(5) * rDr * ir7;
+  acc[0] += -T(3) * c5 + t * ir3;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    acc[1 + i] += -T(3) * c5 * r[i];
+    acc[4 + i] += -T(3) * a[i] * ir5 + T(3) * (c7 - t * ir5) * r[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      acc[7 + 3 * i + j] += -T(3) * ((i == j ? c5 : T(0)) + r[i] * a[j] * ir5 - r[i] * r[j] * c7);
+}
+
 // Final scale factors of the accumulators.
 template <int PR, class T>
 __device__ inline T out_scale(int k) {
@@ -212,6 +282,7 @@ __device__ inline T out_scale(int k) {
   if (PR == P_LAP || PR == P_LAPQD) return f4;
   if (PR == P_STK_L4 || PR == P_STK_G || PR == P_REG_G) return f8;
   if (PR == P_RPY_L4 || PR == P_RPY_G) return k < 3 ? f8 : f4;
+  if (deriv_out(PR)) return (k == 0 || (k >= 4 && k < 7)) ? f4 : f8;   // [p, u, grad p, grad u]
   return k == 0 ? f4 : f8;  // DL, StokesPVel: [p, u]
 }
 

@@ -53,6 +53,8 @@ struct Tree {
   DevBuf w_flag;                    // [nbox] 1 if the box appears in some W list
   // scratch of the build
   DevBuf s_keys2, s_vals2, s_hist, t_keys2, t_vals2;
+  DevBuf sort_flag;                 // [0] full key sort needed, [1..2] its scan lengths
+  DevBuf dense_start;               // dense cell starts of the top levels (sources, targets)
   DevBuf bld_key, bld_sb, bld_se, bld_tb, bld_te, bld_parent, bld_child, bld_cnt, bld_nch,
       bld_choff, bld_cb, bld_ctb, bld_prob;
   DevBuf status;                    // unsigned status word
@@ -81,6 +83,7 @@ struct WorkLists {
 struct Plan {
   // problem
   int kernel = 0, bc = 0, p = 0, q = 0;
+  int deriv_mode = 0;  // derivative target values: 0 grad, 1 Laplacian, 2 traction
   int prec = KAFMM_PREC_MIXED, variant = KAFMM_ML_L4, near_only = 0, kahan = 0;
   int sync = 1;        // kafmm_eval synchronises and checks the device status (KAFMM_OPT_SYNC)
   int rpy_contact = 0; // KAFMM_OPT_RPY_CONTACT: 0 off, 1 on
@@ -125,6 +128,7 @@ struct Plan {
   int tc_stages = 2;                // pipeline depth of the tensor-core kernel (2 or 4)
   int tc_ranges = 4;                // most slot ranges (CTAs) per tile of a small grid (1..8)
   int tc_tiling = 0;                // M->L tiles: 0 automatic, 1 whole V lists, 2 per neighbour
+  int tc_tiles = 1;                 // consecutive tiles per tensor-core CTA (KAFMM_OPT_TC_TILES)
   size_t dev_mem = 0;               // device memory in bytes (read when the operators are built)
   DevBuf unit64, unit32;            // unit surface [n][3]
   DevBuf tm2l64, tm2l32;            // periodic far-image operator [R][R]
@@ -138,6 +142,9 @@ struct Plan {
   DevBuf tiles, tile_meta;          // work lists of the gather-GEMM engine
   HostBuf wl_down, wl_up;           // pinned staging of the work-list build (tree in, lists out)
   cudaEvent_t wl_event = nullptr;   // the last work-list upload (the staging buffers are free after it)
+  cudaEvent_t wl_dl_event = nullptr;   // the last download of the tree's per-box fields
+  bool wl_pending = false;          // downloaded, work lists not laid out yet (worklists_finish)
+  int wl_nb = 0, wl_nb_tc = 0;      // boxes per tile of the pending layout
   double host_wl_ms = 0;            // host time of the last work-list build
   DevBuf m2l_parts;                 // partial M->L sums per offset range (tensor-core path)
   // grouped M->L: sorted pairs (keys, partial indices, ping-pong halves), pair boxes before
@@ -182,6 +189,8 @@ int m2l_pairs_sort(Plan& P);
 // eval.cu
 int evaluate(Plan& P, const void* s_dev, void* g_dev, int dtype);
 int build_worklists(Plan& P, int NB, int NB_TC);
+int worklists_download(Plan& P, int NB, int NB_TC);
+int worklists_finish(Plan& P);
 int rpy_velocity(Plan& P, const void* s_dev, const void* a_dev, const void* g_dev, void* ua_dev,
                  int dtype);
 int rpy_velocity_noalloc(Plan& P, const void* s_dev, const void* a_dev, const void* g_dev,

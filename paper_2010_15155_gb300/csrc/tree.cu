@@ -2,6 +2,7 @@
 // refinement and the U/V/W/X interaction lists of kernel-independent FMM (Sec. II; the
 // refinement rule of Sec. III with a configurable leaf size).
 #include <algorithm>
+#include <cmath>
 
 #include "plan.cuh"
 #include "scan.cuh"
@@ -10,15 +11,18 @@ namespace kafmm {
 
 // ---------------------------------------------------------------------------------------
 // Morton keys.  Cell I = clamp(floor((p - origin) / L * 2^20), 0, 2^20 - 1) per axis in FP64.
+// When L is a power of two, inv_L = 1 / L is exact and the product equals the quotient.
 template <class T>
 __global__ void k_keys(const T* __restrict__ pts, int64_t n, double ox, double oy, double oz,
-                       double L, uint64_t* __restrict__ key, uint32_t* __restrict__ idx,
+                       double L, double inv_L, uint64_t* __restrict__ key, uint32_t* __restrict__ idx,
                        unsigned* status) {
   const double s = (double)(1 << MAX_LEVEL);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double u[3] = {((double)pts[3 * i] - ox) / L, ((double)pts[3 * i + 1] - oy) / L,
-                   ((double)pts[3 * i + 2] - oz) / L};
+    const double d[3] = {(double)pts[3 * i] - ox, (double)pts[3 * i + 1] - oy, (double)pts[3 * i + 2] - oz};
+    double u[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = inv_L > 0.0 ? d[c] * inv_L : d[c] / L;
     uint32_t c[3];
     bool ok = true;
 #pragma unroll
@@ -61,9 +65,11 @@ __device__ inline unsigned radix_digit(uint64_t k, uint32_t v, int shift, const 
   return (unsigned)((k >> shift) & 255);
 }
 
+// run: the pass is skipped when *run == 0 (nullptr: always runs).
 __global__ void k_radix_hist(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                              int64_t n, int shift, const int64_t* __restrict__ poff, int nprob,
-                             uint32_t* __restrict__ hist, int nblk) {
+                             uint32_t* __restrict__ hist, int nblk, const int* run) {
+  if (run && *run == 0) return;
   __shared__ uint32_t cnt[256];
   cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -79,7 +85,8 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ keys, const uint32_t* 
 __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                 uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
                                 int shift, const int64_t* __restrict__ poff, int nprob,
-                                const uint32_t* __restrict__ hist, int nblk) {
+                                const uint32_t* __restrict__ hist, int nblk, const int* run) {
+  if (run && *run == 0) return;
   __shared__ uint32_t wcnt[RS_WARPS][256];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
@@ -128,30 +135,81 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t
   }
 }
 
-// Sorts keys/vals in place (ping-pong through k2/v2): 8 passes over the 60-bit Morton keys,
-// then, for a batch (nprob > 1), 1 or 2 passes over the problem index of each element's
-// caller index (stable, so each problem's points stay in Morton order).
-static void radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* k2, uint32_t* v2, uint32_t* hist,
-                       int64_t n, const int64_t* poff, int nprob, cudaStream_t st, int key_passes = 8) {
-  if (n <= 1) return;
+// Stable LSD passes over (keys, vals), ping-pong through (k2, v2): one pass per entry of
+// shifts, the 8-bit digit of the key at that bit (an entry s >= 64: bits [s - 64, s - 56) of the
+// problem index of the element's caller index).  An odd number of passes ends with a copy back,
+// so the result is always in (keys, vals).  run / run_len: the passes do nothing when *run == 0
+// (*run_len is then 0, else 256 x blocks); nullptr runs them always.
+static void radix_passes(uint64_t* keys, uint32_t* vals, uint64_t* k2, uint32_t* v2, uint32_t* hist,
+                         int64_t n, const int64_t* poff, int nprob, const int* shifts, int npass,
+                         const int* run, const int* run_len, cudaStream_t st) {
+  if (n <= 1 || npass <= 0) return;
   int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
   uint64_t *ka = keys, *kb = k2;
   uint32_t *va = vals, *vb = v2;
-  int npass = key_passes + (nprob > 1 ? (nprob > 256 ? 2 : 1) : 0);
   for (int pass = 0; pass < npass; ++pass) {
-    bool by_prob = pass >= key_passes;
-    int shift = by_prob ? (pass - key_passes) * 8 : pass * 8;
+    const bool by_prob = shifts[pass] >= 64;
+    const int shift = by_prob ? shifts[pass] - 64 : shifts[pass];
     const int64_t* po = by_prob ? poff : nullptr;
-    KL k_radix_hist<<<nblk, RS_THREADS, 0, st>>>(ka, va, n, shift, po, nprob, hist, nblk);
-    scan_excl<uint32_t>(hist, hist, (int64_t)256 * nblk, nullptr, hist + 256 * (int64_t)nblk,
-                        nullptr, st);
-    KL k_radix_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, po, nprob, hist, nblk);
+    KL k_radix_hist<<<nblk, RS_THREADS, 0, st>>>(ka, va, n, shift, po, nprob, hist, nblk, run);
+    scan_excl<uint32_t>(hist, hist, (int64_t)256 * nblk, run_len, hist + 256 * (int64_t)nblk, nullptr, st);
+    KL k_radix_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, po, nprob, hist, nblk, run);
     std::swap(ka, kb);
     std::swap(va, vb);
   }
-  if (npass & 1) {  // the result sits in (k2, v2)
+  if (npass & 1) {  // the result sits in (k2, v2); run passes only come in even numbers
     cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+  }
+}
+
+// The low 2 x key_passes digits of the keys (for short keys), unconditionally.
+static void radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* k2, uint32_t* v2, uint32_t* hist,
+                       int64_t n, cudaStream_t st, int key_passes) {
+  int shifts[8];
+  for (int i = 0; i < key_passes; ++i) shifts[i] = 8 * i;
+  radix_passes(keys, vals, k2, v2, hist, n, nullptr, 1, shifts, key_passes, nullptr, nullptr, st);
+}
+
+// The Morton keys are first sorted on their top 32 bits (bits 28-59: the cells of levels 1-10
+// in order).  That order is all the refinement reads unless a level-10 cell would split, i.e.
+// holds more than q points (sources and targets); k_deep_check looks for a run of key + 1 equal
+// level-10 cells and then the full sort on all 60 bits runs (a stable LSD sort from scratch:
+// the first order only breaks ties, which index order breaks the same way).  With separate
+// targets each set is checked against q / 2, which bounds the sum.
+constexpr int TOP_SHIFTS[4] = {28, 36, 44, 52};
+constexpr int FULL_SHIFTS[8] = {0, 8, 16, 24, 32, 40, 48, 56};
+constexpr int CELL10_SHIFT = 3 * (MAX_LEVEL - 10);
+
+__global__ void k_deep_check(const uint64_t* __restrict__ key, int64_t n, int run, int* flag) {
+  bool deep = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i + run < n; i += (int64_t)gridDim.x * blockDim.x)
+    deep = deep || (key[i] >> CELL10_SHIFT) == (key[i + run] >> CELL10_SHIFT);
+  if (__any_sync(0xffffffffu, deep) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+// flag[1] / flag[2]: the scan lengths of the full passes of the two sets (0 when skipped).
+__global__ void k_deep_lens(int* flag, int len_s, int len_t) {
+  if (threadIdx.x == 0) {
+    flag[1] = flag[0] ? len_s : 0;
+    flag[2] = flag[0] ? len_t : 0;
+  }
+}
+
+// Dense starts of the cells of levels 1-DENSE_LV in the sorted keys of one point set (a single
+// problem): start[cell_off(l) + cell] = first sorted index in the cell, 0x7f7f7f7f when empty.
+constexpr int DENSE_LV = 5;
+constexpr int DENSE_N = ((1 << (3 * (DENSE_LV + 1))) - 8) / 7;
+__host__ __device__ constexpr int dense_off(int l) { return ((1 << (3 * l)) - 8) / 7; }
+
+__global__ void k_cell_starts(const uint64_t* __restrict__ key, int64_t n, int* __restrict__ start) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = key[i], kp = i > 0 ? key[i - 1] : ~0ull;
+#pragma unroll
+    for (int l = 1; l <= DENSE_LV; ++l) {
+      const int sh = 3 * (MAX_LEVEL - l);
+      if (i == 0 || (k >> sh) != (kp >> sh)) start[dense_off(l) + (int)(k >> sh)] = (int)i;
+    }
   }
 }
 
@@ -164,7 +222,9 @@ struct BuildArgs {
   const uint64_t* tkey;
   const int64_t* soff;   // [nprob + 1] source offsets of the problems
   const int64_t* toff;   // [nprob + 1] target offsets
-  int same, q, nprob;
+  const int* dstart_s;   // dense cell starts of levels 1-DENSE_LV (sources, targets) when dense
+  const int* dstart_t;
+  int same, q, nprob, dense;
   int64_t cap_off[MAX_LEVELS + 1];
   int cap[MAX_LEVELS];
 };
@@ -211,10 +271,26 @@ __global__ void k_split(BuildArgs a, int lv, unsigned* status) {
     if (count > a.q && lv < MAX_LEVEL) {   // warp-uniform
       const uint64_t k = a.key[g];
       int v = 0;
-      if (lane < 8)
+      if (a.dense && lv < DENSE_LV) {
+        // child o starts at the first non-empty child o' >= o (suffix minimum over the 8 cell
+        // starts of each set), else at the end of the box
+        v = 0x7f7f7f7f;
+        const int base = dense_off(lv + 1) + (int)(k * 8);
+        if (lane < 8)
+          v = a.dstart_s[base + lane];
+        else if (lane < 16 && !a.same)
+          v = a.dstart_t[base + lane - 8];
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+          const int w = __shfl_down_sync(0xffffffffu, v, d, 8);
+          if ((lane & 7) + d < 8) v = min(v, w);
+        }
+        v = min(v, lane < 8 ? se : te);
+      } else if (lane < 8) {
         v = lower_bound_prefix(a.skey, sb, se, k * 8 + lane, sh);
-      else if (lane < 16 && !a.same)
+      } else if (lane < 16 && !a.same) {
         v = lower_bound_prefix(a.tkey, tb, te, k * 8 + (lane - 8), sh);
+      }
       int cb[9], ctb[9];
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
@@ -712,9 +788,9 @@ static int grid_for(int64_t n, int threads, int maxb = 152 * 8) {
     if (e_ != cudaSuccess) return cuda_fail(P, e_, #call); \
   } while (0)
 
-// Sorts one point set: keys + permutation, sorted positions in the compute type.
-static int sort_points(Plan& P, const void* pts, int64_t n, int dtype, const int64_t* d_off, int nprob,
-                       DevBuf& key, DevBuf& perm, DevBuf& k2, DevBuf& v2, DevBuf& pos) {
+// Keys + permutation of one point set, sorted on the top 32 bits of the keys.
+static int sort_top(Plan& P, const void* pts, int64_t n, int dtype, DevBuf& key, DevBuf& perm, DevBuf& k2,
+                    DevBuf& v2) {
   Tree& T = P.tree;
   cudaStream_t st = P.stream;
   CK(key.reserve(sizeof(uint64_t) * (n + 1)));
@@ -723,35 +799,52 @@ static int sort_points(Plan& P, const void* pts, int64_t n, int dtype, const int
   CK(v2.reserve(sizeof(uint32_t) * (n + 1)));
   int64_t nblk = (n + RS_TILE - 1) / RS_TILE + 1;
   CK(T.s_hist.reserve(sizeof(uint32_t) * (256 * nblk + 256 * nblk / SCAN_TILE + 64)));
+  if (n == 0) return 0;
   unsigned* status = T.status.as<unsigned>();
   int g = grid_for(n, 256);
-  if (n > 0) {
-    if (dtype == KAFMM_F64)
-      KL k_keys<double><<<g, 256, 0, st>>>((const double*)pts, n, P.origin[0], P.origin[1], P.origin[2],
-                                         P.L, key.as<uint64_t>(), perm.as<uint32_t>(), status);
-    else
-      KL k_keys<float><<<g, 256, 0, st>>>((const float*)pts, n, P.origin[0], P.origin[1], P.origin[2],
-                                        P.L, key.as<uint64_t>(), perm.as<uint32_t>(), status);
-    radix_sort(key.as<uint64_t>(), perm.as<uint32_t>(), k2.as<uint64_t>(), v2.as<uint32_t>(),
-               T.s_hist.as<uint32_t>(), n, d_off, nprob, st);
+  int e = 0;
+  const double inv_L = std::frexp(P.L, &e) == 0.5 ? 1.0 / P.L : 0.0;   // exact for a power of two
+  if (dtype == KAFMM_F64)
+    KL k_keys<double><<<g, 256, 0, st>>>((const double*)pts, n, P.origin[0], P.origin[1], P.origin[2], P.L,
+                                       inv_L, key.as<uint64_t>(), perm.as<uint32_t>(), status);
+  else
+    KL k_keys<float><<<g, 256, 0, st>>>((const float*)pts, n, P.origin[0], P.origin[1], P.origin[2], P.L,
+                                      inv_L, key.as<uint64_t>(), perm.as<uint32_t>(), status);
+  radix_passes(key.as<uint64_t>(), perm.as<uint32_t>(), k2.as<uint64_t>(), v2.as<uint32_t>(), T.s_hist.as<uint32_t>(),
+               n, nullptr, 1, TOP_SHIFTS, 4, nullptr, nullptr, st);
+  return 0;
+}
+
+// The full key sort when flag says so (run_len: its scan lengths), the problem passes of a
+// batch, and the sorted positions in the compute type.
+static int sort_finish(Plan& P, const void* pts, int64_t n, int dtype, const int64_t* d_off, int nprob,
+                       const int* flag, const int* run_len, DevBuf& key, DevBuf& perm, DevBuf& k2, DevBuf& v2,
+                       DevBuf& pos) {
+  Tree& T = P.tree;
+  cudaStream_t st = P.stream;
+  uint64_t* kk = key.as<uint64_t>();
+  uint32_t* vv = perm.as<uint32_t>();
+  radix_passes(kk, vv, k2.as<uint64_t>(), v2.as<uint32_t>(), T.s_hist.as<uint32_t>(), n, nullptr, 1, FULL_SHIFTS,
+               8, flag, run_len, st);
+  if (nprob > 1) {
+    const int prob_shifts[2] = {64, 72};
+    radix_passes(kk, vv, k2.as<uint64_t>(), v2.as<uint32_t>(), T.s_hist.as<uint32_t>(), n, d_off, nprob,
+                 prob_shifts, nprob > 256 ? 2 : 1, nullptr, nullptr, st);
   }
   size_t esz = P.fp64() ? sizeof(double4) : sizeof(float4);
   CK(pos.reserve(esz * (n + 1)));
+  int g = grid_for(n, 256);
   if (n > 0) {
     if (P.fp64()) {
       if (dtype == KAFMM_F64)
-        KL k_gather_pos<double, double4><<<g, 256, 0, st>>>((const double*)pts, perm.as<uint32_t>(), n,
-                                                         pos.as<double4>());
+        KL k_gather_pos<double, double4><<<g, 256, 0, st>>>((const double*)pts, vv, n, pos.as<double4>());
       else
-        KL k_gather_pos<float, double4><<<g, 256, 0, st>>>((const float*)pts, perm.as<uint32_t>(), n,
-                                                        pos.as<double4>());
+        KL k_gather_pos<float, double4><<<g, 256, 0, st>>>((const float*)pts, vv, n, pos.as<double4>());
     } else {
       if (dtype == KAFMM_F64)
-        KL k_gather_pos<double, float4><<<g, 256, 0, st>>>((const double*)pts, perm.as<uint32_t>(), n,
-                                                        pos.as<float4>());
+        KL k_gather_pos<double, float4><<<g, 256, 0, st>>>((const double*)pts, vv, n, pos.as<float4>());
       else
-        KL k_gather_pos<float, float4><<<g, 256, 0, st>>>((const float*)pts, perm.as<uint32_t>(), n,
-                                                       pos.as<float4>());
+        KL k_gather_pos<float, float4><<<g, 256, 0, st>>>((const float*)pts, vv, n, pos.as<float4>());
     }
   }
   CK(cudaGetLastError());
@@ -779,13 +872,38 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
                      cudaMemcpyHostToDevice, st));
   cudaEventRecord(P.ev[0], st);
 
-  int rc = sort_points(P, y, ns, dtype, T.d_src_off.as<int64_t>(), n_prob, T.src_key, T.src_perm,
-                       T.s_keys2, T.s_vals2, T.src_pos);
+  int rc = sort_top(P, y, ns, dtype, T.src_key, T.src_perm, T.s_keys2, T.s_vals2);
+  if (!rc && !T.same) rc = sort_top(P, x, nt, dtype, T.trg_key, T.trg_perm, T.t_keys2, T.t_vals2);
   if (rc) return rc;
-  if (!T.same) {
-    rc = sort_points(P, x, nt, dtype, T.d_trg_off.as<int64_t>(), n_prob, T.trg_key, T.trg_perm,
+  CK(T.sort_flag.reserve(sizeof(int) * 4));
+  int* flag = T.sort_flag.as<int>();
+  CK(cudaMemsetAsync(flag, 0, sizeof(int) * 4, st));
+  {
+    const int run = T.same ? P.q : P.q / 2;
+    if (ns > 0)
+      KL k_deep_check<<<grid_for(ns, 256), 256, 0, st>>>(T.src_key.as<uint64_t>(), ns, run, flag);
+    if (!T.same && nt > 0)
+      KL k_deep_check<<<grid_for(nt, 256), 256, 0, st>>>(T.trg_key.as<uint64_t>(), nt, run, flag);
+    const int len_s = 256 * (int)((ns + RS_TILE - 1) / RS_TILE), len_t = 256 * (int)((nt + RS_TILE - 1) / RS_TILE);
+    KL k_deep_lens<<<1, 32, 0, st>>>(flag, len_s, len_t);
+  }
+  rc = sort_finish(P, y, ns, dtype, T.d_src_off.as<int64_t>(), n_prob, flag, flag + 1, T.src_key, T.src_perm,
+                   T.s_keys2, T.s_vals2, T.src_pos);
+  if (!rc && !T.same)
+    rc = sort_finish(P, x, nt, dtype, T.d_trg_off.as<int64_t>(), n_prob, flag, flag + 2, T.trg_key, T.trg_perm,
                      T.t_keys2, T.t_vals2, T.trg_pos);
-    if (rc) return rc;
+  if (rc) return rc;
+  // dense cell starts of the top levels (one problem): the refinement of levels 0 to
+  // DENSE_LV - 1 reads its child boundaries there instead of searching
+  const bool dense = n_prob == 1;
+  if (dense) {
+    CK(T.dense_start.reserve(sizeof(int) * 2 * DENSE_N));
+    CK(cudaMemsetAsync(T.dense_start.p, 0x7f, sizeof(int) * (T.same ? 1 : 2) * DENSE_N, st));
+    if (ns > 0)
+      KL k_cell_starts<<<grid_for(ns, 256), 256, 0, st>>>(T.src_key.as<uint64_t>(), ns, T.dense_start.as<int>());
+    if (!T.same && nt > 0)
+      KL k_cell_starts<<<grid_for(nt, 256), 256, 0, st>>>(T.trg_key.as<uint64_t>(), nt,
+                                                        T.dense_start.as<int>() + DENSE_N);
   }
 
   // per-level capacities: n_prob roots; below, min(n_prob 8^l, 8 * floor(N / (q + 1)) + 8)
@@ -834,6 +952,9 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   a.tkey = T.same ? a.skey : T.trg_key.as<uint64_t>();
   a.same = T.same ? 1 : 0;
   a.q = P.q;
+  a.dense = dense ? 1 : 0;
+  a.dstart_s = dense ? T.dense_start.as<int>() : nullptr;
+  a.dstart_t = dense ? T.dense_start.as<int>() + DENSE_N : nullptr;
   unsigned* status = T.status.as<unsigned>();
   int* d_total = a.cnt + MAX_LEVELS + 1;
   KL k_root<<<grid_for(n_prob, 256), 256, 0, st>>>(a);
@@ -998,7 +1119,7 @@ int m2l_pairs_sort(Plan& P) {
   KL k_m2l_pair_emit<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vocc.as<uint4>(), vmin, T.m2l_base.as<int>(), k1,
                                                       v1, P.m2l_pbox.as<int>(), P.m2l_comb.as<int4>());
   // two 8-bit passes over the 16-bit keys (stable): the sorted values are the partial indices
-  radix_sort(k1, v1, k1 + n + 1, v1 + n + 1, P.m2l_hist.as<uint32_t>(), n, nullptr, 1, st, 2);
+  radix_sort(k1, v1, k1 + n + 1, v1 + n + 1, P.m2l_hist.as<uint32_t>(), n, st, 2);
   KL k_m2l_pair_box<<<grid_for(n, 256), 256, 0, st>>>(v1, P.m2l_pbox.as<int>(), n, P.m2l_box.as<int>());
   P.m2l_part_sorted = v1;
   CK(cudaGetLastError());

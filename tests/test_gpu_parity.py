@@ -19,7 +19,12 @@ from oracle.tree import Tree  # noqa: E402
 from paper_2010_15155_gb300 import kafmm as K  # noqa: E402
 
 KERN = {"laplace": K.LAPLACE, "stokeslet": K.STOKESLET, "rpy": K.RPY, "stokes_dl": K.STOKES_DL,
-        "stokeslet_reg": K.STOKES_REG, "laplace_qd": K.LAPLACE_QD, "stokes_pvel": K.STOKES_PVEL}
+        "stokeslet_reg": K.STOKES_REG, "laplace_qd": K.LAPLACE_QD, "stokes_pvel": K.STOKES_PVEL,
+        "stokes_pvel_grad": K.STOKES_PVEL_GRAD, "stokes_pvel_lapl": K.STOKES_PVEL_LAPL,
+        "stokes_pvel_traction": K.STOKES_PVEL_TRACTION, "stokes_dl_grad": K.STOKES_DL_GRAD,
+        "stokes_dl_lapl": K.STOKES_DL_LAPL, "stokes_dl_traction": K.STOKES_DL_TRACTION}
+DERIV = ["stokes_pvel_grad", "stokes_pvel_lapl", "stokes_pvel_traction", "stokes_dl_grad", "stokes_dl_lapl",
+         "stokes_dl_traction"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -100,7 +105,7 @@ def _near_oracle(kernel, pts, s, q):
 
 
 @pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "rpy", "stokes_dl", "stokeslet_reg",
-                                    "laplace_qd", "stokes_pvel"])
+                                    "laplace_qd", "stokes_pvel"] + DERIV)
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_near_field_matches_oracle(kernel, prec):
     n, q = 3000, 50
@@ -129,7 +134,7 @@ def test_near_field_matches_oracle(kernel, prec):
     ("laplace_qd", "laplace_qd", K.ML_L4, 3000, 6, 40),
     ("stokes_dl_pv", "stokes_dl", K.ML_L4, 1500, 6, 40),
     ("stokes_pvel", "stokes_pvel", K.ML_L4, 1500, 6, 40),
-])
+] + [(k, k, K.ML_L4, 1500, 6, 40) for k in DERIV])
 def test_fp64_gpu_kafmm_matches_cpu_kafmm(problem, kernel, variant, n, p, q):
     if problem == "laplace":
         pts, s = W.laplace_uniform(n, seed=0)
@@ -141,6 +146,28 @@ def test_fp64_gpu_kafmm_matches_cpu_kafmm(problem, kernel, variant, n, p, q):
     g = plan.eval(torch.from_numpy(s).cuda()).cpu().numpy()
     plan.close()
     assert D.rel_l2(g, ref) < 1e-7
+
+
+@pytest.mark.parametrize("kernel", DERIV)
+def test_derivative_targets_mixed_form_against_direct_sum(kernel):
+    """Gradient, Laplacian and traction target values of the mixed form (FP32 near field,
+    tensor-core M->L) and of the FP64 form at p = 10 against the oracle's direct sum on 500
+    sampled targets (measured on a GB300: FP64 form 2e-10 .. 3.5e-8, mixed 1.9e-7 .. 3.4e-7)."""
+    pts, s = _inputs(kernel, 40000, seed=17, dtype=np.float32)
+    idx = np.arange(0, 40000, 80)
+    ref = D.direct(kernel, pts.astype(np.float64)[idx], pts.astype(np.float64), s.astype(np.float64))
+    err = {}
+    for prec in (K.PREC_FP64, K.PREC_MIXED):
+        dt = torch.float64 if prec == K.PREC_FP64 else torch.float32
+        plan = K.Plan(KERN[kernel], p=10, q=64, precision=prec)
+        plan.set_points(torch.from_numpy(pts).to(dt).cuda())
+        g = plan.eval(torch.from_numpy(s).to(dt).cuda()).double().cpu().numpy()
+        if prec == K.PREC_MIXED:
+            assert K.kafmm_get_counters(plan.h)["tensor_core_m2l"] == 1
+        plan.close()
+        err[prec] = D.rel_l2(g[idx], ref)
+    print(kernel, err)
+    assert err[K.PREC_FP64] < 2e-7 and err[K.PREC_MIXED] < 2e-6, err
 
 
 def test_fp64_gpu_kafmm_adaptive_tree_matches_cpu_kafmm():
@@ -462,6 +489,36 @@ def test_tensor_core_pipeline_depths_agree_bit_for_bit(p):
     assert torch.equal(out[2], out[4])
 
 
+@pytest.mark.parametrize("compress,tiling", [(0, 2), (0, 1), (2, 2), (2, 1)])
+def test_tensor_core_tiles_per_cta_agree_bit_for_bit(compress, tiling):
+    """One, two or four consecutive tiles per CTA of the gather-GEMM issue the same MMAs per tile
+    in the same order: identical bits, dense and compressed, grouped and per-class tiles, on an
+    adaptive cloud whose tile count is not a multiple of four."""
+    pts = W.lognormal_points(70001, seed=12).astype(np.float32)
+    f = np.random.default_rng(12).standard_normal((len(pts), 3)).astype(np.float32)
+    y = torch.from_numpy(pts).cuda()
+    s = torch.from_numpy(f).cuda()
+    out = {}
+    for tiles in (1, 2, 4):
+        plan = K.Plan(K.STOKESLET, p=10, q=64, precision=K.PREC_MIXED, variant=K.ML_L4, compress=compress)
+        K.kafmm_set_option(plan.h, K.OPT_TC_TILING, tiling)
+        K.kafmm_set_option(plan.h, K.OPT_TC_TILES, tiles)
+        plan.set_points(y)
+        out[tiles] = plan.eval(s)
+        assert K.kafmm_get_counters(plan.h)["tensor_core_m2l"] == 1
+        plan.close()
+    assert torch.equal(out[1], out[2]) and torch.equal(out[1], out[4])
+
+
+def test_tensor_core_tiles_option_is_validated():
+    plan = K.Plan(K.STOKESLET, p=6, q=64, precision=K.PREC_MIXED)
+    for bad in (0, 3, 8):
+        with pytest.raises(K.KafmmError) as e:
+            K.kafmm_set_option(plan.h, K.OPT_TC_TILES, bad)
+        assert e.value.code == -1
+    plan.close()
+
+
 def test_autotune_picks_a_valid_configuration():
     """kafmm_autotune times the tensor-core pipeline depth and slot-range counts on the current
     points and keeps the fastest; evaluation afterwards equals an evaluation with those options
@@ -475,6 +532,7 @@ def test_autotune_picks_a_valid_configuration():
     chosen = K.kafmm_autotune(plan.h, s, g, K.F32)
     assert chosen["tc_stages"] in (2, 4) and chosen["tc_ranges"] in (1, 2, 4, 8)
     assert chosen["tc_tiling"] in (1, 2) and chosen["leaf_stage"] in (256, 640, 1280)
+    assert chosen["tc_tiles"] in (1, 2, 4)
     tuned = plan.eval(s)
     plan.close()
     ref = K.Plan(K.STOKESLET, p=8, q=64, precision=K.PREC_MIXED, variant=K.ML_L4,
@@ -482,6 +540,7 @@ def test_autotune_picks_a_valid_configuration():
     K.kafmm_set_option(ref.h, K.OPT_TC_RANGES, chosen["tc_ranges"])
     K.kafmm_set_option(ref.h, K.OPT_TC_TILING, chosen["tc_tiling"])
     K.kafmm_set_option(ref.h, K.OPT_LEAF_STAGE, chosen["leaf_stage"])
+    K.kafmm_set_option(ref.h, K.OPT_TC_TILES, chosen["tc_tiles"])
     ref.set_points(y)
     assert torch.equal(ref.eval(s), tuned)
     ref.close()

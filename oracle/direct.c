@@ -567,24 +567,79 @@ static void ewald_stk_block(const double r[3], double L, double xi, int nreal, i
       }
 }
 
-/* g += sum_b K_per(x_a - y_b) s_b; kernel 0 = Laplace (k_s = k_t = 1), 1 = Stokeslet (3). */
+/* Gradient of the periodic Laplace Green's function above, d G_per / d r_i: the real-space
+ * terms differentiated, d/dr (erfc(xi r)/r) = -erfc(xi r)/r^2 - (2 xi/sqrt(pi)) e^{-xi^2 r^2}/r,
+ * and the Fourier terms, -(1/V) sum_{k != 0} e^{-k^2/4xi^2}/k^2 k_i sin(k.r).  At r = 0 the
+ * n = 0 real-space term (the point's own regular part, even in r) contributes nothing. */
+static void ewald_lapgrad_block(const double r[3], double L, double xi, int nreal, int nfour,
+                                double out[3]) {
+  double V = L * L * L, sp = 2.0 * xi / sqrt(PI);
+  out[0] = out[1] = out[2] = 0.0;
+  for (int i = -nreal; i <= nreal; ++i)
+    for (int j = -nreal; j <= nreal; ++j)
+      for (int k = -nreal; k <= nreal; ++k) {
+        double d[3] = {r[0] + i * L, r[1] + j * L, r[2] + k * L};
+        double rr = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (rr == 0.0) continue;
+        double rn = sqrt(rr);
+        double dr = (-erfc(xi * rn) / rr - sp * exp(-xi * xi * rr) / rn) / (4.0 * PI);
+        for (int q = 0; q < 3; ++q) out[q] += dr * d[q] / rn;
+      }
+  for (int a = -nfour; a <= nfour; ++a)
+    for (int b = -nfour; b <= nfour; ++b)
+      for (int c = -nfour; c <= nfour; ++c) {
+        if (a == 0 && b == 0 && c == 0) continue;
+        double kv[3] = {2.0 * PI * a / L, 2.0 * PI * b / L, 2.0 * PI * c / L};
+        double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+        double w = -exp(-k2 / (4.0 * xi * xi)) / k2 / V * sin(kv[0] * r[0] + kv[1] * r[1] + kv[2] * r[2]);
+        for (int q = 0; q < 3; ++q) out[q] += w * kv[q];
+      }
+}
+
+/* Periodic StokesPVel block [p, u] <- [f, q] (4 x 4, row-major), Eqs. stkslp, stkslvel with
+ * every image: u <- f is Hasimoto's periodic Stokeslet; the pressure of a force and the flow of
+ * a source are gradients of the Laplace Green's function, p = -f . grad(1/(4 pi r)) and
+ * u = (q/2) grad(1/(4 pi r)), so periodically -f . grad G_per and (q/2) grad G_per (the zero
+ * mean pressure of Hasimoto's solution, whose uniform backflow balances the net force, and a
+ * uniform sink balancing the net source); p <- q is zero. */
+static void ewald_pvel_block(const double r[3], double L, double xi, int nreal, int nfour, double m[16]) {
+  double s9[9], gl[3];
+  ewald_stk_block(r, L, xi, nreal, nfour, s9);
+  ewald_lapgrad_block(r, L, xi, nreal, nfour, gl);
+  for (int b = 0; b < 3; ++b) m[b] = -gl[b];
+  m[3] = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) m[4 * (1 + a) + b] = s9[3 * a + b];
+    m[4 * (1 + a) + 3] = 0.5 * gl[a];
+  }
+}
+
+/* Rows/columns per point of the periodic kernels: 0 Laplace (1), 1 Stokeslet (3), 2 StokesPVel (4). */
+static int ewald_dim(int kernel) { return kernel == 0 ? 1 : (kernel == 1 ? 3 : 4); }
+
+static void ewald_block(int kernel, const double r[3], double L, double xi, int nreal, int nfour, double* m) {
+  if (kernel == 0)
+    ewald_lap_block(r, L, xi, nreal, nfour, m);
+  else if (kernel == 1)
+    ewald_stk_block(r, L, xi, nreal, nfour, m);
+  else
+    ewald_pvel_block(r, L, xi, nreal, nfour, m);
+}
+
+/* g += sum_b K_per(x_a - y_b) s_b; kernel 0 = Laplace (k_s = k_t = 1), 1 = Stokeslet (3),
+ * 2 = StokesPVel ([f, q] -> [p, u], 4). */
 void orc_ewald_sum(int kernel, const double* x, int64_t nt, const double* y, int64_t ns,
                    const double* s, double L, double xi, int nreal, int nfour, double* g) {
+  const int kt = ewald_dim(kernel);
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t a = 0; a < nt; ++a) {
-    double acc[3] = {0, 0, 0}, m[9];
+    double acc[4] = {0, 0, 0, 0}, m[16];
     for (int64_t b = 0; b < ns; ++b) {
       double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1], x[3 * a + 2] - y[3 * b + 2]};
-      if (kernel == 0) {
-        ewald_lap_block(r, L, xi, nreal, nfour, m);
-        acc[0] += m[0] * s[b];
-      } else {
-        ewald_stk_block(r, L, xi, nreal, nfour, m);
-        for (int p = 0; p < 3; ++p)
-          for (int q = 0; q < 3; ++q) acc[p] += m[3 * p + q] * s[3 * b + q];
-      }
+      ewald_block(kernel, r, L, xi, nreal, nfour, m);
+      for (int p = 0; p < kt; ++p)
+        for (int q = 0; q < kt; ++q) acc[p] += m[kt * p + q] * s[kt * b + q];
     }
-    int kt = kernel == 0 ? 1 : 3;
     for (int p = 0; p < kt; ++p) g[kt * a + p] += acc[p];
   }
 }
@@ -593,20 +648,15 @@ void orc_ewald_sum(int kernel, const double* x, int64_t nt, const double* y, int
  * [nt * kt][ns * kt]. */
 void orc_ewald_matrix(int kernel, const double* x, int64_t nt, const double* y, int64_t ns, double L,
                       double xi, int nreal, int nfour, double* out) {
-  int kt = kernel == 0 ? 1 : 3;
+  const int kt = ewald_dim(kernel);
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t a = 0; a < nt; ++a) {
-    double m[9];
+    double m[16];
     for (int64_t b = 0; b < ns; ++b) {
       double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1], x[3 * a + 2] - y[3 * b + 2]};
-      if (kernel == 0) {
-        ewald_lap_block(r, L, xi, nreal, nfour, m);
-        out[a * ns + b] = m[0];
-      } else {
-        ewald_stk_block(r, L, xi, nreal, nfour, m);
-        for (int p = 0; p < 3; ++p)
-          for (int q = 0; q < 3; ++q) out[(3 * a + p) * (3 * ns) + 3 * b + q] = m[3 * p + q];
-      }
+      ewald_block(kernel, r, L, xi, nreal, nfour, m);
+      for (int p = 0; p < kt; ++p)
+        for (int q = 0; q < kt; ++q) out[(kt * a + p) * (kt * ns) + kt * b + q] = m[kt * p + q];
     }
   }
 }

@@ -36,6 +36,21 @@ Readings of points the paper leaves open:
   (sum_j q_j |y_j - c|^2 - sum_k M_k |ue_k - c|^2) / (6 V) is added back at the end
   (c: root centre, M: the root's equivalent charges).  The Stokeslet needs no such step: a
   uniform body force is balanced by pressure alone.
+* Periodic StokesPVel table (the [f, q] and double-layer problems): the zero-mean periodic
+  pressure of a force and flow of a source are gradients of the periodic Laplace function,
+  grad G_per = grad(harmonic) + r / (3 V), and Hasimoto's Stokeslet carries the matching
+  backflow.  Two source moments are then not fixed by the far field the equivalent density
+  reproduces, and each shifts the result by a constant: the trace of the force dipole
+  tr M = sum f.(y - c) (an isotropic force dipole has no free-space field), which shifts the
+  pressure by tr M / (3 V); and the split of the potential-dipole field between the source
+  dipole d = sum q (y - c) and the force quadrupole, whose potential-dipole content is
+  a = (2 v - w) / 5 with v = sum f |y - c|^2, w = sum (f.(y - c)) (y - c) (the remaining
+  second moments are traceless or have no field).  d + a is fixed by the far field, but the
+  two pieces extend periodically with different constants, shifting the velocity by
+  -d / (6 V) + a / (3 V).  The differences of these constants between the true sources and
+  the root's equivalent density are added at the end (derived here; pinned by the periodic
+  Ewald sums of the StokesPVel kernel).  A double-layer source D is a force dipole -sym(D)
+  and a source q = tr D at its point (the kernel sees only sym(D)).
 """
 from __future__ import annotations
 
@@ -250,6 +265,33 @@ class KAFMM:
         out[:, 3] += dens[:, :3] @ (np.asarray(c_from) - np.asarray(c_to))
         return out
 
+    def _pvel_periodic_shift(self, src, s, root_eq, c0):
+        """Constant pressure and velocity shifts of the periodic StokesPVel table (module
+        notes): the moment differences between the true sources and the root's equivalent
+        density (real units [f, q] at the root's upward equivalent points)."""
+        def moments(dy, f, q, Mi):
+            # dy: positions - c0; f: forces; q: sources; Mi: intrinsic force dipoles [n, 3, 3]
+            trM = np.sum(f * dy) + np.trace(Mi, axis1=1, axis2=2).sum()
+            d = np.sum(q[:, None] * dy, axis=0)
+            v = np.sum(f * np.sum(dy * dy, axis=1)[:, None], axis=0) + 2.0 * np.einsum("njk,nk->j", Mi, dy)
+            w = (np.sum(np.sum(f * dy, axis=1)[:, None] * dy, axis=0)
+                 + np.einsum("njj,nl->l", Mi, dy) + np.einsum("njl,nj->l", Mi, dy))
+            return trM, d, (2.0 * v - w) / 5.0
+        dy = src - c0
+        if self.ks == 9:   # double layer: force dipole -sym(D), source tr D
+            Dm = s.reshape(-1, 3, 3)
+            S = 0.5 * (Dm + np.transpose(Dm, (0, 2, 1)))
+            mt = moments(dy, np.zeros_like(dy), np.trace(S, axis1=1, axis2=2), -S)
+        else:
+            mt = moments(dy, s[:, :3], s[:, 3], np.zeros((len(src), 3, 3)))
+        ue = self._surf("ue", c0, 0) - c0
+        E = root_eq.reshape(-1, 4)
+        me = moments(ue, E[:, :3], E[:, 3], np.zeros((len(E), 3, 3)))
+        V = self.L ** 3
+        dp = (mt[0] - me[0]) / (3.0 * V)
+        du = -(mt[1] - me[1]) / (6.0 * V) + (mt[2] - me[2]) / (3.0 * V)
+        return dp, du
+
     # ---- evaluation ------------------------------------------------------------------------
     def evaluate(self, src, s, trg=None, tree: Tree | None = None, near_only: bool = False):
         """g at the targets (sources if trg is None), [nt, k_t]."""
@@ -282,6 +324,7 @@ class KAFMM:
                             dm = self._shift(M[ch], T.centre(ch), c)
                             chk += self._op("m2m", lv + 1, rel) @ dm
                     M[b] = self._pinv("up", lv) @ chk
+            self.root_equiv = M[0]
 
             # downward pass: V (M->L), X (S->L), L->L, then L = DC2DE * check
             for lv in range(T.nlevels):
@@ -316,6 +359,13 @@ class KAFMM:
             second = np.sum(s[:, 0] * np.sum((src - c0) ** 2, axis=1))
             second_eq = np.sum(M[0][:, 0] * np.sum((ue0 - c0) ** 2, axis=1))
             g += (second - second_eq) / (6.0 * self.L ** 3)
+        if per and self.ml == "stokes_pvel" and not near_only:
+            dp, du = self._pvel_periodic_shift(src, s, M[0], T.centre(0))
+            if self.problem in ("stokes_pvel_traction", "stokes_dl_traction"):
+                g[:, [0, 4, 8]] -= dp           # sigma = -p I + ...
+            else:
+                g[:, 0] += dp
+                g[:, 1:4] += du
         for b in T.leaves():
             ti = T.trg_idx[b]
             if len(ti) == 0:

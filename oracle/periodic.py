@@ -10,8 +10,9 @@ in the authors' earlier work and not in the paper; the reading used here:
   applied to the root's upward equivalent density and added to the root's downward check
   potential (dc, ue: the root's surfaces).
 * G_per is the Ewald sum with the k = 0 mode removed (zero-mean field; the sources must be
-  neutral / force-free), evaluated in C (``direct.c``: Laplace, and the Stokeslet by
-  Hasimoto's splitting).
+  neutral / force-free), evaluated in C (``direct.c``: Laplace, the Stokeslet by Hasimoto's
+  splitting, and StokesPVel from the two: its pressure of a force and flow of a source are
+  gradients of the Laplace Green's function).
 """
 from __future__ import annotations
 
@@ -38,10 +39,13 @@ def _lib():
     return L
 
 
+_KID = {"laplace": (0, 1), "stokeslet": (1, 3), "stokes_pvel": (2, 4)}
+
+
 def ewald_sum(kernel: str, x, y, s, L=1.0, xi_l=XI_L, nreal=NREAL, nfour=NFOUR):
-    """sum_b K_per(x_a - y_b) s_b (FP64); kernel 'laplace' or 'stokeslet'."""
-    kid = 0 if kernel == "laplace" else 1
-    kt = 1 if kid == 0 else 3
+    """sum_b K_per(x_a - y_b) s_b (FP64); kernel 'laplace', 'stokeslet' or 'stokes_pvel'
+    ([f, q] -> [p, u])."""
+    kid, kt = _KID[kernel]
     x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1, 3))
     y = np.ascontiguousarray(np.asarray(y, np.float64).reshape(-1, 3))
     s = np.ascontiguousarray(np.asarray(s, np.float64).reshape(len(y), kt))
@@ -52,8 +56,7 @@ def ewald_sum(kernel: str, x, y, s, L=1.0, xi_l=XI_L, nreal=NREAL, nfour=NFOUR):
 
 
 def ewald_matrix(kernel: str, x, y, L=1.0, xi_l=XI_L, nreal=NREAL, nfour=NFOUR):
-    kid = 0 if kernel == "laplace" else 1
-    kt = 1 if kid == 0 else 3
+    kid, kt = _KID[kernel]
     x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1, 3))
     y = np.ascontiguousarray(np.asarray(y, np.float64).reshape(-1, 3))
     out = np.zeros((kt * len(x), kt * len(y)))

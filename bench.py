@@ -515,8 +515,23 @@ def run_gpu_batched(args):
     info = plan.info()
     ph = {k: float(np.median([p[k] for p in phases])) for k in phases[0]}
     launches = plan_launches(plan)
+    # kafmm_eval of the whole batch alone: eager (host launches) and replayed from one CUDA
+    # graph; their difference bounds what host launch overhead costs the batch
+    eager = []
+    for i in range(max(3, min(5, args.steps))):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.eval(s, g)
+        e1.record(stream)
+        e1.synchronize()
+        eager.append(e0.elapsed_time(e1))
+    eval_graph = eval_graph_timing(plan, s, g, stream, flush, args.steps)
+    eval_graph["eager_ms"] = float(np.mean(eager))
+    eval_graph["launches_per_eval"] = K.kafmm_get_counters(plan.h)["launches_eval"]
     split_used = K.kafmm_get_counters(plan.h)["tc_split"]
     tiling = K.kafmm_get_counters(plan.h)["m2l_tiling"]
+    _, roof = _m2l_roofline(K, plan, info["n_v"], 6 * (p_ord - 1) ** 2 + 2, 4, ph["m2l"])
     plan.close()
 
     # the same 512 problems as sequential single-problem calls (one plan, one stream)
@@ -544,12 +559,6 @@ def run_gpu_batched(args):
     seq.close()
     seq_v = ntot / (float(np.mean(seq_ms)) * 1e-3) / 1e6
 
-    peaks, src = _peaks()
-    n = 6 * (p_ord - 1) ** 2 + 2
-    m2l_flops = info["n_v"] * 2.0 * n * n * 4
-    tf32 = split_used == "tf32x3"
-    peak = peaks["bf16_tflops"] * (1.1 / 2.25) if tf32 else peaks["bf16_tflops"]
-    achieved = m2l_flops / (ph["m2l"] * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -563,9 +572,8 @@ def run_gpu_batched(args):
         "st_gflops": info["near_pairs"] * FLOP_ST_PAIR / (ph["leaves"] * 1e-3) / 1e9,
         "phases_ms": ph,
         "tree": info,
-        "roofline": {"bound": "tensor", "kernel": "m2l", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "peak_source": f"{split_used} dense burst, {src}; useful flops"},
+        "roofline": roof,
+        "eval_only": eval_graph,
         "sequential": {"value": seq_v, "unit": "Mpoints/s", "ms_per_step": float(np.mean(seq_ms)),
                        "gpu_launches_per_step": seq_launches,
                        "what": "the same problems, one kafmm_set_points + kafmm_eval each"},
@@ -607,16 +615,28 @@ def _timed_steps(step, plan, args, world, dev, stream, flush, local):
     return ms, ph, clk
 
 
-def _m2l_roofline(K, plan, flops, m2l_ms):
+def _m2l_roofline(K, plan, n_v, dense_rows, cols, m2l_ms):
+    """M->L roofline of a tensor-core plan: useful flops = V translations x 2 x rows x k x
+    columns, rows x k = r_dn x r_up in compressed coordinates, dense_rows^2 on check potentials;
+    peak: the measured BF16 burst, or the TF32 MMA rate kafmm_measure_peak measured."""
     peaks, src = _peaks()
-    split_used = K.kafmm_get_counters(plan.h)["tc_split"]
-    tiling = K.kafmm_get_counters(plan.h)["m2l_tiling"]
-    tf32 = split_used == "tf32x3"
-    peak = peaks["bf16_tflops"] * (1.1 / 2.25) if tf32 else peaks["bf16_tflops"]
+    cnt = K.kafmm_get_counters(plan.h)
+    split_used, tiling = cnt["tc_split"], cnt["m2l_tiling"]
+    if cnt["compressed_rows"]:
+        flops = n_v * 2.0 * cnt["rank_dn"] * cnt["rank_up"] * cols
+        coords = f"compressed coordinates {cnt['rank_dn']} x {cnt['rank_up']} (padded {cnt['compressed_rows']})"
+    else:
+        flops = n_v * 2.0 * dense_rows * dense_rows * cols
+        coords = f"check potentials {dense_rows} x {dense_rows}"
+    if split_used == "tf32x3":
+        peak, pk = measured_peaks()["tf32_mma_tflops"], "tf32 tcgen05 MMA rate measured by kafmm_measure_peak"
+    else:
+        peak, pk = peaks["bf16_tflops"], f"bf16 dense burst (cuBLAS), {src}"
     achieved = flops / (m2l_ms * 1e-3) / 1e12
     return split_used, {"bound": "tensor", "kernel": "m2l", "achieved": achieved, "peak": peak,
                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                        "peak_source": f"{split_used} dense burst, {src}; useful flops",
+                        "peak_source": f"{split_used}: {pk}; useful flops ({coords}; split products not "
+                                       "counted, max frac 1/3)",
                         "m2l_tiling": tiling}
 
 
@@ -670,7 +690,7 @@ def run_gpu_periodic(args):
     ms, ph, clk = _timed_steps(step, plan, args, world, dev, stream, flush, local)
     info = plan.info()
     n = 6 * (p_ord - 1) ** 2 + 2
-    split_used, roof = _m2l_roofline(K, plan, info["n_v"] * 2.0 * (3 * n) ** 2, ph["m2l"])
+    split_used, roof = _m2l_roofline(K, plan, info["n_v"], 3 * n, 1, ph["m2l"])
     launches = plan_launches(plan)
     line = {
         "metric": METRIC, "value": world * n_pts / (ms * 1e-3) / 1e6, "unit": "Mpoints/s",
@@ -738,7 +758,7 @@ def run_gpu_rpy(args):
     ms, ph, clk = _timed_steps(step, plan, args, world, dev, stream, flush, local)
     info = plan.info()
     n = 6 * (p_ord - 1) ** 2 + 2
-    split_used, roof = _m2l_roofline(K, plan, info["n_v"] * 2.0 * n * n * 4, ph["m2l"])
+    split_used, roof = _m2l_roofline(K, plan, info["n_v"], n, 4, ph["m2l"])
     launches = plan_launches(plan)
     line = {
         "metric": METRIC, "value": world * n_pts / (ms * 1e-3) / 1e6, "unit": "Mpoints/s",

@@ -48,8 +48,7 @@ typedef struct kafmm_plan_s* kafmm_plan_t;
  *                    stkslvel: the fluid source q carries the net flow -1/2 tr D) between and
  *                    from the equivalent surfaces (4 values per surface point).  Check values
  *                    are kept as [h p, u] per box of half-width h, so the translations stay
- *                    level-independent.  Open boundary only (KAFMM_ERR_ARG with
- *                    KAFMM_BC_PXYZ).
+ *                    level-independent.  Open or triply periodic (periodic: sum of tr D = 0).
  *   KAFMM_STOKES_REG [f, eps] -> u,          regularized Stokeslet               k_s=4, k_t=3
  *                    (Sec. II.B, Table tab:ktab_reg): the flow of f spread by the blob
  *                    15 eps^4 / (8 pi (r^2 + eps^2)^{7/2}),
@@ -69,12 +68,12 @@ typedef struct kafmm_plan_s* kafmm_plan_t;
  *                    (Sec. II.C, Eqs. stkslp, stkslvel): force f and fluid source q (twice
  *                    the fluid removed) to pressure and velocity,
  *                    p = r.f/(4 pi r^3), u = G f - r q/(8 pi r^3); G^P for all interactions,
- *                    check values kept as [h p, u] as for KAFMM_STOKES_DL.  Open boundary
- *                    only.
+ *                    check values kept as [h p, u] as for KAFMM_STOKES_DL.  Open or
+ *                    triply periodic (periodic: sum of f = 0 and sum of q = 0).
  *   Derivative target values (PVelGrad, PVelLaplacian and Traction of Table tab:implement;
  *   the T column of Tables tab:ktab_stkslpvelgrad and tab:ktab_stkdlpvelgrad), from [f, q]
  *   sources (KAFMM_STOKES_PVEL_*, k_s=4) or double-layer D sources (KAFMM_STOKES_DL_*, k_s=9),
- *   on the same StokesPVel ML table, open boundary only:
+ *   on the same StokesPVel ML table, open or triply periodic:
  *     *_GRAD      [p, u, d p / d x_1..3, d u_i / d x_j at 7 + 3 i + j]                 k_t=16
  *     *_LAPL      [p, u, lap u]; lap u is evaluated as grad p (the Stokes equation off the
  *                 sources, mu = 1)                                                       k_t=7
@@ -99,8 +98,12 @@ typedef enum {
 /* Boundary conditions (Sec. III.B).  KAFMM_BC_PXYZ: triply periodic in the cube
  * [origin, origin + L)^3; the far images enter through a precomputed operator on the
  * root's multipole density (Sec. III, App. B).  Periodic sums need a zero net source
- * (sum of f = 0 for the Stokeslet, sum of q = 0 for Laplace); the k = 0 Fourier mode is
- * dropped (zero-mean field).  PX and PXY are not provided.
+ * (sum of f = 0 for the Stokeslet, sum of q = 0 for Laplace, both for StokesPVel, sum of
+ * tr D = 0 for the double layer); the k = 0 Fourier mode is dropped (zero-mean field).  The
+ * StokesPVel table adds the constant pressure and velocity shifts of the source moments its
+ * equivalent densities do not carry (the trace of the force dipole, and the split of the
+ * potential-dipole field between source dipoles and force quadrupoles).  PX and PXY are not
+ * provided.
  * KAFMM_BC_WALL (KAFMM_STOKESLET only): a no-slip wall on the plane z = origin_z + L / 2,
  * open elsewhere (Sec. III.C).  Every source and target must lie above it (z in
  * [origin_z + L/2, origin_z + L)), else KAFMM_ERR_DOMAIN; their mirror images fill the lower

@@ -156,9 +156,7 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
     return KAFMM_ERR_ARG;
   }
   *out = nullptr;
-  if ((int)kernel < 0 || (int)kernel > 12 ||
-      ((kernel == KAFMM_LAPLACE_QD || kernel >= KAFMM_STOKES_PVEL || kernel == KAFMM_STOKES_DL) &&
-       bc == KAFMM_BC_PXYZ) ||
+  if ((int)kernel < 0 || (int)kernel > 12 || (kernel == KAFMM_LAPLACE_QD && bc == KAFMM_BC_PXYZ) ||
       (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ && bc != KAFMM_BC_WALL) ||
       (bc == KAFMM_BC_WALL && kernel != KAFMM_STOKESLET) || p < 2 || p > 16 || q < 1 || q > 4096) {
     g_err = "kafmm_plan: invalid kernel, boundary condition, order (2..16) or leaf size (1..4096)";

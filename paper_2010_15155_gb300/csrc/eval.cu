@@ -1019,6 +1019,125 @@ __global__ void k_laplace_periodic_constant(const typename V4<T>::type* __restri
   for (int64_t i = threadIdx.x; i < nt; i += blockDim.x) g[i] += (T)cval;
 }
 
+// Periodic StokesPVel table ([f, q] and double-layer sources): two source moments are not
+// fixed by the far field the root's equivalent density reproduces, and each shifts the zero-mean
+// periodic result by a constant (the periodic grad G_per = grad(harmonic) + r / (3 V)):
+//   p += (tr M_src - tr M_eq) / (3 V),   tr M = sum f.(y - c) (an isotropic force dipole has no
+//                                         free-space field);
+//   u += -(d_src - d_eq) / (6 V) + (a_src - a_eq) / (3 V),  d = sum q (y - c) and the
+//        potential-dipole content of the force quadrupole a = (2 v - w) / 5, v = sum f |y - c|^2,
+//        w = sum (f.(y - c)) (y - c): d + a is fixed by the far field, the two pieces extend
+//        periodically with different constants.
+// A double-layer source D is a force dipole -sym(D) plus a source q = tr D at its point.
+// Partial moments per block, [blocks][10] = tr M, d (3), v (3), w (3), in double.
+template <class T, int PR>
+__global__ void k_pvel_moments(const typename V4<T>::type* __restrict__ spos,
+                               const typename V4<T>::type* __restrict__ sval, int64_t ns, Geo geo,
+                               double* __restrict__ part) {
+  constexpr int NV = ProbInfo<PR>::NV;
+  __shared__ double red[10][32];
+  const double c[3] = {geo.org[0] + 0.5 * geo.L, geo.org[1] + 0.5 * geo.L, geo.org[2] + 0.5 * geo.L};
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ns; j += (int64_t)gridDim.x * blockDim.x) {
+    const double y[3] = {(double)spos[j].x - c[0], (double)spos[j].y - c[1], (double)spos[j].z - c[2]};
+    const double yy = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+    if constexpr (dl_src(PR)) {
+      const auto v0 = sval[j * NV], v1 = sval[j * NV + 1], v2 = sval[j * NV + 2];
+      const double Dm[9] = {(double)v0.x, (double)v0.y, (double)v0.z, (double)v0.w, (double)v1.x,
+                            (double)v1.y, (double)v1.z, (double)v1.w, (double)v2.x};
+      double S[9], Sy[3];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) S[3 * a + b] = 0.5 * (Dm[3 * a + b] + Dm[3 * b + a]);
+      const double tr = S[0] + S[4] + S[8];
+      for (int a = 0; a < 3; ++a) Sy[a] = S[3 * a] * y[0] + S[3 * a + 1] * y[1] + S[3 * a + 2] * y[2];
+      acc[0] -= tr;
+      for (int a = 0; a < 3; ++a) {
+        acc[1 + a] += tr * y[a];
+        acc[4 + a] -= 2.0 * Sy[a];
+        acc[7 + a] -= tr * y[a] + Sy[a];
+      }
+    } else {
+      const auto v = sval[j * NV];
+      const double f[3] = {(double)v.x, (double)v.y, (double)v.z}, q = (double)v.w;
+      const double fy = f[0] * y[0] + f[1] * y[1] + f[2] * y[2];
+      acc[0] += fy;
+      for (int a = 0; a < 3; ++a) {
+        acc[1 + a] += q * y[a];
+        acc[4 + a] += f[a] * yy;
+        acc[7 + a] += fy * y[a];
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = 0; k < 10; ++k) {
+    double x = acc[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[k][w] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 10) {
+    double t = 0;
+    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[threadIdx.x][ww];
+    part[blockIdx.x * 10 + threadIdx.x] = t;
+  }
+}
+
+// One block: the partials in block order, minus the root's equivalent density's moments (real
+// [f, q] per upward equivalent point, box 0), into the shifts sh = [dp, du (3)].
+template <class T>
+__global__ void k_pvel_shift(const double* __restrict__ part, int nblk, const T* __restrict__ up_equiv,
+                             const T* __restrict__ unit, int n, Geo geo, double* __restrict__ sh) {
+  __shared__ double red[10][32];
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const double r0 = 0.5 * geo.L;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double y[3];
+    for (int d = 0; d < 3; ++d) y[d] = ALPHA_UE * r0 * (double)unit[3 * k + d];
+    const double yy = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+    const double f[3] = {(double)up_equiv[4 * k], (double)up_equiv[4 * k + 1], (double)up_equiv[4 * k + 2]};
+    const double q = (double)up_equiv[4 * k + 3];
+    const double fy = f[0] * y[0] + f[1] * y[1] + f[2] * y[2];
+    acc[0] -= fy;
+    for (int a = 0; a < 3; ++a) {
+      acc[1 + a] -= q * y[a];
+      acc[4 + a] -= f[a] * yy;
+      acc[7 + a] -= fy * y[a];
+    }
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = 0; k < 10; ++k) {
+    double x = acc[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[k][w] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m[10];
+    for (int k = 0; k < 10; ++k) {
+      double t = 0;
+      for (int b = 0; b < nblk; ++b) t += part[b * 10 + k];
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[k][ww];
+      m[k] = t;
+    }
+    const double V = geo.L * geo.L * geo.L;
+    sh[0] = m[0] / (3.0 * V);
+    for (int a = 0; a < 3; ++a) sh[1 + a] = -m[1 + a] / (6.0 * V) + (2.0 * m[4 + a] - m[7 + a]) / (15.0 * V);
+  }
+}
+
+// Adds the shifts to [p, u] (the first four target values) of every sorted target.
+template <class T, int KT>
+__global__ void k_pvel_shift_apply(const double* __restrict__ sh, T* __restrict__ g, int64_t nt) {
+  const T d0 = (T)sh[0], d1 = (T)sh[1], d2 = (T)sh[2], d3 = (T)sh[3];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
+    T* o = g + i * KT;
+    o[0] += d0;
+    o[1] += d1;
+    o[2] += d2;
+    o[3] += d3;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Host side.
 #define CK(call)                                           \
@@ -1214,8 +1333,9 @@ int worklists_finish(Plan& P) {
   // pseudo-inverses: up for boxes in W lists (and the root for the periodic Laplace
   // constant), down for leaves with targets
   bool per = P.bc == KAFMM_BC_PXYZ;
+  // (the periodic Laplace constant and the periodic StokesPVel shifts read the root's density)
   for (int b = 0; b < nb; ++b)
-    if (wflag[b] || (b == 0 && per && P.kernel == KAFMM_LAPLACE)) by_cls[0].push_back(b);
+    if (wflag[b] || (b == 0 && per && (P.kernel == KAFMM_LAPLACE || P.ml_stokes == 2))) by_cls[0].push_back(b);
   add_tiles(W, by_cls, NB, W.pup);
   if (per) by_cls[0].push_back(0);
   add_tiles(W, by_cls, NB, W.root);
@@ -1514,6 +1634,17 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
   if (PR == P_LAP && P.bc == KAFMM_BC_PXYZ && !P.near_only && nt > 0) {
     KL k_laplace_periodic_constant<T><<<1, 1024, 0, st>>>(spos, P.s_sorted.as<T4>(), ns, P.up_equiv.as<T>(), unit,
                                                        P.n, geo, P.g_sorted.as<T>(), nt);
+  }
+  if constexpr (pvel_table(PR)) {
+    if (P.bc == KAFMM_BC_PXYZ && !P.near_only && nt > 0) {
+      const int nblk = grid_for(ns, 256, 152 * 4);
+      CK(P.pvel_shift.reserve(sizeof(double) * (10 * (size_t)nblk + 8)));
+      double* part = P.pvel_shift.as<double>();
+      double* sh = part + 10 * nblk;
+      KL k_pvel_moments<T, PR><<<nblk, 256, 0, st>>>(spos, P.s_sorted.as<T4>(), ns, geo, part);
+      KL k_pvel_shift<T><<<1, 256, 0, st>>>(part, ns > 0 ? nblk : 0, P.up_equiv.as<T>(), unit, P.n, geo, sh);
+      KL k_pvel_shift_apply<T, KT><<<grid_for(nt, 256), 256, 0, st>>>(sh, P.g_sorted.as<T>(), nt);
+    }
   }
   // back to the caller's order and dtype
   if (nt > 0) {

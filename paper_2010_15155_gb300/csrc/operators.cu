@@ -297,11 +297,15 @@ __global__ void k_scale_rows(const double* in, const double* w, int n, double* o
 // weight (1 + k^2/4xi^2) e^{-k^2/4xi^2}).  xi = 2 (xi * period = 4), real images |n| <= 2,
 // Fourier modes |m| <= 8 (converged to FP64 rounding).  Where dc_i and ue_j coincide, the n = 0
 // real-space term is replaced by its regular limit and the n = 0 near image is left out.
+// StokesPVel (stokes = 2, 4 x 4 blocks [p, u] <- [f, q]): u <- f is Hasimoto's Stokeslet; the
+// pressure of a force and the flow of a source are gradients of the Laplace function,
+// p = -f . grad G and u = (q / 2) grad G, taken periodically from grad G_per (real-space terms
+// differentiated, Fourier terms -k e^{-k^2/4xi^2} sin(k.r) / (k^2 V)); p <- q is zero.
 __global__ void k_periodic_operator(const double* __restrict__ unit, int n, int stokes, double adc,
                                     double aue, double* __restrict__ T) {
   const double Lp = 2.0, xi = 2.0, V = Lp * Lp * Lp;
   const double sp = 2.0 * xi / sqrt(PI);
-  int R = stokes ? 3 * n : n;
+  int R = stokes == 2 ? 4 * n : (stokes ? 3 * n : n);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
        e += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(e / n), j = (int)(e % n);
@@ -309,6 +313,7 @@ __global__ void k_periodic_operator(const double* __restrict__ unit, int n, int 
     double r[3];
     for (int q = 0; q < 3; ++q) r[q] = __dmul_rn(adc, unit[3 * i + q]) - __dmul_rn(aue, unit[3 * j + q]);
     double m[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double gl[3] = {0, 0, 0};   // grad G_per (StokesPVel)
     double lap = stokes ? 0.0 : -1.0 / (4.0 * xi * xi * V);
     for (int a = -2; a <= 2; ++a)
       for (int b = -2; b <= 2; ++b)
@@ -329,6 +334,10 @@ __global__ void k_periodic_operator(const double* __restrict__ unit, int n, int 
             double A = (h / rn - sp * ex) / (8.0 * PI), B = (h / rn + sp * ex) / (8.0 * PI) / rr;
             for (int p = 0; p < 3; ++p)
               for (int q = 0; q < 3; ++q) m[3 * p + q] += (p == q ? A : 0.0) + B * d[p] * d[q];
+            if (stokes == 2) {   // d/dr (h(r) / r) = -sp e^{-xi^2 r^2} / r - h / r^2
+              double gr = -(sp * ex * rn + h) / (4.0 * PI * rr * rn);
+              for (int q = 0; q < 3; ++q) gl[q] += gr * d[q];
+            }
           }
         }
     for (int a = -8; a <= 8; ++a)
@@ -342,6 +351,10 @@ __global__ void k_periodic_operator(const double* __restrict__ unit, int n, int 
           if (!stokes) {
             lap += g;
           } else {
+            if (stokes == 2) {
+              double sn = -exp(-k2 / (4.0 * xi * xi)) / (k2 * V) * sin(kv[0] * r[0] + kv[1] * r[1] + kv[2] * r[2]);
+              for (int q = 0; q < 3; ++q) gl[q] += sn * kv[q];
+            }
             g *= 1.0 + k2 / (4.0 * xi * xi);
             for (int p = 0; p < 3; ++p)
               for (int q = 0; q < 3; ++q) m[3 * p + q] += g * ((p == q ? 1.0 : 0.0) - kv[p] * kv[q] / k2);
@@ -349,6 +362,13 @@ __global__ void k_periodic_operator(const double* __restrict__ unit, int n, int 
         }
     if (!stokes) {
       T[(int64_t)i * R + j] = lap;
+    } else if (stokes == 2) {
+      for (int q = 0; q < 3; ++q) T[(int64_t)(4 * i) * R + 4 * j + q] = -gl[q];
+      T[(int64_t)(4 * i) * R + 4 * j + 3] = 0.0;
+      for (int p = 0; p < 3; ++p) {
+        for (int q = 0; q < 3; ++q) T[(int64_t)(4 * i + 1 + p) * R + 4 * j + q] = m[3 * p + q];
+        T[(int64_t)(4 * i + 1 + p) * R + 4 * j + 3] = 0.5 * gl[p];
+      }
     } else {
       for (int p = 0; p < 3; ++p)
         for (int q = 0; q < 3; ++q) T[(int64_t)(3 * i + p) * R + 3 * j + q] = m[3 * p + q];

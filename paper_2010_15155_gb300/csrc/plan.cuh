@@ -121,6 +121,7 @@ struct Plan {
   DevBuf opstc_cin;                 // [2][2][rp][Rpad] tf32: U_u^T, U_d^T (compress)
   DevBuf opstc_cout;                // [2][2][R][rp] tf32: V_u S_u^+, V_d S_d^+ (decompress)
   DevBuf up_hat, dn_hat;            // [nbox][rp][C] compressed upward / downward state
+  DevBuf pvel_shift;                // periodic StokesPVel table: moment partials and shifts
   // TMA descriptors: [operator set][128-byte, 64-byte swizzled rows]; sets: dense M->L, dense
   // aux, compressed M->L, compressed aux, compress, decompress
   alignas(64) unsigned char tmaps[6][2][128];

@@ -360,6 +360,13 @@ def _neutral(kernel, n, seed, dtype=np.float64):
     Stokeslet's blob widths eps ~ U(0, 2e-3) in the fourth column."""
     rng = np.random.default_rng(seed)
     pts = rng.random((n, 3))
+    if kernel.startswith("stokes_dl"):          # double layer: sum of tr D = 0
+        s = rng.standard_normal((n, 9))
+        s[:, [0, 4, 8]] -= (s[:, 0] + s[:, 4] + s[:, 8]).mean() / 3.0
+        return pts.astype(dtype), s.astype(dtype)
+    if kernel.startswith("stokes_pvel"):        # [f, q]: sum of f = 0 and sum of q = 0
+        s = rng.standard_normal((n, 4))
+        return pts.astype(dtype), (s - s.mean(axis=0)).astype(dtype)
     kt = 1 if kernel == "laplace" else 3
     s = rng.standard_normal((n, kt))
     s = s - s.mean(axis=0)
@@ -369,20 +376,45 @@ def _neutral(kernel, n, seed, dtype=np.float64):
 
 
 @pytest.mark.parametrize("problem,kernel", [("laplace", "laplace"), ("stokeslet_g", "stokeslet"),
-                                            ("stokeslet_reg_g", "stokeslet_reg")])
+                                            ("stokeslet_reg_g", "stokeslet_reg"), ("stokes_pvel", "stokes_pvel"),
+                                            ("stokes_dl_pv", "stokes_dl"),
+                                            ("stokes_pvel_traction", "stokes_pvel_traction"),
+                                            ("stokes_dl_grad", "stokes_dl_grad")])
 def test_periodic_fp64_gpu_kafmm_matches_cpu_kafmm(problem, kernel):
     """Triply periodic KAFMM (far images through the root operator) vs the oracle's periodic
     plain KAFMM, FP64 both: rel L2 <= 1e-7."""
     from oracle import periodic as Pd
     pts, s = _neutral(kernel, 1500, seed=21)
     p, q = 6, 32
-    ml = "laplace" if kernel == "laplace" else "stokeslet"   # the ML-tree kernel of the table
+    # the ML-tree kernel of the table
+    ml = "laplace" if kernel == "laplace" else ("stokes_pvel" if kernel.startswith(("stokes_pvel", "stokes_dl"))
+                                                else "stokeslet")
     ref = KAFMM(problem, p, q, bc="pxyz", t_m2l=Pd.t_m2l(ml, p)).evaluate(pts, s)
     plan = K.Plan(KERN[kernel], p=p, q=q, bc=K.BC_PXYZ, precision=K.PREC_FP64, variant=K.ML_G)
     plan.set_points(torch.from_numpy(pts).cuda())
     g = plan.eval(torch.from_numpy(s).cuda()).cpu().numpy()
     plan.close()
     assert D.rel_l2(g, ref) < 1e-7
+
+
+@pytest.mark.parametrize("kernel", ["stokes_pvel", "stokes_dl"])
+def test_periodic_pvel_table_mixed_form(kernel):
+    """Triply periodic StokesPVel and double layer in the mixed form (tensor-core M->L on the
+    4-row table, FP32 near field) against the FP64 form (pinned above to the oracle's periodic
+    KAFMM, and through it to the Ewald sum): rel L2 <= 1e-5 at p = 10."""
+    pts, s = _neutral(kernel, 30000, seed=23, dtype=np.float32)
+    out = {}
+    for prec in (K.PREC_FP64, K.PREC_MIXED):
+        dt = torch.float64 if prec == K.PREC_FP64 else torch.float32
+        plan = K.Plan(KERN[kernel], p=10, q=64, bc=K.BC_PXYZ, precision=prec)
+        plan.set_points(torch.from_numpy(pts).to(dt).cuda())
+        out[prec] = plan.eval(torch.from_numpy(s).to(dt).cuda()).double().cpu().numpy()
+        if prec == K.PREC_MIXED:
+            assert K.kafmm_get_counters(plan.h)["tensor_core_m2l"] == 1
+        plan.close()
+    err = D.rel_l2(out[K.PREC_MIXED], out[K.PREC_FP64])
+    print(kernel, err)
+    assert err < 1e-5
 
 
 def test_periodic_fp32_gpu_kafmm_against_ewald_and_translation():

@@ -132,6 +132,57 @@ void orc_laplace_qd(const double* x, int64_t nt, const double* y, int64_t ns,
   }
 }
 
+/* Laplace quadrupoles to potential, gradient and Hessian (LapQPGradGrad of Table
+ * tab:implement; the phi^Q sum of Table tab:rpywall): phi = Q_jk d_j d_k L, L = 1/(4 pi r),
+ * derivatives in x, r = x - y.  With the derivatives of 1/r
+ *   D2_jk   = (3 r_j r_k - delta_jk r^2) / r^5,
+ *   D3_ijk  = -15 r_i r_j r_k / r^7 + 3 (delta_ij r_k + delta_ik r_j + delta_jk r_i) / r^5,
+ *   D4_ijkl = 105 r_i r_j r_k r_l / r^9 - 15 (delta_ij r_k r_l + delta_ik r_j r_l + delta_il r_j r_k
+ *             + delta_jk r_i r_l + delta_jl r_i r_k + delta_kl r_i r_j) / r^7
+ *             + 3 (delta_ij delta_kl + delta_ik delta_jl + delta_il delta_jk) / r^5,
+ * 4 pi phi = Q_jk D2_jk, 4 pi d_i phi = Q_jk D3_ijk, 4 pi d_i d_l phi = Q_jk D4_iljk.
+ * s: Q row-major (Q_jk at 3j+k, 9), g: [phi, grad (3), Hessian xx xy xz yy yz zz (6)] (10). */
+void orc_laplace_quad(const double* x, int64_t nt, const double* y, int64_t ns,
+                      const double* s, double* g) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t a = 0; a < nt; ++a) {
+    double acc[10] = {0};
+    for (int64_t b = 0; b < ns; ++b) {
+      double r[3] = {x[3 * a] - y[3 * b], x[3 * a + 1] - y[3 * b + 1],
+                     x[3 * a + 2] - y[3 * b + 2]};
+      double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (rr == 0.0) continue;
+      const double* Q = s + 9 * b;
+      double rn = sqrt(rr), r5 = rr * rr * rn, r7 = r5 * rr, r9 = r7 * rr;
+      double phi = 0.0, gr[3] = {0, 0, 0}, H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) {
+          double q = Q[3 * j + k];
+          if (q == 0.0) continue;
+          double djk = j == k ? 1.0 : 0.0;
+          phi += q * (3.0 * r[j] * r[k] - djk * rr) / r5;
+          for (int i = 0; i < 3; ++i) {
+            double dij = i == j ? 1.0 : 0.0, dik = i == k ? 1.0 : 0.0;
+            gr[i] += q * (-15.0 * r[i] * r[j] * r[k] / r7 + 3.0 * (dij * r[k] + dik * r[j] + djk * r[i]) / r5);
+            for (int l = 0; l < 3; ++l) {
+              double dil = i == l ? 1.0 : 0.0, djl = j == l ? 1.0 : 0.0, dkl = k == l ? 1.0 : 0.0;
+              H[i][l] += q * (105.0 * r[i] * r[j] * r[k] * r[l] / r9 -
+                              15.0 * (dij * r[k] * r[l] + dik * r[j] * r[l] + dil * r[j] * r[k] +
+                                      djk * r[i] * r[l] + djl * r[i] * r[k] + dkl * r[i] * r[j]) / r7 +
+                              3.0 * (dij * dkl + dik * djl + dil * djk) / r5);
+            }
+          }
+        }
+      acc[0] += phi / (4.0 * PI);
+      for (int i = 0; i < 3; ++i) acc[1 + i] += gr[i] / (4.0 * PI);
+      int c = 4;
+      for (int i = 0; i < 3; ++i)
+        for (int l = i; l < 3; ++l) acc[c++] += H[i][l] / (4.0 * PI);
+    }
+    for (int k = 0; k < 10; ++k) g[10 * a + k] += acc[k];
+  }
+}
+
 /* Stokeslet, Sec. II.B: G_ij = (delta_ij / r + r_i r_j / r^3) / (8 pi).  s: f (3), g: u (3). */
 void orc_stokeslet(const double* x, int64_t nt, const double* y, int64_t ns,
                    const double* s, double* g) {

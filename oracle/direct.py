@@ -9,6 +9,7 @@ Kernels (dimensions k_s x k_t, Table tab:implement):
   laplace_pgradgrad  q -> phi, grad, grad grad    1 x 10  (Table tab:ktab_lapqdpgradgrad)
   laplace_dipole     d -> phi                     3 x 1   (Sec. II.A)
   laplace_qd         [q, d] -> phi, grad, grad grad  4 x 10  (Table tab:ktab_lapqdpgradgrad)
+  laplace_quad       Q -> phi, grad, grad grad    9 x 10  (LapQPGradGrad, Table tab:implement)
   stokeslet          f -> u                       3 x 3   (Sec. II.B)
   stokeslet_reg      [f, eps] -> u                4 x 3   (regularized Stokeslet, Table tab:ktab_reg)
   stokes_pvel        [f, q] -> [p, u]             4 x 4   (StokesPVel, Eqs. stkslp, stkslvel)
@@ -37,6 +38,7 @@ KDIM = {  # kernel -> (k_s, k_t)
     "laplace_pgradgrad": (1, 10),
     "laplace_dipole": (3, 1),
     "laplace_qd": (4, 10),
+    "laplace_quad": (9, 10),
     "stokeslet": (3, 3),
     "stokeslet_reg": (4, 3),
     "stokes_pvel": (4, 4),

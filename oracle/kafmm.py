@@ -75,6 +75,10 @@ PROBLEMS = {
     # charges and dipoles to potential, gradient and Hessian, Table tab:ktab_lapqdpgradgrad:
     # L and L^D from S, charges on M and L, L + grad L + grad grad L to T
     "laplace_qd": (4, 10, "laplace", 1),
+    # quadrupoles to potential, gradient and Hessian (LapQPGradGrad, Table tab:implement; the
+    # phi^Q sum of Table tab:rpywall): the quadrupole potential from S, charges on M and L,
+    # L + grad L + grad grad L to T
+    "laplace_quad": (9, 10, "laplace", 1),
     # Stokes double layer D -> [p, u], Table tab:ktab_stkdlpvelgrad: K from S, the StokesPVel
     # kernel G^P ([f, q] -> [p, u]) between and from the equivalent surfaces
     "stokes_dl_pv": (9, 4, "stokes_pvel", 1),
@@ -201,6 +205,8 @@ class KAFMM:
             return D.direct("laplace", chk, y, s)
         if pr == "laplace_qd":
             return D.direct("laplace", chk, y, s[:, :1]) + D.direct("laplace_dipole", chk, y, s[:, 1:])
+        if pr == "laplace_quad":
+            return D.direct("laplace_quad", chk, y, s)[:, :1]
         if pr in ("stokeslet_g", "rpy_g", "stokeslet_reg_g"):
             kern = {"stokeslet_g": "stokeslet", "rpy_g": "rpy", "stokeslet_reg_g": "stokeslet_reg"}[pr]
             g = D.direct(kern, chk, y, s)
@@ -223,7 +229,7 @@ class KAFMM:
         pr = self.problem
         if pr == "laplace":
             return D.direct("laplace", x, eq, dens[:, 0])
-        if pr == "laplace_qd":
+        if pr in ("laplace_qd", "laplace_quad"):
             return D.direct("laplace_pgradgrad", x, eq, dens[:, 0])
         if pr in ("stokes_dl_pv", "stokes_pvel"):
             return D.direct("stokes_pvel", x, eq, dens.reshape(-1, 4))
@@ -249,7 +255,7 @@ class KAFMM:
         return np.concatenate([u, lap], axis=1)
 
     def _src_to_targets(self, x, y, s) -> np.ndarray:
-        if self.problem in _DERIV:
+        if self.problem in _DERIV or self.problem == "laplace_quad":
             return D.direct(self.problem, x, y, s)
         kern = {"laplace": "laplace", "stokeslet_g": "stokeslet", "stokeslet_l4": "stokeslet",
                 "rpy_g": "rpy", "rpy_l4": "rpy", "stokeslet_reg_g": "stokeslet_reg",

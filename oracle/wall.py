@@ -18,6 +18,21 @@ h = y_3 above the wall):
     u^S:    f_12 = (f_1, f_2, 0) at y,  -f_12 at y^I                       (Stokeslet)
     SD:     charge -f_3 / 2 at y;  charge f_3 / 2 and dipole h (-f_1, -f_2, f_3) at y^I
     SDZ:    charge h f_3 / 2 at y;  charge -h f_3 / 2 at y^I
+
+RPY kernel above the wall (Table tab:rpywall with radius b > 0).  The plain definition is the
+RPY kernel sum's source operator applied to Blake's solution, u = (1 + b^2/6 lap_y) G_wall f
+(``blake_rpy``: the y-Laplacian by a Richardson-extrapolated central difference, error
+O(h^4)).  The table's four sums, assembled as
+    u     = u^S + grad phi^SDZ + x_3 grad phi^SD + x_3 grad phi^Q - [0, 0, phi^SD + phi^Q],
+    lap u = lap u^S + 2 d_3 grad (phi^SD + phi^Q),
+with, besides the Stokeslet reading above:
+    u^S:    RPY sum of (f_12, b) at y and (-f_12, b) at y^I     ([u, lap u] per target)
+    SDZ:    adds the dipole (b^2/6) (0, 0, f_3) at y and at y^I
+    Q:      the quadrupole (b^2/3) [[f_3, 0, 0], [0, f_3, 0], [f_1, f_2, 0]] (phi = Q_jk d_j d_k L)
+Reading: the table prints the quadrupole under "source at y" with 0 at y^I; placed at y^I it
+makes the assembly equal (1 + b^2/6 lap_y) of Blake's solution (a least-squares fit of the
+candidate b^2 terms to that definition gives coefficient 1/3 at y^I and 0 at y), and is used
+everywhere.
 """
 from __future__ import annotations
 
@@ -95,3 +110,82 @@ def table(x, y, f, zw=0.0):
     sd_out = D.direct("laplace_qd", x, yy, sd)
     sdz_out = D.direct("laplace_qd", x, yy, sdz)
     return assemble(x, uS, sd_out, sdz_out, zw)
+
+
+def blake_rpy(x, y, fb, zw=0.0, h=2e-4):
+    """u = sum_b (1 + b_b^2 / 6 lap_y) G_wall(x, y_b) f_b (RPY kernel sum above the wall), FP64;
+    fb = [f, b] per source.  lap_y by the 7-point stencil at h and h / 2, Richardson-extrapolated.
+    A target on a source gets only that source's image field (the free-space self pair is left
+    out, as in every kernel sum here).  Sources must lie more than h above the wall."""
+    x = np.asarray(x, np.float64).reshape(-1, 3)
+    y = np.asarray(y, np.float64).reshape(-1, 3)
+    fb = np.asarray(fb, np.float64).reshape(-1, 4)
+    u = blake(x, y, fb[:, :3], zw)
+    for j in range(len(y)):
+        b = fb[j, 3]
+        if b == 0.0:
+            continue
+        f = fb[j:j + 1, :3]
+        on = np.all(x == y[j], axis=1)          # targets on this source: image part only
+
+        def g(yj):
+            v = blake(x, yj, f, zw)
+            if on.any():
+                v[on] -= D.direct("stokeslet", x[on], yj, f)
+            return v
+        c = g(y[j:j + 1])
+        lap = []
+        for hh in (h, 0.5 * h):
+            acc = -6.0 * c
+            for k in range(3):
+                e = np.zeros(3)
+                e[k] = hh
+                acc = acc + g(y[j:j + 1] + e) + g(y[j:j + 1] - e)
+            lap.append(acc / (hh * hh))
+        u += b * b / 6.0 * (4.0 * lap[1] - lap[0]) / 3.0
+    return u
+
+
+def rpy_table_sources(y, fb, zw=0.0):
+    """Sources of the four sums over [y; y^I] (module docstring): RPY [2n, 4] (f_12, b), SD and
+    SDZ charges + dipoles [2n, 4], quadrupoles [2n, 9] (Q_jk at 3j + k)."""
+    y = np.asarray(y, np.float64).reshape(-1, 3)
+    fb = np.asarray(fb, np.float64).reshape(-1, 4)
+    f, b = fb[:, :3], fb[:, 3]
+    n = len(y)
+    _, sd, sdz = table_sources(y, f, zw)
+    rpy = np.zeros((2 * n, 4))
+    rpy[:n, :2] = f[:, :2]
+    rpy[n:, :2] = -f[:, :2]
+    rpy[:n, 3] = b
+    rpy[n:, 3] = b
+    bb = b * b
+    sdz[:n, 3] += bb / 6.0 * f[:, 2]
+    sdz[n:, 3] += bb / 6.0 * f[:, 2]
+    quad = np.zeros((2 * n, 9))
+    quad[n:, 0] = bb / 3.0 * f[:, 2]
+    quad[n:, 4] = bb / 3.0 * f[:, 2]
+    quad[n:, 6] = bb / 3.0 * f[:, 0]
+    quad[n:, 7] = bb / 3.0 * f[:, 1]
+    return rpy, sd, sdz, quad
+
+
+def rpy_assemble(x, rpy_out, sd_out, sdz_out, q_out, zw=0.0):
+    """[u, lap u] from the four sums' target values: rpy_out [u, lap u] (6), the Laplace sums
+    [phi, grad phi, Hessian xx xy xz yy yz zz] (10)."""
+    x3 = (np.asarray(x, np.float64).reshape(-1, 3)[:, 2] - zw)[:, None]
+    u = rpy_out[:, :3] + sdz_out[:, 1:4] + x3 * (sd_out[:, 1:4] + q_out[:, 1:4])
+    u[:, 2] -= sd_out[:, 0] + q_out[:, 0]
+    h = sd_out + q_out
+    lap = rpy_out[:, 3:6] + 2.0 * h[:, [6, 8, 9]]   # 2 d_3 grad(phi^SD + phi^Q): xz, yz, zz
+    return np.concatenate([u, lap], axis=1)
+
+
+def rpy_table(x, y, fb, zw=0.0):
+    """The paper's four sums as direct FP64 sums over the sources and their images."""
+    x = np.asarray(x, np.float64).reshape(-1, 3)
+    y = np.asarray(y, np.float64).reshape(-1, 3)
+    yy = np.concatenate([y, images(y, zw)])
+    rpy, sd, sdz, quad = rpy_table_sources(y, fb, zw)
+    return rpy_assemble(x, D.direct("rpy", x, yy, rpy), D.direct("laplace_qd", x, yy, sd),
+                        D.direct("laplace_qd", x, yy, sdz), D.direct("laplace_quad", x, yy, quad), zw)

@@ -99,7 +99,8 @@ KERNEL_OF = {"laplace": "laplace", "stokeslet_g": "stokeslet", "stokeslet_l4": "
              "laplace_qd": "laplace_qd", "stokes_dl_pv": "stokes_dl", "stokes_pvel": "stokes_pvel",
              "stokes_pvel_grad": "stokes_pvel_grad", "stokes_pvel_lapl": "stokes_pvel_lapl",
              "stokes_pvel_traction": "stokes_pvel_traction", "stokes_dl_grad": "stokes_dl_grad",
-             "stokes_dl_lapl": "stokes_dl_lapl", "stokes_dl_traction": "stokes_dl_traction"}
+             "stokes_dl_lapl": "stokes_dl_lapl", "stokes_dl_traction": "stokes_dl_traction",
+             "laplace_quad": "laplace_quad"}
 
 
 def _inputs(problem, n, seed=0):
@@ -120,6 +121,7 @@ def _inputs(problem, n, seed=0):
     ("rpy_g", 1200, 40, (4, 6), 1e-3),
     ("stokeslet_reg_g", 1200, 40, (4, 6), 1e-3),
     ("laplace_qd", 2000, 48, (4, 6, 8), 1e-5),
+    ("laplace_quad", 2000, 48, (4, 6, 8), 1e-4),
     ("stokes_dl_pv", 1200, 40, (4, 6), 1e-3),
     ("stokes_pvel", 1200, 40, (4, 6), 1e-3),
     ("stokes_pvel_grad", 1200, 40, (4, 6), 3e-3),

@@ -462,3 +462,33 @@ def test_derivative_kernels_solve_stokes(base, ks):
     assert np.allclose(tr, np.transpose(tr, (0, 2, 1)), rtol=0, atol=1e-13 * np.abs(tr).max())
     assert np.allclose(np.trace(tr, axis1=1, axis2=2), -3 * gr[:, 0], rtol=1e-11,
                        atol=1e-12 * np.abs(gr[:, 0]).max())
+
+
+def test_laplace_quadrupole_against_the_pinned_dipole_kernel():
+    """Quadrupoles Q -> [phi, grad phi, grad grad phi] (LapQPGradGrad): phi = Q_jk d_j d_k L is
+    minus the divergence of dipole potentials, phi_Q = -sum_k d_k phi_D(d = Q_{., k}), checked by
+    central differences of the pinned dipole kernel; grad phi_Q = -sum_k H_D(Q_{., k})_{ik} from
+    the pinned charge + dipole Hessian; the Hessian by central differences of the gradient, and
+    trace-free (phi_Q is harmonic off the sources)."""
+    rng = np.random.default_rng(71)
+    y = rng.random((3, 3))
+    Q = rng.standard_normal((3, 9))
+    hidx = {(0, 0): 4, (0, 1): 5, (0, 2): 6, (1, 1): 7, (1, 2): 8, (2, 2): 9}
+    for xt in (np.array([1.4, -0.3, 0.8]), np.array([0.2, 0.9, -0.6])):
+        g = D.direct("laplace_quad", xt[None], y, Q)[0]
+        phi_ref = 0.0
+        grad_ref = np.zeros(3)
+        for k in range(3):
+            dk = Q.reshape(3, 3, 3)[:, :, k]           # dipoles Q_{., k} of every source
+            fun = lambda z, dk=dk: D.direct("laplace_dipole", z[None], y, dk)[0, :1]
+            phi_ref -= fd_grad(fun, xt, h=1e-5)[0, k]
+            qd = np.concatenate([np.zeros((3, 1)), dk], axis=1)
+            Hd = D.direct("laplace_qd", xt[None], y, qd)[0]
+            for i in range(3):
+                grad_ref[i] -= Hd[hidx[(min(i, k), max(i, k))]]
+        assert np.isclose(g[0], phi_ref, rtol=1e-7, atol=1e-9)
+        assert np.allclose(g[1:4], grad_ref, rtol=1e-12, atol=1e-13 * np.abs(grad_ref).max())
+        H = fd_grad(lambda z: D.direct("laplace_quad", z[None], y, Q)[0, 1:4], xt, h=1e-5)
+        for (i, j), k in hidx.items():
+            assert np.isclose(H[i, j], g[k], rtol=1e-6, atol=1e-8 * np.abs(g[4:]).max())
+        assert abs(g[4] + g[7] + g[9]) < 1e-12 * np.abs(g[4:]).max()

@@ -78,3 +78,48 @@ def test_three_sum_assembly_equals_blake(zw):
     ref = Wl.blake(x, y, f, zw)
     got = Wl.table(x, y, f, zw)
     assert D.rel_l2(got, ref) < 1e-12
+
+
+def _rpy_above(n, rng, zw=0.0):
+    y = _above(n, rng, zw)
+    fb = np.concatenate([rng.standard_normal((n, 3)), rng.uniform(0.005, 0.03, (n, 1))], axis=1)
+    return y, fb
+
+
+@pytest.mark.parametrize("zw", [0.0, 0.5])
+def test_rpy_wall_four_sums_equal_the_definition(zw):
+    """The four-sum assembly of Table tab:rpywall (with the quadrupole at the image) equals
+    (1 + b^2/6 lap_y) of Blake's solution (the RPY kernel sum above the wall), targets off and
+    on the sources; with b = 0 it is the Stokeslet wall's three-sum assembly."""
+    rng = np.random.default_rng(5)
+    y, fb = _rpy_above(60, rng, zw)
+    x = np.concatenate([_above(80, rng, zw), y[:10]])
+    got = Wl.rpy_table(x, y, fb, zw)
+    assert D.rel_l2(got[:, :3], Wl.blake_rpy(x, y, fb, zw)) < 1e-8
+    fb0 = fb.copy()
+    fb0[:, 3] = 0.0
+    assert D.rel_l2(Wl.rpy_table(x, y, fb0, zw)[:, :3], Wl.table(x, y, fb[:, :3], zw)) < 1e-13
+
+
+def test_rpy_wall_laplacian_and_no_slip():
+    """lap u of the assembly equals a Richardson-extrapolated 7-point Laplacian of its u in x,
+    and u vanishes on the wall (the source operator acts on y, Blake's field vanishes on the
+    wall for every y)."""
+    rng = np.random.default_rng(6)
+    y, fb = _rpy_above(20, rng)
+    x = _above(10, rng) + np.array([0.0, 0.0, 0.2])
+    got = Wl.rpy_table(x, y, fb)
+    lap = []
+    for h in (2e-3, 1e-3):
+        acc = -6.0 * Wl.rpy_table(x, y, fb)[:, :3]
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = h
+            acc = acc + Wl.rpy_table(x + e, y, fb)[:, :3] + Wl.rpy_table(x - e, y, fb)[:, :3]
+        lap.append(acc / (h * h))
+    fd = (4.0 * lap[1] - lap[0]) / 3.0
+    assert D.rel_l2(got[:, 3:], fd) < 1e-6
+    xw = rng.random((30, 3)) * 3 - 1
+    xw[:, 2] = 0.0
+    uw = Wl.rpy_table(xw, y, fb)[:, :3]
+    assert np.abs(uw).max() < 1e-12 * np.abs(Wl.rpy_table(xw + [0, 0, 0.3], y, fb)[:, :3]).max()

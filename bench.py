@@ -461,7 +461,7 @@ def run_gpu_batched(args):
     s = torch.from_numpy(f).to(dev)
     g = torch.empty((ntot, 3), dtype=torch.float32, device=dev)
     plan = K.Plan(K.STOKESLET, p=p_ord, q=q_leaf, precision=K.PREC_MIXED, variant=K.ML_L4,
-                  stream=stream.cuda_stream)
+                  stream=stream.cuda_stream, tc_split={"tf32x3": K.TC_TF32X3, "bf16x3": K.TC_BF16X3, "auto": K.TC_AUTO}[args.tc_split])
     K.kafmm_set_option(plan.h, K.OPT_TC_TILING, args.tc_tiling)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -658,7 +658,7 @@ def run_gpu_periodic(args):
     s = torch.from_numpy(f).to(dev)
     g = torch.empty((n_pts, 3), dtype=torch.float32, device=dev)
     plan = K.Plan(K.STOKESLET, p=p_ord, q=q_leaf, bc=K.BC_PXYZ, precision=K.PREC_MIXED,
-                  variant=K.ML_G, stream=stream.cuda_stream)
+                  variant=K.ML_G, stream=stream.cuda_stream, tc_split={"tf32x3": K.TC_TF32X3, "bf16x3": K.TC_BF16X3, "auto": K.TC_AUTO}[args.tc_split])
     K.kafmm_set_option(plan.h, K.OPT_TC_TILING, args.tc_tiling)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     plan.set_points(y)
@@ -735,7 +735,7 @@ def run_gpu_rpy(args):
     g = torch.empty((n_pts, 6), dtype=torch.float32, device=dev)
     ua = torch.empty((n_pts, 3), dtype=torch.float32, device=dev)
     plan = K.Plan(K.RPY, p=p_ord, q=q_leaf, precision=K.PREC_MIXED, variant=K.ML_L4,
-                  stream=stream.cuda_stream)
+                  stream=stream.cuda_stream, tc_split={"tf32x3": K.TC_TF32X3, "bf16x3": K.TC_BF16X3, "auto": K.TC_AUTO}[args.tc_split])
     K.kafmm_set_option(plan.h, K.OPT_RPY_CONTACT, 1)
     K.kafmm_set_option(plan.h, K.OPT_TC_TILING, args.tc_tiling)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)

@@ -78,7 +78,12 @@ typedef struct kafmm_plan_s* kafmm_plan_t;
  *     *_LAPL      [p, u, lap u]; lap u is evaluated as grad p (the Stokes equation off the
  *                 sources, mu = 1)                                                       k_t=7
  *     *_TRACTION  sigma_ij = -p delta_ij + d u_i / d x_j + d u_j / d x_i at 3 i + j
- *                 (Eq. stressdef, mu = 1)                                                k_t=9 */
+ *                 (Eq. stressdef, mu = 1)                                                k_t=9
+ *   KAFMM_LAPLACE_QUAD Q -> [phi, grad phi, grad grad phi]                        k_s=9, k_t=10
+ *                    (LapQPGradGrad of Table tab:implement): quadrupole Q_jk at 3j+k per source,
+ *                    phi = Q_jk d_j d_k (1/(4 pi r)) (derivatives in x); outputs as for
+ *                    KAFMM_LAPLACE_QD.  The quadrupole potential from the sources, charges on
+ *                    the equivalent surfaces (Laplace table).  Open boundary only. */
 typedef enum {
   KAFMM_LAPLACE = 0,
   KAFMM_STOKESLET = 1,
@@ -92,7 +97,8 @@ typedef enum {
   KAFMM_STOKES_PVEL_TRACTION = 9,
   KAFMM_STOKES_DL_GRAD = 10,
   KAFMM_STOKES_DL_LAPL = 11,
-  KAFMM_STOKES_DL_TRACTION = 12
+  KAFMM_STOKES_DL_TRACTION = 12,
+  KAFMM_LAPLACE_QUAD = 13
 } kafmm_kernel;
 
 /* Boundary conditions (Sec. III.B).  KAFMM_BC_PXYZ: triply periodic in the cube
@@ -104,7 +110,7 @@ typedef enum {
  * equivalent densities do not carry (the trace of the force dipole, and the split of the
  * potential-dipole field between source dipoles and force quadrupoles).  PX and PXY are not
  * provided.
- * KAFMM_BC_WALL (KAFMM_STOKESLET only): a no-slip wall on the plane z = origin_z + L / 2,
+ * KAFMM_BC_WALL (KAFMM_STOKESLET and KAFMM_RPY): a no-slip wall on the plane z = origin_z + L / 2,
  * open elsewhere (Sec. III.C).  Every source and target must lie above it (z in
  * [origin_z + L/2, origin_z + L)), else KAFMM_ERR_DOMAIN; their mirror images fill the lower
  * half of the cube.  The flow is Blake's image system, evaluated as one Stokeslet and two
@@ -114,10 +120,18 @@ typedef enum {
  *   u^S: (f_1, f_2, 0) at y and its negative at the image; phi^SD: charge -f_3/2 at y, charge
  *   f_3/2 and dipole h (-f_1, -f_2, f_3) at the image; phi^SDZ: charge h f_3/2 at y, -h f_3/2
  *   at the image (h: the source's height).  A target on a source gets that source's image
- *   field, not its own.  The plan keeps two child plans (Stokeslet and Laplace charges +
- *   dipoles, open boundary, the same p, q and options); kafmm_tree_info, kafmm_phase_times
- *   and kafmm_get_counters report the Stokeslet child; batches, kafmm_autotune, the tree
- *   queries, kafmm_get_operator and the RPY calls answer KAFMM_ERR_ARG. */
+ *   field, not its own.  KAFMM_RPY ([f, b] -> [u, lap u]): the RPY kernel sum above the wall,
+ *   u = (1 + b^2/6 lap_y) G_wall f, from four sums (Table tab:rpywall): an RPY sum of (f_12, b)
+ *   at y and (-f_12, b) at the image, SD as above, SDZ plus the dipole (b^2/6)(0, 0, f_3) at y
+ *   and at the image, and Laplace quadrupoles (b^2/3)[[f_3,0,0],[0,f_3,0],[f_1,f_2,0]] at the
+ *   image (printed under "source at y"; at the image the assembly is the definition), with
+ *     u = u^S + grad phi^SDZ + x_3 grad(phi^SD + phi^Q) - [0, 0, phi^SD + phi^Q],
+ *     lap u = lap u^S + 2 d_3 grad(phi^SD + phi^Q).
+ *   The plan keeps child plans (Stokeslet or RPY, Laplace charges + dipoles, and for RPY
+ *   Laplace quadrupoles; open boundary, the same p, q and options); kafmm_tree_info,
+ *   kafmm_phase_times and kafmm_get_counters report the first child; batches,
+ *   kafmm_autotune, the tree queries, kafmm_get_operator and the RPY velocity calls answer
+ *   KAFMM_ERR_ARG. */
 typedef enum { KAFMM_BC_OPEN = 0, KAFMM_BC_PXYZ = 3, KAFMM_BC_WALL = 4 } kafmm_bc;
 
 typedef enum { KAFMM_F32 = 0, KAFMM_F64 = 1 } kafmm_dtype;
@@ -151,7 +165,10 @@ enum {
    * error of the mixed form against the FP64 form (Stokeslet, N = 262144 uniform): TF32x3
    * 4.7e-6..5.7e-6 for p = 6..10; BF16x3 4.2e-5 (p = 6), 1.1e-5 (p = 8), 6.6e-6 (p = 10),
    * 7e-6 against the direct sum at p = 12, at about 0.7x the time.  AUTO takes BF16x3 for
-   * p >= 10 and TF32x3 below. */
+   * p >= 10 and TF32x3 below on check potentials; in compressed coordinates (KAFMM_OPT_COMPRESS)
+   * BF16x3 for p >= 8 up to 512 compressed rows and TF32x3 otherwise (the orthonormal projections
+   * keep BF16 rounding out of the directions the pseudo-inverses amplify: 512 Stokeslet
+   * problems at p = 8, worst problem 6.2e-6 against the FP64 form). */
   KAFMM_OPT_TC_SPLIT = 6,
   /* 1 (default): kafmm_eval synchronises the plan's stream before it returns and reports a
    * device-side timeout as KAFMM_ERR_TIMEOUT.  0: with device arrays kafmm_eval only enqueues

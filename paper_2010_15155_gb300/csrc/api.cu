@@ -58,6 +58,10 @@ static void configure(Plan& P) {
       P.ks = 4;
       P.kt = 10;
       break;
+    case KAFMM_LAPLACE_QUAD:  // Q -> [phi, grad, grad grad] on the Laplace table
+      P.ks = 9;
+      P.kt = 10;
+      break;
     case KAFMM_STOKES_PVEL:  // [f, q] -> [p, u], G^P for every interaction (Sec. II.C)
       P.ks = 4;
       P.kt = 4;
@@ -156,9 +160,11 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
     return KAFMM_ERR_ARG;
   }
   *out = nullptr;
-  if ((int)kernel < 0 || (int)kernel > 12 || (kernel == KAFMM_LAPLACE_QD && bc == KAFMM_BC_PXYZ) ||
+  if ((int)kernel < 0 || (int)kernel > 13 ||
+      ((kernel == KAFMM_LAPLACE_QD || kernel == KAFMM_LAPLACE_QUAD) && bc == KAFMM_BC_PXYZ) ||
       (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ && bc != KAFMM_BC_WALL) ||
-      (bc == KAFMM_BC_WALL && kernel != KAFMM_STOKESLET) || p < 2 || p > 16 || q < 1 || q > 4096) {
+      (bc == KAFMM_BC_WALL && kernel != KAFMM_STOKESLET && kernel != KAFMM_RPY) || p < 2 || p > 16 || q < 1 ||
+      q > 4096) {
     g_err = "kafmm_plan: invalid kernel, boundary condition, order (2..16) or leaf size (1..4096)";
     return KAFMM_ERR_ARG;
   }
@@ -176,9 +182,11 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
       return KAFMM_ERR_CUDA;
     }
   }
-  if (bc == KAFMM_BC_WALL) {   // the sums of the image system: Stokeslet, Laplace charges + dipoles
-    const kafmm_kernel kk[2] = {KAFMM_STOKESLET, KAFMM_LAPLACE_QD};
-    for (int c = 0; c < 2; ++c) {
+  if (bc == KAFMM_BC_WALL) {   // the sums of the image system: Stokeslet or RPY, Laplace charges +
+                               // dipoles, and (RPY) Laplace quadrupoles
+    const bool rpy = kernel == KAFMM_RPY;
+    const kafmm_kernel kk[3] = {rpy ? KAFMM_RPY : KAFMM_STOKESLET, KAFMM_LAPLACE_QD, KAFMM_LAPLACE_QUAD};
+    for (int c = 0; c < (rpy ? 3 : 2); ++c) {
       int rc = kafmm_plan(kk[c], KAFMM_BC_OPEN, p, q, &P->wall_child[c]);
       if (rc) {
         for (int d = 0; d < c; ++d) kafmm_destroy(P->wall_child[d]);
@@ -194,7 +202,7 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
 
 extern "C" int kafmm_set_option(kafmm_plan_t pl, int key, int64_t value) {
   PLAN_CHECK(pl);
-  for (int c = 0; c < 2; ++c)   // a wall plan's sums take the same options
+  for (int c = 0; c < WALL_CHILDREN; ++c)   // a wall plan's sums take the same options
     if (P.wall_child[c]) {
       int rc = kafmm_set_option(P.wall_child[c], key, value);
       if (rc) return fail(P, rc, "%s", kafmm_last_error(P.wall_child[c]));
@@ -297,7 +305,7 @@ extern "C" int kafmm_set_domain(kafmm_plan_t pl, const double origin[3], double 
   for (int d = 0; d < 3; ++d) P.origin[d] = origin[d];
   P.L = L;
   P.have_points = false;
-  for (int c = 0; c < 2; ++c)
+  for (int c = 0; c < WALL_CHILDREN; ++c)
     if (P.wall_child[c]) kafmm_set_domain(P.wall_child[c], origin, L);
   return 0;
 }
@@ -520,7 +528,7 @@ extern "C" int kafmm_autotune(kafmm_plan_t pl, const void* s, void* g, int dtype
 
 extern "C" int kafmm_status(kafmm_plan_t pl) {
   PLAN_CHECK(pl);
-  for (int c = 0; c < 2; ++c)
+  for (int c = 0; c < WALL_CHILDREN; ++c)
     if (P.wall_child[c]) {
       int rc = kafmm_status(P.wall_child[c]);
       if (rc) return fail(P, rc, "%s", kafmm_last_error(P.wall_child[c]));
@@ -767,7 +775,7 @@ extern "C" int kafmm_get_operator(kafmm_plan_t pl, int slot, double* out) {
 extern "C" int kafmm_destroy(kafmm_plan_t pl) {
   if (!pl) return 0;
   Plan* P = reinterpret_cast<Plan*>(pl);
-  for (int c = 0; c < 2; ++c)
+  for (int c = 0; c < WALL_CHILDREN; ++c)
     if (P->wall_child[c]) kafmm_destroy(P->wall_child[c]);
   for (int i = 0; i < 8; ++i)
     if (P->ev[i]) cudaEventDestroy(P->ev[i]);

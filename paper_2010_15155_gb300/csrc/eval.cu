@@ -42,7 +42,7 @@ __global__ void k_prep_src(const Tin* __restrict__ s, const uint32_t* __restrict
   using T4 = typename V4<T>::type;
   constexpr int KS =
       PR == P_LAP ? 1
-                  : (dl_src(PR) ? 9
+                  : ((dl_src(PR) || PR == P_LAPQ) ? 9
                                 : ((PR == P_RPY_L4 || PR == P_RPY_G || PR == P_REG_G || PR == P_LAPQD || pvel_src(PR))
                                        ? 4
                                        : 3));
@@ -203,6 +203,12 @@ __global__ void __launch_bounds__(128) k_s2check(S2CArgs<T, PR> a) {
               ac[3] += tmp[3];
             } else if (PR == P_LAP) {
               lap_st<T>(r0, r1, r2, v.x, ac);
+            } else if (PR == P_LAPQ) {   // S->M, S->L: the quadrupole potential
+              T4 v1 = sv[j * NV + 1], v2 = sv[j * NV + 2];
+              T Qm[9] = {v.x, v.y, v.z, v.w, v1.x, v1.y, v1.z, v1.w, v2.x};
+              T tmp[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+              quad_st<T>(r0, r1, r2, Qm, tmp);
+              ac[0] += tmp[0];
             } else if (PR == P_LAPQD) {   // S->M, S->L: L for the charge, L^D for the dipole
               T rr = r0 * r0 + r1 * r1 + r2 * r2;
               T ir = inv_r(rr);
@@ -581,7 +587,7 @@ __device__ inline void far_eval(T xl, T yl, T zl, const typename V4<T>::type& p,
     pvel_st<T>(r0, r1, r2, q.x, q.y, q.z, q.w, acc);
   } else if (deriv_out(PR)) {   // M->T, L->T: G^P + grad G^P from the equivalent [f, q]
     pvel_grad_st<T>(r0, r1, r2, q.x, q.y, q.z, q.w, acc);
-  } else if (PR == P_LAPQD) {   // M->T, L->T: equivalent charges, L + grad L + grad grad L
+  } else if (PR == P_LAPQD || PR == P_LAPQ) {   // M->T, L->T: equivalent charges, L + grad L + grad grad L
     lapqd_st<T, false>(r0, r1, r2, q.x, T(0), T(0), T(0), acc);
   } else if (PR == P_STK_L4 || PR == P_RPY_L4) {
     // 8 pi u_i = 2 [phi_i - x_j d_i phi_j + d_i phi_4] with phi = q/r (reference: leaf centre)
@@ -910,6 +916,8 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
                   T Dm[9] = {v.x, v.y, v.z, v.w, v1.x, v1.y, v1.z, v1.w, v2.x};
                   if constexpr (PR == P_DL_D)
                     dl_grad_st<T>(r0, r1, r2, Dm, tmp);
+                  else if constexpr (PR == P_LAPQ)
+                    quad_st<T>(r0, r1, r2, Dm, tmp);
                   else
                     dl_st<T>(r0, r1, r2, Dm, tmp);
                 }
@@ -1685,6 +1693,8 @@ int evaluate(Plan& P, const void* s, void* g, int dtype) {
     pr = P_PVEL;
   else if (P.kernel == KAFMM_STOKES_DL)
     pr = P_DL;
+  else if (P.kernel == KAFMM_LAPLACE_QUAD)
+    pr = P_LAPQ;
   else if (P.kernel == KAFMM_STOKES_PVEL_GRAD || P.kernel == KAFMM_STOKES_PVEL_LAPL ||
            P.kernel == KAFMM_STOKES_PVEL_TRACTION)
     pr = P_PVEL_D;
@@ -1704,6 +1714,7 @@ int evaluate(Plan& P, const void* s, void* g, int dtype) {
     case P_PVEL: return run_eval<T, P_PVEL>(P, s, sd, g);    \
     case P_DL: return run_eval<T, P_DL>(P, s, sd, g);        \
     case P_PVEL_D: return run_eval<T, P_PVEL_D>(P, s, sd, g); \
+    case P_LAPQ: return run_eval<T, P_LAPQ>(P, s, sd, g);    \
     default: return run_eval<T, P_DL_D>(P, s, sd, g);        \
   }
   if (P.fp64()) {

@@ -9,8 +9,10 @@ namespace kafmm {
 // P_PVEL_D / P_DL_D: the StokesPVel and double-layer problems with derivative target values
 // (Tables tab:ktab_stkslpvelgrad, tab:ktab_stkdlpvelgrad): [p, u, grad p, grad u] at every
 // target, from which the Laplacian and traction forms are taken.
+// P_LAPQ: Laplace quadrupole sources (9 values) to [phi, grad phi, grad grad phi] on the Laplace
+// table (LapQPGradGrad of Table tab:implement).
 enum Prob { P_LAP = 0, P_STK_L4 = 1, P_STK_G = 2, P_RPY_L4 = 3, P_RPY_G = 4, P_DL = 5, P_REG_G = 6,
-            P_LAPQD = 7, P_PVEL = 8, P_PVEL_D = 9, P_DL_D = 10 };
+            P_LAPQD = 7, P_PVEL = 8, P_PVEL_D = 9, P_DL_D = 10, P_LAPQ = 11 };
 
 // [f, q] sources, double-layer D sources, and the StokesPVel ML table shared by all four.
 __host__ __device__ constexpr bool pvel_src(int pr) { return pr == P_PVEL || pr == P_PVEL_D; }
@@ -44,6 +46,8 @@ template <>
 struct ProbInfo<P_PVEL_D> { static constexpr int KT = 16, C = 1, D = 4, NV = 1; };
 template <>
 struct ProbInfo<P_DL_D> { static constexpr int KT = 16, C = 1, D = 4, NV = 3; };
+template <>
+struct ProbInfo<P_LAPQ> { static constexpr int KT = 10, C = 1, D = 1, NV = 3; };
 
 template <class T>
 struct V4;
@@ -275,11 +279,47 @@ __device__ inline void dl_grad_st(T r0, T r1, T r2, const T* Dm, T* acc) {
       acc[7 + 3 * i + j] += -T(3) * ((i == j ? c5 : T(0)) + r[i] * a[j] * ir5 - r[i] * r[j] * c7);
 }
 
+// Laplace quadrupole Q (Q_jk at 3j + k) to potential, gradient and Hessian: phi = Q_jk d_j d_k L
+// (L = 1/(4 pi r), derivatives in x), scaled by 1/(4 pi) at the end.  With S = sym(Q),
+// s = S r, rQr = r.Q.r, t = tr Q:
+//   4 pi phi         = 3 rQr / r^5 - t / r^3,
+//   4 pi d_i phi     = -15 r_i rQr / r^7 + 3 (2 s_i + t r_i) / r^5,
+//   4 pi d_i d_l phi = 105 r_i r_l rQr / r^9 - 15 (delta_il rQr + 2 r_l s_i + 2 r_i s_l + t r_i r_l) / r^7
+//                      + 3 (delta_il t + 2 S_il) / r^5;   Hessian order xx xy xz yy yz zz.
+template <class T>
+__device__ inline void quad_st(T r0, T r1, T r2, const T* Q, T* acc) {
+  T ir = inv_r(r0 * r0 + r1 * r1 + r2 * r2);
+  T ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2, ir7 = ir5 * ir2, ir9 = ir7 * ir2;
+  const T r[3] = {r0, r1, r2};
+  T S[9], sv[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) S[3 * a + b] = T(0.5) * (Q[3 * a + b] + Q[3 * b + a]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) sv[a] = S[3 * a] * r0 + S[3 * a + 1] * r1 + S[3 * a + 2] * r2;
+  const T rQr = r0 * sv[0] + r1 * sv[1] + r2 * sv[2];
+  const T t = Q[0] + Q[4] + Q[8];
+  acc[0] += T(3) * rQr * ir5 - t * ir3;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) acc[1 + i] += -T(15) * r[i] * rQr * ir7 + T(3) * (T(2) * sv[i] + t * r[i]) * ir5;
+  int c = 4;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int l = i; l < 3; ++l) {
+      T h = T(105) * r[i] * r[l] * rQr * ir9 -
+            T(15) * (T(2) * r[l] * sv[i] + T(2) * r[i] * sv[l] + t * r[i] * r[l]) * ir7 + T(6) * S[3 * i + l] * ir5;
+      if (i == l) h += -T(15) * rQr * ir7 + T(3) * t * ir5;
+      acc[c++] += h;
+    }
+}
+
 // Final scale factors of the accumulators.
 template <int PR, class T>
 __device__ inline T out_scale(int k) {
   const T f4 = T(1.0 / (4.0 * PI)), f8 = T(1.0 / (8.0 * PI));
-  if (PR == P_LAP || PR == P_LAPQD) return f4;
+  if (PR == P_LAP || PR == P_LAPQD || PR == P_LAPQ) return f4;
   if (PR == P_STK_L4 || PR == P_STK_G || PR == P_REG_G) return f8;
   if (PR == P_RPY_L4 || PR == P_RPY_G) return k < 3 ? f8 : f4;
   if (deriv_out(PR)) return (k == 0 || (k >= 4 && k < 7)) ? f4 : f8;   // [p, u, grad p, grad u]

@@ -55,6 +55,7 @@ struct Tree {
   DevBuf s_keys2, s_vals2, s_hist, t_keys2, t_vals2;
   DevBuf sort_flag;                 // [0] full key sort needed, [1..2] its scan lengths
   DevBuf dense_start;               // dense cell starts of the top levels (sources, targets)
+  DevBuf bld_sync;                  // cooperative refinement: barrier words, block totals
   DevBuf bld_key, bld_sb, bld_se, bld_tb, bld_te, bld_parent, bld_child, bld_cnt, bld_nch,
       bld_choff, bld_cb, bld_ctb, bld_prob;
   DevBuf status;                    // unsigned status word
@@ -79,6 +80,9 @@ struct WorkLists {
   int cup[2] = {0, 0}, cx[2] = {0, 0};       // compressed coordinates: leaves, boxes with X entries
   int leaves_n = 0, xbox_off = 0, xbox_n = 0, leafbox_off = 0;  // plain box lists
 };
+
+// Child plans of a wall plan: Stokeslet or RPY, Laplace charges + dipoles, (RPY) quadrupoles.
+constexpr int WALL_CHILDREN = 3;
 
 struct Plan {
   // problem
@@ -158,8 +162,8 @@ struct Plan {
   long long launches_points = 0, launches_eval = 0;  // kernel launches of the last calls
   // no-slip wall (KAFMM_BC_WALL): the Stokeslet and Laplace charge + dipole child plans over
   // the sources and their images, and the work arrays of the assembly
-  kafmm_plan_t wall_child[2] = {nullptr, nullptr};
-  DevBuf wall_buf[8];
+  kafmm_plan_t wall_child[WALL_CHILDREN] = {nullptr, nullptr, nullptr};
+  DevBuf wall_buf[10];
   cudaEvent_t ev[8] = {0};
   double phase_ms[8] = {0};
   std::string err;

@@ -190,6 +190,10 @@ __global__ void k_rpy_velocity(const typename V4<T>::type* __restrict__ spos,
         if (same && j == (int)i && sx == 0 && sy == 0 && sz == 0) continue;
         typename V4<T>::type y = spos[j], fb = sfb[j];
         T r0 = x.x - (y.x + ox), r1 = x.y - (y.y + oy), r2 = x.z - (y.z + oz);
+        // clearly out of contact for both tests below (the overlap form's r <= a_i + b_j and
+        // the near field's r <= b_i + b_j, each taken in its own arithmetic): nothing to add
+        const T m = (ai > bi ? ai : bi) + fb.w;
+        if (r0 * r0 + r1 * r1 + r2 * r2 > m * m * T(1.0001)) continue;
         if (ci.on) {   // the near field's contact test (its own radii, the same arithmetic)
           if (in_contact<T>(x.x, x.y, x.z, y.x, y.y, y.z, ox, oy, oz, bi, fb.w) &&
               leaves_adjacent(ci.level, ci.key, ci.leaf_of[i], ci.leaf_of[j], sx, sy, sz)) {

@@ -65,11 +65,9 @@ __device__ inline unsigned radix_digit(uint64_t k, uint32_t v, int shift, const 
   return (unsigned)((k >> shift) & 255);
 }
 
-// run: the pass is skipped when *run == 0 (nullptr: always runs).
 __global__ void k_radix_hist(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                              int64_t n, int shift, const int64_t* __restrict__ poff, int nprob,
-                             uint32_t* __restrict__ hist, int nblk, const int* run) {
-  if (run && *run == 0) return;
+                             uint32_t* __restrict__ hist, int nblk) {
   __shared__ uint32_t cnt[256];
   cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -85,8 +83,7 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ keys, const uint32_t* 
 __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                 uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
                                 int shift, const int64_t* __restrict__ poff, int nprob,
-                                const uint32_t* __restrict__ hist, int nblk, const int* run) {
-  if (run && *run == 0) return;
+                                const uint32_t* __restrict__ hist, int nblk) {
   __shared__ uint32_t wcnt[RS_WARPS][256];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
@@ -138,11 +135,9 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t
 // Stable LSD passes over (keys, vals), ping-pong through (k2, v2): one pass per entry of
 // shifts, the 8-bit digit of the key at that bit (an entry s >= 64: bits [s - 64, s - 56) of the
 // problem index of the element's caller index).  An odd number of passes ends with a copy back,
-// so the result is always in (keys, vals).  run / run_len: the passes do nothing when *run == 0
-// (*run_len is then 0, else 256 x blocks); nullptr runs them always.
+// so the result is always in (keys, vals).
 static void radix_passes(uint64_t* keys, uint32_t* vals, uint64_t* k2, uint32_t* v2, uint32_t* hist,
-                         int64_t n, const int64_t* poff, int nprob, const int* shifts, int npass,
-                         const int* run, const int* run_len, cudaStream_t st) {
+                         int64_t n, const int64_t* poff, int nprob, const int* shifts, int npass, cudaStream_t st) {
   if (n <= 1 || npass <= 0) return;
   int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
   uint64_t *ka = keys, *kb = k2;
@@ -151,13 +146,13 @@ static void radix_passes(uint64_t* keys, uint32_t* vals, uint64_t* k2, uint32_t*
     const bool by_prob = shifts[pass] >= 64;
     const int shift = by_prob ? shifts[pass] - 64 : shifts[pass];
     const int64_t* po = by_prob ? poff : nullptr;
-    KL k_radix_hist<<<nblk, RS_THREADS, 0, st>>>(ka, va, n, shift, po, nprob, hist, nblk, run);
-    scan_excl<uint32_t>(hist, hist, (int64_t)256 * nblk, run_len, hist + 256 * (int64_t)nblk, nullptr, st);
-    KL k_radix_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, po, nprob, hist, nblk, run);
+    KL k_radix_hist<<<nblk, RS_THREADS, 0, st>>>(ka, va, n, shift, po, nprob, hist, nblk);
+    scan_excl<uint32_t>(hist, hist, (int64_t)256 * nblk, nullptr, hist + 256 * (int64_t)nblk, nullptr, st);
+    KL k_radix_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, po, nprob, hist, nblk);
     std::swap(ka, kb);
     std::swap(va, vb);
   }
-  if (npass & 1) {  // the result sits in (k2, v2); run passes only come in even numbers
+  if (npass & 1) {  // the result sits in (k2, v2)
     cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
   }
@@ -168,15 +163,16 @@ static void radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* k2, uint32_t* v
                        int64_t n, cudaStream_t st, int key_passes) {
   int shifts[8];
   for (int i = 0; i < key_passes; ++i) shifts[i] = 8 * i;
-  radix_passes(keys, vals, k2, v2, hist, n, nullptr, 1, shifts, key_passes, nullptr, nullptr, st);
+  radix_passes(keys, vals, k2, v2, hist, n, nullptr, 1, shifts, key_passes, st);
 }
 
 // The Morton keys are first sorted on their top 32 bits (bits 28-59: the cells of levels 1-10
 // in order).  That order is all the refinement reads unless a level-10 cell would split, i.e.
-// holds more than q points (sources and targets); k_deep_check looks for a run of key + 1 equal
-// level-10 cells and then the full sort on all 60 bits runs (a stable LSD sort from scratch:
-// the first order only breaks ties, which index order breaks the same way).  With separate
-// targets each set is checked against q / 2, which bounds the sum.
+// holds more than q points (sources and targets); k_deep_check looks for a run of q + 1 equal
+// level-10 cells, the host reads its flag with the level counts, and then the full sort on all
+// 60 bits runs and the tree is built again (a stable LSD sort from scratch: the first order only
+// breaks ties, which index order breaks the same way).  With separate targets each set is
+// checked against q / 2, which bounds the sum.
 constexpr int TOP_SHIFTS[4] = {28, 36, 44, 52};
 constexpr int FULL_SHIFTS[8] = {0, 8, 16, 24, 32, 40, 48, 56};
 constexpr int CELL10_SHIFT = 3 * (MAX_LEVEL - 10);
@@ -186,14 +182,6 @@ __global__ void k_deep_check(const uint64_t* __restrict__ key, int64_t n, int ru
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i + run < n; i += (int64_t)gridDim.x * blockDim.x)
     deep = deep || (key[i] >> CELL10_SHIFT) == (key[i + run] >> CELL10_SHIFT);
   if (__any_sync(0xffffffffu, deep) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
-}
-
-// flag[1] / flag[2]: the scan lengths of the full passes of the two sets (0 when skipped).
-__global__ void k_deep_lens(int* flag, int len_s, int len_t) {
-  if (threadIdx.x == 0) {
-    flag[1] = flag[0] ? len_s : 0;
-    flag[2] = flag[0] ? len_t : 0;
-  }
 }
 
 // Dense starts of the cells of levels 1-DENSE_LV in the sorted keys of one point set (a single
@@ -255,61 +243,75 @@ __global__ void k_root(BuildArgs a) {
     for (int l = 0; l < MAX_LEVELS; ++l) a.cnt[l] = l == 0 ? a.nprob : 0;
 }
 
+// Loads of the refinement: plain, or L2-only (ld.global.cg) inside the cooperative kernel,
+// whose phases read what other blocks wrote earlier in the same launch (an L1 line could still
+// hold an older copy of a neighbouring entry).
+template <bool CG, class V>
+__device__ __forceinline__ V rd(const V* p) {
+  if constexpr (CG)
+    return __ldcg(p);
+  else
+    return *p;
+}
+
 // One warp per box: a box with more than q points splits; lanes 0-7 find the start of child o in
 // the sorted source keys and lanes 8-15 in the target keys (binary searches in parallel, so
-// the root's eight searches over all points are one chain of dependent loads, not eight).
+// the root's eight searches over all points are one chain of dependent loads, not eight; the
+// top levels read their child boundaries from the dense cell-start tables).
+template <bool CG>
+__device__ void split_box(const BuildArgs& a, int lv, int i, int lane) {
+  const int64_t g = a.cap_off[lv] + i;
+  const int sh = 3 * (MAX_LEVEL - lv - 1);
+  const int sb = rd<CG>(a.sb + g), se = rd<CG>(a.se + g), tb = rd<CG>(a.tb + g), te = rd<CG>(a.te + g);
+  const int count = (se - sb) + (a.same ? 0 : (te - tb));
+  int nch = 0;
+  if (count > a.q && lv < MAX_LEVEL) {   // warp-uniform
+    const uint64_t k = rd<CG>(a.key + g);
+    int v = 0;
+    if (a.dense && lv < DENSE_LV) {
+      // child o starts at the first non-empty child o' >= o (suffix minimum over the 8 cell
+      // starts of each set), else at the end of the box
+      v = 0x7f7f7f7f;
+      const int base = dense_off(lv + 1) + (int)(k * 8);
+      if (lane < 8)
+        v = a.dstart_s[base + lane];
+      else if (lane < 16 && !a.same)
+        v = a.dstart_t[base + lane - 8];
+#pragma unroll
+      for (int d = 1; d < 8; d <<= 1) {
+        const int w = __shfl_down_sync(0xffffffffu, v, d, 8);
+        if ((lane & 7) + d < 8) v = min(v, w);
+      }
+      v = min(v, lane < 8 ? se : te);
+    } else if (lane < 8) {
+      v = lower_bound_prefix(a.skey, sb, se, k * 8 + lane, sh);
+    } else if (lane < 16 && !a.same) {
+      v = lower_bound_prefix(a.tkey, tb, te, k * 8 + (lane - 8), sh);
+    }
+    int cb[9], ctb[9];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      cb[o] = __shfl_sync(0xffffffffu, v, o);
+      ctb[o] = __shfl_sync(0xffffffffu, v, 8 + o);
+      if (a.same) ctb[o] = cb[o];
+    }
+    cb[8] = se;
+    ctb[8] = a.same ? se : te;
+    if (lane < 9) {
+      a.cb[g * 9 + lane] = cb[lane];
+      a.ctb[g * 9 + lane] = ctb[lane];
+    }
+#pragma unroll
+    for (int o = 0; o < 8; ++o)
+      nch += ((cb[o + 1] - cb[o]) + (a.same ? 0 : (ctb[o + 1] - ctb[o]))) > 0;
+  }
+  if (lane == 0) a.nch[g] = nch;
+}
+
 __global__ void k_split(BuildArgs a, int lv, unsigned* status) {
   const int n = a.cnt[lv];
-  const int64_t o0 = a.cap_off[lv];
-  const int sh = 3 * (MAX_LEVEL - lv - 1);
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
-    const int64_t g = o0 + i;
-    const int sb = a.sb[g], se = a.se[g], tb = a.tb[g], te = a.te[g];
-    const int count = (se - sb) + (a.same ? 0 : (te - tb));
-    int nch = 0;
-    if (count > a.q && lv < MAX_LEVEL) {   // warp-uniform
-      const uint64_t k = a.key[g];
-      int v = 0;
-      if (a.dense && lv < DENSE_LV) {
-        // child o starts at the first non-empty child o' >= o (suffix minimum over the 8 cell
-        // starts of each set), else at the end of the box
-        v = 0x7f7f7f7f;
-        const int base = dense_off(lv + 1) + (int)(k * 8);
-        if (lane < 8)
-          v = a.dstart_s[base + lane];
-        else if (lane < 16 && !a.same)
-          v = a.dstart_t[base + lane - 8];
-#pragma unroll
-        for (int d = 1; d < 8; d <<= 1) {
-          const int w = __shfl_down_sync(0xffffffffu, v, d, 8);
-          if ((lane & 7) + d < 8) v = min(v, w);
-        }
-        v = min(v, lane < 8 ? se : te);
-      } else if (lane < 8) {
-        v = lower_bound_prefix(a.skey, sb, se, k * 8 + lane, sh);
-      } else if (lane < 16 && !a.same) {
-        v = lower_bound_prefix(a.tkey, tb, te, k * 8 + (lane - 8), sh);
-      }
-      int cb[9], ctb[9];
-#pragma unroll
-      for (int o = 0; o < 8; ++o) {
-        cb[o] = __shfl_sync(0xffffffffu, v, o);
-        ctb[o] = __shfl_sync(0xffffffffu, v, 8 + o);
-        if (a.same) ctb[o] = cb[o];
-      }
-      cb[8] = se;
-      ctb[8] = a.same ? se : te;
-      if (lane < 9) {
-        a.cb[g * 9 + lane] = cb[lane];
-        a.ctb[g * 9 + lane] = ctb[lane];
-      }
-#pragma unroll
-      for (int o = 0; o < 8; ++o)
-        nch += ((cb[o + 1] - cb[o]) + (a.same ? 0 : (ctb[o + 1] - ctb[o]))) > 0;
-    }
-    if (lane == 0) a.nch[g] = nch;
-  }
+  for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) split_box<false>(a, lv, i, lane);
 }
 
 __global__ void k_level_total(BuildArgs a, int lv, const int* total, unsigned* status) {
@@ -325,37 +327,172 @@ __global__ void k_level_total(BuildArgs a, int lv, const int* total, unsigned* s
   }
 }
 
-__global__ void k_emit(BuildArgs a, int lv) {
-  int n = a.cnt[lv];
-  int64_t o0 = a.cap_off[lv];
-  int64_t o1 = a.cap_off[lv + 1];
-  int cap1 = a.cap[lv + 1 < MAX_LEVELS ? lv + 1 : lv];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int64_t g = o0 + i;
-    int j = a.choff[g];
-    int nch = a.nch[g];
-    uint64_t k = a.key[g];
-    for (int o = 0; o < 8; ++o) {
-      int c = -1;
-      if (nch > 0) {
-        int b0 = a.cb[g * 9 + o], b1 = a.cb[g * 9 + o + 1];
-        int t0 = a.ctb[g * 9 + o], t1 = a.ctb[g * 9 + o + 1];
-        int cnt = (b1 - b0) + (a.same ? 0 : (t1 - t0));
-        if (cnt > 0 && j < cap1) {
-          int64_t h = o1 + j;
-          a.key[h] = k * 8 + o;
-          a.sb[h] = b0;
-          a.se[h] = b1;
-          a.tb[h] = a.same ? b0 : t0;
-          a.te[h] = a.same ? b1 : t1;
-          a.parent[h] = i;
-          a.prob[h] = a.prob[g];
-          c = j;
-          ++j;
-        }
+// Children of box i of level lv, numbered from j (the exclusive prefix of the child counts).
+template <bool CG>
+__device__ void emit_box(const BuildArgs& a, int lv, int i, int j) {
+  const int64_t o0 = a.cap_off[lv], o1 = a.cap_off[lv + 1];
+  const int cap1 = a.cap[lv + 1 < MAX_LEVELS ? lv + 1 : lv];
+  const int64_t g = o0 + i;
+  const int nch = rd<CG>(a.nch + g);
+  const uint64_t k = rd<CG>(a.key + g);
+  const int prob = rd<CG>(a.prob + g);
+  for (int o = 0; o < 8; ++o) {
+    int c = -1;
+    if (nch > 0) {
+      const int b0 = rd<CG>(a.cb + g * 9 + o), b1 = rd<CG>(a.cb + g * 9 + o + 1);
+      const int t0 = rd<CG>(a.ctb + g * 9 + o), t1 = rd<CG>(a.ctb + g * 9 + o + 1);
+      const int cnt = (b1 - b0) + (a.same ? 0 : (t1 - t0));
+      if (cnt > 0 && j < cap1) {
+        const int64_t h = o1 + j;
+        a.key[h] = k * 8 + o;
+        a.sb[h] = b0;
+        a.se[h] = b1;
+        a.tb[h] = a.same ? b0 : t0;
+        a.te[h] = a.same ? b1 : t1;
+        a.parent[h] = i;
+        a.prob[h] = prob;
+        c = j;
+        ++j;
       }
-      a.child[g * 8 + o] = c;
     }
+    a.child[g * 8 + o] = c;
+  }
+}
+
+__global__ void k_emit(BuildArgs a, int lv) {
+  const int n = a.cnt[lv];
+  const int64_t o0 = a.cap_off[lv];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    emit_box<false>(a, lv, i, a.choff[o0 + i]);
+}
+
+// Grid barrier of the cooperative refinement: arrival counter and generation, the wait bounded
+// by %globaltimer (ST_TIMEOUT in *status and false when the other blocks did not arrive).
+__device__ bool refine_barrier(unsigned* count, unsigned* gen, unsigned* status, unsigned long long limit_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned g = *(volatile unsigned*)gen;
+    __threadfence();
+    if (atomicAdd(count, 1u) + 1u == gridDim.x) {
+      *(volatile unsigned*)count = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*(volatile unsigned*)gen == g) {
+        if (global_ns() - t0 > limit_ns) {
+          atomicOr(status, (unsigned)ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// The whole refinement in one cooperative launch: the roots, then per level (until one is
+// empty) split (warp per box), the exclusive scan of the child counts (block b scans a
+// contiguous chunk; its offset is the sum of the earlier blocks' totals), the next level's count
+// (clamped to its capacity, ST_OVERFLOW otherwise) and the children (thread per box of the
+// block's own chunk), with grid barriers between the phases.  sync: [count, generation];
+// bsum: one total per block.  A barrier that times out ends every block (ST_TIMEOUT).
+__global__ void __launch_bounds__(256) k_refine(BuildArgs a, int* bsum, unsigned* sync, unsigned* status,
+                                                unsigned long long limit_ns) {
+  __shared__ int s_part[32];
+  __shared__ int s_off, s_tot;
+  const int G = gridDim.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  if (blockIdx.x == 0) {
+    for (int k = threadIdx.x; k < a.nprob; k += blockDim.x) {
+      a.key[k] = 0;
+      a.sb[k] = (int)a.soff[k];
+      a.se[k] = (int)a.soff[k + 1];
+      a.tb[k] = a.same ? (int)a.soff[k] : (int)a.toff[k];
+      a.te[k] = a.same ? (int)a.soff[k + 1] : (int)a.toff[k + 1];
+      a.parent[k] = -1;
+      a.prob[k] = k;
+    }
+    for (int l = threadIdx.x; l < MAX_LEVELS; l += blockDim.x) a.cnt[l] = l == 0 ? a.nprob : 0;
+  }
+  if (!refine_barrier(sync, sync + 1, status, limit_ns)) return;
+  for (int lv = 0; lv < MAX_LEVEL; ++lv) {
+    const int n = __ldcg(a.cnt + lv);
+    if (n == 0) break;   // uniform: every block read the count after the same barrier
+    const int64_t o0 = a.cap_off[lv];
+    for (int i = blockIdx.x * wpb + w; i < n; i += G * wpb) split_box<true>(a, lv, i, lane);
+    if (!refine_barrier(sync, sync + 1, status, limit_ns)) return;
+    // exclusive scan of the child counts over this block's chunk
+    const int chunk = (n + G - 1) / G;
+    const int lo = min(n, blockIdx.x * chunk), hi = min(n, lo + chunk);
+    int carry = 0;
+    for (int base = lo; base < hi; base += blockDim.x) {
+      const int i = base + threadIdx.x;
+      const int v = i < hi ? __ldcg(a.nch + o0 + i) : 0;
+      int x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) s_part[w] = x;
+      __syncthreads();
+      if (w == 0) {
+        const int t = lane < wpb ? s_part[lane] : 0;
+        int xx = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, xx, o);
+          if (lane >= o) xx += y;
+        }
+        s_part[lane] = xx - t;   // exclusive warp offsets
+        if (lane == 31) s_tot = xx;
+      }
+      __syncthreads();
+      if (i < hi) a.choff[o0 + i] = carry + s_part[w] + x - v;
+      carry += s_tot;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = carry;
+    if (!refine_barrier(sync, sync + 1, status, limit_ns)) return;
+    // this block's offset, and (last block) the next level's count
+    int before = 0, all = 0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) {
+      const int t = __ldcg(bsum + b);
+      all += t;
+      if (b < blockIdx.x) before += t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      before += __shfl_down_sync(0xffffffffu, before, o);
+      all += __shfl_down_sync(0xffffffffu, all, o);
+    }
+    if (lane == 0) s_part[w] = before;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int sbf = 0;
+      for (int q = 0; q < wpb; ++q) sbf += s_part[q];
+      s_off = sbf;
+    }
+    __syncthreads();
+    if (lane == 0) s_part[w] = all;
+    __syncthreads();
+    if (threadIdx.x == 0 && blockIdx.x == G - 1 && lv + 1 < MAX_LEVELS) {
+      int t = 0;
+      for (int q = 0; q < wpb; ++q) t += s_part[q];
+      if (t > a.cap[lv + 1]) {
+        atomicOr(status, (unsigned)ST_OVERFLOW);
+        t = a.cap[lv + 1];
+      }
+      a.cnt[lv + 1] = t;
+    }
+    const int off = s_off;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) emit_box<true>(a, lv, i, off + __ldcg(a.choff + o0 + i));
+    if (!refine_barrier(sync, sync + 1, status, limit_ns)) return;
   }
 }
 
@@ -811,25 +948,28 @@ static int sort_top(Plan& P, const void* pts, int64_t n, int dtype, DevBuf& key,
     KL k_keys<float><<<g, 256, 0, st>>>((const float*)pts, n, P.origin[0], P.origin[1], P.origin[2], P.L,
                                       inv_L, key.as<uint64_t>(), perm.as<uint32_t>(), status);
   radix_passes(key.as<uint64_t>(), perm.as<uint32_t>(), k2.as<uint64_t>(), v2.as<uint32_t>(), T.s_hist.as<uint32_t>(),
-               n, nullptr, 1, TOP_SHIFTS, 4, nullptr, nullptr, st);
+               n, nullptr, 1, TOP_SHIFTS, 4, st);
   return 0;
 }
 
-// The full key sort when flag says so (run_len: its scan lengths), the problem passes of a
-// batch, and the sorted positions in the compute type.
+// The full 60-bit key sort of one point set (stable LSD from the current order: the first
+// sort only breaks ties, which index order breaks the same way).
+static void sort_full(Plan& P, int64_t n, DevBuf& key, DevBuf& perm, DevBuf& k2, DevBuf& v2) {
+  radix_passes(key.as<uint64_t>(), perm.as<uint32_t>(), k2.as<uint64_t>(), v2.as<uint32_t>(),
+               P.tree.s_hist.as<uint32_t>(), n, nullptr, 1, FULL_SHIFTS, 8, P.stream);
+}
+
+// The problem passes of a batch and the sorted positions in the compute type.
 static int sort_finish(Plan& P, const void* pts, int64_t n, int dtype, const int64_t* d_off, int nprob,
-                       const int* flag, const int* run_len, DevBuf& key, DevBuf& perm, DevBuf& k2, DevBuf& v2,
-                       DevBuf& pos) {
+                       DevBuf& key, DevBuf& perm, DevBuf& k2, DevBuf& v2, DevBuf& pos) {
   Tree& T = P.tree;
   cudaStream_t st = P.stream;
   uint64_t* kk = key.as<uint64_t>();
   uint32_t* vv = perm.as<uint32_t>();
-  radix_passes(kk, vv, k2.as<uint64_t>(), v2.as<uint32_t>(), T.s_hist.as<uint32_t>(), n, nullptr, 1, FULL_SHIFTS,
-               8, flag, run_len, st);
   if (nprob > 1) {
     const int prob_shifts[2] = {64, 72};
     radix_passes(kk, vv, k2.as<uint64_t>(), v2.as<uint32_t>(), T.s_hist.as<uint32_t>(), n, d_off, nprob,
-                 prob_shifts, nprob > 256 ? 2 : 1, nullptr, nullptr, st);
+                 prob_shifts, nprob > 256 ? 2 : 1, st);
   }
   size_t esz = P.fp64() ? sizeof(double4) : sizeof(float4);
   CK(pos.reserve(esz * (n + 1)));
@@ -849,6 +989,10 @@ static int sort_finish(Plan& P, const void* pts, int64_t n, int dtype, const int
   }
   CK(cudaGetLastError());
   return 0;
+}
+
+__global__ void k_clear_bits(unsigned* status, unsigned mask) {
+  if (threadIdx.x == 0) *status &= ~mask;
 }
 
 int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, int dtype, int n_prob,
@@ -884,27 +1028,8 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
       KL k_deep_check<<<grid_for(ns, 256), 256, 0, st>>>(T.src_key.as<uint64_t>(), ns, run, flag);
     if (!T.same && nt > 0)
       KL k_deep_check<<<grid_for(nt, 256), 256, 0, st>>>(T.trg_key.as<uint64_t>(), nt, run, flag);
-    const int len_s = 256 * (int)((ns + RS_TILE - 1) / RS_TILE), len_t = 256 * (int)((nt + RS_TILE - 1) / RS_TILE);
-    KL k_deep_lens<<<1, 32, 0, st>>>(flag, len_s, len_t);
   }
-  rc = sort_finish(P, y, ns, dtype, T.d_src_off.as<int64_t>(), n_prob, flag, flag + 1, T.src_key, T.src_perm,
-                   T.s_keys2, T.s_vals2, T.src_pos);
-  if (!rc && !T.same)
-    rc = sort_finish(P, x, nt, dtype, T.d_trg_off.as<int64_t>(), n_prob, flag, flag + 2, T.trg_key, T.trg_perm,
-                     T.t_keys2, T.t_vals2, T.trg_pos);
-  if (rc) return rc;
-  // dense cell starts of the top levels (one problem): the refinement of levels 0 to
-  // DENSE_LV - 1 reads its child boundaries there instead of searching
   const bool dense = n_prob == 1;
-  if (dense) {
-    CK(T.dense_start.reserve(sizeof(int) * 2 * DENSE_N));
-    CK(cudaMemsetAsync(T.dense_start.p, 0x7f, sizeof(int) * (T.same ? 1 : 2) * DENSE_N, st));
-    if (ns > 0)
-      KL k_cell_starts<<<grid_for(ns, 256), 256, 0, st>>>(T.src_key.as<uint64_t>(), ns, T.dense_start.as<int>());
-    if (!T.same && nt > 0)
-      KL k_cell_starts<<<grid_for(nt, 256), 256, 0, st>>>(T.trg_key.as<uint64_t>(), nt,
-                                                        T.dense_start.as<int>() + DENSE_N);
-  }
 
   // per-level capacities: n_prob roots; below, min(n_prob 8^l, 8 * floor(N / (q + 1)) + 8)
   // (only a box with more than q points splits, into at most 8 children)
@@ -932,6 +1057,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   CK(T.bld_ctb.reserve(sizeof(int) * off * 9));
   CK(T.bld_cnt.reserve(sizeof(int) * (MAX_LEVELS + 8)));
   CK(T.bld_prob.reserve(sizeof(int) * off));
+  if (dense) CK(T.dense_start.reserve(sizeof(int) * 2 * DENSE_N));
   a.key = T.bld_key.as<uint64_t>();
   a.sb = T.bld_sb.as<int>();
   a.se = T.bld_se.as<int>();
@@ -957,36 +1083,97 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   a.dstart_t = dense ? T.dense_start.as<int>() + DENSE_N : nullptr;
   unsigned* status = T.status.as<unsigned>();
   int* d_total = a.cnt + MAX_LEVELS + 1;
-  KL k_root<<<grid_for(n_prob, 256), 256, 0, st>>>(a);
-  // levels in groups: the first covers the depth a uniform tree of these points would have
-  // (ceil(log8(points / q)) + 1 levels below the root), later ones 4 levels each; after each
-  // group every level's box count and the status are read back at once and the refinement
-  // stops when the next level is empty (a uniform tree of depth 4: one group, one read-back)
+
+  // cooperative refinement: blocks that fit on the GPU at once, at most two per SM
+  int coop_blocks = 0;
+  {
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine, 256, 0) == cudaSuccess)
+      coop_blocks = std::min(per_sm, 2) * nsm;
+    cudaGetLastError();
+  }
+  CK(T.bld_sync.reserve(sizeof(int) * (coop_blocks + 16)));
+
+  // The top-32-bit order suffices unless k_deep_check found a level-10 cell that would split;
+  // the flag is read back with the level counts, and then the points are sorted on all 60 bits
+  // and the tree is built again.
   int cnt[MAX_LEVELS + 1];
   unsigned h_status = 0;
-  int est = 1;
-  for (double m = (double)npts / (double)(P.q > 0 ? P.q : 1) / std::max(1, n_prob); m > 1.0 && est < MAX_LEVEL; m /= 8.0)
-    ++est;
-  for (int l0 = 0, group = est + 1;; group = 4) {
-    int l1 = std::min(MAX_LEVEL, l0 + group);
-    for (int l = l0; l < l1; ++l) {
-      int g = grid_for(a.cap[l], 256);
-      KL k_split<<<grid_for((int64_t)a.cap[l] * 32, 256), 256, 0, st>>>(a, l, status);
-      int* scratch = a.choff + a.cap_off[MAX_LEVELS] + 16;
-      scan_excl<int>(a.nch + a.cap_off[l], a.choff + a.cap_off[l], a.cap[l], a.cnt + l, scratch,
-                     d_total, st);
-      KL k_level_total<<<1, 32, 0, st>>>(a, l, d_total, status);
-      KL k_emit<<<g, 256, 0, st>>>(a, l);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (attempt == 1) {
+      KL k_clear_bits<<<1, 32, 0, st>>>(status, ST_OVERFLOW | ST_TIMEOUT);
+      sort_full(P, ns, T.src_key, T.src_perm, T.s_keys2, T.s_vals2);
+      if (!T.same) sort_full(P, nt, T.trg_key, T.trg_perm, T.t_keys2, T.t_vals2);
     }
-    CK(cudaMemcpyAsync(cnt, a.cnt, sizeof(int) * MAX_LEVELS, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    rc = sort_finish(P, y, ns, dtype, T.d_src_off.as<int64_t>(), n_prob, T.src_key, T.src_perm, T.s_keys2,
+                     T.s_vals2, T.src_pos);
+    if (!rc && !T.same)
+      rc = sort_finish(P, x, nt, dtype, T.d_trg_off.as<int64_t>(), n_prob, T.trg_key, T.trg_perm, T.t_keys2,
+                       T.t_vals2, T.trg_pos);
+    if (rc) return rc;
+    // dense cell starts of the top levels (one problem): the refinement of levels 0 to
+    // DENSE_LV - 1 reads its child boundaries there instead of searching
+    if (dense) {
+      CK(cudaMemsetAsync(T.dense_start.p, 0x7f, sizeof(int) * (T.same ? 1 : 2) * DENSE_N, st));
+      if (ns > 0)
+        KL k_cell_starts<<<grid_for(ns, 256), 256, 0, st>>>(T.src_key.as<uint64_t>(), ns, T.dense_start.as<int>());
+      if (!T.same && nt > 0)
+        KL k_cell_starts<<<grid_for(nt, 256), 256, 0, st>>>(T.trg_key.as<uint64_t>(), nt,
+                                                          T.dense_start.as<int>() + DENSE_N);
+    }
+    bool coop = false;
+    if (coop_blocks > 0) {
+      int* bsum = T.bld_sync.as<int>() + 16;
+      unsigned* sync = T.bld_sync.as<unsigned>();
+      CK(cudaMemsetAsync(sync, 0, sizeof(unsigned) * 2, st));
+      unsigned long long limit = P.wait.hard_ns;
+      void* args[] = {&a, &bsum, &sync, &status, &limit};
+      ++g_launches;
+      coop = cudaLaunchCooperativeKernel((const void*)k_refine, dim3(coop_blocks), dim3(256), args, 0, st) ==
+             cudaSuccess;
+      cudaGetLastError();
+    }
+    if (coop) {
+      CK(cudaMemcpyAsync(cnt, a.cnt, sizeof(int) * MAX_LEVELS, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    } else {
+      // levels in groups of launches: the first covers the depth a uniform tree of these points
+      // would have (ceil(log8(points / q)) + 1 levels below the root), later ones 4 levels
+      // each; after each group every level's box count and the status are read back at once
+      // and the refinement stops when the next level is empty
+      KL k_root<<<grid_for(n_prob, 256), 256, 0, st>>>(a);
+      int est = 1;
+      for (double m = (double)npts / (double)(P.q > 0 ? P.q : 1) / std::max(1, n_prob); m > 1.0 && est < MAX_LEVEL;
+           m /= 8.0)
+        ++est;
+      for (int l0 = 0, group = est + 1;; group = 4) {
+        int l1 = std::min(MAX_LEVEL, l0 + group);
+        for (int l = l0; l < l1; ++l) {
+          int g = grid_for(a.cap[l], 256);
+          KL k_split<<<grid_for((int64_t)a.cap[l] * 32, 256), 256, 0, st>>>(a, l, status);
+          int* scratch = a.choff + a.cap_off[MAX_LEVELS] + 16;
+          scan_excl<int>(a.nch + a.cap_off[l], a.choff + a.cap_off[l], a.cap[l], a.cnt + l, scratch, d_total, st);
+          KL k_level_total<<<1, 32, 0, st>>>(a, l, d_total, status);
+          KL k_emit<<<g, 256, 0, st>>>(a, l);
+        }
+        CK(cudaMemcpyAsync(cnt, a.cnt, sizeof(int) * MAX_LEVELS, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (l1 >= MAX_LEVEL || cnt[l1] == 0 || (h_status & (ST_DOMAIN | ST_OVERFLOW))) break;
+        l0 = l1;
+      }
+    }
+    int h_flag = 0;
+    CK(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (l1 >= MAX_LEVEL || cnt[l1] == 0 || (h_status & (ST_DOMAIN | ST_OVERFLOW))) break;
-    l0 = l1;
+    if (h_status & (ST_DOMAIN | ST_TIMEOUT)) break;
+    if (!h_flag || attempt == 1) break;
   }
   CK(cudaGetLastError());
   if (h_status & ST_DOMAIN)
     return fail(P, KAFMM_ERR_DOMAIN, "a point lies outside [origin, origin + L)^3 or is not finite");
+  if (h_status & ST_TIMEOUT) return fail(P, KAFMM_ERR_TIMEOUT, "octree refinement: a grid barrier timed out");
   if (h_status & ST_OVERFLOW) return fail(P, KAFMM_ERR_NOMEM, "octree level capacity exceeded");
 
   Layout lay;

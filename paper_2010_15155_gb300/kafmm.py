@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libkafmm.so")
 LAPLACE, STOKESLET, RPY, STOKES_DL, STOKES_REG, LAPLACE_QD, STOKES_PVEL = 0, 1, 2, 3, 4, 5, 6
 STOKES_PVEL_GRAD, STOKES_PVEL_LAPL, STOKES_PVEL_TRACTION = 7, 8, 9
 STOKES_DL_GRAD, STOKES_DL_LAPL, STOKES_DL_TRACTION = 10, 11, 12
+LAPLACE_QUAD = 13
 BC_OPEN, BC_PXYZ, BC_WALL = 0, 3, 4
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN, OPT_TC_SPLIT = 1, 2, 3, 4, 5, 6
@@ -32,7 +33,7 @@ PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 ML_G, ML_L4 = 0, 1
 KDIM = {LAPLACE: (1, 1), STOKESLET: (3, 3), RPY: (4, 6), STOKES_DL: (9, 4), STOKES_REG: (4, 3), LAPLACE_QD: (4, 10),
         STOKES_PVEL: (4, 4), STOKES_PVEL_GRAD: (4, 16), STOKES_PVEL_LAPL: (4, 7), STOKES_PVEL_TRACTION: (4, 9),
-        STOKES_DL_GRAD: (9, 16), STOKES_DL_LAPL: (9, 7), STOKES_DL_TRACTION: (9, 9)}
+        STOKES_DL_GRAD: (9, 16), STOKES_DL_LAPL: (9, 7), STOKES_DL_TRACTION: (9, 9), LAPLACE_QUAD: (9, 10)}
 ERRORS = {-1: "KAFMM_ERR_ARG", -2: "KAFMM_ERR_DOMAIN", -3: "KAFMM_ERR_CUDA",
           -4: "KAFMM_ERR_TIMEOUT", -5: "KAFMM_ERR_NOMEM", -6: "KAFMM_ERR_STATE"}
 

@@ -34,10 +34,11 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     lib.kafmm_last_error.restype = ctypes.c_char_p
     lib.kafmm_last_error.argtypes = [ctypes.c_void_p]
     out = ctypes.c_void_p(1)
-    # kernel out of range, PX boundary, p or q out of range, charges + dipoles (open boundary
-    # only) with the triply periodic boundary, and a derivative form with the wall
-    for args in [(13, 0, 8, 64), (-1, 0, 8, 64), (1, 1, 8, 64), (1, 0, 1, 64), (1, 0, 8, 0), (1, 0, 17, 64),
-                 (5, 3, 8, 64), (9, 4, 8, 64)]:
+    # kernel out of range, PX boundary, p or q out of range, charges + dipoles and quadrupoles
+    # (open boundary only) with the triply periodic boundary, and the wall with a derivative
+    # form or Laplace
+    for args in [(14, 0, 8, 64), (-1, 0, 8, 64), (1, 1, 8, 64), (1, 0, 1, 64), (1, 0, 8, 0), (1, 0, 17, 64),
+                 (5, 3, 8, 64), (13, 3, 8, 64), (9, 4, 8, 64), (0, 4, 8, 64)]:
         assert lib.kafmm_plan(*args, ctypes.byref(out)) == -1
         assert out.value is None
         assert len(lib.kafmm_last_error(None)) > 0
@@ -69,7 +70,7 @@ def test_python_constants_match_the_header():
             assert v == 0
         elif short in ("LAPLACE", "STOKESLET", "RPY", "STOKES_DL", "STOKES_REG", "LAPLACE_QD",
                        "STOKES_PVEL", "STOKES_PVEL_GRAD", "STOKES_PVEL_LAPL", "STOKES_PVEL_TRACTION",
-                       "STOKES_DL_GRAD", "STOKES_DL_LAPL", "STOKES_DL_TRACTION"):
+                       "STOKES_DL_GRAD", "STOKES_DL_LAPL", "STOKES_DL_TRACTION", "LAPLACE_QUAD"):
             assert getattr(kafmm, short) == v, name
             assert v in kafmm.KDIM, name
         else:

@@ -22,7 +22,8 @@ KERN = {"laplace": K.LAPLACE, "stokeslet": K.STOKESLET, "rpy": K.RPY, "stokes_dl
         "stokeslet_reg": K.STOKES_REG, "laplace_qd": K.LAPLACE_QD, "stokes_pvel": K.STOKES_PVEL,
         "stokes_pvel_grad": K.STOKES_PVEL_GRAD, "stokes_pvel_lapl": K.STOKES_PVEL_LAPL,
         "stokes_pvel_traction": K.STOKES_PVEL_TRACTION, "stokes_dl_grad": K.STOKES_DL_GRAD,
-        "stokes_dl_lapl": K.STOKES_DL_LAPL, "stokes_dl_traction": K.STOKES_DL_TRACTION}
+        "stokes_dl_lapl": K.STOKES_DL_LAPL, "stokes_dl_traction": K.STOKES_DL_TRACTION,
+        "laplace_quad": K.LAPLACE_QUAD}
 DERIV = ["stokes_pvel_grad", "stokes_pvel_lapl", "stokes_pvel_traction", "stokes_dl_grad", "stokes_dl_lapl",
          "stokes_dl_traction"]
 
@@ -105,7 +106,7 @@ def _near_oracle(kernel, pts, s, q):
 
 
 @pytest.mark.parametrize("kernel", ["laplace", "stokeslet", "rpy", "stokes_dl", "stokeslet_reg",
-                                    "laplace_qd", "stokes_pvel"] + DERIV)
+                                    "laplace_qd", "stokes_pvel", "laplace_quad"] + DERIV)
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_near_field_matches_oracle(kernel, prec):
     n, q = 3000, 50
@@ -134,6 +135,7 @@ def test_near_field_matches_oracle(kernel, prec):
     ("laplace_qd", "laplace_qd", K.ML_L4, 3000, 6, 40),
     ("stokes_dl_pv", "stokes_dl", K.ML_L4, 1500, 6, 40),
     ("stokes_pvel", "stokes_pvel", K.ML_L4, 1500, 6, 40),
+    ("laplace_quad", "laplace_quad", K.ML_L4, 3000, 6, 40),
 ] + [(k, k, K.ML_L4, 1500, 6, 40) for k in DERIV])
 def test_fp64_gpu_kafmm_matches_cpu_kafmm(problem, kernel, variant, n, p, q):
     if problem == "laplace":
@@ -202,7 +204,7 @@ def test_fp32_form_matches_fp64_form(kernel, variant):
 
 
 def test_errors_are_reported_not_trapped():
-    for kern in (K.LAPLACE_QD, K.STOKES_DL, K.STOKES_PVEL):   # open boundary only
+    for kern in (K.LAPLACE_QD, K.LAPLACE_QUAD):   # open boundary only
         with pytest.raises(K.KafmmError) as e:
             K.Plan(kern, p=4, q=32, bc=K.BC_PXYZ)
         assert e.value.code == -1

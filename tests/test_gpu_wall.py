@@ -7,6 +7,9 @@ over the sources and their images assembled at the targets.
   within the FMM error of the order (FP64) and within 1e-5 (mixed).
 * No slip: targets on the wall see a velocity at the level of the FMM error.
 * Points below the wall are rejected with KAFMM_ERR_DOMAIN.
+* RPY above the wall (four sums, Table tab:rpywall): FP64 form against the oracle's CPU KAFMM of
+  the four sums (1e-7), FP64 and mixed forms against the direct sums of the table (pinned to the
+  definition (1 + b^2/6 lap_y) G_wall f), including lap u; no slip.
 """
 import numpy as np
 import pytest
@@ -86,6 +89,60 @@ def test_wall_velocity_vanishes_on_the_wall():
     assert np.linalg.norm(g) < 1e-6 * np.linalg.norm(ga)
 
 
+def _upper_rpy(n, seed):
+    pts, f = _upper(n, seed)
+    b = np.random.default_rng(seed + 100).uniform(0.002, 0.006, (n, 1))
+    return pts, np.concatenate([f, b], axis=1)
+
+
+def _rpy_wall_eval(pts, fb, prec, p, q, trg=None):
+    dt = torch.float64 if prec == K.PREC_FP64 else torch.float32
+    plan = K.Plan(K.RPY, p=p, q=q, bc=K.BC_WALL, precision=prec)
+    plan.set_points(torch.from_numpy(pts).to(dt).cuda(),
+                    None if trg is None else torch.from_numpy(trg).to(dt).cuda())
+    g = plan.eval(torch.from_numpy(fb).to(dt).cuda()).double().cpu().numpy()
+    plan.close()
+    return g
+
+
+def test_rpy_wall_fp64_matches_cpu_kafmm_of_the_four_sums():
+    pts, fb = _upper_rpy(2000, 11)
+    p, q = 6, 40
+    yy = np.concatenate([pts, Wl.images(pts, 0.5)])
+    rpy, sd, sdz, quad = Wl.rpy_table_sources(pts, fb, 0.5)
+    lap = KAFMM("laplace_qd", p, q)
+    ref = Wl.rpy_assemble(pts, KAFMM("rpy_l4", p, q).evaluate(yy, rpy, trg=pts), lap.evaluate(yy, sd, trg=pts),
+                          lap.evaluate(yy, sdz, trg=pts), KAFMM("laplace_quad", p, q).evaluate(yy, quad, trg=pts),
+                          0.5)
+    g = _rpy_wall_eval(pts, fb, K.PREC_FP64, p, q)
+    assert D.rel_l2(g, ref) < 1e-7
+
+
+@pytest.mark.parametrize("prec,tol_u,tol_lap", [(K.PREC_FP64, 1e-6, 1e-5), (K.PREC_MIXED, 2e-5, 1e-4)])
+def test_rpy_wall_against_direct_four_sums(prec, tol_u, tol_lap):
+    """[u, lap u] against the table's direct sums on sampled targets, p = 10 (lap u, a second
+    derivative field, carries a larger FMM error)."""
+    pts, fb = _upper_rpy(40000, 12)
+    idx = np.arange(0, 40000, 40)
+    ref = Wl.rpy_table(pts[idx], pts, fb, 0.5)
+    g = _rpy_wall_eval(pts, fb, prec, 10, 64)[idx]
+    eu, el = D.rel_l2(g[:, :3], ref[:, :3]), D.rel_l2(g[:, 3:], ref[:, 3:])
+    print("rpy wall", prec, eu, el)
+    assert eu < tol_u and el < tol_lap
+
+
+def test_rpy_wall_velocity_vanishes_on_the_wall():
+    pts, fb = _upper_rpy(20000, 13)
+    rng = np.random.default_rng(14)
+    trg = rng.random((500, 3))
+    trg[:, 2] = 0.5
+    g = _rpy_wall_eval(pts, fb, K.PREC_FP64, 10, 64, trg=trg)
+    above = trg.copy()
+    above[:, 2] = 0.6
+    ga = _rpy_wall_eval(pts, fb, K.PREC_FP64, 10, 64, trg=above)
+    assert np.linalg.norm(g[:, :3]) < 1e-6 * np.linalg.norm(ga[:, :3])
+
+
 def test_points_below_the_wall_are_rejected():
     plan = K.Plan(K.STOKESLET, p=4, q=32, bc=K.BC_WALL, precision=K.PREC_FP64)
     bad = torch.tensor([[0.5, 0.5, 0.7], [0.2, 0.3, 0.4]], dtype=torch.float64, device="cuda")
@@ -94,5 +151,5 @@ def test_points_below_the_wall_are_rejected():
     assert e.value.code == -2
     plan.close()
     with pytest.raises(K.KafmmError) as e:
-        K.Plan(K.RPY, p=4, q=32, bc=K.BC_WALL)
+        K.Plan(K.LAPLACE, p=4, q=32, bc=K.BC_WALL)
     assert e.value.code == -1

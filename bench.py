@@ -49,9 +49,11 @@ WORKLOAD = "stokeslet_uniform_256k_p10_q128_l4"
 # pair in the leaf kernel (stk_st): 3 sub, r^2 (5), rsqrt, ir^3 (2), r.f (5), scale (1),
 # 3 x (mul + FMA + FMA = 5) -> 29.
 FLOP_ST_PAIR = 29
-# DRAM bytes (read + written) of one M->L launch of this workload in the mixed form, taken from
-# an ncu capture of the current kernel; None until the kernel in use has been captured
-M2L_DRAM_BYTES = None
+# DRAM bytes (read + written) of one M->L launch of this workload in the default mixed form
+# (compressed coordinates, rank rounded to 64, automatic split, tiles per parent neighbour),
+# from an ncu capture of the current kernel: 80.07 MB read + 224.42 MB written.  Reported only
+# for that configuration; None when the kernel changes until it is captured again.
+M2L_DRAM_BYTES = 304.49e6
 
 
 def _env_rank():
@@ -340,21 +342,25 @@ def run_gpu(args):
     st_ms = near_only_timing(plan, s, g, flush)
     peaks, src = _peaks()
     cnt = K.kafmm_get_counters(plan.h)
-    # dominant kernel: M->L.  Algorithmic flops per launch = V translations x 2 rows x k x 4
-    # channels: rows x k = r_dn x r_up in compressed coordinates (the singular values the two
-    # pseudo-inverses keep), n x n on check potentials.
+    # dominant kernel: M->L.  Algorithmic flops per launch = V translations x 2 n^2 x 4
+    # channels: the method's dense translation of an n-point check potential (the per-unit
+    # figure of the path); in compressed coordinates the kernel executes r_dn x r_up per
+    # translation instead (reported beside it, with the three split products and padding).
     n = 6 * (P_ORDER - 1) ** 2 + 2
+    m2l_flops = info["n_v"] * 2.0 * n * n * 4
     if cnt["compressed_rows"]:
-        m2l_flops = info["n_v"] * 2.0 * cnt["rank_dn"] * cnt["rank_up"] * 4
+        m2l_cmp = info["n_v"] * 2.0 * cnt["rank_dn"] * cnt["rank_up"] * 4
         m2l_exec = info["n_v"] * 2.0 * cnt["compressed_rows"] ** 2 * 4 * 3
-        coords = (f"compressed coordinates: {cnt['rank_dn']} x {cnt['rank_up']} per translation "
-                  f"(padded {cnt['compressed_rows']})")
+        coords = (f"executed in compressed coordinates: {cnt['rank_dn']} x {cnt['rank_up']} per "
+                  f"translation (padded {cnt['compressed_rows']})")
     else:
-        m2l_flops = info["n_v"] * 2.0 * n * n * 4
+        m2l_cmp = m2l_flops
         m2l_exec = info["n_v"] * 2.0 * n * ((n + 63) // 64 * 64) * 4 * 3
         coords = f"check potentials: {n} x {n} per translation"
     m2l_s = ph["m2l"] * 1e-3
     split_used = cnt["tc_split"]
+    default_m2l = (M2L_DRAM_BYTES is not None and args.precision == "mixed" and args.compress == 2 and
+                   args.tc_split == "auto" and cnt["m2l_tiling"] == "per parent neighbour")
     if args.precision == "mixed" and plan_uses_tc(plan):
         # achieved counts useful flops only (the three split products and the padding are not
         # counted); tf32x3 is measured against the TF32 MMA rate of kafmm_measure_peak
@@ -366,8 +372,11 @@ def run_gpu(args):
             peak = peaks["bf16_tflops"]
             pk = f"bf16 dense burst (cuBLAS), {src}"
         achieved = m2l_flops / m2l_s / 1e12
-        peak_note = (f"{split_used}: {pk}; useful flops ({coords}; split products not counted, "
-                     f"max frac 1/3); executed incl. padding {m2l_exec / m2l_s / 1e12:.0f} TFLOP/s")
+        peak_note = (f"{split_used}: {pk}; achieved = algorithmic flops (V translations x 2 x {n}^2 x 4, "
+                     f"the dense translation on check potentials) / M->L time; {coords}: "
+                     f"{m2l_cmp / m2l_s / 1e12:.0f} TFLOP/s useful, "
+                     f"{m2l_exec / m2l_s / 1e12:.0f} TFLOP/s executed with the three split products "
+                     f"and padding")
     elif args.precision == "fp64":
         bound, unit = "alu", "TFLOP/s"
         peak = mpk["fp64_fma_tflops"]
@@ -420,10 +429,10 @@ def run_gpu(args):
         "tree": info,
         "roofline": {"bound": bound, "kernel": "m2l", "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak,
-                     "traffic": M2L_DRAM_BYTES if args.precision == "mixed" else None,
+                     "traffic": M2L_DRAM_BYTES if default_m2l else None,
                      "traffic_source": "DRAM bytes of one M->L launch from an ncu capture of the "
-                                       "current kernel" if M2L_DRAM_BYTES else
-                                       "not captured for the current kernel",
+                                       "current kernel in this configuration" if default_m2l else
+                                       "not captured for this configuration",
                      "peak_source": peak_note},
         "e2e": {"value": world * N_POINTS / (e2e_ms * 1e-3) / 1e6, "unit": "Mpoints/s",
                 "h2d_bytes_per_step": int(pts.nbytes + f.nbytes),
@@ -616,27 +625,31 @@ def _timed_steps(step, plan, args, world, dev, stream, flush, local):
 
 
 def _m2l_roofline(K, plan, n_v, dense_rows, cols, m2l_ms):
-    """M->L roofline of a tensor-core plan: useful flops = V translations x 2 x rows x k x
-    columns, rows x k = r_dn x r_up in compressed coordinates, dense_rows^2 on check potentials;
-    peak: the measured BF16 burst, or the TF32 MMA rate kafmm_measure_peak measured."""
+    """M->L roofline of a tensor-core plan: achieved = algorithmic flops (V translations x 2 x
+    dense_rows^2 x columns: the dense translation on check potentials) / M->L time; the flops
+    executed in compressed coordinates (r_dn x r_up per translation) reported beside it; peak:
+    the measured BF16 burst, or the TF32 MMA rate kafmm_measure_peak measured."""
     peaks, src = _peaks()
     cnt = K.kafmm_get_counters(plan.h)
     split_used, tiling = cnt["tc_split"], cnt["m2l_tiling"]
+    flops = n_v * 2.0 * dense_rows * dense_rows * cols
+    s = m2l_ms * 1e-3
     if cnt["compressed_rows"]:
-        flops = n_v * 2.0 * cnt["rank_dn"] * cnt["rank_up"] * cols
-        coords = f"compressed coordinates {cnt['rank_dn']} x {cnt['rank_up']} (padded {cnt['compressed_rows']})"
+        cmp = n_v * 2.0 * cnt["rank_dn"] * cnt["rank_up"] * cols
+        note = (f"executed in compressed coordinates {cnt['rank_dn']} x {cnt['rank_up']} (padded "
+                f"{cnt['compressed_rows']}): {cmp / s / 1e12:.0f} TFLOP/s useful")
     else:
-        flops = n_v * 2.0 * dense_rows * dense_rows * cols
-        coords = f"check potentials {dense_rows} x {dense_rows}"
+        note = f"check potentials {dense_rows} x {dense_rows}"
     if split_used == "tf32x3":
         peak, pk = measured_peaks()["tf32_mma_tflops"], "tf32 tcgen05 MMA rate measured by kafmm_measure_peak"
     else:
         peak, pk = peaks["bf16_tflops"], f"bf16 dense burst (cuBLAS), {src}"
-    achieved = flops / (m2l_ms * 1e-3) / 1e12
+    achieved = flops / s / 1e12
     return split_used, {"bound": "tensor", "kernel": "m2l", "achieved": achieved, "peak": peak,
                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                        "peak_source": f"{split_used}: {pk}; useful flops ({coords}; split products not "
-                                       "counted, max frac 1/3)",
+                        "peak_source": f"{split_used}: {pk}; achieved = algorithmic flops (the dense "
+                                       f"translation, 2 x {dense_rows}^2 x {cols} per V entry) / M->L time; "
+                                       f"{note}",
                         "m2l_tiling": tiling}
 
 

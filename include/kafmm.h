@@ -124,7 +124,9 @@ typedef enum {
  *   u = (1 + b^2/6 lap_y) G_wall f, from four sums (Table tab:rpywall): an RPY sum of (f_12, b)
  *   at y and (-f_12, b) at the image, SD as above, SDZ plus the dipole (b^2/6)(0, 0, f_3) at y
  *   and at the image, and Laplace quadrupoles (b^2/3)[[f_3,0,0],[0,f_3,0],[f_1,f_2,0]] at the
- *   image (printed under "source at y"; at the image the assembly is the definition), with
+ *   image (printed under "source at y"; at the image the assembly is the definition; spheres
+ *   are expected to lie clear of the wall, h > b: the image terms grow like b^2 / h^3 and, in
+ *   the FP32 and mixed forms, the four sums then cancel to rounding), with
  *     u = u^S + grad phi^SDZ + x_3 grad(phi^SD + phi^Q) - [0, 0, phi^SD + phi^Q],
  *     lap u = lap u^S + 2 d_3 grad(phi^SD + phi^Q).
  *   The plan keeps child plans (Stokeslet or RPY, Laplace charges + dipoles, and for RPY
@@ -166,9 +168,9 @@ enum {
    * 4.7e-6..5.7e-6 for p = 6..10; BF16x3 4.2e-5 (p = 6), 1.1e-5 (p = 8), 6.6e-6 (p = 10),
    * 7e-6 against the direct sum at p = 12, at about 0.7x the time.  AUTO takes BF16x3 for
    * p >= 10 and TF32x3 below on check potentials; in compressed coordinates (KAFMM_OPT_COMPRESS)
-   * BF16x3 for p >= 8 up to 512 compressed rows and TF32x3 otherwise (the orthonormal projections
-   * keep BF16 rounding out of the directions the pseudo-inverses amplify: 512 Stokeslet
-   * problems at p = 8, worst problem 6.2e-6 against the FP64 form). */
+   * BF16x3 up to 512 compressed rows for p >= 10 and up to 256 rows for p = 8, 9, else TF32x3
+   * (the orthonormal projections keep BF16 rounding out of the directions the pseudo-inverses
+   * amplify: 512 Stokeslet problems at p = 8, worst problem 6.2e-6 against the FP64 form). */
   KAFMM_OPT_TC_SPLIT = 6,
   /* 1 (default): kafmm_eval synchronises the plan's stream before it returns and reports a
    * device-side timeout as KAFMM_ERR_TIMEOUT.  0: with device arrays kafmm_eval only enqueues

@@ -623,13 +623,18 @@ static int build_compressed(Plan& P, const double* O, const std::vector<double>&
   }
   sandwich(O + RR * OP_PER, PdT, PuT, CA + rr * CAUX_PER);
   CK(cudaGetLastError());
-  // split format: the plan's when chosen; the automatic choice takes BF16x3 for p >= 8 up to
-  // 512 compressed rows (512 Stokeslet problems at p = 8: worst problem 6.2e-6 against the FP64
-  // form, against 3.4e-6 with TF32x3, at 0.58x the M->L time) and TF32x3 otherwise (the
-  // Stokeslet G table at p = 12: BF16x3 measured 2.6e-5 against the Ewald sum on 2^22 periodic
-  // points, TF32x3 below 1e-5; below p = 8 the ranks are small and TF32x3 costs little)
+  // split format: the plan's when chosen; the automatic choice takes BF16x3 up to 512
+  // compressed rows for p >= 10 and up to 256 rows for p = 8, 9, else TF32x3.  Measured: 512
+  // Stokeslet problems at p = 8 (four-channel table, 192 rows) 6.2e-6 worst problem against the
+  // FP64 form with BF16x3 (3.4e-6 TF32x3) at 0.58x the M->L time; the periodic G table at p = 8
+  // (512 rows) 1.4e-5 against the FP32 form with BF16x3; the G table at p = 12 (640 rows) 2.6e-5
+  // against the Ewald sum on 2^22 periodic points with BF16x3, TF32x3 below 1e-5; below p = 8
+  // the ranks are small and TF32x3 costs little
   P.tc_split_cm = P.tc_split;
-  if (P.tc_split_opt == KAFMM_TC_AUTO) P.tc_split_cm = (rp > 512 || P.p < 8) ? SPLIT_TF32 : SPLIT_BF16;
+  if (P.tc_split_opt == KAFMM_TC_AUTO) {
+    const bool bf16 = (P.p >= 10 && rp <= 512) || (P.p >= 8 && rp <= 256);
+    P.tc_split_cm = bf16 ? SPLIT_BF16 : SPLIT_TF32;
+  }
   if (P.tc_split_cm == SPLIT_TF32) {
     CK(P.opstc_cm2l.reserve(sizeof(float) * 2 * rr * N_M2L));
     KL k_split_tf32<<<2048, 256, 0, st>>>(C, rp, rp, rp, rp, N_M2L, P.opstc_cm2l.as<float>());

@@ -611,13 +611,17 @@ __device__ inline void far_eval(T xl, T yl, T zl, const typename V4<T>::type& p,
   }
 }
 
-// Targets per thread of the leaf kernel: two in the FP32 form for tables of at most six
-// outputs (each staged source or equivalent point then feeds two targets), one otherwise.
+// Targets per thread of the leaf kernel: in the FP32 form four for the Stokeslet (each staged
+// source or equivalent point then feeds four independent pair evaluations), two for the other
+// tables of at most six outputs, one otherwise.
 template <class T, int PR>
-struct LeafTT { static constexpr int V = (sizeof(T) == 4 && ProbInfo<PR>::KT <= 6) ? 2 : 1; };
+struct LeafTT {
+  static constexpr int V = sizeof(T) != 4 ? 1 : ((PR == P_STK_L4 || PR == P_STK_G) ? 4 : (ProbInfo<PR>::KT <= 6 ? 2 : 1));
+};
 
 // Leaf kernel, one block per target leaf.  Work split: a pass takes up to LEAF_THREADS x tt
-// targets (tt = 2 when the leaf holds more than 16 and the table allows it); its targets are
+// targets (tt = 4 when the leaf holds more than 32 and the table allows it, 2 when it holds more
+// than 16); its targets are
 // dealt to S slots of tt targets each, and the G = LEAF_THREADS / S threads of a slot (lane-major:
 // consecutive lanes) split the sources of every interaction list among themselves; the G
 // partial sums of a target are combined by warp shuffles when G divides 32, else through
@@ -659,7 +663,7 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
     __syncthreads();
     if (bail) return;
   }
-  const int tt = (TT == 2 && nt > 16) ? 2 : 1;
+  const int tt = (TT == 4 && nt > 32) ? 4 : ((TT >= 2 && nt > 16) ? 2 : 1);
   const int per_pass = min(nt, LEAF_THREADS * tt);
   const int S = (per_pass + tt - 1) / tt;            // slots
   const int G = max(1, LEAF_THREADS / S);            // threads per slot
@@ -864,11 +868,18 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
                 ye[u] = yg[u] - (float)(sy * a.geo.L);
                 ze[u] = zg[u] - (float)(sz * a.geo.L);
               }
-              if (tt == 2) {
+              if (TT == 4 && tt == 4) {
+                for (int j = grp; j < cnt; j += G) {
+                  const float4 y = bp[base + j], f = bv[base + j];
+#pragma unroll
+                  for (int u = 0; u < TT; ++u) stk_pair_f32(xe[u], ye[u], ze[u], y, f, pe[u]);
+                }
+              } else if (TT >= 2 && tt == 2) {
+                constexpr int U1 = TT >= 2 ? 1 : 0;
                 for (int j = grp; j < cnt; j += G) {
                   const float4 y = bp[base + j], f = bv[base + j];
                   stk_pair_f32(xe[0], ye[0], ze[0], y, f, pe[0]);
-                  stk_pair_f32(xe[TT - 1], ye[TT - 1], ze[TT - 1], y, f, pe[TT - 1]);
+                  stk_pair_f32(xe[U1], ye[U1], ze[U1], y, f, pe[U1]);
                 }
               } else {
                 int j = grp;

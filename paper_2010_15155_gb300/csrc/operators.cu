@@ -73,6 +73,44 @@ __global__ void k_fill_kernel_matrix(const double* __restrict__ unit, int n, int
   }
 }
 
+// Batch of M->L kernel matrices, one per blockIdx.z: K_z = K(dc of the box at the origin <- ue of
+// the box whose centre is 2 offs[z] away), the layout of k_fill_kernel_matrix, K_z at K + z sK.
+__global__ void k_fill_m2l_batch(const double* __restrict__ unit, int n, int stokes, double at, double as,
+                                 const int* __restrict__ offs, double* __restrict__ K, int64_t sK) {
+  const int z = blockIdx.z;
+  const double csx = 2.0 * offs[3 * z], csy = 2.0 * offs[3 * z + 1], csz = 2.0 * offs[3 * z + 2];
+  double* Kz = K + z * sK;
+  int R = stokes == 2 ? 4 * n : (stokes ? 3 * n : n);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / n), j = (int)(e % n);
+    double r0 = (at * unit[3 * i]) - (csx + as * unit[3 * j]);
+    double r1 = (at * unit[3 * i + 1]) - (csy + as * unit[3 * j + 1]);
+    double r2 = (at * unit[3 * i + 2]) - (csz + as * unit[3 * j + 2]);
+    double rr = r0 * r0 + r1 * r1 + r2 * r2;
+    double rn = sqrt(rr);
+    if (!stokes) {
+      Kz[(int64_t)i * R + j] = 1.0 / (4.0 * PI * rn);
+    } else if (stokes == 2) {
+      double r[3] = {r0, r1, r2};
+      double inv = 1.0 / (8.0 * PI * rn), inv3 = inv / rr;
+      for (int b = 0; b < 3; ++b) Kz[(int64_t)(4 * i) * R + 4 * j + b] = 2.0 * r[b] * inv3;
+      Kz[(int64_t)(4 * i) * R + 4 * j + 3] = 0.0;
+      for (int a2 = 0; a2 < 3; ++a2) {
+        for (int b = 0; b < 3; ++b)
+          Kz[(int64_t)(4 * i + 1 + a2) * R + 4 * j + b] = (a2 == b ? inv : 0.0) + r[a2] * r[b] * inv3;
+        Kz[(int64_t)(4 * i + 1 + a2) * R + 4 * j + 3] = -r[a2] * inv3;
+      }
+    } else {
+      double r[3] = {r0, r1, r2};
+      double inv = 1.0 / (8.0 * PI * rn), inv3 = inv / rr;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+          Kz[(int64_t)(3 * i + a) * R + 3 * j + b] = (a == b ? inv : 0.0) + r[a] * r[b] * inv3;
+    }
+  }
+}
+
 // Multiplies every 4th row (rows = 1, starting at first) or column (rows = 0) of the R x R
 // matrix K by f: the StokesPVel p rows or q columns.
 __global__ void k_scale_every4(double* __restrict__ K, int R, int rows, int first, double f) {
@@ -250,8 +288,12 @@ __global__ void k_pinv_weights(double* w, int n, double rcond) {
 
 // C = alpha * op(A) * diag(w) * B with op(A) = A^T when ta (A stored [k][i]) else A ([i][k]).
 // Plain 32x32-tiled FP64 GEMM; n x n x n.
+// Batched over blockIdx.z: A_z = A + z sA, C_z = Cm + (cidx ? cidx[z] : z) sC (B shared).
 __global__ void k_gemm64(const double* __restrict__ A, int ta, const double* __restrict__ w,
-                         const double* __restrict__ B, double alpha, int n, double* __restrict__ Cm) {
+                         const double* __restrict__ B, double alpha, int n, double* __restrict__ Cm,
+                         int64_t sA = 0, int64_t sC = 0, const int* __restrict__ cidx = nullptr) {
+  A += blockIdx.z * sA;
+  Cm += (cidx ? cidx[blockIdx.z] : (int)blockIdx.z) * sC;
   __shared__ double As[32][33], Bs[32][33];
   int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
   int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
@@ -422,9 +464,13 @@ __global__ void k_split_bf16(const double* in, int rows, int cols, int ld, int c
 // General FP64 GEMM, C[M][N] (row stride ldc) = alpha op(A) op(B), op(A)[i][k] = A[i lda + k]
 // (ta = 0) or A[k lda + i] (ta = 1), op(B)[k][j] = B[k ldb + j] (tb = 0) or B[j ldb + k].
 // 32 x 32 tiles; plan time only.
+// Batched over blockIdx.z: A, B and Cm advance by sA, sB and sC per batch index.
 __global__ void k_gemm64g(const double* __restrict__ A, int lda, int ta, const double* __restrict__ B,
                           int ldb, int tb, double* __restrict__ Cm, int ldc, int M, int N, int K,
-                          double alpha) {
+                          double alpha, int64_t sA = 0, int64_t sB = 0, int64_t sC = 0) {
+  A += blockIdx.z * sA;
+  B += blockIdx.z * sB;
+  Cm += blockIdx.z * sC;
   __shared__ double As[32][33], Bs[32][33];
   int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
   int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
@@ -578,7 +624,7 @@ static int build_compressed(Plan& P, const double* O, const std::vector<double>&
   const int rp = std::max(64, (std::max(ru, rd) + 63) / 64 * 64);
   if (rp >= P.Rpad) return 0;   // nothing to gain: keep the dense coordinates
   const size_t rr = (size_t)rp * rp, rR = (size_t)rp * R;
-  DevBuf d_idx, d_sc, cin, cout, cops, X;
+  DevBuf d_idx, d_sc, cin, cout, cops, X, Xb;
   CK(d_idx.reserve(sizeof(int) * 2 * R));
   CK(d_sc.reserve(sizeof(double) * 4 * R));
   CK(cin.reserve(sizeof(double) * 2 * rR));     // U_u^T, U_d^T  [rp][R] each
@@ -608,13 +654,17 @@ static int build_compressed(Plan& P, const double* O, const std::vector<double>&
                                                                        dst, rp, rp, rp, R, 1.0);
   };
   double* C = cops.as<double>();
-  for (int o = 0; o < N_M2L; ++o) {
-    int ox = o % 7 - 3, oy = (o / 7) % 7 - 3, oz = o / 49 - 3;
-    if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) {
-      CK(cudaMemsetAsync(C + rr * o, 0, sizeof(double) * rr, st));
-      continue;
+  {   // the M->L operators in batches (the near offsets are zero and stay zero): X_z = T_z Pu,
+      // C_z = Pd^T X_z, one pair of launches per batch
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(N_M2L, (int64_t)(1.0e9 / (8.0 * R * rp))));
+    CK(Xb.reserve(sizeof(double) * (size_t)chunk * R * rp));
+    for (int o0 = 0; o0 < N_M2L; o0 += chunk) {
+      const int nbt = std::min(chunk, N_M2L - o0);
+      KL k_gemm64g<<<dim3((rp + 31) / 32, (R + 31) / 32, nbt), 256, 0, st>>>(
+          O + RR * (OP_M2L + o0), R, 0, PuT, R, 1, Xb.as<double>(), rp, R, rp, R, 1.0, RR, 0, (int64_t)R * rp);
+      KL k_gemm64g<<<dim3((rp + 31) / 32, (rp + 31) / 32, nbt), 256, 0, st>>>(
+          PdT, R, 0, Xb.as<double>(), rp, 0, C + rr * o0, rp, rp, rp, R, 1.0, 0, (int64_t)R * rp, rr);
     }
-    sandwich(O + RR * (OP_M2L + o), PdT, PuT, C + rr * o);
   }
   double* CA = C + rr * N_M2L;
   for (int c = 0; c < 8; ++c) {
@@ -696,20 +746,45 @@ int build_operators(Plan& P) {
     KL k_gemm64<<<gg, 256, 0, st>>>(K, 0, nullptr, O + RR * f2, 1.0, R, Tm);
     KL k_gemm64<<<gg, 256, 0, st>>>(Tm, 0, nullptr, O + RR * f1, alpha, R, dst);
   };
-  // M->L: centres 2 o apart (box side 2)
-  for (int oz = -3; oz <= 3; ++oz)
-    for (int oy = -3; oy <= 3; ++oy)
-      for (int ox = -3; ox <= 3; ++ox) {
-        int idx = m2l_index(ox, oy, oz);
-        double* dst = O + RR * (OP_M2L + idx);
-        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) {
-          CK(cudaMemsetAsync(dst, 0, sizeof(double) * RR, st));
-          continue;
+  // M->L: centres 2 o apart (box side 2); the 27 near offsets are zero; the other 316 in
+  // batches (kernel matrices of a batch filled by one launch, composed by two batched GEMMs)
+  {
+    std::vector<int> offs, dsti;
+    for (int oz = -3; oz <= 3; ++oz)
+      for (int oy = -3; oy <= 3; ++oy)
+        for (int ox = -3; ox <= 3; ++ox) {
+          const int idx = m2l_index(ox, oy, oz);
+          if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) {
+            CK(cudaMemsetAsync(O + RR * (OP_M2L + idx), 0, sizeof(double) * RR, st));
+            continue;
+          }
+          offs.push_back(ox);
+          offs.push_back(oy);
+          offs.push_back(oz);
+          dsti.push_back(OP_M2L + idx);
         }
-        KL k_fill_kernel_matrix<<<g, 256, 0, st>>>(unit, n, stokes, 0, 0, 0, ALPHA_DC, 2.0 * ox, 2.0 * oy,
-                                                2.0 * oz, ALPHA_UE, K);
-        compose(OP_UP1, OP_UP2, 1.0, dst);
-      }
+    const int nall = (int)dsti.size();
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(nall, (int64_t)(1.0e9 / (16.0 * RR))));
+    DevBuf kb, tb, tab;
+    CK(kb.reserve(sizeof(double) * (size_t)chunk * RR));
+    CK(tb.reserve(sizeof(double) * (size_t)chunk * RR));
+    CK(tab.reserve(sizeof(int) * 4 * (size_t)nall));
+    int* d_offs = tab.as<int>();
+    int* d_dst = d_offs + 3 * nall;
+    CK(cudaMemcpyAsync(d_offs, offs.data(), sizeof(int) * 3 * nall, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_dst, dsti.data(), sizeof(int) * nall, cudaMemcpyHostToDevice, st));
+    for (int c0 = 0; c0 < nall; c0 += chunk) {
+      const int nbt = std::min(chunk, nall - c0);
+      KL k_fill_m2l_batch<<<dim3(g, 1, nbt), 256, 0, st>>>(unit, n, stokes, ALPHA_DC, ALPHA_UE, d_offs + 3 * c0,
+                                                           kb.as<double>(), RR);
+      // Op = (K V) (S^+ U^T), the compose() of one operator for every z of the batch
+      dim3 gb(gg.x, gg.y, nbt);
+      KL k_gemm64<<<gb, 256, 0, st>>>(kb.as<double>(), 0, nullptr, O + RR * OP_UP2, 1.0, R, tb.as<double>(), RR, RR,
+                                    nullptr);
+      KL k_gemm64<<<gb, 256, 0, st>>>(tb.as<double>(), 0, nullptr, O + RR * OP_UP1, 1.0, R, O, RR, RR, d_dst + c0);
+    }
+    CK(cudaStreamSynchronize(st));   // the batch buffers are released on leaving this scope
+  }
   // M->M / L->L: child half-width 1, parent half-width 2, child centre at +-1 per axis
   for (int c = 0; c < 8; ++c) {
     double cx = (c & 1) ? 1.0 : -1.0, cy = (c & 2) ? 1.0 : -1.0, cz = (c & 4) ? 1.0 : -1.0;

@@ -8,8 +8,11 @@
 //   r <= |a-b|       :  M = I / (6 pi max(a, b))
 // i.e. the pass adds (M_overlap - M_far) f for those pairs (M_far = 0 at r = 0, as the sum
 // skips coincident pairs).  With the contact split (FP32 forms, one shared point set) the near
-// field leaves out its pairs within r <= b_i + b_j and this pass adds their whole mobility.  Neighbours come from a dense cell table at a grid level whose cell
-// side is at least a_max + b_max, so every contact partner lies in the 27 surrounding cells.
+// field leaves out its pairs within r <= b_i + b_j and this pass adds their whole mobility.
+// Neighbours come from a dense cell table at a grid level whose cell side is at least the contact
+// reach (max(a_max, b_max) + b_max) divided by H, so every contact partner lies in the (2H + 1)^3
+// surrounding cells; H = 2 where the grid allows it (about half the candidate pairs of H = 1 in
+// dense clusters), and cells farther from the target than the reach are skipped.
 #include <cuda.h>
 
 #include <algorithm>
@@ -160,8 +163,10 @@ __global__ void k_rpy_velocity(const typename V4<T>::type* __restrict__ spos,
                                const typename V4<T>::type* __restrict__ tpos, const T* __restrict__ ta,
                                const uint64_t* __restrict__ tkey, const uint32_t* __restrict__ tperm,
                                int64_t nt, const int* __restrict__ cbeg, const int* __restrict__ cend, int g,
-                               int periodic, double L, int same, const Tio* __restrict__ gin,
-                               Tio* __restrict__ ua, ContactInfo ci) {
+                               int H, double reach, double ox0, double oy0, double oz0, int periodic,
+                               double L, int same, const Tio* __restrict__ gin, Tio* __restrict__ ua,
+                               ContactInfo ci) {
+  const int W = 2 * H + 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
        i += (int64_t)gridDim.x * blockDim.x) {
     typename V4<T>::type x = tpos[i];
@@ -170,9 +175,23 @@ __global__ void k_rpy_velocity(const typename V4<T>::type* __restrict__ spos,
     uint64_t ck = tkey[i] >> (3 * (MAX_LEVEL - g));
     int cx = (int)compact3(ck), cy = (int)compact3(ck >> 1), cz = (int)compact3(ck >> 2);
     int n = 1 << g;
+    const double side = L / (double)n;
+    // the target in cell units, relative to its own cell's low corner (cells farther than the
+    // reach, taken with a margin, hold no contact partner)
+    const double fx = ((double)x.x - ox0) / side - cx, fy = ((double)x.y - oy0) / side - cy,
+                 fz = ((double)x.z - oz0) / side - cz;
+    const double rc = reach / side * (1.0 + 1e-6) + 1e-6;
     T acc[3] = {0, 0, 0};
-    for (int d = 0; d < 27; ++d) {
-      int qx = cx + d % 3 - 1, qy = cy + (d / 3) % 3 - 1, qz = cz + d / 9 - 1;
+    for (int d = 0; d < W * W * W; ++d) {
+      const int ddx = d % W - H, ddy = (d / W) % W - H, ddz = d / (W * W) - H;
+      if (H > 1) {   // distance from the target to the neighbour cell's box, in cell units
+        const double ex = ddx > 0 ? ddx - fx : (ddx < 0 ? fx - (ddx + 1) : 0.0);
+        const double ey = ddy > 0 ? ddy - fy : (ddy < 0 ? fy - (ddy + 1) : 0.0);
+        const double ez = ddz > 0 ? ddz - fz : (ddz < 0 ? fz - (ddz + 1) : 0.0);
+        const double mx = ex > 0 ? ex : 0.0, my = ey > 0 ? ey : 0.0, mz = ez > 0 ? ez : 0.0;
+        if (mx * mx + my * my + mz * mz > rc * rc) continue;
+      }
+      int qx = cx + ddx, qy = cy + ddy, qz = cz + ddz;
       int sx = 0, sy = 0, sz = 0;
       if (qx < 0 || qx >= n || qy < 0 || qy >= n || qz < 0 || qz >= n) {
         if (!periodic) continue;
@@ -264,9 +283,20 @@ int run(Plan& P, const void* s, const void* a, const void* g, void* ua, int dtyp
   memcpy(&amax, &h[0], 4);
   memcpy(&bmax, &h[1], 4);
   double reach = (std::max((double)amax, (double)bmax) + (double)bmax) * (1.0 + 1e-6) / P.L;
-  int lev = 0;
-  while (lev < 8 && reach > 0 && 1.0 / (double)(1 << (lev + 1)) >= reach) ++lev;
-  if (reach <= 0) lev = 8;
+  // cells of at least half the reach and a 5^3 stencil where the grid has at least 5 cells per
+  // side (level <= 8), else cells of at least the reach and 3^3
+  int lev = 0, H = 1;
+  while (lev < 8 && reach > 0 && 1.0 / (double)(1 << (lev + 1)) >= 0.5 * reach) ++lev;
+  if (reach > 0 && lev >= 3 && 1.0 / (double)(1 << lev) >= 0.5 * reach) {
+    H = 2;
+  } else {
+    lev = 0;
+    while (lev < 8 && reach > 0 && 1.0 / (double)(1 << (lev + 1)) >= reach) ++lev;
+  }
+  if (reach <= 0) {
+    lev = 8;
+    H = 1;
+  }
   int64_t ncell = 1ll << (3 * lev);
   CK(cb.reserve(sizeof(int) * ncell));
   CK(ce.reserve(sizeof(int) * ncell));
@@ -279,12 +309,14 @@ int run(Plan& P, const void* s, const void* a, const void* g, void* ua, int dtyp
   if (nt > 0) {
     if (dtype == KAFMM_F64)
       KL k_rpy_velocity<T, double><<<grid_for(nt, 128), 128, 0, st>>>(
-          spos, fb.as<T4>(), tpos, ta.as<T>(), tkey, tperm, nt, cb.as<int>(), ce.as<int>(), lev,
-          P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const double*)g, (double*)ua, contact_info(P));
+          spos, fb.as<T4>(), tpos, ta.as<T>(), tkey, tperm, nt, cb.as<int>(), ce.as<int>(), lev, H, reach * P.L,
+          P.origin[0], P.origin[1], P.origin[2], P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const double*)g,
+          (double*)ua, contact_info(P));
     else
       KL k_rpy_velocity<T, float><<<grid_for(nt, 128), 128, 0, st>>>(
-          spos, fb.as<T4>(), tpos, ta.as<T>(), tkey, tperm, nt, cb.as<int>(), ce.as<int>(), lev,
-          P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const float*)g, (float*)ua, contact_info(P));
+          spos, fb.as<T4>(), tpos, ta.as<T>(), tkey, tperm, nt, cb.as<int>(), ce.as<int>(), lev, H, reach * P.L,
+          P.origin[0], P.origin[1], P.origin[2], P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const float*)g,
+          (float*)ua, contact_info(P));
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
@@ -418,12 +450,12 @@ int run_noalloc(Plan& P, const void* s, const void* a, const void* g, void* ua, 
   if (nt > 0) {
     if (dtype == KAFMM_F64)
       KL k_rpy_velocity<T, double><<<grid_for(nt, 128), 128, 0, st>>>(
-          spos, fb, tpos, ta, tkey, tperm, nt, cb, ce, lev, P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0,
-          (const double*)g, (double*)ua, contact_info(P));
+          spos, fb, tpos, ta, tkey, tperm, nt, cb, ce, lev, 1, reach * P.L, P.origin[0], P.origin[1], P.origin[2],
+          P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const double*)g, (double*)ua, contact_info(P));
     else
       KL k_rpy_velocity<T, float><<<grid_for(nt, 128), 128, 0, st>>>(
-          spos, fb, tpos, ta, tkey, tperm, nt, cb, ce, lev, P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0,
-          (const float*)g, (float*)ua, contact_info(P));
+          spos, fb, tpos, ta, tkey, tperm, nt, cb, ce, lev, 1, reach * P.L, P.origin[0], P.origin[1], P.origin[2],
+          P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const float*)g, (float*)ua, contact_info(P));
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));

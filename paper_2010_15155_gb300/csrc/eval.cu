@@ -798,7 +798,9 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
           bulk_g2s(dv + used * NV, a.sval + (int64_t)s0 * NV, (uint32_t)(take * NV * sizeof(T4)), &bar[bf]);
           bytes += (uint32_t)(take * (1 + NV) * sizeof(T4));
           ent_cnt[bf][ne] = take;
-          ent_sc[bf][ne] = entry_shift(ent);
+          // the shift code (0..26), plus 32 for the target leaf's own unshifted sources (the
+          // only entry that can hold a target's own point, r = 0)
+          ent_sc[bf][ne] = entry_shift(ent) + ((sbx == b && entry_shift(ent) == 13) ? 32 : 0);
           ++ne;
           used += take;
         }
@@ -847,7 +849,8 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
         int base = 0;
         for (int e = 0; e < ent_n[bf]; ++e) {
           int sx, sy, sz;
-          shift_decode(ent_sc[bf][e], sx, sy, sz);
+          const bool self_ent = ent_sc[bf][e] >= 32;
+          shift_decode(ent_sc[bf][e] & 31, sx, sy, sz);
           const T ox = (T)(sx * a.geo.L) - cx, oy = (T)(sy * a.geo.L) - cy, oz = (T)(sz * a.geo.L) - cz;
           const int cnt = ent_cnt[bf][e];
           T pe[TT][KT];  // partial sums of this entry (plain mode)
@@ -869,10 +872,18 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(LeafArgs<T, PR> a) {
                 ze[u] = zg[u] - (float)(sz * a.geo.L);
               }
               if (TT == 4 && tt == 4) {
-                for (int j = grp; j < cnt; j += G) {
-                  const float4 y = bp[base + j], f = bv[base + j];
+                if (self_ent) {
+                  for (int j = grp; j < cnt; j += G) {
+                    const float4 y = bp[base + j], f = bv[base + j];
 #pragma unroll
-                  for (int u = 0; u < TT; ++u) stk_pair_f32(xe[u], ye[u], ze[u], y, f, pe[u]);
+                    for (int u = 0; u < TT; ++u) stk_pair_f32<true>(xe[u], ye[u], ze[u], y, f, pe[u]);
+                  }
+                } else {
+                  for (int j = grp; j < cnt; j += G) {
+                    const float4 y = bp[base + j], f = bv[base + j];
+#pragma unroll
+                    for (int u = 0; u < TT; ++u) stk_pair_f32<false>(xe[u], ye[u], ze[u], y, f, pe[u]);
+                  }
                 }
               } else if (TT >= 2 && tt == 2) {
                 constexpr int U1 = TT >= 2 ? 1 : 0;

@@ -96,12 +96,14 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
 }
 
 // One Stokeslet pair in FP32 accumulated into acc[0..2] (scaled by 1/(8 pi) at the end):
-// acc += f / r + r (r.f) / r^3 with r = x - y; zero for r = 0.
+// acc += f / r + r (r.f) / r^3 with r = x - y; zero for r = 0.  GUARD = false where r = 0
+// cannot occur (sources of another box, or of an image of the target's box: distinct points).
+template <bool GUARD = true>
 __device__ __forceinline__ void stk_pair_f32(float xe, float ye, float ze, const float4& y,
                                              const float4& f, float* acc) {
   float r0 = xe - y.x, r1 = ye - y.y, r2 = ze - y.z;
   float rr = fmaf(r0, r0, fmaf(r1, r1, r2 * r2));
-  float ir = rr > 0.f ? rsqrt_ftz(rr) : 0.f;
+  float ir = GUARD ? (rr > 0.f ? rsqrt_ftz(rr) : 0.f) : rsqrt_ftz(rr);
   float rf = fmaf(r0, f.x, fmaf(r1, f.y, r2 * f.z)) * (ir * ir * ir);
   acc[0] = fmaf(r0, rf, fmaf(f.x, ir, acc[0]));
   acc[1] = fmaf(r1, rf, fmaf(f.y, ir, acc[1]));

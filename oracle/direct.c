@@ -795,3 +795,67 @@ void orc_stokeslet_wall(const double* x, int64_t nt, const double* y, int64_t ns
     for (int i = 0; i < 3; ++i) g[3 * a + i] += acc[i] / (8.0 * PI);
   }
 }
+
+/* ---------------------------------------------------------------------------------------
+ * Singly and doubly periodic image sums (Sec. III.B, boundaries PX and PXY): the kernel
+ * matrix summed over the images n L of a 1D lattice (axes = 1: n = (a, 0, 0)) or a 2D
+ * lattice (axes = 2: n = (a, b, 0)), taken in square shells max|n| = s for s from nmin up,
+ * with the partial sums S_N over nmin <= max|n| <= N written out for N = n0 2^k, k < nlev
+ * (the caller extrapolates N -> infinity).  kernel 0: Laplace 1/(4 pi r), 1 x 1 blocks;
+ * kernel 1: Stokeslet (delta_ij / r + r_i r_j / r^3) / (8 pi), 3 x 3 blocks.
+ * out[k][kt nt][kt ns] (row: target a, output component i; column: source b, component j).
+ * Pairs at zero distance are skipped.
+ * ------------------------------------------------------------------------------------- */
+static void lattice_pair(int kernel, const double r[3], double* m) {
+  const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  if (rr == 0.0) return;
+  const double rn = sqrt(rr);
+  if (kernel == 0) {
+    m[0] += 1.0 / (4.0 * PI * rn);
+    return;
+  }
+  const double r3 = rr * rn;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) m[3 * i + j] += ((i == j ? 1.0 / rn : 0.0) + r[i] * r[j] / r3) / (8.0 * PI);
+}
+
+void orc_lattice_matrix(int kernel, int axes, const double* x, int64_t nt, const double* y,
+                        int64_t ns, double L, int nmin, int n0, int nlev, double* out) {
+  const int kt = kernel == 0 ? 1 : 3;
+  const int64_t rows = kt * nt, cols = kt * ns;
+  const int nmax = n0 << (nlev - 1);
+#pragma omp parallel for collapse(2) schedule(dynamic, 8)
+  for (int64_t a = 0; a < nt; ++a)
+    for (int64_t b = 0; b < ns; ++b) {
+      double m[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      int lev = 0;
+      for (int s = nmin; s <= nmax; ++s) {
+        /* the images of shell s: (+-s, 0) for the 1D lattice; the square ring max(|i|,|j|) = s
+         * for the 2D lattice (rows j = +-s, then columns i = +-s between them) */
+        int cnt = axes == 1 ? 2 : 8 * s;
+        for (int e = 0; e < cnt; ++e) {
+          int i, j;
+          if (axes == 1) {
+            i = e == 0 ? -s : s;
+            j = 0;
+          } else if (e < 2 * (2 * s + 1)) {
+            i = -s + e % (2 * s + 1);
+            j = e < 2 * s + 1 ? -s : s;
+          } else {
+            int e2 = e - 2 * (2 * s + 1);
+            i = e2 % 2 == 0 ? -s : s;
+            j = -s + 1 + e2 / 2;
+          }
+          double r[3] = {x[3 * a] - y[3 * b] - i * L, x[3 * a + 1] - y[3 * b + 1] - j * L,
+                         x[3 * a + 2] - y[3 * b + 2]};
+          lattice_pair(kernel, r, m);
+        }
+        if (s == (n0 << lev)) {
+          for (int p = 0; p < kt; ++p)
+            for (int q = 0; q < kt; ++q)
+              out[(int64_t)lev * rows * cols + (kt * a + p) * cols + kt * b + q] = m[kt * p + q];
+          ++lev;
+        }
+      }
+    }
+}

@@ -27,6 +27,8 @@ Readings of points the paper leaves open:
       lap u_i = - d_i d_j phi_j.
   The RPY source term (b^2/6) lap G f adds a Laplace dipole (b^2/3) f to channel 4.  Moving
   a representation from reference c to c' adds (c - c') . q_{1:3} to channel 4.
+* Singly and doubly periodic (``bc='px'``, ``'pxy'``): as below with the lattice of images
+  along x (and y) and its far-image operator from ``oracle.lattice`` (neutral sources).
 * Periodic (``bc='pxyz'``): the tree covers the source images with shift in {-1,0,1}^3 (lists
   with wrap, ``oracle.tree``); all farther images enter through one operator T_M2L applied to
   the root's multipole density and added to the root's downward check potential.  For the
@@ -58,6 +60,9 @@ import numpy as np
 
 from . import direct as D
 from .tree import Tree
+
+# periodic axes of each boundary (the ``periodic`` argument of ``Tree``)
+PERIODIC_AXES = {"open": False, "px": "x", "pxy": "xy", "pxyz": True}
 
 PI = np.pi
 ALPHA = dict(ue=1.05, uc=2.95, de=2.95, dc=1.05)
@@ -304,11 +309,11 @@ class KAFMM:
         src = np.asarray(src, dtype=np.float64).reshape(-1, 3)
         s = np.asarray(s, dtype=np.float64).reshape(len(src), self.ks)
         T = tree or Tree(src, trg, q=self.q, origin=self.origin, L=self.L,
-                         periodic=(self.bc == "pxyz"))
+                         periodic=PERIODIC_AXES[self.bc])
         self.tree = T
         x = T.trg
         nb = T.nbox
-        per = self.bc == "pxyz"
+        per = self.bc != "open"
         L = self.L
         M = [None] * nb
         Lden = [None] * nb
@@ -359,13 +364,13 @@ class KAFMM:
 
         # leaves: L->T, M->T (W), S->T (U)
         g = np.zeros((len(x), self.kt))
-        if per and self.problem == "laplace" and not near_only:
+        if self.bc == "pxyz" and self.problem == "laplace" and not near_only:
             c0 = T.centre(0)
             ue0 = self._surf("ue", c0, 0)
             second = np.sum(s[:, 0] * np.sum((src - c0) ** 2, axis=1))
             second_eq = np.sum(M[0][:, 0] * np.sum((ue0 - c0) ** 2, axis=1))
             g += (second - second_eq) / (6.0 * self.L ** 3)
-        if per and self.ml == "stokes_pvel" and not near_only:
+        if self.bc == "pxyz" and self.ml == "stokes_pvel" and not near_only:
             dp, du = self._pvel_periodic_shift(src, s, M[0], T.centre(0))
             if self.problem in ("stokes_pvel_traction", "stokes_dl_traction"):
                 g[:, [0, 4, 8]] -= dp           # sigma = -p I + ...

@@ -20,14 +20,28 @@ Readings used here (the paper defers the details):
   W(B), leaf B: descendants A of B's colleagues with A not adjacent to B and parent(A)
   adjacent to B.
   X(B): all A with B in W(A).
-* Triply periodic (``periodic=True``): adjacency and colleagues are taken modulo the cube;
-  every list entry carries the integer image shift (in units of L) applied to the source box.
+* Periodic (``periodic=True`` or "xyz": triply; "x": singly, along x; "xy": doubly, along x
+  and y): adjacency and colleagues are taken modulo the cube along the periodic axes; every
+  list entry carries the integer image shift (in units of L) applied to the source box, zero
+  along the other axes.
 """
 from __future__ import annotations
 
 import numpy as np
 
 MAX_LEVEL = 20
+
+
+def periodic_axes(periodic) -> tuple:
+    """(x, y, z) flags of the periodic axes: False/None -> none, True -> all three, or a
+    string naming the axes ("x", "xy", "xyz")."""
+    if periodic is None or periodic is False:
+        return (False, False, False)
+    if periodic is True:
+        return (True, True, True)
+    if isinstance(periodic, str):
+        return tuple(a in periodic for a in "xyz")
+    return tuple(bool(v) for v in periodic)
 
 
 def cells(points, origin=0.0, L=1.0) -> np.ndarray:
@@ -44,7 +58,8 @@ class Tree:
         self.origin = float(origin)
         self.L = float(L)
         self.q = int(q)
-        self.periodic = bool(periodic)
+        self.axes = periodic_axes(periodic)
+        self.periodic = any(self.axes)
         self.same = trg is None
         self.src = np.asarray(src, dtype=np.float64).reshape(-1, 3)
         self.trg = self.src if self.same else np.asarray(trg, dtype=np.float64).reshape(-1, 3)
@@ -111,9 +126,8 @@ class Tree:
         return bool(np.all(la <= hb) and np.all(lb <= ha))
 
     def _shifts(self):
-        if not self.periodic:
-            return [(0, 0, 0)]
-        return [(i, j, k) for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)]
+        r = [(-1, 0, 1) if a else (0,) for a in self.axes]
+        return [(i, j, k) for i in r[0] for j in r[1] for k in r[2]]
 
     def colleagues(self, b: int):
         """Same-level boxes (with their image shift) adjacent to b, b itself included."""
@@ -122,11 +136,9 @@ class Tree:
         out = []
         for d in [(i, j, k) for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)]:
             a = self.anchor[b] + np.array(d)
-            shift = np.zeros(3, dtype=np.int64)
-            if self.periodic:
-                shift = np.floor_divide(a, n)
-                a = a - shift * n
-            elif np.any(a < 0) or np.any(a >= n):
+            shift = np.floor_divide(a, n) * np.array(self.axes, dtype=np.int64)
+            a = a - shift * n
+            if np.any(a < 0) or np.any(a >= n):
                 continue
             c = self.lookup.get((lv, tuple(int(v) for v in a)))
             if c is not None:
@@ -145,7 +157,7 @@ class Tree:
         for b in range(nb):
             lv = int(self.level[b])
             # V: children of parent's colleagues, not adjacent to b.  With periodic wrap the
-            # root's colleagues are its 26 images, so level-1 boxes get a V list too.
+            # root's colleagues are its images, so level-1 boxes get a V list too.
             if lv >= 2 or (self.periodic and lv >= 1):
                 for (c, sh) in self.colleagues(int(self.parent[b])):
                     for ch in self.children[c]:
@@ -198,7 +210,7 @@ class Tree:
     def route_count(self, tb: int, sb: int, sh=(0, 0, 0)) -> int:
         """Number of list routes by which the sources of leaf sb (moved by sh domains) reach
         the targets of leaf tb.  A correct set of lists gives exactly 1 for every pair of
-        leaves (and every image shift in the 3x3x3 block when periodic)."""
+        leaves (and every image shift of the near image block when periodic)."""
         n = 0
         sh = tuple(sh)
         if (sb, sh) in self.U[tb]:

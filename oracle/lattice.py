@@ -25,6 +25,8 @@ the paper).  The reading used here for PX and PXY:
   component pair); the operator is projected onto neutral densities by subtracting, per
   output row and source component, the mean over the equivalent points, which changes
   nothing for a neutral density and removes the divergent part.
+* No-slip wall with PX / PXY (``wall_table``, ``wall_rpy_table``, ``wall_blake``): the image
+  system of ``oracle.wall`` with every sum taken over the lattice.
 """
 from __future__ import annotations
 
@@ -33,6 +35,7 @@ import ctypes
 import numpy as np
 
 from . import direct as D
+from . import wall as Wl
 from .kafmm import ALPHA, surface
 
 AXES = {"px": 1, "pxy": 2}
@@ -87,28 +90,67 @@ def check_neutral(kernel: str, s) -> None:
                              f"(column {c} sums to {s[:, c].sum():.3e})")
 
 
-def lattice_sum(kernel: str, x, y, s, bc: str, L: float = 1.0, n0: int | None = None,
-                nlev: int | None = None) -> np.ndarray:
-    """O1 for PX / PXY: the symmetric lattice sum of ``direct.direct(kernel)`` over all images,
-    extrapolated in the truncation N (FP64).  Pairs at zero distance are skipped."""
+def _extrapolated(fn, x, kt: int, bc: str, L: float, n0: int | None, nlev: int | None) -> np.ndarray:
+    """sum over the lattice of fn(x - n L) (fn: the sum over the sources at the given targets,
+    [m, kt]), in square shells, extrapolated in the truncation N."""
     n0 = n0 or EXTRAP[bc][0]
     nlev = nlev or EXTRAP[bc][1]
-    ks, kt = D.KDIM[kernel]
     x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
-    y = np.asarray(y, dtype=np.float64).reshape(-1, 3)
-    s = np.asarray(s, dtype=np.float64).reshape(len(y), ks)
-    check_neutral(kernel, s)
     g = np.zeros((len(x), kt))
     parts = []
     for sh in range(0, n0 * 2 ** (nlev - 1) + 1):
+        # K(x - (y + n L)) as K((x - n L) - y): the shell's images of the targets, one call
         n = shifts(bc, sh).astype(np.float64) * L
-        ys = (y[None, :, :] + n[:, None, :]).reshape(-1, 3)
-        ss = np.tile(s, (len(n), 1))
-        D.direct(kernel, x, ys, ss, g)
+        xs = (x[None, :, :] - n[:, None, :]).reshape(-1, 3)
+        g += fn(xs).reshape(len(n), len(x), kt).sum(axis=0)
         if sh >= n0 and (sh // n0) & (sh // n0 - 1) == 0 and sh % n0 == 0:
             parts.append(g.copy())
     assert len(parts) == nlev
     return richardson(parts, n0)
+
+
+def lattice_sum(kernel: str, x, y, s, bc: str, L: float = 1.0, n0: int | None = None,
+                nlev: int | None = None) -> np.ndarray:
+    """O1 for PX / PXY: the symmetric lattice sum of ``direct.direct(kernel)`` over all images,
+    extrapolated in the truncation N (FP64).  Pairs at zero distance are skipped."""
+    ks, kt = D.KDIM[kernel]
+    y = np.asarray(y, dtype=np.float64).reshape(-1, 3)
+    s = np.asarray(s, dtype=np.float64).reshape(len(y), ks)
+    check_neutral(kernel, s)
+    return _extrapolated(lambda xs: D.direct(kernel, xs, y, s), x, kt, bc, L, n0, nlev)
+
+
+def wall_blake(x, y, f, bc: str, zw: float, L: float = 1.0) -> np.ndarray:
+    """Stokeslets above a no-slip wall at x_3 = zw, periodic along x (and y): the lattice sum
+    of Blake's image system (``wall.blake``).  Its far field falls off like 1/r^3 along the
+    wall, so the sum converges for any net force."""
+    y = np.asarray(y, dtype=np.float64).reshape(-1, 3)
+    f = np.asarray(f, dtype=np.float64).reshape(-1, 3)
+    return _extrapolated(lambda xs: Wl.blake(xs, y, f, zw), x, 3, bc, L, None, None)
+
+
+def wall_table(x, y, f, bc: str, zw: float, L: float = 1.0) -> np.ndarray:
+    """The paper's three sums of the wall (Table tab:rpywall, b = 0), each summed over the
+    lattice (each is neutral: a source and its image carry opposite charges or forces), and
+    assembled at the targets."""
+    x = np.asarray(x, np.float64).reshape(-1, 3)
+    y = np.asarray(y, np.float64).reshape(-1, 3)
+    yy = np.concatenate([y, Wl.images(y, zw)])
+    fs, sd, sdz = Wl.table_sources(y, f, zw)
+    return Wl.assemble(x, lattice_sum("stokeslet", x, yy, fs, bc, L), lattice_sum("laplace_qd", x, yy, sd, bc, L),
+                       lattice_sum("laplace_qd", x, yy, sdz, bc, L), zw)
+
+
+def wall_rpy_table(x, y, fb, bc: str, zw: float, L: float = 1.0) -> np.ndarray:
+    """RPY above the wall, periodic along x (and y): the four sums of Table tab:rpywall over the
+    lattice, assembled into [u, lap u]."""
+    x = np.asarray(x, np.float64).reshape(-1, 3)
+    y = np.asarray(y, np.float64).reshape(-1, 3)
+    yy = np.concatenate([y, Wl.images(y, zw)])
+    rpy, sd, sdz, quad = Wl.rpy_table_sources(y, fb, zw)
+    return Wl.rpy_assemble(x, lattice_sum("rpy", x, yy, rpy, bc, L), lattice_sum("laplace_qd", x, yy, sd, bc, L),
+                           lattice_sum("laplace_qd", x, yy, sdz, bc, L),
+                           lattice_sum("laplace_quad", x, yy, quad, bc, L), zw)
 
 
 def lattice_matrix(ml: str, x, y, bc: str, L: float = 1.0, nmin: int = 2, n0: int | None = None,

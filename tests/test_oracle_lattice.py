@@ -13,6 +13,9 @@ Sec. III.B) against results fixed by the mathematics, not by the oracle's own fo
 * periodicity along the lattice, invariance under a common shift, rejection of non-neutral
   sources;
 * the interaction lists with wrap along some axes reach every pair of leaves exactly once;
+* above a no-slip wall: the lattice sums of the image-system table equal the lattice sum of
+  Blake's solution (and, for RPY, of its definition with the source Laplacian), and the plane
+  mean is the layered shear flow fixed by the reduced 1D Stokes equation with no slip;
 * the CPU KAFMM with the far-image operator converges to the lattice sum with the order and
   is invariant under a shift of all points along the periodic axes (the paper's translation
   test, Sec. III.B).
@@ -25,6 +28,7 @@ from scipy.special import erf, erfc, k0
 
 from oracle import direct as D
 from oracle import lattice as La
+from oracle import wall as Wl
 from oracle.kafmm import KAFMM
 from oracle.tree import Tree
 
@@ -217,3 +221,49 @@ def test_kafmm_doubly_periodic_translation_invariance():
     ref = La.lattice_sum("stokeslet", pts, pts, s, "pxy")
     e = D.rel_l2(g0, ref)
     assert D.rel_l2(g1, g0) < 3 * e + 1e-12, (D.rel_l2(g1, g0), e)
+
+
+def _above(n, seed, lo=0.6, hi=0.9):
+    rng = np.random.default_rng(seed)
+    y = rng.random((n, 3))
+    y[:, 2] = lo + (hi - lo) * y[:, 2]
+    return y, rng.standard_normal((n, 3))
+
+
+@pytest.mark.parametrize("bc", ["px", "pxy"])
+def test_periodic_wall_table_equals_blake_lattice_sum(bc):
+    """The wall's three neutral sums over the lattice, assembled (Table tab:rpywall, b = 0),
+    equal the lattice sum of Blake's closed-form image system for forces with a net part."""
+    y, f = _above(10, seed=14)
+    x, _ = _above(6, seed=15, lo=0.5, hi=1.0)
+    a = La.wall_blake(x, y, f, bc, 0.5)
+    b = La.wall_table(x, y, f, bc, 0.5)
+    assert D.rel_l2(b, a) < 1e-10
+
+
+def test_doubly_periodic_wall_mean_flow_is_the_layered_shear():
+    """Mean over x, y above a wall at z_w with no slip: d2/dz2 mean u = -sum f delta(z - z_j) / A
+    and mean u = 0 on the wall, so the tangential mean is sum f_j min(z - z_w, h_j) / A (a shear
+    below each layer, uniform above it) and the normal mean vanishes."""
+    y, f = _above(8, seed=16, lo=0.75, hi=0.8)
+    M = 24
+    a = (np.arange(M) + 0.37) / M
+    X, Y = np.meshgrid(a, a, indexing="ij")
+    for z in (0.53, 0.99):
+        xs = np.stack([X.ravel(), Y.ravel(), np.full(M * M, z)], axis=1)
+        u = La.wall_blake(xs, y, f, "pxy", 0.5).mean(axis=0)
+        w = np.minimum(z - 0.5, y[:, 2] - 0.5)
+        ref = np.array([np.sum(f[:, 0] * w), np.sum(f[:, 1] * w), 0.0])
+        assert np.abs(u - ref).max() < 1e-8 * np.abs(ref).max(), (z, u, ref)
+
+
+def test_periodic_rpy_wall_table_equals_the_definition():
+    """RPY above the wall, singly periodic: the lattice sums of the four table sums, assembled,
+    equal the lattice sum of the definition (1 + b^2/6 lap_y) G_wall f."""
+    rng = np.random.default_rng(17)
+    y, f = _above(3, seed=17, lo=0.65, hi=0.85)
+    fb = np.concatenate([f, rng.uniform(0.02, 0.05, (3, 1))], axis=1)
+    x, _ = _above(4, seed=18, lo=0.55, hi=0.95)
+    ref = La._extrapolated(lambda xs: Wl.blake_rpy(xs, y, fb, 0.5), x, 3, "px", 1.0, 16, 6)
+    got = La.wall_rpy_table(x, y, fb, "px", 0.5)[:, :3]
+    assert D.rel_l2(got, ref) < 1e-9

@@ -101,15 +101,32 @@ typedef enum {
   KAFMM_LAPLACE_QUAD = 13
 } kafmm_kernel;
 
-/* Boundary conditions (Sec. III.B).  KAFMM_BC_PXYZ: triply periodic in the cube
+/* Boundary conditions (Sec. III.B, Table tab:implement).
+ * KAFMM_BC_PX / KAFMM_BC_PXY: singly periodic along x / doubly periodic along x and y, with
+ * period L (the cube [origin, origin + L)^3; every point must lie inside it, the other axes are
+ * open).  For KAFMM_LAPLACE, KAFMM_LAPLACE_QD, KAFMM_LAPLACE_QUAD, KAFMM_STOKESLET, KAFMM_RPY
+ * and KAFMM_STOKES_REG (the kernels whose M->L table is Laplace or the Stokeslet G; the
+ * StokesPVel-table kernels answer KAFMM_ERR_ARG).  The sources must be neutral in the monopole
+ * (sum of q = 0, sum of f = 0; a net charge or force makes the image sum diverge, like log r
+ * along a line and like r over a plane).  The result is the limit of the symmetric sums over the
+ * images with max|n| <= N (n along the periodic axes), which exists for neutral sources.  The
+ * tree's lists wrap along the periodic axes (images with shift -1, 0, 1), and the farther images
+ * enter through an operator on the root's multipole density, computed once per plan as the FP64
+ * image sum over max|n| = 2 ... N, N = 128 (plane) or 2048 (line), extrapolated in N and
+ * projected onto neutral densities.
+ * KAFMM_BC_PXYZ: triply periodic in the cube
  * [origin, origin + L)^3; the far images enter through a precomputed operator on the
  * root's multipole density (Sec. III, App. B).  Periodic sums need a zero net source
  * (sum of f = 0 for the Stokeslet, sum of q = 0 for Laplace, both for StokesPVel, sum of
  * tr D = 0 for the double layer); the k = 0 Fourier mode is dropped (zero-mean field).  The
  * StokesPVel table adds the constant pressure and velocity shifts of the source moments its
  * equivalent densities do not carry (the trace of the force dipole, and the split of the
- * potential-dipole field between source dipoles and force quadrupoles).  PX and PXY are not
- * provided.
+ * potential-dipole field between source dipoles and force quadrupoles).
+ * KAFMM_BC_WALL_PX / KAFMM_BC_WALL_PXY (KAFMM_STOKESLET and KAFMM_RPY): the wall below combined
+ * with periodicity along x / along x and y (period L): the same image system, its sums taken
+ * singly / doubly periodic (their sources and images are neutral by construction, so any net
+ * force is allowed; above a plane lattice a net force parallel to the wall drives a uniform
+ * flow far from it).
  * KAFMM_BC_WALL (KAFMM_STOKESLET and KAFMM_RPY): a no-slip wall on the plane z = origin_z + L / 2,
  * open elsewhere (Sec. III.C).  Every source and target must lie above it (z in
  * [origin_z + L/2, origin_z + L)), else KAFMM_ERR_DOMAIN; their mirror images fill the lower
@@ -130,11 +147,19 @@ typedef enum {
  *     u = u^S + grad phi^SDZ + x_3 grad(phi^SD + phi^Q) - [0, 0, phi^SD + phi^Q],
  *     lap u = lap u^S + 2 d_3 grad(phi^SD + phi^Q).
  *   The plan keeps child plans (Stokeslet or RPY, Laplace charges + dipoles, and for RPY
- *   Laplace quadrupoles; open boundary, the same p, q and options); kafmm_tree_info,
+ *   Laplace quadrupoles; the same p, q and options); kafmm_tree_info,
  *   kafmm_phase_times and kafmm_get_counters report the first child; batches,
  *   kafmm_autotune, the tree queries, kafmm_get_operator and the RPY velocity calls answer
  *   KAFMM_ERR_ARG. */
-typedef enum { KAFMM_BC_OPEN = 0, KAFMM_BC_PXYZ = 3, KAFMM_BC_WALL = 4 } kafmm_bc;
+typedef enum {
+  KAFMM_BC_OPEN = 0,
+  KAFMM_BC_PX = 1,
+  KAFMM_BC_PXY = 2,
+  KAFMM_BC_PXYZ = 3,
+  KAFMM_BC_WALL = 4,
+  KAFMM_BC_WALL_PX = 5,
+  KAFMM_BC_WALL_PXY = 6
+} kafmm_bc;
 
 typedef enum { KAFMM_F32 = 0, KAFMM_F64 = 1 } kafmm_dtype;
 
@@ -154,7 +179,7 @@ enum {
    *   KAFMM_ML_G  -- the Stokeslet G on M and L points (Tables tab:ktab_rpy, tab:ktab_reg);
    *   KAFMM_ML_L4 -- four Laplace channels per point (charges f and (y - c).f about the box
    *                  centre c); a linear, low-dimensional ML-tree table in the sense of
-   *                  Sec. II.  Ignored for Laplace; PXYZ always uses KAFMM_ML_G. */
+   *                  Sec. II.  Ignored for Laplace; periodic boundaries always use KAFMM_ML_G. */
   KAFMM_OPT_ML_VARIANT = 2,
   /* cudaStream_t, passed as an integer. */
   KAFMM_OPT_STREAM = 3,
@@ -272,7 +297,8 @@ enum {
  * 6(p-1)^2 + 2 equivalent points per surface, 2 <= p <= 16) and the leaf size q (a box is
  * split while it holds more than q points, Sec. III; 1 <= q <= 4096).  Builds the FP64
  * translation operators on the current CUDA device (pseudo-inverses by one-sided Jacobi
- * SVD, Sec. II; the periodic operator by Ewald lattice sums).  *out receives the plan. */
+ * SVD, Sec. II; the periodic operator by Ewald lattice sums (PXYZ) or extrapolated image sums
+ * (PX, PXY)).  *out receives the plan. */
 int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int max_pts_per_leaf,
                kafmm_plan_t* out);
 

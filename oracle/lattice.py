@@ -98,14 +98,22 @@ def _extrapolated(fn, x, kt: int, bc: str, L: float, n0: int | None, nlev: int |
     x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
     g = np.zeros((len(x), kt))
     parts = []
-    for sh in range(0, n0 * 2 ** (nlev - 1) + 1):
-        # K(x - (y + n L)) as K((x - n L) - y): the shell's images of the targets, one call
-        n = shifts(bc, sh).astype(np.float64) * L
-        xs = (x[None, :, :] - n[:, None, :]).reshape(-1, 3)
-        g += fn(xs).reshape(len(n), len(x), kt).sum(axis=0)
-        if sh >= n0 and (sh // n0) & (sh // n0 - 1) == 0 and sh % n0 == 0:
+    snaps = [n0 << k for k in range(nlev)]
+    batch = []
+
+    def flush():
+        # K(x - (y + n L)) as K((x - n L) - y): the images of the targets, one call per batch
+        if batch:
+            n = np.concatenate(batch).astype(np.float64) * L
+            xs = (x[None, :, :] - n[:, None, :]).reshape(-1, 3)
+            g[:] += fn(xs).reshape(len(n), len(x), kt).sum(axis=0)
+            batch.clear()
+    for sh in range(0, snaps[-1] + 1):
+        batch.append(shifts(bc, sh))
+        if sh in snaps or sum(len(v) for v in batch) * len(x) > 200000:
+            flush()
+        if sh in snaps:
             parts.append(g.copy())
-    assert len(parts) == nlev
     return richardson(parts, n0)
 
 

@@ -34,7 +34,7 @@ int cuda_fail(Plan& P, cudaError_t e, const char* where) {
 // Problem dimensions from kernel, boundary condition and ML variant.
 static void configure(Plan& P) {
   int v = P.variant;
-  if (P.bc == KAFMM_BC_PXYZ) v = KAFMM_ML_G;
+  if (periodic_mask(P.bc)) v = KAFMM_ML_G;
   P.ml_stokes = 0;
   P.C = 1;
   P.D = 1;
@@ -160,10 +160,14 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
     return KAFMM_ERR_ARG;
   }
   *out = nullptr;
+  // singly / doubly periodic: the kernels on the Laplace or Stokeslet M->L table
+  const bool px_ok = kernel == KAFMM_LAPLACE || kernel == KAFMM_LAPLACE_QD || kernel == KAFMM_LAPLACE_QUAD ||
+                     kernel == KAFMM_STOKESLET || kernel == KAFMM_RPY || kernel == KAFMM_STOKES_REG;
   if ((int)kernel < 0 || (int)kernel > 13 ||
       ((kernel == KAFMM_LAPLACE_QD || kernel == KAFMM_LAPLACE_QUAD) && bc == KAFMM_BC_PXYZ) ||
-      (bc != KAFMM_BC_OPEN && bc != KAFMM_BC_PXYZ && bc != KAFMM_BC_WALL) ||
-      (bc == KAFMM_BC_WALL && kernel != KAFMM_STOKESLET && kernel != KAFMM_RPY) || p < 2 || p > 16 || q < 1 ||
+      ((int)bc < KAFMM_BC_OPEN || (int)bc > KAFMM_BC_WALL_PXY) ||
+      ((bc == KAFMM_BC_PX || bc == KAFMM_BC_PXY) && !px_ok) ||
+      (bc >= KAFMM_BC_WALL && kernel != KAFMM_STOKESLET && kernel != KAFMM_RPY) || p < 2 || p > 16 || q < 1 ||
       q > 4096) {
     g_err = "kafmm_plan: invalid kernel, boundary condition, order (2..16) or leaf size (1..4096)";
     return KAFMM_ERR_ARG;
@@ -182,12 +186,14 @@ extern "C" int kafmm_plan(kafmm_kernel kernel, kafmm_bc bc, int p, int q, kafmm_
       return KAFMM_ERR_CUDA;
     }
   }
-  if (bc == KAFMM_BC_WALL) {   // the sums of the image system: Stokeslet or RPY, Laplace charges +
+  if (bc >= KAFMM_BC_WALL) {   // the sums of the image system: Stokeslet or RPY, Laplace charges +
                                // dipoles, and (RPY) Laplace quadrupoles
     const bool rpy = kernel == KAFMM_RPY;
     const kafmm_kernel kk[3] = {rpy ? KAFMM_RPY : KAFMM_STOKESLET, KAFMM_LAPLACE_QD, KAFMM_LAPLACE_QUAD};
     for (int c = 0; c < (rpy ? 3 : 2); ++c) {
-      int rc = kafmm_plan(kk[c], KAFMM_BC_OPEN, p, q, &P->wall_child[c]);
+      // open, or periodic along x (and y) with the wall
+      const kafmm_bc cbc = bc == KAFMM_BC_WALL ? KAFMM_BC_OPEN : (bc == KAFMM_BC_WALL_PX ? KAFMM_BC_PX : KAFMM_BC_PXY);
+      int rc = kafmm_plan(kk[c], cbc, p, q, &P->wall_child[c]);
       if (rc) {
         for (int d = 0; d < c; ++d) kafmm_destroy(P->wall_child[d]);
         for (int i = 0; i < 8; ++i) cudaEventDestroy(P->ev[i]);

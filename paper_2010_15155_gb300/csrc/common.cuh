@@ -11,6 +11,11 @@
 
 namespace kafmm {
 
+// Periodic axes of a boundary condition: bit 0 = x, bit 1 = y, bit 2 = z (PX, PXY, PXYZ).
+inline int periodic_mask(int bc) {
+  return bc == KAFMM_BC_PX ? 1 : (bc == KAFMM_BC_PXY ? 3 : (bc == KAFMM_BC_PXYZ ? 7 : 0));
+}
+
 // Count of kernel launches issued by this thread (reported per set_points + eval).
 extern thread_local long long g_launches;
 #define KL ++::kafmm::g_launches,

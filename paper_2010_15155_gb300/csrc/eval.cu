@@ -1291,7 +1291,8 @@ int worklists_finish(Plan& P) {
     uint64_t k = key[b];
     return (int)((k & 1) | ((k >> 1) & 1) << 1 | ((k >> 2) & 1) << 2);
   };
-  int vmin = P.bc == KAFMM_BC_PXYZ ? 1 : 2;
+  const bool per = periodic_mask(P.bc) != 0;
+  int vmin = per ? 1 : 2;
   // M->L: all boxes at levels >= vmin, by octant class (the class fixes the offset of each V
   // slot).  Tensor-core tiles take NB_TC boxes.
   for (int b = 0; b < nb; ++b)
@@ -1348,7 +1349,7 @@ int worklists_finish(Plan& P) {
   // periodic, at the root; with the open boundary levels 0 and 1 are never read, so their M->M
   // is skipped.
   for (int l = 0; l < MAX_LEVELS; ++l) {
-    bool needed = l >= vmin || (P.bc == KAFMM_BC_PXYZ && l == 0);
+    bool needed = l >= vmin || (per && l == 0);
     if (needed)
       for (int b = T.lvl_start[l]; b < T.lvl_start[l + 1]; ++b)
         if (!leaf[b]) by_cls[0].push_back(b);
@@ -1356,16 +1357,16 @@ int worklists_finish(Plan& P) {
   }
   // L->L per level (levels >= vmin + 1; and level 1 from the root when periodic)
   for (int l = 0; l < MAX_LEVELS; ++l) {
-    if (l >= 1 && (l >= vmin + 1 || P.bc == KAFMM_BC_PXYZ))
+    if (l >= 1 && (l >= vmin + 1 || per))
       for (int b = T.lvl_start[l]; b < T.lvl_start[l + 1]; ++b) by_cls[cls(b)].push_back(b);
     add_tiles(W, by_cls, NB, W.l2l[l]);
   }
   // pseudo-inverses: up for boxes in W lists (and the root for the periodic Laplace
   // constant), down for leaves with targets
-  bool per = P.bc == KAFMM_BC_PXYZ;
-  // (the periodic Laplace constant and the periodic StokesPVel shifts read the root's density)
+  // (the triply periodic Laplace constant and StokesPVel shifts read the root's density)
+  const bool pxyz = P.bc == KAFMM_BC_PXYZ;
   for (int b = 0; b < nb; ++b)
-    if (wflag[b] || (b == 0 && per && (P.kernel == KAFMM_LAPLACE || P.ml_stokes == 2))) by_cls[0].push_back(b);
+    if (wflag[b] || (b == 0 && pxyz && (P.kernel == KAFMM_LAPLACE || P.ml_stokes == 2))) by_cls[0].push_back(b);
   add_tiles(W, by_cls, NB, W.pup);
   if (per) by_cls[0].push_back(0);
   add_tiles(W, by_cls, NB, W.root);
@@ -1480,7 +1481,7 @@ static int run_eval(Plan& P, const void* s_in, int s_dtype, void* g_out) {
   geo.L = P.L;
   for (int d = 0; d < 3; ++d) geo.org[d] = P.origin[d];
   TreeView tv = T_.view();
-  tv.periodic = P.bc == KAFMM_BC_PXYZ;
+  tv.periodic = periodic_mask(P.bc);
   const T* unit = P.fp64() ? (const T*)P.unit64.p : (const T*)P.unit32.p;
   const T* ops = P.fp64() ? (const T*)P.ops64.p : (const T*)P.ops32.p;
 

@@ -418,6 +418,97 @@ __global__ void k_periodic_operator(const double* __restrict__ unit, int n, int 
   }
 }
 
+// Singly / doubly periodic far-image operator at unit scale (root half-width 1, period 2):
+//   T[i][j] = lim_{N -> inf} sum_{2 <= max|n| <= N} K(dc_i - ue_j - 2 n)
+// over the images n = (a, 0, 0) (axes 1, PX) or (a, b, 0) (axes 2, PXY), in square shells
+// max|n| = s.  One thread per (dc point, ue point) pair accumulates the Laplace value
+// (stokes = 0) or the 3 x 3 Stokeslet block (stokes = 1) and writes the partial sums at
+// N = n0 2^k, k < nlev, to part[k][R][R]; k_lattice_extrapolate takes N -> infinity.
+__global__ void k_lattice_partials(const double* __restrict__ unit, int n, int stokes, double adc, double aue,
+                                   int axes, int n0, int nlev, double* __restrict__ part) {
+  const int D = stokes ? 3 : 1;
+  const int64_t R = (int64_t)D * n, RR = R * R;
+  const int nmax = n0 << (nlev - 1);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    double r[3];
+    for (int q = 0; q < 3; ++q) r[q] = adc * unit[3 * i + q] - aue * unit[3 * j + q];
+    double m[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    auto add = [&](int a, int b) {
+      const double d0 = r[0] - 2.0 * a, d1 = r[1] - 2.0 * b, d2 = r[2];
+      const double ri = rsqrt(d0 * d0 + d1 * d1 + d2 * d2);
+      if (!stokes) {
+        m[0] += ri;
+        return;
+      }
+      const double r3 = ri * ri * ri;
+      const double d[3] = {d0, d1, d2};
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) m[3 * p + q] += (p == q ? ri : 0.0) + d[p] * d[q] * r3;
+    };
+    int lev = 0;
+    for (int s = 2; s <= nmax; ++s) {
+      if (axes == 1) {
+        add(-s, 0);
+        add(s, 0);
+      } else {   // the ring max(|a|, |b|) = s: four sides of 2 s images, each corner once
+        for (int t = -s; t < s; ++t) {
+          add(t, -s);
+          add(s, t);
+          add(-t, s);
+          add(-s, -t);
+        }
+      }
+      if (s == (n0 << lev)) {
+        const double c = stokes ? 1.0 / (8.0 * PI) : 1.0 / (4.0 * PI);
+        for (int p = 0; p < D; ++p)
+          for (int q = 0; q < D; ++q) part[lev * RR + (int64_t)(D * i + p) * R + D * j + q] = c * m[D * p + q];
+        ++lev;
+      }
+    }
+  }
+}
+
+// N -> infinity from the partial sums at N = n0 2^k: the tails are power series in 1/N (sums
+// of smooth functions over the lattice cells outside a square, by the midpoint rule), removed
+// one power per level by repeated Richardson extrapolation.
+__global__ void k_lattice_extrapolate(const double* __restrict__ part, int nlev, int64_t count,
+                                      double* __restrict__ T) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double t[12];
+    for (int k = 0; k < nlev; ++k) t[k] = part[k * count + e];
+    for (int j = 1; j < nlev; ++j) {
+      const double f = (double)(1 << j);
+      for (int k = 0; k + j < nlev; ++k) t[k] = (f * t[k + 1] - t[k]) / (f - 1.0);
+    }
+    T[e] = t[0];
+  }
+}
+
+// Projection onto neutral densities: per row of T (R x R, D components per point) and source
+// component c, subtract the mean over the n equivalent points.  The image sums of a net charge
+// or force diverge with N (a constant matrix per component pair); a neutral density is left
+// unchanged.  One block of 256 threads per row.
+__global__ void k_project_neutral(double* __restrict__ T, int n, int D) {
+  const int64_t R = (int64_t)D * n;
+  double* row = T + blockIdx.x * R;
+  __shared__ double part[3][256];
+  double acc[3] = {0, 0, 0};
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    for (int c = 0; c < D; ++c) acc[c] += row[D * j + c];
+  for (int c = 0; c < 3; ++c) part[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int c = 0; c < 3; ++c) part[c][threadIdx.x] += part[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    for (int c = 0; c < D; ++c) row[D * j + c] -= part[c][0] / n;
+}
+
 __global__ void k_round32(const double* in, int64_t n, float* out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
@@ -803,6 +894,20 @@ int build_operators(Plan& P) {
   if (P.bc == KAFMM_BC_PXYZ) {  // root far images, composed with the upward pseudo-inverse
     KL k_periodic_operator<<<1024, 128, 0, st>>>(unit, n, stokes, ALPHA_DC, ALPHA_UE, K);
     compose(OP_UP1, OP_UP2, 1.0, O + RR * OP_PER);
+  } else if (P.bc == KAFMM_BC_PX || P.bc == KAFMM_BC_PXY) {
+    // images along a line: N = 16 ... 2048 (4097 images, extrapolated to rounding); over a
+    // plane: N = 4 ... 128 (66049 images, about 1e-9)
+    const int axes = P.bc == KAFMM_BC_PX ? 1 : 2;
+    const int n0 = axes == 1 ? 16 : 4, nlev = axes == 1 ? 8 : 6;
+    DevBuf part;
+    CK(part.reserve(sizeof(double) * RR * nlev));
+    KL k_lattice_partials<<<(int)(((int64_t)n * n + 127) / 128), 128, 0, st>>>(unit, n, stokes, ALPHA_DC,
+                                                                               ALPHA_UE, axes, n0, nlev,
+                                                                               part.as<double>());
+    KL k_lattice_extrapolate<<<2048, 256, 0, st>>>(part.as<double>(), nlev, (int64_t)RR, K);
+    KL k_project_neutral<<<R, 256, 0, st>>>(K, n, stokes ? 3 : 1);
+    compose(OP_UP1, OP_UP2, 1.0, O + RR * OP_PER);
+    CK(cudaStreamSynchronize(st));   // the partial sums are released on leaving this scope
   } else {
     CK(cudaMemsetAsync(O + RR * OP_PER, 0, sizeof(double) * RR, st));
   }

@@ -192,16 +192,15 @@ __global__ void k_rpy_velocity(const typename V4<T>::type* __restrict__ spos,
         if (mx * mx + my * my + mz * mz > rc * rc) continue;
       }
       int qx = cx + ddx, qy = cy + ddy, qz = cz + ddz;
-      int sx = 0, sy = 0, sz = 0;
-      if (qx < 0 || qx >= n || qy < 0 || qy >= n || qz < 0 || qz >= n) {
-        if (!periodic) continue;
-        sx = qx < 0 ? -1 : (qx >= n ? 1 : 0);
-        sy = qy < 0 ? -1 : (qy >= n ? 1 : 0);
-        sz = qz < 0 ? -1 : (qz >= n ? 1 : 0);
-        qx -= sx * n;
-        qy -= sy * n;
-        qz -= sz * n;
-      }
+      // outside the cube: the image cell along a periodic axis (bit 0 = x, 1 = y, 2 = z of
+      // periodic), none along an open one
+      const int sx = qx < 0 ? -1 : (qx >= n ? 1 : 0);
+      const int sy = qy < 0 ? -1 : (qy >= n ? 1 : 0);
+      const int sz = qz < 0 ? -1 : (qz >= n ? 1 : 0);
+      if ((sx && !(periodic & 1)) || (sy && !(periodic & 2)) || (sz && !(periodic & 4))) continue;
+      qx -= sx * n;
+      qy -= sy * n;
+      qz -= sz * n;
       uint64_t c = morton3((uint32_t)qx, (uint32_t)qy, (uint32_t)qz);
       int b0 = cbeg[c], b1 = cend[c];
       T ox = (T)(sx * L), oy = (T)(sy * L), oz = (T)(sz * L);
@@ -310,12 +309,12 @@ int run(Plan& P, const void* s, const void* a, const void* g, void* ua, int dtyp
     if (dtype == KAFMM_F64)
       KL k_rpy_velocity<T, double><<<grid_for(nt, 128), 128, 0, st>>>(
           spos, fb.as<T4>(), tpos, ta.as<T>(), tkey, tperm, nt, cb.as<int>(), ce.as<int>(), lev, H, reach * P.L,
-          P.origin[0], P.origin[1], P.origin[2], P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const double*)g,
+          P.origin[0], P.origin[1], P.origin[2], periodic_mask(P.bc), P.L, Tr.same ? 1 : 0, (const double*)g,
           (double*)ua, contact_info(P));
     else
       KL k_rpy_velocity<T, float><<<grid_for(nt, 128), 128, 0, st>>>(
           spos, fb.as<T4>(), tpos, ta.as<T>(), tkey, tperm, nt, cb.as<int>(), ce.as<int>(), lev, H, reach * P.L,
-          P.origin[0], P.origin[1], P.origin[2], P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const float*)g,
+          P.origin[0], P.origin[1], P.origin[2], periodic_mask(P.bc), P.L, Tr.same ? 1 : 0, (const float*)g,
           (float*)ua, contact_info(P));
   }
   CK(cudaGetLastError());
@@ -451,11 +450,11 @@ int run_noalloc(Plan& P, const void* s, const void* a, const void* g, void* ua, 
     if (dtype == KAFMM_F64)
       KL k_rpy_velocity<T, double><<<grid_for(nt, 128), 128, 0, st>>>(
           spos, fb, tpos, ta, tkey, tperm, nt, cb, ce, lev, 1, reach * P.L, P.origin[0], P.origin[1], P.origin[2],
-          P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const double*)g, (double*)ua, contact_info(P));
+          periodic_mask(P.bc), P.L, Tr.same ? 1 : 0, (const double*)g, (double*)ua, contact_info(P));
     else
       KL k_rpy_velocity<T, float><<<grid_for(nt, 128), 128, 0, st>>>(
           spos, fb, tpos, ta, tkey, tperm, nt, cb, ce, lev, 1, reach * P.L, P.origin[0], P.origin[1], P.origin[2],
-          P.bc == KAFMM_BC_PXYZ, P.L, Tr.same ? 1 : 0, (const float*)g, (float*)ua, contact_info(P));
+          periodic_mask(P.bc), P.L, Tr.same ? 1 : 0, (const float*)g, (float*)ua, contact_info(P));
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));

@@ -564,7 +564,8 @@ __device__ inline int deepest_box(const TreeView& t, int lv, int pb, int ax, int
   return pb;
 }
 
-// Neighbour cell a + d at level lv: wraps (periodic) or reports absence.  s: image shift.
+// Neighbour cell a + d at level lv along one axis: wraps (periodic along that axis) or reports
+// absence.  s: image shift.
 __device__ inline bool neighbour(int periodic, int lv, int a, int d, int& c, int& s) {
   int n = 1 << lv;
   c = a + d;
@@ -615,8 +616,8 @@ __global__ void k_vtab(TreeView t, int32_t* __restrict__ vtab) {
     bool inner = abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1;
     if (!inner && (lv >= 2 || (t.periodic && lv >= 1))) {
       int cx, cy, cz, sx, sy, sz;
-      if (neighbour(t.periodic, lv, ax, ox, cx, sx) && neighbour(t.periodic, lv, ay, oy, cy, sy) &&
-          neighbour(t.periodic, lv, az, oz, cz, sz)) {
+      if (neighbour(t.periodic & 1, lv, ax, ox, cx, sx) && neighbour(t.periodic & 2, lv, ay, oy, cy, sy) &&
+          neighbour(t.periodic & 4, lv, az, oz, cz, sz)) {
         int s = find_box(t, lv, t.prob[b], cx, cy, cz);
         if (s >= 0) e = pack_entry(s, shift_code(sx, sy, sz));
       }
@@ -659,8 +660,8 @@ __global__ void k_lists(TreeView t, ListOut o) {
     if (is_leaf && lane < 27) {
       const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
       int cx, cy, cz;
-      if (neighbour(t.periodic, lv, ax, dx, cx, sx) && neighbour(t.periodic, lv, ay, dy, cy, sy) &&
-          neighbour(t.periodic, lv, az, dz, cz, sz)) {
+      if (neighbour(t.periodic & 1, lv, ax, dx, cx, sx) && neighbour(t.periodic & 2, lv, ay, dy, cy, sy) &&
+          neighbour(t.periodic & 4, lv, az, dz, cz, sz)) {
         sc = shift_code(sx, sy, sz);
         nb = deepest_box(t, lv, pb, cx, cy, cz);
         const int nl = t.level[nb];
@@ -727,8 +728,9 @@ __global__ void k_lists(TreeView t, ListOut o) {
       anchor_of(t.key[p], px_, py_, pz_);
       const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
       int cx, cy, cz, xsx, xsy, xsz;
-      if (neighbour(t.periodic, lv - 1, px_, dx, cx, xsx) && neighbour(t.periodic, lv - 1, py_, dy, cy, xsy) &&
-          neighbour(t.periodic, lv - 1, pz_, dz, cz, xsz)) {
+      if (neighbour(t.periodic & 1, lv - 1, px_, dx, cx, xsx) &&
+          neighbour(t.periodic & 2, lv - 1, py_, dy, cy, xsy) &&
+          neighbour(t.periodic & 4, lv - 1, pz_, dz, cz, xsz)) {
         const int xb = deepest_box(t, lv - 1, pb, cx, cy, cz);
         if (t.leaf[xb]) {
           const int nl = t.level[xb];
@@ -1223,7 +1225,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
 
   // ---- lists
   TreeView tv = T.view();
-  tv.periodic = P.bc == KAFMM_BC_PXYZ;
+  tv.periodic = periodic_mask(P.bc);
   CK(T.u_off.reserve(sizeof(int64_t) * (nb + 1 + nb / SCAN_TILE + 64)));
   CK(T.w_off.reserve(sizeof(int64_t) * (nb + 1 + nb / SCAN_TILE + 64)));
   CK(T.x_off.reserve(sizeof(int64_t) * (nb + 1 + nb / SCAN_TILE + 64)));
@@ -1273,7 +1275,7 @@ int build_tree(Plan& P, const void* y, int64_t ns, const void* x, int64_t nt, in
   CK(T.m2l_meta.reserve(sizeof(int) * (216 + 1 + nb / SCAN_TILE + 64)));
   unsigned* meta = T.m2l_meta.as<unsigned>();   // [0..216) per (neighbour, class), [216] total
   CK(cudaMemsetAsync(meta, 0, sizeof(unsigned) * 217, st));
-  const int vmin = P.bc == KAFMM_BC_PXYZ ? 1 : 2;
+  const int vmin = periodic_mask(P.bc) ? 1 : 2;
   KL k_tree_stats<<<grid_for(nb, 256), 256, 0, st>>>(tv, T.vtab.as<int32_t>(), stats, T.vocc.as<uint4>(),
                                                    vmin, T.m2l_cnt.as<int>(), meta);
   scan_excl<int>(T.m2l_cnt.as<int>(), T.m2l_base.as<int>(), nb, nullptr,
@@ -1292,7 +1294,7 @@ int m2l_pairs_sort(Plan& P) {
   cudaStream_t st = P.stream;
   const int nb = T.nbox;
   const int64_t n = T.m2l_npairs;
-  const int vmin = P.bc == KAFMM_BC_PXYZ ? 1 : 2;
+  const int vmin = periodic_mask(P.bc) ? 1 : 2;
   CK(P.m2l_keys.reserve(sizeof(uint64_t) * 2 * (n + 1)));
   CK(P.m2l_vals.reserve(sizeof(uint32_t) * 2 * (n + 1)));
   CK(P.m2l_pbox.reserve(sizeof(int) * (n + 1)));

@@ -22,7 +22,7 @@ LAPLACE, STOKESLET, RPY, STOKES_DL, STOKES_REG, LAPLACE_QD, STOKES_PVEL = 0, 1, 
 STOKES_PVEL_GRAD, STOKES_PVEL_LAPL, STOKES_PVEL_TRACTION = 7, 8, 9
 STOKES_DL_GRAD, STOKES_DL_LAPL, STOKES_DL_TRACTION = 10, 11, 12
 LAPLACE_QUAD = 13
-BC_OPEN, BC_PXYZ, BC_WALL = 0, 3, 4
+BC_OPEN, BC_PX, BC_PXY, BC_PXYZ, BC_WALL, BC_WALL_PX, BC_WALL_PXY = 0, 1, 2, 3, 4, 5, 6
 F32, F64 = 0, 1
 OPT_PRECISION, OPT_ML_VARIANT, OPT_STREAM, OPT_NEAR_ONLY, OPT_KAHAN, OPT_TC_SPLIT = 1, 2, 3, 4, 5, 6
 OPT_SYNC, OPT_TC_STAGES, OPT_TC_RANGES, OPT_RPY_CONTACT, OPT_TC_TILING = 7, 8, 9, 10, 11

@@ -34,11 +34,13 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     lib.kafmm_last_error.restype = ctypes.c_char_p
     lib.kafmm_last_error.argtypes = [ctypes.c_void_p]
     out = ctypes.c_void_p(1)
-    # kernel out of range, PX boundary, p or q out of range, charges + dipoles and quadrupoles
-    # (open boundary only) with the triply periodic boundary, and the wall with a derivative
-    # form or Laplace
-    for args in [(14, 0, 8, 64), (-1, 0, 8, 64), (1, 1, 8, 64), (1, 0, 1, 64), (1, 0, 8, 0), (1, 0, 17, 64),
-                 (5, 3, 8, 64), (13, 3, 8, 64), (9, 4, 8, 64), (0, 4, 8, 64)]:
+    # kernel or boundary out of range, p or q out of range, charges + dipoles and quadrupoles
+    # with the triply periodic boundary, the wall (alone or with PX / PXY) with a derivative
+    # form or Laplace, and the StokesPVel-table kernels (double layer, StokesPVel, their
+    # derivative forms) with the singly or doubly periodic boundary
+    for args in [(14, 0, 8, 64), (-1, 0, 8, 64), (1, 7, 8, 64), (1, -1, 8, 64), (1, 0, 1, 64), (1, 0, 8, 0),
+                 (1, 0, 17, 64), (5, 3, 8, 64), (13, 3, 8, 64), (9, 4, 8, 64), (0, 4, 8, 64), (0, 5, 8, 64),
+                 (4, 6, 8, 64), (3, 1, 8, 64), (6, 2, 8, 64), (9, 2, 8, 64), (12, 1, 8, 64)]:
         assert lib.kafmm_plan(*args, ctypes.byref(out)) == -1
         assert out.value is None
         assert len(lib.kafmm_last_error(None)) > 0

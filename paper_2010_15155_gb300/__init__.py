@@ -18,7 +18,9 @@ Example (Stokeslet, sources = targets, forces f, mixed precision on the tensor c
 Other problems: ``K.LAPLACE`` (q -> phi), ``K.RPY`` ([f, b] -> [u, lap u], then
 ``K.kafmm_rpy_velocity`` for sphere velocities), ``K.STOKES_DL`` (D -> [p, u]),
 ``K.STOKES_REG`` ([f, eps] -> u), ``K.LAPLACE_QD`` ([q, d] -> [phi, grad, Hessian]),
-``K.STOKES_PVEL`` ([f, q] -> [p, u]).  ``bc=K.BC_PXYZ`` for triply periodic sums,
+``K.STOKES_PVEL`` ([f, q] -> [p, u]).  ``bc=K.BC_PX``, ``K.BC_PXY`` or ``K.BC_PXYZ`` for
+singly, doubly or triply periodic sums, ``K.BC_WALL`` (``K.BC_WALL_PX``, ``K.BC_WALL_PXY``) for
+a no-slip wall (with periodicity along it),
 ``precision=K.PREC_FP64`` for the plain FP64 form, ``set_points_batched`` for many independent
 problems in one forest, ``K.kafmm_autotune`` to time the tensor-core configurations.
 """

@@ -802,7 +802,8 @@ void orc_stokeslet_wall(const double* x, int64_t nt, const double* y, int64_t ns
  * lattice (axes = 2: n = (a, b, 0)), taken in square shells max|n| = s for s from nmin up,
  * with the partial sums S_N over nmin <= max|n| <= N written out for N = n0 2^k, k < nlev
  * (the caller extrapolates N -> infinity).  kernel 0: Laplace 1/(4 pi r), 1 x 1 blocks;
- * kernel 1: Stokeslet (delta_ij / r + r_i r_j / r^3) / (8 pi), 3 x 3 blocks.
+ * kernel 1: Stokeslet (delta_ij / r + r_i r_j / r^3) / (8 pi), 3 x 3 blocks; kernel 2:
+ * StokesPVel [p, u] <- [f, q] (as orc_stokes_pvel), 4 x 4 blocks.
  * out[k][kt nt][kt ns] (row: target a, output component i; column: source b, component j).
  * Pairs at zero distance are skipped.
  * ------------------------------------------------------------------------------------- */
@@ -815,19 +816,28 @@ static void lattice_pair(int kernel, const double r[3], double* m) {
     return;
   }
   const double r3 = rr * rn;
+  if (kernel == 2) {   /* StokesPVel block: rows [p, u], columns [f, q] (Eqs. stkslp, stkslvel) */
+    for (int j = 0; j < 3; ++j) m[j] += r[j] / (4.0 * PI * r3);
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j)
+        m[4 * (1 + i) + j] += ((i == j ? 1.0 / rn : 0.0) + r[i] * r[j] / r3) / (8.0 * PI);
+      m[4 * (1 + i) + 3] += -r[i] / (8.0 * PI * r3);
+    }
+    return;
+  }
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) m[3 * i + j] += ((i == j ? 1.0 / rn : 0.0) + r[i] * r[j] / r3) / (8.0 * PI);
 }
 
 void orc_lattice_matrix(int kernel, int axes, const double* x, int64_t nt, const double* y,
                         int64_t ns, double L, int nmin, int n0, int nlev, double* out) {
-  const int kt = kernel == 0 ? 1 : 3;
+  const int kt = kernel == 0 ? 1 : (kernel == 1 ? 3 : 4);
   const int64_t rows = kt * nt, cols = kt * ns;
   const int nmax = n0 << (nlev - 1);
 #pragma omp parallel for collapse(2) schedule(dynamic, 8)
   for (int64_t a = 0; a < nt; ++a)
     for (int64_t b = 0; b < ns; ++b) {
-      double m[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      double m[16] = {0};
       int lev = 0;
       for (int s = nmin; s <= nmax; ++s) {
         /* the images of shell s: (+-s, 0) for the 1D lattice; the square ring max(|i|,|j|) = s

@@ -27,6 +27,11 @@ the paper).  The reading used here for PX and PXY:
   nothing for a neutral density and removes the divergent part.
 * No-slip wall with PX / PXY (``wall_table``, ``wall_rpy_table``, ``wall_blake``): the image
   system of ``oracle.wall`` with every sum taken over the lattice.
+* StokesPVel table ([f, q] and double-layer sources): only the forces must be neutral; the
+  fields of q and D fall off like 1/r^2 and are odd, so their symmetric sums converge.  The
+  far-image operator is projected on the force columns only.  Being real-space image sums of
+  the field outside the cell, these need none of the moment shifts of the triply periodic
+  Ewald convention (pinned by the KAFMM's convergence to the lattice sum).
 """
 from __future__ import annotations
 
@@ -44,8 +49,13 @@ AXES = {"px": 1, "pxy": 2}
 EXTRAP = {"px": (16, 8), "pxy": (4, 6)}
 
 # source columns that carry the kernel's monopole (must sum to zero)
+# (StokesPVel: the forces; its sources q and the double layer's D have fields that fall off
+# like 1/r^2 and odd, whose symmetric sums converge without a condition)
 MONOPOLE = {"laplace": [0], "laplace_pgradgrad": [0], "laplace_qd": [0], "laplace_quad": [],
-            "stokeslet": [0, 1, 2], "stokeslet_reg": [0, 1, 2], "rpy": [0, 1, 2]}
+            "stokeslet": [0, 1, 2], "stokeslet_reg": [0, 1, 2], "rpy": [0, 1, 2],
+            "stokes_pvel": [0, 1, 2], "stokes_pvel_grad": [0, 1, 2], "stokes_pvel_lapl": [0, 1, 2],
+            "stokes_pvel_traction": [0, 1, 2], "stokes_dl": [], "stokes_dl_grad": [], "stokes_dl_lapl": [],
+            "stokes_dl_traction": []}
 
 
 def _lib():
@@ -163,13 +173,13 @@ def wall_rpy_table(x, y, fb, bc: str, zw: float, L: float = 1.0) -> np.ndarray:
 
 def lattice_matrix(ml: str, x, y, bc: str, L: float = 1.0, nmin: int = 2, n0: int | None = None,
                    nlev: int | None = None) -> np.ndarray:
-    """Kernel matrix (ml 'laplace' or 'stokeslet') summed over the images with
+    """Kernel matrix (ml 'laplace', 'stokeslet' or 'stokes_pvel') summed over the images with
     nmin <= max|n| <= N, extrapolated in N.  Rows: targets x (by component), columns:
     sources y (by component)."""
     n0 = n0 or EXTRAP[bc][0]
     nlev = nlev or EXTRAP[bc][1]
-    kid = {"laplace": 0, "stokeslet": 1}[ml]
-    kt = 1 if kid == 0 else 3
+    kid = {"laplace": 0, "stokeslet": 1, "stokes_pvel": 2}[ml]
+    kt = (1, 3, 4)[kid]
     x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1, 3))
     y = np.ascontiguousarray(np.asarray(y, np.float64).reshape(-1, 3))
     out = np.zeros((nlev, kt * len(x), kt * len(y)))
@@ -188,8 +198,9 @@ def t_m2l(ml: str, p: int, bc: str, L: float = 1.0, origin: float = 0.0) -> np.n
     dc = c + ALPHA["dc"] * r0 * unit
     ue = c + ALPHA["ue"] * r0 * unit
     T = lattice_matrix(ml, dc, ue, bc, L)
-    kt = 1 if ml == "laplace" else 3
+    kt = {"laplace": 1, "stokeslet": 3, "stokes_pvel": 4}[ml]
     n = len(unit)
     Tv = T.reshape(T.shape[0], n, kt)
-    Tv -= Tv.mean(axis=1, keepdims=True)
+    mono = [0] if ml == "laplace" else [0, 1, 2]    # the StokesPVel q column converges as is
+    Tv[:, :, mono] -= Tv[:, :, mono].mean(axis=1, keepdims=True)
     return Tv.reshape(T.shape)

@@ -267,3 +267,47 @@ def test_periodic_rpy_wall_table_equals_the_definition():
     ref = La._extrapolated(lambda xs: Wl.blake_rpy(xs, y, fb, 0.5), x, 3, "px", 1.0, 16, 6)
     got = La.wall_rpy_table(x, y, fb, "px", 0.5)[:, :3]
     assert D.rel_l2(got, ref) < 1e-9
+
+
+def test_doubly_periodic_pvel_and_double_layer_plane_means():
+    """Mean over x, y outside a layer of StokesPVel and double-layer sources (1D Stokes
+    equations with mu = 1): forces give the tangential flow -sum f |z - z_j| / (2A) and no
+    normal flow; a source q sends -q / (4A) each way (its flux -q/2 split between the two
+    sides); a double layer D is the force dipole -sym(D) plus the source tr D, so the mean flow
+    jumps by -(D_az + D_za) / (2A) tangentially and by -tr D / (2A) normally across it."""
+    rng = np.random.default_rng(19)
+    y = 0.3 + 0.4 * rng.random((20, 3))
+    s = rng.standard_normal((20, 4))
+    s[:, :3] -= s[:, :3].mean(axis=0)
+    for z in (-0.2, 1.2):
+        g = La.lattice_sum("stokes_pvel", _plane_grid(z), y, s, "pxy").mean(axis=0)
+        sg, dz = np.sign(z - y[:, 2]), np.abs(z - y[:, 2])
+        ref = np.array([np.sum(s[:, 2] * sg) / 2, -0.5 * np.sum(s[:, 0] * dz), -0.5 * np.sum(s[:, 1] * dz),
+                        -np.sum(s[:, 3] * sg) / 4])
+        assert np.abs(g - ref).max() < 1e-8, (z, g, ref)
+    Dd = rng.standard_normal((20, 9))
+    lo = La.lattice_sum("stokes_dl", _plane_grid(-0.2), y, Dd, "pxy").mean(axis=0)
+    hi = La.lattice_sum("stokes_dl", _plane_grid(1.2), y, Dd, "pxy").mean(axis=0)
+    Dm = Dd.reshape(-1, 3, 3)
+    jump = np.array([0.0, -np.sum(Dm[:, 0, 2] + Dm[:, 2, 0]) / 2, -np.sum(Dm[:, 1, 2] + Dm[:, 2, 1]) / 2,
+                     -np.sum(np.trace(Dm, axis1=1, axis2=2)) / 2])
+    assert np.abs((hi - lo) - jump).max() < 1e-8, (hi - lo, jump)
+
+
+@pytest.mark.parametrize("bc,problem,kernel", [("px", "stokes_pvel", "stokes_pvel"),
+                                               ("pxy", "stokes_dl_pv", "stokes_dl")])
+def test_kafmm_pvel_table_converges_to_lattice_sum(bc, problem, kernel):
+    """The StokesPVel table ([f, q] and double-layer sources) with the far-image operator of
+    the line or plane lattice converges to the lattice sum: unlike the triply periodic Ewald
+    convention, the real-space image sums depend only on the field outside the cell, so no
+    moment shifts enter."""
+    rng = np.random.default_rng(20)
+    pts = rng.random((200, 3))
+    ks = 4 if kernel == "stokes_pvel" else 9
+    s = rng.standard_normal((200, ks))
+    if ks == 4:
+        s[:, :3] -= s[:, :3].mean(axis=0)
+    ref = La.lattice_sum(kernel, pts, pts, s, bc)
+    errs = [D.rel_l2(KAFMM(problem, p, 16, bc=bc, t_m2l=_t("stokes_pvel", p, bc)).evaluate(pts, s), ref)
+            for p in (4, 6)]
+    assert errs[1] < errs[0] / 10 and errs[1] < 1e-3, errs
